@@ -1,0 +1,129 @@
+"""Pins of the oracle's particle-learning cycle (paper Sections 2 and 4).
+
+- Known variances: particle learning reduces to a fully adapted particle filter
+  whose filtered means, variances and log-likelihood must agree with the Kalman
+  filter (the closed form of the Bayes filter for the linear Gaussian model)
+  within Monte Carlo error.
+- Known states: the sufficient-statistic recursion must reproduce the conjugate
+  inverse-gamma posterior IG(a0 + T/2, b0 + sum r^2 / 2) exactly, and the
+  parameter draws must follow that law.
+- Prior: the paper's priors IG(5, 4) and IG(5, 0.4) have means equal to the
+  true sigma^2 = 1 and tau^2 = 0.1, which pins the shape/scale reading.
+
+Tolerances are Monte Carlo bounds calibrated on seeds other than the ones used
+here, with a wide margin; any systematic error (a dropped term, the wrong time
+index, a transposed variance) is tens of standard errors away.
+"""
+import numpy as np
+import pytest
+from scipy import stats
+
+from paper_1212_1639_gb300 import synth
+
+
+@pytest.fixture(scope="module")
+def series():
+    x, y = synth.local_level_series(1212, 100, sigma2=1.0, tau2=0.1)
+    return x, y
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("scheme", [0, 1, 2, 3])
+def test_known_variances_match_kalman(orc, series, precision, scheme):
+    _, y = series
+    n = 1 << 15
+    km, kv, kll = orc.kalman(y, 0.0, 10.0, 1.0, 0.1)
+    cfg = orc.make_config(n, seed=100 + scheme, scheme=scheme, precision=precision,
+                          known_variances=True, sigma2=1.0, tau2=0.1)
+    f = orc.Filter(cfg)
+    z, vr = [], []
+    for t in range(y.size):
+        f.step(y[t])
+        e = f.estimate()
+        assert e["t"] == t + 1
+        z.append((e["x_mean"] - km[t]) / np.sqrt(kv[t] / n))
+        vr.append(e["x_var"] / kv[t])
+    z = np.array(z)
+    assert np.max(np.abs(z)) < 12, np.max(np.abs(z))
+    assert np.sqrt(np.mean(z ** 2)) < 4
+    assert np.max(np.abs(np.array(vr[5:]) - 1)) < 0.1
+    assert abs(f.estimate()["log_marglik"] - kll) < 0.25
+    # known-variance mode leaves the parameters untouched
+    s = f.state()
+    assert np.all(s["sigma2"] == np.float32(1.0) if precision == 0 else s["sigma2"] == 1.0)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_known_states_conjugate_inverse_gamma(orc, precision):
+    T = 50
+    x, y = synth.local_level_series(7, T, sigma2=1.0, tau2=0.1)
+    if precision == 0:
+        # the FP32 state path works with binary32 states and observations
+        x = x.astype(np.float32).astype(np.float64)
+        y = y.astype(np.float32).astype(np.float64)
+    n = 20_000
+    a0s, b0s, a0t, b0t = 3.0, 2.0, 5.0, 0.4
+    cfg = orc.make_config(n, seed=3, precision=precision, a_sigma=a0s, b_sigma=b0s,
+                          a_tau=a0t, b_tau=b0t)
+    out, rc = orc.suffstat_known_states(cfg, x, y)
+    assert rc == 0
+    bs_ref = b0s + 0.5 * np.sum((y - x[1:]) ** 2)
+    bt_ref = b0t + 0.5 * np.sum(np.diff(x) ** 2)
+    tol = 1e-12 if precision == 1 else 1e-6
+    assert np.allclose(out["b_sigma"], bs_ref, rtol=tol, atol=0)
+    assert np.allclose(out["b_tau"], bt_ref, rtol=tol, atol=0)
+    a_s, a_t = a0s + T / 2, a0t + T / 2
+    for key, a, b in (("sigma2", a_s, bs_ref), ("tau2", a_t, bt_ref)):
+        d = out[key]
+        mean, sd = b / (a - 1), b / ((a - 1) * np.sqrt(a - 2))
+        assert abs(d.mean() - mean) < 5 * sd / np.sqrt(n)
+        assert stats.kstest(d, stats.invgamma(a, scale=b).cdf).pvalue > 1e-4
+
+
+def test_prior_means_pin_shape_scale(orc):
+    n = 1 << 16
+    cfg = orc.make_config(n, seed=11, precision=1, a_sigma=5.0, b_sigma=4.0, a_tau=5.0,
+                          b_tau=0.4, x0_mean=0.0, x0_var=10.0)
+    s = orc.Filter(cfg).state()
+    # IG(5, 4): mean 4/4 = 1 = sigma^2; IG(5, 0.4): mean 0.1 = tau^2 (paper Section 4)
+    for key, mean, a, b in (("sigma2", 1.0, 5.0, 4.0), ("tau2", 0.1, 5.0, 0.4)):
+        sd = b / ((a - 1) * np.sqrt(a - 2))
+        assert abs(s[key].mean() - mean) < 5 * sd / np.sqrt(n)
+        assert stats.kstest(s[key], stats.invgamma(a, scale=b).cdf).pvalue > 1e-4
+    assert abs(s["x"].mean()) < 5 * np.sqrt(10 / n)
+    assert abs(s["x"].var() / 10 - 1) < 5 * np.sqrt(2 / n)
+    assert np.all(s["b_sigma"] == 4.0) and np.all(s["b_tau"] == 0.4)
+
+
+def test_learning_concentrates_near_truth(orc):
+    """Unknown variances, T = 500: the posterior means land near the truth."""
+    x, y = synth.local_level_series(1639, 500, sigma2=1.0, tau2=0.1)
+    cfg = orc.make_config(1 << 13, seed=5, precision=1)
+    f = orc.Filter(cfg)
+    f.run(y)
+    e = f.estimate()
+    assert 0.7 < e["sigma2_mean"] < 1.4
+    assert 0.03 < e["tau2_mean"] < 0.3
+    assert abs(e["x_mean"] - x[-1]) < 4 * np.sqrt(e["x_var"] + 0.5)
+    assert np.isfinite(e["log_marglik"])
+
+
+def test_fp32_and_fp64_agree_statistically(orc, series):
+    _, y = series
+    ests = {}
+    for prec in (0, 1):
+        f = orc.Filter(orc.make_config(1 << 14, seed=21, precision=prec))
+        f.run(y[:60])
+        ests[prec] = f.estimate()
+    for k in ("x_mean", "sigma2_mean", "tau2_mean"):
+        assert abs(ests[0][k] - ests[1][k]) < 0.1 * max(1.0, abs(ests[1][k]))
+    assert abs(ests[0]["log_marglik"] - ests[1]["log_marglik"]) < 1.0
+
+
+def test_fp32_state_is_binary32_and_fixed_point(orc):
+    f = orc.Filter(orc.make_config(64, seed=1, precision=0))
+    f.step(0.3)
+    r = f.state_raw()
+    assert r["x"].dtype == np.float32 and r["b_sigma"].dtype == np.uint64
+    d = f.state()
+    assert np.array_equal(d["b_sigma"], r["b_sigma"].astype(np.float64) * 2.0 ** -32)

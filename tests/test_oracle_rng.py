@@ -1,0 +1,127 @@
+"""Pins of the oracle's counter-based RNG and its uniform / normal / gamma draws.
+
+Philox4x32-10 and Philox4x64-10 (Salmon et al. 2011) are checked against two
+independent implementations: triton's (run by its CPU interpreter) for 4x32 and
+numpy's Philox bit generator for 4x64.  The derived draws are checked against
+their distributions.
+"""
+import os
+import subprocess
+import sys
+import textwrap
+
+import numpy as np
+import pytest
+from scipy import stats
+
+
+def test_philox4x64_matches_numpy(orc):
+    rng = np.random.default_rng(7)
+    ctr = rng.integers(1, 2**63, size=(64, 4), dtype=np.uint64)
+    key = rng.integers(0, 2**63, size=(64, 2), dtype=np.uint64)
+    ours = orc.philox4x64(ctr, key)
+    for i in range(64):
+        prev = ctr[i].copy()
+        prev[0] -= np.uint64(1)  # numpy increments the counter before each block
+        g = np.random.Philox(counter=prev, key=key[i])
+        assert np.array_equal(g.random_raw(4).astype(np.uint64), ours[i]), i
+
+
+_TRITON_SCRIPT = textwrap.dedent("""
+    import os, sys
+    os.environ["TRITON_INTERPRET"] = "1"
+    import numpy as np, torch, triton, triton.language as tl
+
+    @triton.jit
+    def k(c_ptr, seed_ptr, out_ptr, n: tl.constexpr):
+        i = tl.arange(0, n)
+        c0 = tl.load(c_ptr + 4 * i + 0)
+        c1 = tl.load(c_ptr + 4 * i + 1)
+        c2 = tl.load(c_ptr + 4 * i + 2)
+        c3 = tl.load(c_ptr + 4 * i + 3)
+        s = tl.load(seed_ptr + i)
+        a, b, c, d = tl.philox(s, c0, c1, c2, c3)
+        tl.store(out_ptr + 4 * i + 0, a)
+        tl.store(out_ptr + 4 * i + 1, b)
+        tl.store(out_ptr + 4 * i + 2, c)
+        tl.store(out_ptr + 4 * i + 3, d)
+
+    data = np.load(sys.argv[1])
+    ctr = torch.from_numpy(data["ctr"].astype(np.int64).astype(np.int32))
+    seed = torch.from_numpy(data["seed"].astype(np.int64))
+    out = torch.zeros_like(ctr)
+    k[(1,)](ctr, seed, out, ctr.shape[0] // 4)
+    np.save(sys.argv[2], out.numpy().view(np.uint32))
+""")
+
+
+def test_philox4x32_matches_triton_interpreter(orc, tmp_path):
+    pytest.importorskip("triton")
+    pytest.importorskip("torch")
+    rng = np.random.default_rng(11)
+    n = 64
+    ctr = rng.integers(0, 2**32, size=(n, 4), dtype=np.uint64).astype(np.uint32)
+    seed = rng.integers(0, 2**63, size=n, dtype=np.int64)
+    key = np.stack([(seed & 0xFFFFFFFF).astype(np.uint32),
+                    (seed >> 32).astype(np.uint32)], axis=1)
+    ours = orc.philox4x32(ctr, key)
+    inp = tmp_path / "in.npz"
+    outp = tmp_path / "out.npy"
+    np.savez(inp, ctr=ctr.reshape(-1), seed=seed)
+    script = tmp_path / "tri.py"
+    script.write_text(_TRITON_SCRIPT)
+    env = dict(os.environ, TRITON_INTERPRET="1")
+    r = subprocess.run([sys.executable, str(script), str(inp), str(outp)], env=env,
+                       capture_output=True, text=True, timeout=600)
+    if r.returncode != 0:
+        pytest.skip("triton interpreter unavailable: " + r.stderr[-300:])
+    theirs = np.load(outp).reshape(n, 4)
+    assert np.array_equal(ours, theirs)
+
+
+def test_draw_counter_layout(orc):
+    # draw(seed, filter, t, j, purpose, attempt) = Philox4x32-10 with
+    # counter (j, t, filter, purpose | attempt << 8) and key (seed lo, seed hi).
+    seed = 0x123456789ABCDEF0
+    d = orc.draws(seed, 7, 5, 100, 3, orc.P_GAMMA_TAU, attempt=2)
+    ctr = np.array([[100 + i, 5, 7, orc.P_GAMMA_TAU | (2 << 8)] for i in range(3)], np.uint32)
+    key = np.array([[seed & 0xFFFFFFFF, seed >> 32]] * 3, np.uint32)
+    assert np.array_equal(d, orc.philox4x32(ctr, key))
+
+
+def test_uniform_f32_exact_grid_and_chisq(orc):
+    w = orc.draws(1, 0, 0, 0, 1 << 16, orc.P_STATE).reshape(-1)
+    u = orc.unif_f32(w)
+    assert u.min() > 0 and u.max() < 1
+    m = u.astype(np.float64) * 2**24
+    assert np.all(np.mod(m, 2) == 1)  # odd multiples of 2^-24: (2*(w>>9)+1) * 2^-24
+    assert np.array_equal(m, 2.0 * (w >> 9).astype(np.float64) + 1.0)
+    counts = np.bincount((u * 64).astype(int), minlength=64)
+    assert stats.chisquare(counts).pvalue > 1e-4
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_box_muller_normal(orc, dtype):
+    z = orc.normals(3, 0, 9, orc.P_STATE, 200_000, dtype).astype(np.float64)
+    assert abs(z.mean()) < 5 / np.sqrt(z.size)
+    assert abs(z.var() - 1) < 5 * np.sqrt(2 / z.size)
+    assert stats.kstest(z, "norm").pvalue > 1e-4
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+@pytest.mark.parametrize("a", [1.0, 3.0, 5.0, 50.5])
+def test_gamma_marsaglia_tsang(orc, dtype, a):
+    g, fail = orc.gammas(a, 5, 1, 3, orc.P_GAMMA_SIGMA, 100_000, dtype)
+    assert fail == 0
+    assert stats.kstest(g.astype(np.float64), stats.gamma(a).cdf).pvalue > 1e-4
+    assert abs(g.mean() - a) < 5 * np.sqrt(a / g.size)
+
+
+def test_streams_differ_by_purpose_and_time(orc):
+    a = orc.draws(9, 0, 0, 0, 1024, orc.P_STATE)
+    b = orc.draws(9, 0, 0, 0, 1024, orc.P_GAMMA_SIGMA)
+    c = orc.draws(9, 0, 1, 0, 1024, orc.P_STATE)
+    d = orc.draws(9, 1, 0, 0, 1024, orc.P_STATE)
+    e = orc.draws(9, 0, 0, 0, 1024, orc.P_STATE, attempt=1)
+    words = [x.tobytes() for x in (a, b, c, d, e)]
+    assert len(set(words)) == 5
