@@ -1,0 +1,421 @@
+#!/usr/bin/env python3
+"""Benchmark of the particle-learning cycle (arXiv 1212.1639) on GB300.
+
+Workload (one "step" = one full cycle: weights, CDF, resampling, propagation):
+the local-level model of the paper's Section 4 at scale -- one filter, N = 2^20
+particles, FP32 state, systematic resampling, observations from a seeded
+series of T = 1000 (x_0 = 0, sigma^2 = 1, tau^2 = 0.1), IG(3, 2) priors.
+
+value  : particle-steps/s over the K timed cycles, device time from CUDA events
+         on the filter's stream, inputs resident in HBM; the 90 MB working set
+         fits in L2, so L2 is flushed (256 MB write) before every timed cycle,
+         outside the events.
+e2e    : the same metric through the C ABI with host buffers: each step sends
+         one observation from host memory (pf_step) and reads the posterior
+         summaries back (pf_estimate), wall-clock timed.
+roofline: the dominant kernel's algorithmic bytes per launch / its mean
+         CUDA-event duration (pf_step_profiled), against the measured copy
+         bandwidth in MEASURED_PEAKS.json.
+Extra keys: the same cycle at N = 2^24 (the single-filter target size) and
+with multinomial resampling.
+
+--impl reference times the CPU oracle (single-threaded) on a bounded sample of
+the same workload.  Under torchrun every rank runs its own independent filter
+(no collective on the data path; weak scaling).
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle_steps_per_sec"
+UNIT = "particle-steps/s"
+N_DEFAULT = 1 << 20
+T_SERIES = 1000
+L2_FLUSH_BYTES = 256 << 20
+
+# Algorithmic bytes per particle per launch, FP32 state:
+BYTES_PER_PARTICLE = {
+    "weights": 12 + 4,            # read x, sigma2, tau2; write l
+    "scan": 4 + 8,                # read l; write Q
+    "spacing_scan": 8,            # write S
+    "merge_systematic": 8 + 4,    # read Q; write ancestors
+    "merge_multinomial": 8 + 8 + 4,  # read Q and S; write ancestors
+    "cutpoint_search": 8 + 4,     # read Q; write I
+    "cutpoint_method": 4 + 8 + 4,  # read I, Q at the start; write ancestors
+    "propagate": 4 + 28 + 28,     # read ancestor; gather 28 B record; write 28 B record
+}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=200)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--n", type=int, default=N_DEFAULT)
+    p.add_argument("--scheme", default="systematic")
+    p.add_argument("--no-extra", action="store_true", help="skip the 2^24 and multinomial lines")
+    p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def kernels_hash():
+    h = hashlib.sha256()
+    for f in ("kernels.cuh", "device.cuh", "api.cu"):
+        h.update(open(os.path.join(ROOT, "paper_1212_1639_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel, n):
+    """dram bytes per launch from the committed ncu summary, scaled to n
+    particles; None if the kernels changed since the capture."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    rec = {}
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        k, v = line.split(":", 1)
+        rec[k.strip()] = v.strip()
+    if rec.get("kernels_hash") != kernels_hash():
+        return None
+    key = "%s_bytes_per_particle" % kernel
+    if key not in rec:
+        return None
+    return float(rec[key]) * n
+
+
+def time_cycles(f, y_dev, start, K, stream, flush):
+    """K timed cycles; L2 flushed before each, outside the events."""
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(K)]
+    for i in range(K):
+        if flush is not None:
+            flush.zero_()
+        ev[i][0].record(stream)
+        f.run(y_dev[start + i:start + i + 1])
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in ev)
+
+
+def kernel_profile(f, y, start, P, flush):
+    """Mean per-kernel durations (ms) over P profiled cycles."""
+    import torch
+    acc = {}
+    for i in range(P):
+        if flush is not None:
+            flush.zero_()
+            torch.cuda.synchronize()
+        for k, v in f.step_profiled(float(y[start + i])).items():
+            acc.setdefault(k, []).append(v)
+    return {k: sum(v) / len(v) for k, v in acc.items()}
+
+
+def run_config(pf, n, scheme, K, W, y, y_dev, rank, flush, stream):
+    import torch
+    f = pf.Filter(n, seed=1639 + rank, filter_id=rank, scheme=scheme, precision="fp32",
+                  stream=stream)
+    f.run(y_dev[:W])
+    f.sync()
+    return f
+
+
+def bench_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1212_1639_gb300 import pf, synth
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)  # flushes and events go on the filters' stream
+    n, K, W = args.n, args.steps, max(args.warmup, 3)
+    total_steps = W + K + 64
+    _, y = synth.local_level_series(1639, max(T_SERIES, total_steps), filter_id=rank)
+    y_dev = torch.from_numpy(y).cuda()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    f = run_config(pf, n, args.scheme, K, W, y, y_dev, rank, flush, stream)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    phys = int(vis.split(",")[local]) if vis and vis.split(",")[local].isdigit() else local
+    clk = Clocks(phys)
+    clk.start()
+    t_wall0 = time.perf_counter()
+    ms = time_cycles(f, y_dev, W, K, stream, flush)
+    t_wall1 = time.perf_counter()
+    clocks = clk.stop()
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    value = world * n * K / (ms / 1e3)
+
+    # per-kernel durations (live, CUDA events on the filter's stream)
+    prof = kernel_profile(f, y, W + K, 10, flush)
+    kernels = {}
+    hbm, hbm_kind = peaks()
+    for kname, kms in prof.items():
+        key = kname
+        if kname == "merge":
+            key = "merge_multinomial" if "multinomial" in args.scheme else "merge_systematic"
+        byts = BYTES_PER_PARTICLE[key] * n
+        kernels[kname] = {"ms": round(kms, 5), "bytes": byts,
+                          "gbs": round(byts / (kms / 1e3) / 1e9, 1)}
+    dom = max(prof, key=prof.get)
+    dkey = "merge_multinomial" if dom == "merge" and "multinomial" in args.scheme else (
+        "merge_systematic" if dom == "merge" else dom)
+    achieved = kernels[dom]["gbs"]
+    traffic = recorded_traffic(dkey, n)
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm,
+                "peak_kind": hbm_kind, "unit": "GB/s", "frac": round(achieved / hbm, 4),
+                "traffic": traffic, "algorithmic_bytes": kernels[dom]["bytes"]}
+    cycle_bytes = sum(v["bytes"] for v in kernels.values())
+    cycle_ms = sum(prof.values())
+
+    # end to end through the C ABI with host buffers
+    fe = pf.Filter(n, seed=7 + rank, filter_id=rank, scheme=args.scheme, precision="fp32",
+                   stream=stream)
+    fe.run(y[:W])
+    fe.sync()
+    Ke = min(K, 100)
+    e2e_s = 0.0
+    for i in range(Ke):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fe.step(float(y[W + i]))
+        est = fe.estimate()
+        e2e_s += time.perf_counter() - t0
+    assert est["t"] == W + Ke
+    if world > 1:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * n * Ke / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8,
+           "d2h_bytes_per_step": 104, "steps": Ke,
+           "note": "pf_step(y from host) + pf_estimate (reduction, 104-byte summary D2H, sync) per step; "
+                   "L2 flushed before each step outside the timer"}
+    fe.close()
+
+    extra = {}
+    if not args.no_extra and rank == 0:
+        # single-filter target size: 2^24 particles, working set 1.6 GB > L2
+        n24 = 1 << 24
+        f24 = pf.Filter(n24, seed=24, scheme=args.scheme, precision="fp32", stream=stream)
+        f24.run(y_dev[:3])
+        f24.sync()
+        K24 = min(K, 50)
+        ms24 = time_cycles(f24, y_dev, 3, K24, stream, None)
+        prof24 = kernel_profile(f24, y, 3 + K24, 5, None)
+        b24 = {k: BYTES_PER_PARTICLE["merge_systematic" if k == "merge" else k] * n24 for k in prof24}
+        extra["n_2p24"] = {
+            "value": n24 * K24 / (ms24 / 1e3), "unit": UNIT, "steps": K24,
+            "ms_per_step": ms24 / K24, "l2": "inputs larger than L2 (no flush)",
+            "cycle_hbm_frac": round(sum(b24.values()) / (ms24 / K24 / 1e3) / 1e9 / hbm, 4),
+            "kernels": {k: {"ms": round(v, 5), "gbs": round(b24[k] / (v / 1e3) / 1e9, 1)}
+                        for k, v in prof24.items()}}
+        f24.close()
+        if "multinomial" not in args.scheme:
+            fm = pf.Filter(n, seed=3, scheme="multinomial", precision="fp32", stream=stream)
+            fm.run(y_dev[:W])
+            fm.sync()
+            Km = min(K, 100)
+            msm = time_cycles(fm, y_dev, W, Km, stream, flush)
+            profm = kernel_profile(fm, y, W + Km, 5, flush)
+            extra["multinomial"] = {
+                "value": n * Km / (msm / 1e3), "unit": UNIT, "steps": Km, "ms_per_step": msm / Km,
+                "kernels": {k: round(v, 5) for k, v in profm.items()}}
+            fm.close()
+    f.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(n, args.scheme, y)
+
+    launches_per_cycle = len(prof)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+        "warmup": W, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "local-level particle learning, one filter per GPU, "
+                               "N=2^20, FP32 state, %s resampling, T=1000 seeded series" % args.scheme,
+                   "n_particles": n, "scheme": args.scheme, "precision": "fp32",
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "flushed (256 MB write) before every timed cycle, outside the events"},
+        "roofline": roofline,
+        "cycle": {"bytes": cycle_bytes, "ms_sum_of_kernels": round(cycle_ms, 5),
+                  "hbm_frac_of_graph_time": round(cycle_bytes / (ms / K / 1e3) / 1e9 / hbm, 4),
+                  "kernels": kernels},
+        "e2e": e2e,
+        "gpu_launches": launches_per_cycle * K,
+        "clocks": clocks,
+        "wall_s_timed": round(t_wall1 - t_wall0, 3),
+    }
+    line.update(extra)
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    if world > 1:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line))
+
+
+def cpu_baseline(n, scheme, y, budget_s=15.0):
+    """The oracle as it stands, single-threaded, on a bounded sample of the
+    workload: the same N and series, as many cycles as fit in ~budget_s."""
+    from oracle import oracle as orc
+
+    sch = {"systematic": orc.SYSTEMATIC, "multinomial": orc.MULTINOMIAL,
+           "systematic_cutpoint": orc.SYSTEMATIC_CUTPOINT,
+           "multinomial_cutpoint": orc.MULTINOMIAL_CUTPOINT}[scheme]
+    o = orc.Filter(orc.make_config(n, seed=1639, scheme=sch, precision=orc.FP32))
+    steps, t0 = 0, time.perf_counter()
+    while steps < 3 or (time.perf_counter() - t0 < budget_s and steps < 200):
+        o.step(y[steps])
+        steps += 1
+    dt = time.perf_counter() - t0
+    o.close()
+    return {"value": n * steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "N=%d particles, first %d cycles of the same series (FP32 state, %s)"
+                      % (n, steps, scheme)}
+
+
+def bench_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from oracle import oracle as orc
+    from paper_1212_1639_gb300 import synth
+
+    n = args.n
+    # each step is one cycle of the workload; the particle count is the full
+    # 2^20 so each step costs ~0.3 s of CPU -- bound the run to a few minutes
+    K = min(args.steps, 200)
+    W = min(args.warmup, 3)
+    _, y = synth.local_level_series(1639, max(T_SERIES, W + K + 1))
+    sch = {"systematic": orc.SYSTEMATIC, "multinomial": orc.MULTINOMIAL}.get(args.scheme, orc.SYSTEMATIC)
+    o = orc.Filter(orc.make_config(n, seed=1639, scheme=sch, precision=orc.FP32))
+    for i in range(W):
+        o.step(y[i])
+    t0 = time.perf_counter()
+    deadline = t0 + 240.0
+    done = 0
+    for i in range(K):
+        o.step(y[W + i])
+        done += 1
+        if time.perf_counter() > deadline:
+            break
+    dt = time.perf_counter() - t0
+    value = n * done / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": done, "warmup": W, "ms_per_step": dt * 1e3 / done, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "local-level particle learning, one filter, N=2^20, FP32 state, "
+                               "%s resampling, T=1000 seeded series" % args.scheme,
+                   "n_particles": n, "scheme": args.scheme, "precision": "fp32"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "N=%d, %d cycles (of %d requested) on one host core"
+                                   % (n, done, K)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        bench_reference(args)
+    else:
+        bench_ours(args)
+
+
+if __name__ == "__main__":
+    main()

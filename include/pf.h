@@ -1,0 +1,203 @@
+/*
+ * pf.h -- C ABI of the GB300 particle-learning library (libpf.so).
+ *
+ * Implements one full particle-learning cycle of McAlinn & Nakatsuma,
+ * "Parallel Resampling for Fully Parallelized Particle Filters"
+ * (arXiv 1212.1639): predictive-likelihood weights, the resampling CDF,
+ * parallel resampling against that CDF, and propagation of the state and its
+ * conjugate sufficient statistics (paper Section 2, Algorithm "Particle
+ * Learning"; Section 3, resampling; Section 4, the local-level model
+ *   y_t = x_t + v_t, v_t ~ N(0, sigma^2);  x_t = x_{t-1} + w_t, w_t ~ N(0, tau^2)
+ * with inverse-gamma priors on sigma^2 and tau^2).
+ *
+ * Every step runs on the GPU (sm_103a).  Host <-> device traffic is limited to
+ * the observations going in and summaries coming out (paper Section 3.2,
+ * closing paragraph: transfers only at the edges).
+ *
+ * Conventions
+ *  - All functions return a pf_status; none throws or exits.  On failure
+ *    pf_last_error() returns a thread-local message.
+ *  - A filter handle owns all of its device memory.  A handle is not
+ *    thread-safe; distinct handles are independent.
+ *  - A CUDA error or a device error word (lookback timeout, non-finite
+ *    weights, a gamma sampler that rejected 16 times) makes the handle
+ *    sticky-failed: every later call except pf_destroy returns that status.
+ *  - Calls are asynchronous on the handle's stream unless stated otherwise;
+ *    device errors surface at the next synchronising call (pf_estimate,
+ *    pf_sync, pf_get_*).
+ *  - Pointers documented as "host or device" may be either (the copy uses
+ *    unified addressing).
+ *  - Random draws are addressed by (seed, filter_id, t, particle, purpose):
+ *    counter-based Philox4x32-10, so results do not depend on launch shapes.
+ */
+#ifndef PF_H
+#define PF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PF_OK = 0,
+  PF_ERR_INVALID = 1,  /* bad argument (NULL, n out of range, bad enum, a0 < 1) */
+  PF_ERR_OOM = 2,      /* device or pinned allocation failed */
+  PF_ERR_CUDA = 3,     /* a CUDA runtime call failed */
+  PF_ERR_NUMERIC = 4,  /* non-finite or negative weights, all-zero CDF, gamma sampler failure */
+  PF_ERR_TIMEOUT = 5,  /* a bounded device wait (scan lookback) gave up */
+  PF_ERR_BUSY = 6      /* admission refused (memory budget) */
+} pf_status;
+
+/* Resampling scheme (paper Section 3.1).  All schemes draw ancestors from the
+ * same exact integer CDF Q (Q_i = sum_{l<=i} W_l, T = Q_{n-1}); slot j's
+ * ancestor is the first i with Q_i > position_j.
+ *  MULTINOMIAL            positions = order statistics of n iid uniforms on
+ *                         [0, T), generated in ascending order (exponential
+ *                         spacings), matched to the CDF by a merge.
+ *  SYSTEMATIC             positions = (j + u0) T / n, one uniform u0.
+ *  MULTINOMIAL_CUTPOINT   same positions as MULTINOMIAL, searched with the
+ *                         paper's parallelized cut-point search and cut-point
+ *                         method (Section 3.2); identical output.
+ *  SYSTEMATIC_CUTPOINT    same positions as SYSTEMATIC, cut-point search.
+ * Ancestors come out in nondecreasing order (the sorted expansion of the
+ * offspring counts). */
+typedef enum {
+  PF_MULTINOMIAL = 0,
+  PF_SYSTEMATIC = 1,
+  PF_MULTINOMIAL_CUTPOINT = 2,
+  PF_SYSTEMATIC_CUTPOINT = 3
+} pf_scheme;
+
+/* State precision (the paper's GPU(sp) and GPU(dp) modes, Section 4).
+ * FP32: x, sigma^2, tau^2 in binary32, sufficient statistics as exact 64-bit
+ *       fixed point (2^-32 units), log marginal likelihood accumulated in
+ *       binary64 from an exact 128-bit fixed-point particle sum.
+ * FP64: everything in binary64. */
+typedef enum { PF_FP32 = 0, PF_FP64 = 1 } pf_precision;
+
+/* Optional device allocator (e.g. a caching allocator).  alloc returns NULL on
+ * failure.  stream is the handle's cudaStream_t. */
+typedef void* (*pf_alloc_fn)(size_t bytes, void* stream, void* ctx);
+typedef void (*pf_free_fn)(void* ptr, void* stream, void* ctx);
+
+typedef struct {
+  uint64_t n_particles;    /* 1 .. PF_MAX_PARTICLES */
+  uint64_t seed;           /* Philox key */
+  uint32_t filter_id;      /* third Philox counter word: independent streams per filter */
+  int32_t scheme;          /* pf_scheme */
+  int32_t precision;       /* pf_precision */
+  int32_t known_variances; /* nonzero: sigma^2, tau^2 fixed (no learning; Kalman check) */
+  double x0_mean, x0_var;  /* x_0 ~ N(x0_mean, x0_var) */
+  double a_sigma, b_sigma; /* sigma^2 ~ IG(a_sigma, b_sigma), shape/scale, a_sigma >= 1 */
+  double a_tau, b_tau;     /* tau^2 ~ IG(a_tau, b_tau), a_tau >= 1 */
+  double sigma2, tau2;     /* used when known_variances != 0 */
+  void* stream;            /* cudaStream_t; NULL = legacy default stream */
+  pf_alloc_fn alloc;       /* NULL: cudaMallocAsync / cudaFreeAsync on stream */
+  pf_free_fn free;
+  void* alloc_ctx;
+} pf_config;
+
+#define PF_MAX_PARTICLES (1ull << 26)
+
+/* Posterior summaries after t observations (paper Section 2, the paragraph
+ * after Algorithm "Particle Learning": posterior statistics of theta from the
+ * particles).  Means and population variances over the particles; the log
+ * marginal likelihood log p(y_1..y_t) is the particle estimate
+ * sum_s [ log (1/n) sum_i p(y_s | z_{s-1}^(i)) ]. */
+typedef struct {
+  uint64_t t;
+  double x_mean, x_var;
+  double sigma2_mean, sigma2_var;
+  double tau2_mean, tau2_var;
+  double log_marglik;
+} pf_estimates;
+
+typedef struct pf_filter pf_filter;
+
+/* Create a filter and enqueue its initialisation (Algorithm "Particle
+ * Learning", Step 0: x_0, sigma^2, tau^2 drawn from the priors).  *out
+ * receives the handle.  Errors: PF_ERR_INVALID, PF_ERR_OOM, PF_ERR_CUDA. */
+pf_status pf_create(const pf_config* cfg, pf_filter** out);
+
+/* Enqueue one cycle for observation y = y_{t+1} (Steps 1-4): weights
+ * w_i ~ p(y | z_t^(i)), the CDF, resampling, propagation of x, update of the
+ * sufficient statistics, draw of sigma^2 and tau^2.  Asynchronous. */
+pf_status pf_step(pf_filter* f, double y);
+
+/* Enqueue n_steps cycles for the observations y[0..n_steps) (host or device
+ * pointer, binary64).  Replays a CUDA graph of one cycle. */
+pf_status pf_run(pf_filter* f, const double* y, uint32_t n_steps);
+
+/* Reduce the particles to posterior summaries (paper Section 2) and copy
+ * them to *out (host).  Synchronises the handle's stream. */
+pf_status pf_estimate(pf_filter* f, pf_estimates* out);
+
+/* Wait for all enqueued work and check the device error word. */
+pf_status pf_sync(pf_filter* f);
+
+/* Measurement: run one cycle exactly as pf_step does, but with each kernel
+ * launched on its own (no graph) and bracketed by CUDA events on the
+ * handle's stream.  Writes up to max_kernels kernel durations in
+ * milliseconds to kernel_ms (host), their static names to kernel_names (host,
+ * may be NULL) and the count to *n_kernels.  Synchronises. */
+pf_status pf_step_profiled(pf_filter* f, double y, float* kernel_ms, const char** kernel_names,
+                           int max_kernels, int* n_kernels);
+
+/* Copy the current particles out (paper Section 4, "Store": optional).
+ * Buffers are host or device; NULL skips an array.  FP32 filters write
+ * float x/sigma2/tau2 and uint64 fixed-point (2^-32) b_sigma/b_tau; FP64
+ * filters write doubles.  Synchronises. */
+pf_status pf_get_particles(pf_filter* f, void* x, void* sigma2, void* tau2, void* b_sigma,
+                           void* b_tau);
+
+/* Copy the last cycle's ancestor indices (n uint32, host or device) and,
+ * if Q is not NULL, its CDF (n uint64).  Synchronises. */
+pf_status pf_get_ancestors(pf_filter* f, uint32_t* anc, uint64_t* Q);
+
+/* Free every device buffer of the handle (after the stream's pending work).
+ * NULL-safe. */
+pf_status pf_destroy(pf_filter* f);
+
+/* Thread-local description of the last failure on this thread. */
+const char* pf_last_error(void);
+
+/* Resampling alone (paper Section 3): quantise the n binary32 weights
+ * w_dev[0..n) (nonnegative, not all zero; need not be normalised) to the
+ * exact CDF, W_i = floor(w_i 2^(k-e)) with k = 61 - ceil(log2 n) and
+ * max_i w_i = f 2^e, f in [1/2, 1), and write n ancestor indices to anc_dev
+ * (nondecreasing).  Draws use (seed, filter_id, t).  Device pointers on
+ * `stream` (cudaStream_t, may be NULL); the call borrows them.  Scratch is
+ * allocated with cudaMallocAsync on the stream and freed before return of the
+ * stream work.  Errors: PF_ERR_INVALID (NULL, n out of range, bad scheme);
+ * PF_ERR_NUMERIC (a negative / non-finite weight or all zero), detected on
+ * the device and reported after a stream synchronisation, which this call
+ * performs. */
+pf_status pf_resample(const float* w_dev, uint64_t n, uint64_t seed, uint32_t filter_id,
+                      uint32_t t, int32_t scheme, uint32_t* anc_dev, void* stream);
+
+/* The exact fixed-point resampling CDF of eq. (resample.cdf) for binary32
+ * weights: Q_dev[i] = sum_{l<=i} W_l (uint64), W as in pf_resample.  Device
+ * pointers; synchronises.  Errors as pf_resample. */
+pf_status pf_cdf(const float* w_dev, uint64_t n, uint64_t* Q_dev, void* stream);
+
+/* Algorithm "Parallelized Cut-Point Search" (paper Section 3.2) on a finished
+ * CDF Q_dev[0..n) (nondecreasing, Q_{n-1} = T > 0, T <= 2^62): writes the
+ * cut-points I_dev[k] = min{i : Q_i / T > k / n}, k = 0..n-1 (0-based), via
+ * L_i = ceil(n Q_i / T).  Device pointers; synchronises. */
+pf_status pf_cutpoint_search(const uint64_t* Q_dev, uint64_t n, uint32_t* I_dev, void* stream);
+
+/* Algorithm "Parallelized Cut-Point Method" (paper Section 3.2) for explicit
+ * integer positions U_dev[0..m) in [0, T): thread j starts at
+ * I_{floor(n U_j / T)} and climbs while Q_k <= U_j; anc_dev[j] = k.
+ * Device pointers; synchronises. */
+pf_status pf_cutpoint_method(const uint64_t* Q_dev, uint64_t n, const uint32_t* I_dev,
+                             const uint64_t* U_dev, uint64_t m, uint32_t* anc_dev,
+                             void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PF_H */

@@ -1,0 +1,741 @@
+// C ABI of the particle-learning library (declared in include/pf.h).
+//
+// Host logic only: argument checks, device allocation, launch configuration,
+// CUDA-graph capture of one cycle, the observation ring, and error mapping.
+// Every step of the method runs in the kernels of kernels.cuh.
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/pf.h"
+#include "kernels.cuh"
+
+using namespace pfk;
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+pf_status set_err(pf_status s, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return s;
+}
+
+#define CK(call)                                                                        \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      return set_err(PF_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));     \
+  } while (0)
+
+inline uint64_t cdiv(uint64_t a, uint64_t b) { return (a + b - 1) / b; }
+
+int cdf_shift(uint64_t n) {
+  int c = 0;
+  while ((1ull << c) < n) ++c;
+  return 61 - c;
+}
+
+constexpr uint32_t RING = 8192;          // observation ring (doubles)
+constexpr uint32_t RING_CHUNK = RING / 4;
+
+pf_status map_err(uint32_t err) {
+  if (err & ERR_TIMEOUT) return set_err(PF_ERR_TIMEOUT, "device look-back wait timed out");
+  if (err & ERR_WEIGHTS) return set_err(PF_ERR_NUMERIC, "weights negative, non-finite or all zero");
+  if (err & ERR_NUMERIC)
+    return set_err(PF_ERR_NUMERIC, "non-finite likelihood, empty CDF or gamma sampler failure");
+  return PF_OK;
+}
+
+}  // namespace
+
+struct pf_filter {
+  pf_config cfg;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  uint64_t n = 0;
+  int k = 0;
+  uint32_t ntiles = 0;
+  bool fp64 = false, learn = true;
+  int scheme = 0;
+  std::vector<void*> allocs;
+  void* x[2] = {}; void* s2[2] = {}; void* t2[2] = {}; void* bs[2] = {}; void* bt[2] = {};
+  void* ell = nullptr;
+  uint64_t* Q = nullptr;
+  uint64_t* S = nullptr;
+  uint32_t* anc = nullptr;
+  uint32_t* I = nullptr;
+  uint64_t* stat_w[2] = {};
+  uint64_t* stat_e[2] = {};
+  void* part = nullptr;
+  double* part_est = nullptr;
+  Ctl* ctl = nullptr;
+  double* y_ring = nullptr;
+  double* y_pinned = nullptr;
+  Ctl* ctl_host = nullptr;  // pinned mirror for summaries
+  cudaEvent_t ring_ev[4] = {};
+  uint64_t host_t = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  pf_status sticky = PF_OK;
+};
+
+namespace {
+
+pf_status dev_alloc(pf_filter* f, size_t bytes, void** out) {
+  bytes = (bytes + 255) & ~size_t(255);
+  void* p = nullptr;
+  if (f->cfg.alloc) {
+    p = f->cfg.alloc(bytes, f->stream, f->cfg.alloc_ctx);
+    if (!p) return set_err(PF_ERR_OOM, "allocator callback returned NULL for %zu bytes", bytes);
+  } else {
+    cudaError_t e = cudaMallocAsync(&p, bytes, f->stream);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return set_err(e == cudaErrorMemoryAllocation ? PF_ERR_OOM : PF_ERR_CUDA,
+                     "cudaMallocAsync(%zu): %s", bytes, cudaGetErrorString(e));
+    }
+  }
+  if (((uintptr_t)p & 15) != 0) return set_err(PF_ERR_INVALID, "allocator returned a pointer not 16-byte aligned");
+  f->allocs.push_back(p);
+  *out = p;
+  return PF_OK;
+}
+
+void free_all(pf_filter* f) {
+  for (void* p : f->allocs) {
+    if (f->cfg.alloc && f->cfg.free) f->cfg.free(p, f->stream, f->cfg.alloc_ctx);
+    else if (!f->cfg.alloc) cudaFreeAsync(p, f->stream);
+  }
+  f->allocs.clear();
+}
+
+template <class R>
+FilterArgs<R> filter_args(pf_filter* f) {
+  typedef typename SuffT<R>::B B;
+  FilterArgs<R> a;
+  for (int p = 0; p < 2; ++p) {
+    a.st[p].x = (R*)f->x[p];
+    a.st[p].s2 = (R*)f->s2[p];
+    a.st[p].t2 = (R*)f->t2[p];
+    a.st[p].bs = (B*)f->bs[p];
+    a.st[p].bt = (B*)f->bt[p];
+    a.stat_w[p] = f->stat_w[p];
+    a.stat_e[p] = f->stat_e[p];
+  }
+  a.ell = (R*)f->ell;
+  a.Q = f->Q;
+  a.S = f->S;
+  a.anc = f->anc;
+  a.I = f->I;
+  a.part = f->part;
+  a.part_est = f->part_est;
+  a.ctl = f->ctl;
+  a.y_ring = f->y_ring;
+  a.cap = RING;
+  a.n = f->n;
+  a.ntiles = f->ntiles;
+  a.k = f->k;
+  a.seed = f->cfg.seed;
+  a.filter = f->cfg.filter_id;
+  a.x0_mean = f->cfg.x0_mean;
+  a.x0_var = f->cfg.x0_var;
+  a.a_sigma = f->cfg.a_sigma;
+  a.b_sigma = f->cfg.b_sigma;
+  a.a_tau = f->cfg.a_tau;
+  a.b_tau = f->cfg.b_tau;
+  a.sigma2 = f->cfg.sigma2;
+  a.tau2 = f->cfg.tau2;
+  return a;
+}
+
+// Optional per-kernel event timer (pf_step_profiled).
+struct KTimer {
+  static constexpr int MAX = 8;
+  cudaEvent_t ev[MAX + 1];
+  const char* names[MAX];
+  int count = 0;
+};
+inline void mark(KTimer* tm, const char* name, cudaStream_t s) {
+  if (!tm || tm->count >= KTimer::MAX) return;
+  tm->names[tm->count] = name;
+  cudaEventRecord(tm->ev[++tm->count], s);
+}
+
+bool is_multinomial(int scheme) { return scheme == PF_MULTINOMIAL || scheme == PF_MULTINOMIAL_CUTPOINT; }
+bool is_cutpoint(int scheme) { return scheme == PF_MULTINOMIAL_CUTPOINT || scheme == PF_SYSTEMATIC_CUTPOINT; }
+
+// Resampling kernels shared by the filter cycle and pf_resample: from a
+// finished CDF Q (and spacing prefix S) to ancestors.
+pf_status launch_resample(int scheme, const PosArgs& pa, uint64_t n, uint32_t* I,
+                          cudaStream_t s, KTimer* tm = nullptr) {
+  const bool multi = is_multinomial(scheme);
+  if (!is_cutpoint(scheme)) {
+    const unsigned grid = (unsigned)cdiv(2 * n, MERGE_D);
+    if (multi) k_merge<POS_MULTINOMIAL><<<grid, BLOCK, 0, s>>>(pa);
+    else k_merge<POS_SYSTEMATIC><<<grid, BLOCK, 0, s>>>(pa);
+    mark(tm, "merge", s);
+  } else {
+    const unsigned grid = (unsigned)cdiv(n, BLOCK);
+    k_cutpoint_search<<<grid, BLOCK, 0, s>>>(pa.Q, n, I);
+    mark(tm, "cutpoint_search", s);
+    if (multi) k_cutpoint_method<POS_MULTINOMIAL><<<grid, BLOCK, 0, s>>>(pa);
+    else k_cutpoint_method<POS_SYSTEMATIC><<<grid, BLOCK, 0, s>>>(pa);
+    mark(tm, "cutpoint_method", s);
+  }
+  CK(cudaGetLastError());
+  return PF_OK;
+}
+
+// One cycle (Steps 1-4), enqueued on f->stream; reads t and y on the device.
+template <class R>
+pf_status enqueue_cycle(pf_filter* f, KTimer* tm = nullptr) {
+  cudaStream_t s = f->stream;
+  FilterArgs<R> a = filter_args<R>(f);
+  const uint64_t n = f->n;
+  if (tm) cudaEventRecord(tm->ev[0], s);
+  k_weights<R><<<(unsigned)cdiv(n, (uint64_t)BLOCK * W_PER_THREAD), BLOCK, 0, s>>>(a);
+  mark(tm, "weights", s);
+  ScanArgs sa;
+  sa.src = f->ell;
+  sa.Q = f->Q;
+  sa.stat[0] = f->stat_w[0];
+  sa.stat[1] = f->stat_w[1];
+  sa.part = f->part;
+  sa.ctl = f->ctl;
+  sa.t_dev = &f->ctl->t;
+  sa.t_arg = 0;
+  sa.n = n;
+  sa.k = f->k;
+  sa.vec_ok = 1;
+  k_scan<FROM_LOGLIK, R><<<f->ntiles, BLOCK, 0, s>>>(sa);
+  mark(tm, "scan", s);
+  if (is_multinomial(f->scheme)) {
+    SpacingArgs sp;
+    sp.S = f->S;
+    sp.stat[0] = f->stat_e[0];
+    sp.stat[1] = f->stat_e[1];
+    sp.ctl = f->ctl;
+    sp.t_dev = &f->ctl->t;
+    sp.t_arg = 0;
+    sp.n = n;
+    sp.seed = f->cfg.seed;
+    sp.filter = f->cfg.filter_id;
+    k_spacing_scan<<<f->ntiles, BLOCK, 0, s>>>(sp);
+    mark(tm, "spacing_scan", s);
+  }
+  PosArgs pa;
+  pa.Q = f->Q;
+  pa.S = f->S;
+  pa.anc = f->anc;
+  pa.I = f->I;
+  pa.ctl = f->ctl;
+  pa.t_dev = &f->ctl->t;
+  pa.t_arg = 0;
+  pa.n = n;
+  pa.seed = f->cfg.seed;
+  pa.filter = f->cfg.filter_id;
+  pf_status st = launch_resample(f->scheme, pa, n, f->I, s, tm);
+  if (st != PF_OK) return st;
+  if (f->learn) k_propagate<R, true><<<(unsigned)cdiv(n, BLOCK), BLOCK, 0, s>>>(a);
+  else k_propagate<R, false><<<(unsigned)cdiv(n, BLOCK), BLOCK, 0, s>>>(a);
+  mark(tm, "propagate", s);
+  CK(cudaGetLastError());
+  return PF_OK;
+}
+
+pf_status build_graph(pf_filter* f) {
+  CK(cudaStreamBeginCapture(f->stream, cudaStreamCaptureModeThreadLocal));
+  pf_status st = f->fp64 ? enqueue_cycle<double>(f) : enqueue_cycle<float>(f);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(f->stream, &g);
+  if (st != PF_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  if (e != cudaSuccess) return set_err(PF_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+  f->graph = g;
+  CK(cudaGraphInstantiate(&f->exec, g, 0));
+  return PF_OK;
+}
+
+// Stage observations y[0..cnt) for device cycles host_t .. host_t+cnt-1 into
+// the ring (cnt never crosses a ring chunk boundary).
+pf_status stage_obs(pf_filter* f, const double* y, uint32_t cnt, bool dev_src) {
+  const uint32_t slot = (uint32_t)(f->host_t % RING);
+  const uint32_t chunk = slot / RING_CHUNK;
+  if (slot % RING_CHUNK == 0 && f->host_t >= RING) CK(cudaEventSynchronize(f->ring_ev[chunk]));
+  if (dev_src) {
+    CK(cudaMemcpyAsync(f->y_ring + slot, y, cnt * sizeof(double), cudaMemcpyDeviceToDevice, f->stream));
+  } else {
+    std::memcpy(f->y_pinned + slot, y, cnt * sizeof(double));
+    CK(cudaMemcpyAsync(f->y_ring + slot, f->y_pinned + slot, cnt * sizeof(double),
+                       cudaMemcpyHostToDevice, f->stream));
+  }
+  return PF_OK;
+}
+
+pf_status launch_cycles(pf_filter* f, uint32_t cnt) {
+  for (uint32_t i = 0; i < cnt; ++i) {
+    CK(cudaGraphLaunch(f->exec, f->stream));
+    f->host_t++;
+    if (f->host_t % RING_CHUNK == 0)
+      CK(cudaEventRecord(f->ring_ev[((f->host_t - 1) % RING) / RING_CHUNK], f->stream));
+  }
+  return PF_OK;
+}
+
+pf_status check_handle(pf_filter* f) {
+  if (!f) return set_err(PF_ERR_INVALID, "NULL filter handle");
+  if (f->sticky != PF_OK) return set_err(f->sticky, "filter is in a failed state (%d)", (int)f->sticky);
+  return PF_OK;
+}
+
+pf_status sync_and_check(pf_filter* f) {
+  cudaError_t e = cudaMemcpyAsync(f->ctl_host, f->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, f->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(f->stream);
+  if (e != cudaSuccess) {
+    f->sticky = PF_ERR_CUDA;
+    return set_err(PF_ERR_CUDA, "stream: %s", cudaGetErrorString(e));
+  }
+  pf_status st = map_err(f->ctl_host->err);
+  if (st != PF_OK) f->sticky = st;
+  return st;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* pf_last_error(void) { return g_err; }
+
+pf_status pf_create(const pf_config* cfg, pf_filter** out) {
+  if (!cfg || !out) return set_err(PF_ERR_INVALID, "NULL argument");
+  *out = nullptr;
+  if (cfg->n_particles < 1 || cfg->n_particles > PF_MAX_PARTICLES)
+    return set_err(PF_ERR_INVALID, "n_particles must be in [1, 2^26]");
+  if (cfg->scheme < 0 || cfg->scheme > 3) return set_err(PF_ERR_INVALID, "bad scheme");
+  if (cfg->precision != PF_FP32 && cfg->precision != PF_FP64) return set_err(PF_ERR_INVALID, "bad precision");
+  if (!cfg->known_variances && !(cfg->a_sigma >= 1.0 && cfg->a_tau >= 1.0))
+    return set_err(PF_ERR_INVALID, "prior shapes must be >= 1");
+  if (!(cfg->b_sigma > 0 && cfg->b_tau > 0 && cfg->x0_var >= 0))
+    return set_err(PF_ERR_INVALID, "prior scales must be > 0 and x0_var >= 0");
+  if (cfg->known_variances && !(cfg->sigma2 > 0 && cfg->tau2 > 0))
+    return set_err(PF_ERR_INVALID, "known variances must be > 0");
+  if ((cfg->alloc == nullptr) != (cfg->free == nullptr))
+    return set_err(PF_ERR_INVALID, "alloc and free must both be set or both NULL");
+  pf_filter* f = new (std::nothrow) pf_filter();
+  if (!f) return set_err(PF_ERR_OOM, "host allocation failed");
+  f->cfg = *cfg;
+  f->n = cfg->n_particles;
+  f->k = cdf_shift(f->n);
+  f->ntiles = (uint32_t)cdiv(f->n, TILE);
+  f->fp64 = cfg->precision == PF_FP64;
+  f->learn = !cfg->known_variances;
+  f->scheme = cfg->scheme;
+  pf_status st = PF_OK;
+  auto bail = [&](pf_status s) {
+    pf_destroy(f);
+    return s;
+  };
+  if (cfg->stream) {
+    f->stream = (cudaStream_t)cfg->stream;
+  } else {
+    cudaError_t e = cudaStreamCreateWithFlags(&f->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      delete f;
+      return set_err(PF_ERR_CUDA, "cudaStreamCreate: %s", cudaGetErrorString(e));
+    }
+    f->own_stream = true;
+  }
+  const size_t rs = f->fp64 ? 8 : 4;
+  const size_t n = f->n;
+  for (int p = 0; p < 2; ++p) {
+    if ((st = dev_alloc(f, n * rs, &f->x[p])) != PF_OK) return bail(st);
+    if ((st = dev_alloc(f, n * rs, &f->s2[p])) != PF_OK) return bail(st);
+    if ((st = dev_alloc(f, n * rs, &f->t2[p])) != PF_OK) return bail(st);
+    if ((st = dev_alloc(f, n * 8, &f->bs[p])) != PF_OK) return bail(st);
+    if ((st = dev_alloc(f, n * 8, &f->bt[p])) != PF_OK) return bail(st);
+    if ((st = dev_alloc(f, (size_t)f->ntiles * 8, (void**)&f->stat_w[p])) != PF_OK) return bail(st);
+    if ((st = dev_alloc(f, (size_t)f->ntiles * 8, (void**)&f->stat_e[p])) != PF_OK) return bail(st);
+  }
+  if ((st = dev_alloc(f, n * rs, &f->ell)) != PF_OK) return bail(st);
+  if ((st = dev_alloc(f, n * 8, (void**)&f->Q)) != PF_OK) return bail(st);
+  if (is_multinomial(f->scheme) && (st = dev_alloc(f, (n + 1) * 8, (void**)&f->S)) != PF_OK) return bail(st);
+  if ((st = dev_alloc(f, n * 4, (void**)&f->anc)) != PF_OK) return bail(st);
+  if (is_cutpoint(f->scheme) && (st = dev_alloc(f, n * 4, (void**)&f->I)) != PF_OK) return bail(st);
+  if ((st = dev_alloc(f, (size_t)f->ntiles * 16, &f->part)) != PF_OK) return bail(st);
+  const uint64_t est_blocks = cdiv(n, (uint64_t)BLOCK * EST_PER_THREAD);
+  if ((st = dev_alloc(f, est_blocks * 6 * 8, (void**)&f->part_est)) != PF_OK) return bail(st);
+  if ((st = dev_alloc(f, sizeof(Ctl), (void**)&f->ctl)) != PF_OK) return bail(st);
+  if ((st = dev_alloc(f, RING * sizeof(double), (void**)&f->y_ring)) != PF_OK) return bail(st);
+  if (cudaHostAlloc((void**)&f->y_pinned, RING * sizeof(double), cudaHostAllocDefault) != cudaSuccess ||
+      cudaHostAlloc((void**)&f->ctl_host, sizeof(Ctl), cudaHostAllocDefault) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(set_err(PF_ERR_OOM, "pinned host allocation failed"));
+  }
+  for (int i = 0; i < 4; ++i) {
+    if (cudaEventCreateWithFlags(&f->ring_ev[i], cudaEventDisableTiming) != cudaSuccess)
+      return bail(set_err(PF_ERR_CUDA, "cudaEventCreate failed"));
+  }
+  // control block: t = 0, no error, max = -inf, counters 0
+  Ctl c0;
+  std::memset(&c0, 0, sizeof(c0));
+  {
+    if (f->fp64) {
+      double ninf = -__builtin_inf();
+      uint64_t b;
+      std::memcpy(&b, &ninf, 8);
+      c0.maxenc = (b & 0x8000000000000000ull) ? ~b : (b | 0x8000000000000000ull);
+    } else {
+      float ninf = -__builtin_inff();
+      uint32_t b;
+      std::memcpy(&b, &ninf, 4);
+      c0.maxenc = (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+    }
+  }
+  *f->ctl_host = c0;
+  if (cudaMemcpyAsync(f->ctl, f->ctl_host, sizeof(Ctl), cudaMemcpyHostToDevice, f->stream) != cudaSuccess)
+    return bail(set_err(PF_ERR_CUDA, "control block upload failed"));
+  for (int p = 0; p < 2; ++p) {
+    if (cudaMemsetAsync(f->stat_w[p], 0, (size_t)f->ntiles * 8, f->stream) != cudaSuccess ||
+        cudaMemsetAsync(f->stat_e[p], 0, (size_t)f->ntiles * 8, f->stream) != cudaSuccess)
+      return bail(set_err(PF_ERR_CUDA, "status memset failed"));
+  }
+  const unsigned grid = (unsigned)cdiv(n, BLOCK);
+  if (f->fp64) {
+    FilterArgs<double> a = filter_args<double>(f);
+    if (f->learn) k_init<double, true><<<grid, BLOCK, 0, f->stream>>>(a);
+    else k_init<double, false><<<grid, BLOCK, 0, f->stream>>>(a);
+  } else {
+    FilterArgs<float> a = filter_args<float>(f);
+    if (f->learn) k_init<float, true><<<grid, BLOCK, 0, f->stream>>>(a);
+    else k_init<float, false><<<grid, BLOCK, 0, f->stream>>>(a);
+  }
+  if (cudaGetLastError() != cudaSuccess) return bail(set_err(PF_ERR_CUDA, "init kernel launch failed"));
+  if ((st = build_graph(f)) != PF_OK) return bail(st);
+  *out = f;
+  return PF_OK;
+}
+
+pf_status pf_step(pf_filter* f, double y) {
+  pf_status st = check_handle(f);
+  if (st != PF_OK) return st;
+  if ((st = stage_obs(f, &y, 1, false)) != PF_OK) return f->sticky = st;
+  if ((st = launch_cycles(f, 1)) != PF_OK) return f->sticky = st;
+  return PF_OK;
+}
+
+pf_status pf_run(pf_filter* f, const double* y, uint32_t n_steps) {
+  pf_status st = check_handle(f);
+  if (st != PF_OK) return st;
+  if (!y && n_steps) return set_err(PF_ERR_INVALID, "NULL observations");
+  cudaPointerAttributes attr;
+  bool dev = false;
+  if (n_steps && cudaPointerGetAttributes(&attr, y) == cudaSuccess)
+    dev = attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+  cudaGetLastError();
+  uint32_t done = 0;
+  while (done < n_steps) {
+    const uint32_t slot = (uint32_t)(f->host_t % RING);
+    uint32_t cnt = RING_CHUNK - slot % RING_CHUNK;
+    if (cnt > n_steps - done) cnt = n_steps - done;
+    if ((st = stage_obs(f, y + done, cnt, dev)) != PF_OK) return f->sticky = st;
+    if ((st = launch_cycles(f, cnt)) != PF_OK) return f->sticky = st;
+    done += cnt;
+  }
+  return PF_OK;
+}
+
+pf_status pf_step_profiled(pf_filter* f, double y, float* kernel_ms, const char** kernel_names,
+                           int max_kernels, int* n_kernels) {
+  pf_status st = check_handle(f);
+  if (st != PF_OK) return st;
+  if (!kernel_ms || !n_kernels || max_kernels < 1) return set_err(PF_ERR_INVALID, "NULL output");
+  KTimer tm;
+  for (int i = 0; i <= KTimer::MAX; ++i) CK(cudaEventCreate(&tm.ev[i]));
+  if ((st = stage_obs(f, &y, 1, false)) == PF_OK)
+    st = f->fp64 ? enqueue_cycle<double>(f, &tm) : enqueue_cycle<float>(f, &tm);
+  if (st == PF_OK) {
+    f->host_t++;
+    if (f->host_t % RING_CHUNK == 0)
+      cudaEventRecord(f->ring_ev[((f->host_t - 1) % RING) / RING_CHUNK], f->stream);
+    st = sync_and_check(f);
+  }
+  if (st == PF_OK) {
+    const int cnt = tm.count < max_kernels ? tm.count : max_kernels;
+    for (int i = 0; i < cnt; ++i) {
+      cudaEventElapsedTime(&kernel_ms[i], tm.ev[i], tm.ev[i + 1]);
+      if (kernel_names) kernel_names[i] = tm.names[i];
+    }
+    *n_kernels = cnt;
+  } else {
+    f->sticky = st;
+  }
+  for (int i = 0; i <= KTimer::MAX; ++i) cudaEventDestroy(tm.ev[i]);
+  return st;
+}
+
+pf_status pf_sync(pf_filter* f) {
+  pf_status st = check_handle(f);
+  if (st != PF_OK) return st;
+  return sync_and_check(f);
+}
+
+pf_status pf_estimate(pf_filter* f, pf_estimates* out) {
+  pf_status st = check_handle(f);
+  if (st != PF_OK) return st;
+  if (!out) return set_err(PF_ERR_INVALID, "NULL output");
+  const unsigned grid = (unsigned)cdiv(f->n, (uint64_t)BLOCK * EST_PER_THREAD);
+  if (f->fp64) k_estimate<double><<<grid, BLOCK, 0, f->stream>>>(filter_args<double>(f));
+  else k_estimate<float><<<grid, BLOCK, 0, f->stream>>>(filter_args<float>(f));
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    f->sticky = PF_ERR_CUDA;
+    return set_err(PF_ERR_CUDA, "estimate launch: %s", cudaGetErrorString(e));
+  }
+  if ((st = sync_and_check(f)) != PF_OK) return st;
+  const double* v = f->ctl_host->est;
+  out->t = (uint64_t)v[0];
+  out->x_mean = v[1];
+  out->x_var = v[2];
+  out->sigma2_mean = v[3];
+  out->sigma2_var = v[4];
+  out->tau2_mean = v[5];
+  out->tau2_var = v[6];
+  out->log_marglik = v[7];
+  return PF_OK;
+}
+
+pf_status pf_get_particles(pf_filter* f, void* x, void* sigma2, void* tau2, void* b_sigma,
+                           void* b_tau) {
+  pf_status st = check_handle(f);
+  if (st != PF_OK) return st;
+  if ((st = sync_and_check(f)) != PF_OK) return st;
+  const int p = (int)(f->ctl_host->t & 1);
+  const size_t rs = f->fp64 ? 8 : 4;
+  void* dst[5] = {x, sigma2, tau2, b_sigma, b_tau};
+  void* src[5] = {f->x[p], f->s2[p], f->t2[p], f->bs[p], f->bt[p]};
+  const size_t sz[5] = {rs, rs, rs, 8, 8};
+  for (int i = 0; i < 5; ++i)
+    if (dst[i]) CK(cudaMemcpyAsync(dst[i], src[i], f->n * sz[i], cudaMemcpyDefault, f->stream));
+  CK(cudaStreamSynchronize(f->stream));
+  return PF_OK;
+}
+
+pf_status pf_get_ancestors(pf_filter* f, uint32_t* anc, uint64_t* Q) {
+  pf_status st = check_handle(f);
+  if (st != PF_OK) return st;
+  if ((st = sync_and_check(f)) != PF_OK) return st;
+  if (anc) CK(cudaMemcpyAsync(anc, f->anc, f->n * 4, cudaMemcpyDefault, f->stream));
+  if (Q) CK(cudaMemcpyAsync(Q, f->Q, f->n * 8, cudaMemcpyDefault, f->stream));
+  CK(cudaStreamSynchronize(f->stream));
+  return PF_OK;
+}
+
+pf_status pf_destroy(pf_filter* f) {
+  if (!f) return PF_OK;
+  if (f->stream) cudaStreamSynchronize(f->stream);
+  if (f->exec) cudaGraphExecDestroy(f->exec);
+  if (f->graph) cudaGraphDestroy(f->graph);
+  free_all(f);
+  if (f->stream) cudaStreamSynchronize(f->stream);
+  for (int i = 0; i < 4; ++i)
+    if (f->ring_ev[i]) cudaEventDestroy(f->ring_ev[i]);
+  if (f->y_pinned) cudaFreeHost(f->y_pinned);
+  if (f->ctl_host) cudaFreeHost(f->ctl_host);
+  if (f->own_stream) cudaStreamDestroy(f->stream);
+  cudaGetLastError();
+  delete f;
+  return PF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Standalone resampling and the paper's cut-point primitives.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct Scratch {
+  uint64_t* Q;
+  uint64_t* S;
+  uint32_t* I;
+  uint64_t* stat[2];
+  uint64_t* stat_e[2];
+  Ctl* ctl;
+  void* base;
+};
+
+size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+// Lay out the scratch of pf_resample / pf_cdf inside one allocation.
+size_t scratch_layout(uint64_t n, bool need_Q, bool multi, bool cut, char* base, Scratch* s) {
+  const uint64_t ntiles = cdiv(n, TILE);
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    char* p = base ? base + off : nullptr;
+    off += align256(bytes);
+    return p;
+  };
+  s->ctl = (Ctl*)take(sizeof(Ctl));
+  s->stat[0] = (uint64_t*)take(ntiles * 8);
+  s->stat[1] = (uint64_t*)take(ntiles * 8);
+  s->stat_e[0] = (uint64_t*)take(ntiles * 8);
+  s->stat_e[1] = (uint64_t*)take(ntiles * 8);
+  const size_t zero_bytes = off;  // everything above must start at zero
+  s->Q = need_Q ? (uint64_t*)take(n * 8) : nullptr;
+  s->S = multi ? (uint64_t*)take((n + 1) * 8) : nullptr;
+  s->I = cut ? (uint32_t*)take(n * 4) : nullptr;
+  s->base = base;
+  (void)zero_bytes;
+  return off;
+}
+
+size_t scratch_zero_bytes(uint64_t n) {
+  const uint64_t ntiles = cdiv(n, TILE);
+  return align256(sizeof(Ctl)) + 4 * align256(ntiles * 8);
+}
+
+// Weights -> Q (and S for multinomial) -> ancestors, on stream s with the
+// given scratch (already zeroed in its first scratch_zero_bytes bytes).
+pf_status run_resample(const float* w, uint64_t n, uint64_t seed, uint32_t filter, uint32_t t,
+                       int scheme, uint32_t* anc, uint64_t* Q_out, const Scratch& sc,
+                       cudaStream_t s) {
+  const uint32_t ntiles = (uint32_t)cdiv(n, TILE);
+  const unsigned gmax = (unsigned)(cdiv(n, BLOCK) < 152 * 8 ? cdiv(n, BLOCK) : 152 * 8);
+  k_wmax<<<gmax, BLOCK, 0, s>>>(w, n, sc.ctl);
+  ScanArgs sa;
+  sa.src = w;
+  sa.Q = Q_out ? Q_out : sc.Q;
+  sa.stat[0] = sc.stat[0];
+  sa.stat[1] = sc.stat[1];
+  sa.part = nullptr;
+  sa.ctl = sc.ctl;
+  sa.t_dev = nullptr;
+  sa.t_arg = 0;
+  sa.n = n;
+  sa.k = cdf_shift(n);
+  sa.vec_ok = ((uintptr_t)w & 15) == 0;
+  k_scan<FROM_WEIGHTS, float><<<ntiles, BLOCK, 0, s>>>(sa);
+  CK(cudaGetLastError());
+  if (!anc) return PF_OK;
+  if (is_multinomial(scheme)) {
+    SpacingArgs sp;
+    sp.S = sc.S;
+    sp.stat[0] = sc.stat_e[0];
+    sp.stat[1] = sc.stat_e[1];
+    sp.ctl = sc.ctl;
+    sp.t_dev = nullptr;
+    sp.t_arg = t;
+    sp.n = n;
+    sp.seed = seed;
+    sp.filter = filter;
+    k_spacing_scan<<<ntiles, BLOCK, 0, s>>>(sp);
+  }
+  PosArgs pa;
+  pa.Q = sa.Q;
+  pa.S = sc.S;
+  pa.anc = anc;
+  pa.I = sc.I;
+  pa.ctl = sc.ctl;
+  pa.t_dev = nullptr;
+  pa.t_arg = t;
+  pa.n = n;
+  pa.seed = seed;
+  pa.filter = filter;
+  return launch_resample(scheme, pa, n, sc.I, s);
+}
+
+pf_status finish_and_check(const Scratch& sc, cudaStream_t s) {
+  Ctl h;
+  CK(cudaMemcpyAsync(&h, sc.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (h.maxenc == 0) return set_err(PF_ERR_NUMERIC, "all weights are zero");
+  return map_err(h.err);
+}
+
+pf_status resample_common(const float* w, uint64_t n, uint64_t seed, uint32_t filter,
+                          uint32_t t, int scheme, uint32_t* anc, uint64_t* Q_out, void* stream) {
+  if (!w || (!anc && !Q_out)) return set_err(PF_ERR_INVALID, "NULL pointer");
+  if (n < 1 || n > PF_MAX_PARTICLES) return set_err(PF_ERR_INVALID, "n must be in [1, 2^26]");
+  if (scheme < 0 || scheme > 3) return set_err(PF_ERR_INVALID, "bad scheme");
+  cudaStream_t s = (cudaStream_t)stream;
+  Scratch sc;
+  const bool multi = anc && is_multinomial(scheme), cut = anc && is_cutpoint(scheme);
+  const size_t bytes = scratch_layout(n, Q_out == nullptr, multi, cut, nullptr, &sc);
+  void* base = nullptr;
+  cudaError_t e = cudaMallocAsync(&base, bytes, s);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return set_err(PF_ERR_OOM, "cudaMallocAsync(%zu): %s", bytes, cudaGetErrorString(e));
+  }
+  scratch_layout(n, Q_out == nullptr, multi, cut, (char*)base, &sc);
+  pf_status st = PF_OK;
+  if (cudaMemsetAsync(base, 0, scratch_zero_bytes(n), s) != cudaSuccess)
+    st = set_err(PF_ERR_CUDA, "scratch memset failed");
+  if (st == PF_OK) st = run_resample(w, n, seed, filter, t, scheme, anc, Q_out, sc, s);
+  pf_status st2 = PF_OK;
+  if (st == PF_OK) st2 = finish_and_check(sc, s);
+  cudaFreeAsync(base, s);
+  if (st == PF_OK && cudaStreamSynchronize(s) != cudaSuccess)
+    st = set_err(PF_ERR_CUDA, "stream synchronisation failed");
+  return st != PF_OK ? st : st2;
+}
+
+pf_status read_total(const uint64_t* Q, uint64_t n, cudaStream_t s, uint64_t* T) {
+  CK(cudaMemcpyAsync(T, Q + n - 1, 8, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (*T == 0 || *T > (1ull << 62)) return set_err(PF_ERR_INVALID, "CDF total must be in [1, 2^62]");
+  return PF_OK;
+}
+
+}  // namespace
+
+pf_status pf_resample(const float* w_dev, uint64_t n, uint64_t seed, uint32_t filter_id,
+                      uint32_t t, int32_t scheme, uint32_t* anc_dev, void* stream) {
+  if (!anc_dev) return set_err(PF_ERR_INVALID, "NULL ancestor output");
+  return resample_common(w_dev, n, seed, filter_id, t, scheme, anc_dev, nullptr, stream);
+}
+
+pf_status pf_cdf(const float* w_dev, uint64_t n, uint64_t* Q_dev, void* stream) {
+  if (!Q_dev) return set_err(PF_ERR_INVALID, "NULL CDF output");
+  return resample_common(w_dev, n, 0, 0, 0, PF_SYSTEMATIC, nullptr, Q_dev, stream);
+}
+
+pf_status pf_cutpoint_search(const uint64_t* Q_dev, uint64_t n, uint32_t* I_dev, void* stream) {
+  if (!Q_dev || !I_dev) return set_err(PF_ERR_INVALID, "NULL pointer");
+  if (n < 1 || n > PF_MAX_PARTICLES) return set_err(PF_ERR_INVALID, "n must be in [1, 2^26]");
+  cudaStream_t s = (cudaStream_t)stream;
+  uint64_t T;
+  pf_status st = read_total(Q_dev, n, s, &T);
+  if (st != PF_OK) return st;
+  k_cutpoint_search<<<(unsigned)cdiv(n, BLOCK), BLOCK, 0, s>>>(Q_dev, n, I_dev);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));
+  return PF_OK;
+}
+
+pf_status pf_cutpoint_method(const uint64_t* Q_dev, uint64_t n, const uint32_t* I_dev,
+                             const uint64_t* U_dev, uint64_t m, uint32_t* anc_dev, void* stream) {
+  if (!Q_dev || !I_dev || (m && (!U_dev || !anc_dev))) return set_err(PF_ERR_INVALID, "NULL pointer");
+  if (n < 1 || n > PF_MAX_PARTICLES || m > PF_MAX_PARTICLES)
+    return set_err(PF_ERR_INVALID, "n and m must be at most 2^26 (n >= 1)");
+  cudaStream_t s = (cudaStream_t)stream;
+  uint64_t T;
+  pf_status st = read_total(Q_dev, n, s, &T);
+  if (st != PF_OK) return st;
+  if (m == 0) return PF_OK;
+  k_cutpoint_method_explicit<<<(unsigned)cdiv(m, BLOCK), BLOCK, 0, s>>>(Q_dev, n, I_dev, U_dev, m,
+                                                                     anc_dev);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));
+  return PF_OK;
+}
+
+}  // extern "C"

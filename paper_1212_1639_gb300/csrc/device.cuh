@@ -1,0 +1,413 @@
+// Device building blocks of the particle-learning cycle (sm_103a).
+//
+// This translation-unit-shared header holds the per-element arithmetic that
+// every kernel uses: the counter-based RNG, exactly representable uniforms,
+// deterministic elementary functions, Box-Muller normals, the Marsaglia-Tsang
+// gamma sampler and 128-bit integer helpers.
+//
+// Determinism contract.  The library is compiled with -fmad=false, IEEE
+// division and square root, and no flush-to-zero, and every floating-point
+// expression below is written as one IEEE operation per statement.  Given the
+// same inputs the results are therefore bit-identical on any IEEE-754
+// machine that evaluates the same operation sequence, which is what makes the
+// quantised CDF (and hence every ancestor index) a deterministic function of
+// the particle state.
+#pragma once
+#include <cstdint>
+
+namespace pfk {
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror & Shaw, "Parallel random numbers: as
+// easy as 1, 2, 3", SC'11): ten rounds of the Philox S-box on a 128-bit
+// counter with a 64-bit key bumped by the golden-ratio Weyl constants.
+// ---------------------------------------------------------------------------
+struct U4 {
+  uint32_t a, b, c, d;
+};
+
+__device__ __forceinline__ U4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                     uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c0);
+    const uint32_t lo0 = 0xD2511F53u * c0;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2);
+    const uint32_t lo1 = 0xCD9E8D57u * c2;
+    c0 = hi1 ^ c1 ^ k0;
+    c1 = lo1;
+    c2 = hi0 ^ c3 ^ k1;
+    c3 = lo0;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return U4{c0, c1, c2, c3};
+}
+
+enum Purpose : uint32_t {
+  P_INIT_X = 1, P_INIT_SIGMA = 2, P_INIT_TAU = 3,
+  P_STATE = 4, P_GAMMA_SIGMA = 5, P_GAMMA_TAU = 6,
+  P_SYS_OFFSET = 7, P_SPACING = 8,
+};
+
+// Draw (seed, filter, t, j, purpose, attempt): counter (j, t, filter,
+// purpose | attempt << 8), key (seed lo, seed hi).
+__device__ __forceinline__ U4 draw(uint64_t seed, uint32_t filter, uint32_t t, uint32_t j,
+                                   uint32_t purpose, uint32_t attempt) {
+  return philox(j, t, filter, purpose | (attempt << 8), (uint32_t)seed, (uint32_t)(seed >> 32));
+}
+
+// Uniforms on (0,1) whose conversion is exact.
+__device__ __forceinline__ float unif_f32(uint32_t w) {
+  return __uint2float_rn(2u * (w >> 9) + 1u) * 0x1p-24f;
+}
+__device__ __forceinline__ double unif_f64(uint32_t lo, uint32_t hi) {
+  const uint64_t R = ((uint64_t)hi << 32) | lo;
+  return __ull2double_rn(2ull * (R >> 12) + 1ull) * 0x1p-53;
+}
+__device__ __forceinline__ double unif_f64_32(uint32_t w) {
+  return __ull2double_rn(2ull * w + 1ull) * 0x1p-33;
+}
+
+// ---------------------------------------------------------------------------
+// Deterministic elementary functions.
+//  log x : x = f 2^e, f in [sqrt(1/2), sqrt(2)); log f = 2 atanh(z),
+//          z = (f-1)/(f+1), series through z^(2K)/(2K+1) (K = 4 / 10);
+//          log x = e ln2 + log f.
+//  exp r : Taylor polynomial through r^D/D! (D = 7 / 13) on a Cody-Waite
+//          reduced argument.
+//  cos(2 pi u): octant reduction of u in [0,1] and Taylor polynomials of cos
+//          (through x^10 / x^16) and sin (through x^9 / x^17) on |x| <= pi/4.
+// Constants are the exact values rounded to nearest in the working format.
+// ---------------------------------------------------------------------------
+template <class R> struct Cst;
+template <> struct Cst<float> {
+  static constexpr float LN2 = 0x1.62e430p-1f;
+  static constexpr float LN2_HI = 0x1.62e400p-1f;
+  static constexpr float LN2_LO = 0x1.7f7d1cp-20f;
+  static constexpr float INV_LN2 = 0x1.715476p+0f;
+  static constexpr float TWO_PI = 0x1.921fb6p+2f;
+  static constexpr float SQRT_HALF = 0x1.6a09e6p-1f;
+  static constexpr float SQUEEZE = 0x1.0f27bcp-5f;  // Marsaglia-Tsang 0.0331
+};
+template <> struct Cst<double> {
+  static constexpr double LN2 = 0x1.62e42fefa39efp-1;
+  static constexpr double LN2_HI = 0x1.62e42fefa2000p-1;
+  static constexpr double LN2_LO = 0x1.9ef35793c7673p-41;
+  static constexpr double INV_LN2 = 0x1.71547652b82fep+0;
+  static constexpr double TWO_PI = 0x1.921fb54442d18p+2;
+  static constexpr double SQRT_HALF = 0x1.6a09e667f3bcdp-1;
+  static constexpr double SQUEEZE = 0x1.0f27bb2fec56dp-5;
+};
+
+// log of a positive normal number.
+__device__ __forceinline__ float det_log(float x) {
+  int e;
+  float f = frexpf(x, &e);
+  if (f < Cst<float>::SQRT_HALF) {
+    f = f * 2.0f;
+    e = e - 1;
+  }
+  const float num = f - 1.0f;
+  const float den = f + 1.0f;
+  const float z = num / den;
+  const float z2 = z * z;
+  float p = 0x1.c71c72p-4f;   // 1/9
+  p = p * z2; p = p + 0x1.24924ap-3f;  // 1/7
+  p = p * z2; p = p + 0x1.99999ap-3f;  // 1/5
+  p = p * z2; p = p + 0x1.555556p-2f;  // 1/3
+  p = p * z2; p = p + 1.0f;
+  const float two_z = z * 2.0f;
+  const float lf = two_z * p;
+  const float el = __int2float_rn(e) * Cst<float>::LN2;
+  return el + lf;
+}
+__device__ __forceinline__ double det_log(double x) {
+  int e;
+  double f = frexp(x, &e);
+  if (f < Cst<double>::SQRT_HALF) {
+    f = f * 2.0;
+    e = e - 1;
+  }
+  const double num = f - 1.0;
+  const double den = f + 1.0;
+  const double z = num / den;
+  const double z2 = z * z;
+  // 1/(2m+1), m = 10 .. 0
+  const double c[11] = {0x1.8618618618618p-5, 0x1.af286bca1af28p-5, 0x1.e1e1e1e1e1e1ep-5,
+                        0x1.1111111111111p-4, 0x1.3b13b13b13b14p-4, 0x1.745d1745d1746p-4,
+                        0x1.c71c71c71c71cp-4, 0x1.2492492492492p-3, 0x1.999999999999ap-3,
+                        0x1.5555555555555p-2, 0x1p+0};
+  double p = c[0];
+#pragma unroll
+  for (int m = 1; m < 11; ++m) {
+    p = p * z2;
+    p = p + c[m];
+  }
+  const double two_z = z * 2.0;
+  const double lf = two_z * p;
+  const double el = (double)e * Cst<double>::LN2;
+  return el + lf;
+}
+
+// Taylor polynomial of exp on the reduced argument.
+__device__ __forceinline__ float det_exp_core(float r) {
+  const float c[8] = {0x1.a01a02p-13f, 0x1.6c16c2p-10f, 0x1.111112p-7f, 0x1.555556p-5f,
+                      0x1.555556p-3f, 0x1p-1f, 0x1p+0f, 0x1p+0f};  // 1/7! .. 1/0!
+  float p = c[0];
+#pragma unroll
+  for (int k = 1; k < 8; ++k) {
+    p = p * r;
+    p = p + c[k];
+  }
+  return p;
+}
+__device__ __forceinline__ double det_exp_core(double r) {
+  const double c[14] = {0x1.6124613a86d09p-33, 0x1.1eed8eff8d898p-29, 0x1.ae64567f544e4p-26,
+                        0x1.27e4fb7789f5cp-22, 0x1.71de3a556c734p-19, 0x1.a01a01a01a01ap-16,
+                        0x1.a01a01a01a01ap-13, 0x1.6c16c16c16c17p-10, 0x1.1111111111111p-7,
+                        0x1.5555555555555p-5,  0x1.5555555555555p-3,  0x1p-1,
+                        0x1p+0,                0x1p+0};  // 1/13! .. 1/0!
+  double p = c[0];
+#pragma unroll
+  for (int k = 1; k < 14; ++k) {
+    p = p * r;
+    p = p + c[k];
+  }
+  return p;
+}
+
+__device__ __forceinline__ float cos_poly(float x) {
+  const float x2 = x * x;
+  // (-1)^m / (2m)!, m = 5 .. 0
+  const float c[6] = {-0x1.27e4fcp-22f, 0x1.a01a02p-16f, -0x1.6c16c2p-10f, 0x1.555556p-5f,
+                      -0x1p-1f, 0x1p+0f};
+  float p = c[0];
+#pragma unroll
+  for (int m = 1; m < 6; ++m) {
+    p = p * x2;
+    p = p + c[m];
+  }
+  return p;
+}
+__device__ __forceinline__ float sin_poly(float x) {
+  const float x2 = x * x;
+  // (-1)^m / (2m+1)!, m = 4 .. 0
+  const float c[5] = {0x1.71de3ap-19f, -0x1.a01a02p-13f, 0x1.111112p-7f, -0x1.555556p-3f,
+                      0x1p+0f};
+  float p = c[0];
+#pragma unroll
+  for (int m = 1; m < 5; ++m) {
+    p = p * x2;
+    p = p + c[m];
+  }
+  return x * p;
+}
+__device__ __forceinline__ double cos_poly(double x) {
+  const double x2 = x * x;
+  // (-1)^m / (2m)!, m = 8 .. 0
+  const double c[9] = {0x1.ae7f3e733b81fp-45, -0x1.93974a8c07c9dp-37, 0x1.1eed8eff8d898p-29,
+                       -0x1.27e4fb7789f5cp-22, 0x1.a01a01a01a01ap-16, -0x1.6c16c16c16c17p-10,
+                       0x1.5555555555555p-5, -0x1p-1, 0x1p+0};
+  double p = c[0];
+#pragma unroll
+  for (int m = 1; m < 9; ++m) {
+    p = p * x2;
+    p = p + c[m];
+  }
+  return p;
+}
+__device__ __forceinline__ double sin_poly(double x) {
+  const double x2 = x * x;
+  // (-1)^m / (2m+1)!, m = 8 .. 0
+  const double c[9] = {0x1.952c77030ad4ap-49, -0x1.ae7f3e733b81fp-41, 0x1.6124613a86d09p-33,
+                       -0x1.ae64567f544e4p-26, 0x1.71de3a556c734p-19, -0x1.a01a01a01a01ap-13,
+                       0x1.1111111111111p-7, -0x1.5555555555555p-3, 0x1p+0};
+  double p = c[0];
+#pragma unroll
+  for (int m = 1; m < 9; ++m) {
+    p = p * x2;
+    p = p + c[m];
+  }
+  return x * p;
+}
+
+template <class R>
+__device__ __forceinline__ R det_cos2pi(R u) {
+  const R v = u - rint(u);
+  const R w = fabs(v);
+  if (w <= (R)0.125) {
+    const R x = Cst<R>::TWO_PI * w;
+    return cos_poly(x);
+  } else if (w <= (R)0.375) {
+    const R a = (R)0.25 - w;
+    const R x = Cst<R>::TWO_PI * a;
+    return sin_poly(x);
+  } else {
+    const R a = (R)0.5 - w;
+    const R x = Cst<R>::TWO_PI * a;
+    return -cos_poly(x);
+  }
+}
+
+__device__ __forceinline__ float pow2f(int n) {  // n in [-126, 127]
+  return __int_as_float((n + 127) << 23);
+}
+__device__ __forceinline__ double pow2d(int n) {  // n in [-1022, 1023]
+  return __longlong_as_double((long long)(n + 1023) << 52);
+}
+__device__ __forceinline__ float pow2(int n, float) { return pow2f(n); }
+__device__ __forceinline__ double pow2(int n, double) { return pow2d(n); }
+
+// Quantised CDF weight: e = exp(dl) (0 below dl = -50) and
+// W = min(floor(e * 2^k), 2^k) for dl <= 0.
+template <class R>
+__device__ __forceinline__ uint64_t quant_exp(R dl, int k, R* e_out) {
+  if (!(dl >= (R)-50)) {
+    *e_out = (R)0;
+    return 0;
+  }
+  const R t = dl * Cst<R>::INV_LN2;
+  const R nr = rint(t);
+  const int n = (int)nr;
+  const R a = nr * Cst<R>::LN2_HI;
+  const R b = dl - a;
+  const R c = nr * Cst<R>::LN2_LO;
+  const R r = b - c;
+  const R p = det_exp_core(r);
+  *e_out = p * pow2(n, (R)0);
+  const int sc = n + k;
+  uint64_t W = 0;
+  if (sc >= 0) {
+    const R v = p * pow2(sc, (R)0);
+    W = (uint64_t)v;
+  }
+  const uint64_t cap = 1ull << k;
+  return W > cap ? cap : W;
+}
+
+// Box-Muller, first output, from one 128-bit draw; and the extra uniform.
+__device__ __forceinline__ float bm_normal_f(const U4& w) {
+  const float u1 = unif_f32(w.a);
+  const float u2 = unif_f32(w.b);
+  const float L = det_log(u1);
+  const float m2 = L * -2.0f;
+  const float r = sqrtf(m2);
+  const float c = det_cos2pi(u2);
+  return r * c;
+}
+__device__ __forceinline__ double bm_normal_d(const U4& w) {
+  const double u1 = unif_f64(w.a, w.b);
+  const double u2 = unif_f64_32(w.c);
+  const double L = det_log(u1);
+  const double m2 = L * -2.0;
+  const double r = sqrt(m2);
+  const double c = det_cos2pi(u2);
+  return r * c;
+}
+__device__ __forceinline__ float bm_normal(const U4& w, float) { return bm_normal_f(w); }
+__device__ __forceinline__ double bm_normal(const U4& w, double) { return bm_normal_d(w); }
+__device__ __forceinline__ float extra_uniform(const U4& w, float) { return unif_f32(w.c); }
+__device__ __forceinline__ double extra_uniform(const U4& w, double) { return unif_f64_32(w.d); }
+
+// Gamma(a, 1) for a >= 1 by Marsaglia & Tsang (2000), d = a - 1/3,
+// c = 1/sqrt(9d).  Attempt k uses draw (purpose, k); after 16 rejections
+// *fail is set and d is returned.
+template <class R>
+__device__ __forceinline__ R gamma_mt(R d, R c, uint64_t seed, uint32_t filter, uint32_t t,
+                                      uint32_t j, uint32_t purpose, bool* fail) {
+  for (uint32_t attempt = 0; attempt < 16; ++attempt) {
+    const U4 w = draw(seed, filter, t, j, purpose, attempt);
+    const R Z = bm_normal(w, (R)0);
+    const R U = extra_uniform(w, (R)0);
+    const R cz = c * Z;
+    const R v = (R)1 + cz;
+    if (!(v > (R)0)) continue;
+    const R vv = v * v;
+    const R v3 = vv * v;
+    const R Z2 = Z * Z;
+    const R z4 = Z2 * Z2;
+    const R sq = Cst<R>::SQUEEZE * z4;
+    const R thr = (R)1 - sq;
+    if (U < thr) return d * v3;
+    const R lhs = det_log(U);
+    const R a1 = (R)1 - v3;
+    const R a2 = det_log(v3);
+    const R a3 = a1 + a2;
+    const R a4 = d * a3;
+    const R a5 = (R)0.5 * Z2;
+    const R rhs = a5 + a4;
+    if (lhs < rhs) return d * v3;
+  }
+  *fail = true;
+  return d;
+}
+
+// ---------------------------------------------------------------------------
+// 128-bit unsigned helpers (hi, lo).
+// ---------------------------------------------------------------------------
+struct U128 {
+  uint64_t hi, lo;
+};
+__device__ __forceinline__ U128 mul64(uint64_t a, uint64_t b) {
+  return U128{__umul64hi(a, b), a * b};
+}
+__device__ __forceinline__ U128 add128(U128 x, uint64_t y) {
+  const uint64_t lo = x.lo + y;
+  return U128{x.hi + (lo < y ? 1ull : 0ull), lo};
+}
+__device__ __forceinline__ U128 add128(U128 x, U128 y) {
+  const uint64_t lo = x.lo + y.lo;
+  return U128{x.hi + y.hi + (lo < y.lo ? 1ull : 0ull), lo};
+}
+__device__ __forceinline__ bool le128(U128 x, U128 y) {
+  return x.hi < y.hi || (x.hi == y.hi && x.lo <= y.lo);
+}
+__device__ __forceinline__ bool lt128(U128 x, U128 y) {
+  return x.hi < y.hi || (x.hi == y.hi && x.lo < y.lo);
+}
+__device__ __forceinline__ U128 shl128(uint64_t v, int s) {  // v << s, 0 <= s < 128
+  if (s == 0) return U128{0, v};
+  if (s < 64) return U128{v >> (64 - s), v << s};
+  return U128{v << (s - 64), 0};
+}
+
+// floor(X / d) for X = (xh, xl) when the quotient is below 2^53: binary64
+// estimate, then exact correction with 128-bit products.
+__device__ __forceinline__ uint64_t div128_small(U128 X, uint64_t d) {
+  const double xd = __ull2double_rn(X.hi) * 0x1p64 + __ull2double_rn(X.lo);
+  const double qd = xd / __ull2double_rn(d);
+  uint64_t q = qd <= 0.0 ? 0ull : __double2ull_rz(qd);
+  for (int it = 0; it < 8; ++it) {
+    const U128 p = mul64(q, d);
+    if (!le128(p, X)) {
+      --q;
+      continue;
+    }
+    const U128 p1 = add128(p, d);
+    if (le128(p1, X)) {
+      ++q;
+      continue;
+    }
+    break;
+  }
+  return q;
+}
+
+// Order-preserving encodings for atomicMax on floating point.
+__device__ __forceinline__ uint32_t enc_f(float x) {
+  const uint32_t b = __float_as_uint(x);
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float dec_f(uint32_t e) {
+  return __uint_as_float((e & 0x80000000u) ? (e & 0x7fffffffu) : ~e);
+}
+__device__ __forceinline__ unsigned long long enc_d(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  return (b & 0x8000000000000000ull) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double dec_d(unsigned long long e) {
+  return __longlong_as_double((long long)((e & 0x8000000000000000ull) ? (e & 0x7fffffffffffffffull) : ~e));
+}
+
+}  // namespace pfk

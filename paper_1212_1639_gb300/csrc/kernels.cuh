@@ -1,0 +1,1051 @@
+// Kernels of the particle-learning cycle (sm_103a).
+//
+// One cycle for observation y = y_{t+1} (paper Section 2, Algorithm
+// "Particle Learning"):
+//   k_weights       l_i = log p(y | x_i, sigma_i^2, tau_i^2) + log(2 pi)/2, max_i l_i
+//   k_scan          W_i = quantised exp(l_i - max), Q = inclusive scan of W
+//                   (eq. resample.cdf as exact 64-bit integers), single pass
+//                   with decoupled look-back
+//   k_spacing_scan  (multinomial) S = inclusive scan of exponential spacings
+//   k_merge         ancestors a_j = #{i : Q_i * A <= B_j} by a merge of the
+//                   sorted positions B with the CDF
+//   k_cutpoint_*    the paper's Section 3.2 algorithms (same ancestors)
+//   k_propagate     gather ancestor, draw x, update b_sigma/b_tau, draw theta
+//   k_estimate      posterior summaries on demand
+//
+// Data layout in HBM (structure of arrays, one entry per particle):
+//   x, sigma2, tau2 : R (binary32 or binary64), two ping-pong copies
+//   b_sigma, b_tau  : uint64 2^-32 fixed point (FP32) / binary64 (FP64)
+//   l               : R,    Q : uint64,   S : uint64 (n+1),   anc : uint32
+#pragma once
+#include <cstdint>
+
+#include "device.cuh"
+
+namespace pfk {
+
+constexpr int BLOCK = 256;
+constexpr int WARPS = BLOCK / 32;
+constexpr int CHUNK = 128;                 // elements per warp per chunk (4 per lane)
+constexpr int CHUNKS = 4;                  // chunks per warp
+constexpr int TILE = WARPS * CHUNKS * CHUNK;  // 4096 elements per scan tile
+constexpr int MERGE_D = 2048;              // merged elements per merge CTA
+constexpr int MERGE_E = MERGE_D / BLOCK;   // merged elements per thread
+
+constexpr uint64_t FLAG_A = 1ull << 62;    // tile aggregate published
+constexpr uint64_t FLAG_P = 2ull << 62;    // tile inclusive prefix published
+constexpr uint64_t VAL_MASK = (1ull << 62) - 1;
+constexpr uint32_t SPIN_LIMIT = 1u << 22;  // bounded look-back wait
+
+enum ErrBits : uint32_t {
+  ERR_TIMEOUT = 1u,   // look-back gave up
+  ERR_NUMERIC = 2u,   // non-finite max, gamma sampler failure, b overflow
+  ERR_WEIGHTS = 4u,   // negative / non-finite / all-zero input weights
+};
+
+// Per-filter control block in device memory.
+struct Ctl {
+  uint32_t t;             // cycles completed
+  uint32_t err;           // ErrBits
+  unsigned long long maxenc;  // order-encoded max of l (or of the input weights)
+  uint32_t ticket_w;      // scan tile ticket
+  uint32_t ticket_e;      // spacing scan tile ticket
+  uint32_t done_prop;     // last-block counter of k_propagate
+  uint32_t done_est;      // last-block counter of k_estimate
+  double logml;           // accumulated log marginal likelihood
+  double est[8];          // t, x mean/var, sigma2 mean/var, tau2 mean/var, log_marglik
+};
+
+__device__ __forceinline__ void st_release(uint64_t* p, uint64_t v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ uint64_t ld_acquire(const uint64_t* p) {
+  uint64_t v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ uint32_t ld_volatile_u32(const uint32_t* p) {
+  return *(volatile const uint32_t*)p;
+}
+
+template <class T>
+__device__ __forceinline__ T shfl_up(T v, int d) {
+  return __shfl_up_sync(0xffffffffu, v, d);
+}
+__device__ __forceinline__ uint64_t warp_incl_scan(uint64_t v, int lane) {
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint64_t o = __shfl_up_sync(0xffffffffu, v, d);
+    if (lane >= d) v += o;
+  }
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// State views.
+// ---------------------------------------------------------------------------
+template <class R> struct SuffT;
+template <> struct SuffT<float> { typedef uint64_t B; };
+template <> struct SuffT<double> { typedef double B; };
+
+template <class R>
+struct StateV {
+  R* x;
+  R* s2;
+  R* t2;
+  typename SuffT<R>::B* bs;
+  typename SuffT<R>::B* bt;
+};
+
+template <class R>
+struct FilterArgs {
+  StateV<R> st[2];          // ping-pong by cycle parity
+  R* ell;
+  uint64_t* Q;
+  uint64_t* S;              // n+1 spacing prefix (multinomial)
+  uint32_t* anc;
+  uint32_t* I;              // cut-point table
+  uint64_t* stat_w[2];      // scan tile status, by parity
+  uint64_t* stat_e[2];      // spacing scan tile status, by parity
+  void* part;               // per-tile log-ML partial (U128 for FP32, double for FP64)
+  double* part_est;         // per-block estimate partials
+  Ctl* ctl;
+  const double* y_ring;
+  uint32_t cap;
+  uint64_t n;
+  uint32_t ntiles;
+  int k;                    // CDF shift: W <= 2^k
+  uint64_t seed;
+  uint32_t filter;
+  double x0_mean, x0_var, a_sigma, b_sigma, a_tau, b_tau, sigma2, tau2;
+};
+
+// ---------------------------------------------------------------------------
+// Initialisation (Algorithm "Particle Learning", Step 0).
+// ---------------------------------------------------------------------------
+template <class R> struct SuffOps;
+template <> struct SuffOps<float> {
+  static __device__ __forceinline__ uint64_t from_prior(double b) {
+    return __double2ull_rz(b * 0x1p32);
+  }
+  static __device__ __forceinline__ uint64_t add_half_square(uint64_t b, float r, bool* fail) {
+    const float r2 = r * r;
+    const float h = 0.5f * r2;
+    const float v = h * 0x1p32f;
+    if (!(v < 0x1p63f)) {
+      *fail = true;
+      return b;
+    }
+    return b + __float2ull_rz(v);
+  }
+  static __device__ __forceinline__ float ig(uint64_t b, float G) {
+    const float bf = __ull2float_rn(b);
+    const float bs = bf * 0x1p-32f;
+    return bs / G;
+  }
+};
+template <> struct SuffOps<double> {
+  static __device__ __forceinline__ double from_prior(double b) { return b; }
+  static __device__ __forceinline__ double add_half_square(double b, double r, bool*) {
+    const double r2 = r * r;
+    const double h = 0.5 * r2;
+    return b + h;
+  }
+  static __device__ __forceinline__ double ig(double b, double G) { return b / G; }
+};
+
+// (d, c) of Marsaglia-Tsang for shape a, in binary64.
+__device__ __forceinline__ void mt_constants(double a, double* d, double* c) {
+  const double ONE_THIRD = 0x1.5555555555555p-2;
+  const double dd = a - ONE_THIRD;
+  const double nine_d = 9.0 * dd;
+  const double s = sqrt(nine_d);
+  *d = dd;
+  *c = 1.0 / s;
+}
+
+template <class R, bool LEARN>
+__global__ void __launch_bounds__(BLOCK) k_init(FilterArgs<R> a) {
+  __shared__ double s_c[6];
+  if (threadIdx.x == 0) {
+    double ds, cs, dt, ct;
+    mt_constants(a.a_sigma, &ds, &cs);
+    mt_constants(a.a_tau, &dt, &ct);
+    s_c[0] = ds; s_c[1] = cs; s_c[2] = dt; s_c[3] = ct;
+    s_c[4] = sqrt(a.x0_var);
+  }
+  __syncthreads();
+  const uint64_t j = (uint64_t)blockIdx.x * BLOCK + threadIdx.x;
+  if (j >= a.n) return;
+  const StateV<R> st = a.st[0];
+  const R x0m = (R)a.x0_mean;
+  const R sdx = (R)s_c[4];
+  const R Z = bm_normal(draw(a.seed, a.filter, 0, (uint32_t)j, P_INIT_X, 0), (R)0);
+  const R p = sdx * Z;
+  st.x[j] = x0m + p;
+  const auto bs0 = SuffOps<R>::from_prior(a.b_sigma);
+  const auto bt0 = SuffOps<R>::from_prior(a.b_tau);
+  st.bs[j] = bs0;
+  st.bt[j] = bt0;
+  if (!LEARN) {
+    st.s2[j] = (R)a.sigma2;
+    st.t2[j] = (R)a.tau2;
+    return;
+  }
+  bool fail = false;
+  const R Gs = gamma_mt<R>((R)s_c[0], (R)s_c[1], a.seed, a.filter, 0, (uint32_t)j, P_INIT_SIGMA, &fail);
+  const R Gt = gamma_mt<R>((R)s_c[2], (R)s_c[3], a.seed, a.filter, 0, (uint32_t)j, P_INIT_TAU, &fail);
+  st.s2[j] = SuffOps<R>::ig(bs0, Gs);
+  st.t2[j] = SuffOps<R>::ig(bt0, Gt);
+  if (fail) atomicOr(&a.ctl->err, ERR_NUMERIC);
+}
+
+// ---------------------------------------------------------------------------
+// Step 1a: predictive log-likelihood and its maximum.
+// ---------------------------------------------------------------------------
+template <class R>
+__device__ __forceinline__ R log_pred(R x, R s2, R t2, R y) {
+  const R s = s2 + t2;
+  const R dx = y - x;
+  const R q = dx * dx;
+  const R lg = det_log(s);
+  const R r = q / s;
+  const R sum = lg + r;
+  return (R)-0.5 * sum;
+}
+
+__device__ __forceinline__ unsigned long long enc_max(float x) { return enc_f(x); }
+__device__ __forceinline__ unsigned long long enc_max(double x) { return enc_d(x); }
+
+template <class R>
+__device__ __forceinline__ R block_max(R v, R* s_red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if (lane == 0) s_red[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    v = lane < WARPS ? s_red[lane] : (R)-INFINITY;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  }
+  return v;
+}
+
+// Four particles per thread, vectorised.
+constexpr int W_PER_THREAD = 4;
+
+template <class R>
+__global__ void __launch_bounds__(BLOCK) k_weights(FilterArgs<R> a) {
+  __shared__ R s_red[WARPS];
+  const uint32_t t = a.ctl->t;
+  const StateV<R> st = (t & 1) ? a.st[1] : a.st[0];
+  const R yr = (R)a.y_ring[t % a.cap];
+  const uint64_t base = ((uint64_t)blockIdx.x * BLOCK + threadIdx.x) * W_PER_THREAD;
+  R mx = (R)-INFINITY;
+  bool bad = false;
+  if (base + W_PER_THREAD <= a.n) {
+    R xv[4], sv[4], tv[4], lv[4];
+    if constexpr (sizeof(R) == 4) {
+      const float4 X = *reinterpret_cast<const float4*>(st.x + base);
+      const float4 Sg = *reinterpret_cast<const float4*>(st.s2 + base);
+      const float4 Tu = *reinterpret_cast<const float4*>(st.t2 + base);
+      xv[0] = X.x; xv[1] = X.y; xv[2] = X.z; xv[3] = X.w;
+      sv[0] = Sg.x; sv[1] = Sg.y; sv[2] = Sg.z; sv[3] = Sg.w;
+      tv[0] = Tu.x; tv[1] = Tu.y; tv[2] = Tu.z; tv[3] = Tu.w;
+    } else {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) { xv[e] = st.x[base + e]; sv[e] = st.s2[base + e]; tv[e] = st.t2[base + e]; }
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      lv[e] = log_pred<R>(xv[e], sv[e], tv[e], yr);
+      bad |= !(lv[e] < (R)INFINITY);  // NaN or +inf
+      mx = fmax(mx, lv[e]);
+    }
+    if constexpr (sizeof(R) == 4) {
+      *reinterpret_cast<float4*>(a.ell + base) = make_float4(lv[0], lv[1], lv[2], lv[3]);
+    } else {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) a.ell[base + e] = lv[e];
+    }
+  } else {
+    for (uint64_t i = base; i < a.n; ++i) {
+      const R l = log_pred<R>(st.x[i], st.s2[i], st.t2[i], yr);
+      bad |= !(l < (R)INFINITY);
+      mx = fmax(mx, l);
+      a.ell[i] = l;
+    }
+  }
+  if (bad) atomicOr(&a.ctl->err, ERR_NUMERIC);
+  mx = block_max<R>(mx, s_red);
+  if (threadIdx.x == 0 && mx > (R)-INFINITY) atomicMax(&a.ctl->maxenc, enc_max(mx));
+}
+
+// ---------------------------------------------------------------------------
+// Step 1b: the exact fixed-point CDF by a single-pass decoupled look-back scan
+// (Merrill & Garland 2016).  Tiles are claimed through an atomic ticket so a
+// tile's predecessors are always resident or finished; the look-back wait is
+// bounded and reports ERR_TIMEOUT instead of hanging.
+//
+// Warp w of a tile owns elements [512 w, 512 w + 512) as 4 chunks of 128;
+// lane l owns elements 4l..4l+3 of each chunk, so every load and store
+// instruction of the warp covers one contiguous span.
+// ---------------------------------------------------------------------------
+
+// Sum of exp(l_i - m) for the log marginal likelihood: exact 2^-96 fixed
+// point in FP32 mode (binary32 terms >= 2^-73 are integers there).
+struct ESum32 {
+  U128 s;
+  __device__ __forceinline__ void zero() { s.hi = 0; s.lo = 0; }
+  __device__ __forceinline__ void add(float e) {
+    if (e == 0.0f) return;
+    const uint32_t b = __float_as_uint(e);
+    const uint64_t mant = (b & 0x7fffffu) | 0x800000u;
+    const int sh = (int)(b >> 23) - 54;  // e * 2^96 = mant * 2^(exponent bits - 54)
+    s = add128(s, shl128(mant, sh));
+  }
+  __device__ __forceinline__ void add(const ESum32& o) { s = add128(s, o.s); }
+  __device__ __forceinline__ ESum32 shfl_xor(int m) const {
+    ESum32 r;
+    r.s.hi = __shfl_xor_sync(0xffffffffu, s.hi, m);
+    r.s.lo = __shfl_xor_sync(0xffffffffu, s.lo, m);
+    return r;
+  }
+};
+struct ESum64 {
+  double s;
+  __device__ __forceinline__ void zero() { s = 0.0; }
+  __device__ __forceinline__ void add(double e) { s = s + e; }
+  __device__ __forceinline__ void add(const ESum64& o) { s = s + o.s; }
+  __device__ __forceinline__ ESum64 shfl_xor(int m) const {
+    ESum64 r;
+    r.s = __shfl_xor_sync(0xffffffffu, s, m);
+    return r;
+  }
+};
+template <class R> struct ESumT;
+template <> struct ESumT<float> { typedef ESum32 T; };
+template <> struct ESumT<double> { typedef ESum64 T; };
+
+// Tile look-back by warp 0.  Returns the exclusive prefix of the tile (in
+// lane 0).  `total` is the tile aggregate.
+__device__ __forceinline__ uint64_t lookback(uint64_t* stat, uint32_t tile, uint64_t total,
+                                             uint32_t* err) {
+  const int lane = threadIdx.x & 31;
+  if (tile == 0) {
+    if (lane == 0) st_release(&stat[0], FLAG_P | total);
+    return 0;
+  }
+  if (lane == 0) st_release(&stat[tile], FLAG_A | total);
+  uint64_t excl = 0;
+  int64_t look = (int64_t)tile - 1;
+  bool timed_out = false;
+  while (true) {
+    const int64_t idx = look - lane;
+    uint64_t v = FLAG_P;  // before tile 0: a zero prefix
+    if (idx >= 0) {
+      uint32_t spins = 0;
+      v = ld_acquire(&stat[idx]);
+      while ((v >> 62) == 0) {
+        if (++spins > SPIN_LIMIT) {
+          timed_out = true;
+          v = FLAG_P;
+          break;
+        }
+        __nanosleep(32);
+        v = ld_acquire(&stat[idx]);
+      }
+    }
+    const uint32_t pmask = __ballot_sync(0xffffffffu, (v >> 62) == 2);
+    uint64_t contrib = v & VAL_MASK;
+    if (pmask) {
+      const int first = __ffs(pmask) - 1;  // nearest predecessor holding a prefix
+      if (lane > first) contrib = 0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) contrib += __shfl_xor_sync(0xffffffffu, contrib, o);
+      excl += contrib;
+      break;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) contrib += __shfl_xor_sync(0xffffffffu, contrib, o);
+    excl += contrib;
+    look -= 32;
+  }
+  if (__any_sync(0xffffffffu, timed_out) && lane == 0) atomicOr(err, ERR_TIMEOUT);
+  if (lane == 0) st_release(&stat[tile], FLAG_P | ((excl + total) & VAL_MASK));
+  return excl;
+}
+
+// Scan sources.
+enum ScanMode { FROM_LOGLIK = 0, FROM_WEIGHTS = 1 };
+
+struct ScanArgs {
+  const void* src;          // l (R) or w (float)
+  uint64_t* Q;
+  uint64_t* stat[2];        // tile status by cycle parity; the other parity's
+                            // entries are cleared for the next cycle
+  void* part;               // per-tile log-ML partial (FROM_LOGLIK)
+  Ctl* ctl;
+  const uint32_t* t_dev;    // cycle index in device memory, or NULL
+  uint32_t t_arg;
+  uint64_t n;
+  int k;
+  int vec_ok;               // src is 16-byte aligned
+};
+
+template <int MODE, class R>
+__global__ void __launch_bounds__(BLOCK) k_scan(ScanArgs a) {
+  typedef typename ESumT<R>::T ES;
+  __shared__ uint32_t s_tile;
+  __shared__ uint64_t s_warp_tot[WARPS];
+  __shared__ uint64_t s_excl;
+  __shared__ ES s_es[WARPS];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) s_tile = atomicAdd(&a.ctl->ticket_w, 1u);
+  __syncthreads();
+  const uint32_t tile = s_tile;
+  const uint64_t wbase = (uint64_t)tile * TILE + (uint64_t)warp * (CHUNKS * CHUNK);
+  const uint32_t par = (a.t_dev ? *a.t_dev : a.t_arg) & 1u;
+  uint64_t* const stat = par ? a.stat[1] : a.stat[0];
+  uint64_t* const stat_next = par ? a.stat[0] : a.stat[1];
+
+  // the value that quantisation is relative to
+  R m = (R)0;
+  int escale = 0;
+  if (MODE == FROM_LOGLIK) {
+    if constexpr (sizeof(R) == 4) m = dec_f((uint32_t)a.ctl->maxenc);
+    else m = dec_d(a.ctl->maxenc);
+  } else {
+    int e;
+    (void)frexpf(__uint_as_float((uint32_t)a.ctl->maxenc), &e);
+    escale = a.k - e;
+  }
+
+  uint64_t W[CHUNKS][4];
+  ES es;
+  es.zero();
+#pragma unroll
+  for (int c = 0; c < CHUNKS; ++c) {
+    const uint64_t i0 = wbase + (uint64_t)c * CHUNK + 4 * lane;
+    R v[4];
+    if (i0 + 4 <= a.n && a.vec_ok) {
+      if constexpr (sizeof(R) == 4) {
+        const float4 f = *reinterpret_cast<const float4*>((const float*)a.src + i0);
+        v[0] = f.x; v[1] = f.y; v[2] = f.z; v[3] = f.w;
+      } else {
+        const double2 f0 = *reinterpret_cast<const double2*>((const double*)a.src + i0);
+        const double2 f1 = *reinterpret_cast<const double2*>((const double*)a.src + i0 + 2);
+        v[0] = f0.x; v[1] = f0.y; v[2] = f1.x; v[3] = f1.y;
+      }
+    } else {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) v[e] = (i0 + e < a.n) ? ((const R*)a.src)[i0 + e] : (R)0;
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      uint64_t w = 0;
+      if (i0 + e < a.n) {
+        if (MODE == FROM_LOGLIK) {
+          R ex;
+          const R dl = v[e] - m;
+          w = quant_exp<R>(dl, a.k, &ex);
+          es.add(ex);
+        } else {
+          const float wf = (float)v[e];
+          if (!(wf >= 0.0f) || !(wf < INFINITY)) atomicOr(&a.ctl->err, ERR_WEIGHTS);
+          else w = __float2ull_rz(ldexpf(wf, escale));
+        }
+      }
+      W[c][e] = w;
+    }
+  }
+
+  // warp-level inclusive prefix (in element order) of this warp's 512 values
+  uint64_t carry = 0;
+#pragma unroll
+  for (int c = 0; c < CHUNKS; ++c) {
+    W[c][1] += W[c][0];
+    W[c][2] += W[c][1];
+    W[c][3] += W[c][2];
+    const uint64_t incl = warp_incl_scan(W[c][3], lane);
+    const uint64_t excl_l = incl - W[c][3] + carry;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) W[c][e] += excl_l;
+    carry += __shfl_sync(0xffffffffu, incl, 31);
+  }
+  if (lane == 0) s_warp_tot[warp] = carry;
+  if (MODE == FROM_LOGLIK) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) es.add(es.shfl_xor(o));
+    if (lane == 0) s_es[warp] = es;
+  }
+  __syncthreads();
+
+  if (warp == 0) {
+    uint64_t wt = lane < WARPS ? s_warp_tot[lane] : 0;
+    const uint64_t wincl = warp_incl_scan(wt, lane);
+    if (lane < WARPS) s_warp_tot[lane] = wincl - wt;  // exclusive warp offsets
+    const uint64_t total = __shfl_sync(0xffffffffu, wincl, 31);
+    const uint64_t excl = lookback(stat, tile, total, &a.ctl->err);
+    if (lane == 0) {
+      s_excl = excl;
+      stat_next[tile] = 0;
+      if (MODE == FROM_LOGLIK) {
+        ES tot = s_es[0];
+        for (int w = 1; w < WARPS; ++w) tot.add(s_es[w]);
+        reinterpret_cast<ES*>(a.part)[tile] = tot;
+      }
+    }
+  }
+  __syncthreads();
+  const uint64_t off = s_excl + s_warp_tot[warp];
+
+  // store: two instructions per chunk, each covering 64 contiguous elements
+#pragma unroll
+  for (int c = 0; c < CHUNKS; ++c) {
+    const uint64_t cbase = wbase + (uint64_t)c * CHUNK;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      // lane l writes elements 64h + 2l and 64h + 2l + 1, which lane 16h + l/2
+      // holds at positions 2(l & 1) and 2(l & 1) + 1
+      const int src = 16 * h + (lane >> 1);
+      const bool upper = (lane & 1) != 0;
+      const uint64_t a0 = __shfl_sync(0xffffffffu, W[c][0], src);
+      const uint64_t a1 = __shfl_sync(0xffffffffu, W[c][1], src);
+      const uint64_t a2 = __shfl_sync(0xffffffffu, W[c][2], src);
+      const uint64_t a3 = __shfl_sync(0xffffffffu, W[c][3], src);
+      const uint64_t v0 = (upper ? a2 : a0) + off;
+      const uint64_t v1 = (upper ? a3 : a1) + off;
+      const uint64_t i = cbase + 64 * h + 2 * lane;
+      if (i + 2 <= a.n) {
+        *reinterpret_cast<ulonglong2*>(a.Q + i) = make_ulonglong2(v0, v1);
+      } else if (i < a.n) {
+        a.Q[i] = v0;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Multinomial positions: exponential spacings (Carpenter, Clifford &
+// Fearnhead 1999).  E_l = floor(-log(u_l) 2^31), u_l from draw
+// (seed, filter, t, l >> 2, SPACING) word l & 3; S = inclusive scan of E over
+// l = 0..n-1 by the same look-back scan, and S[n] = S[n-1] + E_n.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t spacing_E(uint64_t seed, uint32_t filter, uint32_t t,
+                                              uint64_t l, const U4& w) {
+  const uint32_t word = (l & 3) == 0 ? w.a : (l & 3) == 1 ? w.b : (l & 3) == 2 ? w.c : w.d;
+  const float u = unif_f32(word);
+  const float L = det_log(u);
+  const float x = -L * 0x1p31f;
+  return __float2ull_rz(x);
+}
+
+struct SpacingArgs {
+  uint64_t* S;
+  uint64_t* stat[2];
+  Ctl* ctl;
+  const uint32_t* t_dev;    // cycle index in device memory, or NULL
+  uint32_t t_arg;
+  uint64_t n;
+  uint64_t seed;
+  uint32_t filter;
+};
+
+__global__ void __launch_bounds__(BLOCK) k_spacing_scan(SpacingArgs a) {
+  __shared__ uint32_t s_tile;
+  __shared__ uint64_t s_warp_tot[WARPS];
+  __shared__ uint64_t s_excl;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) s_tile = atomicAdd(&a.ctl->ticket_e, 1u);
+  __syncthreads();
+  const uint32_t tile = s_tile;
+  const uint32_t t = a.t_dev ? *a.t_dev : a.t_arg;
+  const uint64_t wbase = (uint64_t)tile * TILE + (uint64_t)warp * (CHUNKS * CHUNK);
+  uint64_t W[CHUNKS][4];
+#pragma unroll
+  for (int c = 0; c < CHUNKS; ++c) {
+    const uint64_t i0 = wbase + (uint64_t)c * CHUNK + 4 * lane;  // multiple of 4
+    const U4 w = draw(a.seed, a.filter, t, (uint32_t)(i0 >> 2), P_SPACING, 0);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      uint64_t v = 0;
+      if (i0 + e < a.n) {
+        const uint32_t word = e == 0 ? w.a : e == 1 ? w.b : e == 2 ? w.c : w.d;
+        const float u = unif_f32(word);
+        const float L = det_log(u);
+        const float x = -L * 0x1p31f;
+        v = __float2ull_rz(x);
+      }
+      W[c][e] = v;
+    }
+  }
+  uint64_t carry = 0;
+#pragma unroll
+  for (int c = 0; c < CHUNKS; ++c) {
+    W[c][1] += W[c][0];
+    W[c][2] += W[c][1];
+    W[c][3] += W[c][2];
+    const uint64_t incl = warp_incl_scan(W[c][3], lane);
+    const uint64_t excl_l = incl - W[c][3] + carry;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) W[c][e] += excl_l;
+    carry += __shfl_sync(0xffffffffu, incl, 31);
+  }
+  if (lane == 0) s_warp_tot[warp] = carry;
+  __syncthreads();
+  if (warp == 0) {
+    uint64_t wt = lane < WARPS ? s_warp_tot[lane] : 0;
+    const uint64_t wincl = warp_incl_scan(wt, lane);
+    if (lane < WARPS) s_warp_tot[lane] = wincl - wt;
+    const uint64_t total = __shfl_sync(0xffffffffu, wincl, 31);
+    uint64_t* const stat = (t & 1u) ? a.stat[1] : a.stat[0];
+    uint64_t* const stat_next = (t & 1u) ? a.stat[0] : a.stat[1];
+    const uint64_t excl = lookback(stat, tile, total, &a.ctl->err);
+    if (lane == 0) {
+      s_excl = excl;
+      stat_next[tile] = 0;
+    }
+  }
+  __syncthreads();
+  const uint64_t off = s_excl + s_warp_tot[warp];
+#pragma unroll
+  for (int c = 0; c < CHUNKS; ++c) {
+    const uint64_t i0 = wbase + (uint64_t)c * CHUNK + 4 * lane;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const uint64_t i = i0 + e;
+      if (i < a.n) a.S[i] = W[c][e] + off;
+      if (i == a.n - 1) {
+        // S[n] = S[n-1] + E_n
+        const uint64_t ln = a.n;
+        const U4 w = draw(a.seed, a.filter, t, (uint32_t)(ln >> 2), P_SPACING, 0);
+        a.S[ln] = W[c][e] + off + spacing_E(a.seed, a.filter, t, ln, w);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Resampling by merge (paper Section 3.1, multinomial with sorted uniforms;
+// systematic): the merged order of the CDF keys KQ_i = Q_i * A and the
+// position keys KB_j is cut into equal diagonals (merge path, Green, McColl
+// & Bader 2012).  Each CTA finds its two diagonal splits with a warp-wide
+// 32-ary search, stages both key ranges in shared memory and merges.
+// Ties go to the CDF (Q_i * A <= B_j means particle i lies below slot j).
+// ---------------------------------------------------------------------------
+enum PosKind { POS_MULTINOMIAL = 0, POS_SYSTEMATIC = 1 };
+
+struct PosArgs {
+  const uint64_t* Q;
+  const uint64_t* S;      // multinomial: spacing prefix, n+1 entries
+  uint32_t* anc;
+  const uint32_t* I;      // cut-point table (cut-point kernels)
+  Ctl* ctl;
+  const uint32_t* t_dev;
+  uint32_t t_arg;
+  uint64_t n;
+  uint64_t seed;
+  uint32_t filter;
+};
+
+template <int POS>
+struct PosKeys {
+  const uint64_t* Q;
+  const uint64_t* S;
+  uint64_t n, T, A, r;
+  __device__ __forceinline__ U128 kq(uint64_t i) const { return mul64(Q[i], A); }
+  __device__ __forceinline__ U128 kb(uint64_t j) const {
+    if (POS == POS_SYSTEMATIC) return add128(mul64(j, T), r);
+    return mul64(S[j], T);
+  }
+};
+
+template <int POS>
+__device__ __forceinline__ PosKeys<POS> make_keys(const PosArgs& a) {
+  PosKeys<POS> K;
+  K.Q = a.Q;
+  K.S = a.S;
+  K.n = a.n;
+  K.T = a.Q[a.n - 1];
+  const uint32_t t = a.t_dev ? *a.t_dev : a.t_arg;
+  if (POS == POS_SYSTEMATIC) {
+    K.A = a.n;
+    const U4 w = draw(a.seed, a.filter, t, 0, P_SYS_OFFSET, 0);
+    const uint64_t R = ((uint64_t)w.b << 32) | w.a;
+    K.r = __umul64hi(R, K.T);
+  } else {
+    K.A = a.S[a.n];
+    K.r = 0;
+  }
+  return K;
+}
+
+// Number of CDF elements among the first d merged elements, by warp-wide
+// 32-ary search.  P(i) = (KQ_{i-1} <= KB_{d-i}) is true then false in i.
+template <int POS>
+__device__ __forceinline__ uint64_t warp_split(const PosKeys<POS>& K, uint64_t d) {
+  const int lane = threadIdx.x & 31;
+  uint64_t lo = d > K.n ? d - K.n : 0;
+  uint64_t hi = d < K.n ? d : K.n;
+  while (hi > lo) {
+    const uint64_t span = hi - lo;
+    const uint64_t q = lo + 1 + (span * (uint64_t)lane) / 32;
+    const bool p = le128(K.kq(q - 1), K.kb(d - q));
+    const uint32_t m = __ballot_sync(0xffffffffu, p);
+    if (m == 0) {
+      hi = lo;
+    } else {
+      const int kstar = 31 - __clz(m);  // trues form a prefix: last true lane
+      const uint64_t qk = __shfl_sync(0xffffffffu, q, kstar);
+      const uint64_t qn = __shfl_sync(0xffffffffu, q, kstar < 31 ? kstar + 1 : 31);
+      lo = qk;
+      if (kstar < 31) hi = qn - 1;
+    }
+  }
+  return lo;
+}
+
+template <int POS>
+__global__ void __launch_bounds__(BLOCK) k_merge(PosArgs a) {
+  __shared__ U128 s_key[MERGE_D];
+  __shared__ uint64_t s_split[2];
+  const PosKeys<POS> K = make_keys<POS>(a);
+  if (K.T == 0 || K.A == 0) {  // empty CDF: flag, keep every index in range
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&a.ctl->err, ERR_NUMERIC);
+    for (uint64_t j = (uint64_t)blockIdx.x * BLOCK + threadIdx.x; j < a.n;
+         j += (uint64_t)gridDim.x * BLOCK)
+      a.anc[j] = (uint32_t)j;
+    return;
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint64_t total = 2 * a.n;
+  const uint64_t d0 = (uint64_t)blockIdx.x * MERGE_D;
+  const uint64_t d1 = d0 + MERGE_D < total ? d0 + MERGE_D : total;
+  if (warp < 2) {
+    const uint64_t s = warp_split<POS>(K, warp == 0 ? d0 : d1);
+    if (lane == 0) s_split[warp] = s;
+  }
+  __syncthreads();
+  const uint64_t i0 = s_split[0], i1 = s_split[1];
+  const uint64_t j0 = d0 - i0, j1 = d1 - i1;
+  const int nA = (int)(i1 - i0), nB = (int)(j1 - j0);
+  for (int e = threadIdx.x; e < nA; e += BLOCK) s_key[e] = K.kq(i0 + e);
+  for (int e = threadIdx.x; e < nB; e += BLOCK) s_key[nA + e] = K.kb(j0 + e);
+  __syncthreads();
+  // this thread's diagonal range within the CTA's merge
+  const int dl0 = threadIdx.x * MERGE_E;
+  const int len = nA + nB;
+  if (dl0 >= len) return;
+  const int dl1 = dl0 + MERGE_E < len ? dl0 + MERGE_E : len;
+  // local split on diagonal dl0: largest ia with ia == lo or A[ia-1] <= B[dl0-ia]
+  int lo = dl0 > nB ? dl0 - nB : 0;
+  int hi = dl0 < nA ? dl0 : nA;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (le128(s_key[mid - 1], s_key[nA + dl0 - mid])) lo = mid;
+    else hi = mid - 1;
+  }
+  int ia = lo, jb = dl0 - lo;
+  for (int d = dl0; d < dl1; ++d) {
+    const bool takeA = jb >= nB || (ia < nA && le128(s_key[ia], s_key[nA + jb]));
+    if (takeA) {
+      ++ia;
+    } else {
+      const uint64_t an = i0 + ia;  // < n whenever T > 0
+      a.anc[j0 + jb] = (uint32_t)(an < a.n ? an : a.n - 1);
+      ++jb;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// The paper's Section 3.2 algorithms.
+// Parallelized Cut-Point Search: thread i computes L_i = ceil(n Q_i / T) and
+// writes I_k = i for L_{i-1} <= k < L_i.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t ceil_nq_over_t(uint64_t n, uint64_t q, uint64_t T) {
+  const U128 X = mul64(n, q);
+  const uint64_t f = div128_small(X, T);
+  const U128 p = mul64(f, T);
+  return (p.hi == X.hi && p.lo == X.lo) ? f : f + 1;
+}
+
+__global__ void __launch_bounds__(BLOCK) k_cutpoint_search(const uint64_t* Q, uint64_t n,
+                                                           uint32_t* I) {
+  const uint64_t i = (uint64_t)blockIdx.x * BLOCK + threadIdx.x;
+  if (i >= n) return;
+  const uint64_t T = Q[n - 1];
+  if (T == 0) {
+    I[i] = (uint32_t)i;
+    return;
+  }
+  uint64_t Li = ceil_nq_over_t(n, Q[i], T);
+  uint64_t Lp = i == 0 ? 0 : ceil_nq_over_t(n, Q[i - 1], T);
+  Li = Li < n ? Li : n;  // L_i <= n whenever Q_i <= T
+  Lp = Lp < n ? Lp : n;
+  for (uint64_t k = Lp; k < Li; ++k) I[k] = (uint32_t)i;
+}
+
+// Parallelized Cut-Point Method for the scheme's positions: bucket b_j
+// (systematic: j; multinomial: floor(n S_j / S_n)), start at I_{b_j}, climb
+// while KQ_k <= KB_j.
+template <int POS>
+__global__ void __launch_bounds__(BLOCK) k_cutpoint_method(PosArgs a) {
+  const uint64_t j = (uint64_t)blockIdx.x * BLOCK + threadIdx.x;
+  if (j >= a.n) return;
+  const PosKeys<POS> K = make_keys<POS>(a);
+  if (K.T == 0 || K.A == 0) {
+    if (j == 0) atomicOr(&a.ctl->err, ERR_NUMERIC);
+    a.anc[j] = (uint32_t)j;
+    return;
+  }
+  uint64_t b = j;
+  if (POS == POS_MULTINOMIAL) b = div128_small(mul64(a.n, a.S[j]), K.A);
+  uint64_t k = a.I[b < a.n ? b : a.n - 1];
+  const U128 kb = K.kb(j);
+  while (k < a.n && le128(K.kq(k), kb)) ++k;
+  a.anc[j] = (uint32_t)(k < a.n ? k : a.n - 1);
+}
+
+// Explicit integer positions U_j in [0, T) (A = 1).
+__global__ void __launch_bounds__(BLOCK) k_cutpoint_method_explicit(
+    const uint64_t* Q, uint64_t n, const uint32_t* I, const uint64_t* U, uint64_t m,
+    uint32_t* anc) {
+  const uint64_t j = (uint64_t)blockIdx.x * BLOCK + threadIdx.x;
+  if (j >= m) return;
+  const uint64_t T = Q[n - 1];
+  const uint64_t u = U[j];
+  const uint64_t b = T ? div128_small(mul64(n, u), T) : 0;
+  uint64_t k = I[b < n ? b : n - 1];
+  while (k < n && Q[k] <= u) ++k;
+  anc[j] = (uint32_t)(k < n ? k : n - 1);
+}
+
+// ---------------------------------------------------------------------------
+// Steps 2-4: propagate x, update the sufficient statistics, draw theta.
+// The last block to finish folds the log-ML partials, resets the per-cycle
+// counters and advances t.
+// ---------------------------------------------------------------------------
+template <class R> struct ResidObs;
+template <> struct ResidObs<float> {
+  static __device__ __forceinline__ float f(double, float yr, float xj) { return yr - xj; }
+};
+template <> struct ResidObs<double> {
+  static __device__ __forceinline__ double f(double y, double, double xj) { return y - xj; }
+};
+
+__device__ __forceinline__ double esum_value(const ESum32& e) {
+  return __ull2double_rn(e.s.hi) * 0x1p-32 + __ull2double_rn(e.s.lo) * 0x1p-96;
+}
+__device__ __forceinline__ double esum_value(const ESum64& e) { return e.s; }
+
+template <class R>
+__device__ void fold_cycle(FilterArgs<R>& a, uint32_t t) {
+  typedef typename ESumT<R>::T ES;
+  __shared__ ES s_part[BLOCK];
+  ES acc;
+  acc.zero();
+  for (uint32_t b = threadIdx.x; b < a.ntiles; b += BLOCK)
+    acc.add(reinterpret_cast<const ES*>(a.part)[b]);
+  s_part[threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ES tot = s_part[0];
+    for (int i = 1; i < BLOCK; ++i) tot.add(s_part[i]);
+    const double m = sizeof(R) == 4 ? (double)dec_f((uint32_t)a.ctl->maxenc)
+                                    : dec_d(a.ctl->maxenc);
+    const double LOG_2PI = 0x1.d67f1c864beb5p+0;
+    const double inc = m + log(esum_value(tot)) - log((double)a.n) - 0.5 * LOG_2PI;
+    a.ctl->logml = a.ctl->logml + inc;
+    a.ctl->maxenc = sizeof(R) == 4 ? (unsigned long long)enc_f(-INFINITY) : enc_d(-INFINITY);
+    a.ctl->ticket_w = 0;
+    a.ctl->ticket_e = 0;
+    a.ctl->done_prop = 0;
+    __threadfence();
+    a.ctl->t = t + 1;
+  }
+}
+
+template <class R, bool LEARN>
+__global__ void __launch_bounds__(BLOCK) k_propagate(FilterArgs<R> a) {
+  __shared__ double s_c[4];
+  __shared__ bool s_last;
+  const uint32_t t = a.ctl->t;
+  if (LEARN && threadIdx.x == 0) {
+    double ds, cs, dt, ct;
+    mt_constants(a.a_sigma + 0.5 * (double)(t + 1), &ds, &cs);
+    mt_constants(a.a_tau + 0.5 * (double)(t + 1), &dt, &ct);
+    s_c[0] = ds; s_c[1] = cs; s_c[2] = dt; s_c[3] = ct;
+  }
+  __syncthreads();
+  const StateV<R> src = (t & 1) ? a.st[1] : a.st[0];
+  const StateV<R> dst = (t & 1) ? a.st[0] : a.st[1];
+  const double y = a.y_ring[t % a.cap];
+  const R yr = (R)y;
+  const uint64_t j = (uint64_t)blockIdx.x * BLOCK + threadIdx.x;
+  bool fail = false;
+  if (j < a.n) {
+    const uint32_t an0 = a.anc[j];
+    const uint32_t an = an0 < a.n ? an0 : (uint32_t)(a.n - 1);
+    const R xa = src.x[an], sa = src.s2[an], ta = src.t2[an];
+    const R s = sa + ta;
+    const R p = sa * ta;
+    const R V = p / s;
+    const R n1 = xa * sa;
+    const R n2 = yr * ta;
+    const R nn = n1 + n2;
+    const R mu = nn / s;
+    const R sv = sqrt(V);
+    const R Z = bm_normal(draw(a.seed, a.filter, t, (uint32_t)j, P_STATE, 0), (R)0);
+    const R xz = sv * Z;
+    const R xj = mu + xz;
+    dst.x[j] = xj;
+    if (LEARN) {
+      const R rs = ResidObs<R>::f(y, yr, xj);
+      const R rt = xj - xa;
+      const auto bsn = SuffOps<R>::add_half_square(src.bs[an], rs, &fail);
+      const auto btn = SuffOps<R>::add_half_square(src.bt[an], rt, &fail);
+      const R Gs = gamma_mt<R>((R)s_c[0], (R)s_c[1], a.seed, a.filter, t, (uint32_t)j,
+                               P_GAMMA_SIGMA, &fail);
+      const R Gt = gamma_mt<R>((R)s_c[2], (R)s_c[3], a.seed, a.filter, t, (uint32_t)j,
+                               P_GAMMA_TAU, &fail);
+      dst.bs[j] = bsn;
+      dst.bt[j] = btn;
+      dst.s2[j] = SuffOps<R>::ig(bsn, Gs);
+      dst.t2[j] = SuffOps<R>::ig(btn, Gt);
+    } else {
+      dst.s2[j] = sa;
+      dst.t2[j] = ta;
+      dst.bs[j] = src.bs[an];
+      dst.bt[j] = src.bt[an];
+    }
+  }
+  if (__syncthreads_or(fail) && threadIdx.x == 0) atomicOr(&a.ctl->err, ERR_NUMERIC);
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = atomicAdd(&a.ctl->done_prop, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (s_last) {
+    __threadfence();
+    fold_cycle<R>(a, t);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Posterior summaries (on demand): population means and variances of x,
+// sigma^2 and tau^2.  Per block: sums of v - c and (v - c)^2 with c the value
+// of particle 0 (shift against cancellation), accumulated in binary64 across
+// threads; the last block folds the block partials in block order.
+// ---------------------------------------------------------------------------
+constexpr int EST_PER_THREAD = 8;
+
+template <class R>
+__global__ void __launch_bounds__(BLOCK) k_estimate(FilterArgs<R> a) {
+  __shared__ double s_sum[6][WARPS];
+  __shared__ bool s_last;
+  const uint32_t t = a.ctl->t;
+  const StateV<R> st = (t & 1) ? a.st[1] : a.st[0];
+  const R c0 = st.x[0], c1 = st.s2[0], c2 = st.t2[0];
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  {
+    R loc[6] = {0, 0, 0, 0, 0, 0};
+    const uint64_t base = ((uint64_t)blockIdx.x * BLOCK + threadIdx.x) * EST_PER_THREAD;
+#pragma unroll
+    for (int e = 0; e < EST_PER_THREAD; ++e) {
+      const uint64_t i = base + e;
+      if (i < a.n) {
+        const R dx = st.x[i] - c0, ds = st.s2[i] - c1, dt = st.t2[i] - c2;
+        loc[0] += dx; loc[1] += dx * dx;
+        loc[2] += ds; loc[3] += ds * ds;
+        loc[4] += dt; loc[5] += dt * dt;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 6; ++q) acc[q] = (double)loc[q];
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    double v = acc[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) s_sum[q][warp] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 6) {
+    double v = 0;
+    for (int w = 0; w < WARPS; ++w) v += s_sum[threadIdx.x][w];
+    a.part_est[(uint64_t)blockIdx.x * 6 + threadIdx.x] = v;
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = atomicAdd(&a.ctl->done_est, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  // fold the block partials: thread i sums blocks i, i + BLOCK, ... (a fixed
+  // assignment, so the result is run-to-run deterministic), then one thread
+  // per column sums the BLOCK thread totals in order
+  __shared__ double s_col[6][BLOCK];
+  {
+    double v[6] = {0, 0, 0, 0, 0, 0};
+    for (uint32_t b = threadIdx.x; b < gridDim.x; b += BLOCK) {
+#pragma unroll
+      for (int q = 0; q < 6; ++q) v[q] += __ldcg(a.part_est + (uint64_t)b * 6 + q);
+    }
+#pragma unroll
+    for (int q = 0; q < 6; ++q) s_col[q][threadIdx.x] = v[q];
+  }
+  __syncthreads();
+  __shared__ double s_tot[6];
+  if (threadIdx.x < 6) {
+    double v = 0;
+    for (int i = 0; i < BLOCK; ++i) v += s_col[threadIdx.x][i];
+    s_tot[threadIdx.x] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const double n = (double)a.n;
+    const double cs[3] = {(double)c0, (double)c1, (double)c2};
+    a.ctl->est[0] = (double)t;
+    for (int q = 0; q < 3; ++q) {
+      const double m1 = s_tot[2 * q] / n;
+      const double m2 = s_tot[2 * q + 1] / n;
+      a.ctl->est[1 + 2 * q] = cs[q] + m1;
+      a.ctl->est[2 + 2 * q] = m2 - m1 * m1;
+    }
+    a.ctl->est[7] = a.ctl->logml;
+    a.ctl->done_est = 0;
+  }
+}
+
+// Maximum of binary32 input weights (pf_resample): non-negative floats order
+// as their bit patterns.
+__global__ void __launch_bounds__(BLOCK) k_wmax(const float* w, uint64_t n, Ctl* ctl) {
+  __shared__ uint32_t s_red[WARPS];
+  uint32_t mx = 0;
+  bool bad = false;
+  for (uint64_t i = (uint64_t)blockIdx.x * BLOCK + threadIdx.x; i < n;
+       i += (uint64_t)gridDim.x * BLOCK) {
+    const float v = w[i];
+    if (!(v >= 0.0f) || !(v < INFINITY)) bad = true;
+    else mx = max(mx, __float_as_uint(v));
+  }
+  if (bad) atomicOr(&ctl->err, ERR_WEIGHTS);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0) s_red[warp] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = 1; i < WARPS; ++i) mx = max(mx, s_red[i]);
+    mx = max(mx, s_red[0]);
+    atomicMax(&ctl->maxenc, (unsigned long long)mx);
+  }
+}
+
+}  // namespace pfk

@@ -1,0 +1,255 @@
+"""Thin ctypes binding of libpf.so (include/pf.h).
+
+Argument marshalling only: every step of the particle-learning cycle runs in
+the library's CUDA kernels.  PyTorch supplies device memory (through the
+allocator callbacks) and streams.  Importing this module loads libpf.so and
+raises if it has not been built; there is no fallback path.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpf.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError("libpf.so is not built: run __graft_entry__.build() "
+                      "(or python paper_1212_1639_gb300/build.py)")
+
+_lib = C.CDLL(LIB_PATH)
+
+PF_OK, PF_ERR_INVALID, PF_ERR_OOM, PF_ERR_CUDA, PF_ERR_NUMERIC, PF_ERR_TIMEOUT, PF_ERR_BUSY = range(7)
+STATUS_NAMES = {0: "PF_OK", 1: "PF_ERR_INVALID", 2: "PF_ERR_OOM", 3: "PF_ERR_CUDA",
+                4: "PF_ERR_NUMERIC", 5: "PF_ERR_TIMEOUT", 6: "PF_ERR_BUSY"}
+MULTINOMIAL, SYSTEMATIC, MULTINOMIAL_CUTPOINT, SYSTEMATIC_CUTPOINT = 0, 1, 2, 3
+SCHEMES = {"multinomial": 0, "systematic": 1, "multinomial_cutpoint": 2, "systematic_cutpoint": 3}
+FP32, FP64 = 0, 1
+MAX_PARTICLES = 1 << 26
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
+
+
+class PfConfig(C.Structure):
+    _fields_ = [("n_particles", C.c_uint64), ("seed", C.c_uint64), ("filter_id", C.c_uint32),
+                ("scheme", C.c_int32), ("precision", C.c_int32),
+                ("known_variances", C.c_int32),
+                ("x0_mean", C.c_double), ("x0_var", C.c_double),
+                ("a_sigma", C.c_double), ("b_sigma", C.c_double),
+                ("a_tau", C.c_double), ("b_tau", C.c_double),
+                ("sigma2", C.c_double), ("tau2", C.c_double),
+                ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN),
+                ("alloc_ctx", C.c_void_p)]
+
+
+class PfEstimates(C.Structure):
+    _fields_ = [("t", C.c_uint64), ("x_mean", C.c_double), ("x_var", C.c_double),
+                ("sigma2_mean", C.c_double), ("sigma2_var", C.c_double),
+                ("tau2_mean", C.c_double), ("tau2_var", C.c_double),
+                ("log_marglik", C.c_double)]
+
+
+_V = C.c_void_p
+_SIGS = {
+    "pf_create": [C.POINTER(PfConfig), C.POINTER(_V)],
+    "pf_step": [_V, C.c_double],
+    "pf_run": [_V, _V, C.c_uint32],
+    "pf_estimate": [_V, C.POINTER(PfEstimates)],
+    "pf_sync": [_V],
+    "pf_step_profiled": [_V, C.c_double, C.POINTER(C.c_float), C.POINTER(C.c_char_p), C.c_int,
+                         C.POINTER(C.c_int)],
+    "pf_get_particles": [_V, _V, _V, _V, _V, _V],
+    "pf_get_ancestors": [_V, _V, _V],
+    "pf_destroy": [_V],
+    "pf_resample": [_V, C.c_uint64, C.c_uint64, C.c_uint32, C.c_uint32, C.c_int32, _V, _V],
+    "pf_cdf": [_V, C.c_uint64, _V, _V],
+    "pf_cutpoint_search": [_V, C.c_uint64, _V, _V],
+    "pf_cutpoint_method": [_V, C.c_uint64, _V, _V, C.c_uint64, _V, _V],
+}
+for _name, _args in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = C.c_int
+_lib.pf_last_error.restype = C.c_char_p
+_lib.pf_last_error.argtypes = []
+
+
+class PfError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        msg = _lib.pf_last_error().decode(errors="replace")
+        super().__init__("%s: %s (%s)" % (where, STATUS_NAMES.get(status, status), msg))
+
+
+def _check(status, where):
+    if status != PF_OK:
+        raise PfError(status, where)
+
+
+def last_error():
+    return _lib.pf_last_error().decode(errors="replace")
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(stream):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr())
+
+
+class TorchAllocator:
+    """Device allocations of a filter handle through torch's caching allocator."""
+
+    def __init__(self):
+        torch = _torch()
+        self.device = torch.cuda.current_device()
+
+        def _alloc(nbytes, stream, ctx):
+            try:
+                return torch.cuda.caching_allocator_alloc(int(nbytes), self.device, stream)
+            except Exception:
+                return None
+
+        def _free(ptr, stream, ctx):
+            try:
+                torch.cuda.caching_allocator_delete(ptr)
+            except Exception:
+                pass
+
+        self.alloc = ALLOC_FN(_alloc)
+        self.free = FREE_FN(_free)
+
+
+class Filter:
+    """One particle-learning filter (paper Section 2, Algorithm "Particle Learning")."""
+
+    def __init__(self, n, seed=1212, filter_id=0, scheme="systematic", precision="fp32",
+                 x0_mean=0.0, x0_var=10.0, a_sigma=3.0, b_sigma=2.0, a_tau=3.0, b_tau=2.0,
+                 known_variances=False, sigma2=1.0, tau2=0.1, stream=None, torch_alloc=True):
+        torch = _torch()
+        self.n = int(n)
+        self.precision = FP64 if precision in ("fp64", FP64) else FP32
+        self.scheme = SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
+        # a real (non-legacy) stream: the cycle is captured as a CUDA graph on it
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        if self.stream.cuda_stream == 0:
+            raise ValueError("pass a non-default torch.cuda.Stream (the cycle is graph-captured)")
+        self._alloc = TorchAllocator() if torch_alloc else None
+        cfg = PfConfig(n_particles=self.n, seed=seed, filter_id=filter_id, scheme=self.scheme,
+                       precision=self.precision, known_variances=int(bool(known_variances)),
+                       x0_mean=x0_mean, x0_var=x0_var, a_sigma=a_sigma, b_sigma=b_sigma,
+                       a_tau=a_tau, b_tau=b_tau, sigma2=sigma2, tau2=tau2,
+                       stream=C.c_void_p(self.stream.cuda_stream))
+        if self._alloc is not None:
+            cfg.alloc = self._alloc.alloc
+            cfg.free = self._alloc.free
+        self._cfg = cfg
+        h = C.c_void_p()
+        _check(_lib.pf_create(C.byref(cfg), C.byref(h)), "pf_create")
+        self.h = h
+
+    def step(self, y):
+        _check(_lib.pf_step(self.h, float(y)), "pf_step")
+
+    def run(self, y):
+        """y: a float64 CUDA tensor (device-resident observations) or array-like."""
+        torch = _torch()
+        if isinstance(y, torch.Tensor) and y.is_cuda:
+            y = y.to(torch.float64).contiguous()
+            if self.stream != torch.cuda.current_stream():
+                self.stream.wait_stream(torch.cuda.current_stream())
+                y.record_stream(self.stream)
+            _check(_lib.pf_run(self.h, _ptr(y), y.numel()), "pf_run")
+        else:
+            arr = np.ascontiguousarray(np.asarray(y, dtype=np.float64))
+            _check(_lib.pf_run(self.h, arr.ctypes.data_as(C.c_void_p), arr.size), "pf_run")
+
+    def sync(self):
+        _check(_lib.pf_sync(self.h), "pf_sync")
+
+    def step_profiled(self, y):
+        """One cycle with per-kernel CUDA-event timing: {kernel name: ms}."""
+        ms = (C.c_float * 8)()
+        names = (C.c_char_p * 8)()
+        cnt = C.c_int()
+        _check(_lib.pf_step_profiled(self.h, float(y), ms, names, 8, C.byref(cnt)),
+               "pf_step_profiled")
+        return {names[i].decode(): float(ms[i]) for i in range(cnt.value)}
+
+    def estimate(self):
+        e = PfEstimates()
+        _check(_lib.pf_estimate(self.h, C.byref(e)), "pf_estimate")
+        return {f: getattr(e, f) for f, _ in PfEstimates._fields_}
+
+    def particles(self):
+        torch = _torch()
+        rt = torch.float64 if self.precision == FP64 else torch.float32
+        bt = torch.float64 if self.precision == FP64 else torch.int64  # uint64 bits
+        out = [torch.empty(self.n, dtype=rt, device="cuda") for _ in range(3)]
+        out += [torch.empty(self.n, dtype=bt, device="cuda") for _ in range(2)]
+        _check(_lib.pf_get_particles(self.h, *[_ptr(t) for t in out]), "pf_get_particles")
+        return dict(zip(("x", "sigma2", "tau2", "b_sigma", "b_tau"), out))
+
+    def ancestors(self, with_cdf=False):
+        torch = _torch()
+        anc = torch.empty(self.n, dtype=torch.int32, device="cuda")
+        Q = torch.empty(self.n, dtype=torch.int64, device="cuda") if with_cdf else None
+        _check(_lib.pf_get_ancestors(self.h, _ptr(anc), _ptr(Q) if Q is not None else None),
+               "pf_get_ancestors")
+        return (anc, Q) if with_cdf else anc
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.pf_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def resample(w, seed, filter_id=0, t=0, scheme="systematic", out=None, stream=None):
+    """Ancestors (int32 CUDA tensor viewed as uint32) for float32 CUDA weights w."""
+    torch = _torch()
+    assert w.is_cuda and w.dtype == torch.float32 and w.is_contiguous()
+    n = w.numel()
+    anc = out if out is not None else torch.empty(n, dtype=torch.int32, device=w.device)
+    sch = SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
+    _check(_lib.pf_resample(_ptr(w), n, seed, filter_id, t, sch, _ptr(anc), _stream_ptr(stream)),
+           "pf_resample")
+    return anc
+
+
+def cdf(w, stream=None):
+    torch = _torch()
+    assert w.is_cuda and w.dtype == torch.float32 and w.is_contiguous()
+    Q = torch.empty(w.numel(), dtype=torch.int64, device=w.device)
+    _check(_lib.pf_cdf(_ptr(w), w.numel(), _ptr(Q), _stream_ptr(stream)), "pf_cdf")
+    return Q
+
+
+def cutpoint_search(Q, stream=None):
+    torch = _torch()
+    I = torch.empty(Q.numel(), dtype=torch.int32, device=Q.device)
+    _check(_lib.pf_cutpoint_search(_ptr(Q), Q.numel(), _ptr(I), _stream_ptr(stream)),
+           "pf_cutpoint_search")
+    return I
+
+
+def cutpoint_method(Q, I, U, stream=None):
+    torch = _torch()
+    anc = torch.empty(U.numel(), dtype=torch.int32, device=Q.device)
+    _check(_lib.pf_cutpoint_method(_ptr(Q), Q.numel(), _ptr(I), _ptr(U), U.numel(), _ptr(anc),
+                                   _stream_ptr(stream)), "pf_cutpoint_method")
+    return anc
