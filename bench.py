@@ -46,6 +46,7 @@ BYTES_PER_PARTICLE = {
     "weights": 12 + 4,            # read x, sigma2, tau2; write l
     "scan": 4 + 8,                # read l; write Q
     "spacing_scan": 8,            # write S
+    "partition": 0,               # one merge-path split per 2048 merged elements
     "merge_systematic": 8 + 4,    # read Q; write ancestors
     "merge_multinomial": 8 + 8 + 4,  # read Q and S; write ancestors
     "cutpoint_search": 8 + 4,     # read Q; write I
@@ -295,6 +296,7 @@ def bench_ours(args):
         ms24 = time_cycles(f24, y_dev, 3, K24, stream, None)
         prof24 = kernel_profile(f24, y, 3 + K24, 5, None)
         b24 = {k: BYTES_PER_PARTICLE["merge_systematic" if k == "merge" else k] * n24 for k in prof24}
+        b24 = {k: max(v, 1) for k, v in b24.items()}
         extra["n_2p24"] = {
             "value": n24 * K24 / (ms24 / 1e3), "unit": UNIT, "steps": K24,
             "ms_per_step": ms24 / K24, "l2": "inputs larger than L2 (no flush)",

@@ -56,6 +56,12 @@ void or_det_cos2pi_f32(const float* in, float* out, uint64_t n) {
 void or_det_cos2pi_f64(const double* in, double* out, uint64_t n) {
   for (uint64_t i = 0; i < n; ++i) out[i] = det_cos2pi<double>(in[i]);
 }
+void or_det_sincos2pi_f32(const float* in, float* s, float* c, uint64_t n) {
+  for (uint64_t i = 0; i < n; ++i) det_sincos2pi<float>(in[i], &s[i], &c[i]);
+}
+void or_det_sincos2pi_f64(const double* in, double* s, double* c, uint64_t n) {
+  for (uint64_t i = 0; i < n; ++i) det_sincos2pi<double>(in[i], &s[i], &c[i]);
+}
 void or_quant_exp_f32(const float* dl, uint64_t n, int k, uint64_t* W, float* e) {
   for (uint64_t i = 0; i < n; ++i) W[i] = quant_exp<float>(dl[i], k, &e[i]);
 }

@@ -61,15 +61,18 @@ double unif_f64_32(uint32_t w);                 // (2*w+1) * 2^-33
 template <class R> R det_log(R x);          // x > 0, finite, normal
 template <class R> R det_exp_core(R r);     // Taylor polynomial of exp on |r| <= ~0.35
 template <class R> R det_cos2pi(R u);       // cos(2*pi*u) for u in [0, 1]
+template <class R> void det_sincos2pi(R u, R* s, R* c);  // both, same reduction
 
 // Quantised weight of the fixed-point CDF: for dl = l_i - max_j l_j <= 0,
 // *e = exp(dl) as evaluated by the deterministic exp (0 below dl = -50),
 // return floor(*e * 2^k) clamped to 2^k.
 template <class R> uint64_t quant_exp(R dl, int k, R* e);
 
-// Standard normal by Box-Muller (first output) from one 128-bit draw, and the
-// extra uniform the gamma sampler needs from the same draw.
+// Standard normal by Box-Muller (first output) from one 128-bit draw, both
+// outputs (cos and sin branches), and the extra uniform the gamma sampler
+// needs from the same draw.
 template <class R> R bm_normal(const W4& w);
+template <class R> void bm_normal2(const W4& w, R* zc, R* zs);
 template <class R> R extra_uniform(const W4& w);
 
 // Gamma(a, 1) by Marsaglia & Tsang (2000), a >= 1, with d = a - 1/3 and
@@ -77,6 +80,18 @@ template <class R> R extra_uniform(const W4& w);
 // draw (purpose, attempt k); after 16 rejections *fail is set and d returned.
 template <class R> R gamma_mt(R d, R c, uint64_t seed, uint32_t filter, uint32_t t,
                               uint32_t j, uint32_t purpose, int* fail);
+// The same with the first attempt's (Z, U) given; attempts k >= 1 use draw
+// (purpose, k).
+template <class R> R gamma_mt_from(R d, R c, R Z0, R U0, uint64_t seed, uint32_t filter,
+                                   uint32_t t, uint32_t j, uint32_t purpose, int* fail);
+
+// The draws of one propagation step for slot j: two 128-bit draws,
+// A = (j, t, STATE, attempt 0) and B = (j, t, STATE, attempt 1).  Box-Muller
+// on A gives the state normal (cos branch) and the first normal of the
+// sigma^2 gamma draw (sin branch); A's extra uniform is that draw's first
+// uniform; B gives the tau^2 gamma draw's first normal and uniform.
+template <class R> void theta_draws(uint64_t seed, uint32_t filter, uint32_t t, uint32_t j,
+                                    R* Zx, R* Zs, R* Us, R* Zt, R* Ut);
 
 // Shape constants (d, c) of Marsaglia-Tsang for shape a, in double.
 void mt_constants(double a, double* d, double* c);

@@ -50,6 +50,8 @@ def _declare(L):
         "or_det_exp_core_f64": (V, [f64p, f64p, U64]),
         "or_det_cos2pi_f32": (V, [f32p, f32p, U64]),
         "or_det_cos2pi_f64": (V, [f64p, f64p, U64]),
+        "or_det_sincos2pi_f32": (V, [f32p, f32p, f32p, U64]),
+        "or_det_sincos2pi_f64": (V, [f64p, f64p, f64p, U64]),
         "or_quant_exp_f32": (V, [f32p, U64, I, u64p, f32p]),
         "or_quant_exp_f64": (V, [f64p, U64, I, u64p, f64p]),
         "or_normals_f32": (V, [U64, U32, U32, U32, U64, f32p]),
@@ -140,6 +142,15 @@ def det_exp_core(x, dtype=np.float32):
 
 def det_cos2pi(x, dtype=np.float32):
     return _vec("or_det_cos2pi_f32" if dtype == np.float32 else "or_det_cos2pi_f64", x, dtype)
+
+
+def det_sincos2pi(x, dtype=np.float32):
+    x = np.ascontiguousarray(x, dtype)
+    s = np.zeros_like(x)
+    c = np.zeros_like(x)
+    f = lib().or_det_sincos2pi_f32 if dtype == np.float32 else lib().or_det_sincos2pi_f64
+    f(x, s, c, x.size)
+    return s, c
 
 
 def quant_exp(dl, k, dtype=np.float32):

@@ -172,7 +172,8 @@ template <class R> class Filter : public FilterBase {
       R nn = n1 + n2;
       R mu = nn / s;
       R sv = std::sqrt(V);
-      R Z = bm_normal<R>(draw(cfg.seed, cfg.filter_id, t, (uint32_t)j, P_STATE, 0));
+      R Z, Zs, Us, Zt, Ut;
+      theta_draws<R>(cfg.seed, cfg.filter_id, t, (uint32_t)j, &Z, &Zs, &Us, &Zt, &Ut);
       R xz = sv * Z;
       R xj = mu + xz;
       xn[j] = xj;
@@ -184,10 +185,10 @@ template <class R> class Filter : public FilterBase {
       R rt = xj - xa;
       bsn[j] = Suff<R>::add_half_square(bs[a], rs, &fail);
       btn[j] = Suff<R>::add_half_square(bt[a], rt, &fail);
-      R Gs = gamma_mt<R>((R)ds, (R)cs, cfg.seed, cfg.filter_id, t, (uint32_t)j,
-                         P_GAMMA_SIGMA, &fail);
-      R Gt = gamma_mt<R>((R)dt, (R)ct, cfg.seed, cfg.filter_id, t, (uint32_t)j,
-                         P_GAMMA_TAU, &fail);
+      R Gs = gamma_mt_from<R>((R)ds, (R)cs, Zs, Us, cfg.seed, cfg.filter_id, t, (uint32_t)j,
+                              P_GAMMA_SIGMA, &fail);
+      R Gt = gamma_mt_from<R>((R)dt, (R)ct, Zt, Ut, cfg.seed, cfg.filter_id, t, (uint32_t)j,
+                              P_GAMMA_TAU, &fail);
       s2n[j] = Suff<R>::ig(bsn[j], Gs);
       t2n[j] = Suff<R>::ig(btn[j], Gt);
     }
@@ -279,10 +280,12 @@ int suffstat_known_states(const Config& cfg, const double* xpath, const double* 
       double ds, cs, dt, ct;
       mt_constants(cfg.a_sigma + 0.5 * (double)(t + 1), &ds, &cs);
       mt_constants(cfg.a_tau + 0.5 * (double)(t + 1), &dt, &ct);
-      R Gs = gamma_mt<R>((R)ds, (R)cs, cfg.seed, cfg.filter_id, t, (uint32_t)j,
-                         P_GAMMA_SIGMA, &fail);
-      R Gt = gamma_mt<R>((R)dt, (R)ct, cfg.seed, cfg.filter_id, t, (uint32_t)j,
-                         P_GAMMA_TAU, &fail);
+      R Zx, Zs, Us, Zt, Ut;
+      theta_draws<R>(cfg.seed, cfg.filter_id, t, (uint32_t)j, &Zx, &Zs, &Us, &Zt, &Ut);
+      R Gs = gamma_mt_from<R>((R)ds, (R)cs, Zs, Us, cfg.seed, cfg.filter_id, t, (uint32_t)j,
+                              P_GAMMA_SIGMA, &fail);
+      R Gt = gamma_mt_from<R>((R)dt, (R)ct, Zt, Ut, cfg.seed, cfg.filter_id, t, (uint32_t)j,
+                              P_GAMMA_TAU, &fail);
       s2v = Suff<R>::ig(bs, Gs);
       t2v = Suff<R>::ig(bt, Gt);
     }

@@ -153,10 +153,7 @@ template <class R> R det_log(R x) {
   R z = num / den;
   R z2 = z * z;
   R p = inv_odd<R>(K<R>::LOG_K);
-  for (int m = K<R>::LOG_K - 1; m >= 0; --m) {
-    p = p * z2;
-    p = p + inv_odd<R>(m);
-  }
+  for (int m = K<R>::LOG_K - 1; m >= 0; --m) p = std::fma(p, z2, inv_odd<R>(m));
   R two_z = z * (R)2;
   R logf = two_z * p;
   R elog2 = (R)e * K<R>::LN2;
@@ -165,10 +162,7 @@ template <class R> R det_log(R x) {
 
 template <class R> R det_exp_core(R r) {
   R p = inv_fact<R>(K<R>::EXP_D);
-  for (int k = K<R>::EXP_D - 1; k >= 0; --k) {
-    p = p * r;
-    p = p + inv_fact<R>(k);
-  }
+  for (int k = K<R>::EXP_D - 1; k >= 0; --k) p = std::fma(p, r, inv_fact<R>(k));
   return p;
 }
 
@@ -178,8 +172,7 @@ template <class R> static inline R cos_poly(R x) {
   R p = (kk & 1) ? -inv_fact<R>(2 * kk) : inv_fact<R>(2 * kk);
   for (int m = kk - 1; m >= 0; --m) {
     R c = (m & 1) ? -inv_fact<R>(2 * m) : inv_fact<R>(2 * m);
-    p = p * x2;
-    p = p + c;
+    p = std::fma(p, x2, c);
   }
   return p;
 }
@@ -189,8 +182,7 @@ template <class R> static inline R sin_poly(R x) {
   R p = (kk & 1) ? -inv_fact<R>(2 * kk + 1) : inv_fact<R>(2 * kk + 1);
   for (int m = kk - 1; m >= 0; --m) {
     R c = (m & 1) ? -inv_fact<R>(2 * m + 1) : inv_fact<R>(2 * m + 1);
-    p = p * x2;
-    p = p + c;
+    p = std::fma(p, x2, c);
   }
   return x * p;
 }
@@ -210,6 +202,32 @@ template <class R> R det_cos2pi(R u) {
     R x = K<R>::TWO_PI * a;
     return -cos_poly(x);
   }
+}
+
+// sin(2 pi u) and cos(2 pi u) together, same reduction as det_cos2pi:
+// with w = |u - rint(u)|, the octant picks the argument x = 2 pi a and which
+// of the two polynomials gives each value; sin takes the sign of u - rint(u).
+template <class R> void det_sincos2pi(R u, R* s, R* c) {
+  R v = u - std::rint(u);
+  R w = std::fabs(v);
+  R sv, cv;
+  if (w <= (R)0.125) {
+    R x = K<R>::TWO_PI * w;
+    sv = sin_poly(x);
+    cv = cos_poly(x);
+  } else if (w <= (R)0.375) {
+    R a = (R)0.25 - w;
+    R x = K<R>::TWO_PI * a;
+    sv = cos_poly(x);
+    cv = sin_poly(x);
+  } else {
+    R a = (R)0.5 - w;
+    R x = K<R>::TWO_PI * a;
+    sv = sin_poly(x);
+    cv = -cos_poly(x);
+  }
+  *s = v < (R)0 ? -sv : sv;
+  *c = cv;
 }
 
 template <class R> static inline R pow2(int n) { return std::ldexp((R)1, n); }
@@ -258,6 +276,28 @@ template <> double bm_normal<double>(const W4& w) {
   double c = det_cos2pi(u2);
   return r * c;
 }
+template <> void bm_normal2<float>(const W4& w, float* zc, float* zs) {
+  float u1 = unif_f32(w.w[0]);
+  float u2 = unif_f32(w.w[1]);
+  float L = det_log(u1);
+  float m2 = L * -2.0f;
+  float r = std::sqrt(m2);
+  float sn, cs;
+  det_sincos2pi(u2, &sn, &cs);
+  *zc = r * cs;
+  *zs = r * sn;
+}
+template <> void bm_normal2<double>(const W4& w, double* zc, double* zs) {
+  double u1 = unif_f64(w.w[0], w.w[1]);
+  double u2 = unif_f64_32(w.w[2]);
+  double L = det_log(u1);
+  double m2 = L * -2.0;
+  double r = std::sqrt(m2);
+  double sn, cs;
+  det_sincos2pi(u2, &sn, &cs);
+  *zc = r * cs;
+  *zs = r * sn;
+}
 template <> float extra_uniform<float>(const W4& w) { return unif_f32(w.w[2]); }
 template <> double extra_uniform<double>(const W4& w) { return unif_f64_32(w.w[3]); }
 
@@ -270,12 +310,15 @@ void mt_constants(double a, double* d, double* c) {
   *c = 1.0 / s;
 }
 
-template <class R> R gamma_mt(R d, R c, uint64_t seed, uint32_t filter, uint32_t t,
-                              uint32_t j, uint32_t purpose, int* fail) {
+template <class R> R gamma_mt_from(R d, R c, R Z0, R U0, uint64_t seed, uint32_t filter,
+                                   uint32_t t, uint32_t j, uint32_t purpose, int* fail) {
   for (uint32_t attempt = 0; attempt < 16; ++attempt) {
-    W4 w = draw(seed, filter, t, j, purpose, attempt);
-    R Z = bm_normal<R>(w);
-    R U = extra_uniform<R>(w);
+    R Z = Z0, U = U0;
+    if (attempt > 0) {
+      W4 w = draw(seed, filter, t, j, purpose, attempt);
+      Z = bm_normal<R>(w);
+      U = extra_uniform<R>(w);
+    }
     R cz = c * Z;
     R v = (R)1 + cz;
     if (!(v > (R)0)) continue;
@@ -299,6 +342,23 @@ template <class R> R gamma_mt(R d, R c, uint64_t seed, uint32_t filter, uint32_t
   return d;
 }
 
+template <class R> R gamma_mt(R d, R c, uint64_t seed, uint32_t filter, uint32_t t,
+                              uint32_t j, uint32_t purpose, int* fail) {
+  W4 w = draw(seed, filter, t, j, purpose, 0);
+  return gamma_mt_from<R>(d, c, bm_normal<R>(w), extra_uniform<R>(w), seed, filter, t, j,
+                          purpose, fail);
+}
+
+template <class R> void theta_draws(uint64_t seed, uint32_t filter, uint32_t t, uint32_t j,
+                                    R* Zx, R* Zs, R* Us, R* Zt, R* Ut) {
+  W4 A = draw(seed, filter, t, j, P_STATE, 0);
+  W4 B = draw(seed, filter, t, j, P_STATE, 1);
+  bm_normal2<R>(A, Zx, Zs);
+  *Us = extra_uniform<R>(A);
+  *Zt = bm_normal<R>(B);
+  *Ut = extra_uniform<R>(B);
+}
+
 template float det_log<float>(float);
 template double det_log<double>(double);
 template float det_exp_core<float>(float);
@@ -309,5 +369,15 @@ template uint64_t quant_exp<float>(float, int, float*);
 template uint64_t quant_exp<double>(double, int, double*);
 template float gamma_mt<float>(float, float, uint64_t, uint32_t, uint32_t, uint32_t, uint32_t, int*);
 template double gamma_mt<double>(double, double, uint64_t, uint32_t, uint32_t, uint32_t, uint32_t, int*);
+template float gamma_mt_from<float>(float, float, float, float, uint64_t, uint32_t, uint32_t,
+                                    uint32_t, uint32_t, int*);
+template double gamma_mt_from<double>(double, double, double, double, uint64_t, uint32_t,
+                                      uint32_t, uint32_t, uint32_t, int*);
+template void det_sincos2pi<float>(float, float*, float*);
+template void det_sincos2pi<double>(double, double*, double*);
+template void theta_draws<float>(uint64_t, uint32_t, uint32_t, uint32_t, float*, float*, float*,
+                                 float*, float*);
+template void theta_draws<double>(uint64_t, uint32_t, uint32_t, uint32_t, double*, double*,
+                                  double*, double*, double*);
 
 }  // namespace oracle

@@ -65,6 +65,7 @@ struct pf_filter {
   uint32_t ntiles = 0;
   bool fp64 = false, learn = true;
   int scheme = 0;
+  unsigned prop_grid = 0;  // persistent propagate grid
   std::vector<void*> allocs;
   void* x[2] = {}; void* s2[2] = {}; void* t2[2] = {}; void* bs[2] = {}; void* bt[2] = {};
   void* ell = nullptr;
@@ -72,6 +73,7 @@ struct pf_filter {
   uint64_t* S = nullptr;
   uint32_t* anc = nullptr;
   uint32_t* I = nullptr;
+  uint64_t* splits = nullptr;  // merge-path partition
   uint64_t* stat_w[2] = {};
   uint64_t* stat_e[2] = {};
   void* part = nullptr;
@@ -174,13 +176,25 @@ bool is_cutpoint(int scheme) { return scheme == PF_MULTINOMIAL_CUTPOINT || schem
 
 // Resampling kernels shared by the filter cycle and pf_resample: from a
 // finished CDF Q (and spacing prefix S) to ancestors.
+inline uint32_t merge_chunks(uint64_t n) { return (uint32_t)cdiv(2 * n, MERGE_D); }
+inline uint32_t sys_chunks(uint64_t n) { return (uint32_t)cdiv(2 * n, SYS_D); }
+
 pf_status launch_resample(int scheme, const PosArgs& pa, uint64_t n, uint32_t* I,
-                          cudaStream_t s, KTimer* tm = nullptr) {
+                          uint64_t* splits, cudaStream_t s, KTimer* tm = nullptr) {
   const bool multi = is_multinomial(scheme);
-  if (!is_cutpoint(scheme)) {
-    const unsigned grid = (unsigned)cdiv(2 * n, MERGE_D);
-    if (multi) k_merge<POS_MULTINOMIAL><<<grid, BLOCK, 0, s>>>(pa);
-    else k_merge<POS_SYSTEMATIC><<<grid, BLOCK, 0, s>>>(pa);
+  if (!is_cutpoint(scheme) && multi) {
+    const uint32_t chunks = merge_chunks(n);
+    const unsigned pgrid = (unsigned)cdiv((uint64_t)(chunks + 1) * 32, BLOCK);
+    k_partition<POS_MULTINOMIAL><<<pgrid, BLOCK, 0, s>>>(pa, splits, chunks + 1, MERGE_D);
+    mark(tm, "partition", s);
+    k_merge<POS_MULTINOMIAL><<<chunks, BLOCK, 0, s>>>(pa, splits);
+    mark(tm, "merge", s);
+  } else if (!is_cutpoint(scheme)) {
+    const uint32_t chunks = sys_chunks(n);
+    const unsigned pgrid = (unsigned)cdiv((uint64_t)(chunks + 1) * 32, BLOCK);
+    k_partition<POS_SYSTEMATIC><<<pgrid, BLOCK, 0, s>>>(pa, splits, chunks + 1, SYS_D);
+    mark(tm, "partition", s);
+    k_merge_sys<<<chunks, SYS_THREADS, 0, s>>>(pa, splits);
     mark(tm, "merge", s);
   } else {
     const unsigned grid = (unsigned)cdiv(n, BLOCK);
@@ -242,10 +256,10 @@ pf_status enqueue_cycle(pf_filter* f, KTimer* tm = nullptr) {
   pa.n = n;
   pa.seed = f->cfg.seed;
   pa.filter = f->cfg.filter_id;
-  pf_status st = launch_resample(f->scheme, pa, n, f->I, s, tm);
+  pf_status st = launch_resample(f->scheme, pa, n, f->I, f->splits, s, tm);
   if (st != PF_OK) return st;
-  if (f->learn) k_propagate<R, true><<<(unsigned)cdiv(n, BLOCK), BLOCK, 0, s>>>(a);
-  else k_propagate<R, false><<<(unsigned)cdiv(n, BLOCK), BLOCK, 0, s>>>(a);
+  if (f->learn) k_propagate<R, true><<<f->prop_grid, BLOCK, 0, s>>>(a);
+  else k_propagate<R, false><<<f->prop_grid, BLOCK, 0, s>>>(a);
   mark(tm, "propagate", s);
   CK(cudaGetLastError());
   return PF_OK;
@@ -371,6 +385,7 @@ pf_status pf_create(const pf_config* cfg, pf_filter** out) {
   if (is_multinomial(f->scheme) && (st = dev_alloc(f, (n + 1) * 8, (void**)&f->S)) != PF_OK) return bail(st);
   if ((st = dev_alloc(f, n * 4, (void**)&f->anc)) != PF_OK) return bail(st);
   if (is_cutpoint(f->scheme) && (st = dev_alloc(f, n * 4, (void**)&f->I)) != PF_OK) return bail(st);
+  if ((st = dev_alloc(f, ((size_t)merge_chunks(n) + 1) * 8, (void**)&f->splits)) != PF_OK) return bail(st);
   if ((st = dev_alloc(f, (size_t)f->ntiles * 16, &f->part)) != PF_OK) return bail(st);
   const uint64_t est_blocks = cdiv(n, (uint64_t)BLOCK * EST_PER_THREAD);
   if ((st = dev_alloc(f, est_blocks * 6 * 8, (void**)&f->part_est)) != PF_OK) return bail(st);
@@ -420,6 +435,23 @@ pf_status pf_create(const pf_config* cfg, pf_filter** out) {
     else k_init<float, false><<<grid, BLOCK, 0, f->stream>>>(a);
   }
   if (cudaGetLastError() != cudaSuccess) return bail(set_err(PF_ERR_CUDA, "init kernel launch failed"));
+  {
+    // persistent propagate grid: resident blocks per SM x SMs, at most one
+    // block per BLOCK slots
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t e;
+    if (f->fp64)
+      e = f->learn ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_propagate<double, true>, BLOCK, 0)
+                   : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_propagate<double, false>, BLOCK, 0);
+    else
+      e = f->learn ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_propagate<float, true>, BLOCK, 0)
+                   : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_propagate<float, false>, BLOCK, 0);
+    if (e != cudaSuccess || per_sm < 1 || sms < 1) return bail(set_err(PF_ERR_CUDA, "occupancy query failed"));
+    const uint64_t want = cdiv(n, BLOCK), cap = (uint64_t)per_sm * (uint64_t)sms;
+    f->prop_grid = (unsigned)(want < cap ? want : cap);
+  }
   if ((st = build_graph(f)) != PF_OK) return bail(st);
   *out = f;
   return PF_OK;
@@ -566,6 +598,7 @@ struct Scratch {
   uint64_t* Q;
   uint64_t* S;
   uint32_t* I;
+  uint64_t* splits;
   uint64_t* stat[2];
   uint64_t* stat_e[2];
   Ctl* ctl;
@@ -592,6 +625,7 @@ size_t scratch_layout(uint64_t n, bool need_Q, bool multi, bool cut, char* base,
   s->Q = need_Q ? (uint64_t*)take(n * 8) : nullptr;
   s->S = multi ? (uint64_t*)take((n + 1) * 8) : nullptr;
   s->I = cut ? (uint32_t*)take(n * 4) : nullptr;
+  s->splits = (uint64_t*)take(((size_t)merge_chunks(n) + 1) * 8);
   s->base = base;
   (void)zero_bytes;
   return off;
@@ -649,7 +683,7 @@ pf_status run_resample(const float* w, uint64_t n, uint64_t seed, uint32_t filte
   pa.n = n;
   pa.seed = seed;
   pa.filter = filter;
-  return launch_resample(scheme, pa, n, sc.I, s);
+  return launch_resample(scheme, pa, n, sc.I, sc.splits, s);
 }
 
 pf_status finish_and_check(const Scratch& sc, cudaStream_t s) {

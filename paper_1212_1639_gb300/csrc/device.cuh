@@ -57,9 +57,12 @@ __device__ __forceinline__ U4 draw(uint64_t seed, uint32_t filter, uint32_t t, u
   return philox(j, t, filter, purpose | (attempt << 8), (uint32_t)seed, (uint32_t)(seed >> 32));
 }
 
-// Uniforms on (0,1) whose conversion is exact.
+// Uniforms on (0,1) whose conversion is exact: (2 (w >> 9) + 1) 2^-24.
+// m = w >> 9 < 2^23 is converted exactly by the 2^23 bias trick.
 __device__ __forceinline__ float unif_f32(uint32_t w) {
-  return __uint2float_rn(2u * (w >> 9) + 1u) * 0x1p-24f;
+  const float fm = __uint_as_float(0x4B000000u | (w >> 9)) - 8388608.0f;  // = m exactly
+  const float a = fm * 0x1p-23f;
+  return a + 0x1p-24f;  // exact: 24 significant bits
 }
 __device__ __forceinline__ double unif_f64(uint32_t lo, uint32_t hi) {
   const uint64_t R = ((uint64_t)hi << 32) | lo;
@@ -100,10 +103,22 @@ template <> struct Cst<double> {
   static constexpr double SQUEEZE = 0x1.0f27bb2fec56dp-5;
 };
 
+// Exact small-integer to binary32 conversion (|e| < 2^22) by the 1.5 * 2^23 bias.
+__device__ __forceinline__ float small_int_to_f32(int e) {
+  return __int_as_float(0x4B400000 + e) - 12582912.0f;
+}
+
 // log of a positive normal number.
 __device__ __forceinline__ float det_log(float x) {
   int e;
-  float f = frexpf(x, &e);
+  float f;
+  const uint32_t b = __float_as_uint(x);
+  if ((b & 0x7f800000u) != 0) {  // normal: frexp by bit manipulation
+    e = (int)(b >> 23) - 126;
+    f = __uint_as_float((b & 0x807fffffu) | 0x3f000000u);
+  } else {
+    f = frexpf(x, &e);
+  }
   if (f < Cst<float>::SQRT_HALF) {
     f = f * 2.0f;
     e = e - 1;
@@ -112,14 +127,14 @@ __device__ __forceinline__ float det_log(float x) {
   const float den = f + 1.0f;
   const float z = num / den;
   const float z2 = z * z;
-  float p = 0x1.c71c72p-4f;   // 1/9
-  p = p * z2; p = p + 0x1.24924ap-3f;  // 1/7
-  p = p * z2; p = p + 0x1.99999ap-3f;  // 1/5
-  p = p * z2; p = p + 0x1.555556p-2f;  // 1/3
-  p = p * z2; p = p + 1.0f;
+  float p = 0x1.c71c72p-4f;              // 1/9
+  p = __fmaf_rn(p, z2, 0x1.24924ap-3f);  // 1/7
+  p = __fmaf_rn(p, z2, 0x1.99999ap-3f);  // 1/5
+  p = __fmaf_rn(p, z2, 0x1.555556p-2f);  // 1/3
+  p = __fmaf_rn(p, z2, 1.0f);
   const float two_z = z * 2.0f;
   const float lf = two_z * p;
-  const float el = __int2float_rn(e) * Cst<float>::LN2;
+  const float el = small_int_to_f32(e) * Cst<float>::LN2;
   return el + lf;
 }
 __device__ __forceinline__ double det_log(double x) {
@@ -140,10 +155,7 @@ __device__ __forceinline__ double det_log(double x) {
                         0x1.5555555555555p-2, 0x1p+0};
   double p = c[0];
 #pragma unroll
-  for (int m = 1; m < 11; ++m) {
-    p = p * z2;
-    p = p + c[m];
-  }
+  for (int m = 1; m < 11; ++m) p = __fma_rn(p, z2, c[m]);
   const double two_z = z * 2.0;
   const double lf = two_z * p;
   const double el = (double)e * Cst<double>::LN2;
@@ -156,10 +168,7 @@ __device__ __forceinline__ float det_exp_core(float r) {
                       0x1.555556p-3f, 0x1p-1f, 0x1p+0f, 0x1p+0f};  // 1/7! .. 1/0!
   float p = c[0];
 #pragma unroll
-  for (int k = 1; k < 8; ++k) {
-    p = p * r;
-    p = p + c[k];
-  }
+  for (int k = 1; k < 8; ++k) p = __fmaf_rn(p, r, c[k]);
   return p;
 }
 __device__ __forceinline__ double det_exp_core(double r) {
@@ -170,10 +179,7 @@ __device__ __forceinline__ double det_exp_core(double r) {
                         0x1p+0,                0x1p+0};  // 1/13! .. 1/0!
   double p = c[0];
 #pragma unroll
-  for (int k = 1; k < 14; ++k) {
-    p = p * r;
-    p = p + c[k];
-  }
+  for (int k = 1; k < 14; ++k) p = __fma_rn(p, r, c[k]);
   return p;
 }
 
@@ -184,10 +190,7 @@ __device__ __forceinline__ float cos_poly(float x) {
                       -0x1p-1f, 0x1p+0f};
   float p = c[0];
 #pragma unroll
-  for (int m = 1; m < 6; ++m) {
-    p = p * x2;
-    p = p + c[m];
-  }
+  for (int m = 1; m < 6; ++m) p = __fmaf_rn(p, x2, c[m]);
   return p;
 }
 __device__ __forceinline__ float sin_poly(float x) {
@@ -197,10 +200,7 @@ __device__ __forceinline__ float sin_poly(float x) {
                       0x1p+0f};
   float p = c[0];
 #pragma unroll
-  for (int m = 1; m < 5; ++m) {
-    p = p * x2;
-    p = p + c[m];
-  }
+  for (int m = 1; m < 5; ++m) p = __fmaf_rn(p, x2, c[m]);
   return x * p;
 }
 __device__ __forceinline__ double cos_poly(double x) {
@@ -211,10 +211,7 @@ __device__ __forceinline__ double cos_poly(double x) {
                        0x1.5555555555555p-5, -0x1p-1, 0x1p+0};
   double p = c[0];
 #pragma unroll
-  for (int m = 1; m < 9; ++m) {
-    p = p * x2;
-    p = p + c[m];
-  }
+  for (int m = 1; m < 9; ++m) p = __fma_rn(p, x2, c[m]);
   return p;
 }
 __device__ __forceinline__ double sin_poly(double x) {
@@ -225,29 +222,35 @@ __device__ __forceinline__ double sin_poly(double x) {
                        0x1.1111111111111p-7, -0x1.5555555555555p-3, 0x1p+0};
   double p = c[0];
 #pragma unroll
-  for (int m = 1; m < 9; ++m) {
-    p = p * x2;
-    p = p + c[m];
-  }
+  for (int m = 1; m < 9; ++m) p = __fma_rn(p, x2, c[m]);
   return x * p;
 }
 
+// sin and cos of 2 pi u for u in [0, 1]: v = u - rint(u), w = |v|; the
+// octant of w selects the reduced argument a (w, 1/4 - w or 1/2 - w, all
+// exact) and which polynomial gives each value; sin takes the sign of v.
+// Both polynomials are always evaluated, so the selection is branch-free.
+template <class R>
+__device__ __forceinline__ void det_sincos2pi(R u, R* s_out, R* c_out) {
+  const R ru = u > (R)0.5 ? (R)1 : (R)0;  // rint(u) for u in [0, 1] (0.5 rounds to even 0)
+  const R v = u - ru;
+  const R w = fabs(v);
+  const bool o1 = w <= (R)0.125;
+  const bool o3 = w > (R)0.375;
+  const R a = o1 ? w : (o3 ? (R)0.5 - w : (R)0.25 - w);
+  const R x = Cst<R>::TWO_PI * a;
+  const R S = sin_poly(x);
+  const R C = cos_poly(x);
+  const R sv = (o1 || o3) ? S : C;
+  const R cv = o1 ? C : (o3 ? -C : S);
+  *s_out = v < (R)0 ? -sv : sv;
+  *c_out = cv;
+}
 template <class R>
 __device__ __forceinline__ R det_cos2pi(R u) {
-  const R v = u - rint(u);
-  const R w = fabs(v);
-  if (w <= (R)0.125) {
-    const R x = Cst<R>::TWO_PI * w;
-    return cos_poly(x);
-  } else if (w <= (R)0.375) {
-    const R a = (R)0.25 - w;
-    const R x = Cst<R>::TWO_PI * a;
-    return sin_poly(x);
-  } else {
-    const R a = (R)0.5 - w;
-    const R x = Cst<R>::TWO_PI * a;
-    return -cos_poly(x);
-  }
+  R s, c;
+  det_sincos2pi(u, &s, &c);
+  return c;
 }
 
 __device__ __forceinline__ float pow2f(int n) {  // n in [-126, 127]
@@ -259,6 +262,9 @@ __device__ __forceinline__ double pow2d(int n) {  // n in [-1022, 1023]
 __device__ __forceinline__ float pow2(int n, float) { return pow2f(n); }
 __device__ __forceinline__ double pow2(int n, double) { return pow2d(n); }
 
+__device__ __forceinline__ uint64_t f2u64_rz(float v);
+__device__ __forceinline__ uint64_t f2u64_rz(double v);
+
 // Quantised CDF weight: e = exp(dl) (0 below dl = -50) and
 // W = min(floor(e * 2^k), 2^k) for dl <= 0.
 template <class R>
@@ -268,8 +274,17 @@ __device__ __forceinline__ uint64_t quant_exp(R dl, int k, R* e_out) {
     return 0;
   }
   const R t = dl * Cst<R>::INV_LN2;
-  const R nr = rint(t);
-  const int n = (int)nr;
+  R nr;
+  int n;
+  if constexpr (sizeof(R) == 4) {
+    // round to nearest even by the 1.5 * 2^23 bias (|t| < 2^22)
+    const float biased = t + 12582912.0f;
+    nr = biased - 12582912.0f;
+    n = __float_as_int(biased) - 0x4B400000;
+  } else {
+    nr = rint(t);
+    n = (int)nr;
+  }
   const R a = nr * Cst<R>::LN2_HI;
   const R b = dl - a;
   const R c = nr * Cst<R>::LN2_LO;
@@ -280,7 +295,7 @@ __device__ __forceinline__ uint64_t quant_exp(R dl, int k, R* e_out) {
   uint64_t W = 0;
   if (sc >= 0) {
     const R v = p * pow2(sc, (R)0);
-    W = (uint64_t)v;
+    W = f2u64_rz(v);
   }
   const uint64_t cap = 1ull << k;
   return W > cap ? cap : W;
@@ -305,6 +320,30 @@ __device__ __forceinline__ double bm_normal_d(const U4& w) {
   const double c = det_cos2pi(u2);
   return r * c;
 }
+__device__ __forceinline__ void bm_normal2_f(const U4& w, float* zc, float* zs) {
+  const float u1 = unif_f32(w.a);
+  const float u2 = unif_f32(w.b);
+  const float L = det_log(u1);
+  const float m2 = L * -2.0f;
+  const float r = sqrtf(m2);
+  float sn, cs;
+  det_sincos2pi(u2, &sn, &cs);
+  *zc = r * cs;
+  *zs = r * sn;
+}
+__device__ __forceinline__ void bm_normal2_d(const U4& w, double* zc, double* zs) {
+  const double u1 = unif_f64(w.a, w.b);
+  const double u2 = unif_f64_32(w.c);
+  const double L = det_log(u1);
+  const double m2 = L * -2.0;
+  const double r = sqrt(m2);
+  double sn, cs;
+  det_sincos2pi(u2, &sn, &cs);
+  *zc = r * cs;
+  *zs = r * sn;
+}
+__device__ __forceinline__ void bm_normal2(const U4& w, float* zc, float* zs) { bm_normal2_f(w, zc, zs); }
+__device__ __forceinline__ void bm_normal2(const U4& w, double* zc, double* zs) { bm_normal2_d(w, zc, zs); }
 __device__ __forceinline__ float bm_normal(const U4& w, float) { return bm_normal_f(w); }
 __device__ __forceinline__ double bm_normal(const U4& w, double) { return bm_normal_d(w); }
 __device__ __forceinline__ float extra_uniform(const U4& w, float) { return unif_f32(w.c); }
@@ -314,12 +353,15 @@ __device__ __forceinline__ double extra_uniform(const U4& w, double) { return un
 // c = 1/sqrt(9d).  Attempt k uses draw (purpose, k); after 16 rejections
 // *fail is set and d is returned.
 template <class R>
-__device__ __forceinline__ R gamma_mt(R d, R c, uint64_t seed, uint32_t filter, uint32_t t,
-                                      uint32_t j, uint32_t purpose, bool* fail) {
+__device__ __forceinline__ R gamma_mt_from(R d, R c, R Z0, R U0, uint64_t seed, uint32_t filter,
+                                           uint32_t t, uint32_t j, uint32_t purpose, bool* fail) {
   for (uint32_t attempt = 0; attempt < 16; ++attempt) {
-    const U4 w = draw(seed, filter, t, j, purpose, attempt);
-    const R Z = bm_normal(w, (R)0);
-    const R U = extra_uniform(w, (R)0);
+    R Z = Z0, U = U0;
+    if (attempt > 0) {
+      const U4 w = draw(seed, filter, t, j, purpose, attempt);
+      Z = bm_normal(w, (R)0);
+      U = extra_uniform(w, (R)0);
+    }
     const R cz = c * Z;
     const R v = (R)1 + cz;
     if (!(v > (R)0)) continue;
@@ -341,6 +383,48 @@ __device__ __forceinline__ R gamma_mt(R d, R c, uint64_t seed, uint32_t filter, 
   }
   *fail = true;
   return d;
+}
+// Marsaglia-Tsang attempt 0 restricted to the squeeze: returns true and
+// *G = d v^3 when v > 0 and U < 1 - 0.0331 Z^4 (the same test, in the same
+// order, as the first step of gamma_mt_from); otherwise the draw must be
+// finished by gamma_mt_from with the same (Z, U).
+template <class R>
+__device__ __forceinline__ bool gamma_mt_squeeze(R d, R c, R Z, R U, R* G) {
+  const R cz = c * Z;
+  const R v = (R)1 + cz;
+  if (!(v > (R)0)) return false;
+  const R vv = v * v;
+  const R v3 = vv * v;
+  const R Z2 = Z * Z;
+  const R z4 = Z2 * Z2;
+  const R sq = Cst<R>::SQUEEZE * z4;
+  const R thr = (R)1 - sq;
+  if (!(U < thr)) return false;
+  *G = d * v3;
+  return true;
+}
+
+template <class R>
+__device__ __forceinline__ R gamma_mt(R d, R c, uint64_t seed, uint32_t filter, uint32_t t,
+                                      uint32_t j, uint32_t purpose, bool* fail) {
+  const U4 w = draw(seed, filter, t, j, purpose, 0);
+  return gamma_mt_from<R>(d, c, bm_normal(w, (R)0), extra_uniform(w, (R)0), seed, filter, t, j,
+                          purpose, fail);
+}
+
+// The draws of one propagation step for slot j: A = (j, t, STATE, 0) gives
+// the state normal (cos branch) and the sigma^2 gamma draw's first normal
+// (sin branch) and uniform; B = (j, t, STATE, 1) gives the tau^2 gamma
+// draw's first normal and uniform.
+template <class R>
+__device__ __forceinline__ void theta_draws(uint64_t seed, uint32_t filter, uint32_t t,
+                                            uint32_t j, R* Zx, R* Zs, R* Us, R* Zt, R* Ut) {
+  const U4 A = draw(seed, filter, t, j, P_STATE, 0);
+  const U4 B = draw(seed, filter, t, j, P_STATE, 1);
+  bm_normal2(A, Zx, Zs);
+  *Us = extra_uniform(A, (R)0);
+  *Zt = bm_normal(B, (R)0);
+  *Ut = extra_uniform(B, (R)0);
 }
 
 // ---------------------------------------------------------------------------
@@ -393,6 +477,39 @@ __device__ __forceinline__ uint64_t div128_small(U128 X, uint64_t d) {
   }
   return q;
 }
+
+// Conversions between binary32 and uint64 with integer instructions only
+// (the hardware 64-bit conversions issue on the binary64 pipe, which is a
+// small fraction of the binary32 rate on this part).  Results equal the C
+// conversions: truncation toward zero, and round-to-nearest-even.
+__device__ __forceinline__ uint64_t f2u64_rz(float v) {  // v >= 0, finite, < 2^64
+  const uint32_t b = __float_as_uint(v);
+  const int e = (int)(b >> 23) - 127;
+  if (e < 0) return 0;
+  const uint64_t m = (b & 0x7fffffu) | 0x800000u;
+  return e >= 23 ? (m << (e - 23)) : (m >> (23 - e));
+}
+__device__ __forceinline__ float u64_to_f32_rn(uint64_t b) {
+  if (b == 0) return 0.0f;
+  const int p = 63 - __clzll((long long)b);  // leading bit
+  uint64_t m;
+  int e = p;
+  if (p <= 23) {
+    m = b << (23 - p);
+  } else {
+    const int s = p - 23;
+    m = b >> s;
+    const uint64_t rem = b & ((1ull << s) - 1);
+    const uint64_t half = 1ull << (s - 1);
+    if (rem > half || (rem == half && (m & 1))) m += 1;
+    if (m == (1ull << 24)) {
+      m >>= 1;
+      e += 1;
+    }
+  }
+  return __uint_as_float(((uint32_t)(e + 127) << 23) | ((uint32_t)m & 0x7fffffu));
+}
+__device__ __forceinline__ uint64_t f2u64_rz(double v) { return __double2ull_rz(v); }
 
 // Order-preserving encodings for atomicMax on floating point.
 __device__ __forceinline__ uint32_t enc_f(float x) {

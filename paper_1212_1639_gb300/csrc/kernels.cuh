@@ -54,6 +54,14 @@ struct Ctl {
   uint32_t done_est;      // last-block counter of k_estimate
   double logml;           // accumulated log marginal likelihood
   double est[8];          // t, x mean/var, sigma2 mean/var, tau2 mean/var, log_marglik
+  // per-cycle constants written by k_weights (block 0) for k_propagate:
+  double y;               // this cycle's observation y_{t+1}
+  double mtd[4];          // Marsaglia-Tsang (d, c) for sigma^2 and tau^2, binary64
+  float yf;               // y rounded to binary32
+  float mtf[4];           // the same constants rounded to binary32
+  // resampling key constants written by k_partition (block 0) for k_merge:
+  // T = Q_{n-1}, A (n or S_n) and the systematic offset r
+  uint64_t keyT, keyA, keyR;
 };
 
 __device__ __forceinline__ void st_release(uint64_t* p, uint64_t v) {
@@ -136,10 +144,10 @@ template <> struct SuffOps<float> {
       *fail = true;
       return b;
     }
-    return b + __float2ull_rz(v);
+    return b + f2u64_rz(v);
   }
   static __device__ __forceinline__ float ig(uint64_t b, float G) {
-    const float bf = __ull2float_rn(b);
+    const float bf = u64_to_f32_rn(b);
     const float bs = bf * 0x1p-32f;
     return bs / G;
   }
@@ -238,9 +246,27 @@ constexpr int W_PER_THREAD = 4;
 template <class R>
 __global__ void __launch_bounds__(BLOCK) k_weights(FilterArgs<R> a) {
   __shared__ R s_red[WARPS];
+  __shared__ R s_y;
   const uint32_t t = a.ctl->t;
   const StateV<R> st = (t & 1) ? a.st[1] : a.st[0];
-  const R yr = (R)a.y_ring[t % a.cap];
+  if (threadIdx.x == 0) {
+    const double y = a.y_ring[t % a.cap];
+    s_y = (R)y;
+    if (blockIdx.x == 0) {
+      // this cycle's constants for k_propagate: observation and the
+      // Marsaglia-Tsang (d, c) of the shapes a0 + (t+1)/2
+      double ds, cs, dt, ct;
+      mt_constants(a.a_sigma + 0.5 * (double)(t + 1), &ds, &cs);
+      mt_constants(a.a_tau + 0.5 * (double)(t + 1), &dt, &ct);
+      Ctl* c = a.ctl;
+      c->y = y;
+      c->yf = (float)y;
+      c->mtd[0] = ds; c->mtd[1] = cs; c->mtd[2] = dt; c->mtd[3] = ct;
+      c->mtf[0] = (float)ds; c->mtf[1] = (float)cs; c->mtf[2] = (float)dt; c->mtf[3] = (float)ct;
+    }
+  }
+  __syncthreads();
+  const R yr = s_y;
   const uint64_t base = ((uint64_t)blockIdx.x * BLOCK + threadIdx.x) * W_PER_THREAD;
   R mx = (R)-INFINITY;
   bool bad = false;
@@ -299,11 +325,15 @@ struct ESum32 {
   U128 s;
   __device__ __forceinline__ void zero() { s.hi = 0; s.lo = 0; }
   __device__ __forceinline__ void add(float e) {
-    if (e == 0.0f) return;
+    // e = 0 or e >= 2^-73: e * 2^96 = mant * 2^(exponent bits - 54), an
+    // integer below 2^97; added without branches
     const uint32_t b = __float_as_uint(e);
-    const uint64_t mant = (b & 0x7fffffu) | 0x800000u;
-    const int sh = (int)(b >> 23) - 54;  // e * 2^96 = mant * 2^(exponent bits - 54)
-    s = add128(s, shl128(mant, sh));
+    const uint32_t E = b >> 23;
+    const uint64_t mant = E ? (uint64_t)((b & 0x7fffffu) | 0x800000u) : 0ull;
+    const int sh = E > 54u ? (int)E - 54 : 0;
+    const uint64_t lo = sh < 64 ? mant << sh : 0ull;
+    const uint64_t hi = sh == 0 ? 0ull : (sh < 64 ? mant >> (64 - sh) : mant << (sh - 64));
+    s = add128(s, U128{hi, lo});
   }
   __device__ __forceinline__ void add(const ESum32& o) { s = add128(s, o.s); }
   __device__ __forceinline__ ESum32 shfl_xor(int m) const {
@@ -395,7 +425,7 @@ struct ScanArgs {
 };
 
 template <int MODE, class R>
-__global__ void __launch_bounds__(BLOCK) k_scan(ScanArgs a) {
+__global__ void __launch_bounds__(BLOCK, 4) k_scan(ScanArgs a) {
   typedef typename ESumT<R>::T ES;
   __shared__ uint32_t s_tile;
   __shared__ uint64_t s_warp_tot[WARPS];
@@ -454,7 +484,7 @@ __global__ void __launch_bounds__(BLOCK) k_scan(ScanArgs a) {
         } else {
           const float wf = (float)v[e];
           if (!(wf >= 0.0f) || !(wf < INFINITY)) atomicOr(&a.ctl->err, ERR_WEIGHTS);
-          else w = __float2ull_rz(ldexpf(wf, escale));
+          else w = f2u64_rz(ldexpf(wf, escale));
         }
       }
       W[c][e] = w;
@@ -501,28 +531,18 @@ __global__ void __launch_bounds__(BLOCK) k_scan(ScanArgs a) {
   __syncthreads();
   const uint64_t off = s_excl + s_warp_tot[warp];
 
-  // store: two instructions per chunk, each covering 64 contiguous elements
+  // store: each lane writes its four consecutive values as two 16-byte stores
 #pragma unroll
   for (int c = 0; c < CHUNKS; ++c) {
-    const uint64_t cbase = wbase + (uint64_t)c * CHUNK;
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      // lane l writes elements 64h + 2l and 64h + 2l + 1, which lane 16h + l/2
-      // holds at positions 2(l & 1) and 2(l & 1) + 1
-      const int src = 16 * h + (lane >> 1);
-      const bool upper = (lane & 1) != 0;
-      const uint64_t a0 = __shfl_sync(0xffffffffu, W[c][0], src);
-      const uint64_t a1 = __shfl_sync(0xffffffffu, W[c][1], src);
-      const uint64_t a2 = __shfl_sync(0xffffffffu, W[c][2], src);
-      const uint64_t a3 = __shfl_sync(0xffffffffu, W[c][3], src);
-      const uint64_t v0 = (upper ? a2 : a0) + off;
-      const uint64_t v1 = (upper ? a3 : a1) + off;
-      const uint64_t i = cbase + 64 * h + 2 * lane;
-      if (i + 2 <= a.n) {
-        *reinterpret_cast<ulonglong2*>(a.Q + i) = make_ulonglong2(v0, v1);
-      } else if (i < a.n) {
-        a.Q[i] = v0;
-      }
+    const uint64_t i0 = wbase + (uint64_t)c * CHUNK + 4 * lane;
+    const uint64_t q0 = W[c][0] + off, q1 = W[c][1] + off, q2 = W[c][2] + off, q3 = W[c][3] + off;
+    if (i0 + 4 <= a.n) {
+      *reinterpret_cast<ulonglong2*>(a.Q + i0) = make_ulonglong2(q0, q1);
+      *reinterpret_cast<ulonglong2*>(a.Q + i0 + 2) = make_ulonglong2(q2, q3);
+    } else {
+      if (i0 < a.n) a.Q[i0] = q0;
+      if (i0 + 1 < a.n) a.Q[i0 + 1] = q1;
+      if (i0 + 2 < a.n) a.Q[i0 + 2] = q2;
     }
   }
 }
@@ -539,7 +559,7 @@ __device__ __forceinline__ uint64_t spacing_E(uint64_t seed, uint32_t filter, ui
   const float u = unif_f32(word);
   const float L = det_log(u);
   const float x = -L * 0x1p31f;
-  return __float2ull_rz(x);
+  return f2u64_rz(x);
 }
 
 struct SpacingArgs {
@@ -553,7 +573,7 @@ struct SpacingArgs {
   uint32_t filter;
 };
 
-__global__ void __launch_bounds__(BLOCK) k_spacing_scan(SpacingArgs a) {
+__global__ void __launch_bounds__(BLOCK, 4) k_spacing_scan(SpacingArgs a) {
   __shared__ uint32_t s_tile;
   __shared__ uint64_t s_warp_tot[WARPS];
   __shared__ uint64_t s_excl;
@@ -576,7 +596,7 @@ __global__ void __launch_bounds__(BLOCK) k_spacing_scan(SpacingArgs a) {
         const float u = unif_f32(word);
         const float L = det_log(u);
         const float x = -L * 0x1p31f;
-        v = __float2ull_rz(x);
+        v = f2u64_rz(x);
       }
       W[c][e] = v;
     }
@@ -613,17 +633,30 @@ __global__ void __launch_bounds__(BLOCK) k_spacing_scan(SpacingArgs a) {
 #pragma unroll
   for (int c = 0; c < CHUNKS; ++c) {
     const uint64_t i0 = wbase + (uint64_t)c * CHUNK + 4 * lane;
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const uint64_t i = i0 + e;
-      if (i < a.n) a.S[i] = W[c][e] + off;
-      if (i == a.n - 1) {
-        // S[n] = S[n-1] + E_n
-        const uint64_t ln = a.n;
-        const U4 w = draw(a.seed, a.filter, t, (uint32_t)(ln >> 2), P_SPACING, 0);
-        a.S[ln] = W[c][e] + off + spacing_E(a.seed, a.filter, t, ln, w);
-      }
+    if (i0 + 4 <= a.n) {
+      *reinterpret_cast<ulonglong2*>(a.S + i0) = make_ulonglong2(W[c][0] + off, W[c][1] + off);
+      *reinterpret_cast<ulonglong2*>(a.S + i0 + 2) = make_ulonglong2(W[c][2] + off, W[c][3] + off);
     }
+    if (i0 + 4 > a.n) {
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+        if (i0 + e < a.n) a.S[i0 + e] = W[c][e] + off;
+    }
+  }
+  // S[n] = S[n-1] + E_n, by the thread holding element n-1
+  const uint64_t last = a.n - 1;
+  const uint64_t lb = last - wbase;  // position of n-1 in this warp's 512 elements
+  if (last >= wbase && lb < CHUNKS * CHUNK && ((lb % CHUNK) >> 2) == (uint64_t)lane) {
+    const int c = (int)(lb / CHUNK), e = (int)(lb & 3);
+    uint64_t v = 0;
+#pragma unroll
+    for (int cc = 0; cc < CHUNKS; ++cc)
+#pragma unroll
+      for (int ee = 0; ee < 4; ++ee)
+        if (cc == c && ee == e) v = W[cc][ee];
+    const uint64_t ln = a.n;
+    const U4 w = draw(a.seed, a.filter, t, (uint32_t)(ln >> 2), P_SPACING, 0);
+    a.S[ln] = v + off + spacing_E(a.seed, a.filter, t, ln, w);
   }
 }
 
@@ -707,11 +740,42 @@ __device__ __forceinline__ uint64_t warp_split(const PosKeys<POS>& K, uint64_t d
   return lo;
 }
 
+// Merge-path partition: the split of diagonal d = c * MERGE_D, one warp per
+// split, all splits searched concurrently.  Block 0 also publishes the key
+// constants (T, A, r) for k_merge.
 template <int POS>
-__global__ void __launch_bounds__(BLOCK) k_merge(PosArgs a) {
-  __shared__ U128 s_key[MERGE_D];
-  __shared__ uint64_t s_split[2];
+__global__ void __launch_bounds__(BLOCK) k_partition(PosArgs a, uint64_t* splits,
+                                                     uint32_t nsplits, uint32_t tile) {
   const PosKeys<POS> K = make_keys<POS>(a);
+  const int lane = threadIdx.x & 31;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    a.ctl->keyT = K.T;
+    a.ctl->keyA = K.A;
+    a.ctl->keyR = K.r;
+  }
+  const uint32_t wid = (uint32_t)(((uint64_t)blockIdx.x * BLOCK + threadIdx.x) >> 5);
+  if (wid >= nsplits) return;  // uniform per warp
+  const uint64_t total = 2 * a.n;
+  const uint64_t d = (uint64_t)wid * tile < total ? (uint64_t)wid * tile : total;
+  uint64_t sp;
+  if (K.T == 0 || K.A == 0) {
+    sp = d < a.n ? d : a.n;  // empty CDF: any monotone split; k_merge flags it
+  } else {
+    sp = warp_split<POS>(K, d);
+  }
+  if (lane == 0) splits[wid] = sp;
+}
+
+template <int POS>
+__global__ void __launch_bounds__(BLOCK) k_merge(PosArgs a, const uint64_t* splits) {
+  __shared__ U128 s_key[MERGE_D];
+  PosKeys<POS> K;
+  K.Q = a.Q;
+  K.S = a.S;
+  K.n = a.n;
+  K.T = a.ctl->keyT;
+  K.A = a.ctl->keyA;
+  K.r = a.ctl->keyR;
   if (K.T == 0 || K.A == 0) {  // empty CDF: flag, keep every index in range
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&a.ctl->err, ERR_NUMERIC);
     for (uint64_t j = (uint64_t)blockIdx.x * BLOCK + threadIdx.x; j < a.n;
@@ -719,16 +783,10 @@ __global__ void __launch_bounds__(BLOCK) k_merge(PosArgs a) {
       a.anc[j] = (uint32_t)j;
     return;
   }
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint64_t total = 2 * a.n;
   const uint64_t d0 = (uint64_t)blockIdx.x * MERGE_D;
   const uint64_t d1 = d0 + MERGE_D < total ? d0 + MERGE_D : total;
-  if (warp < 2) {
-    const uint64_t s = warp_split<POS>(K, warp == 0 ? d0 : d1);
-    if (lane == 0) s_split[warp] = s;
-  }
-  __syncthreads();
-  const uint64_t i0 = s_split[0], i1 = s_split[1];
+  const uint64_t i0 = splits[blockIdx.x], i1 = splits[blockIdx.x + 1];
   const uint64_t j0 = d0 - i0, j1 = d1 - i1;
   const int nA = (int)(i1 - i0), nB = (int)(j1 - j0);
   for (int e = threadIdx.x; e < nA; e += BLOCK) s_key[e] = K.kq(i0 + e);
@@ -757,6 +815,142 @@ __global__ void __launch_bounds__(BLOCK) k_merge(PosArgs a) {
       a.anc[j0 + jb] = (uint32_t)(an < a.n ? an : a.n - 1);
       ++jb;
     }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Systematic resampling by a per-thread walk.  Slot j's key is j T + r
+// (A = n), so slots are equally spaced and particle i owns the slots
+// [R_{i-1}, R_i) with R_i = #{j : j T + r < n Q_i}.  Each CTA takes one
+// merge-path tile (particles [i0, i1), slots [j0, j1), j0 <= R_i <= j1 for
+// its particles).  Thread t walks 16 consecutive particles: it finds its
+// first slot once (a division by T through a 64-bit reciprocal), then emits
+// a_j = i while j T + r < n Q_i, stepping the key by T.  A particle owning
+// more than SYS_CAP slots records a run that the whole CTA fills.  The
+// ancestors are staged in shared memory and written out coalesced.
+// ---------------------------------------------------------------------------
+constexpr int SYS_D = 8192;
+constexpr int SYS_THREADS = 512;
+constexpr int SYS_PER = 16;      // particles per thread (SYS_D / SYS_THREADS)
+constexpr int SYS_CAP = 32;      // slots emitted one by one per particle
+constexpr int SYS_MAX_RUNS = SYS_D / SYS_CAP + 2;
+
+__device__ __forceinline__ U128 sub128(U128 x, uint64_t y) {
+  return U128{x.hi - (x.lo < y ? 1ull : 0ull), x.lo - y};
+}
+__device__ __forceinline__ U128 sub128(U128 x, U128 y) {
+  return U128{x.hi - y.hi - (x.lo < y.lo ? 1ull : 0ull), x.lo - y.lo};
+}
+
+struct SysDiv {      // reciprocal of T for quotients below 2^32
+  uint64_t T, m;     // m = floor((2^64 - 1) / (T >> s))
+  int s;             // T >> s lies in [2^31, 2^32) (s = 0 if T < 2^32)
+};
+__device__ __forceinline__ SysDiv make_sysdiv(uint64_t T) {
+  SysDiv d;
+  d.T = T;
+  const int bits = 64 - __clzll((long long)T);
+  d.s = bits > 32 ? bits - 32 : 0;
+  d.m = 0xffffffffffffffffull / (T >> d.s);
+  return d;
+}
+// floor(Z / T) for Z < T * 2^32: reciprocal estimate, exact correction.
+__device__ __forceinline__ uint64_t sys_floor_div(U128 Z, const SysDiv& d) {
+  const uint64_t zs = d.s ? ((Z.lo >> d.s) | (Z.hi << (64 - d.s))) : Z.lo;
+  uint64_t q = __umul64hi(zs, d.m);
+  U128 P = mul64(q, d.T);
+  for (int it = 0; it < 8 && lt128(Z, P); ++it) {
+    --q;
+    P = sub128(P, d.T);
+  }
+  for (int it = 0; it < 8; ++it) {
+    const U128 P1 = add128(P, d.T);
+    if (lt128(Z, P1)) break;
+    ++q;
+    P = P1;
+  }
+  return q;
+}
+// R(Q) = #{j in [0, n) : j T + r < n Q} = clamp(ceil((n Q - r) / T), 0, n).
+__device__ __forceinline__ uint64_t sys_first_slot(uint64_t Qi, uint64_t n, uint64_t r,
+                                                   const SysDiv& d) {
+  const U128 X = mul64(Qi, n);
+  if (le128(X, U128{0, r})) return 0;
+  const U128 Z = sub128(sub128(X, r), 1ull);  // ceil(Y/T) = floor((Y-1)/T) + 1
+  const uint64_t q = sys_floor_div(Z, d) + 1;
+  return q < n ? q : n;
+}
+
+__global__ void __launch_bounds__(SYS_THREADS) k_merge_sys(PosArgs a, const uint64_t* splits) {
+  __shared__ uint32_t s_anc[SYS_D];
+  __shared__ uint32_t s_run[SYS_MAX_RUNS][3];
+  __shared__ uint32_t s_nruns;
+  const uint64_t T = a.ctl->keyT, r = a.ctl->keyR, n = a.n;
+  if (T == 0) {  // empty CDF: flag, keep every index in range
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&a.ctl->err, ERR_NUMERIC);
+    for (uint64_t j = (uint64_t)blockIdx.x * SYS_THREADS + threadIdx.x; j < n;
+         j += (uint64_t)gridDim.x * SYS_THREADS)
+      a.anc[j] = (uint32_t)j;
+    return;
+  }
+  const uint64_t total = 2 * n;
+  const uint64_t d0 = (uint64_t)blockIdx.x * SYS_D;
+  const uint64_t d1 = d0 + SYS_D < total ? d0 + SYS_D : total;
+  const uint64_t i0 = splits[blockIdx.x], i1 = splits[blockIdx.x + 1];
+  const uint64_t j0 = d0 - i0, j1 = d1 - i1;
+  const uint32_t nB = (uint32_t)(j1 - j0);
+  if (threadIdx.x == 0) s_nruns = 0;
+  __syncthreads();
+  const SysDiv dv = make_sysdiv(T);
+  auto add_run = [&](uint64_t st, uint64_t en, uint64_t val) {
+    const uint32_t k = atomicAdd(&s_nruns, 1u);
+    if (k < SYS_MAX_RUNS) {
+      s_run[k][0] = (uint32_t)(st - j0);
+      s_run[k][1] = (uint32_t)(en - j0);
+      s_run[k][2] = (uint32_t)val;
+    }
+  };
+  if (i0 == i1) {
+    if (threadIdx.x == 0 && nB) add_run(j0, j1, i0);  // every slot belongs to particle i0
+  } else {
+    const uint64_t ib = i0 + (uint64_t)threadIdx.x * SYS_PER;
+    if (ib < i1) {
+      const uint64_t ie = ib + SYS_PER < i1 ? ib + SYS_PER : i1;
+      uint64_t j = threadIdx.x == 0 ? j0 : sys_first_slot(a.Q[ib - 1], n, r, dv);
+      j = j < j0 ? j0 : (j > j1 ? j1 : j);
+      U128 KB = add128(mul64(j, T), r);
+      for (uint64_t i = ib; i < ie; ++i) {
+        const U128 KQ = mul64(a.Q[i], n);
+        int emitted = 0;
+        while (j < j1 && lt128(KB, KQ)) {
+          if (emitted == SYS_CAP) {  // a heavy particle: jump to its last slot
+            uint64_t R = sys_first_slot(a.Q[i], n, r, dv);
+            R = R < j ? j : (R > j1 ? j1 : R);
+            add_run(j, R, i);
+            j = R;
+            KB = add128(mul64(j, T), r);
+            break;
+          }
+          s_anc[j - j0] = (uint32_t)i;
+          ++j;
+          KB = add128(KB, T);
+          ++emitted;
+        }
+      }
+      if (ie == i1 && j < j1) add_run(j, j1, i1);  // remaining slots belong to particle i1
+    }
+  }
+  __syncthreads();
+  const uint32_t nr = s_nruns < SYS_MAX_RUNS ? s_nruns : SYS_MAX_RUNS;
+  if (s_nruns > SYS_MAX_RUNS && threadIdx.x == 0) atomicOr(&a.ctl->err, ERR_NUMERIC);
+  for (uint32_t k = 0; k < nr; ++k) {
+    const uint32_t st = s_run[k][0], en = s_run[k][1], v = s_run[k][2];
+    for (uint32_t q = st + threadIdx.x; q < en; q += SYS_THREADS) s_anc[q] = v;
+  }
+  __syncthreads();
+  for (uint32_t q = threadIdx.x; q < nB; q += SYS_THREADS) {
+    const uint32_t v = s_anc[q];
+    a.anc[j0 + q] = v < n ? v : (uint32_t)(n - 1);
   }
 }
 
@@ -841,97 +1035,180 @@ __device__ __forceinline__ double esum_value(const ESum32& e) {
 }
 __device__ __forceinline__ double esum_value(const ESum64& e) { return e.s; }
 
+// Run by the last warp of k_propagate: fold the per-tile log-ML partials
+// (lane-strided, then butterfly: a fixed order), accumulate the increment
+// m + log(sum_i e_i) - log n - log(2 pi)/2, reset the per-cycle counters and
+// advance t.
 template <class R>
-__device__ void fold_cycle(FilterArgs<R>& a, uint32_t t) {
+__device__ void fold_cycle_warp(const FilterArgs<R>& a, uint32_t t) {
   typedef typename ESumT<R>::T ES;
-  __shared__ ES s_part[BLOCK];
+  const int lane = threadIdx.x & 31;
   ES acc;
   acc.zero();
-  for (uint32_t b = threadIdx.x; b < a.ntiles; b += BLOCK)
-    acc.add(reinterpret_cast<const ES*>(a.part)[b]);
-  s_part[threadIdx.x] = acc;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    ES tot = s_part[0];
-    for (int i = 1; i < BLOCK; ++i) tot.add(s_part[i]);
-    const double m = sizeof(R) == 4 ? (double)dec_f((uint32_t)a.ctl->maxenc)
-                                    : dec_d(a.ctl->maxenc);
+  for (uint32_t b = lane; b < a.ntiles; b += 32) acc.add(reinterpret_cast<const ES*>(a.part)[b]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc.add(acc.shfl_xor(o));
+  if (lane == 0) {
+    Ctl* c = a.ctl;
+    const double m = sizeof(R) == 4 ? (double)dec_f((uint32_t)c->maxenc) : dec_d(c->maxenc);
     const double LOG_2PI = 0x1.d67f1c864beb5p+0;
-    const double inc = m + log(esum_value(tot)) - log((double)a.n) - 0.5 * LOG_2PI;
-    a.ctl->logml = a.ctl->logml + inc;
-    a.ctl->maxenc = sizeof(R) == 4 ? (unsigned long long)enc_f(-INFINITY) : enc_d(-INFINITY);
-    a.ctl->ticket_w = 0;
-    a.ctl->ticket_e = 0;
-    a.ctl->done_prop = 0;
+    const double inc = m + log(esum_value(acc)) - log((double)a.n) - 0.5 * LOG_2PI;
+    c->logml = c->logml + inc;
+    c->maxenc = sizeof(R) == 4 ? (unsigned long long)enc_f(-INFINITY) : enc_d(-INFINITY);
+    c->ticket_w = 0;
+    c->ticket_e = 0;
+    c->done_prop = 0;
     __threadfence();
-    a.ctl->t = t + 1;
+    c->t = t + 1;
   }
 }
 
+// A gamma draw that missed the Marsaglia-Tsang squeeze on its first attempt,
+// finished after the block's fast path (same arithmetic, later in time).
+template <class R>
+struct GammaItem {
+  typename SuffT<R>::B b;  // updated sufficient statistic (the IG scale)
+  R Z, U;                  // attempt-0 normal and uniform
+  uint32_t j;              // slot
+  uint32_t which;          // 0: sigma^2, 1: tau^2
+};
+
+// One ancestor's record, gathered ahead of its use.
+template <class R>
+struct Gathered {
+  R x, s2, t2;
+  typename SuffT<R>::B bs, bt;
+};
+template <class R>
+__device__ __forceinline__ Gathered<R> gather_rec(const StateV<R>& src, uint32_t an) {
+  Gathered<R> g;
+  g.x = src.x[an];
+  g.s2 = src.s2[an];
+  g.t2 = src.t2[an];
+  g.bs = src.bs[an];
+  g.bt = src.bt[an];
+  return g;
+}
+
+// Persistent grid: thread (block b, lane t) handles slots j = b*BLOCK + t +
+// k * stride.  The ancestor index is loaded two slots ahead and the ancestor's
+// record one slot ahead, so the dependent index -> gather latency overlaps the
+// arithmetic of the current slot.
 template <class R, bool LEARN>
 __global__ void __launch_bounds__(BLOCK) k_propagate(FilterArgs<R> a) {
-  __shared__ double s_c[4];
-  __shared__ bool s_last;
-  const uint32_t t = a.ctl->t;
-  if (LEARN && threadIdx.x == 0) {
-    double ds, cs, dt, ct;
-    mt_constants(a.a_sigma + 0.5 * (double)(t + 1), &ds, &cs);
-    mt_constants(a.a_tau + 0.5 * (double)(t + 1), &dt, &ct);
-    s_c[0] = ds; s_c[1] = cs; s_c[2] = dt; s_c[3] = ct;
-  }
-  __syncthreads();
+  __shared__ GammaItem<R> s_q[2 * BLOCK];
+  __shared__ uint32_t s_qn;
+  const Ctl* c = a.ctl;
+  const uint32_t t = c->t;
   const StateV<R> src = (t & 1) ? a.st[1] : a.st[0];
   const StateV<R> dst = (t & 1) ? a.st[0] : a.st[1];
-  const double y = a.y_ring[t % a.cap];
-  const R yr = (R)y;
-  const uint64_t j = (uint64_t)blockIdx.x * BLOCK + threadIdx.x;
+  const double y = c->y;
+  R yr, ds, cs, dt, ct;
+  if constexpr (sizeof(R) == 4) {
+    yr = c->yf; ds = c->mtf[0]; cs = c->mtf[1]; dt = c->mtf[2]; ct = c->mtf[3];
+  } else {
+    yr = y; ds = c->mtd[0]; cs = c->mtd[1]; dt = c->mtd[2]; ct = c->mtd[3];
+  }
+  const int lane = threadIdx.x & 31;
+  const uint64_t n = a.n;
+  const uint64_t stride = (uint64_t)gridDim.x * BLOCK;
+  const uint64_t iters = (n + stride - 1) / stride;
+  auto clampi = [&](uint32_t v) { return v < n ? v : (uint32_t)(n - 1); };
+  uint64_t j = (uint64_t)blockIdx.x * BLOCK + threadIdx.x;
+  uint32_t an = j < n ? clampi(a.anc[j]) : 0;
+  uint32_t an_next = j + stride < n ? clampi(a.anc[j + stride]) : 0;
+  Gathered<R> cur = gather_rec<R>(src, an);
   bool fail = false;
-  if (j < a.n) {
-    const uint32_t an0 = a.anc[j];
-    const uint32_t an = an0 < a.n ? an0 : (uint32_t)(a.n - 1);
-    const R xa = src.x[an], sa = src.s2[an], ta = src.t2[an];
-    const R s = sa + ta;
-    const R p = sa * ta;
-    const R V = p / s;
-    const R n1 = xa * sa;
-    const R n2 = yr * ta;
-    const R nn = n1 + n2;
-    const R mu = nn / s;
-    const R sv = sqrt(V);
-    const R Z = bm_normal(draw(a.seed, a.filter, t, (uint32_t)j, P_STATE, 0), (R)0);
-    const R xz = sv * Z;
-    const R xj = mu + xz;
-    dst.x[j] = xj;
-    if (LEARN) {
-      const R rs = ResidObs<R>::f(y, yr, xj);
-      const R rt = xj - xa;
-      const auto bsn = SuffOps<R>::add_half_square(src.bs[an], rs, &fail);
-      const auto btn = SuffOps<R>::add_half_square(src.bt[an], rt, &fail);
-      const R Gs = gamma_mt<R>((R)s_c[0], (R)s_c[1], a.seed, a.filter, t, (uint32_t)j,
-                               P_GAMMA_SIGMA, &fail);
-      const R Gt = gamma_mt<R>((R)s_c[2], (R)s_c[3], a.seed, a.filter, t, (uint32_t)j,
-                               P_GAMMA_TAU, &fail);
-      dst.bs[j] = bsn;
-      dst.bt[j] = btn;
-      dst.s2[j] = SuffOps<R>::ig(bsn, Gs);
-      dst.t2[j] = SuffOps<R>::ig(btn, Gt);
-    } else {
-      dst.s2[j] = sa;
-      dst.t2[j] = ta;
-      dst.bs[j] = src.bs[an];
-      dst.bt[j] = src.bt[an];
+  for (uint64_t it = 0; it < iters; ++it, j += stride) {
+    // prefetch: the index two slots ahead, the record one slot ahead
+    const uint32_t an_next2 = j + 2 * stride < n ? clampi(a.anc[j + 2 * stride]) : 0;
+    const Gathered<R> nxt = gather_rec<R>(src, an_next);
+    if (LEARN && threadIdx.x == 0) s_qn = 0;
+    if (LEARN) __syncthreads();
+    bool defer_s = false, defer_t = false;
+    typename SuffT<R>::B bsn = 0, btn = 0;
+    R Zs = 0, Us = 0, Zt = 0, Ut = 0;
+    if (j < n) {
+      const R xa = cur.x, sa = cur.s2, ta = cur.t2;
+      const R s = sa + ta;
+      const R p = sa * ta;
+      const R V = p / s;
+      const R n1 = xa * sa;
+      const R n2 = yr * ta;
+      const R nn = n1 + n2;
+      const R mu = nn / s;
+      const R sv = sqrt(V);
+      R Z;
+      theta_draws<R>(a.seed, a.filter, t, (uint32_t)j, &Z, &Zs, &Us, &Zt, &Ut);
+      const R xz = sv * Z;
+      const R xj = mu + xz;
+      dst.x[j] = xj;
+      if (LEARN) {
+        const R rs = ResidObs<R>::f(y, yr, xj);
+        const R rt = xj - xa;
+        bsn = SuffOps<R>::add_half_square(cur.bs, rs, &fail);
+        btn = SuffOps<R>::add_half_square(cur.bt, rt, &fail);
+        dst.bs[j] = bsn;
+        dst.bt[j] = btn;
+        R Gs, Gt;
+        if (gamma_mt_squeeze<R>(ds, cs, Zs, Us, &Gs)) dst.s2[j] = SuffOps<R>::ig(bsn, Gs);
+        else defer_s = true;
+        if (gamma_mt_squeeze<R>(dt, ct, Zt, Ut, &Gt)) dst.t2[j] = SuffOps<R>::ig(btn, Gt);
+        else defer_t = true;
+      } else {
+        dst.s2[j] = sa;
+        dst.t2[j] = ta;
+        dst.bs[j] = cur.bs;
+        dst.bt[j] = cur.bt;
+      }
     }
+    if (LEARN) {
+      // queue the draws that missed the squeeze (one shared atomic per warp
+      // and gamma), then finish them with the whole block
+#pragma unroll
+      for (int g = 0; g < 2; ++g) {
+        const bool d = g == 0 ? defer_s : defer_t;
+        const uint32_t m = __ballot_sync(0xffffffffu, d);
+        if (m) {
+          uint32_t base = 0;
+          if (lane == 0) base = atomicAdd(&s_qn, (uint32_t)__popc(m));
+          base = __shfl_sync(0xffffffffu, base, 0);
+          if (d) {
+            GammaItem<R> itm;
+            itm.b = g == 0 ? bsn : btn;
+            itm.Z = g == 0 ? Zs : Zt;
+            itm.U = g == 0 ? Us : Ut;
+            itm.j = (uint32_t)j;
+            itm.which = (uint32_t)g;
+            s_q[base + __popc(m & ((1u << lane) - 1u))] = itm;
+          }
+        }
+      }
+      __syncthreads();
+      const uint32_t qn = s_qn;
+      for (uint32_t k = threadIdx.x; k < qn; k += BLOCK) {
+        const GammaItem<R> itm = s_q[k];
+        const bool sig = itm.which == 0;
+        const R G = gamma_mt_from<R>(sig ? ds : dt, sig ? cs : ct, itm.Z, itm.U, a.seed, a.filter,
+                                     t, itm.j, sig ? P_GAMMA_SIGMA : P_GAMMA_TAU, &fail);
+        const R v = SuffOps<R>::ig(itm.b, G);
+        if (sig) dst.s2[itm.j] = v;
+        else dst.t2[itm.j] = v;
+      }
+      __syncthreads();
+    }
+    cur = nxt;
+    an_next = an_next2;
   }
-  if (__syncthreads_or(fail) && threadIdx.x == 0) atomicOr(&a.ctl->err, ERR_NUMERIC);
-  if (threadIdx.x == 0) {
-    __threadfence();
-    s_last = atomicAdd(&a.ctl->done_prop, 1u) == gridDim.x - 1;
-  }
-  __syncthreads();
-  if (s_last) {
-    __threadfence();
-    fold_cycle<R>(a, t);
-  }
+  (void)an;
+  if (__any_sync(0xffffffffu, fail) && lane == 0) atomicOr(&a.ctl->err, ERR_NUMERIC);
+  // The fold reads only what earlier kernels wrote (tile partials, the
+  // control block), so the completion count needs no fence; every warp has
+  // read t before its increment.
+  bool last = false;
+  if (lane == 0) last = atomicAdd(&a.ctl->done_prop, 1u) == gridDim.x * WARPS - 1;
+  last = __shfl_sync(0xffffffffu, last, 0);
+  if (last) fold_cycle_warp<R>(a, t);
 }
 
 // ---------------------------------------------------------------------------

@@ -86,3 +86,16 @@ def test_det_cos2pi_accuracy(orc, dtype):
     # absolute error in units of eps (cos has zeros, where relative error is meaningless)
     assert np.max(np.abs(got - ref)) <= 2 * np.finfo(dtype).eps
     assert got[0] == 1 and got[-1] == -1
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_det_sincos2pi_accuracy_and_consistency(orc, dtype):
+    if dtype == np.float64 and not HAVE_EXT:
+        pytest.skip("no extended precision reference on this platform")
+    u = np.concatenate([np.linspace(0, 1, 400_001), [0.125, 0.375, 0.625, 0.875]]).astype(dtype)
+    s, c = orc.det_sincos2pi(u, dtype)
+    ang = LD(2) * np.pi * u.astype(LD)
+    assert np.max(np.abs(s.astype(LD) - np.sin(ang))) <= 2 * np.finfo(dtype).eps
+    assert np.max(np.abs(c.astype(LD) - np.cos(ang))) <= 2 * np.finfo(dtype).eps
+    # the cos output is the same function as det_cos2pi
+    assert np.array_equal(c, orc.det_cos2pi(u, dtype))
