@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdarg>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -313,7 +314,9 @@ pf_status check_handle(pf_filter* f) {
 }
 
 pf_status sync_and_check(pf_filter* f) {
-  cudaError_t e = cudaMemcpyAsync(f->ctl_host, f->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, f->stream);
+  // t, the error word, counters and the summaries: the fields before the
+  // per-cycle constants (104 bytes)
+  cudaError_t e = cudaMemcpyAsync(f->ctl_host, f->ctl, offsetof(Ctl, y), cudaMemcpyDeviceToHost, f->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(f->stream);
   if (e != cudaSuccess) {
     f->sticky = PF_ERR_CUDA;
@@ -605,7 +608,7 @@ struct Scratch {
   void* base;
 };
 
-size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+constexpr size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
 // Lay out the scratch of pf_resample / pf_cdf inside one allocation.
 size_t scratch_layout(uint64_t n, bool need_Q, bool multi, bool cut, char* base, Scratch* s) {
