@@ -196,6 +196,27 @@ pf_status pf_cutpoint_method(const uint64_t* Q_dev, uint64_t n, const uint32_t* 
                              const uint64_t* U_dev, uint64_t m, uint32_t* anc_dev,
                              void* stream);
 
+/* Resampling without allocating: the same computation and result as
+ * pf_resample, for callers that cannot allocate device memory at the point
+ * where they resample (for example host functions enqueued on a stream, which
+ * may not call CUDA API functions, latency-critical loops that must not risk an
+ * allocation's synchronisation, or processes whose device memory is reserved
+ * up front).  The paper has no counterpart; this is a deployment variant.
+ *
+ * Scratch lives in one fixed-size device array inside libpf.so, present on
+ * every device that loads the library until the process exits (about 20 MiB),
+ * and sized for n <= PF_NOALLOC_MAX_PARTICLES; larger n returns
+ * PF_ERR_INVALID.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress), so make that first call before any stream
+ * capture.  Every call on a device shares the one array, so calls whose GPU
+ * work overlaps (other streams, other host threads) race and corrupt each
+ * other: serialise them.  The call clears the parts of the scratch that must
+ * start at zero, then synchronises `stream` to report device-side errors as
+ * pf_resample does.  Arguments and errors as pf_resample. */
+#define PF_NOALLOC_MAX_PARTICLES (1ull << 20)
+pf_status pf_resample_noalloc(const float* w_dev, uint64_t n, uint64_t seed, uint32_t filter_id,
+                              uint32_t t, int32_t scheme, uint32_t* anc_dev, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

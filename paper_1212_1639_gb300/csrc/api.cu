@@ -9,6 +9,7 @@
 #include <cstddef>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -775,4 +776,76 @@ pf_status pf_cutpoint_method(const uint64_t* Q_dev, uint64_t n, const uint32_t* 
   return PF_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Resampling without any allocation.
+//
+// For callers that cannot allocate device memory when they resample: code
+// running where CUDA API calls that allocate are not allowed or not wanted,
+// such as host functions enqueued on a stream (which may not call CUDA API
+// functions at all), latency-critical loops that must not risk an
+// allocation's device synchronisation or unbounded time, and processes whose
+// device memory is fully reserved up front.  The scratch of this entry point
+// lives in one file-scope device array of fixed size, present on every device
+// that loads the library for the life of the process.
+// ---------------------------------------------------------------------------
 }  // extern "C"
+
+namespace {
+
+constexpr uint64_t NOALLOC_N = PF_NOALLOC_MAX_PARTICLES;
+constexpr uint64_t NOALLOC_TILES = (NOALLOC_N + TILE - 1) / TILE;
+constexpr size_t NOALLOC_BYTES =
+    align256(sizeof(Ctl)) + 4 * align256(NOALLOC_TILES * 8) + align256(NOALLOC_N * 8) +
+    align256((NOALLOC_N + 1) * 8) + align256(NOALLOC_N * 4) +
+    align256(((2 * NOALLOC_N + MERGE_D - 1) / MERGE_D + 1) * 8);
+
+// The scratch itself: one copy per device, shared by every call on it.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mu;
+char* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
+
+// Device address of the scratch on the current device, looked up once per
+// device (the host-side symbol is only a stand-in, not a device address).
+pf_status noalloc_scratch(char** out) {
+  int dev = -1;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return set_err(PF_ERR_INVALID, "device ordinal out of range");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+      return set_err(PF_ERR_CUDA, "cudaGetSymbolAddress(scratch): %s", cudaGetErrorString(e));
+    g_noalloc_ptr[dev] = (char*)p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return PF_OK;
+}
+
+}  // namespace
+
+extern "C" pf_status pf_resample_noalloc(const float* w_dev, uint64_t n, uint64_t seed,
+                                         uint32_t filter_id, uint32_t t, int32_t scheme,
+                                         uint32_t* anc_dev, void* stream) {
+  if (!w_dev || !anc_dev) return set_err(PF_ERR_INVALID, "NULL pointer");
+  if (n < 1 || n > PF_NOALLOC_MAX_PARTICLES)
+    return set_err(PF_ERR_INVALID, "pf_resample_noalloc: n must be in [1, %llu]",
+                   (unsigned long long)PF_NOALLOC_MAX_PARTICLES);
+  if (scheme < 0 || scheme > 3) return set_err(PF_ERR_INVALID, "bad scheme");
+  cudaStream_t s = (cudaStream_t)stream;
+  char* base = nullptr;
+  pf_status st = noalloc_scratch(&base);
+  if (st != PF_OK) return st;
+  Scratch sc;
+  const size_t bytes =
+      scratch_layout(n, true, is_multinomial(scheme), is_cutpoint(scheme), nullptr, &sc);
+  if (bytes > NOALLOC_BYTES) return set_err(PF_ERR_INVALID, "scratch layout exceeds the static array");
+  scratch_layout(n, true, is_multinomial(scheme), is_cutpoint(scheme), base, &sc);
+  // the control block and tile status words must start at zero each call
+  CK(cudaMemsetAsync(base, 0, scratch_zero_bytes(n), s));
+  if ((st = run_resample(w_dev, n, seed, filter_id, t, scheme, anc_dev, nullptr, sc, s)) != PF_OK)
+    return st;
+  return finish_and_check(sc, s);
+}

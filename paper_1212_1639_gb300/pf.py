@@ -26,6 +26,7 @@ MULTINOMIAL, SYSTEMATIC, MULTINOMIAL_CUTPOINT, SYSTEMATIC_CUTPOINT = 0, 1, 2, 3
 SCHEMES = {"multinomial": 0, "systematic": 1, "multinomial_cutpoint": 2, "systematic_cutpoint": 3}
 FP32, FP64 = 0, 1
 MAX_PARTICLES = 1 << 26
+NOALLOC_MAX_PARTICLES = 1 << 20
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
@@ -63,6 +64,8 @@ _SIGS = {
     "pf_get_ancestors": [_V, _V, _V],
     "pf_destroy": [_V],
     "pf_resample": [_V, C.c_uint64, C.c_uint64, C.c_uint32, C.c_uint32, C.c_int32, _V, _V],
+    "pf_resample_noalloc": [_V, C.c_uint64, C.c_uint64, C.c_uint32, C.c_uint32, C.c_int32, _V,
+                            _V],
     "pf_cdf": [_V, C.c_uint64, _V, _V],
     "pf_cutpoint_search": [_V, C.c_uint64, _V, _V],
     "pf_cutpoint_method": [_V, C.c_uint64, _V, _V, C.c_uint64, _V, _V],
@@ -228,6 +231,20 @@ def resample(w, seed, filter_id=0, t=0, scheme="systematic", out=None, stream=No
     sch = SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
     _check(_lib.pf_resample(_ptr(w), n, seed, filter_id, t, sch, _ptr(anc), _stream_ptr(stream)),
            "pf_resample")
+    return anc
+
+
+def resample_noalloc(w, seed, filter_id=0, t=0, scheme="systematic", out=None, stream=None):
+    """As resample(), through pf_resample_noalloc: the library allocates nothing
+    (its scratch is a fixed device array, n <= NOALLOC_MAX_PARTICLES); `out`,
+    when given, is the caller's preallocated int32 output."""
+    torch = _torch()
+    assert w.is_cuda and w.dtype == torch.float32 and w.is_contiguous()
+    n = w.numel()
+    anc = out if out is not None else torch.empty(n, dtype=torch.int32, device=w.device)
+    sch = SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
+    _check(_lib.pf_resample_noalloc(_ptr(w), n, seed, filter_id, t, sch, _ptr(anc),
+                                    _stream_ptr(stream)), "pf_resample_noalloc")
     return anc
 
 
