@@ -293,9 +293,17 @@ __device__ __forceinline__ uint64_t quant_exp(R dl, int k, R* e_out) {
   *e_out = p * pow2(n, (R)0);
   const int sc = n + k;
   uint64_t W = 0;
-  if (sc >= 0) {
-    const R v = p * pow2(sc, (R)0);
-    W = f2u64_rz(v);
+  if constexpr (sizeof(R) == 4) {
+    // floor(p * 2^sc) straight from p's bits: p = m24 2^(E - 23)
+    const uint32_t pb = __float_as_uint(p);
+    const int sh = (int)(pb >> 23) - 150 + sc;
+    const uint32_t m24 = (pb & 0x7fffffu) | 0x800000u;
+    if (sc >= 0) W = sh >= 0 ? ((uint64_t)m24 << sh) : (uint64_t)(m24 >> (-sh < 31 ? -sh : 31));
+  } else {
+    if (sc >= 0) {
+      const R v = p * pow2(sc, (R)0);
+      W = f2u64_rz(v);
+    }
   }
   const uint64_t cap = 1ull << k;
   return W > cap ? cap : W;
@@ -435,6 +443,13 @@ struct U128 {
 };
 __device__ __forceinline__ U128 mul64(uint64_t a, uint64_t b) {
   return U128{__umul64hi(a, b), a * b};
+}
+// a * b for b < 2^32: two 32x32 -> 64 products instead of a 64x64 multiply.
+__device__ __forceinline__ U128 mul64x32(uint64_t a, uint32_t b) {
+  const uint64_t p0 = (uint64_t)(uint32_t)a * b;
+  const uint64_t p1 = (a >> 32) * (uint64_t)b;
+  const uint64_t lo = p0 + (p1 << 32);
+  return U128{(p1 >> 32) + (lo < p0 ? 1ull : 0ull), lo};
 }
 __device__ __forceinline__ U128 add128(U128 x, uint64_t y) {
   const uint64_t lo = x.lo + y;

@@ -64,12 +64,15 @@ struct Ctl {
   uint64_t keyT, keyA, keyR;
 };
 
-__device__ __forceinline__ void st_release(uint64_t* p, uint64_t v) {
-  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+// Tile status words carry their value and flag in one aligned 64-bit word and
+// nothing else is read through them, so relaxed (single-copy atomic) accesses
+// suffice; unlike acquire loads, several can be in flight at once.
+__device__ __forceinline__ void st_status(uint64_t* p, uint64_t v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
-__device__ __forceinline__ uint64_t ld_acquire(const uint64_t* p) {
+__device__ __forceinline__ uint64_t ld_status(const uint64_t* p) {
   uint64_t v;
-  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
 }
 __device__ __forceinline__ uint32_t ld_volatile_u32(const uint32_t* p) {
@@ -326,7 +329,7 @@ struct ESum32 {
   __device__ __forceinline__ void zero() { s.hi = 0; s.lo = 0; }
   __device__ __forceinline__ void add(float e) {
     // e = 0 or e >= 2^-73: e * 2^96 = mant * 2^(exponent bits - 54), an
-    // integer below 2^97; added without branches
+    // integer below 2^101 (e < 16 for a thread's partial); added without branches
     const uint32_t b = __float_as_uint(e);
     const uint32_t E = b >> 23;
     const uint64_t mant = E ? (uint64_t)((b & 0x7fffffu) | 0x800000u) : 0ull;
@@ -359,51 +362,69 @@ template <> struct ESumT<float> { typedef ESum32 T; };
 template <> struct ESumT<double> { typedef ESum64 T; };
 
 // Tile look-back by warp 0.  Returns the exclusive prefix of the tile (in
-// lane 0).  `total` is the tile aggregate.
+// lane 0).  `total` is the tile aggregate.  Each round reads a window of 128
+// predecessors (four status words per lane, loads issued together), so a
+// tile far from the last published prefix needs few round trips.
+constexpr int LB_PER_LANE = 4;
+
+__device__ __forceinline__ uint64_t spin_status(const uint64_t* p, bool* timed_out) {
+  uint64_t v = ld_status(p);
+  uint32_t spins = 0;
+  while ((v >> 62) == 0) {
+    if (++spins > SPIN_LIMIT) {
+      *timed_out = true;
+      return FLAG_P;
+    }
+    __nanosleep(32);
+    v = ld_status(p);
+  }
+  return v;
+}
+
 __device__ __forceinline__ uint64_t lookback(uint64_t* stat, uint32_t tile, uint64_t total,
                                              uint32_t* err) {
   const int lane = threadIdx.x & 31;
   if (tile == 0) {
-    if (lane == 0) st_release(&stat[0], FLAG_P | total);
+    if (lane == 0) st_status(&stat[0], FLAG_P | total);
     return 0;
   }
-  if (lane == 0) st_release(&stat[tile], FLAG_A | total);
+  if (lane == 0) st_status(&stat[tile], FLAG_A | total);
   uint64_t excl = 0;
   int64_t look = (int64_t)tile - 1;
   bool timed_out = false;
   while (true) {
-    const int64_t idx = look - lane;
-    uint64_t v = FLAG_P;  // before tile 0: a zero prefix
-    if (idx >= 0) {
-      uint32_t spins = 0;
-      v = ld_acquire(&stat[idx]);
-      while ((v >> 62) == 0) {
-        if (++spins > SPIN_LIMIT) {
-          timed_out = true;
-          v = FLAG_P;
-          break;
-        }
-        __nanosleep(32);
-        v = ld_acquire(&stat[idx]);
-      }
-    }
-    const uint32_t pmask = __ballot_sync(0xffffffffu, (v >> 62) == 2);
-    uint64_t contrib = v & VAL_MASK;
-    if (pmask) {
-      const int first = __ffs(pmask) - 1;  // nearest predecessor holding a prefix
-      if (lane > first) contrib = 0;
+    // lane l covers distances LB_PER_LANE*l .. LB_PER_LANE*l + 3 below `look`
+    uint64_t v[LB_PER_LANE];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) contrib += __shfl_xor_sync(0xffffffffu, contrib, o);
-      excl += contrib;
-      break;
+    for (int k = 0; k < LB_PER_LANE; ++k) {
+      const int64_t idx = look - (LB_PER_LANE * lane + k);
+      v[k] = idx >= 0 ? ld_status(&stat[idx]) : FLAG_P;  // before tile 0: a zero prefix
+    }
+#pragma unroll
+    for (int k = 0; k < LB_PER_LANE; ++k) {
+      const int64_t idx = look - (LB_PER_LANE * lane + k);
+      if ((v[k] >> 62) == 0) v[k] = spin_status(&stat[idx], &timed_out);
+    }
+    int first_p = LB_PER_LANE;
+#pragma unroll
+    for (int k = LB_PER_LANE - 1; k >= 0; --k)
+      if ((v[k] >> 62) == 2) first_p = k;
+    const uint32_t pmask = __ballot_sync(0xffffffffu, first_p < LB_PER_LANE);
+    const int stop_lane = pmask ? __ffs(pmask) - 1 : 32;
+    uint64_t contrib = 0;
+#pragma unroll
+    for (int k = 0; k < LB_PER_LANE; ++k) {
+      const bool take = lane < stop_lane || (lane == stop_lane && k <= first_p);
+      if (take) contrib += v[k] & VAL_MASK;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) contrib += __shfl_xor_sync(0xffffffffu, contrib, o);
     excl += contrib;
-    look -= 32;
+    if (pmask) break;
+    look -= 32 * LB_PER_LANE;
   }
   if (__any_sync(0xffffffffu, timed_out) && lane == 0) atomicOr(err, ERR_TIMEOUT);
-  if (lane == 0) st_release(&stat[tile], FLAG_P | ((excl + total) & VAL_MASK));
+  if (lane == 0) st_status(&stat[tile], FLAG_P | ((excl + total) & VAL_MASK));
   return excl;
 }
 
@@ -424,9 +445,15 @@ struct ScanArgs {
   int vec_ok;               // src is 16-byte aligned
 };
 
+// Thread-blocked scan: thread t of a tile owns the 16 consecutive elements
+// [16 t, 16 t + 16), so the running sum is two integer adds per element and
+// the warp / block scans run once per 16 elements.
+constexpr int SCAN_PER = TILE / BLOCK;  // 16
+
 template <int MODE, class R>
 __global__ void __launch_bounds__(BLOCK, 4) k_scan(ScanArgs a) {
   typedef typename ESumT<R>::T ES;
+  __shared__ uint64_t s_stage[BLOCK * (SCAN_PER + 1)];
   __shared__ uint32_t s_tile;
   __shared__ uint64_t s_warp_tot[WARPS];
   __shared__ uint64_t s_excl;
@@ -435,7 +462,7 @@ __global__ void __launch_bounds__(BLOCK, 4) k_scan(ScanArgs a) {
   if (threadIdx.x == 0) s_tile = atomicAdd(&a.ctl->ticket_w, 1u);
   __syncthreads();
   const uint32_t tile = s_tile;
-  const uint64_t wbase = (uint64_t)tile * TILE + (uint64_t)warp * (CHUNKS * CHUNK);
+  const uint64_t base = (uint64_t)tile * TILE + (uint64_t)threadIdx.x * SCAN_PER;
   const uint32_t par = (a.t_dev ? *a.t_dev : a.t_arg) & 1u;
   uint64_t* const stat = par ? a.stat[1] : a.stat[0];
   uint64_t* const stat_next = par ? a.stat[0] : a.stat[1];
@@ -452,71 +479,77 @@ __global__ void __launch_bounds__(BLOCK, 4) k_scan(ScanArgs a) {
     escale = a.k - e;
   }
 
-  uint64_t W[CHUNKS][4];
-  ES es;
-  es.zero();
+  const bool full = base + SCAN_PER <= a.n;
+  uint64_t W[SCAN_PER];
+  R epart = (R)0;  // this thread's sum of exp(l - m), fixed order
+  uint64_t run = 0;
 #pragma unroll
-  for (int c = 0; c < CHUNKS; ++c) {
-    const uint64_t i0 = wbase + (uint64_t)c * CHUNK + 4 * lane;
+  for (int q = 0; q < SCAN_PER / 4; ++q) {
+    // four values at a time, consumed as soon as they arrive
     R v[4];
-    if (i0 + 4 <= a.n && a.vec_ok) {
+    if (full && a.vec_ok) {
       if constexpr (sizeof(R) == 4) {
-        const float4 f = *reinterpret_cast<const float4*>((const float*)a.src + i0);
+        const float4 f = *reinterpret_cast<const float4*>((const float*)a.src + base + 4 * q);
         v[0] = f.x; v[1] = f.y; v[2] = f.z; v[3] = f.w;
       } else {
-        const double2 f0 = *reinterpret_cast<const double2*>((const double*)a.src + i0);
-        const double2 f1 = *reinterpret_cast<const double2*>((const double*)a.src + i0 + 2);
+        const double2 f0 = *reinterpret_cast<const double2*>((const double*)a.src + base + 4 * q);
+        const double2 f1 = *reinterpret_cast<const double2*>((const double*)a.src + base + 4 * q + 2);
         v[0] = f0.x; v[1] = f0.y; v[2] = f1.x; v[3] = f1.y;
       }
     } else {
 #pragma unroll
-      for (int e = 0; e < 4; ++e) v[e] = (i0 + e < a.n) ? ((const R*)a.src)[i0 + e] : (R)0;
+      for (int e = 0; e < 4; ++e)
+        v[e] = (base + 4 * q + e < a.n) ? ((const R*)a.src)[base + 4 * q + e] : (R)0;
     }
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       uint64_t w = 0;
-      if (i0 + e < a.n) {
+      if (full || base + 4 * q + e < a.n) {
         if (MODE == FROM_LOGLIK) {
           R ex;
           const R dl = v[e] - m;
           w = quant_exp<R>(dl, a.k, &ex);
-          es.add(ex);
+          epart = epart + ex;
         } else {
           const float wf = (float)v[e];
           if (!(wf >= 0.0f) || !(wf < INFINITY)) atomicOr(&a.ctl->err, ERR_WEIGHTS);
           else w = f2u64_rz(ldexpf(wf, escale));
         }
       }
-      W[c][e] = w;
+      run += w;
+      W[4 * q + e] = run;  // inclusive running sum
     }
   }
-
-  // warp-level inclusive prefix (in element order) of this warp's 512 values
-  uint64_t carry = 0;
-#pragma unroll
-  for (int c = 0; c < CHUNKS; ++c) {
-    W[c][1] += W[c][0];
-    W[c][2] += W[c][1];
-    W[c][3] += W[c][2];
-    const uint64_t incl = warp_incl_scan(W[c][3], lane);
-    const uint64_t excl_l = incl - W[c][3] + carry;
-#pragma unroll
-    for (int e = 0; e < 4; ++e) W[c][e] += excl_l;
-    carry += __shfl_sync(0xffffffffu, incl, 31);
-  }
-  if (lane == 0) s_warp_tot[warp] = carry;
+  // warp exclusive offsets of the thread totals, then the block
+  const uint64_t tt = W[SCAN_PER - 1];
+  const uint64_t tincl = warp_incl_scan(tt, lane);
+  if (lane == 31) s_warp_tot[warp] = tincl;
   if (MODE == FROM_LOGLIK) {
+    ES es;
+    es.zero();
+    es.add(epart);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) es.add(es.shfl_xor(o));
     if (lane == 0) s_es[warp] = es;
   }
   __syncthreads();
-
   if (warp == 0) {
     uint64_t wt = lane < WARPS ? s_warp_tot[lane] : 0;
     const uint64_t wincl = warp_incl_scan(wt, lane);
     if (lane < WARPS) s_warp_tot[lane] = wincl - wt;  // exclusive warp offsets
-    const uint64_t total = __shfl_sync(0xffffffffu, wincl, 31);
+  }
+  __syncthreads();
+  // stage the tile-local inclusive prefix (padded rows of 17 words), so that
+  // no per-element state is live across the look-back
+  {
+    const uint64_t toff = s_warp_tot[warp] + (tincl - tt);
+#pragma unroll
+    for (int e = 0; e < SCAN_PER; ++e) s_stage[threadIdx.x * (SCAN_PER + 1) + e] = W[e] + toff;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    // tile total = last thread's staged inclusive value
+    const uint64_t total = s_stage[(BLOCK - 1) * (SCAN_PER + 1) + SCAN_PER - 1];
     const uint64_t excl = lookback(stat, tile, total, &a.ctl->err);
     if (lane == 0) {
       s_excl = excl;
@@ -529,21 +562,19 @@ __global__ void __launch_bounds__(BLOCK, 4) k_scan(ScanArgs a) {
     }
   }
   __syncthreads();
-  const uint64_t off = s_excl + s_warp_tot[warp];
-
-  // store: each lane writes its four consecutive values as two 16-byte stores
+  const uint64_t off = s_excl;
+  const uint64_t tbase = (uint64_t)tile * TILE;
+  if (tbase + TILE <= a.n) {
 #pragma unroll
-  for (int c = 0; c < CHUNKS; ++c) {
-    const uint64_t i0 = wbase + (uint64_t)c * CHUNK + 4 * lane;
-    const uint64_t q0 = W[c][0] + off, q1 = W[c][1] + off, q2 = W[c][2] + off, q3 = W[c][3] + off;
-    if (i0 + 4 <= a.n) {
-      *reinterpret_cast<ulonglong2*>(a.Q + i0) = make_ulonglong2(q0, q1);
-      *reinterpret_cast<ulonglong2*>(a.Q + i0 + 2) = make_ulonglong2(q2, q3);
-    } else {
-      if (i0 < a.n) a.Q[i0] = q0;
-      if (i0 + 1 < a.n) a.Q[i0 + 1] = q1;
-      if (i0 + 2 < a.n) a.Q[i0 + 2] = q2;
+    for (int r = 0; r < TILE / (2 * BLOCK); ++r) {
+      const int q = 2 * threadIdx.x + 2 * BLOCK * r;  // even: q and q+1 share a row
+      const int si = (q >> 4) * (SCAN_PER + 1) + (q & 15);
+      *reinterpret_cast<ulonglong2*>(a.Q + tbase + q) =
+          make_ulonglong2(s_stage[si] + off, s_stage[si + 1] + off);
     }
+  } else {
+    for (int q = threadIdx.x; q < TILE; q += BLOCK)
+      if (tbase + q < a.n) a.Q[tbase + q] = s_stage[(q >> 4) * (SCAN_PER + 1) + (q & 15)] + off;
   }
 }
 
@@ -573,7 +604,7 @@ struct SpacingArgs {
   uint32_t filter;
 };
 
-__global__ void __launch_bounds__(BLOCK, 4) k_spacing_scan(SpacingArgs a) {
+__global__ void __launch_bounds__(BLOCK, 3) k_spacing_scan(SpacingArgs a) {
   __shared__ uint32_t s_tile;
   __shared__ uint64_t s_warp_tot[WARPS];
   __shared__ uint64_t s_excl;
@@ -688,9 +719,12 @@ struct PosKeys {
   const uint64_t* Q;
   const uint64_t* S;
   uint64_t n, T, A, r;
-  __device__ __forceinline__ U128 kq(uint64_t i) const { return mul64(Q[i], A); }
+  __device__ __forceinline__ U128 kq(uint64_t i) const {
+    if (POS == POS_SYSTEMATIC) return mul64x32(Q[i], (uint32_t)A);  // A = n < 2^32
+    return mul64(Q[i], A);
+  }
   __device__ __forceinline__ U128 kb(uint64_t j) const {
-    if (POS == POS_SYSTEMATIC) return add128(mul64(j, T), r);
+    if (POS == POS_SYSTEMATIC) return add128(mul64x32(T, (uint32_t)j), r);
     return mul64(S[j], T);
   }
 };
@@ -832,7 +866,7 @@ __global__ void __launch_bounds__(BLOCK) k_merge(PosArgs a, const uint64_t* spli
 constexpr int SYS_D = 8192;
 constexpr int SYS_THREADS = 512;
 constexpr int SYS_PER = 16;      // particles per thread (SYS_D / SYS_THREADS)
-constexpr int SYS_CAP = 32;      // slots emitted one by one per particle
+constexpr int SYS_CAP = 8;       // slots emitted one by one per particle
 constexpr int SYS_MAX_RUNS = SYS_D / SYS_CAP + 2;
 
 __device__ __forceinline__ U128 sub128(U128 x, uint64_t y) {
@@ -874,7 +908,7 @@ __device__ __forceinline__ uint64_t sys_floor_div(U128 Z, const SysDiv& d) {
 // R(Q) = #{j in [0, n) : j T + r < n Q} = clamp(ceil((n Q - r) / T), 0, n).
 __device__ __forceinline__ uint64_t sys_first_slot(uint64_t Qi, uint64_t n, uint64_t r,
                                                    const SysDiv& d) {
-  const U128 X = mul64(Qi, n);
+  const U128 X = mul64x32(Qi, (uint32_t)n);
   if (le128(X, U128{0, r})) return 0;
   const U128 Z = sub128(sub128(X, r), 1ull);  // ceil(Y/T) = floor((Y-1)/T) + 1
   const uint64_t q = sys_floor_div(Z, d) + 1;
@@ -918,17 +952,18 @@ __global__ void __launch_bounds__(SYS_THREADS) k_merge_sys(PosArgs a, const uint
       const uint64_t ie = ib + SYS_PER < i1 ? ib + SYS_PER : i1;
       uint64_t j = threadIdx.x == 0 ? j0 : sys_first_slot(a.Q[ib - 1], n, r, dv);
       j = j < j0 ? j0 : (j > j1 ? j1 : j);
-      U128 KB = add128(mul64(j, T), r);
+      U128 KB = add128(mul64x32(T, (uint32_t)j), r);
       for (uint64_t i = ib; i < ie; ++i) {
-        const U128 KQ = mul64(a.Q[i], n);
+        const uint64_t qi = a.Q[i];
+        const U128 KQ = mul64x32(qi, (uint32_t)n);
         int emitted = 0;
         while (j < j1 && lt128(KB, KQ)) {
           if (emitted == SYS_CAP) {  // a heavy particle: jump to its last slot
-            uint64_t R = sys_first_slot(a.Q[i], n, r, dv);
+            uint64_t R = sys_first_slot(qi, n, r, dv);
             R = R < j ? j : (R > j1 ? j1 : R);
             add_run(j, R, i);
             j = R;
-            KB = add128(mul64(j, T), r);
+            KB = add128(mul64x32(T, (uint32_t)j), r);
             break;
           }
           s_anc[j - j0] = (uint32_t)i;
