@@ -137,9 +137,13 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def pow2_label(n):
+    return "2^%d" % (n.bit_length() - 1) if n & (n - 1) == 0 else str(n)
+
+
 def kernels_hash():
     h = hashlib.sha256()
-    for f in ("kernels.cuh", "device.cuh", "api.cu"):
+    for f in ("kernels.cuh", "device.cuh"):
         h.update(open(os.path.join(ROOT, "paper_1212_1639_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -327,7 +331,8 @@ def bench_ours(args):
         "warmup": W, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "local-level particle learning, one filter per GPU, "
-                               "N=2^20, FP32 state, %s resampling, T=1000 seeded series" % args.scheme,
+                               "N=%s, FP32 state, %s resampling, T=1000 seeded series"
+                               % (pow2_label(args.n), args.scheme),
                    "n_particles": n, "scheme": args.scheme, "precision": "fp32",
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "flushed (256 MB write) before every timed cycle, outside the events"},
@@ -400,8 +405,9 @@ def bench_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": done, "warmup": W, "ms_per_step": dt * 1e3 / done, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "local-level particle learning, one filter, N=2^20, FP32 state, "
-                               "%s resampling, T=1000 seeded series" % args.scheme,
+        "config": {"workload": "local-level particle learning, one filter per GPU, "
+                               "N=%s, FP32 state, %s resampling, T=1000 seeded series"
+                               % (pow2_label(n), args.scheme),
                    "n_particles": n, "scheme": args.scheme, "precision": "fp32"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": "N=%d, %d cycles (of %d requested) on one host core"
