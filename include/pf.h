@@ -217,6 +217,98 @@ pf_status pf_cutpoint_method(const uint64_t* Q_dev, uint64_t n, const uint32_t* 
 pf_status pf_resample_noalloc(const float* w_dev, uint64_t n, uint64_t seed, uint32_t filter_id,
                               uint32_t t, int32_t scheme, uint32_t* anc_dev, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Batched filters: many independent particle-learning filters of uneven size
+ * advanced together, one persistent kernel launch per cycle (replayed from a
+ * CUDA graph).  Each CTA of the launch takes whole filters from a work list
+ * ordered by size, largest first, and runs the full cycle of the paper's
+ * Algorithm "Particle Learning" (Steps 1-4) for each with block barriers
+ * only.  The paper runs one filter at a time; batching is a deployment
+ * variant of the same cycle.
+ *
+ * Every filter of a batch gives bit for bit the results of a standalone
+ * pf_create filter with the same pf_config: the same ancestors, particles,
+ * summaries and log marginal likelihood.
+ *
+ * Particles of all filters live in one device pool sized at creation (the
+ * HBM budget); filters are admitted into slots while the pool and the slots
+ * have room (first fit, 32-particle granules) and leave with
+ * pf_batch_remove.  Scheme and precision are shared by the whole batch.
+ * --------------------------------------------------------------------------- */
+typedef struct pf_batch pf_batch;
+
+typedef struct {
+  uint32_t max_filters;      /* slots; 0 = the number of initial filters */
+  uint64_t hbm_budget_bytes; /* device bytes for the particle pool; 0 = exactly
+                                what the initial filters need */
+  int32_t scheme;            /* pf_scheme of every filter (the cut-point variants
+                                give the same ancestors as their base schemes) */
+  int32_t precision;         /* pf_precision of every filter */
+  void* stream;              /* cudaStream_t; NULL = a stream the batch creates */
+  pf_alloc_fn alloc;         /* NULL: cudaMallocAsync / cudaFreeAsync */
+  pf_free_fn free;
+  void* alloc_ctx;
+} pf_batch_opts;
+
+typedef struct {
+  uint32_t max_filters, resident;       /* slots, slots in use */
+  uint64_t pool_particles;              /* pool capacity */
+  uint64_t used_particles;              /* taken by resident filters (rounded to granules) */
+  uint64_t bytes_per_particle;          /* device bytes per pool particle */
+  uint64_t pool_bytes;
+  uint32_t grid, block;                 /* persistent launch shape of the cycle kernel */
+  uint64_t cycles;                      /* pf_batch_step calls that launched work */
+} pf_batch_info;
+
+/* Create a batch with n initial filters cfgs[0..n) (host array, may be NULL
+ * when n = 0) in slots 0..n-1, and enqueue their initialisation (Step 0).
+ * Per filter, cfgs[i] supplies n_particles, seed, filter_id, the priors and
+ * known-variance settings; its scheme and precision must equal opts'; its
+ * stream and allocator fields are ignored.  Errors: PF_ERR_INVALID,
+ * PF_ERR_OOM, PF_ERR_CUDA, PF_ERR_BUSY (the budget cannot hold the initial
+ * filters).  Synchronises. */
+pf_status pf_batch_create(const pf_config* cfgs, uint32_t n, const pf_batch_opts* opts,
+                          pf_batch** out);
+
+/* Admit one more filter: the lowest free slot goes to *slot and its
+ * initialisation is enqueued.  PF_ERR_BUSY when no slot is free or no free
+ * pool range holds cfg->n_particles (nothing changes then).  Synchronises. */
+pf_status pf_batch_add(pf_batch* b, const pf_config* cfg, uint32_t* slot);
+
+/* Release a slot and its pool range (reused only by work enqueued later on
+ * the batch's stream).  PF_ERR_INVALID for a slot not in use. */
+pf_status pf_batch_remove(pf_batch* b, uint32_t slot);
+
+/* Enqueue one cycle for the resident filters s with mask[s] != 0 (mask NULL:
+ * every resident filter), filter s consuming observation y[s].  y and mask
+ * are host arrays indexed by slot (max_filters entries).  Asynchronous: one
+ * host-to-device copy of the work list (16 bytes per stepped filter) and one
+ * graph launch. */
+pf_status pf_batch_step(pf_batch* b, const double* y, const uint8_t* mask);
+
+/* Posterior summaries of the resident filters selected by mask (NULL: all),
+ * written to out[slot] (host array of max_filters entries; other entries are
+ * left alone).  Synchronises.  Returns the error of the first selected filter
+ * whose device error word is set (PF_ERR_NUMERIC); its summaries are still
+ * written. */
+pf_status pf_batch_estimate(pf_batch* b, const uint8_t* mask, pf_estimates* out);
+
+/* Wait for the batch's enqueued work. */
+pf_status pf_batch_sync(pf_batch* b);
+
+/* Copy one filter's particles (as pf_get_particles) or its last cycle's
+ * ancestors and CDF (as pf_get_ancestors).  Buffers host or device; NULL
+ * skips an array.  Synchronise. */
+pf_status pf_batch_get_particles(pf_batch* b, uint32_t slot, void* x, void* sigma2, void* tau2,
+                                 void* b_sigma, void* b_tau);
+pf_status pf_batch_get_ancestors(pf_batch* b, uint32_t slot, uint32_t* anc, uint64_t* Q);
+
+/* Occupancy of the pool and slots, and the launch shape.  Host only. */
+pf_status pf_batch_get_info(pf_batch* b, pf_batch_info* out);
+
+/* Free the batch after its stream's pending work.  NULL-safe. */
+pf_status pf_batch_destroy(pf_batch* b);
+
 #ifdef __cplusplus
 }
 #endif

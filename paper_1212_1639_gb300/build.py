@@ -14,7 +14,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "libpf.so")
 SOURCES = ["api.cu"]
-DEPS = ["api.cu", "kernels.cuh", "device.cuh"]
+DEPS = ["api.cu", "kernels.cuh", "device.cuh", "batch.cuh", "batch_api.cuh"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 

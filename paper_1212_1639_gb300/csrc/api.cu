@@ -849,3 +849,5 @@ extern "C" pf_status pf_resample_noalloc(const float* w_dev, uint64_t n, uint64_
     return st;
   return finish_and_check(sc, s);
 }
+
+#include "batch_api.cuh"

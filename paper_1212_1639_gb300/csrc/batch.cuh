@@ -1,0 +1,592 @@
+// Batched particle learning: many independent filters of uneven size, one
+// persistent launch per cycle.
+//
+// Each CTA takes whole filters from a work list ordered by size (largest
+// first) and runs the complete cycle of a filter with block barriers only:
+//   1. predictive weights l_i and their maximum (Algorithm "Particle
+//      Learning", Step 1),
+//   2. the exact fixed-point CDF (Section 3) by a chunked block scan with a
+//      carry between chunks,
+//   3. resampling (Section 3.1): systematic by a per-thread walk over equally
+//      spaced slot keys, multinomial by exponential spacings (a second
+//      chunked block scan) and the same walk over the sorted position keys,
+//   4. propagation of x, the sufficient statistics and theta (Steps 2-4),
+//      with the block's queue of gamma draws that missed the squeeze,
+// then folds the filter's log marginal likelihood increment and advances its
+// cycle counter.
+//
+// Every per-particle operation (weights, quantisation, draws keyed by the
+// filter's seed and id, the resampling keys, the propagation arithmetic) is
+// the one of the single-filter kernels, and the per-thread partial sums of the
+// log-ML and of the summaries are taken over the same particle groups and
+// folded in the same order, so a filter in a batch reproduces a standalone
+// filter with the same configuration bit for bit.
+#pragma once
+#include "kernels.cuh"
+
+namespace pfk {
+
+// Per-filter state of a batch, one per slot (device array).
+struct BatchFilter {
+  uint64_t off;        // first particle in the pooled arrays (multiple of 32)
+  uint64_t seed;       // Philox key
+  uint32_t n;          // particles (0: free slot)
+  uint32_t filter_id;  // third Philox counter word
+  uint32_t t;          // cycles completed
+  uint32_t err;        // ErrBits
+  int32_t k;           // CDF shift: W <= 2^k
+  uint32_t learn;      // 0: sigma^2, tau^2 known (held at their given values)
+  double x0_mean, x0_var, a_sigma, b_sigma, a_tau, b_tau, sigma2, tau2;
+  double logml;        // accumulated log marginal likelihood
+};
+
+// One entry of a cycle's work list.
+struct BatchItem {
+  uint32_t slot;
+  uint32_t pad;
+  double y;            // this filter's observation for the cycle
+};
+
+template <class R>
+struct BatchArgs {
+  StateV<R> st[2];          // pooled particles, ping-pong by each filter's parity
+  R* ell;                   // per particle
+  uint64_t* Q;              // per particle
+  uint64_t* S;              // per particle (multinomial spacing prefix S_0..S_{n-1})
+  uint32_t* anc;            // per particle
+  BatchFilter* F;           // per slot
+  const BatchItem* items;   // work list, largest filters first
+  const uint32_t* count;    // number of items (device)
+  uint32_t* ctr;            // [0] next item, [1] finished CTAs; both 0 between launches
+  double* est;              // k_batch_estimate: BATCH_EST_ROW doubles per item, in list order
+  int commit;               // 0: a trial cycle that leaves t, log-ML and err untouched
+};
+
+constexpr int BB = BLOCK;                 // threads per CTA (the scan tile's 256)
+constexpr int BATCH_EST_ROW = 9;          // t, 6 summaries, log-ML, error bits
+constexpr int BB_CAP = 32;                // slots emitted per particle before a run
+constexpr int BB_MAX_RUNS = 1024;         // runs per tile held in shared memory
+
+// Exclusive block prefix of one value per thread, and the block total.
+__device__ __forceinline__ uint64_t block_excl_scan(uint64_t v, uint64_t* s_warp,
+                                                    uint64_t* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint64_t incl = warp_incl_scan(v, lane);
+  if (lane == 31) s_warp[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const uint64_t w = lane < WARPS ? s_warp[lane] : 0;
+    const uint64_t wi = warp_incl_scan(w, lane);
+    if (lane < WARPS) s_warp[lane] = wi - w;
+    if (lane == WARPS - 1) s_warp[WARPS] = wi;
+  }
+  __syncthreads();
+  const uint64_t excl = s_warp[warp] + incl - v;
+  *total = s_warp[WARPS];
+  __syncthreads();  // s_warp is reused by the next call
+  return excl;
+}
+
+// #{j in [lo, n) : S_j T < key} for nondecreasing S, by bisection.
+__device__ __forceinline__ uint64_t multi_first_slot(const uint64_t* S, uint64_t n, uint64_t T,
+                                                     U128 key, uint64_t lo) {
+  uint64_t hi = n;
+  while (lo < hi) {
+    const uint64_t mid = (lo + hi) >> 1;
+    if (lt128(mul64(S[mid], T), key)) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+template <class R, int POS>
+__global__ void __launch_bounds__(BB) k_batch_cycle(BatchArgs<R> a) {
+  typedef typename ESumT<R>::T ES;
+  __shared__ uint64_t s_warp[WARPS + 1];
+  __shared__ R s_red[WARPS];
+  __shared__ ES s_es[WARPS];
+  __shared__ ES s_fold[32];
+  __shared__ uint32_t s_work;
+  __shared__ uint32_t s_run[BB_MAX_RUNS][3];
+  __shared__ uint32_t s_nruns;
+  __shared__ GammaItem<R> s_q[2 * BB];
+  __shared__ uint32_t s_qn;
+  __shared__ double s_c[4];
+  __shared__ uint64_t s_SN;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t count = *a.count;
+
+  while (true) {
+    if (threadIdx.x == 0) s_work = atomicAdd(&a.ctr[0], 1u);
+    __syncthreads();
+    const uint32_t w = s_work;
+    if (w >= count) break;
+    const BatchItem item = a.items[w];
+    BatchFilter* F = &a.F[item.slot];
+    const uint64_t off = F->off, n = F->n, seed = F->seed;
+    const uint32_t fid = F->filter_id, t = F->t;
+    const int k = F->k;
+    const bool learn = F->learn != 0;
+    const StateV<R> src = (t & 1) ? a.st[1] : a.st[0];
+    const StateV<R> dst = (t & 1) ? a.st[0] : a.st[1];
+    const double y = item.y;
+    const R yr = (R)y;
+    if (threadIdx.x == 0) {
+      // Marsaglia-Tsang (d, c) of the shapes a0 + (t+1)/2
+      double ds, cs, dt, ct;
+      mt_constants(F->a_sigma + 0.5 * (double)(t + 1), &ds, &cs);
+      mt_constants(F->a_tau + 0.5 * (double)(t + 1), &dt, &ct);
+      s_c[0] = ds; s_c[1] = cs; s_c[2] = dt; s_c[3] = ct;
+    }
+    if (threadIdx.x < 32) s_fold[threadIdx.x].zero();
+    bool fail = false;
+
+    // 1. weights and their maximum, four particles per thread
+    R mx = (R)-INFINITY;
+    for (uint64_t i = 4 * (uint64_t)threadIdx.x; i < n; i += 4 * BB) {
+      if (i + 4 <= n) {
+        R xv[4], sv[4], tv[4], lv[4];
+        if constexpr (sizeof(R) == 4) {
+          const float4 X = *reinterpret_cast<const float4*>(src.x + off + i);
+          const float4 Sg = *reinterpret_cast<const float4*>(src.s2 + off + i);
+          const float4 Tu = *reinterpret_cast<const float4*>(src.t2 + off + i);
+          xv[0] = X.x; xv[1] = X.y; xv[2] = X.z; xv[3] = X.w;
+          sv[0] = Sg.x; sv[1] = Sg.y; sv[2] = Sg.z; sv[3] = Sg.w;
+          tv[0] = Tu.x; tv[1] = Tu.y; tv[2] = Tu.z; tv[3] = Tu.w;
+        } else {
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            xv[e] = src.x[off + i + e]; sv[e] = src.s2[off + i + e]; tv[e] = src.t2[off + i + e];
+          }
+        }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          lv[e] = log_pred<R>(xv[e], sv[e], tv[e], yr);
+          fail |= !(lv[e] < (R)INFINITY);  // NaN or +inf
+          mx = fmax(mx, lv[e]);
+        }
+        if constexpr (sizeof(R) == 4) {
+          *reinterpret_cast<float4*>(a.ell + off + i) = make_float4(lv[0], lv[1], lv[2], lv[3]);
+        } else {
+#pragma unroll
+          for (int e = 0; e < 4; ++e) a.ell[off + i + e] = lv[e];
+        }
+      } else {
+        for (uint64_t q = i; q < n; ++q) {
+          const R l = log_pred<R>(src.x[off + q], src.s2[off + q], src.t2[off + q], yr);
+          fail |= !(l < (R)INFINITY);
+          mx = fmax(mx, l);
+          a.ell[off + q] = l;
+        }
+      }
+    }
+    const R m0 = block_max<R>(mx, s_red);  // valid in warp 0
+    __syncthreads();
+    if (threadIdx.x == 0) s_red[0] = m0;
+    __syncthreads();
+    const R m = s_red[0];
+    if (!(m > (R)-INFINITY)) fail = true;
+
+    // 2. quantised weights and their inclusive scan, one 4096-particle tile
+    // at a time; thread t owns the tile's particles [16 t, 16 t + 16)
+    uint64_t carry = 0;
+    uint32_t tile = 0;
+    for (uint64_t c0 = 0; c0 < n; c0 += TILE, ++tile) {
+      const uint64_t base = c0 + (uint64_t)threadIdx.x * SCAN_PER;
+      const bool full = base + SCAN_PER <= n;
+      uint64_t W[SCAN_PER];
+      R epart = (R)0;  // this thread's sum of exp(l - m), fixed order
+      uint64_t run = 0;
+#pragma unroll
+      for (int q = 0; q < SCAN_PER / 4; ++q) {
+        R v[4];
+        if (full) {
+          if constexpr (sizeof(R) == 4) {
+            const float4 f = *reinterpret_cast<const float4*>(a.ell + off + base + 4 * q);
+            v[0] = f.x; v[1] = f.y; v[2] = f.z; v[3] = f.w;
+          } else {
+            const double2 f0 = *reinterpret_cast<const double2*>(a.ell + off + base + 4 * q);
+            const double2 f1 = *reinterpret_cast<const double2*>(a.ell + off + base + 4 * q + 2);
+            v[0] = f0.x; v[1] = f0.y; v[2] = f1.x; v[3] = f1.y;
+          }
+        } else {
+#pragma unroll
+          for (int e = 0; e < 4; ++e)
+            v[e] = (base + 4 * q + e < n) ? a.ell[off + base + 4 * q + e] : (R)0;
+        }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          uint64_t wq = 0;
+          if (full || base + 4 * q + e < n) {
+            R ex;
+            const R dl = v[e] - m;
+            wq = quant_exp<R>(dl, k, &ex);
+            epart = epart + ex;
+          }
+          run += wq;
+          W[4 * q + e] = run;  // inclusive running sum
+        }
+      }
+      {
+        ES es;
+        es.zero();
+        es.add(epart);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) es.add(es.shfl_xor(o));
+        if (lane == 0) s_es[warp] = es;
+      }
+      uint64_t total;
+      const uint64_t excl = block_excl_scan(run, s_warp, &total);  // its barriers publish s_es
+      if (threadIdx.x == 0) {
+        // the tile's partial, folded as the single-filter fold does: tiles
+        // lane-strided over 32 accumulators, each summed in tile order
+        ES tot = s_es[0];
+        for (int q = 1; q < WARPS; ++q) tot.add(s_es[q]);
+        s_fold[tile & 31].add(tot);
+      }
+      const uint64_t o = carry + excl;
+#pragma unroll
+      for (int e = 0; e < SCAN_PER; ++e)
+        if (full || base + e < n) a.Q[off + base + e] = o + W[e];
+      carry += total;
+    }
+    const uint64_t T = carry;
+    if (T == 0) fail = true;
+    __syncthreads();  // Q complete
+
+    // 3. resampling: slot keys B_j against the CDF keys Q_i A (ties go to the
+    // CDF); thread t walks the particles [16 t, 16 t + 16) of each tile from
+    // its first slot; a particle with more than BB_CAP slots leaves a run for
+    // the whole block
+    uint64_t A = n, r = 0;
+    if (POS == POS_SYSTEMATIC) {
+      const U4 wr = draw(seed, fid, t, 0, P_SYS_OFFSET, 0);
+      const uint64_t Rw = ((uint64_t)wr.b << 32) | wr.a;
+      r = __umul64hi(Rw, T);
+    } else {
+      // spacings S_l = E_0 + ... + E_l for l = 0..n (Carpenter, Clifford &
+      // Fearnhead 1999); S_n stays in shared memory
+      uint64_t cs = 0;
+      for (uint64_t c0 = 0; c0 <= n; c0 += TILE) {
+        const uint64_t base = c0 + (uint64_t)threadIdx.x * SCAN_PER;
+        uint64_t Ev[SCAN_PER];
+        uint64_t run = 0;
+#pragma unroll
+        for (int q = 0; q < SCAN_PER / 4; ++q) {
+          const uint64_t l0 = base + 4 * q;  // multiple of 4
+          U4 wd = {0, 0, 0, 0};
+          if (l0 <= n) wd = draw(seed, fid, t, (uint32_t)(l0 >> 2), P_SPACING, 0);
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            uint64_t E = 0;
+            if (l0 + e <= n) E = spacing_E(seed, fid, t, l0 + e, wd);
+            run += E;
+            Ev[4 * q + e] = run;
+          }
+        }
+        uint64_t total;
+        const uint64_t excl = block_excl_scan(run, s_warp, &total);
+        const uint64_t o = cs + excl;
+#pragma unroll
+        for (int e = 0; e < SCAN_PER; ++e) {
+          const uint64_t l = base + e;
+          if (l < n) a.S[off + l] = o + Ev[e];
+          else if (l == n) s_SN = o + Ev[e];
+        }
+        cs += total;
+      }
+      __syncthreads();
+      A = s_SN;
+    }
+    const SysDiv dv = make_sysdiv(T > 0 ? T : 1);
+    const uint64_t* Sf = a.S + off;
+    if (threadIdx.x == 0) s_nruns = 0;
+    __syncthreads();
+    for (uint64_t c0 = 0; c0 < n; c0 += TILE) {
+      const uint64_t ib = c0 + (uint64_t)threadIdx.x * SCAN_PER;
+      if (T > 0 && ib < n) {
+        const uint64_t ie = ib + SCAN_PER < n ? ib + SCAN_PER : n;
+        uint64_t j = 0;
+        if (ib > 0) {
+          const uint64_t qp = a.Q[off + ib - 1];
+          j = POS == POS_SYSTEMATIC ? sys_first_slot(qp, n, r, dv)
+                                    : multi_first_slot(Sf, n, T, mul64(qp, A), 0);
+        }
+        for (uint64_t i = ib; i < ie; ++i) {
+          const uint64_t qi = a.Q[off + i];
+          const U128 KQ = POS == POS_SYSTEMATIC ? mul64x32(qi, (uint32_t)n) : mul64(qi, A);
+          int emitted = 0;
+          while (j < n) {
+            const U128 KB = POS == POS_SYSTEMATIC ? add128(mul64x32(T, (uint32_t)j), r)
+                                                  : mul64(Sf[j], T);
+            if (!lt128(KB, KQ)) break;
+            if (emitted == BB_CAP) {  // a heavy particle: hand its other slots to the block
+              uint64_t R2 = POS == POS_SYSTEMATIC ? sys_first_slot(qi, n, r, dv)
+                                                  : multi_first_slot(Sf, n, T, KQ, j);
+              R2 = R2 < j ? j : R2;
+              const uint32_t kr = atomicAdd(&s_nruns, 1u);
+              if (kr < BB_MAX_RUNS) {
+                s_run[kr][0] = (uint32_t)j;
+                s_run[kr][1] = (uint32_t)R2;
+                s_run[kr][2] = (uint32_t)i;
+              } else {
+                for (uint64_t q = j; q < R2; ++q) a.anc[off + q] = (uint32_t)i;
+              }
+              j = R2;
+              break;
+            }
+            a.anc[off + j] = (uint32_t)i;
+            ++j;
+            ++emitted;
+          }
+        }
+      }
+      __syncthreads();
+      const uint32_t nr = s_nruns < BB_MAX_RUNS ? s_nruns : BB_MAX_RUNS;
+      for (uint32_t q = 0; q < nr; ++q) {
+        const uint32_t st = s_run[q][0], en = s_run[q][1], v = s_run[q][2];
+        for (uint32_t jj = st + threadIdx.x; jj < en; jj += BB) a.anc[off + jj] = v;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) s_nruns = 0;
+      __syncthreads();
+    }
+    if (T == 0) {  // empty CDF (flagged): keep every index in range
+      for (uint64_t j = threadIdx.x; j < n; j += BB) a.anc[off + j] = (uint32_t)j;
+    }
+    __syncthreads();
+
+    // 4. propagation, one slot per thread per pass, deferred gamma draws
+    const R ds = (R)s_c[0], cs = (R)s_c[1], dt = (R)s_c[2], ct = (R)s_c[3];
+    for (uint64_t j0 = 0; j0 < n; j0 += BB) {
+      const uint64_t j = j0 + threadIdx.x;
+      if (threadIdx.x == 0) s_qn = 0;
+      __syncthreads();
+      bool defer_s = false, defer_t = false;
+      typename SuffT<R>::B bsn = 0, btn = 0;
+      R Zs = 0, Us = 0, Zt = 0, Ut = 0;
+      if (j < n) {
+        uint32_t an = a.anc[off + j];
+        an = an < n ? an : (uint32_t)(n - 1);
+        const uint64_t g = off + an;
+        const R xa = src.x[g], sa = src.s2[g], ta = src.t2[g];
+        const R s = sa + ta;
+        const R p = sa * ta;
+        const R V = p / s;
+        const R n1 = xa * sa;
+        const R n2 = yr * ta;
+        const R nn = n1 + n2;
+        const R mu = nn / s;
+        const R sv = sqrt(V);
+        R Z;
+        theta_draws<R>(seed, fid, t, (uint32_t)j, &Z, &Zs, &Us, &Zt, &Ut);
+        const R xz = sv * Z;
+        const R xj = mu + xz;
+        const uint64_t d = off + j;
+        dst.x[d] = xj;
+        if (learn) {
+          const R rs = ResidObs<R>::f(y, yr, xj);
+          const R rt = xj - xa;
+          bsn = SuffOps<R>::add_half_square(src.bs[g], rs, &fail);
+          btn = SuffOps<R>::add_half_square(src.bt[g], rt, &fail);
+          dst.bs[d] = bsn;
+          dst.bt[d] = btn;
+          R Gs, Gt;
+          if (gamma_mt_squeeze<R>(ds, cs, Zs, Us, &Gs)) dst.s2[d] = SuffOps<R>::ig(bsn, Gs);
+          else defer_s = true;
+          if (gamma_mt_squeeze<R>(dt, ct, Zt, Ut, &Gt)) dst.t2[d] = SuffOps<R>::ig(btn, Gt);
+          else defer_t = true;
+        } else {
+          dst.s2[d] = sa;
+          dst.t2[d] = ta;
+          dst.bs[d] = src.bs[g];
+          dst.bt[d] = src.bt[g];
+        }
+      }
+#pragma unroll
+      for (int gi = 0; gi < 2; ++gi) {
+        const bool dfr = gi == 0 ? defer_s : defer_t;
+        const uint32_t msk = __ballot_sync(0xffffffffu, dfr);
+        if (msk) {
+          uint32_t basei = 0;
+          if (lane == 0) basei = atomicAdd(&s_qn, (uint32_t)__popc(msk));
+          basei = __shfl_sync(0xffffffffu, basei, 0);
+          if (dfr) {
+            GammaItem<R> itm;
+            itm.b = gi == 0 ? bsn : btn;
+            itm.Z = gi == 0 ? Zs : Zt;
+            itm.U = gi == 0 ? Us : Ut;
+            itm.j = (uint32_t)j;
+            itm.which = (uint32_t)gi;
+            s_q[basei + __popc(msk & ((1u << lane) - 1u))] = itm;
+          }
+        }
+      }
+      __syncthreads();
+      const uint32_t qn = s_qn;
+      for (uint32_t q = threadIdx.x; q < qn; q += BB) {
+        const GammaItem<R> itm = s_q[q];
+        const bool sig = itm.which == 0;
+        const R G = gamma_mt_from<R>(sig ? ds : dt, sig ? cs : ct, itm.Z, itm.U, seed, fid, t,
+                                     itm.j, sig ? P_GAMMA_SIGMA : P_GAMMA_TAU, &fail);
+        const R v = SuffOps<R>::ig(itm.b, G);
+        if (sig) dst.s2[off + itm.j] = v;
+        else dst.t2[off + itm.j] = v;
+      }
+      __syncthreads();
+    }
+
+    // fold the cycle into the filter's log-ML (the single-filter fold's
+    // butterfly over the 32 tile accumulators) and advance t
+    const bool any_fail = __syncthreads_or(fail);
+    if (warp == 0) {
+      ES acc = s_fold[lane];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc.add(acc.shfl_xor(o));
+      if (lane == 0 && a.commit) {
+        const double LOG_2PI = 0x1.d67f1c864beb5p+0;
+        const double md = (double)m;
+        const double inc = md + log(esum_value(acc)) - log((double)n) - 0.5 * LOG_2PI;
+        F->logml = F->logml + inc;
+        if (any_fail) F->err |= ERR_NUMERIC;
+        F->t = t + 1;
+      }
+    }
+    __syncthreads();
+  }
+  // the last CTA out resets the work counters for the next launch
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(&a.ctr[1], 1u) == gridDim.x - 1) {
+      a.ctr[0] = 0;
+      a.ctr[1] = 0;
+    }
+  }
+}
+
+// Initialisation (Step 0) of the listed filters, one filter per CTA pass;
+// the same draws and arithmetic as k_init.
+template <class R>
+__global__ void __launch_bounds__(BB) k_batch_init(BatchArgs<R> a) {
+  __shared__ double s_c[5];
+  const uint32_t count = *a.count;
+  for (uint32_t w = blockIdx.x; w < count; w += gridDim.x) {
+    BatchFilter* F = &a.F[a.items[w].slot];
+    const uint64_t off = F->off, n = F->n, seed = F->seed;
+    const uint32_t fid = F->filter_id;
+    const bool learn = F->learn != 0;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double ds, cs, dt, ct;
+      mt_constants(F->a_sigma, &ds, &cs);
+      mt_constants(F->a_tau, &dt, &ct);
+      s_c[0] = ds; s_c[1] = cs; s_c[2] = dt; s_c[3] = ct;
+      s_c[4] = sqrt(F->x0_var);
+    }
+    __syncthreads();
+    const StateV<R> st = a.st[0];
+    const R x0m = (R)F->x0_mean;
+    const R sdx = (R)s_c[4];
+    const auto bs0 = SuffOps<R>::from_prior(F->b_sigma);
+    const auto bt0 = SuffOps<R>::from_prior(F->b_tau);
+    bool fail = false;
+    for (uint64_t j = threadIdx.x; j < n; j += BB) {
+      const uint64_t g = off + j;
+      const R Z = bm_normal(draw(seed, fid, 0, (uint32_t)j, P_INIT_X, 0), (R)0);
+      const R p = sdx * Z;
+      st.x[g] = x0m + p;
+      st.bs[g] = bs0;
+      st.bt[g] = bt0;
+      if (!learn) {
+        st.s2[g] = (R)F->sigma2;
+        st.t2[g] = (R)F->tau2;
+        continue;
+      }
+      const R Gs = gamma_mt<R>((R)s_c[0], (R)s_c[1], seed, fid, 0, (uint32_t)j, P_INIT_SIGMA, &fail);
+      const R Gt = gamma_mt<R>((R)s_c[2], (R)s_c[3], seed, fid, 0, (uint32_t)j, P_INIT_TAU, &fail);
+      st.s2[g] = SuffOps<R>::ig(bs0, Gs);
+      st.t2[g] = SuffOps<R>::ig(bt0, Gt);
+    }
+    if (__syncthreads_or(fail) && threadIdx.x == 0) F->err |= ERR_NUMERIC;
+  }
+}
+
+// Posterior summaries of the listed filters, one filter per CTA pass.  The
+// particles are taken in the single-filter estimate's groups (2048 per
+// virtual block, 8 per thread, shifted by particle 0) and the group sums are
+// folded in its order, so the summaries equal a standalone filter's.
+template <class R>
+__global__ void __launch_bounds__(BB) k_batch_estimate(BatchArgs<R> a) {
+  __shared__ double s_sum[6][WARPS];
+  __shared__ double s_col[6][BB];
+  __shared__ double s_tot[6];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t count = *a.count;
+  constexpr uint64_t GROUP = (uint64_t)BLOCK * EST_PER_THREAD;
+  for (uint32_t w = blockIdx.x; w < count; w += gridDim.x) {
+    const BatchFilter* F = &a.F[a.items[w].slot];
+    const uint64_t off = F->off, n = F->n;
+    const uint32_t t = F->t;
+    const StateV<R> st = (t & 1) ? a.st[1] : a.st[0];
+    const R c0 = st.x[off], c1 = st.s2[off], c2 = st.t2[off];
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 6; ++q) s_col[q][threadIdx.x] = 0.0;
+    const uint64_t nblk = (n + GROUP - 1) / GROUP;
+    for (uint64_t b = 0; b < nblk; ++b) {
+      double acc[6];
+      {
+        R loc[6] = {0, 0, 0, 0, 0, 0};
+        const uint64_t base = b * GROUP + (uint64_t)threadIdx.x * EST_PER_THREAD;
+#pragma unroll
+        for (int e = 0; e < EST_PER_THREAD; ++e) {
+          const uint64_t i = base + e;
+          if (i < n) {
+            const R dx = st.x[off + i] - c0, ds = st.s2[off + i] - c1, dt = st.t2[off + i] - c2;
+            loc[0] += dx; loc[1] += dx * dx;
+            loc[2] += ds; loc[3] += ds * ds;
+            loc[4] += dt; loc[5] += dt * dt;
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < 6; ++q) acc[q] = (double)loc[q];
+      }
+#pragma unroll
+      for (int q = 0; q < 6; ++q) {
+        double v = acc[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) s_sum[q][warp] = v;
+      }
+      __syncthreads();
+      if (threadIdx.x < 6) {
+        double v = 0;
+        for (int ww = 0; ww < WARPS; ++ww) v += s_sum[threadIdx.x][ww];
+        s_col[threadIdx.x][b % BB] += v;
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x < 6) {
+      double v = 0;
+      for (int i = 0; i < BB; ++i) v += s_col[threadIdx.x][i];
+      s_tot[threadIdx.x] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const double nd = (double)n;
+      const double cs[3] = {(double)c0, (double)c1, (double)c2};
+      double* o = a.est + (uint64_t)w * BATCH_EST_ROW;
+      o[0] = (double)t;
+      for (int q = 0; q < 3; ++q) {
+        const double m1 = s_tot[2 * q] / nd;
+        const double m2 = s_tot[2 * q + 1] / nd;
+        o[1 + 2 * q] = cs[q] + m1;
+        o[2 + 2 * q] = m2 - m1 * m1;
+      }
+      o[7] = F->logml;
+      o[8] = (double)F->err;
+    }
+  }
+}
+
+}  // namespace pfk

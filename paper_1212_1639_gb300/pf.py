@@ -51,6 +51,20 @@ class PfEstimates(C.Structure):
                 ("log_marglik", C.c_double)]
 
 
+class PfBatchOpts(C.Structure):
+    _fields_ = [("max_filters", C.c_uint32), ("hbm_budget_bytes", C.c_uint64),
+                ("scheme", C.c_int32), ("precision", C.c_int32),
+                ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN),
+                ("alloc_ctx", C.c_void_p)]
+
+
+class PfBatchInfo(C.Structure):
+    _fields_ = [("max_filters", C.c_uint32), ("resident", C.c_uint32),
+                ("pool_particles", C.c_uint64), ("used_particles", C.c_uint64),
+                ("bytes_per_particle", C.c_uint64), ("pool_bytes", C.c_uint64),
+                ("grid", C.c_uint32), ("block", C.c_uint32), ("cycles", C.c_uint64)]
+
+
 _V = C.c_void_p
 _SIGS = {
     "pf_create": [C.POINTER(PfConfig), C.POINTER(_V)],
@@ -69,6 +83,16 @@ _SIGS = {
     "pf_cdf": [_V, C.c_uint64, _V, _V],
     "pf_cutpoint_search": [_V, C.c_uint64, _V, _V],
     "pf_cutpoint_method": [_V, C.c_uint64, _V, _V, C.c_uint64, _V, _V],
+    "pf_batch_create": [C.POINTER(PfConfig), C.c_uint32, C.POINTER(PfBatchOpts), C.POINTER(_V)],
+    "pf_batch_add": [_V, C.POINTER(PfConfig), C.POINTER(C.c_uint32)],
+    "pf_batch_remove": [_V, C.c_uint32],
+    "pf_batch_step": [_V, _V, _V],
+    "pf_batch_estimate": [_V, _V, C.POINTER(PfEstimates)],
+    "pf_batch_sync": [_V],
+    "pf_batch_get_particles": [_V, C.c_uint32, _V, _V, _V, _V, _V],
+    "pf_batch_get_ancestors": [_V, C.c_uint32, _V, _V],
+    "pf_batch_get_info": [_V, C.POINTER(PfBatchInfo)],
+    "pf_batch_destroy": [_V],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -130,6 +154,18 @@ class TorchAllocator:
 
         self.alloc = ALLOC_FN(_alloc)
         self.free = FREE_FN(_free)
+
+
+def filter_config(n, seed=1212, filter_id=0, scheme="systematic", precision="fp32",
+                  x0_mean=0.0, x0_var=10.0, a_sigma=3.0, b_sigma=2.0, a_tau=3.0, b_tau=2.0,
+                  known_variances=False, sigma2=1.0, tau2=0.1):
+    """A pf_config for one filter (stream and allocator fields left empty)."""
+    return PfConfig(n_particles=int(n), seed=int(seed), filter_id=int(filter_id),
+                    scheme=SCHEMES[scheme] if isinstance(scheme, str) else int(scheme),
+                    precision=FP64 if precision in ("fp64", FP64) else FP32,
+                    known_variances=int(bool(known_variances)), x0_mean=x0_mean, x0_var=x0_var,
+                    a_sigma=a_sigma, b_sigma=b_sigma, a_tau=a_tau, b_tau=b_tau,
+                    sigma2=sigma2, tau2=tau2)
 
 
 class Filter:
@@ -213,6 +249,133 @@ class Filter:
     def close(self):
         if getattr(self, "h", None):
             _lib.pf_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many independent filters advanced by one persistent launch per cycle
+    (pf_batch_*).  `filters` is a list of dicts of filter_config() keyword
+    arguments (n, seed, filter_id, priors, ...); scheme and precision are the
+    batch's.  Slots are indexed 0..max_filters-1; the initial filters take
+    slots 0..len(filters)-1."""
+
+    def __init__(self, filters=(), scheme="systematic", precision="fp32", max_filters=0,
+                 hbm_budget_bytes=0, stream=None, torch_alloc=True):
+        torch = _torch()
+        self.scheme = SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
+        self.precision = FP64 if precision in ("fp64", FP64) else FP32
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        if self.stream.cuda_stream == 0:
+            raise ValueError("pass a non-default torch.cuda.Stream (the cycle is graph-captured)")
+        self._alloc = TorchAllocator() if torch_alloc else None
+        cfgs = [self._cfg(f) for f in filters]
+        arr = (PfConfig * max(len(cfgs), 1))(*cfgs)
+        opts = PfBatchOpts(max_filters=int(max_filters), hbm_budget_bytes=int(hbm_budget_bytes),
+                           scheme=self.scheme, precision=self.precision,
+                           stream=C.c_void_p(self.stream.cuda_stream))
+        if self._alloc is not None:
+            opts.alloc = self._alloc.alloc
+            opts.free = self._alloc.free
+        self._opts = opts
+        h = C.c_void_p()
+        _check(_lib.pf_batch_create(arr, len(cfgs), C.byref(opts), C.byref(h)), "pf_batch_create")
+        self.h = h
+        self.max_filters = self.info()["max_filters"]
+        self._n = {}
+        for i, f in enumerate(filters):
+            self._n[i] = int(f["n"])
+
+    def _cfg(self, f):
+        kw = dict(f)
+        kw["scheme"] = self.scheme
+        kw["precision"] = self.precision
+        return filter_config(**kw)
+
+    def add(self, **f):
+        """Admit one filter; returns its slot, or raises PfError (PF_ERR_BUSY
+        when the pool or the slots are full)."""
+        cfg = self._cfg(f)
+        slot = C.c_uint32()
+        _check(_lib.pf_batch_add(self.h, C.byref(cfg), C.byref(slot)), "pf_batch_add")
+        self._n[slot.value] = int(f["n"])
+        return slot.value
+
+    def try_add(self, **f):
+        """add(), but None instead of an exception when admission is refused."""
+        cfg = self._cfg(f)
+        slot = C.c_uint32()
+        st = _lib.pf_batch_add(self.h, C.byref(cfg), C.byref(slot))
+        if st == PF_ERR_BUSY:
+            return None
+        _check(st, "pf_batch_add")
+        self._n[slot.value] = int(f["n"])
+        return slot.value
+
+    def remove(self, slot):
+        _check(_lib.pf_batch_remove(self.h, int(slot)), "pf_batch_remove")
+        self._n.pop(int(slot), None)
+
+    def step(self, y, mask=None):
+        """y: float64 array of max_filters observations (indexed by slot);
+        mask: optional uint8/bool array selecting the filters to step."""
+        y = np.ascontiguousarray(np.asarray(y, dtype=np.float64))
+        assert y.size >= self.max_filters
+        mp = None
+        if mask is not None:
+            mask = np.ascontiguousarray(np.asarray(mask, dtype=np.uint8))
+            assert mask.size >= self.max_filters
+            mp = mask.ctypes.data_as(C.c_void_p)
+        _check(_lib.pf_batch_step(self.h, y.ctypes.data_as(C.c_void_p), mp), "pf_batch_step")
+
+    def sync(self):
+        _check(_lib.pf_batch_sync(self.h), "pf_batch_sync")
+
+    def estimates(self, mask=None):
+        """{slot: summaries dict} for the selected resident filters."""
+        out = (PfEstimates * self.max_filters)()
+        mp = None
+        if mask is not None:
+            mask = np.ascontiguousarray(np.asarray(mask, dtype=np.uint8))
+            mp = mask.ctypes.data_as(C.c_void_p)
+        _check(_lib.pf_batch_estimate(self.h, mp, out), "pf_batch_estimate")
+        sel = [s for s in self._n if mask is None or mask[s]]
+        return {s: {f: getattr(out[s], f) for f, _ in PfEstimates._fields_} for s in sel}
+
+    def particles(self, slot):
+        torch = _torch()
+        n = self._n[int(slot)]
+        rt = torch.float64 if self.precision == FP64 else torch.float32
+        bt = torch.float64 if self.precision == FP64 else torch.int64
+        out = [torch.empty(n, dtype=rt, device="cuda") for _ in range(3)]
+        out += [torch.empty(n, dtype=bt, device="cuda") for _ in range(2)]
+        _check(_lib.pf_batch_get_particles(self.h, int(slot), *[_ptr(t) for t in out]),
+               "pf_batch_get_particles")
+        return dict(zip(("x", "sigma2", "tau2", "b_sigma", "b_tau"), out))
+
+    def ancestors(self, slot, with_cdf=False):
+        torch = _torch()
+        n = self._n[int(slot)]
+        anc = torch.empty(n, dtype=torch.int32, device="cuda")
+        Q = torch.empty(n, dtype=torch.int64, device="cuda") if with_cdf else None
+        _check(_lib.pf_batch_get_ancestors(self.h, int(slot), _ptr(anc),
+                                           _ptr(Q) if Q is not None else None),
+               "pf_batch_get_ancestors")
+        return (anc, Q) if with_cdf else anc
+
+    def info(self):
+        i = PfBatchInfo()
+        _check(_lib.pf_batch_get_info(self.h, C.byref(i)), "pf_batch_get_info")
+        return {f: getattr(i, f) for f, _ in PfBatchInfo._fields_}
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.pf_batch_destroy(self.h)
             self.h = None
 
     def __del__(self):
