@@ -373,6 +373,7 @@ def bench_batched(pf, synth, stream, K=20, W=3, Kp=3, n_filters=4096, seed=4096)
     specs = [dict(n=int(ns[i]), seed=seed + i, filter_id=i) for i in range(n_filters)]
     total = int(ns.sum())
     b = pf.Batch(specs, scheme="systematic", precision="fp32", stream=stream)
+    shapes, chosen = b.tune(ys[0])  # trial cycles: launch shape only, no result changes
     for t in range(W):
         b.step(ys[t])
     b.sync()
@@ -413,6 +414,8 @@ def bench_batched(pf, synth, stream, K=20, W=3, Kp=3, n_filters=4096, seed=4096)
                     "from prior-drawn variances, FP32, systematic" % (n_filters, total),
         "value": total / (ms_b / 1e3), "unit": UNIT, "steps": K, "ms_per_step": ms_b,
         "gpu_launches_per_step": 1, "launch": {"grid": info["grid"], "block": info["block"]},
+        "autotune": {"chosen": chosen,
+                     "shapes": [{"block": bl, "grid": g, "ms": round(m, 4)} for bl, g, m in shapes]},
         "hbm_frac": round(byts / (ms_b / 1e3) / 1e9 / hbm, 4),
         "per_filter_launches": {"value": total / (ms_p / 1e3), "unit": UNIT, "steps": Kp,
                                 "ms_per_step": ms_p, "host_wall_ms_per_step": wall_p * 1e3,

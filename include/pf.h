@@ -244,6 +244,7 @@ typedef struct {
   int32_t scheme;            /* pf_scheme of every filter (the cut-point variants
                                 give the same ancestors as their base schemes) */
   int32_t precision;         /* pf_precision of every filter */
+  int32_t autotune;          /* nonzero: the first pf_batch_step runs pf_batch_tune */
   void* stream;              /* cudaStream_t; NULL = a stream the batch creates */
   pf_alloc_fn alloc;         /* NULL: cudaMallocAsync / cudaFreeAsync */
   pf_free_fn free;
@@ -257,8 +258,19 @@ typedef struct {
   uint64_t bytes_per_particle;          /* device bytes per pool particle */
   uint64_t pool_bytes;
   uint32_t grid, block;                 /* persistent launch shape of the cycle kernel */
+  uint32_t tuned;                       /* nonzero once pf_batch_tune has chosen it */
   uint64_t cycles;                      /* pf_batch_step calls that launched work */
 } pf_batch_info;
+
+/* Launch shapes timed by pf_batch_tune. */
+#define PF_BATCH_MAX_SHAPES 16
+typedef struct {
+  uint32_t n_shapes;
+  uint32_t block[PF_BATCH_MAX_SHAPES];  /* threads per CTA */
+  uint32_t grid[PF_BATCH_MAX_SHAPES];   /* CTAs of the persistent launch */
+  float ms[PF_BATCH_MAX_SHAPES];        /* mean trial cycle time */
+  uint32_t chosen;                      /* index of the shape kept */
+} pf_batch_tuning;
 
 /* Create a batch with n initial filters cfgs[0..n) (host array, may be NULL
  * when n = 0) in slots 0..n-1, and enqueue their initialisation (Step 0).
@@ -285,6 +297,21 @@ pf_status pf_batch_remove(pf_batch* b, uint32_t slot);
  * host-to-device copy of the work list (16 bytes per stepped filter) and one
  * graph launch. */
 pf_status pf_batch_step(pf_batch* b, const double* y, const uint8_t* mask);
+
+/* Autotuner: time the cycle of the selected filters (y, mask as in
+ * pf_batch_step) under every candidate launch shape -- 256 or 512 threads per
+ * CTA, 1 up to the resident maximum of CTAs per SM -- and keep the fastest
+ * for later cycles.  The trial cycles commit nothing (t, the log marginal
+ * likelihood and the error words are unchanged; the next pf_batch_step
+ * overwrites every buffer they wrote), and the launch shape never changes a
+ * result.  *out (may be NULL) receives the timings.  Synchronises. */
+pf_status pf_batch_tune(pf_batch* b, const double* y, const uint8_t* mask, pf_batch_tuning* out);
+
+/* Fix the launch shape instead of tuning: block 256 or 512 threads per CTA,
+ * grid 1 .. the resident maximum of CTAs for that block size (any CTA count
+ * works: CTAs take filters from the work list until it is empty).  Counts as
+ * tuned.  Synchronises.  PF_ERR_INVALID for an unsupported shape. */
+pf_status pf_batch_set_shape(pf_batch* b, uint32_t block, uint32_t grid);
 
 /* Posterior summaries of the resident filters selected by mask (NULL: all),
  * written to out[slot] (host array of max_filters entries; other entries are

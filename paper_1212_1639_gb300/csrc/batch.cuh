@@ -62,12 +62,14 @@ struct BatchArgs {
   int commit;               // 0: a trial cycle that leaves t, log-ML and err untouched
 };
 
-constexpr int BB = BLOCK;                 // threads per CTA (the scan tile's 256)
+constexpr int BB = BLOCK;                 // threads per CTA of the init and summary kernels
 constexpr int BATCH_EST_ROW = 9;          // t, 6 summaries, log-ML, error bits
 constexpr int BB_CAP = 32;                // slots emitted per particle before a run
 constexpr int BB_MAX_RUNS = 1024;         // runs per tile held in shared memory
 
-// Exclusive block prefix of one value per thread, and the block total.
+// Exclusive block prefix of one value per thread (NW warps), and the block
+// total.
+template <int NW>
 __device__ __forceinline__ uint64_t block_excl_scan(uint64_t v, uint64_t* s_warp,
                                                     uint64_t* total) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -75,16 +77,30 @@ __device__ __forceinline__ uint64_t block_excl_scan(uint64_t v, uint64_t* s_warp
   if (lane == 31) s_warp[warp] = incl;
   __syncthreads();
   if (warp == 0) {
-    const uint64_t w = lane < WARPS ? s_warp[lane] : 0;
+    const uint64_t w = lane < NW ? s_warp[lane] : 0;
     const uint64_t wi = warp_incl_scan(w, lane);
-    if (lane < WARPS) s_warp[lane] = wi - w;
-    if (lane == WARPS - 1) s_warp[WARPS] = wi;
+    if (lane < NW) s_warp[lane] = wi - w;
+    if (lane == NW - 1) s_warp[NW] = wi;
   }
   __syncthreads();
   const uint64_t excl = s_warp[warp] + incl - v;
-  *total = s_warp[WARPS];
+  *total = s_warp[NW];
   __syncthreads();  // s_warp is reused by the next call
   return excl;
+}
+
+// Maximum over the block (NW warps), returned to every thread.
+template <class R, int NW>
+__device__ __forceinline__ R block_max_all(R v, R* s_red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if (lane == 0) s_red[warp] = v;
+  __syncthreads();
+  R m = s_red[0];
+  for (int i = 1; i < NW; ++i) m = fmax(m, s_red[i]);
+  __syncthreads();  // s_red is reused by the next call
+  return m;
 }
 
 // #{j in [lo, n) : S_j T < key} for nondecreasing S, by bisection.
@@ -99,17 +115,24 @@ __device__ __forceinline__ uint64_t multi_first_slot(const uint64_t* S, uint64_t
   return lo;
 }
 
-template <class R, int POS>
-__global__ void __launch_bounds__(BB) k_batch_cycle(BatchArgs<R> a) {
+// NT threads per CTA (a multiple of the 256-thread scan tile): each pass of
+// the scan covers NT / 256 tiles of 4096 particles, thread t owning the
+// particles [16 t, 16 t + 16) of the pass, which is exactly the single-filter
+// scan's ownership.
+template <class R, int POS, int NT>
+__global__ void __launch_bounds__(NT) k_batch_cycle(BatchArgs<R> a) {
   typedef typename ESumT<R>::T ES;
-  __shared__ uint64_t s_warp[WARPS + 1];
-  __shared__ R s_red[WARPS];
-  __shared__ ES s_es[WARPS];
+  constexpr int NW = NT / 32;
+  constexpr int TPP = NT / BLOCK;          // scan tiles per pass
+  constexpr uint64_t PASS = (uint64_t)TPP * TILE;
+  __shared__ uint64_t s_warp[NW + 1];
+  __shared__ R s_red[NW];
+  __shared__ ES s_es[NW];
   __shared__ ES s_fold[32];
   __shared__ uint32_t s_work;
   __shared__ uint32_t s_run[BB_MAX_RUNS][3];
   __shared__ uint32_t s_nruns;
-  __shared__ GammaItem<R> s_q[2 * BB];
+  __shared__ GammaItem<R> s_q[2 * NT];
   __shared__ uint32_t s_qn;
   __shared__ double s_c[4];
   __shared__ uint64_t s_SN;
@@ -143,7 +166,7 @@ __global__ void __launch_bounds__(BB) k_batch_cycle(BatchArgs<R> a) {
 
     // 1. weights and their maximum, four particles per thread
     R mx = (R)-INFINITY;
-    for (uint64_t i = 4 * (uint64_t)threadIdx.x; i < n; i += 4 * BB) {
+    for (uint64_t i = 4 * (uint64_t)threadIdx.x; i < n; i += 4 * NT) {
       if (i + 4 <= n) {
         R xv[4], sv[4], tv[4], lv[4];
         if constexpr (sizeof(R) == 4) {
@@ -180,18 +203,14 @@ __global__ void __launch_bounds__(BB) k_batch_cycle(BatchArgs<R> a) {
         }
       }
     }
-    const R m0 = block_max<R>(mx, s_red);  // valid in warp 0
-    __syncthreads();
-    if (threadIdx.x == 0) s_red[0] = m0;
-    __syncthreads();
-    const R m = s_red[0];
+    const R m = block_max_all<R, NW>(mx, s_red);
     if (!(m > (R)-INFINITY)) fail = true;
 
-    // 2. quantised weights and their inclusive scan, one 4096-particle tile
-    // at a time; thread t owns the tile's particles [16 t, 16 t + 16)
+    // 2. quantised weights and their inclusive scan, NT / 256 tiles of 4096
+    // particles per pass; thread t owns the pass's particles [16 t, 16 t + 16)
     uint64_t carry = 0;
     uint32_t tile = 0;
-    for (uint64_t c0 = 0; c0 < n; c0 += TILE, ++tile) {
+    for (uint64_t c0 = 0; c0 < n; c0 += PASS, tile += TPP) {
       const uint64_t base = c0 + (uint64_t)threadIdx.x * SCAN_PER;
       const bool full = base + SCAN_PER <= n;
       uint64_t W[SCAN_PER];
@@ -236,13 +255,18 @@ __global__ void __launch_bounds__(BB) k_batch_cycle(BatchArgs<R> a) {
         if (lane == 0) s_es[warp] = es;
       }
       uint64_t total;
-      const uint64_t excl = block_excl_scan(run, s_warp, &total);  // its barriers publish s_es
+      const uint64_t excl = block_excl_scan<NW>(run, s_warp, &total);  // its barriers publish s_es
       if (threadIdx.x == 0) {
-        // the tile's partial, folded as the single-filter fold does: tiles
-        // lane-strided over 32 accumulators, each summed in tile order
-        ES tot = s_es[0];
-        for (int q = 1; q < WARPS; ++q) tot.add(s_es[q]);
-        s_fold[tile & 31].add(tot);
+        // each tile's partial (its 8 warps in order), folded as the
+        // single-filter fold does: tiles lane-strided over 32 accumulators,
+        // each summed in tile order
+#pragma unroll
+        for (int tp = 0; tp < TPP; ++tp) {
+          if (c0 + (uint64_t)tp * TILE >= n) break;
+          ES tot = s_es[tp * WARPS];
+          for (int q = 1; q < WARPS; ++q) tot.add(s_es[tp * WARPS + q]);
+          s_fold[(tile + tp) & 31].add(tot);
+        }
       }
       const uint64_t o = carry + excl;
 #pragma unroll
@@ -255,7 +279,7 @@ __global__ void __launch_bounds__(BB) k_batch_cycle(BatchArgs<R> a) {
     __syncthreads();  // Q complete
 
     // 3. resampling: slot keys B_j against the CDF keys Q_i A (ties go to the
-    // CDF); thread t walks the particles [16 t, 16 t + 16) of each tile from
+    // CDF); thread t walks the particles [16 t, 16 t + 16) of each pass from
     // its first slot; a particle with more than BB_CAP slots leaves a run for
     // the whole block
     uint64_t A = n, r = 0;
@@ -267,7 +291,7 @@ __global__ void __launch_bounds__(BB) k_batch_cycle(BatchArgs<R> a) {
       // spacings S_l = E_0 + ... + E_l for l = 0..n (Carpenter, Clifford &
       // Fearnhead 1999); S_n stays in shared memory
       uint64_t cs = 0;
-      for (uint64_t c0 = 0; c0 <= n; c0 += TILE) {
+      for (uint64_t c0 = 0; c0 <= n; c0 += PASS) {
         const uint64_t base = c0 + (uint64_t)threadIdx.x * SCAN_PER;
         uint64_t Ev[SCAN_PER];
         uint64_t run = 0;
@@ -285,7 +309,7 @@ __global__ void __launch_bounds__(BB) k_batch_cycle(BatchArgs<R> a) {
           }
         }
         uint64_t total;
-        const uint64_t excl = block_excl_scan(run, s_warp, &total);
+        const uint64_t excl = block_excl_scan<NW>(run, s_warp, &total);
         const uint64_t o = cs + excl;
 #pragma unroll
         for (int e = 0; e < SCAN_PER; ++e) {
@@ -302,7 +326,7 @@ __global__ void __launch_bounds__(BB) k_batch_cycle(BatchArgs<R> a) {
     const uint64_t* Sf = a.S + off;
     if (threadIdx.x == 0) s_nruns = 0;
     __syncthreads();
-    for (uint64_t c0 = 0; c0 < n; c0 += TILE) {
+    for (uint64_t c0 = 0; c0 < n; c0 += PASS) {
       const uint64_t ib = c0 + (uint64_t)threadIdx.x * SCAN_PER;
       if (T > 0 && ib < n) {
         const uint64_t ie = ib + SCAN_PER < n ? ib + SCAN_PER : n;
@@ -345,20 +369,20 @@ __global__ void __launch_bounds__(BB) k_batch_cycle(BatchArgs<R> a) {
       const uint32_t nr = s_nruns < BB_MAX_RUNS ? s_nruns : BB_MAX_RUNS;
       for (uint32_t q = 0; q < nr; ++q) {
         const uint32_t st = s_run[q][0], en = s_run[q][1], v = s_run[q][2];
-        for (uint32_t jj = st + threadIdx.x; jj < en; jj += BB) a.anc[off + jj] = v;
+        for (uint32_t jj = st + threadIdx.x; jj < en; jj += NT) a.anc[off + jj] = v;
       }
       __syncthreads();
       if (threadIdx.x == 0) s_nruns = 0;
       __syncthreads();
     }
     if (T == 0) {  // empty CDF (flagged): keep every index in range
-      for (uint64_t j = threadIdx.x; j < n; j += BB) a.anc[off + j] = (uint32_t)j;
+      for (uint64_t j = threadIdx.x; j < n; j += NT) a.anc[off + j] = (uint32_t)j;
     }
     __syncthreads();
 
     // 4. propagation, one slot per thread per pass, deferred gamma draws
     const R ds = (R)s_c[0], cs = (R)s_c[1], dt = (R)s_c[2], ct = (R)s_c[3];
-    for (uint64_t j0 = 0; j0 < n; j0 += BB) {
+    for (uint64_t j0 = 0; j0 < n; j0 += NT) {
       const uint64_t j = j0 + threadIdx.x;
       if (threadIdx.x == 0) s_qn = 0;
       __syncthreads();
@@ -424,7 +448,7 @@ __global__ void __launch_bounds__(BB) k_batch_cycle(BatchArgs<R> a) {
       }
       __syncthreads();
       const uint32_t qn = s_qn;
-      for (uint32_t q = threadIdx.x; q < qn; q += BB) {
+      for (uint32_t q = threadIdx.x; q < qn; q += NT) {
         const GammaItem<R> itm = s_q[q];
         const bool sig = itm.which == 0;
         const R G = gamma_mt_from<R>(sig ? ds : dt, sig ? cs : ct, itm.Z, itm.U, seed, fid, t,

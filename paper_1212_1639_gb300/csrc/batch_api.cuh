@@ -44,6 +44,9 @@ struct pf_batch {
   double* est_pin = nullptr;
   cudaGraphExec_t exec[kRing] = {};
   unsigned grid = 0;                 // persistent grid of the cycle kernel
+  int nt = 256;                      // its threads per CTA
+  bool autotune = false, tuned = false;
+  std::vector<std::pair<int, unsigned>> shapes;  // (threads per CTA, grid) candidates
   std::vector<uint32_t> order;       // resident slots, largest filter first
   std::map<uint64_t, uint64_t> free_ranges;  // pool offset -> length (particles)
   uint64_t used = 0;                 // particles of resident filters (rounded)
@@ -117,22 +120,56 @@ void set_list(BatchArgs<double>& a, const char* list) {
   a.items = (const BatchItem*)(list + 16);
 }
 
-// Launch the cycle kernel for the list at `list` (device).
+// The cycle kernel for a precision, resampling positions and block size.
+typedef void (*BatchKernelF)(BatchArgs<float>);
+typedef void (*BatchKernelD)(BatchArgs<double>);
+template <class R> struct BatchKernelT;
+template <> struct BatchKernelT<float> { typedef BatchKernelF F; };
+template <> struct BatchKernelT<double> { typedef BatchKernelD F; };
+
+template <class R>
+typename BatchKernelT<R>::F batch_kernel(int pos, int nt) {
+  if (pos == POS_SYSTEMATIC)
+    return nt == 512 ? k_batch_cycle<R, POS_SYSTEMATIC, 512> : k_batch_cycle<R, POS_SYSTEMATIC, 256>;
+  return nt == 512 ? k_batch_cycle<R, POS_MULTINOMIAL, 512> : k_batch_cycle<R, POS_MULTINOMIAL, 256>;
+}
+
+// Launch the cycle kernel for the list at `list` (device) with the batch's
+// current launch shape.
 pf_status launch_batch_cycle(pf_batch* b, const char* list, int commit, cudaStream_t s) {
   if (b->fp64) {
     BatchArgs<double> a = batch_args<double>(b);
     set_list(a, list);
     a.commit = commit;
-    if (b->pos == POS_SYSTEMATIC) k_batch_cycle<double, POS_SYSTEMATIC><<<b->grid, BB, 0, s>>>(a);
-    else k_batch_cycle<double, POS_MULTINOMIAL><<<b->grid, BB, 0, s>>>(a);
+    batch_kernel<double>(b->pos, b->nt)<<<b->grid, b->nt, 0, s>>>(a);
   } else {
     BatchArgs<float> a = batch_args<float>(b);
     set_list(a, list);
     a.commit = commit;
-    if (b->pos == POS_SYSTEMATIC) k_batch_cycle<float, POS_SYSTEMATIC><<<b->grid, BB, 0, s>>>(a);
-    else k_batch_cycle<float, POS_MULTINOMIAL><<<b->grid, BB, 0, s>>>(a);
+    batch_kernel<float>(b->pos, b->nt)<<<b->grid, b->nt, 0, s>>>(a);
   }
   CK(cudaGetLastError());
+  return PF_OK;
+}
+
+// Candidate launch shapes: 256 or 512 threads per CTA, 1 .. the resident
+// maximum of CTAs per SM.  The first is the default before tuning (256
+// threads, as many CTAs as fit).
+pf_status batch_shapes(pf_batch* b) {
+  int dev = 0, sms = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  b->shapes.clear();
+  for (int nt : {256, 512}) {
+    int per_sm = 0;
+    cudaError_t e = b->fp64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<double>(b->pos, nt), nt, 0)
+                            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<float>(b->pos, nt), nt, 0);
+    if (e != cudaSuccess) return set_err(PF_ERR_CUDA, "occupancy query: %s", cudaGetErrorString(e));
+    for (int k = per_sm; k >= 1; --k) b->shapes.push_back({nt, (unsigned)(k * sms)});
+  }
+  if (b->shapes.empty() || sms < 1) return set_err(PF_ERR_CUDA, "no launch shape fits");
+  b->nt = b->shapes[0].first;
+  b->grid = b->shapes[0].second;
   return PF_OK;
 }
 
@@ -282,6 +319,10 @@ pf_status batch_admit(pf_batch* b, const pf_config* cfgs, uint32_t cnt, uint32_t
 
 pf_status batch_build_graphs(pf_batch* b) {
   for (int r = 0; r < pf_batch::kRing; ++r) {
+    if (b->exec[r]) {
+      cudaGraphExecDestroy(b->exec[r]);
+      b->exec[r] = nullptr;
+    }
     CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
     pf_status st = launch_batch_cycle(b, b->list_dev[r], 1, b->stream);
     cudaGraph_t g = nullptr;
@@ -397,23 +438,8 @@ pf_status pf_batch_create(const pf_config* cfgs, uint32_t n, const pf_batch_opts
   b->Fh.assign(maxf, BatchFilter());
   std::memset(b->Fh.data(), 0, (size_t)maxf * sizeof(BatchFilter));
   b->free_ranges[0] = pool;
-  {
-    // persistent grid: resident CTAs per SM x SMs
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaError_t e;
-    if (b->fp64)
-      e = b->pos == POS_SYSTEMATIC
-              ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_cycle<double, POS_SYSTEMATIC>, BB, 0)
-              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_cycle<double, POS_MULTINOMIAL>, BB, 0);
-    else
-      e = b->pos == POS_SYSTEMATIC
-              ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_cycle<float, POS_SYSTEMATIC>, BB, 0)
-              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_cycle<float, POS_MULTINOMIAL>, BB, 0);
-    if (e != cudaSuccess || per_sm < 1 || sms < 1) return bail(set_err(PF_ERR_CUDA, "occupancy query failed"));
-    b->grid = (unsigned)per_sm * (unsigned)sms;
-  }
+  b->autotune = opts->autotune != 0;
+  if ((st = batch_shapes(b)) != PF_OK) return bail(st);
   if (n && (st = batch_admit(b, cfgs, n, nullptr)) != PF_OK) return bail(st);
   if ((st = batch_build_graphs(b)) != PF_OK) return bail(st);
   *out = b;
@@ -441,11 +467,14 @@ pf_status pf_batch_remove(pf_batch* b, uint32_t slot) {
   return PF_OK;
 }
 
-pf_status pf_batch_step(pf_batch* b, const double* y, const uint8_t* mask) {
-  pf_status st = check_batch(b);
-  if (st != PF_OK) return st;
-  if (!y) return set_err(PF_ERR_INVALID, "NULL observations");
-  const uint32_t r = b->ring;
+}  // extern "C"
+
+namespace {
+
+// Fill work list r (pinned) with the selected resident filters, largest
+// first, and copy it to the device.  Returns the number of items.
+pf_status stage_cycle_list(pf_batch* b, uint32_t r, const double* y, const uint8_t* mask,
+                           uint32_t* cnt_out) {
   CK(cudaEventSynchronize(b->list_ev[r]));  // the list copied from this buffer has left
   BatchItem* items = (BatchItem*)(b->list_pin[r] + 16);
   uint32_t cnt = 0;
@@ -456,12 +485,109 @@ pf_status pf_batch_step(pf_batch* b, const double* y, const uint8_t* mask) {
     items[cnt].y = y[s];
     ++cnt;
   }
+  *cnt_out = cnt;
   if (cnt == 0) return PF_OK;
   *(uint32_t*)b->list_pin[r] = cnt;
-  cudaError_t e = cudaMemcpyAsync(b->list_dev[r], b->list_pin[r], 16 + (size_t)cnt * sizeof(BatchItem),
-                                  cudaMemcpyHostToDevice, b->stream);
-  if (e == cudaSuccess) e = cudaEventRecord(b->list_ev[r], b->stream);
-  if (e == cudaSuccess) e = cudaGraphLaunch(b->exec[r], b->stream);
+  CK(cudaMemcpyAsync(b->list_dev[r], b->list_pin[r], 16 + (size_t)cnt * sizeof(BatchItem),
+                     cudaMemcpyHostToDevice, b->stream));
+  CK(cudaEventRecord(b->list_ev[r], b->stream));
+  return PF_OK;
+}
+
+// Time every candidate launch shape on trial cycles of list r (which commit
+// nothing: t, log-ML and the error words stay as they are, and the next real
+// cycle rewrites everything else the trials wrote), keep the fastest and
+// re-capture the cycle graphs with it.
+pf_status batch_tune_list(pf_batch* b, uint32_t r, pf_batch_tuning* out) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  const int reps = 2;
+  float best = 0.0f;
+  size_t best_i = 0;
+  pf_status st = PF_OK;
+  std::vector<float> ms(b->shapes.size(), 0.0f);
+  for (size_t i = 0; i < b->shapes.size() && st == PF_OK; ++i) {
+    b->nt = b->shapes[i].first;
+    b->grid = b->shapes[i].second;
+    st = launch_batch_cycle(b, b->list_dev[r], 0, b->stream);  // warm-up
+    if (st == PF_OK) cudaEventRecord(e0, b->stream);
+    for (int k = 0; k < reps && st == PF_OK; ++k) st = launch_batch_cycle(b, b->list_dev[r], 0, b->stream);
+    if (st != PF_OK) break;
+    cudaEventRecord(e1, b->stream);
+    cudaError_t e = cudaEventSynchronize(e1);
+    if (e != cudaSuccess) {
+      st = set_err(PF_ERR_CUDA, "tuning: %s", cudaGetErrorString(e));
+      break;
+    }
+    cudaEventElapsedTime(&ms[i], e0, e1);
+    ms[i] /= reps;
+    if (i == 0 || ms[i] < best) {
+      best = ms[i];
+      best_i = i;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != PF_OK) return st;
+  b->nt = b->shapes[best_i].first;
+  b->grid = b->shapes[best_i].second;
+  b->tuned = true;
+  if (out) {
+    std::memset(out, 0, sizeof(*out));
+    const size_t m = std::min<size_t>(b->shapes.size(), PF_BATCH_MAX_SHAPES);
+    out->n_shapes = (uint32_t)m;
+    for (size_t i = 0; i < m; ++i) {
+      out->block[i] = (uint32_t)b->shapes[i].first;
+      out->grid[i] = b->shapes[i].second;
+      out->ms[i] = ms[i];
+    }
+    out->chosen = (uint32_t)best_i;
+  }
+  return batch_build_graphs(b);
+}
+
+}  // namespace
+
+extern "C" {
+
+pf_status pf_batch_tune(pf_batch* b, const double* y, const uint8_t* mask, pf_batch_tuning* out) {
+  pf_status st = check_batch(b);
+  if (st != PF_OK) return st;
+  if (!y) return set_err(PF_ERR_INVALID, "NULL observations");
+  const uint32_t r = b->ring;
+  uint32_t cnt = 0;
+  if ((st = stage_cycle_list(b, r, y, mask, &cnt)) != PF_OK) return batch_fail(b, st);
+  if (cnt == 0) return set_err(PF_ERR_INVALID, "no filter selected");
+  b->ring = (r + 1) % pf_batch::kRing;
+  return batch_fail(b, batch_tune_list(b, r, out));
+}
+
+pf_status pf_batch_set_shape(pf_batch* b, uint32_t block, uint32_t grid) {
+  pf_status st = check_batch(b);
+  if (st != PF_OK) return st;
+  if (block != 256 && block != 512) return set_err(PF_ERR_INVALID, "block must be 256 or 512");
+  unsigned cap = 0;
+  for (auto& sh : b->shapes)
+    if (sh.first == (int)block) cap = std::max(cap, sh.second);
+  if (grid < 1 || grid > cap) return set_err(PF_ERR_INVALID, "grid must be in [1, %u] for block %u", cap, block);
+  CK(cudaStreamSynchronize(b->stream));
+  b->nt = (int)block;
+  b->grid = grid;
+  b->tuned = true;
+  return batch_fail(b, batch_build_graphs(b));
+}
+
+pf_status pf_batch_step(pf_batch* b, const double* y, const uint8_t* mask) {
+  pf_status st = check_batch(b);
+  if (st != PF_OK) return st;
+  if (!y) return set_err(PF_ERR_INVALID, "NULL observations");
+  const uint32_t r = b->ring;
+  uint32_t cnt = 0;
+  if ((st = stage_cycle_list(b, r, y, mask, &cnt)) != PF_OK) return batch_fail(b, st);
+  if (cnt == 0) return PF_OK;
+  if (b->autotune && !b->tuned && (st = batch_tune_list(b, r, nullptr)) != PF_OK) return batch_fail(b, st);
+  cudaError_t e = cudaGraphLaunch(b->exec[r], b->stream);
   if (e != cudaSuccess) {
     b->sticky = PF_ERR_CUDA;
     return set_err(PF_ERR_CUDA, "batch step: %s", cudaGetErrorString(e));
@@ -578,7 +704,8 @@ pf_status pf_batch_get_info(pf_batch* b, pf_batch_info* out) {
   out->bytes_per_particle = b->bytes_per_particle;
   out->pool_bytes = b->pool * b->bytes_per_particle;
   out->grid = b->grid;
-  out->block = BB;
+  out->block = (uint32_t)b->nt;
+  out->tuned = b->tuned ? 1u : 0u;
   out->cycles = b->cycles;
   return PF_OK;
 }

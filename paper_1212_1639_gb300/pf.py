@@ -53,16 +53,26 @@ class PfEstimates(C.Structure):
 
 class PfBatchOpts(C.Structure):
     _fields_ = [("max_filters", C.c_uint32), ("hbm_budget_bytes", C.c_uint64),
-                ("scheme", C.c_int32), ("precision", C.c_int32),
+                ("scheme", C.c_int32), ("precision", C.c_int32), ("autotune", C.c_int32),
                 ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN),
                 ("alloc_ctx", C.c_void_p)]
+
+
+BATCH_MAX_SHAPES = 16
+
+
+class PfBatchTuning(C.Structure):
+    _fields_ = [("n_shapes", C.c_uint32), ("block", C.c_uint32 * BATCH_MAX_SHAPES),
+                ("grid", C.c_uint32 * BATCH_MAX_SHAPES), ("ms", C.c_float * BATCH_MAX_SHAPES),
+                ("chosen", C.c_uint32)]
 
 
 class PfBatchInfo(C.Structure):
     _fields_ = [("max_filters", C.c_uint32), ("resident", C.c_uint32),
                 ("pool_particles", C.c_uint64), ("used_particles", C.c_uint64),
                 ("bytes_per_particle", C.c_uint64), ("pool_bytes", C.c_uint64),
-                ("grid", C.c_uint32), ("block", C.c_uint32), ("cycles", C.c_uint64)]
+                ("grid", C.c_uint32), ("block", C.c_uint32), ("tuned", C.c_uint32),
+                ("cycles", C.c_uint64)]
 
 
 _V = C.c_void_p
@@ -88,6 +98,8 @@ _SIGS = {
     "pf_batch_remove": [_V, C.c_uint32],
     "pf_batch_step": [_V, _V, _V],
     "pf_batch_estimate": [_V, _V, C.POINTER(PfEstimates)],
+    "pf_batch_tune": [_V, _V, _V, C.POINTER(PfBatchTuning)],
+    "pf_batch_set_shape": [_V, C.c_uint32, C.c_uint32],
     "pf_batch_sync": [_V],
     "pf_batch_get_particles": [_V, C.c_uint32, _V, _V, _V, _V, _V],
     "pf_batch_get_ancestors": [_V, C.c_uint32, _V, _V],
@@ -266,7 +278,7 @@ class Batch:
     slots 0..len(filters)-1."""
 
     def __init__(self, filters=(), scheme="systematic", precision="fp32", max_filters=0,
-                 hbm_budget_bytes=0, stream=None, torch_alloc=True):
+                 hbm_budget_bytes=0, autotune=False, stream=None, torch_alloc=True):
         torch = _torch()
         self.scheme = SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
         self.precision = FP64 if precision in ("fp64", FP64) else FP32
@@ -278,6 +290,7 @@ class Batch:
         arr = (PfConfig * max(len(cfgs), 1))(*cfgs)
         opts = PfBatchOpts(max_filters=int(max_filters), hbm_budget_bytes=int(hbm_budget_bytes),
                            scheme=self.scheme, precision=self.precision,
+                           autotune=int(bool(autotune)),
                            stream=C.c_void_p(self.stream.cuda_stream))
         if self._alloc is not None:
             opts.alloc = self._alloc.alloc
@@ -335,6 +348,24 @@ class Batch:
 
     def sync(self):
         _check(_lib.pf_batch_sync(self.h), "pf_batch_sync")
+
+    def tune(self, y, mask=None):
+        """Time the candidate launch shapes on trial cycles (which change no
+        result) and keep the fastest; returns [(block, grid, ms)] and the
+        chosen index."""
+        y = np.ascontiguousarray(np.asarray(y, dtype=np.float64))
+        mp = None
+        if mask is not None:
+            mask = np.ascontiguousarray(np.asarray(mask, dtype=np.uint8))
+            mp = mask.ctypes.data_as(C.c_void_p)
+        out = PfBatchTuning()
+        _check(_lib.pf_batch_tune(self.h, y.ctypes.data_as(C.c_void_p), mp, C.byref(out)),
+               "pf_batch_tune")
+        shapes = [(out.block[i], out.grid[i], out.ms[i]) for i in range(out.n_shapes)]
+        return shapes, out.chosen
+
+    def set_shape(self, block, grid):
+        _check(_lib.pf_batch_set_shape(self.h, int(block), int(grid)), "pf_batch_set_shape")
 
     def estimates(self, mask=None):
         """{slot: summaries dict} for the selected resident filters."""

@@ -187,3 +187,36 @@ def test_batch_rejects_bad_configs(pf):
         b.remove(1)
     assert e.value.status == pf.PF_ERR_INVALID
     b.close()
+
+
+@pytest.mark.parametrize("scheme", ["systematic", "multinomial"])
+def test_batch_launch_shapes_change_no_result(pf, scheme):
+    """The autotuner's trial cycles commit nothing, and every candidate launch
+    shape (256 or 512 threads, 1 .. max CTAs) gives the same bits."""
+    sizes = [70000, 9000, 4099, 300, 1, 20000, 5000, 140001]
+    specs = [_spec(i, n) for i, n in enumerate(sizes)]
+    T = 3
+    ys = [_series(i, T) for i in range(len(specs))]
+    tuned = pf.Batch(specs, scheme=scheme, autotune=True)
+    ref = pf.Batch(specs, scheme=scheme)
+    shapes, chosen = ref.tune(np.array([y[0] for y in ys]))
+    assert len(shapes) >= 2 and 0 <= chosen < len(shapes)
+    assert {b for b, _, _ in shapes} == {256, 512}
+    assert all(ms > 0 for _, _, ms in shapes)
+    others = []
+    for blk, grid, _ in shapes[:6]:
+        o = pf.Batch(specs, scheme=scheme)
+        o.set_shape(blk, max(1, grid // 7))   # fewer CTAs than filters, too
+        others.append(o)
+    for t in range(T):
+        y = np.array([ys[i][t] for i in range(len(specs))])
+        for b in [tuned, ref] + others:
+            b.step(y)
+    assert tuned.info()["tuned"] == 1
+    est = ref.estimates()
+    for b in [tuned] + others:
+        assert b.estimates() == est
+        for i in range(len(specs)):
+            _same_particles(_raw(b.particles(i), 0), _raw(ref.particles(i), 0))
+        b.close()
+    ref.close()
