@@ -69,6 +69,9 @@ def parse():
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     p.add_argument("--batched-only", action="store_true",
                    help="print only the batched-filters measurement (one JSON line)")
+    p.add_argument("--served-only", action="store_true",
+                   help="print only the served measurements (one JSON line)")
+    p.add_argument("--served-seconds", type=float, default=60.0)
     return p.parse_args()
 
 
@@ -139,6 +142,14 @@ class Clocks:
         sm.sort()
         return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(mx), "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def phys_gpu(local=0):
+    """nvidia-smi index of this process's GPU."""
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis and len(vis.split(",")) > local and vis.split(",")[local].isdigit():
+        return int(vis.split(",")[local])
+    return local
 
 
 def pow2_label(n):
@@ -231,9 +242,7 @@ def bench_ours(args):
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
-    phys = int(vis.split(",")[local]) if vis and vis.split(",")[local].isdigit() else local
-    clk = Clocks(phys)
+    clk = Clocks(phys_gpu(local))
     clk.start()
     t_wall0 = time.perf_counter()
     ms = time_cycles(f, y_dev, W, K, stream, flush)
@@ -324,6 +333,9 @@ def bench_ours(args):
                 "kernels": {k: round(v, 5) for k, v in profm.items()}}
             fm.close()
         extra["batched"] = bench_batched(pf, synth, stream)
+        extra["served"] = bench_served(pf, synth, stream, duration=args.served_seconds)
+        extra["served_admission"] = bench_served(pf, synth, stream, duration=20.0, budget_gb=8.0,
+                                                 session_s=10.0)
     f.close()
 
     cpu = None
@@ -413,9 +425,11 @@ def bench_batched(pf, synth, stream, K=20, W=3, Kp=3, n_filters=4096, seed=4096)
         "workload": "%d local-level filters, N log-uniform in [256, 65536] (sum %d), own series "
                     "from prior-drawn variances, FP32, systematic" % (n_filters, total),
         "value": total / (ms_b / 1e3), "unit": UNIT, "steps": K, "ms_per_step": ms_b,
-        "gpu_launches_per_step": 1, "launch": {"grid": info["grid"], "block": info["block"]},
+        "gpu_launches_per_step": 1,
+        "launch": {"grid": info["grid"], "block": info["block"], "cluster": info["cluster"],
+                   "big_min": info["big_min"]},
         "autotune": {"chosen": chosen,
-                     "shapes": [{"block": bl, "grid": g, "ms": round(m, 4)} for bl, g, m in shapes]},
+                     "shapes": [dict(sh, ms=round(sh["ms"], 4)) for sh in shapes]},
         "hbm_frac": round(byts / (ms_b / 1e3) / 1e9 / hbm, 4),
         "per_filter_launches": {"value": total / (ms_p / 1e3), "unit": UNIT, "steps": Kp,
                                 "ms_per_step": ms_p, "host_wall_ms_per_step": wall_p * 1e3,
@@ -423,6 +437,85 @@ def bench_batched(pf, synth, stream, K=20, W=3, Kp=3, n_filters=4096, seed=4096)
                                 "note": "pf_step on each filter in turn, one stream"},
         "speedup_vs_per_filter": round(ms_p / ms_b, 2),
         "accuracy": "bit-identical per filter (tests/test_gpu_batch.py)",
+    }
+
+
+def served_events(pf, synth, n_streams, duration, rate, seed, session_s=None):
+    """Poisson observation events for n_streams streams (N log-uniform in
+    [512, 131072], own series from prior-drawn variances).  Without
+    session_s every stream is open for the whole run; with it, stream i is
+    open for session_s seconds starting at a uniform time."""
+    ns, s2, t2 = synth.batch_specs(n_streams, seed, 512, 131072)
+    rng = np.random.default_rng([seed, 0x5E55])
+    if session_s is None:
+        start = np.zeros(n_streams)
+        life = np.full(n_streams, duration)
+    else:
+        start = rng.random(n_streams) * (duration - session_s)
+        life = np.full(n_streams, session_s)
+    ts, ids, ys = [], [], []
+    for i in range(n_streams):
+        k = rng.poisson(rate * life[i])
+        a = np.sort(rng.random(k)) * life[i] + start[i]
+        ys.append(synth.local_level_series(seed + i, k, sigma2=s2[i], tau2=t2[i], filter_id=i)[1])
+        ts.append(a)
+        ids.append(np.full(k, i, np.uint64))
+    t = np.concatenate([start] + ts + [start + life + 1e-3])
+    kind = np.concatenate([np.full(n_streams, pf.EVENT_OPEN, np.uint8)] +
+                          [np.zeros(len(a), np.uint8) for a in ts] +
+                          [np.full(n_streams, pf.EVENT_CLOSE, np.uint8)])
+    sid = np.concatenate([np.arange(n_streams, dtype=np.uint64)] + ids +
+                         [np.arange(n_streams, dtype=np.uint64)])
+    y = np.concatenate([np.zeros(n_streams)] + ys + [np.zeros(n_streams)])
+    pri = np.where(kind == pf.EVENT_OPEN, 0, np.where(kind == pf.EVENT_CLOSE, 2, 1))
+    order = np.lexsort((pri, t))
+    cfgs = [dict(n=int(ns[i]), seed=seed + i, filter_id=i) for i in range(n_streams)]
+    return t[order], kind[order], sid[order], y[order], cfgs, int(ns.sum())
+
+
+def bench_served(pf, synth, stream, duration=60.0, budget_gb=120.0, n_streams=10000,
+                 rate=20.0, seed=10000, session_s=None, cluster=8, big_min=16384):
+    """Continuous-batching server under Poisson load: 10,000 streams at 20
+    observations/s each (200k/s aggregate), device-resident state admitted
+    under an HBM budget; throughput and latency percentiles."""
+    import torch
+    t, kind, sid, y, cfgs, total = served_events(pf, synth, n_streams, duration, rate, seed,
+                                                 session_s)
+    srv = pf.Server(max_streams=n_streams, hbm_budget_bytes=int(budget_gb * 1e9),
+                    scheme="systematic", precision="fp32", max_inflight=2, cluster=cluster,
+                    big_min=big_min, stream=stream)
+    clk = Clocks(phys_gpu())
+    clk.start()
+    t0 = time.perf_counter()
+    srv.replay(t, kind, sid, y, cfgs)
+    srv.drain(duration + 600)
+    wall = time.perf_counter() - t0
+    clocks = clk.stop()
+    st = srv.stats()
+    srv.close()
+    torch.cuda.empty_cache()
+    return {
+        "workload": "%d streams, N log-uniform in [512, 131072] (sum %d), Poisson %.0f obs/s "
+                    "per stream (%.0f/s aggregate) for %.0f s%s, FP32, systematic, budget %.0f GB"
+                    % (n_streams, total, rate, rate * n_streams, duration,
+                       "" if session_s is None else ", sessions of %.0f s" % session_s, budget_gb),
+        "value": st["particle_steps_per_s"], "unit": UNIT,
+        "obs_per_s": st["obs_per_s"], "observations": st["completed"],
+        "latency_us": {"p50": round(st["p50_us"], 1), "p90": round(st["p90_us"], 1),
+                       "p99": round(st["p99_us"], 1), "max": round(st["max_us"], 1),
+                       "mean": round(st["mean_us"], 1)},
+        "cycles": st["cycles"], "mean_streams_per_cycle": round(st["mean_cycle_streams"], 1),
+        "max_streams_per_cycle": st["max_cycle_streams"],
+        "gpu_launches": 2 * st["cycles"],
+        "launch": {"block": st["block"], "grid": st["grid"], "cluster": st["cluster"],
+                   "big_min": big_min if st["cluster"] > 1 else None},
+        "admission": {"admitted": st["admitted"], "admitted_after_wait": st["admitted_after_wait"],
+                      "mean_wait_us": round(st["mean_admission_wait_us"], 1),
+                      "pool_particles": st["pool_particles"]},
+        "replay_max_lag_us": round(st["replay_max_lag_us"], 1), "wall_s": round(wall, 2),
+        "clocks": clocks,
+        "note": "latency = submit -> the stream's summaries on the host; each result equals "
+                "the stream alone (tests/test_gpu_serve.py)",
     }
 
 
@@ -500,6 +593,18 @@ def main():
         stream = torch.cuda.Stream()
         torch.cuda.set_stream(stream)
         print(json.dumps(bench_batched(pf, synth, stream, K=args.steps, W=max(args.warmup, 3))))
+    elif args.served_only:
+        import torch
+
+        from paper_1212_1639_gb300 import pf, synth
+        stream = torch.cuda.Stream()
+        torch.cuda.set_stream(stream)
+        print(json.dumps({
+            "served": bench_served(pf, synth, stream, duration=args.served_seconds),
+            "served_no_clusters": bench_served(pf, synth, stream, duration=args.served_seconds,
+                                               cluster=1),
+            "served_admission": bench_served(pf, synth, stream, duration=20.0, budget_gb=8.0,
+                                             session_s=10.0)}))
     else:
         bench_ours(args)
 

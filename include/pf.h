@@ -258,7 +258,9 @@ typedef struct {
   uint64_t bytes_per_particle;          /* device bytes per pool particle */
   uint64_t pool_bytes;
   uint32_t grid, block;                 /* persistent launch shape of the cycle kernel */
-  uint32_t tuned;                       /* nonzero once pf_batch_tune has chosen it */
+  uint32_t cluster;                     /* CTAs per cluster (1: no clusters) */
+  uint32_t big_min;                     /* clusters take filters of at least this many particles */
+  uint32_t tuned;                       /* nonzero once pf_batch_tune or pf_batch_set_shape chose it */
   uint64_t cycles;                      /* pf_batch_step calls that launched work */
 } pf_batch_info;
 
@@ -268,6 +270,8 @@ typedef struct {
   uint32_t n_shapes;
   uint32_t block[PF_BATCH_MAX_SHAPES];  /* threads per CTA */
   uint32_t grid[PF_BATCH_MAX_SHAPES];   /* CTAs of the persistent launch */
+  uint32_t cluster[PF_BATCH_MAX_SHAPES];  /* CTAs per cluster */
+  uint32_t big_min[PF_BATCH_MAX_SHAPES];  /* filter size from which a whole cluster takes it */
   float ms[PF_BATCH_MAX_SHAPES];        /* mean trial cycle time */
   uint32_t chosen;                      /* index of the shape kept */
 } pf_batch_tuning;
@@ -278,13 +282,14 @@ typedef struct {
  * known-variance settings; its scheme and precision must equal opts'; its
  * stream and allocator fields are ignored.  Errors: PF_ERR_INVALID,
  * PF_ERR_OOM, PF_ERR_CUDA, PF_ERR_BUSY (the budget cannot hold the initial
- * filters).  Synchronises. */
+ * filters).  The initialisation runs asynchronously on the batch's stream. */
 pf_status pf_batch_create(const pf_config* cfgs, uint32_t n, const pf_batch_opts* opts,
                           pf_batch** out);
 
 /* Admit one more filter: the lowest free slot goes to *slot and its
- * initialisation is enqueued.  PF_ERR_BUSY when no slot is free or no free
- * pool range holds cfg->n_particles (nothing changes then).  Synchronises. */
+ * initialisation is enqueued (asynchronous; it does not wait for cycles in
+ * flight).  PF_ERR_BUSY when no slot is free or no free pool range holds
+ * cfg->n_particles (nothing changes then). */
 pf_status pf_batch_add(pf_batch* b, const pf_config* cfg, uint32_t* slot);
 
 /* Release a slot and its pool range (reused only by work enqueued later on
@@ -299,19 +304,27 @@ pf_status pf_batch_remove(pf_batch* b, uint32_t slot);
 pf_status pf_batch_step(pf_batch* b, const double* y, const uint8_t* mask);
 
 /* Autotuner: time the cycle of the selected filters (y, mask as in
- * pf_batch_step) under every candidate launch shape -- 256 or 512 threads per
- * CTA, 1 up to the resident maximum of CTAs per SM -- and keep the fastest
- * for later cycles.  The trial cycles commit nothing (t, the log marginal
+ * pf_batch_step) under every candidate launch shape and keep the fastest for
+ * later cycles.  Candidates: one CTA per filter with 256 or 512 threads and 1
+ * up to the resident maximum of CTAs per SM; and thread-block clusters of 2,
+ * 4 or 8 CTAs of 256 threads, where filters of at least 1 or 4 scan tiles
+ * (4096 particles) per CTA of the cluster are processed by a whole cluster
+ * together (exchanging their scan totals through distributed shared memory)
+ * and smaller ones by single CTAs.  The trial cycles commit nothing (t, the log marginal
  * likelihood and the error words are unchanged; the next pf_batch_step
  * overwrites every buffer they wrote), and the launch shape never changes a
  * result.  *out (may be NULL) receives the timings.  Synchronises. */
 pf_status pf_batch_tune(pf_batch* b, const double* y, const uint8_t* mask, pf_batch_tuning* out);
 
-/* Fix the launch shape instead of tuning: block 256 or 512 threads per CTA,
- * grid 1 .. the resident maximum of CTAs for that block size (any CTA count
- * works: CTAs take filters from the work list until it is empty).  Counts as
- * tuned.  Synchronises.  PF_ERR_INVALID for an unsupported shape. */
-pf_status pf_batch_set_shape(pf_batch* b, uint32_t block, uint32_t grid);
+/* Fix the launch shape instead of tuning: block 256 or 512 threads per CTA
+ * without clusters (cluster 0 or 1), or 256 threads in clusters of 2, 4 or 8
+ * CTAs, which take the filters of at least big_min particles together; grid
+ * a multiple of the cluster size up to the resident maximum for the shape
+ * (any count works: CTAs and clusters take filters from the work list until
+ * it is empty).  Counts as tuned.  Synchronises.  PF_ERR_INVALID for an
+ * unsupported shape. */
+pf_status pf_batch_set_shape(pf_batch* b, uint32_t block, uint32_t grid, uint32_t cluster,
+                             uint32_t big_min);
 
 /* Posterior summaries of the resident filters selected by mask (NULL: all),
  * written to out[slot] (host array of max_filters entries; other entries are
@@ -335,6 +348,113 @@ pf_status pf_batch_get_info(pf_batch* b, pf_batch_info* out);
 
 /* Free the batch after its stream's pending work.  NULL-safe. */
 pf_status pf_batch_destroy(pf_batch* b);
+
+/* ---------------------------------------------------------------------------
+ * Serving: streams of observations that arrive at any time, each stream a
+ * particle-learning filter whose state stays on the device.  A worker thread
+ * inside the library does continuous batching: every cycle it takes the
+ * oldest pending observation of every resident stream that has one, runs
+ * them as one batched cycle (the pf_batch kernel) followed by the summaries
+ * of the stepped streams, and keeps up to max_inflight cycles on the device
+ * while it forms the next cycle from what has arrived meanwhile.  Streams are
+ * admitted in FIFO order while the pool (sized by the HBM budget) and the
+ * slots have room; a stream that does not fit waits (its observations queue)
+ * until others close.
+ *
+ * Each observation yields one result: the stream's posterior summaries after
+ * that observation, bit for bit what a standalone filter with the stream's
+ * configuration gives after the same observations, however the streams were
+ * interleaved.  Latency is measured from the submit call to the moment the
+ * worker sees the summaries on the host.
+ *
+ * Thread safety: open / submit / close / poll / stats may be called from any
+ * threads; the handle serialises them.
+ * --------------------------------------------------------------------------- */
+typedef struct pf_server pf_server;
+
+typedef struct {
+  uint32_t max_streams;       /* slots (resident streams at most) */
+  uint64_t hbm_budget_bytes;  /* device bytes of the particle pool (> 0) */
+  int32_t scheme;             /* pf_scheme of every stream */
+  int32_t precision;          /* pf_precision of every stream */
+  uint32_t max_inflight;      /* cycles on the device at once, 1..4 (0 = 2) */
+  int32_t keep_results;       /* nonzero: keep per-observation results for pf_server_poll */
+  uint32_t block, grid;       /* launch shape (0 = the batch default) */
+  uint32_t cluster, big_min;  /* clusters of CTAs for large streams (0 = none) */
+  void* stream;               /* cudaStream_t; NULL = one the server creates */
+  pf_alloc_fn alloc;          /* NULL: cudaMallocAsync / cudaFreeAsync */
+  pf_free_fn free;
+  void* alloc_ctx;
+} pf_server_opts;
+
+typedef struct {
+  uint64_t stream_id;
+  uint64_t seq;              /* observation index within the stream, from 0 */
+  pf_estimates est;          /* summaries after this observation */
+  float latency_us;          /* submit -> summaries on the host */
+  int32_t status;            /* PF_OK, or PF_ERR_NUMERIC if the filter's error word is set */
+} pf_server_result;
+
+typedef struct {
+  uint64_t submitted, completed;        /* observations */
+  uint64_t cycles, particle_steps;      /* batched cycles; sum of n over completed observations */
+  uint64_t streams_opened, streams_closed, admitted, admitted_after_wait;
+  uint32_t waiting, resident;           /* streams now waiting for admission / resident */
+  uint64_t pool_particles, used_particles;
+  double mean_cycle_streams;            /* streams per cycle */
+  uint32_t max_cycle_streams;
+  double mean_admission_wait_us, replay_max_lag_us;
+  double wall_s;                        /* first submit -> last result */
+  double particle_steps_per_s, obs_per_s;
+  double mean_us, p50_us, p90_us, p99_us, max_us;  /* observation latency */
+  uint32_t grid, block, cluster;
+} pf_server_stats;
+
+/* Replay event kinds (pf_server_replay). */
+#define PF_EVENT_OBS 0
+#define PF_EVENT_CLOSE 1
+#define PF_EVENT_OPEN 2
+
+/* Create a server and start its worker thread.  Errors: PF_ERR_INVALID,
+ * PF_ERR_OOM, PF_ERR_CUDA. */
+pf_status pf_server_create(const pf_server_opts* opts, pf_server** out);
+
+/* Open stream `id` (any caller-chosen unique value) with configuration cfg
+ * (as for pf_batch_add: scheme and precision must be the server's).  The
+ * stream enters the admission queue; it is initialised once admitted.
+ * PF_ERR_BUSY if it can never fit the pool. */
+pf_status pf_server_open(pf_server* s, uint64_t id, const pf_config* cfg);
+
+/* Queue observation y for stream id (time-stamped now). */
+pf_status pf_server_submit(pf_server* s, uint64_t id, double y);
+
+/* Close stream id once its queued observations are done; its slot and pool
+ * range then go to waiting streams. */
+pf_status pf_server_close(pf_server* s, uint64_t id);
+
+/* Load generator: a library thread replays count events at times t_s[i]
+ * (seconds from this call, nondecreasing): kind[i] PF_EVENT_OBS submits y[i]
+ * to stream ids[i], PF_EVENT_CLOSE closes it, PF_EVENT_OPEN opens it with
+ * cfgs[ids[i]] (cfgs has n_cfgs entries).  The arrays are copied; the call
+ * returns at once.  PF_ERR_BUSY while another replay runs. */
+pf_status pf_server_replay(pf_server* s, uint64_t count, const double* t_s, const uint8_t* kind,
+                           const uint64_t* ids, const double* y, const pf_config* cfgs,
+                           uint64_t n_cfgs);
+
+/* Wait (up to timeout_s) until the replay has finished and every submitted
+ * observation has its result.  PF_ERR_TIMEOUT otherwise. */
+pf_status pf_server_drain(pf_server* s, double timeout_s);
+
+/* Move up to max finished results (in completion order) to out; *n gets the
+ * count.  Results are kept only with opts.keep_results. */
+pf_status pf_server_poll(pf_server* s, pf_server_result* out, uint32_t max, uint32_t* n);
+
+/* Counters, throughput and latency percentiles so far. */
+pf_status pf_server_get_stats(pf_server* s, pf_server_stats* out);
+
+/* Stop the worker after the cycles in flight, free everything.  Observations
+ * still queued are dropped.  NULL-safe. */
+pf_status pf_server_destroy(pf_server* s);
 
 #ifdef __cplusplus
 }

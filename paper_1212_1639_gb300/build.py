@@ -13,8 +13,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "libpf.so")
-SOURCES = ["api.cu"]
-DEPS = ["api.cu", "kernels.cuh", "device.cuh", "batch.cuh", "batch_api.cuh"]
+SOURCES = ["api.cu", "batch_f32.cu", "batch_f64.cu"]
+DEPS = ["api.cu", "batch_f32.cu", "batch_f64.cu", "kernels.cuh", "device.cuh", "batch.cuh",
+        "batch_launch.h", "batch_kernels.cuh", "batch_api.cuh", "server_api.cuh"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 
@@ -51,7 +52,7 @@ def build(force=False, verbose=False):
         if p.wait() != 0:
             raise RuntimeError("nvcc failed: " + " ".join(cmd))
     tmp = LIB + ".tmp.%d" % os.getpid()
-    subprocess.run([nvcc(), ARCH, "-shared", "-o", tmp] + objs + ["-lcudart"], check=True)
+    subprocess.run([nvcc(), ARCH, "-shared", "-o", tmp] + objs + ["-lcudart", "-lpthread"], check=True)
     os.replace(tmp, LIB)
     return LIB
 

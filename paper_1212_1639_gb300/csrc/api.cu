@@ -851,3 +851,4 @@ extern "C" pf_status pf_resample_noalloc(const float* w_dev, uint64_t n, uint64_
 }
 
 #include "batch_api.cuh"
+#include "server_api.cuh"

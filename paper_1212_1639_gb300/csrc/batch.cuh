@@ -40,6 +40,13 @@ struct BatchFilter {
   double logml;        // accumulated log marginal likelihood
 };
 
+// One entry of an admission list: the slot and its new record.
+struct BatchInit {
+  uint32_t slot;
+  uint32_t pad[3];
+  BatchFilter rec;
+};
+
 // One entry of a cycle's work list.
 struct BatchItem {
   uint32_t slot;
@@ -56,9 +63,11 @@ struct BatchArgs {
   uint32_t* anc;            // per particle
   BatchFilter* F;           // per slot
   const BatchItem* items;   // work list, largest filters first
-  const uint32_t* count;    // number of items (device)
-  uint32_t* ctr;            // [0] next item, [1] finished CTAs; both 0 between launches
+  const uint32_t* count;    // [0] number of items, [1] large items (cluster launches)
+  uint32_t* ctr;            // [0] next large item, [1] finished CTAs, [2] next other item;
+                            // all 0 between launches
   double* est;              // k_batch_estimate: BATCH_EST_ROW doubles per item, in list order
+  const BatchInit* inits;   // k_batch_init: the admitted filters (count in *count)
   int commit;               // 0: a trial cycle that leaves t, log-ML and err untouched
 };
 
@@ -115,59 +124,119 @@ __device__ __forceinline__ uint64_t multi_first_slot(const uint64_t* S, uint64_t
   return lo;
 }
 
-// NT threads per CTA (a multiple of the 256-thread scan tile): each pass of
-// the scan covers NT / 256 tiles of 4096 particles, thread t owning the
-// particles [16 t, 16 t + 16) of the pass, which is exactly the single-filter
-// scan's ownership.
-template <class R, int POS, int NT>
-__global__ void __launch_bounds__(NT) k_batch_cycle(BatchArgs<R> a) {
+// ---------------------------------------------------------------------------
+// Thread-block clusters (sm_90+): a large filter is processed by the CTAs of
+// one cluster together.  They exchange per-round totals through distributed
+// shared memory and meet at cluster barriers (release / acquire at cluster
+// scope, which also orders their global-memory writes).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// Barrier over the G CTAs processing one filter (G = 1: the CTA itself).
+__device__ __forceinline__ void group_sync(uint32_t G) {
+  if (G > 1)
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\t"
+                 "barrier.cluster.wait.acquire.aligned;" ::: "memory");
+  else
+    __syncthreads();
+}
+__device__ __forceinline__ uint32_t dsm_addr(const void* p, uint32_t rank) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+// Read a shared variable of CTA `rank` of this cluster.
+template <class T>
+__device__ __forceinline__ T dsm_ld(const T* p, uint32_t rank) {
+  static_assert(sizeof(T) == 4 || sizeof(T) % 8 == 0, "4-byte or 8-byte words");
+  T v;
+  if constexpr (sizeof(T) == 4) {
+    uint32_t u;
+    asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(u) : "r"(dsm_addr(p, rank)) : "memory");
+    memcpy(&v, &u, 4);
+  } else {
+#pragma unroll
+    for (int i = 0; i < (int)(sizeof(T) / 8); ++i) {
+      uint64_t u;
+      asm volatile("ld.shared::cluster.u64 %0, [%1];"
+                   : "=l"(u) : "r"(dsm_addr((const char*)p + 8 * i, rank)) : "memory");
+      memcpy((char*)&v + 8 * i, &u, 8);
+    }
+  }
+  return v;
+}
+
+// Shared memory of the cycle kernel.
+template <class R, int NT>
+struct BatchSmem {
+  typedef typename ESumT<R>::T ES;
+  uint64_t warp[NT / 32 + 1];
+  R red[NT / 32];
+  ES es[NT / 32];
+  ES fold[32];                   // log-ML tile partials, lane-strided (group rank 0)
+  uint32_t run[BB_MAX_RUNS][3];
+  GammaItem<R> q[2 * NT];
+  double c[4];
+  uint32_t nruns, qn;
+  // read by the other CTAs of a group (distributed shared memory)
+  R gmax;                        // this CTA's maximum of l
+  uint64_t utot[2];              // this round's pass total, by round parity
+  ES ues[2][NT / BLOCK];         // this round's tile partials, by round parity
+  uint64_t SN;                   // S_n, if this CTA produced it
+  uint32_t fail;
+  uint32_t work;                 // the group leader's claimed item
+  // broadcasts within the CTA
+  uint64_t roff, rsum;
+  R m;
+  uint32_t wb;
+};
+
+// One cycle of one filter by a group of G CTAs (G = 1: one CTA; G > 1: the
+// CTAs of a cluster, this one being `rank`).  The particles are cut into
+// passes of NT / 256 scan tiles; round j gives pass j G + rank to this CTA.
+// Thread t of a pass owns its particles [16 t, 16 t + 16) -- the
+// single-filter scan's ownership -- and the tile partials of the log-ML are
+// folded in tile order, so the result does not depend on G.
+template <class R, int POS, int NT, uint32_t G>
+__device__ __forceinline__ void batch_filter(const BatchArgs<R>& a, const BatchItem item,
+                                             BatchSmem<R, NT>& sm, const uint32_t rank) {
   typedef typename ESumT<R>::T ES;
   constexpr int NW = NT / 32;
   constexpr int TPP = NT / BLOCK;          // scan tiles per pass
   constexpr uint64_t PASS = (uint64_t)TPP * TILE;
-  __shared__ uint64_t s_warp[NW + 1];
-  __shared__ R s_red[NW];
-  __shared__ ES s_es[NW];
-  __shared__ ES s_fold[32];
-  __shared__ uint32_t s_work;
-  __shared__ uint32_t s_run[BB_MAX_RUNS][3];
-  __shared__ uint32_t s_nruns;
-  __shared__ GammaItem<R> s_q[2 * NT];
-  __shared__ uint32_t s_qn;
-  __shared__ double s_c[4];
-  __shared__ uint64_t s_SN;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint32_t count = *a.count;
+  BatchFilter* F = &a.F[item.slot];
+  const uint64_t off = F->off, n = F->n, seed = F->seed;
+  const uint32_t fid = F->filter_id, t = F->t;
+  const int k = F->k;
+  const bool learn = F->learn != 0;
+  const StateV<R> src = (t & 1) ? a.st[1] : a.st[0];
+  const StateV<R> dst = (t & 1) ? a.st[0] : a.st[1];
+  const double y = item.y;
+  const R yr = (R)y;
+  if (threadIdx.x == 0) {
+    // Marsaglia-Tsang (d, c) of the shapes a0 + (t+1)/2
+    double ds, cs, dt, ct;
+    mt_constants(F->a_sigma + 0.5 * (double)(t + 1), &ds, &cs);
+    mt_constants(F->a_tau + 0.5 * (double)(t + 1), &dt, &ct);
+    sm.c[0] = ds; sm.c[1] = cs; sm.c[2] = dt; sm.c[3] = ct;
+  }
+  if (rank == 0 && threadIdx.x < 32) sm.fold[threadIdx.x].zero();
+  bool fail = false;
+  const uint64_t passes = (n + PASS - 1) / PASS;
+  const uint64_t rounds = (passes + G - 1) / G;
 
-  while (true) {
-    if (threadIdx.x == 0) s_work = atomicAdd(&a.ctr[0], 1u);
-    __syncthreads();
-    const uint32_t w = s_work;
-    if (w >= count) break;
-    const BatchItem item = a.items[w];
-    BatchFilter* F = &a.F[item.slot];
-    const uint64_t off = F->off, n = F->n, seed = F->seed;
-    const uint32_t fid = F->filter_id, t = F->t;
-    const int k = F->k;
-    const bool learn = F->learn != 0;
-    const StateV<R> src = (t & 1) ? a.st[1] : a.st[0];
-    const StateV<R> dst = (t & 1) ? a.st[0] : a.st[1];
-    const double y = item.y;
-    const R yr = (R)y;
-    if (threadIdx.x == 0) {
-      // Marsaglia-Tsang (d, c) of the shapes a0 + (t+1)/2
-      double ds, cs, dt, ct;
-      mt_constants(F->a_sigma + 0.5 * (double)(t + 1), &ds, &cs);
-      mt_constants(F->a_tau + 0.5 * (double)(t + 1), &dt, &ct);
-      s_c[0] = ds; s_c[1] = cs; s_c[2] = dt; s_c[3] = ct;
-    }
-    if (threadIdx.x < 32) s_fold[threadIdx.x].zero();
-    bool fail = false;
-
-    // 1. weights and their maximum, four particles per thread
-    R mx = (R)-INFINITY;
-    for (uint64_t i = 4 * (uint64_t)threadIdx.x; i < n; i += 4 * NT) {
-      if (i + 4 <= n) {
+  // 1. weights and their maximum, four particles per thread
+  R mx = (R)-INFINITY;
+  for (uint64_t jr = 0; jr < rounds; ++jr) {
+    const uint64_t lo = (jr * G + rank) * PASS;
+    const uint64_t hi = lo + PASS < n ? lo + PASS : n;
+    for (uint64_t i = lo + 4 * (uint64_t)threadIdx.x; i < hi; i += 4 * NT) {
+      if (i + 4 <= hi) {
         R xv[4], sv[4], tv[4], lv[4];
         if constexpr (sizeof(R) == 4) {
           const float4 X = *reinterpret_cast<const float4*>(src.x + off + i);
@@ -195,7 +264,7 @@ __global__ void __launch_bounds__(NT) k_batch_cycle(BatchArgs<R> a) {
           for (int e = 0; e < 4; ++e) a.ell[off + i + e] = lv[e];
         }
       } else {
-        for (uint64_t q = i; q < n; ++q) {
+        for (uint64_t q = i; q < hi; ++q) {
           const R l = log_pred<R>(src.x[off + q], src.s2[off + q], src.t2[off + q], yr);
           fail |= !(l < (R)INFINITY);
           mx = fmax(mx, l);
@@ -203,280 +272,386 @@ __global__ void __launch_bounds__(NT) k_batch_cycle(BatchArgs<R> a) {
         }
       }
     }
-    const R m = block_max_all<R, NW>(mx, s_red);
-    if (!(m > (R)-INFINITY)) fail = true;
+  }
+  R m = block_max_all<R, NW>(mx, sm.red);
+  if (G > 1) {
+    if (threadIdx.x == 0) sm.gmax = m;
+    group_sync(G);
+    if (threadIdx.x == 0) {
+      R v = m;
+      for (uint32_t r = 0; r < G; ++r) v = fmax(v, dsm_ld(&sm.gmax, r));
+      sm.m = v;
+    }
+    __syncthreads();
+    m = sm.m;
+  }
+  if (!(m > (R)-INFINITY)) fail = true;
 
-    // 2. quantised weights and their inclusive scan, NT / 256 tiles of 4096
-    // particles per pass; thread t owns the pass's particles [16 t, 16 t + 16)
-    uint64_t carry = 0;
-    uint32_t tile = 0;
-    for (uint64_t c0 = 0; c0 < n; c0 += PASS, tile += TPP) {
-      const uint64_t base = c0 + (uint64_t)threadIdx.x * SCAN_PER;
-      const bool full = base + SCAN_PER <= n;
-      uint64_t W[SCAN_PER];
-      R epart = (R)0;  // this thread's sum of exp(l - m), fixed order
+  // One round of an exclusive scan over the group: this CTA's pass total
+  // goes out, its offset within the round and the round total come back.
+  uint32_t par = 0;  // parity of the exchange buffers, alternating every round
+  auto round_offsets = [&](uint64_t total, uint64_t* roff, uint64_t* rsum) {
+    if (G == 1) {
+      *roff = 0;
+      *rsum = total;
+      return;
+    }
+    if (threadIdx.x == 0) sm.utot[par] = total;
+    group_sync(G);
+    if (warp == 0) {
+      const uint64_t v = (uint32_t)lane < G ? dsm_ld(&sm.utot[par], (uint32_t)lane) : 0ull;
+      const uint64_t incl = warp_incl_scan(v, lane);
+      if ((uint32_t)lane == rank) sm.roff = incl - v;
+      if (lane == 31) sm.rsum = incl;
+    }
+  };
+
+  // 2. quantised weights and their inclusive scan, round by round
+  uint64_t carry = 0;
+  for (uint64_t jr = 0; jr < rounds; ++jr, par ^= 1u) {
+    const uint64_t pidx = jr * G + rank;
+    const uint64_t c0 = pidx * PASS;
+    const uint64_t base = c0 + (uint64_t)threadIdx.x * SCAN_PER;
+    const bool full = base + SCAN_PER <= n;
+    uint64_t W[SCAN_PER];
+    R epart = (R)0;  // this thread's sum of exp(l - m), fixed order
+    uint64_t run = 0;
+#pragma unroll
+    for (int q = 0; q < SCAN_PER / 4; ++q) {
+      R v[4];
+      if (full) {
+        if constexpr (sizeof(R) == 4) {
+          const float4 f = *reinterpret_cast<const float4*>(a.ell + off + base + 4 * q);
+          v[0] = f.x; v[1] = f.y; v[2] = f.z; v[3] = f.w;
+        } else {
+          const double2 f0 = *reinterpret_cast<const double2*>(a.ell + off + base + 4 * q);
+          const double2 f1 = *reinterpret_cast<const double2*>(a.ell + off + base + 4 * q + 2);
+          v[0] = f0.x; v[1] = f0.y; v[2] = f1.x; v[3] = f1.y;
+        }
+      } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+          v[e] = (base + 4 * q + e < n) ? a.ell[off + base + 4 * q + e] : (R)0;
+      }
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        uint64_t wq = 0;
+        if (full || base + 4 * q + e < n) {
+          R ex;
+          const R dl = v[e] - m;
+          wq = quant_exp<R>(dl, k, &ex);
+          epart = epart + ex;
+        }
+        run += wq;
+        W[4 * q + e] = run;  // inclusive running sum
+      }
+    }
+    {
+      ES es;
+      es.zero();
+      es.add(epart);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) es.add(es.shfl_xor(o));
+      if (lane == 0) sm.es[warp] = es;
+    }
+    uint64_t total;
+    const uint64_t excl = block_excl_scan<NW>(run, sm.warp, &total);  // its barriers publish sm.es
+    if (threadIdx.x == 0) {
+      // each tile's partial: its 8 warps in order
+#pragma unroll
+      for (int tp = 0; tp < TPP; ++tp) {
+        ES tot = sm.es[tp * WARPS];
+        for (int q = 1; q < WARPS; ++q) tot.add(sm.es[tp * WARPS + q]);
+        sm.ues[par][tp] = tot;
+      }
+    }
+    uint64_t roff, rsum;
+    round_offsets(total, &roff, &rsum);
+    if (threadIdx.x == 0 && rank == 0) {
+      // the round's tile partials into the fold, in tile order: tiles
+      // lane-strided over 32 accumulators, as the single-filter fold does
+      for (uint32_t r = 0; r < G; ++r) {
+#pragma unroll
+        for (int tp = 0; tp < TPP; ++tp) {
+          const uint64_t tile = (jr * G + r) * TPP + tp;
+          if (tile * TILE >= n) continue;
+          const ES pt = G == 1 ? sm.ues[par][tp] : dsm_ld(&sm.ues[par][tp], r);
+          sm.fold[tile & 31].add(pt);
+        }
+      }
+    }
+    if (G > 1) {
+      __syncthreads();
+      roff = sm.roff;
+      rsum = sm.rsum;
+    }
+    const uint64_t o = carry + roff + excl;
+#pragma unroll
+    for (int e = 0; e < SCAN_PER; ++e)
+      if (full || base + e < n) a.Q[off + base + e] = o + W[e];
+    carry += rsum;
+  }
+  const uint64_t T = carry;
+  if (T == 0) fail = true;
+
+  // 3. resampling: slot keys B_j against the CDF keys Q_i A (ties go to the
+  // CDF); thread t walks the particles [16 t, 16 t + 16) of each of this
+  // CTA's passes from its first slot; a particle with more than BB_CAP slots
+  // leaves a run for the whole CTA
+  uint64_t A = n, r = 0;
+  if (POS == POS_SYSTEMATIC) {
+    const U4 wr = draw(seed, fid, t, 0, P_SYS_OFFSET, 0);
+    const uint64_t Rw = ((uint64_t)wr.b << 32) | wr.a;
+    r = __umul64hi(Rw, T);
+    group_sync(G);  // Q complete
+  } else {
+    // spacings S_l = E_0 + ... + E_l for l = 0..n (Carpenter, Clifford &
+    // Fearnhead 1999), the same rounds; S_n stays in shared memory
+    const uint64_t passes_e = (n + 1 + PASS - 1) / PASS;
+    const uint64_t rounds_e = (passes_e + G - 1) / G;
+    uint64_t cs = 0;
+    for (uint64_t jr = 0; jr < rounds_e; ++jr, par ^= 1u) {
+      const uint64_t base = (jr * G + rank) * PASS + (uint64_t)threadIdx.x * SCAN_PER;
+      uint64_t Ev[SCAN_PER];
       uint64_t run = 0;
 #pragma unroll
       for (int q = 0; q < SCAN_PER / 4; ++q) {
-        R v[4];
-        if (full) {
-          if constexpr (sizeof(R) == 4) {
-            const float4 f = *reinterpret_cast<const float4*>(a.ell + off + base + 4 * q);
-            v[0] = f.x; v[1] = f.y; v[2] = f.z; v[3] = f.w;
-          } else {
-            const double2 f0 = *reinterpret_cast<const double2*>(a.ell + off + base + 4 * q);
-            const double2 f1 = *reinterpret_cast<const double2*>(a.ell + off + base + 4 * q + 2);
-            v[0] = f0.x; v[1] = f0.y; v[2] = f1.x; v[3] = f1.y;
-          }
-        } else {
-#pragma unroll
-          for (int e = 0; e < 4; ++e)
-            v[e] = (base + 4 * q + e < n) ? a.ell[off + base + 4 * q + e] : (R)0;
-        }
+        const uint64_t l0 = base + 4 * q;  // multiple of 4
+        U4 wd = {0, 0, 0, 0};
+        if (l0 <= n) wd = draw(seed, fid, t, (uint32_t)(l0 >> 2), P_SPACING, 0);
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-          uint64_t wq = 0;
-          if (full || base + 4 * q + e < n) {
-            R ex;
-            const R dl = v[e] - m;
-            wq = quant_exp<R>(dl, k, &ex);
-            epart = epart + ex;
-          }
-          run += wq;
-          W[4 * q + e] = run;  // inclusive running sum
+          uint64_t E = 0;
+          if (l0 + e <= n) E = spacing_E(seed, fid, t, l0 + e, wd);
+          run += E;
+          Ev[4 * q + e] = run;
         }
-      }
-      {
-        ES es;
-        es.zero();
-        es.add(epart);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) es.add(es.shfl_xor(o));
-        if (lane == 0) s_es[warp] = es;
       }
       uint64_t total;
-      const uint64_t excl = block_excl_scan<NW>(run, s_warp, &total);  // its barriers publish s_es
-      if (threadIdx.x == 0) {
-        // each tile's partial (its 8 warps in order), folded as the
-        // single-filter fold does: tiles lane-strided over 32 accumulators,
-        // each summed in tile order
-#pragma unroll
-        for (int tp = 0; tp < TPP; ++tp) {
-          if (c0 + (uint64_t)tp * TILE >= n) break;
-          ES tot = s_es[tp * WARPS];
-          for (int q = 1; q < WARPS; ++q) tot.add(s_es[tp * WARPS + q]);
-          s_fold[(tile + tp) & 31].add(tot);
-        }
+      const uint64_t excl = block_excl_scan<NW>(run, sm.warp, &total);
+      uint64_t roff, rsum;
+      round_offsets(total, &roff, &rsum);
+      if (G > 1) {
+        __syncthreads();
+        roff = sm.roff;
+        rsum = sm.rsum;
       }
-      const uint64_t o = carry + excl;
+      const uint64_t o = cs + roff + excl;
 #pragma unroll
-      for (int e = 0; e < SCAN_PER; ++e)
-        if (full || base + e < n) a.Q[off + base + e] = o + W[e];
-      carry += total;
-    }
-    const uint64_t T = carry;
-    if (T == 0) fail = true;
-    __syncthreads();  // Q complete
-
-    // 3. resampling: slot keys B_j against the CDF keys Q_i A (ties go to the
-    // CDF); thread t walks the particles [16 t, 16 t + 16) of each pass from
-    // its first slot; a particle with more than BB_CAP slots leaves a run for
-    // the whole block
-    uint64_t A = n, r = 0;
-    if (POS == POS_SYSTEMATIC) {
-      const U4 wr = draw(seed, fid, t, 0, P_SYS_OFFSET, 0);
-      const uint64_t Rw = ((uint64_t)wr.b << 32) | wr.a;
-      r = __umul64hi(Rw, T);
-    } else {
-      // spacings S_l = E_0 + ... + E_l for l = 0..n (Carpenter, Clifford &
-      // Fearnhead 1999); S_n stays in shared memory
-      uint64_t cs = 0;
-      for (uint64_t c0 = 0; c0 <= n; c0 += PASS) {
-        const uint64_t base = c0 + (uint64_t)threadIdx.x * SCAN_PER;
-        uint64_t Ev[SCAN_PER];
-        uint64_t run = 0;
-#pragma unroll
-        for (int q = 0; q < SCAN_PER / 4; ++q) {
-          const uint64_t l0 = base + 4 * q;  // multiple of 4
-          U4 wd = {0, 0, 0, 0};
-          if (l0 <= n) wd = draw(seed, fid, t, (uint32_t)(l0 >> 2), P_SPACING, 0);
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            uint64_t E = 0;
-            if (l0 + e <= n) E = spacing_E(seed, fid, t, l0 + e, wd);
-            run += E;
-            Ev[4 * q + e] = run;
-          }
-        }
-        uint64_t total;
-        const uint64_t excl = block_excl_scan<NW>(run, s_warp, &total);
-        const uint64_t o = cs + excl;
-#pragma unroll
-        for (int e = 0; e < SCAN_PER; ++e) {
-          const uint64_t l = base + e;
-          if (l < n) a.S[off + l] = o + Ev[e];
-          else if (l == n) s_SN = o + Ev[e];
-        }
-        cs += total;
+      for (int e = 0; e < SCAN_PER; ++e) {
+        const uint64_t l = base + e;
+        if (l < n) a.S[off + l] = o + Ev[e];
+        else if (l == n) sm.SN = o + Ev[e];
       }
-      __syncthreads();
-      A = s_SN;
+      cs += rsum;
     }
-    const SysDiv dv = make_sysdiv(T > 0 ? T : 1);
-    const uint64_t* Sf = a.S + off;
-    if (threadIdx.x == 0) s_nruns = 0;
+    group_sync(G);  // Q, S and S_n complete
+    if (threadIdx.x == 0) {
+      const uint32_t owner = (uint32_t)((n / PASS) % G);
+      sm.roff = G == 1 ? sm.SN : dsm_ld(&sm.SN, owner);
+    }
     __syncthreads();
-    for (uint64_t c0 = 0; c0 < n; c0 += PASS) {
-      const uint64_t ib = c0 + (uint64_t)threadIdx.x * SCAN_PER;
-      if (T > 0 && ib < n) {
-        const uint64_t ie = ib + SCAN_PER < n ? ib + SCAN_PER : n;
-        uint64_t j = 0;
-        if (ib > 0) {
-          const uint64_t qp = a.Q[off + ib - 1];
-          j = POS == POS_SYSTEMATIC ? sys_first_slot(qp, n, r, dv)
-                                    : multi_first_slot(Sf, n, T, mul64(qp, A), 0);
-        }
-        for (uint64_t i = ib; i < ie; ++i) {
-          const uint64_t qi = a.Q[off + i];
-          const U128 KQ = POS == POS_SYSTEMATIC ? mul64x32(qi, (uint32_t)n) : mul64(qi, A);
-          int emitted = 0;
-          while (j < n) {
-            const U128 KB = POS == POS_SYSTEMATIC ? add128(mul64x32(T, (uint32_t)j), r)
-                                                  : mul64(Sf[j], T);
-            if (!lt128(KB, KQ)) break;
-            if (emitted == BB_CAP) {  // a heavy particle: hand its other slots to the block
-              uint64_t R2 = POS == POS_SYSTEMATIC ? sys_first_slot(qi, n, r, dv)
-                                                  : multi_first_slot(Sf, n, T, KQ, j);
-              R2 = R2 < j ? j : R2;
-              const uint32_t kr = atomicAdd(&s_nruns, 1u);
-              if (kr < BB_MAX_RUNS) {
-                s_run[kr][0] = (uint32_t)j;
-                s_run[kr][1] = (uint32_t)R2;
-                s_run[kr][2] = (uint32_t)i;
-              } else {
-                for (uint64_t q = j; q < R2; ++q) a.anc[off + q] = (uint32_t)i;
-              }
-              j = R2;
-              break;
+    A = sm.roff;
+  }
+  const SysDiv dv = make_sysdiv(T > 0 ? T : 1);
+  const uint64_t* Sf = a.S + off;
+  if (threadIdx.x == 0) sm.nruns = 0;
+  __syncthreads();
+  for (uint64_t jr = 0; jr < rounds; ++jr) {
+    const uint64_t ib = (jr * G + rank) * PASS + (uint64_t)threadIdx.x * SCAN_PER;
+    if (T > 0 && ib < n) {
+      const uint64_t ie = ib + SCAN_PER < n ? ib + SCAN_PER : n;
+      uint64_t j = 0;
+      if (ib > 0) {
+        const uint64_t qp = a.Q[off + ib - 1];
+        j = POS == POS_SYSTEMATIC ? sys_first_slot(qp, n, r, dv)
+                                  : multi_first_slot(Sf, n, T, mul64(qp, A), 0);
+      }
+      for (uint64_t i = ib; i < ie; ++i) {
+        const uint64_t qi = a.Q[off + i];
+        const U128 KQ = POS == POS_SYSTEMATIC ? mul64x32(qi, (uint32_t)n) : mul64(qi, A);
+        int emitted = 0;
+        while (j < n) {
+          const U128 KB = POS == POS_SYSTEMATIC ? add128(mul64x32(T, (uint32_t)j), r)
+                                                : mul64(Sf[j], T);
+          if (!lt128(KB, KQ)) break;
+          if (emitted == BB_CAP) {  // a heavy particle: hand its other slots to the CTA
+            uint64_t R2 = POS == POS_SYSTEMATIC ? sys_first_slot(qi, n, r, dv)
+                                                : multi_first_slot(Sf, n, T, KQ, j);
+            R2 = R2 < j ? j : R2;
+            const uint32_t kr = atomicAdd(&sm.nruns, 1u);
+            if (kr < BB_MAX_RUNS) {
+              sm.run[kr][0] = (uint32_t)j;
+              sm.run[kr][1] = (uint32_t)R2;
+              sm.run[kr][2] = (uint32_t)i;
+            } else {
+              for (uint64_t q = j; q < R2; ++q) a.anc[off + q] = (uint32_t)i;
             }
-            a.anc[off + j] = (uint32_t)i;
-            ++j;
-            ++emitted;
+            j = R2;
+            break;
           }
+          a.anc[off + j] = (uint32_t)i;
+          ++j;
+          ++emitted;
         }
-      }
-      __syncthreads();
-      const uint32_t nr = s_nruns < BB_MAX_RUNS ? s_nruns : BB_MAX_RUNS;
-      for (uint32_t q = 0; q < nr; ++q) {
-        const uint32_t st = s_run[q][0], en = s_run[q][1], v = s_run[q][2];
-        for (uint32_t jj = st + threadIdx.x; jj < en; jj += NT) a.anc[off + jj] = v;
-      }
-      __syncthreads();
-      if (threadIdx.x == 0) s_nruns = 0;
-      __syncthreads();
-    }
-    if (T == 0) {  // empty CDF (flagged): keep every index in range
-      for (uint64_t j = threadIdx.x; j < n; j += NT) a.anc[off + j] = (uint32_t)j;
-    }
-    __syncthreads();
-
-    // 4. propagation, one slot per thread per pass, deferred gamma draws
-    const R ds = (R)s_c[0], cs = (R)s_c[1], dt = (R)s_c[2], ct = (R)s_c[3];
-    for (uint64_t j0 = 0; j0 < n; j0 += NT) {
-      const uint64_t j = j0 + threadIdx.x;
-      if (threadIdx.x == 0) s_qn = 0;
-      __syncthreads();
-      bool defer_s = false, defer_t = false;
-      typename SuffT<R>::B bsn = 0, btn = 0;
-      R Zs = 0, Us = 0, Zt = 0, Ut = 0;
-      if (j < n) {
-        uint32_t an = a.anc[off + j];
-        an = an < n ? an : (uint32_t)(n - 1);
-        const uint64_t g = off + an;
-        const R xa = src.x[g], sa = src.s2[g], ta = src.t2[g];
-        const R s = sa + ta;
-        const R p = sa * ta;
-        const R V = p / s;
-        const R n1 = xa * sa;
-        const R n2 = yr * ta;
-        const R nn = n1 + n2;
-        const R mu = nn / s;
-        const R sv = sqrt(V);
-        R Z;
-        theta_draws<R>(seed, fid, t, (uint32_t)j, &Z, &Zs, &Us, &Zt, &Ut);
-        const R xz = sv * Z;
-        const R xj = mu + xz;
-        const uint64_t d = off + j;
-        dst.x[d] = xj;
-        if (learn) {
-          const R rs = ResidObs<R>::f(y, yr, xj);
-          const R rt = xj - xa;
-          bsn = SuffOps<R>::add_half_square(src.bs[g], rs, &fail);
-          btn = SuffOps<R>::add_half_square(src.bt[g], rt, &fail);
-          dst.bs[d] = bsn;
-          dst.bt[d] = btn;
-          R Gs, Gt;
-          if (gamma_mt_squeeze<R>(ds, cs, Zs, Us, &Gs)) dst.s2[d] = SuffOps<R>::ig(bsn, Gs);
-          else defer_s = true;
-          if (gamma_mt_squeeze<R>(dt, ct, Zt, Ut, &Gt)) dst.t2[d] = SuffOps<R>::ig(btn, Gt);
-          else defer_t = true;
-        } else {
-          dst.s2[d] = sa;
-          dst.t2[d] = ta;
-          dst.bs[d] = src.bs[g];
-          dst.bt[d] = src.bt[g];
-        }
-      }
-#pragma unroll
-      for (int gi = 0; gi < 2; ++gi) {
-        const bool dfr = gi == 0 ? defer_s : defer_t;
-        const uint32_t msk = __ballot_sync(0xffffffffu, dfr);
-        if (msk) {
-          uint32_t basei = 0;
-          if (lane == 0) basei = atomicAdd(&s_qn, (uint32_t)__popc(msk));
-          basei = __shfl_sync(0xffffffffu, basei, 0);
-          if (dfr) {
-            GammaItem<R> itm;
-            itm.b = gi == 0 ? bsn : btn;
-            itm.Z = gi == 0 ? Zs : Zt;
-            itm.U = gi == 0 ? Us : Ut;
-            itm.j = (uint32_t)j;
-            itm.which = (uint32_t)gi;
-            s_q[basei + __popc(msk & ((1u << lane) - 1u))] = itm;
-          }
-        }
-      }
-      __syncthreads();
-      const uint32_t qn = s_qn;
-      for (uint32_t q = threadIdx.x; q < qn; q += NT) {
-        const GammaItem<R> itm = s_q[q];
-        const bool sig = itm.which == 0;
-        const R G = gamma_mt_from<R>(sig ? ds : dt, sig ? cs : ct, itm.Z, itm.U, seed, fid, t,
-                                     itm.j, sig ? P_GAMMA_SIGMA : P_GAMMA_TAU, &fail);
-        const R v = SuffOps<R>::ig(itm.b, G);
-        if (sig) dst.s2[off + itm.j] = v;
-        else dst.t2[off + itm.j] = v;
-      }
-      __syncthreads();
-    }
-
-    // fold the cycle into the filter's log-ML (the single-filter fold's
-    // butterfly over the 32 tile accumulators) and advance t
-    const bool any_fail = __syncthreads_or(fail);
-    if (warp == 0) {
-      ES acc = s_fold[lane];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) acc.add(acc.shfl_xor(o));
-      if (lane == 0 && a.commit) {
-        const double LOG_2PI = 0x1.d67f1c864beb5p+0;
-        const double md = (double)m;
-        const double inc = md + log(esum_value(acc)) - log((double)n) - 0.5 * LOG_2PI;
-        F->logml = F->logml + inc;
-        if (any_fail) F->err |= ERR_NUMERIC;
-        F->t = t + 1;
       }
     }
     __syncthreads();
+    const uint32_t nr = sm.nruns < BB_MAX_RUNS ? sm.nruns : BB_MAX_RUNS;
+    for (uint32_t q = 0; q < nr; ++q) {
+      const uint32_t st = sm.run[q][0], en = sm.run[q][1], v = sm.run[q][2];
+      for (uint32_t jj = st + threadIdx.x; jj < en; jj += NT) a.anc[off + jj] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) sm.nruns = 0;
+    __syncthreads();
+  }
+  if (T == 0) {  // empty CDF (flagged): keep every index in range
+    for (uint64_t j = rank * NT + threadIdx.x; j < n; j += (uint64_t)G * NT)
+      a.anc[off + j] = (uint32_t)j;
+  }
+  group_sync(G);  // every ancestor written
+
+  // 4. propagation, one slot per thread per pass (slot blocks of NT dealt
+  // round-robin over the group), deferred gamma draws
+  const R ds = (R)sm.c[0], cs = (R)sm.c[1], dt = (R)sm.c[2], ct = (R)sm.c[3];
+  for (uint64_t j0 = (uint64_t)rank * NT; j0 < n; j0 += (uint64_t)G * NT) {
+    const uint64_t j = j0 + threadIdx.x;
+    if (threadIdx.x == 0) sm.qn = 0;
+    __syncthreads();
+    bool defer_s = false, defer_t = false;
+    typename SuffT<R>::B bsn = 0, btn = 0;
+    R Zs = 0, Us = 0, Zt = 0, Ut = 0;
+    if (j < n) {
+      uint32_t an = a.anc[off + j];
+      an = an < n ? an : (uint32_t)(n - 1);
+      const uint64_t g = off + an;
+      const R xa = src.x[g], sa = src.s2[g], ta = src.t2[g];
+      const R s = sa + ta;
+      const R p = sa * ta;
+      const R V = p / s;
+      const R n1 = xa * sa;
+      const R n2 = yr * ta;
+      const R nn = n1 + n2;
+      const R mu = nn / s;
+      const R sv = sqrt(V);
+      R Z;
+      theta_draws<R>(seed, fid, t, (uint32_t)j, &Z, &Zs, &Us, &Zt, &Ut);
+      const R xz = sv * Z;
+      const R xj = mu + xz;
+      const uint64_t d = off + j;
+      dst.x[d] = xj;
+      if (learn) {
+        const R rs = ResidObs<R>::f(y, yr, xj);
+        const R rt = xj - xa;
+        bsn = SuffOps<R>::add_half_square(src.bs[g], rs, &fail);
+        btn = SuffOps<R>::add_half_square(src.bt[g], rt, &fail);
+        dst.bs[d] = bsn;
+        dst.bt[d] = btn;
+        R Gs, Gt;
+        if (gamma_mt_squeeze<R>(ds, cs, Zs, Us, &Gs)) dst.s2[d] = SuffOps<R>::ig(bsn, Gs);
+        else defer_s = true;
+        if (gamma_mt_squeeze<R>(dt, ct, Zt, Ut, &Gt)) dst.t2[d] = SuffOps<R>::ig(btn, Gt);
+        else defer_t = true;
+      } else {
+        dst.s2[d] = sa;
+        dst.t2[d] = ta;
+        dst.bs[d] = src.bs[g];
+        dst.bt[d] = src.bt[g];
+      }
+    }
+#pragma unroll
+    for (int gi = 0; gi < 2; ++gi) {
+      const bool dfr = gi == 0 ? defer_s : defer_t;
+      const uint32_t msk = __ballot_sync(0xffffffffu, dfr);
+      if (msk) {
+        uint32_t basei = 0;
+        if (lane == 0) basei = atomicAdd(&sm.qn, (uint32_t)__popc(msk));
+        basei = __shfl_sync(0xffffffffu, basei, 0);
+        if (dfr) {
+          GammaItem<R> itm;
+          itm.b = gi == 0 ? bsn : btn;
+          itm.Z = gi == 0 ? Zs : Zt;
+          itm.U = gi == 0 ? Us : Ut;
+          itm.j = (uint32_t)j;
+          itm.which = (uint32_t)gi;
+          sm.q[basei + __popc(msk & ((1u << lane) - 1u))] = itm;
+        }
+      }
+    }
+    __syncthreads();
+    const uint32_t qn = sm.qn;
+    for (uint32_t q = threadIdx.x; q < qn; q += NT) {
+      const GammaItem<R> itm = sm.q[q];
+      const bool sig = itm.which == 0;
+      const R G2 = gamma_mt_from<R>(sig ? ds : dt, sig ? cs : ct, itm.Z, itm.U, seed, fid, t,
+                                    itm.j, sig ? P_GAMMA_SIGMA : P_GAMMA_TAU, &fail);
+      const R v = SuffOps<R>::ig(itm.b, G2);
+      if (sig) dst.s2[off + itm.j] = v;
+      else dst.t2[off + itm.j] = v;
+    }
+    __syncthreads();
+  }
+
+  // fold the cycle into the filter's log-ML (the single-filter fold's
+  // butterfly over the 32 tile accumulators) and advance t
+  bool any_fail = __syncthreads_or(fail);
+  if (G > 1) {
+    if (threadIdx.x == 0) sm.fail = any_fail ? 1u : 0u;
+    group_sync(G);
+  }
+  if (rank == 0 && warp == 0) {
+    if (G > 1) {
+      const uint32_t f = (uint32_t)lane < G ? dsm_ld(&sm.fail, (uint32_t)lane) : 0u;
+      any_fail = __any_sync(0xffffffffu, f != 0u);
+    }
+    ES acc = sm.fold[lane];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc.add(acc.shfl_xor(o));
+    if (lane == 0 && a.commit) {
+      const double LOG_2PI = 0x1.d67f1c864beb5p+0;
+      const double md = (double)m;
+      const double inc = md + log(esum_value(acc)) - log((double)n) - 0.5 * LOG_2PI;
+      F->logml = F->logml + inc;
+      if (any_fail) F->err |= ERR_NUMERIC;
+      F->t = t + 1;
+    }
+  }
+  __syncthreads();
+}
+
+// The persistent cycle kernel.  With CL > 1 (launched as clusters of CL
+// CTAs) each cluster first takes the large filters -- the first count[1]
+// items of the size-ordered list -- one at a time and processes each with
+// all its CTAs; then every CTA takes the remaining filters one at a time on
+// its own.  count[0] is the number of items.
+template <class R, int POS, int NT, int CL>
+__global__ void __launch_bounds__(NT, NT == 256 ? (POS == POS_SYSTEMATIC && CL == 1 ? 4 : 3) : 1)
+k_batch_cycle(BatchArgs<R> a) {
+  __shared__ BatchSmem<R, NT> sm;
+  const uint32_t count = a.count[0];
+  uint32_t nbig = 0;
+  if constexpr (CL > 1) {
+    nbig = a.count[1] < count ? a.count[1] : count;
+    const uint32_t rank = cluster_ctarank();
+    while (true) {
+      if (rank == 0 && threadIdx.x == 0) sm.work = atomicAdd(&a.ctr[0], 1u);
+      group_sync(CL);
+      if (threadIdx.x == 0) sm.wb = dsm_ld(&sm.work, 0u);
+      __syncthreads();
+      const uint32_t w = sm.wb;
+      group_sync(CL);  // the leader's claim is read before it changes or the leader exits
+      if (w >= nbig) break;
+      batch_filter<R, POS, NT, (uint32_t)CL>(a, a.items[w], sm, rank);
+    }
+  }
+  while (true) {
+    if (threadIdx.x == 0) sm.wb = nbig + atomicAdd(&a.ctr[2], 1u);
+    __syncthreads();
+    const uint32_t w = sm.wb;
+    __syncthreads();
+    if (w >= count) break;
+    batch_filter<R, POS, NT, 1u>(a, a.items[w], sm, 0u);
   }
   // the last CTA out resets the work counters for the next launch
   if (threadIdx.x == 0) {
@@ -484,35 +659,39 @@ __global__ void __launch_bounds__(NT) k_batch_cycle(BatchArgs<R> a) {
     if (atomicAdd(&a.ctr[1], 1u) == gridDim.x - 1) {
       a.ctr[0] = 0;
       a.ctr[1] = 0;
+      a.ctr[2] = 0;
     }
   }
 }
 
-// Initialisation (Step 0) of the listed filters, one filter per CTA pass;
-// the same draws and arithmetic as k_init.
+// Admission: write each admitted filter's record into its slot and
+// initialise its particles (Step 0), one filter per CTA pass; the same draws
+// and arithmetic as k_init.
 template <class R>
 __global__ void __launch_bounds__(BB) k_batch_init(BatchArgs<R> a) {
   __shared__ double s_c[5];
   const uint32_t count = *a.count;
   for (uint32_t w = blockIdx.x; w < count; w += gridDim.x) {
-    BatchFilter* F = &a.F[a.items[w].slot];
-    const uint64_t off = F->off, n = F->n, seed = F->seed;
-    const uint32_t fid = F->filter_id;
-    const bool learn = F->learn != 0;
+    const BatchFilter* rec = &a.inits[w].rec;
+    BatchFilter* F = &a.F[a.inits[w].slot];
+    const uint64_t off = rec->off, n = rec->n, seed = rec->seed;
+    const uint32_t fid = rec->filter_id;
+    const bool learn = rec->learn != 0;
     __syncthreads();
     if (threadIdx.x == 0) {
+      *F = *rec;
       double ds, cs, dt, ct;
-      mt_constants(F->a_sigma, &ds, &cs);
-      mt_constants(F->a_tau, &dt, &ct);
+      mt_constants(rec->a_sigma, &ds, &cs);
+      mt_constants(rec->a_tau, &dt, &ct);
       s_c[0] = ds; s_c[1] = cs; s_c[2] = dt; s_c[3] = ct;
-      s_c[4] = sqrt(F->x0_var);
+      s_c[4] = sqrt(rec->x0_var);
     }
     __syncthreads();
     const StateV<R> st = a.st[0];
-    const R x0m = (R)F->x0_mean;
+    const R x0m = (R)rec->x0_mean;
     const R sdx = (R)s_c[4];
-    const auto bs0 = SuffOps<R>::from_prior(F->b_sigma);
-    const auto bt0 = SuffOps<R>::from_prior(F->b_tau);
+    const auto bs0 = SuffOps<R>::from_prior(rec->b_sigma);
+    const auto bt0 = SuffOps<R>::from_prior(rec->b_tau);
     bool fail = false;
     for (uint64_t j = threadIdx.x; j < n; j += BB) {
       const uint64_t g = off + j;
@@ -522,8 +701,8 @@ __global__ void __launch_bounds__(BB) k_batch_init(BatchArgs<R> a) {
       st.bs[g] = bs0;
       st.bt[g] = bt0;
       if (!learn) {
-        st.s2[g] = (R)F->sigma2;
-        st.t2[g] = (R)F->tau2;
+        st.s2[g] = (R)rec->sigma2;
+        st.t2[g] = (R)rec->tau2;
         continue;
       }
       const R Gs = gamma_mt<R>((R)s_c[0], (R)s_c[1], seed, fid, 0, (uint32_t)j, P_INIT_SIGMA, &fail);

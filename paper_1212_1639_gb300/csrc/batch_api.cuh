@@ -9,8 +9,9 @@
 #pragma once
 #include <algorithm>
 #include <map>
+#include <set>
 
-#include "batch.cuh"
+#include "batch_launch.h"
 
 struct pf_batch {
   int scheme = 0;          // as configured (cut-point variants give the same ancestors)
@@ -42,12 +43,28 @@ struct pf_batch {
   uint32_t ring = 0;
   double* est_dev = nullptr;
   double* est_pin = nullptr;
+  // admission lists (slot + record per admitted filter), a ring of pinned
+  // staging buffers so that admitting never waits for cycles in flight
+  static constexpr int kAdm = 4;
+  char* adm_dev[kAdm] = {};
+  char* adm_pin[kAdm] = {};
+  cudaEvent_t adm_ev[kAdm] = {};
+  uint32_t adm_ring = 0;
   cudaGraphExec_t exec[kRing] = {};
   unsigned grid = 0;                 // persistent grid of the cycle kernel
   int nt = 256;                      // its threads per CTA
+  int cl = 1;                        // CTAs per cluster (1: no clusters)
+  uint32_t big_min = 0;              // cluster launches: filters this large use a whole cluster
   bool autotune = false, tuned = false;
-  std::vector<std::pair<int, unsigned>> shapes;  // (threads per CTA, grid) candidates
+  struct Shape {
+    int nt;
+    unsigned grid;
+    int cl;
+    uint32_t big_min;
+  };
+  std::vector<Shape> shapes;         // candidates of the autotuner
   std::vector<uint32_t> order;       // resident slots, largest filter first
+  std::set<uint32_t> free_slots;
   std::map<uint64_t, uint64_t> free_ranges;  // pool offset -> length (particles)
   uint64_t used = 0;                 // particles of resident filters (rounded)
   uint32_t resident = 0;
@@ -107,6 +124,7 @@ BatchArgs<R> batch_args(pf_batch* b) {
   a.count = nullptr;
   a.ctr = b->ctr;
   a.est = b->est_dev;
+  a.inits = nullptr;
   a.commit = 1;
   return a;
 }
@@ -120,57 +138,65 @@ void set_list(BatchArgs<double>& a, const char* list) {
   a.items = (const BatchItem*)(list + 16);
 }
 
-// The cycle kernel for a precision, resampling positions and block size.
-typedef void (*BatchKernelF)(BatchArgs<float>);
-typedef void (*BatchKernelD)(BatchArgs<double>);
-template <class R> struct BatchKernelT;
-template <> struct BatchKernelT<float> { typedef BatchKernelF F; };
-template <> struct BatchKernelT<double> { typedef BatchKernelD F; };
-
-template <class R>
-typename BatchKernelT<R>::F batch_kernel(int pos, int nt) {
-  if (pos == POS_SYSTEMATIC)
-    return nt == 512 ? k_batch_cycle<R, POS_SYSTEMATIC, 512> : k_batch_cycle<R, POS_SYSTEMATIC, 256>;
-  return nt == 512 ? k_batch_cycle<R, POS_MULTINOMIAL, 512> : k_batch_cycle<R, POS_MULTINOMIAL, 256>;
-}
-
 // Launch the cycle kernel for the list at `list` (device) with the batch's
 // current launch shape.
 pf_status launch_batch_cycle(pf_batch* b, const char* list, int commit, cudaStream_t s) {
+  cudaError_t e;
   if (b->fp64) {
     BatchArgs<double> a = batch_args<double>(b);
     set_list(a, list);
     a.commit = commit;
-    batch_kernel<double>(b->pos, b->nt)<<<b->grid, b->nt, 0, s>>>(a);
+    e = batch_cycle_launch<double>(b->pos, b->nt, b->cl, b->grid, a, s);
   } else {
     BatchArgs<float> a = batch_args<float>(b);
     set_list(a, list);
     a.commit = commit;
-    batch_kernel<float>(b->pos, b->nt)<<<b->grid, b->nt, 0, s>>>(a);
+    e = batch_cycle_launch<float>(b->pos, b->nt, b->cl, b->grid, a, s);
   }
-  CK(cudaGetLastError());
+  if (e != cudaSuccess) return set_err(PF_ERR_CUDA, "batch cycle launch: %s", cudaGetErrorString(e));
   return PF_OK;
 }
 
-// Candidate launch shapes: 256 or 512 threads per CTA, 1 .. the resident
-// maximum of CTAs per SM.  The first is the default before tuning (256
-// threads, as many CTAs as fit).
+unsigned resident_grid(const pf_batch* b, int nt, int cl, int sms) {
+  return b->fp64 ? batch_cycle_resident<double>(b->pos, nt, cl, sms)
+                 : batch_cycle_resident<float>(b->pos, nt, cl, sms);
+}
+
+// Candidate launch shapes: 256 or 512 threads per CTA with 1 .. the resident
+// maximum of CTAs per SM; and clusters of 2, 4 or 8 CTAs of 256 threads (as
+// many as fit) that take filters of at least 1 or 4 tiles per CTA together.
+// The first is the default before tuning (256 threads, as many CTAs as fit,
+// no clusters).
 pf_status batch_shapes(pf_batch* b) {
   int dev = 0, sms = 0;
   CK(cudaGetDevice(&dev));
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  if (sms < 1) return set_err(PF_ERR_CUDA, "no multiprocessors");
   b->shapes.clear();
   for (int nt : {256, 512}) {
-    int per_sm = 0;
-    cudaError_t e = b->fp64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<double>(b->pos, nt), nt, 0)
-                            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<float>(b->pos, nt), nt, 0);
-    if (e != cudaSuccess) return set_err(PF_ERR_CUDA, "occupancy query: %s", cudaGetErrorString(e));
-    for (int k = per_sm; k >= 1; --k) b->shapes.push_back({nt, (unsigned)(k * sms)});
+    const unsigned g = resident_grid(b, nt, 1, sms);
+    for (unsigned k = g / (unsigned)sms; k >= 1; --k) b->shapes.push_back({nt, k * (unsigned)sms, 1, 0});
   }
-  if (b->shapes.empty() || sms < 1) return set_err(PF_ERR_CUDA, "no launch shape fits");
-  b->nt = b->shapes[0].first;
-  b->grid = b->shapes[0].second;
+  for (int cl : {2, 4, 8}) {
+    const unsigned g = resident_grid(b, 256, cl, sms);
+    if (g == 0) continue;
+    for (uint32_t tiles : {1u, 4u}) b->shapes.push_back({256, g, cl, tiles * (uint32_t)cl * (uint32_t)TILE});
+  }
+  if (b->shapes.empty()) return set_err(PF_ERR_CUDA, "no launch shape fits");
+  b->nt = b->shapes[0].nt;
+  b->grid = b->shapes[0].grid;
+  b->cl = b->shapes[0].cl;
+  b->big_min = b->shapes[0].big_min;
   return PF_OK;
+}
+
+// Number of leading items of a size-ordered list that a cluster launch gives
+// to whole clusters.
+uint32_t big_items(const pf_batch* b, const BatchItem* items, uint32_t cnt) {
+  if (b->cl == 1) return 0;
+  uint32_t k = 0;
+  while (k < cnt && b->Fh[items[k].slot].n >= b->big_min) ++k;
+  return k;
 }
 
 pf_status check_batch(pf_batch* b) {
@@ -236,6 +262,91 @@ bool larger_first(const pf_batch* b, uint32_t a, uint32_t c) {
   return a < c;
 }
 
+// Reserve the lowest free slot and a pool range for one filter and record it
+// on the host; false (nothing changed) when either is missing.
+bool batch_reserve(pf_batch* b, const pf_config& c, uint32_t* slot_out) {
+  if (b->free_slots.empty()) {
+    set_err(PF_ERR_BUSY, "no free slot (%u of %u in use)", b->resident, b->max_filters);
+    return false;
+  }
+  const uint64_t len = round_pool(c.n_particles);
+  uint64_t off = 0;
+  if (!pool_take(b, len, &off)) {
+    set_err(PF_ERR_BUSY, "particle pool full: %llu particles requested, %llu of %llu in use",
+            (unsigned long long)c.n_particles, (unsigned long long)b->used,
+            (unsigned long long)b->pool);
+    return false;
+  }
+  const uint32_t slot = *b->free_slots.begin();
+  b->free_slots.erase(b->free_slots.begin());
+  BatchFilter f;
+  std::memset(&f, 0, sizeof(f));
+  f.off = off;
+  f.seed = c.seed;
+  f.n = (uint32_t)c.n_particles;
+  f.filter_id = c.filter_id;
+  f.k = cdf_shift(c.n_particles);
+  f.learn = c.known_variances ? 0u : 1u;
+  f.x0_mean = c.x0_mean; f.x0_var = c.x0_var;
+  f.a_sigma = c.a_sigma; f.b_sigma = c.b_sigma;
+  f.a_tau = c.a_tau; f.b_tau = c.b_tau;
+  f.sigma2 = c.sigma2; f.tau2 = c.tau2;
+  b->Fh[slot] = f;
+  b->used += len;
+  b->resident++;
+  b->order.insert(std::lower_bound(b->order.begin(), b->order.end(), slot,
+                                   [&](uint32_t a2, uint32_t c2) { return larger_first(b, a2, c2); }),
+                  slot);
+  *slot_out = slot;
+  return true;
+}
+
+// Undo batch_reserve (host bookkeeping only; device work enqueued later on
+// the batch's stream is what reuses the range).
+void batch_release(pf_batch* b, uint32_t slot) {
+  const uint64_t len = round_pool(b->Fh[slot].n);
+  pool_give(b, b->Fh[slot].off, len);
+  b->used -= len;
+  b->resident--;
+  b->order.erase(std::find(b->order.begin(), b->order.end(), slot));
+  std::memset(&b->Fh[slot], 0, sizeof(BatchFilter));
+  b->free_slots.insert(slot);
+}
+
+// One admission list for the reserved slots: their records and one init
+// launch.  Waits only for the copy made from the same staging buffer
+// pf_batch::kAdm admissions ago.
+pf_status batch_init_slots(pf_batch* b, const uint32_t* slots, uint32_t cnt) {
+  if (cnt == 0) return PF_OK;
+  const uint32_t ar = b->adm_ring;
+  CK(cudaEventSynchronize(b->adm_ev[ar]));
+  BatchInit* inits = (BatchInit*)(b->adm_pin[ar] + 16);
+  for (uint32_t i = 0; i < cnt; ++i) {
+    std::memset(&inits[i], 0, sizeof(BatchInit));
+    inits[i].slot = slots[i];
+    inits[i].rec = b->Fh[slots[i]];
+  }
+  *(uint32_t*)b->adm_pin[ar] = cnt;
+  CK(cudaMemcpyAsync(b->adm_dev[ar], b->adm_pin[ar], 16 + (size_t)cnt * sizeof(BatchInit),
+                     cudaMemcpyHostToDevice, b->stream));
+  CK(cudaEventRecord(b->adm_ev[ar], b->stream));
+  b->adm_ring = (ar + 1) % pf_batch::kAdm;
+  const unsigned grid = (unsigned)std::min<uint64_t>(cnt, 4096);
+  if (b->fp64) {
+    BatchArgs<double> a = batch_args<double>(b);
+    a.count = (const uint32_t*)b->adm_dev[ar];
+    a.inits = (const BatchInit*)(b->adm_dev[ar] + 16);
+    CK(batch_init_launch<double>(grid, a, b->stream));
+  } else {
+    BatchArgs<float> a = batch_args<float>(b);
+    a.count = (const uint32_t*)b->adm_dev[ar];
+    a.inits = (const BatchInit*)(b->adm_dev[ar] + 16);
+    CK(batch_init_launch<float>(grid, a, b->stream));
+  }
+  CK(cudaGetLastError());
+  return PF_OK;
+}
+
 // Admit the filters cfgs[0..cnt) into free slots and enqueue their
 // initialisation.  All or nothing: on PF_ERR_BUSY nothing is admitted.
 pf_status batch_admit(pf_batch* b, const pf_config* cfgs, uint32_t cnt, uint32_t* slots) {
@@ -243,78 +354,18 @@ pf_status batch_admit(pf_batch* b, const pf_config* cfgs, uint32_t cnt, uint32_t
     pf_status st = validate_member(b, &cfgs[i]);
     if (st != PF_OK) return st;
   }
-  if (b->resident + cnt > b->max_filters)
-    return set_err(PF_ERR_BUSY, "no free slot (%u of %u in use)", b->resident, b->max_filters);
-  std::vector<std::pair<uint64_t, uint64_t>> taken;
   std::vector<uint32_t> got;
-  uint32_t next_slot = 0;
-  pf_status st = PF_OK;
-  for (uint32_t i = 0; i < cnt && st == PF_OK; ++i) {
-    const uint64_t len = round_pool(cfgs[i].n_particles);
-    uint64_t off = 0;
-    if (!pool_take(b, len, &off)) {
-      st = set_err(PF_ERR_BUSY, "particle pool full: %llu particles requested, %llu of %llu in use",
-                   (unsigned long long)cfgs[i].n_particles, (unsigned long long)b->used,
-                   (unsigned long long)b->pool);
-      break;
-    }
-    taken.push_back({off, len});
-    while (b->Fh[next_slot].n != 0 ||
-           std::find(got.begin(), got.end(), next_slot) != got.end())
-      ++next_slot;
-    got.push_back(next_slot);
-  }
-  if (st != PF_OK) {
-    for (auto& r : taken) pool_give(b, r.first, r.second);
-    return st;
-  }
-  // the slots' records, then the init list
-  BatchItem* items = (BatchItem*)(b->list_pin[pf_batch::kRing] + 16);
+  got.reserve(cnt);
   for (uint32_t i = 0; i < cnt; ++i) {
-    const pf_config& c = cfgs[i];
-    BatchFilter f;
-    std::memset(&f, 0, sizeof(f));
-    f.off = taken[i].first;
-    f.seed = c.seed;
-    f.n = (uint32_t)c.n_particles;
-    f.filter_id = c.filter_id;
-    f.k = cdf_shift(c.n_particles);
-    f.learn = c.known_variances ? 0u : 1u;
-    f.x0_mean = c.x0_mean; f.x0_var = c.x0_var;
-    f.a_sigma = c.a_sigma; f.b_sigma = c.b_sigma;
-    f.a_tau = c.a_tau; f.b_tau = c.b_tau;
-    f.sigma2 = c.sigma2; f.tau2 = c.tau2;
-    b->Fh[got[i]] = f;
-    b->used += taken[i].second;
-    b->resident++;
-    items[i].slot = got[i];
-    items[i].pad = 0;
-    items[i].y = 0.0;
-    b->order.insert(std::lower_bound(b->order.begin(), b->order.end(), got[i],
-                                     [&](uint32_t a2, uint32_t c2) { return larger_first(b, a2, c2); }),
-                    got[i]);
-    if (slots) slots[i] = got[i];
+    uint32_t slot = 0;
+    if (!batch_reserve(b, cfgs[i], &slot)) {
+      for (uint32_t s2 : got) batch_release(b, s2);
+      return PF_ERR_BUSY;
+    }
+    got.push_back(slot);
   }
-  *(uint32_t*)b->list_pin[pf_batch::kRing] = cnt;
-  // the records go up one by one (slots need not be contiguous); the
-  // pinned list buffer is reused only after this synchronisation
-  for (uint32_t i = 0; i < cnt; ++i)
-    CK(cudaMemcpyAsync(b->F + got[i], &b->Fh[got[i]], sizeof(BatchFilter), cudaMemcpyHostToDevice, b->stream));
-  CK(cudaMemcpyAsync(b->list_dev[pf_batch::kRing], b->list_pin[pf_batch::kRing], 16 + (size_t)cnt * sizeof(BatchItem),
-                     cudaMemcpyHostToDevice, b->stream));
-  const unsigned grid = (unsigned)std::min<uint64_t>(cnt, 4096);
-  if (b->fp64) {
-    BatchArgs<double> a = batch_args<double>(b);
-    set_list(a, b->list_dev[pf_batch::kRing]);
-    k_batch_init<double><<<grid, BB, 0, b->stream>>>(a);
-  } else {
-    BatchArgs<float> a = batch_args<float>(b);
-    set_list(a, b->list_dev[pf_batch::kRing]);
-    k_batch_init<float><<<grid, BB, 0, b->stream>>>(a);
-  }
-  CK(cudaGetLastError());
-  CK(cudaStreamSynchronize(b->stream));
-  return PF_OK;
+  if (slots) std::copy(got.begin(), got.end(), slots);
+  return batch_init_slots(b, got.data(), cnt);
 }
 
 pf_status batch_build_graphs(pf_batch* b) {
@@ -432,12 +483,23 @@ pf_status pf_batch_create(const pf_config* cfgs, uint32_t n, const pf_batch_opts
   for (int r = 0; r < pf_batch::kRing; ++r)
     if (cudaEventCreateWithFlags(&b->list_ev[r], cudaEventDisableTiming) != cudaSuccess)
       return bail(set_err(PF_ERR_CUDA, "cudaEventCreate failed"));
+  for (int r = 0; r < pf_batch::kAdm; ++r) {
+    const size_t ab = 16 + (size_t)maxf * sizeof(BatchInit);
+    if ((st = batch_alloc(b, ab, (void**)&b->adm_dev[r])) != PF_OK) return bail(st);
+    if (cudaHostAlloc((void**)&b->adm_pin[r], ab, cudaHostAllocDefault) != cudaSuccess) {
+      cudaGetLastError();
+      return bail(set_err(PF_ERR_OOM, "pinned host allocation failed"));
+    }
+    if (cudaEventCreateWithFlags(&b->adm_ev[r], cudaEventDisableTiming) != cudaSuccess)
+      return bail(set_err(PF_ERR_CUDA, "cudaEventCreate failed"));
+  }
   if (cudaMemsetAsync(b->ctr, 0, 256, b->stream) != cudaSuccess ||
       cudaMemsetAsync(b->F, 0, (size_t)maxf * sizeof(BatchFilter), b->stream) != cudaSuccess)
     return bail(set_err(PF_ERR_CUDA, "batch memset failed"));
   b->Fh.assign(maxf, BatchFilter());
   std::memset(b->Fh.data(), 0, (size_t)maxf * sizeof(BatchFilter));
   b->free_ranges[0] = pool;
+  for (uint32_t i = 0; i < maxf; ++i) b->free_slots.insert(b->free_slots.end(), i);
   b->autotune = opts->autotune != 0;
   if ((st = batch_shapes(b)) != PF_OK) return bail(st);
   if (n && (st = batch_admit(b, cfgs, n, nullptr)) != PF_OK) return bail(st);
@@ -459,11 +521,7 @@ pf_status pf_batch_remove(pf_batch* b, uint32_t slot) {
   if (st != PF_OK) return st;
   if (slot >= b->max_filters || b->Fh[slot].n == 0) return set_err(PF_ERR_INVALID, "slot %u is not in use", slot);
   // the slot's range is reused only by later work on the same stream
-  pool_give(b, b->Fh[slot].off, round_pool(b->Fh[slot].n));
-  b->used -= round_pool(b->Fh[slot].n);
-  b->resident--;
-  b->order.erase(std::find(b->order.begin(), b->order.end(), slot));
-  std::memset(&b->Fh[slot], 0, sizeof(BatchFilter));
+  batch_release(b, slot);
   return PF_OK;
 }
 
@@ -487,7 +545,8 @@ pf_status stage_cycle_list(pf_batch* b, uint32_t r, const double* y, const uint8
   }
   *cnt_out = cnt;
   if (cnt == 0) return PF_OK;
-  *(uint32_t*)b->list_pin[r] = cnt;
+  ((uint32_t*)b->list_pin[r])[0] = cnt;
+  ((uint32_t*)b->list_pin[r])[1] = big_items(b, items, cnt);
   CK(cudaMemcpyAsync(b->list_dev[r], b->list_pin[r], 16 + (size_t)cnt * sizeof(BatchItem),
                      cudaMemcpyHostToDevice, b->stream));
   CK(cudaEventRecord(b->list_ev[r], b->stream));
@@ -507,9 +566,20 @@ pf_status batch_tune_list(pf_batch* b, uint32_t r, pf_batch_tuning* out) {
   size_t best_i = 0;
   pf_status st = PF_OK;
   std::vector<float> ms(b->shapes.size(), 0.0f);
+  // the list's large-item count depends on the shape: rewrite it per shape
+  BatchItem* items = (BatchItem*)(b->list_pin[r] + 16);
+  const uint32_t cnt = ((uint32_t*)b->list_pin[r])[0];
   for (size_t i = 0; i < b->shapes.size() && st == PF_OK; ++i) {
-    b->nt = b->shapes[i].first;
-    b->grid = b->shapes[i].second;
+    b->nt = b->shapes[i].nt;
+    b->grid = b->shapes[i].grid;
+    b->cl = b->shapes[i].cl;
+    b->big_min = b->shapes[i].big_min;
+    if (i > 0) {
+      CK(cudaEventSynchronize(b->list_ev[r]));
+      ((uint32_t*)b->list_pin[r])[1] = big_items(b, items, cnt);
+      CK(cudaMemcpyAsync(b->list_dev[r], b->list_pin[r], 16, cudaMemcpyHostToDevice, b->stream));
+      CK(cudaEventRecord(b->list_ev[r], b->stream));
+    }
     st = launch_batch_cycle(b, b->list_dev[r], 0, b->stream);  // warm-up
     if (st == PF_OK) cudaEventRecord(e0, b->stream);
     for (int k = 0; k < reps && st == PF_OK; ++k) st = launch_batch_cycle(b, b->list_dev[r], 0, b->stream);
@@ -530,16 +600,25 @@ pf_status batch_tune_list(pf_batch* b, uint32_t r, pf_batch_tuning* out) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (st != PF_OK) return st;
-  b->nt = b->shapes[best_i].first;
-  b->grid = b->shapes[best_i].second;
+  b->nt = b->shapes[best_i].nt;
+  b->grid = b->shapes[best_i].grid;
+  b->cl = b->shapes[best_i].cl;
+  b->big_min = b->shapes[best_i].big_min;
   b->tuned = true;
+  // the staged list is about to run with the kept shape
+  CK(cudaEventSynchronize(b->list_ev[r]));
+  ((uint32_t*)b->list_pin[r])[1] = big_items(b, items, cnt);
+  CK(cudaMemcpyAsync(b->list_dev[r], b->list_pin[r], 16, cudaMemcpyHostToDevice, b->stream));
+  CK(cudaEventRecord(b->list_ev[r], b->stream));
   if (out) {
     std::memset(out, 0, sizeof(*out));
     const size_t m = std::min<size_t>(b->shapes.size(), PF_BATCH_MAX_SHAPES);
     out->n_shapes = (uint32_t)m;
     for (size_t i = 0; i < m; ++i) {
-      out->block[i] = (uint32_t)b->shapes[i].first;
-      out->grid[i] = b->shapes[i].second;
+      out->block[i] = (uint32_t)b->shapes[i].nt;
+      out->grid[i] = b->shapes[i].grid;
+      out->cluster[i] = (uint32_t)b->shapes[i].cl;
+      out->big_min[i] = b->shapes[i].big_min;
       out->ms[i] = ms[i];
     }
     out->chosen = (uint32_t)best_i;
@@ -563,17 +642,24 @@ pf_status pf_batch_tune(pf_batch* b, const double* y, const uint8_t* mask, pf_ba
   return batch_fail(b, batch_tune_list(b, r, out));
 }
 
-pf_status pf_batch_set_shape(pf_batch* b, uint32_t block, uint32_t grid) {
+pf_status pf_batch_set_shape(pf_batch* b, uint32_t block, uint32_t grid, uint32_t cluster,
+                             uint32_t big_min) {
   pf_status st = check_batch(b);
   if (st != PF_OK) return st;
-  if (block != 256 && block != 512) return set_err(PF_ERR_INVALID, "block must be 256 or 512");
-  unsigned cap = 0;
+  if (cluster == 0) cluster = 1;
+  const pf_batch::Shape* fit = nullptr;
   for (auto& sh : b->shapes)
-    if (sh.first == (int)block) cap = std::max(cap, sh.second);
-  if (grid < 1 || grid > cap) return set_err(PF_ERR_INVALID, "grid must be in [1, %u] for block %u", cap, block);
+    if (sh.nt == (int)block && sh.cl == (int)cluster && (!fit || sh.grid > fit->grid)) fit = &sh;
+  if (!fit)
+    return set_err(PF_ERR_INVALID, "unsupported shape: block %u, cluster %u (256 or 512 threads "
+                   "without clusters, 256 threads with clusters of 2, 4 or 8)", block, cluster);
+  if (grid < cluster || grid > fit->grid || grid % cluster != 0)
+    return set_err(PF_ERR_INVALID, "grid must be a multiple of %u in [%u, %u]", cluster, cluster, fit->grid);
   CK(cudaStreamSynchronize(b->stream));
   b->nt = (int)block;
   b->grid = grid;
+  b->cl = (int)cluster;
+  b->big_min = cluster > 1 ? big_min : 0;
   b->tuned = true;
   return batch_fail(b, batch_build_graphs(b));
 }
@@ -627,16 +713,16 @@ pf_status pf_batch_estimate(pf_batch* b, const uint8_t* mask, pf_estimates* out)
   CK(cudaMemcpyAsync(b->list_dev[pf_batch::kRing], lp, 16 + (size_t)cnt * sizeof(BatchItem),
                      cudaMemcpyHostToDevice, b->stream));
   const unsigned grid = (unsigned)std::min<uint64_t>(cnt, b->grid);
+  cudaError_t e;
   if (b->fp64) {
     BatchArgs<double> a = batch_args<double>(b);
     set_list(a, b->list_dev[pf_batch::kRing]);
-    k_batch_estimate<double><<<grid, BB, 0, b->stream>>>(a);
+    e = batch_estimate_launch<double>(grid, a, b->stream);
   } else {
     BatchArgs<float> a = batch_args<float>(b);
     set_list(a, b->list_dev[pf_batch::kRing]);
-    k_batch_estimate<float><<<grid, BB, 0, b->stream>>>(a);
+    e = batch_estimate_launch<float>(grid, a, b->stream);
   }
-  cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(b->est_pin, b->est_dev, (size_t)cnt * BATCH_EST_ROW * 8, cudaMemcpyDeviceToHost, b->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
@@ -705,6 +791,8 @@ pf_status pf_batch_get_info(pf_batch* b, pf_batch_info* out) {
   out->pool_bytes = b->pool * b->bytes_per_particle;
   out->grid = b->grid;
   out->block = (uint32_t)b->nt;
+  out->cluster = (uint32_t)b->cl;
+  out->big_min = b->big_min;
   out->tuned = b->tuned ? 1u : 0u;
   out->cycles = b->cycles;
   return PF_OK;
@@ -724,6 +812,10 @@ pf_status pf_batch_destroy(pf_batch* b) {
   if (b->stream) cudaStreamSynchronize(b->stream);
   for (int r = 0; r <= pf_batch::kRing; ++r)
     if (b->list_pin[r]) cudaFreeHost(b->list_pin[r]);
+  for (int r = 0; r < pf_batch::kAdm; ++r) {
+    if (b->adm_pin[r]) cudaFreeHost(b->adm_pin[r]);
+    if (b->adm_ev[r]) cudaEventDestroy(b->adm_ev[r]);
+  }
   if (b->est_pin) cudaFreeHost(b->est_pin);
   if (b->own_stream) cudaStreamDestroy(b->stream);
   cudaGetLastError();

@@ -604,7 +604,7 @@ struct SpacingArgs {
   uint32_t filter;
 };
 
-__global__ void __launch_bounds__(BLOCK, 3) k_spacing_scan(SpacingArgs a) {
+static __global__ void __launch_bounds__(BLOCK, 3) k_spacing_scan(SpacingArgs a) {
   __shared__ uint32_t s_tile;
   __shared__ uint64_t s_warp_tot[WARPS];
   __shared__ uint64_t s_excl;
@@ -915,7 +915,7 @@ __device__ __forceinline__ uint64_t sys_first_slot(uint64_t Qi, uint64_t n, uint
   return q < n ? q : n;
 }
 
-__global__ void __launch_bounds__(SYS_THREADS) k_merge_sys(PosArgs a, const uint64_t* splits) {
+static __global__ void __launch_bounds__(SYS_THREADS) k_merge_sys(PosArgs a, const uint64_t* splits) {
   __shared__ uint32_t s_anc[SYS_D];
   __shared__ uint32_t s_run[SYS_MAX_RUNS][3];
   __shared__ uint32_t s_nruns;
@@ -1001,7 +1001,7 @@ __device__ __forceinline__ uint64_t ceil_nq_over_t(uint64_t n, uint64_t q, uint6
   return (p.hi == X.hi && p.lo == X.lo) ? f : f + 1;
 }
 
-__global__ void __launch_bounds__(BLOCK) k_cutpoint_search(const uint64_t* Q, uint64_t n,
+static __global__ void __launch_bounds__(BLOCK) k_cutpoint_search(const uint64_t* Q, uint64_t n,
                                                            uint32_t* I) {
   const uint64_t i = (uint64_t)blockIdx.x * BLOCK + threadIdx.x;
   if (i >= n) return;
@@ -1039,7 +1039,7 @@ __global__ void __launch_bounds__(BLOCK) k_cutpoint_method(PosArgs a) {
 }
 
 // Explicit integer positions U_j in [0, T) (A = 1).
-__global__ void __launch_bounds__(BLOCK) k_cutpoint_method_explicit(
+static __global__ void __launch_bounds__(BLOCK) k_cutpoint_method_explicit(
     const uint64_t* Q, uint64_t n, const uint32_t* I, const uint64_t* U, uint64_t m,
     uint32_t* anc) {
   const uint64_t j = (uint64_t)blockIdx.x * BLOCK + threadIdx.x;
@@ -1337,7 +1337,7 @@ __global__ void __launch_bounds__(BLOCK) k_estimate(FilterArgs<R> a) {
 
 // Maximum of binary32 input weights (pf_resample): non-negative floats order
 // as their bit patterns.
-__global__ void __launch_bounds__(BLOCK) k_wmax(const float* w, uint64_t n, Ctl* ctl) {
+static __global__ void __launch_bounds__(BLOCK) k_wmax(const float* w, uint64_t n, Ctl* ctl) {
   __shared__ uint32_t s_red[WARPS];
   uint32_t mx = 0;
   bool bad = false;

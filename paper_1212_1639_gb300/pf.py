@@ -63,7 +63,8 @@ BATCH_MAX_SHAPES = 16
 
 class PfBatchTuning(C.Structure):
     _fields_ = [("n_shapes", C.c_uint32), ("block", C.c_uint32 * BATCH_MAX_SHAPES),
-                ("grid", C.c_uint32 * BATCH_MAX_SHAPES), ("ms", C.c_float * BATCH_MAX_SHAPES),
+                ("grid", C.c_uint32 * BATCH_MAX_SHAPES), ("cluster", C.c_uint32 * BATCH_MAX_SHAPES),
+                ("big_min", C.c_uint32 * BATCH_MAX_SHAPES), ("ms", C.c_float * BATCH_MAX_SHAPES),
                 ("chosen", C.c_uint32)]
 
 
@@ -71,9 +72,41 @@ class PfBatchInfo(C.Structure):
     _fields_ = [("max_filters", C.c_uint32), ("resident", C.c_uint32),
                 ("pool_particles", C.c_uint64), ("used_particles", C.c_uint64),
                 ("bytes_per_particle", C.c_uint64), ("pool_bytes", C.c_uint64),
-                ("grid", C.c_uint32), ("block", C.c_uint32), ("tuned", C.c_uint32),
-                ("cycles", C.c_uint64)]
+                ("grid", C.c_uint32), ("block", C.c_uint32), ("cluster", C.c_uint32),
+                ("big_min", C.c_uint32), ("tuned", C.c_uint32), ("cycles", C.c_uint64)]
 
+
+class PfServerOpts(C.Structure):
+    _fields_ = [("max_streams", C.c_uint32), ("hbm_budget_bytes", C.c_uint64),
+                ("scheme", C.c_int32), ("precision", C.c_int32),
+                ("max_inflight", C.c_uint32), ("keep_results", C.c_int32),
+                ("block", C.c_uint32), ("grid", C.c_uint32),
+                ("cluster", C.c_uint32), ("big_min", C.c_uint32),
+                ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN),
+                ("alloc_ctx", C.c_void_p)]
+
+
+class PfServerResult(C.Structure):
+    _fields_ = [("stream_id", C.c_uint64), ("seq", C.c_uint64), ("est", PfEstimates),
+                ("latency_us", C.c_float), ("status", C.c_int32)]
+
+
+class PfServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64),
+                ("cycles", C.c_uint64), ("particle_steps", C.c_uint64),
+                ("streams_opened", C.c_uint64), ("streams_closed", C.c_uint64),
+                ("admitted", C.c_uint64), ("admitted_after_wait", C.c_uint64),
+                ("waiting", C.c_uint32), ("resident", C.c_uint32),
+                ("pool_particles", C.c_uint64), ("used_particles", C.c_uint64),
+                ("mean_cycle_streams", C.c_double), ("max_cycle_streams", C.c_uint32),
+                ("mean_admission_wait_us", C.c_double), ("replay_max_lag_us", C.c_double),
+                ("wall_s", C.c_double), ("particle_steps_per_s", C.c_double),
+                ("obs_per_s", C.c_double), ("mean_us", C.c_double), ("p50_us", C.c_double),
+                ("p90_us", C.c_double), ("p99_us", C.c_double), ("max_us", C.c_double),
+                ("grid", C.c_uint32), ("block", C.c_uint32), ("cluster", C.c_uint32)]
+
+
+EVENT_OBS, EVENT_CLOSE, EVENT_OPEN = 0, 1, 2
 
 _V = C.c_void_p
 _SIGS = {
@@ -99,12 +132,21 @@ _SIGS = {
     "pf_batch_step": [_V, _V, _V],
     "pf_batch_estimate": [_V, _V, C.POINTER(PfEstimates)],
     "pf_batch_tune": [_V, _V, _V, C.POINTER(PfBatchTuning)],
-    "pf_batch_set_shape": [_V, C.c_uint32, C.c_uint32],
+    "pf_batch_set_shape": [_V, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32],
     "pf_batch_sync": [_V],
     "pf_batch_get_particles": [_V, C.c_uint32, _V, _V, _V, _V, _V],
     "pf_batch_get_ancestors": [_V, C.c_uint32, _V, _V],
     "pf_batch_get_info": [_V, C.POINTER(PfBatchInfo)],
     "pf_batch_destroy": [_V],
+    "pf_server_create": [C.POINTER(PfServerOpts), C.POINTER(_V)],
+    "pf_server_open": [_V, C.c_uint64, C.POINTER(PfConfig)],
+    "pf_server_submit": [_V, C.c_uint64, C.c_double],
+    "pf_server_close": [_V, C.c_uint64],
+    "pf_server_replay": [_V, C.c_uint64, _V, _V, _V, _V, _V, C.c_uint64],
+    "pf_server_drain": [_V, C.c_double],
+    "pf_server_poll": [_V, C.POINTER(PfServerResult), C.c_uint32, C.POINTER(C.c_uint32)],
+    "pf_server_get_stats": [_V, C.POINTER(PfServerStats)],
+    "pf_server_destroy": [_V],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -361,11 +403,13 @@ class Batch:
         out = PfBatchTuning()
         _check(_lib.pf_batch_tune(self.h, y.ctypes.data_as(C.c_void_p), mp, C.byref(out)),
                "pf_batch_tune")
-        shapes = [(out.block[i], out.grid[i], out.ms[i]) for i in range(out.n_shapes)]
+        shapes = [dict(block=out.block[i], grid=out.grid[i], cluster=out.cluster[i],
+                       big_min=out.big_min[i], ms=out.ms[i]) for i in range(out.n_shapes)]
         return shapes, out.chosen
 
-    def set_shape(self, block, grid):
-        _check(_lib.pf_batch_set_shape(self.h, int(block), int(grid)), "pf_batch_set_shape")
+    def set_shape(self, block, grid, cluster=1, big_min=0):
+        _check(_lib.pf_batch_set_shape(self.h, int(block), int(grid), int(cluster), int(big_min)),
+               "pf_batch_set_shape")
 
     def estimates(self, mask=None):
         """{slot: summaries dict} for the selected resident filters."""
@@ -407,6 +451,98 @@ class Batch:
     def close(self):
         if getattr(self, "h", None):
             _lib.pf_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching server of filter streams (pf_server_*): streams
+    open, receive observations at any time and close; a library worker thread
+    batches the pending observations of all resident streams into batched
+    cycles; streams are admitted in FIFO order within an HBM budget."""
+
+    def __init__(self, max_streams, hbm_budget_bytes, scheme="systematic", precision="fp32",
+                 max_inflight=2, keep_results=False, block=0, grid=0, cluster=0, big_min=0,
+                 stream=None, torch_alloc=True):
+        torch = _torch()
+        self.scheme = SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
+        self.precision = FP64 if precision in ("fp64", FP64) else FP32
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        if self.stream.cuda_stream == 0:
+            raise ValueError("pass a non-default torch.cuda.Stream (cycles are graph-captured)")
+        self._alloc = TorchAllocator() if torch_alloc else None
+        opts = PfServerOpts(max_streams=int(max_streams), hbm_budget_bytes=int(hbm_budget_bytes),
+                            scheme=self.scheme, precision=self.precision,
+                            max_inflight=int(max_inflight), keep_results=int(bool(keep_results)),
+                            block=int(block), grid=int(grid), cluster=int(cluster),
+                            big_min=int(big_min), stream=C.c_void_p(self.stream.cuda_stream))
+        if self._alloc is not None:
+            opts.alloc = self._alloc.alloc
+            opts.free = self._alloc.free
+        self._opts = opts
+        h = C.c_void_p()
+        _check(_lib.pf_server_create(C.byref(opts), C.byref(h)), "pf_server_create")
+        self.h = h
+
+    def config(self, **f):
+        kw = dict(f)
+        kw["scheme"] = self.scheme
+        kw["precision"] = self.precision
+        return filter_config(**kw)
+
+    def open(self, stream_id, **f):
+        cfg = self.config(**f)
+        _check(_lib.pf_server_open(self.h, int(stream_id), C.byref(cfg)), "pf_server_open")
+
+    def submit(self, stream_id, y):
+        _check(_lib.pf_server_submit(self.h, int(stream_id), float(y)), "pf_server_submit")
+
+    def close_stream(self, stream_id):
+        _check(_lib.pf_server_close(self.h, int(stream_id)), "pf_server_close")
+
+    def replay(self, t_s, kind, ids, y, cfgs=()):
+        """Events at times t_s (seconds from now): kind EVENT_OBS (submit y to
+        ids), EVENT_CLOSE, EVENT_OPEN (with cfgs[id], a list of dicts)."""
+        t_s = np.ascontiguousarray(t_s, dtype=np.float64)
+        kind = np.ascontiguousarray(kind, dtype=np.uint8)
+        ids = np.ascontiguousarray(ids, dtype=np.uint64)
+        y = np.ascontiguousarray(y, dtype=np.float64)
+        arr = (PfConfig * max(len(cfgs), 1))(*[self.config(**c) for c in cfgs])
+        _check(_lib.pf_server_replay(self.h, t_s.size, t_s.ctypes.data_as(C.c_void_p),
+                                     kind.ctypes.data_as(C.c_void_p),
+                                     ids.ctypes.data_as(C.c_void_p), y.ctypes.data_as(C.c_void_p),
+                                     arr, len(cfgs)), "pf_server_replay")
+
+    def drain(self, timeout_s=600.0):
+        _check(_lib.pf_server_drain(self.h, float(timeout_s)), "pf_server_drain")
+
+    def poll(self, max_results=1 << 16):
+        """Finished results: list of (stream_id, seq, summaries dict, latency_us, status)."""
+        buf = (PfServerResult * max_results)()
+        out = []
+        while True:
+            n = C.c_uint32()
+            _check(_lib.pf_server_poll(self.h, buf, max_results, C.byref(n)), "pf_server_poll")
+            for i in range(n.value):
+                r = buf[i]
+                est = {f: getattr(r.est, f) for f, _ in PfEstimates._fields_}
+                out.append((r.stream_id, r.seq, est, r.latency_us, r.status))
+            if n.value < max_results:
+                return out
+
+    def stats(self):
+        st = PfServerStats()
+        _check(_lib.pf_server_get_stats(self.h, C.byref(st)), "pf_server_get_stats")
+        return {f: getattr(st, f) for f, _ in PfServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.pf_server_destroy(self.h)
             self.h = None
 
     def __del__(self):

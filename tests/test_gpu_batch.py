@@ -201,12 +201,21 @@ def test_batch_launch_shapes_change_no_result(pf, scheme):
     ref = pf.Batch(specs, scheme=scheme)
     shapes, chosen = ref.tune(np.array([y[0] for y in ys]))
     assert len(shapes) >= 2 and 0 <= chosen < len(shapes)
-    assert {b for b, _, _ in shapes} == {256, 512}
-    assert all(ms > 0 for _, _, ms in shapes)
+    assert {sh["block"] for sh in shapes} == {256, 512}
+    assert {sh["cluster"] for sh in shapes} >= {1, 2, 4, 8}
+    assert all(sh["ms"] > 0 for sh in shapes)
     others = []
-    for blk, grid, _ in shapes[:6]:
+    for sh in shapes:
         o = pf.Batch(specs, scheme=scheme)
-        o.set_shape(blk, max(1, grid // 7))   # fewer CTAs than filters, too
+        cl = sh["cluster"]
+        grid = max(cl, sh["grid"] // 7 // cl * cl)  # fewer CTAs than filters, too
+        o.set_shape(sh["block"], grid, cl, sh["big_min"])
+        others.append(o)
+    # clusters taking every filter of 1 or more particles, and filters of
+    # fewer tiles than CTAs in the cluster
+    for cl in (2, 8):
+        o = pf.Batch(specs, scheme=scheme)
+        o.set_shape(256, cl * 3, cl, 1)
         others.append(o)
     for t in range(T):
         y = np.array([ys[i][t] for i in range(len(specs))])

@@ -1,0 +1,139 @@
+"""Serving (pf_server_*): continuous batching of filter streams.
+
+Every observation's result (the stream's posterior summaries after it) must
+be exactly what a standalone filter of the stream's configuration gives
+after the same observations, whatever the interleaving with other streams,
+the composition of the batched cycles, the number of cycles in flight, or
+the time a stream waited for admission under the HBM budget.
+"""
+import time
+
+import numpy as np
+import pytest
+
+from paper_1212_1639_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _cfg(i, n):
+    return dict(n=n, seed=9000 + 31 * i, filter_id=100 + i)
+
+
+def _alone(pf, cfg, ys):
+    f = pf.Filter(cfg["n"], seed=cfg["seed"], filter_id=cfg["filter_id"], scheme="systematic",
+                  precision="fp32")
+    out = []
+    for y in ys:
+        f.step(y)
+        out.append(f.estimate())
+    f.close()
+    return out
+
+
+def _check_against_alone(pf, results, cfgs, series):
+    by = {}
+    for sid, seq, est, lat, status in results:
+        assert status == pf.PF_OK
+        assert lat > 0
+        by.setdefault(sid, {})[seq] = est
+    for sid, cfg in cfgs.items():
+        ys = series[sid]
+        got = by.get(sid, {})
+        assert sorted(got) == list(range(len(ys))), sid
+        ref = _alone(pf, cfg, ys)
+        for k in range(len(ys)):
+            assert got[k] == ref[k], (sid, k)
+
+
+def _bytes_per_particle(pf):
+    b = pf.Batch([dict(n=32, seed=1, filter_id=0)], max_filters=1)
+    v = b.info()["bytes_per_particle"]
+    b.close()
+    return v
+
+
+@pytest.mark.parametrize("inflight", [1, 3])
+def test_served_results_equal_alone_results(pf, inflight):
+    sizes = {11: 1, 22: 300, 33: 4099, 44: 20000, 55: 140001, 66: 7000, 77: 2}
+    cfgs = {sid: _cfg(k, n) for k, (sid, n) in enumerate(sizes.items())}
+    rng = np.random.default_rng(inflight)
+    series = {sid: synth.local_level_series(sid, int(rng.integers(3, 9)), filter_id=sid)[1]
+              for sid in sizes}
+    srv = pf.Server(max_streams=16, hbm_budget_bytes=1 << 30, max_inflight=inflight,
+                    keep_results=True)
+    for sid, c in cfgs.items():
+        srv.open(sid, **c)
+    todo = [(sid, k) for sid, ys in series.items() for k in range(len(ys))]
+    # interleave the streams randomly, each stream's observations in order
+    nxt = {sid: 0 for sid in series}
+    order = rng.permutation(len(todo))
+    for i in order:
+        sid = todo[i][0]
+        srv.submit(sid, series[sid][nxt[sid]])
+        nxt[sid] += 1
+        if rng.random() < 0.3:
+            time.sleep(0.002)  # let cycles of different compositions form
+    for sid in series:
+        srv.close_stream(sid)
+    srv.drain(120)
+    st = srv.stats()
+    n_obs = sum(len(v) for v in series.values())
+    assert st["submitted"] == st["completed"] == n_obs
+    assert st["streams_closed"] == len(series) and st["resident"] == 0
+    assert st["cycles"] >= max(len(v) for v in series.values())
+    assert 0 < st["p50_us"] <= st["p99_us"] <= st["max_us"]
+    _check_against_alone(pf, srv.poll(), cfgs, series)
+    srv.close()
+
+
+def test_admission_waits_for_budget_and_results_stay_exact(pf):
+    """A budget of 25,000 particles: streams that do not fit wait in FIFO
+    order and enter as earlier streams close."""
+    per = _bytes_per_particle(pf)
+    sizes = {1: 20000, 2: 9000, 3: 9000, 4: 15000, 5: 3000, 6: 20000}
+    cfgs = {sid: _cfg(sid, n) for sid, n in sizes.items()}
+    series = {sid: synth.local_level_series(50 + sid, 4, filter_id=sid)[1] for sid in sizes}
+    srv = pf.Server(max_streams=4, hbm_budget_bytes=per * 25000, keep_results=True)
+    with pytest.raises(pf.PfError) as e:
+        srv.open(99, **_cfg(99, 40000))          # can never fit
+    assert e.value.status == pf.PF_ERR_BUSY
+    for sid, c in cfgs.items():
+        srv.open(sid, **c)
+        for y in series[sid]:
+            srv.submit(sid, y)
+        srv.close_stream(sid)
+    srv.drain(120)
+    st = srv.stats()
+    assert st["admitted"] == len(sizes) and st["streams_closed"] == len(sizes)
+    assert st["completed"] == sum(len(v) for v in series.values())
+    assert st["used_particles"] == 0 and st["waiting"] == 0
+    _check_against_alone(pf, srv.poll(), cfgs, series)
+    srv.close()
+
+
+def test_replayed_poisson_load(pf):
+    """The library's replay thread drives Poisson arrivals (open, observations,
+    close); every observation completes and the latency percentiles are
+    ordered."""
+    n_streams, dur, rate = 6, 0.5, 40.0
+    sizes = [512, 3000, 131072, 700, 20000, 5000]
+    cfgs = [_cfg(i, n) for i, n in enumerate(sizes)]
+    arr = synth.poisson_arrivals(rate, n_streams, dur, seed=3)
+    series = {i: synth.local_level_series(700 + i, len(a), filter_id=i)[1] for i, a in enumerate(arr)}
+    ev = [(0.0, pf.EVENT_OPEN, i, 0.0) for i in range(n_streams)]
+    for i, a in enumerate(arr):
+        ev += [(float(t), pf.EVENT_OBS, i, float(series[i][k])) for k, t in enumerate(a)]
+        ev.append((dur + 0.01, pf.EVENT_CLOSE, i, 0.0))
+    ev.sort(key=lambda e: (e[0], e[1] != pf.EVENT_OPEN))
+    t, kind, ids, y = (np.array(c) for c in zip(*ev))
+    srv = pf.Server(max_streams=8, hbm_budget_bytes=1 << 30, keep_results=True)
+    srv.replay(t, kind, ids, y, cfgs)
+    srv.drain(120)
+    st = srv.stats()
+    assert st["submitted"] == st["completed"] == sum(len(a) for a in arr)
+    assert 0 < st["p50_us"] <= st["p90_us"] <= st["p99_us"] <= st["max_us"]
+    assert st["obs_per_s"] > 0 and st["particle_steps"] == sum(
+        len(a) * n for a, n in zip(arr, sizes))
+    _check_against_alone(pf, srv.poll(), {i: c for i, c in enumerate(cfgs)}, series)
+    srv.close()
