@@ -72,6 +72,8 @@ def parse():
     p.add_argument("--served-only", action="store_true",
                    help="print only the served measurements (one JSON line)")
     p.add_argument("--served-seconds", type=float, default=60.0)
+    p.add_argument("--precision-only", action="store_true",
+                   help="print only the FP32-vs-FP64 precision report (one JSON line)")
     return p.parse_args()
 
 
@@ -333,6 +335,7 @@ def bench_ours(args):
                 "kernels": {k: round(v, 5) for k, v in profm.items()}}
             fm.close()
         extra["batched"] = bench_batched(pf, synth, stream)
+        extra["precision"] = bench_precision(pf, synth, stream)
         extra["served"] = bench_served(pf, synth, stream, duration=args.served_seconds)
         extra["served_admission"] = bench_served(pf, synth, stream, duration=20.0, budget_gb=8.0,
                                                  session_s=10.0)
@@ -474,7 +477,7 @@ def served_events(pf, synth, n_streams, duration, rate, seed, session_s=None):
 
 
 def bench_served(pf, synth, stream, duration=60.0, budget_gb=120.0, n_streams=10000,
-                 rate=20.0, seed=10000, session_s=None, cluster=8, big_min=16384):
+                 rate=20.0, seed=10000, session_s=None, cluster=8, big_min=16384, warmup_s=5.0):
     """Continuous-batching server under Poisson load: 10,000 streams at 20
     observations/s each (200k/s aggregate), device-resident state admitted
     under an HBM budget; throughput and latency percentiles."""
@@ -483,7 +486,7 @@ def bench_served(pf, synth, stream, duration=60.0, budget_gb=120.0, n_streams=10
                                                  session_s)
     srv = pf.Server(max_streams=n_streams, hbm_budget_bytes=int(budget_gb * 1e9),
                     scheme="systematic", precision="fp32", max_inflight=2, cluster=cluster,
-                    big_min=big_min, stream=stream)
+                    big_min=big_min, warmup_s=warmup_s, stream=stream)
     clk = Clocks(phys_gpu())
     clk.start()
     t0 = time.perf_counter()
@@ -504,6 +507,10 @@ def bench_served(pf, synth, stream, duration=60.0, budget_gb=120.0, n_streams=10
         "latency_us": {"p50": round(st["p50_us"], 1), "p90": round(st["p90_us"], 1),
                        "p99": round(st["p99_us"], 1), "max": round(st["max_us"], 1),
                        "mean": round(st["mean_us"], 1)},
+        "latency_us_after_warmup": {"warmup_s": warmup_s, "observations": st["steady_count"],
+                                    "p50": round(st["steady_p50_us"], 1),
+                                    "p90": round(st["steady_p90_us"], 1),
+                                    "p99": round(st["steady_p99_us"], 1)},
         "cycles": st["cycles"], "mean_streams_per_cycle": round(st["mean_cycle_streams"], 1),
         "max_streams_per_cycle": st["max_cycle_streams"],
         "gpu_launches": 2 * st["cycles"],
@@ -517,6 +524,48 @@ def bench_served(pf, synth, stream, duration=60.0, budget_gb=120.0, n_streams=10
         "note": "latency = submit -> the stream's summaries on the host; each result equals "
                 "the stream alone (tests/test_gpu_serve.py)",
     }
+
+
+def bench_precision(pf, synth, stream, reps=8):
+    """FP32 state against FP64 state on the same draws, per posterior summary
+    and step, in units of the Monte Carlo sd of the estimate (the spread of
+    FP64 filters over `reps` independent seeds).  FP64 filters equal the FP64
+    oracle within 1e-12 at every step (tests/test_gpu_precision.py), so these
+    are the FP32 errors against the FP64 oracle."""
+    import torch
+    keys = ("x_mean", "sigma2_mean", "tau2_mean", "log_marglik")
+    out = {}
+    for name, n, T, scheme, seed in (("N=1024, T=100, multinomial", 1024, 100, "multinomial", 1212),
+                                     ("N=2^20, T=100, systematic", 1 << 20, 100, "systematic", 1639)):
+        _, y = synth.local_level_series(seed, T)
+
+        def path(sd, prec, anc_ref=None):
+            f = pf.Filter(n, seed=sd, scheme=scheme, precision=prec, stream=stream)
+            est, ancs = [], []
+            for t in range(T):
+                f.step(y[t])
+                est.append([f.estimate()[k] for k in keys])
+                if anc_ref is not None:
+                    ancs.append(f.ancestors().cpu())
+            f.close()
+            return np.array(est), ancs
+
+        e64, a64 = path(seed, "fp64", True)
+        e32, a32 = path(seed, "fp32", True)
+        first = next((t for t in range(T) if not torch.equal(a32[t], a64[t])), None)
+        rep = np.stack([path(seed + 1000 + r, "fp64")[0] for r in range(reps)])
+        mc = rep.std(axis=0, ddof=1)
+        z = np.abs(e32 - e64) / mc
+        out[name] = {
+            "max_abs_err_in_mc_sd": dict(zip(keys, np.round(z.max(axis=0), 3).tolist())),
+            "mean_abs_err_in_mc_sd": dict(zip(keys, np.round(z.mean(axis=0), 3).tolist())),
+            "final": {k: {"fp64": float(e64[-1, i]), "fp32": float(e32[-1, i]),
+                          "mc_sd": float(mc[-1, i])} for i, k in enumerate(keys)},
+            "first_step_fp32_ancestors_differ": first}
+    out["note"] = ("FP32-state against FP64-state filters with the same seeds; errors in units of "
+                   "the Monte Carlo sd measured over %d FP64 seeds; FP64 equals the FP64 oracle "
+                   "within 1e-12 (tests/test_gpu_precision.py)" % reps)
+    return out
 
 
 def cpu_baseline(n, scheme, y, budget_s=15.0):
@@ -593,6 +642,13 @@ def main():
         stream = torch.cuda.Stream()
         torch.cuda.set_stream(stream)
         print(json.dumps(bench_batched(pf, synth, stream, K=args.steps, W=max(args.warmup, 3))))
+    elif args.precision_only:
+        import torch
+
+        from paper_1212_1639_gb300 import pf, synth
+        stream = torch.cuda.Stream()
+        torch.cuda.set_stream(stream)
+        print(json.dumps(bench_precision(pf, synth, stream)))
     elif args.served_only:
         import torch
 

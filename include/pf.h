@@ -381,6 +381,8 @@ typedef struct {
   int32_t keep_results;       /* nonzero: keep per-observation results for pf_server_poll */
   uint32_t block, grid;       /* launch shape (0 = the batch default) */
   uint32_t cluster, big_min;  /* clusters of CTAs for large streams (0 = none) */
+  double warmup_s;            /* steady-state latency counts observations submitted this
+                                 long after the first one */
   void* stream;               /* cudaStream_t; NULL = one the server creates */
   pf_alloc_fn alloc;          /* NULL: cudaMallocAsync / cudaFreeAsync */
   pf_free_fn free;
@@ -407,6 +409,8 @@ typedef struct {
   double wall_s;                        /* first submit -> last result */
   double particle_steps_per_s, obs_per_s;
   double mean_us, p50_us, p90_us, p99_us, max_us;  /* observation latency */
+  uint64_t steady_count;                            /* observations after the warm-up window */
+  double steady_p50_us, steady_p90_us, steady_p99_us;
   uint32_t grid, block, cluster;
 } pf_server_stats;
 

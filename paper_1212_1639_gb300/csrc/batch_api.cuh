@@ -502,6 +502,8 @@ pf_status pf_batch_create(const pf_config* cfgs, uint32_t n, const pf_batch_opts
   for (uint32_t i = 0; i < maxf; ++i) b->free_slots.insert(b->free_slots.end(), i);
   b->autotune = opts->autotune != 0;
   if ((st = batch_shapes(b)) != PF_OK) return bail(st);
+  if ((b->fp64 ? batch_prepare<double>() : batch_prepare<float>()) != cudaSuccess)
+    return bail(set_err(PF_ERR_CUDA, "loading the batch kernels failed"));
   if (n && (st = batch_admit(b, cfgs, n, nullptr)) != PF_OK) return bail(st);
   if ((st = batch_build_graphs(b)) != PF_OK) return bail(st);
   *out = b;

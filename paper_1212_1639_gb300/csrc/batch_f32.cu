@@ -7,6 +7,7 @@ template cudaError_t batch_cycle_launch<float>(int, int, int, unsigned, const Ba
                                             cudaStream_t);
 template unsigned batch_cycle_resident<float>(int, int, int, int);
 template cudaError_t batch_init_launch<float>(unsigned, const BatchArgs<float>&, cudaStream_t);
+template cudaError_t batch_prepare<float>();
 template cudaError_t batch_estimate_launch<float>(unsigned, const BatchArgs<float>&, cudaStream_t);
 
 }  // namespace pfk

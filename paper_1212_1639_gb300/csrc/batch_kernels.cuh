@@ -84,6 +84,14 @@ cudaError_t batch_init_launch(unsigned grid, const BatchArgs<R>& a, cudaStream_t
 }
 
 template <class R>
+cudaError_t batch_prepare() {
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, k_batch_init<R>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_batch_estimate<R>);
+  return e;
+}
+
+template <class R>
 cudaError_t batch_estimate_launch(unsigned grid, const BatchArgs<R>& a, cudaStream_t s) {
   k_batch_estimate<R><<<grid, BB, 0, s>>>(a);
   return cudaGetLastError();

@@ -23,6 +23,11 @@ unsigned batch_cycle_resident(int pos, int nt, int cl, int sms);
 template <class R>
 cudaError_t batch_init_launch(unsigned grid, const BatchArgs<R>& a, cudaStream_t s);
 
+// Load the init and summary kernels now (module loading is otherwise lazy,
+// at the first launch).
+template <class R>
+cudaError_t batch_prepare();
+
 template <class R>
 cudaError_t batch_estimate_launch(unsigned grid, const BatchArgs<R>& a, cudaStream_t s);
 

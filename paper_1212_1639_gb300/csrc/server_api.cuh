@@ -81,6 +81,8 @@ struct pf_server {
   uint32_t ring = 0;
   std::deque<pf_server_result> results;
   std::vector<float> lat_us;
+  std::vector<float> sub_s;                  // submit time of each result, s after the first submit
+  double warmup_s = 0;
   // counters
   uint64_t submitted = 0, completed = 0, cycles = 0, particle_steps = 0, admitted = 0,
            admitted_after_wait = 0, streams_opened = 0, streams_closed = 0, items_total = 0;
@@ -166,6 +168,7 @@ void srv_retire_front(pf_server* s) {
     const double* v = rows + i * BATCH_EST_ROW;
     const float lat = (float)(t - it.t_sub);
     s->lat_us.push_back(lat);
+    s->sub_s.push_back((float)((it.t_sub - s->t_first_sub) * 1e-6));
     auto sit = s->streams.find(it.id);
     if (sit != s->streams.end()) {
       sit->second.inflight--;
@@ -420,6 +423,7 @@ pf_status pf_server_create(const pf_server_opts* opts, pf_server** out) {
     return st;
   }
   s->max_inflight = opts->max_inflight ? opts->max_inflight : 2;
+  s->warmup_s = opts->warmup_s > 0 ? opts->warmup_s : 0.0;
   s->keep_results = opts->keep_results != 0;
   if (opts->block || opts->cluster) {
     const uint32_t blk = opts->block ? opts->block : 256;
@@ -563,13 +567,13 @@ pf_status pf_server_get_stats(pf_server* s, pf_server_stats* out) {
     out->particle_steps_per_s = (double)s->particle_steps / out->wall_s;
     out->obs_per_s = (double)s->completed / out->wall_s;
   }
+  auto pct = [&](double q) {
+    const size_t k = std::min(lat.size() - 1, (size_t)(q * (double)(lat.size() - 1) + 0.5));
+    std::nth_element(lat.begin(), lat.begin() + k, lat.end());
+    return (double)lat[k];
+  };
   lat = s->lat_us;
   if (!lat.empty()) {
-    auto pct = [&](double q) {
-      const size_t k = std::min(lat.size() - 1, (size_t)(q * (double)(lat.size() - 1) + 0.5));
-      std::nth_element(lat.begin(), lat.begin() + k, lat.end());
-      return (double)lat[k];
-    };
     double sum = 0;
     for (float v : lat) sum += v;
     out->mean_us = sum / (double)lat.size();
@@ -577,6 +581,16 @@ pf_status pf_server_get_stats(pf_server* s, pf_server_stats* out) {
     out->p90_us = pct(0.90);
     out->p99_us = pct(0.99);
     out->max_us = (double)*std::max_element(lat.begin(), lat.end());
+  }
+  // steady state: observations submitted after the warm-up window
+  lat.clear();
+  for (size_t i = 0; i < s->lat_us.size(); ++i)
+    if (s->sub_s[i] >= s->warmup_s) lat.push_back(s->lat_us[i]);
+  out->steady_count = lat.size();
+  if (!lat.empty()) {
+    out->steady_p50_us = pct(0.50);
+    out->steady_p90_us = pct(0.90);
+    out->steady_p99_us = pct(0.99);
   }
   out->grid = s->b->grid;
   out->block = (uint32_t)s->b->nt;

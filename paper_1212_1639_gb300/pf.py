@@ -81,7 +81,7 @@ class PfServerOpts(C.Structure):
                 ("scheme", C.c_int32), ("precision", C.c_int32),
                 ("max_inflight", C.c_uint32), ("keep_results", C.c_int32),
                 ("block", C.c_uint32), ("grid", C.c_uint32),
-                ("cluster", C.c_uint32), ("big_min", C.c_uint32),
+                ("cluster", C.c_uint32), ("big_min", C.c_uint32), ("warmup_s", C.c_double),
                 ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN),
                 ("alloc_ctx", C.c_void_p)]
 
@@ -103,6 +103,8 @@ class PfServerStats(C.Structure):
                 ("wall_s", C.c_double), ("particle_steps_per_s", C.c_double),
                 ("obs_per_s", C.c_double), ("mean_us", C.c_double), ("p50_us", C.c_double),
                 ("p90_us", C.c_double), ("p99_us", C.c_double), ("max_us", C.c_double),
+                ("steady_count", C.c_uint64), ("steady_p50_us", C.c_double),
+                ("steady_p90_us", C.c_double), ("steady_p99_us", C.c_double),
                 ("grid", C.c_uint32), ("block", C.c_uint32), ("cluster", C.c_uint32)]
 
 
@@ -468,7 +470,7 @@ class Server:
 
     def __init__(self, max_streams, hbm_budget_bytes, scheme="systematic", precision="fp32",
                  max_inflight=2, keep_results=False, block=0, grid=0, cluster=0, big_min=0,
-                 stream=None, torch_alloc=True):
+                 warmup_s=0.0, stream=None, torch_alloc=True):
         torch = _torch()
         self.scheme = SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
         self.precision = FP64 if precision in ("fp64", FP64) else FP32
@@ -480,7 +482,8 @@ class Server:
                             scheme=self.scheme, precision=self.precision,
                             max_inflight=int(max_inflight), keep_results=int(bool(keep_results)),
                             block=int(block), grid=int(grid), cluster=int(cluster),
-                            big_min=int(big_min), stream=C.c_void_p(self.stream.cuda_stream))
+                            big_min=int(big_min), warmup_s=float(warmup_s),
+                            stream=C.c_void_p(self.stream.cuda_stream))
         if self._alloc is not None:
             opts.alloc = self._alloc.alloc
             opts.free = self._alloc.free
