@@ -179,9 +179,9 @@ struct BatchSmem {
   ES es[NT / 32];
   ES fold[32];                   // log-ML tile partials, lane-strided (group rank 0)
   uint32_t run[BB_MAX_RUNS][3];
-  GammaItem<R> q[2 * NT];
+  GammaItem<R> wq[NT / 32][WQ_CAP];   // per-warp queues of deferred gamma draws
   double c[4];
-  uint32_t nruns, qn;
+  uint32_t nruns;
   // read by the other CTAs of a group (distributed shared memory)
   R gmax;                        // this CTA's maximum of l
   uint64_t utot[2];              // this round's pass total, by round parity
@@ -513,12 +513,21 @@ __device__ __forceinline__ void batch_filter(const BatchArgs<R>& a, const BatchI
   group_sync(G);  // every ancestor written
 
   // 4. propagation, one slot per thread per pass (slot blocks of NT dealt
-  // round-robin over the group), deferred gamma draws
+  // round-robin over the group); draws that miss the squeeze go to the
+  // warp's queue, which the warp finishes 32 at a time
   const R ds = (R)sm.c[0], cs = (R)sm.c[1], dt = (R)sm.c[2], ct = (R)sm.c[3];
+  GammaItem<R>* const wq = sm.wq[warp];
+  uint32_t qn = 0;  // warp-uniform
+  auto finish = [&](const GammaItem<R>& itm) {
+    const bool sig = itm.which == 0;
+    const R G2 = gamma_mt_from<R>(sig ? ds : dt, sig ? cs : ct, itm.Z, itm.U, seed, fid, t,
+                                  itm.j, sig ? P_GAMMA_SIGMA : P_GAMMA_TAU, &fail);
+    const R v = SuffOps<R>::ig(itm.b, G2);
+    if (sig) dst.s2[off + itm.j] = v;
+    else dst.t2[off + itm.j] = v;
+  };
   for (uint64_t j0 = (uint64_t)rank * NT; j0 < n; j0 += (uint64_t)G * NT) {
     const uint64_t j = j0 + threadIdx.x;
-    if (threadIdx.x == 0) sm.qn = 0;
-    __syncthreads();
     bool defer_s = false, defer_t = false;
     typename SuffT<R>::B bsn = 0, btn = 0;
     R Zs = 0, Us = 0, Zt = 0, Ut = 0;
@@ -560,38 +569,11 @@ __device__ __forceinline__ void batch_filter(const BatchArgs<R>& a, const BatchI
         dst.bt[d] = src.bt[g];
       }
     }
-#pragma unroll
-    for (int gi = 0; gi < 2; ++gi) {
-      const bool dfr = gi == 0 ? defer_s : defer_t;
-      const uint32_t msk = __ballot_sync(0xffffffffu, dfr);
-      if (msk) {
-        uint32_t basei = 0;
-        if (lane == 0) basei = atomicAdd(&sm.qn, (uint32_t)__popc(msk));
-        basei = __shfl_sync(0xffffffffu, basei, 0);
-        if (dfr) {
-          GammaItem<R> itm;
-          itm.b = gi == 0 ? bsn : btn;
-          itm.Z = gi == 0 ? Zs : Zt;
-          itm.U = gi == 0 ? Us : Ut;
-          itm.j = (uint32_t)j;
-          itm.which = (uint32_t)gi;
-          sm.q[basei + __popc(msk & ((1u << lane) - 1u))] = itm;
-        }
-      }
-    }
-    __syncthreads();
-    const uint32_t qn = sm.qn;
-    for (uint32_t q = threadIdx.x; q < qn; q += NT) {
-      const GammaItem<R> itm = sm.q[q];
-      const bool sig = itm.which == 0;
-      const R G2 = gamma_mt_from<R>(sig ? ds : dt, sig ? cs : ct, itm.Z, itm.U, seed, fid, t,
-                                    itm.j, sig ? P_GAMMA_SIGMA : P_GAMMA_TAU, &fail);
-      const R v = SuffOps<R>::ig(itm.b, G2);
-      if (sig) dst.s2[off + itm.j] = v;
-      else dst.t2[off + itm.j] = v;
-    }
-    __syncthreads();
+    wq_push<R>(wq, qn, defer_s, GammaItem<R>{bsn, Zs, Us, (uint32_t)j, 0u}, lane);
+    wq_push<R>(wq, qn, defer_t, GammaItem<R>{btn, Zt, Ut, (uint32_t)j, 1u}, lane);
+    wq_drain<R>(wq, qn, 32u, lane, finish);
   }
+  wq_drain<R>(wq, qn, 1u, lane, finish);
 
   // fold the cycle into the filter's log-ML (the single-filter fold's
   // butterfly over the 32 tile accumulators) and advance t

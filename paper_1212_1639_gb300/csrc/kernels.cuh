@@ -1099,7 +1099,7 @@ __device__ void fold_cycle_warp(const FilterArgs<R>& a, uint32_t t) {
 }
 
 // A gamma draw that missed the Marsaglia-Tsang squeeze on its first attempt,
-// finished after the block's fast path (same arithmetic, later in time).
+// finished after the warp's fast path (same arithmetic, later in time).
 template <class R>
 struct GammaItem {
   typename SuffT<R>::B b;  // updated sufficient statistic (the IG scale)
@@ -1107,6 +1107,33 @@ struct GammaItem {
   uint32_t j;              // slot
   uint32_t which;          // 0: sigma^2, 1: tau^2
 };
+
+// Per-warp queue of such draws.  A warp pushes at most 64 per pass and
+// finishes them 32 at a time (one per lane) once 32 are queued, so no block
+// barrier is needed and the lanes of a finishing round are all busy.
+constexpr uint32_t WQ_CAP = 96;
+
+template <class R>
+__device__ __forceinline__ void wq_push(GammaItem<R>* q, uint32_t& qn, bool dfr,
+                                        const GammaItem<R>& itm, int lane) {
+  const uint32_t m = __ballot_sync(0xffffffffu, dfr);
+  if (dfr) q[qn + __popc(m & ((1u << lane) - 1u))] = itm;
+  qn += __popc(m);
+}
+
+// Finish queued draws, 32 per round, while at least `lo` (>= 1) are queued.
+template <class R, class Fin>
+__device__ __forceinline__ void wq_drain(GammaItem<R>* q, uint32_t& qn, uint32_t lo, int lane,
+                                         Fin fin) {
+  __syncwarp();
+  while (qn >= lo) {
+    const uint32_t take = qn < 32u ? qn : 32u;
+    const uint32_t base = qn - take;
+    if ((uint32_t)lane < take) fin(q[base + lane]);
+    qn = base;
+    __syncwarp();
+  }
+}
 
 // One ancestor's record, gathered ahead of its use.
 template <class R>
@@ -1130,9 +1157,8 @@ __device__ __forceinline__ Gathered<R> gather_rec(const StateV<R>& src, uint32_t
 // record one slot ahead, so the dependent index -> gather latency overlaps the
 // arithmetic of the current slot.
 template <class R, bool LEARN>
-__global__ void __launch_bounds__(BLOCK) k_propagate(FilterArgs<R> a) {
-  __shared__ GammaItem<R> s_q[2 * BLOCK];
-  __shared__ uint32_t s_qn;
+__global__ void __launch_bounds__(BLOCK, 5) k_propagate(FilterArgs<R> a) {
+  __shared__ GammaItem<R> s_q[WARPS][WQ_CAP];
   const Ctl* c = a.ctl;
   const uint32_t t = c->t;
   const StateV<R> src = (t & 1) ? a.st[1] : a.st[0];
@@ -1145,21 +1171,29 @@ __global__ void __launch_bounds__(BLOCK) k_propagate(FilterArgs<R> a) {
     yr = y; ds = c->mtd[0]; cs = c->mtd[1]; dt = c->mtd[2]; ct = c->mtd[3];
   }
   const int lane = threadIdx.x & 31;
+  GammaItem<R>* const wq = s_q[threadIdx.x >> 5];
+  uint32_t qn = 0;  // warp-uniform
   const uint64_t n = a.n;
   const uint64_t stride = (uint64_t)gridDim.x * BLOCK;
   const uint64_t iters = (n + stride - 1) / stride;
   auto clampi = [&](uint32_t v) { return v < n ? v : (uint32_t)(n - 1); };
+  bool fail = false;
+  auto finish = [&](const GammaItem<R>& itm) {
+    const bool sig = itm.which == 0;
+    const R G = gamma_mt_from<R>(sig ? ds : dt, sig ? cs : ct, itm.Z, itm.U, a.seed, a.filter, t,
+                                 itm.j, sig ? P_GAMMA_SIGMA : P_GAMMA_TAU, &fail);
+    const R v = SuffOps<R>::ig(itm.b, G);
+    if (sig) dst.s2[itm.j] = v;
+    else dst.t2[itm.j] = v;
+  };
   uint64_t j = (uint64_t)blockIdx.x * BLOCK + threadIdx.x;
   uint32_t an = j < n ? clampi(a.anc[j]) : 0;
   uint32_t an_next = j + stride < n ? clampi(a.anc[j + stride]) : 0;
   Gathered<R> cur = gather_rec<R>(src, an);
-  bool fail = false;
   for (uint64_t it = 0; it < iters; ++it, j += stride) {
     // prefetch: the index two slots ahead, the record one slot ahead
     const uint32_t an_next2 = j + 2 * stride < n ? clampi(a.anc[j + 2 * stride]) : 0;
     const Gathered<R> nxt = gather_rec<R>(src, an_next);
-    if (LEARN && threadIdx.x == 0) s_qn = 0;
-    if (LEARN) __syncthreads();
     bool defer_s = false, defer_t = false;
     typename SuffT<R>::B bsn = 0, btn = 0;
     R Zs = 0, Us = 0, Zt = 0, Ut = 0;
@@ -1198,43 +1232,16 @@ __global__ void __launch_bounds__(BLOCK) k_propagate(FilterArgs<R> a) {
       }
     }
     if (LEARN) {
-      // queue the draws that missed the squeeze (one shared atomic per warp
-      // and gamma), then finish them with the whole block
-#pragma unroll
-      for (int g = 0; g < 2; ++g) {
-        const bool d = g == 0 ? defer_s : defer_t;
-        const uint32_t m = __ballot_sync(0xffffffffu, d);
-        if (m) {
-          uint32_t base = 0;
-          if (lane == 0) base = atomicAdd(&s_qn, (uint32_t)__popc(m));
-          base = __shfl_sync(0xffffffffu, base, 0);
-          if (d) {
-            GammaItem<R> itm;
-            itm.b = g == 0 ? bsn : btn;
-            itm.Z = g == 0 ? Zs : Zt;
-            itm.U = g == 0 ? Us : Ut;
-            itm.j = (uint32_t)j;
-            itm.which = (uint32_t)g;
-            s_q[base + __popc(m & ((1u << lane) - 1u))] = itm;
-          }
-        }
-      }
-      __syncthreads();
-      const uint32_t qn = s_qn;
-      for (uint32_t k = threadIdx.x; k < qn; k += BLOCK) {
-        const GammaItem<R> itm = s_q[k];
-        const bool sig = itm.which == 0;
-        const R G = gamma_mt_from<R>(sig ? ds : dt, sig ? cs : ct, itm.Z, itm.U, a.seed, a.filter,
-                                     t, itm.j, sig ? P_GAMMA_SIGMA : P_GAMMA_TAU, &fail);
-        const R v = SuffOps<R>::ig(itm.b, G);
-        if (sig) dst.s2[itm.j] = v;
-        else dst.t2[itm.j] = v;
-      }
-      __syncthreads();
+      // queue the draws that missed the squeeze; the warp finishes them 32
+      // at a time
+      wq_push<R>(wq, qn, defer_s, GammaItem<R>{bsn, Zs, Us, (uint32_t)j, 0u}, lane);
+      wq_push<R>(wq, qn, defer_t, GammaItem<R>{btn, Zt, Ut, (uint32_t)j, 1u}, lane);
+      wq_drain<R>(wq, qn, 32u, lane, finish);
     }
     cur = nxt;
     an_next = an_next2;
   }
+  if (LEARN) wq_drain<R>(wq, qn, 1u, lane, finish);
   (void)an;
   if (__any_sync(0xffffffffu, fail) && lane == 0) atomicOr(&a.ctl->err, ERR_NUMERIC);
   // The fold reads only what earlier kernels wrote (tile partials, the
