@@ -54,6 +54,8 @@ BYTES_PER_PARTICLE = {
     "cutpoint_search": 8 + 4,     # read Q; write I
     "cutpoint_method": 4 + 8 + 4,  # read I, Q at the start; write ancestors
     "propagate": 4 + 28 + 28,     # read ancestor; gather 28 B record; write 28 B record
+    "cdf_resample": 4 + 8 + 4,   # read l; write Q; write ancestors (l is read twice, the
+                                  # second time mostly from L2)
 }
 
 

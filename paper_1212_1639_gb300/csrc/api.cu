@@ -68,6 +68,8 @@ struct pf_filter {
   bool fp64 = false, learn = true;
   int scheme = 0;
   unsigned prop_grid = 0;  // persistent propagate grid
+  unsigned cdf_grid = 0;   // cooperative CDF + systematic resampling grid (0: not used)
+  uint64_t* cta_tot = nullptr;
   std::vector<void*> allocs;
   void* x[2] = {}; void* s2[2] = {}; void* t2[2] = {}; void* bs[2] = {}; void* bt[2] = {};
   void* ell = nullptr;
@@ -231,8 +233,10 @@ pf_status enqueue_cycle(pf_filter* f, KTimer* tm = nullptr) {
   sa.n = n;
   sa.k = f->k;
   sa.vec_ok = 1;
-  k_scan<FROM_LOGLIK, R><<<f->ntiles, BLOCK, 0, s>>>(sa);
-  mark(tm, "scan", s);
+  if (!f->cdf_grid) {
+    k_scan<FROM_LOGLIK, R><<<f->ntiles, BLOCK, 0, s>>>(sa);
+    mark(tm, "scan", s);
+  }
   if (is_multinomial(f->scheme)) {
     SpacingArgs sp;
     sp.S = f->S;
@@ -258,8 +262,24 @@ pf_status enqueue_cycle(pf_filter* f, KTimer* tm = nullptr) {
   pa.n = n;
   pa.seed = f->cfg.seed;
   pa.filter = f->cfg.filter_id;
-  pf_status st = launch_resample(f->scheme, pa, n, f->I, f->splits, s, tm);
-  if (st != PF_OK) return st;
+  if (f->cdf_grid) {
+    // systematic: the CDF and the resampling in one cooperative launch
+    cudaLaunchConfig_t cfg;
+    std::memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = dim3(f->cdf_grid, 1, 1);
+    cfg.blockDim = dim3(BLOCK, 1, 1);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    CK(cudaLaunchKernelEx(&cfg, k_cdf_sys<R>, a, f->cta_tot));
+    mark(tm, "cdf_resample", s);
+  } else {
+    pf_status st = launch_resample(f->scheme, pa, n, f->I, f->splits, s, tm);
+    if (st != PF_OK) return st;
+  }
   if (f->learn) k_propagate<R, true><<<f->prop_grid, BLOCK, 0, s>>>(a);
   else k_propagate<R, false><<<f->prop_grid, BLOCK, 0, s>>>(a);
   mark(tm, "propagate", s);
@@ -455,6 +475,16 @@ pf_status pf_create(const pf_config* cfg, pf_filter** out) {
     if (e != cudaSuccess || per_sm < 1 || sms < 1) return bail(set_err(PF_ERR_CUDA, "occupancy query failed"));
     const uint64_t want = cdiv(n, BLOCK), cap = (uint64_t)per_sm * (uint64_t)sms;
     f->prop_grid = (unsigned)(want < cap ? want : cap);
+    if (f->scheme == PF_SYSTEMATIC) {
+      // cooperative grid: every CTA resident at once (it waits on the others)
+      int cdf_sm = 0;
+      e = f->fp64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cdf_sm, k_cdf_sys<double>, BLOCK, 0)
+                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cdf_sm, k_cdf_sys<float>, BLOCK, 0);
+      if (e != cudaSuccess || cdf_sm < 1) return bail(set_err(PF_ERR_CUDA, "occupancy query failed"));
+      const uint64_t g = (uint64_t)cdf_sm * (uint64_t)sms;
+      f->cdf_grid = (unsigned)(f->ntiles < g ? f->ntiles : g);
+      if ((st = dev_alloc(f, (size_t)f->cdf_grid * 8, (void**)&f->cta_tot)) != PF_OK) return bail(st);
+    }
   }
   if ((st = build_graph(f)) != PF_OK) return bail(st);
   *out = f;

@@ -52,6 +52,7 @@ struct Ctl {
   uint32_t ticket_e;      // spacing scan tile ticket
   uint32_t done_prop;     // last-block counter of k_propagate
   uint32_t done_est;      // last-block counter of k_estimate
+  uint32_t gbar;          // grid barrier of k_cdf_sys
   double logml;           // accumulated log marginal likelihood
   double est[8];          // t, x mean/var, sigma2 mean/var, tau2 mean/var, log_marglik
   // per-cycle constants written by k_weights (block 0) for k_propagate:
@@ -868,6 +869,7 @@ constexpr int SYS_THREADS = 512;
 constexpr int SYS_PER = 16;      // particles per thread (SYS_D / SYS_THREADS)
 constexpr int SYS_CAP = 8;       // slots emitted one by one per particle
 constexpr int SYS_MAX_RUNS = SYS_D / SYS_CAP + 2;
+constexpr int BB_RUNS = 512;     // k_cdf_sys: runs per tile held in shared memory
 
 __device__ __forceinline__ U128 sub128(U128 x, uint64_t y) {
   return U128{x.hi - (x.lo < y ? 1ull : 0ull), x.lo - y};
@@ -1053,6 +1055,231 @@ static __global__ void __launch_bounds__(BLOCK) k_cutpoint_method_explicit(
 }
 
 // ---------------------------------------------------------------------------
+// The CDF and systematic resampling in one cooperative launch (Steps 1b-1c
+// of the cycle for the systematic scheme).  Every CTA owns a contiguous range
+// of 4096-particle tiles:
+//   phase 1  the exact sum of its quantised weights W_i;
+//   barrier  all CTAs (the launch is cooperative, so all are resident; the
+//            wait is bounded and reports ERR_TIMEOUT);
+//   phase 2  its exclusive prefix and T from the CTA sums, then for each of
+//            its tiles the block scan of W with a carry -- thread t holds
+//            Q_i for its 16 particles [16 t, 16 t + 16) and Q before them in
+//            registers -- the CDF written out, and the systematic walk of its
+//            particles straight from those registers.
+// The quantisation, the per-thread log-ML partials (16 particles, fixed
+// order) and the tile partials are those of k_scan, and the ancestors those
+// of k_merge_sys: the results are the same bits.  Instead of a look-back
+// over tiles in flight, one grid-wide barrier; the weights l are read twice
+// (the second time mostly from L2).
+// ---------------------------------------------------------------------------
+template <class R>
+__global__ void __launch_bounds__(BLOCK, 3) k_cdf_sys(FilterArgs<R> a, uint64_t* cta_tot) {
+  typedef typename ESumT<R>::T ES;
+  __shared__ uint64_t s_warp[WARPS + 1];
+  __shared__ ES s_es[WARPS];
+  __shared__ uint64_t s_bc[2];
+  __shared__ uint32_t s_run[BB_RUNS][3];
+  __shared__ uint32_t s_nruns;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  Ctl* c = a.ctl;
+  const uint64_t n = a.n;
+  const uint32_t ntiles = a.ntiles;
+  const uint32_t per = (ntiles + gridDim.x - 1) / gridDim.x;
+  const uint32_t tb = blockIdx.x * per < ntiles ? blockIdx.x * per : ntiles;
+  const uint32_t te = tb + per < ntiles ? tb + per : ntiles;
+  const uint32_t t = c->t;
+  R m;
+  if constexpr (sizeof(R) == 4) m = dec_f((uint32_t)c->maxenc);
+  else m = dec_d(c->maxenc);
+  const int k = a.k;
+  // loads this thread's 16 weights of tile `tile` and quantises them
+  auto quant16 = [&](uint32_t tile, uint64_t* W, R* epart) {
+    const uint64_t base = (uint64_t)tile * TILE + (uint64_t)threadIdx.x * SCAN_PER;
+    const bool full = base + SCAN_PER <= n;
+    uint64_t run = 0;
+    R ep = (R)0;
+#pragma unroll
+    for (int q = 0; q < SCAN_PER / 4; ++q) {
+      R v[4];
+      if (full) {
+        if constexpr (sizeof(R) == 4) {
+          const float4 f = *reinterpret_cast<const float4*>(a.ell + base + 4 * q);
+          v[0] = f.x; v[1] = f.y; v[2] = f.z; v[3] = f.w;
+        } else {
+          const double2 f0 = *reinterpret_cast<const double2*>(a.ell + base + 4 * q);
+          const double2 f1 = *reinterpret_cast<const double2*>(a.ell + base + 4 * q + 2);
+          v[0] = f0.x; v[1] = f0.y; v[2] = f1.x; v[3] = f1.y;
+        }
+      } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) v[e] = (base + 4 * q + e < n) ? a.ell[base + 4 * q + e] : (R)0;
+      }
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        uint64_t w = 0;
+        if (full || base + 4 * q + e < n) {
+          R ex;
+          const R dl = v[e] - m;
+          w = quant_exp<R>(dl, k, &ex);
+          ep = ep + ex;
+        }
+        run += w;
+        W[4 * q + e] = run;  // inclusive running sum
+      }
+    }
+    *epart = ep;
+  };
+  // block sum of one value per thread, returned to every thread
+  auto block_sum = [&](uint64_t v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) s_warp[warp] = v;
+    __syncthreads();
+    uint64_t tot = 0;
+    for (int w = 0; w < WARPS; ++w) tot += s_warp[w];
+    __syncthreads();
+    return tot;
+  };
+
+  // phase 1: this CTA's sum of W
+  uint64_t mine = 0;
+  for (uint32_t tile = tb; tile < te; ++tile) {
+    uint64_t W[SCAN_PER];
+    R ep;
+    quant16(tile, W, &ep);
+    mine += W[SCAN_PER - 1];
+  }
+  mine = block_sum(mine);
+  if (threadIdx.x == 0) {
+    st_status(&cta_tot[blockIdx.x], mine);
+    __threadfence();
+    atomicAdd(&c->gbar, 1u);
+    uint32_t spins = 0;
+    while (ld_volatile_u32(&c->gbar) < gridDim.x) {
+      if (++spins > SPIN_LIMIT) {
+        atomicOr(&c->err, ERR_TIMEOUT);
+        break;
+      }
+      __nanosleep(64);
+    }
+    __threadfence();
+  }
+  __syncthreads();
+
+  // phase 2: this CTA's exclusive prefix and the total T
+  uint64_t pre = 0, all = 0;
+  for (uint32_t b = threadIdx.x; b < gridDim.x; b += BLOCK) {
+    const uint64_t v = ld_status(&cta_tot[b]);
+    all += v;
+    if (b < blockIdx.x) pre += v;
+  }
+  pre = block_sum(pre);
+  const uint64_t T = block_sum(all);
+  const U4 wr = draw(a.seed, a.filter, t, 0, P_SYS_OFFSET, 0);
+  const uint64_t r = __umul64hi(((uint64_t)wr.b << 32) | wr.a, T);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    c->keyT = T;
+    c->keyA = n;
+    c->keyR = r;
+    if (T == 0) atomicOr(&c->err, ERR_NUMERIC);
+  }
+  const SysDiv dv = make_sysdiv(T > 0 ? T : 1);
+  if (threadIdx.x == 0) s_nruns = 0;
+  __syncthreads();
+  uint64_t carry = pre;
+  for (uint32_t tile = tb; tile < te; ++tile) {
+    uint64_t W[SCAN_PER];
+    R ep;
+    quant16(tile, W, &ep);
+    {
+      ES es;
+      es.zero();
+      es.add(ep);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) es.add(es.shfl_xor(o));
+      if (lane == 0) s_es[warp] = es;
+    }
+    // block exclusive scan of the thread totals
+    const uint64_t tt = W[SCAN_PER - 1];
+    const uint64_t incl = warp_incl_scan(tt, lane);
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+      const uint64_t wt = lane < WARPS ? s_warp[lane] : 0;
+      const uint64_t wi = warp_incl_scan(wt, lane);
+      if (lane < WARPS) s_warp[lane] = wi - wt;
+      if (lane == WARPS - 1) s_bc[0] = wi;
+      if (lane == 0) {
+        ES tot = s_es[0];
+        for (int w = 1; w < WARPS; ++w) tot.add(s_es[w]);
+        reinterpret_cast<ES*>(a.part)[tile] = tot;
+      }
+    }
+    __syncthreads();
+    const uint64_t o = carry + s_warp[warp] + (incl - tt);  // Q just before this thread's particles
+    const uint64_t tile_tot = s_bc[0];
+    const uint64_t base = (uint64_t)tile * TILE + (uint64_t)threadIdx.x * SCAN_PER;
+    if (base + SCAN_PER <= n) {
+#pragma unroll
+      for (int e = 0; e < SCAN_PER; e += 2)
+        *reinterpret_cast<ulonglong2*>(a.Q + base + e) = make_ulonglong2(o + W[e], o + W[e + 1]);
+    } else {
+#pragma unroll
+      for (int e = 0; e < SCAN_PER; ++e)
+        if (base + e < n) a.Q[base + e] = o + W[e];
+    }
+    // systematic walk of this thread's particles from its first slot
+    if (T > 0 && base < n) {
+      uint64_t j = base == 0 ? 0 : sys_first_slot(o, n, r, dv);
+      U128 KB = add128(mul64x32(T, (uint32_t)j), r);
+#pragma unroll
+      for (int e = 0; e < SCAN_PER; ++e) {
+        const uint64_t i = base + e;
+        if (i >= n) continue;
+        const uint64_t qi = o + W[e];
+        const U128 KQ = mul64x32(qi, (uint32_t)n);
+        int emitted = 0;
+        while (j < n && lt128(KB, KQ)) {
+          if (emitted == SYS_CAP) {  // a heavy particle: its other slots become a run
+            uint64_t Rr = sys_first_slot(qi, n, r, dv);
+            Rr = Rr < j ? j : Rr;
+            const uint32_t kr = atomicAdd(&s_nruns, 1u);
+            if (kr < BB_RUNS) {
+              s_run[kr][0] = (uint32_t)j;
+              s_run[kr][1] = (uint32_t)Rr;
+              s_run[kr][2] = (uint32_t)i;
+            } else {
+              for (uint64_t q = j; q < Rr; ++q) a.anc[q] = (uint32_t)i;
+            }
+            j = Rr;
+            KB = add128(mul64x32(T, (uint32_t)j), r);
+            break;
+          }
+          a.anc[j] = (uint32_t)i;
+          ++j;
+          KB = add128(KB, T);
+          ++emitted;
+        }
+      }
+    }
+    __syncthreads();
+    const uint32_t nr = s_nruns < BB_RUNS ? s_nruns : BB_RUNS;
+    for (uint32_t q = 0; q < nr; ++q) {
+      const uint32_t st = s_run[q][0], en = s_run[q][1], v = s_run[q][2];
+      for (uint32_t jj = st + threadIdx.x; jj < en; jj += BLOCK) a.anc[jj] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) s_nruns = 0;
+    carry += tile_tot;
+  }
+  if (T == 0) {  // empty CDF (flagged): keep every index in range
+    for (uint64_t j = (uint64_t)blockIdx.x * BLOCK + threadIdx.x; j < n;
+         j += (uint64_t)gridDim.x * BLOCK)
+      a.anc[j] = (uint32_t)j;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Steps 2-4: propagate x, update the sufficient statistics, draw theta.
 // The last block to finish folds the log-ML partials, resets the per-cycle
 // counters and advances t.
@@ -1093,6 +1320,7 @@ __device__ void fold_cycle_warp(const FilterArgs<R>& a, uint32_t t) {
     c->ticket_w = 0;
     c->ticket_e = 0;
     c->done_prop = 0;
+    c->gbar = 0;
     __threadfence();
     c->t = t + 1;
   }
