@@ -30,10 +30,11 @@ __device__ __forceinline__ U4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint
                                      uint32_t k0, uint32_t k1) {
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
-    const uint32_t hi0 = __umulhi(0xD2511F53u, c0);
-    const uint32_t lo0 = 0xD2511F53u * c0;
-    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2);
-    const uint32_t lo1 = 0xCD9E8D57u * c2;
+    // one 32 x 32 -> 64-bit product each: its halves are the S-box outputs
+    const uint64_t p0 = (uint64_t)0xD2511F53u * c0;
+    const uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
+    const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
     c0 = hi1 ^ c1 ^ k0;
     c1 = lo1;
     c2 = hi0 ^ c3 ^ k1;
@@ -504,25 +505,20 @@ __device__ __forceinline__ uint64_t f2u64_rz(float v) {  // v >= 0, finite, < 2^
   const uint64_t m = (b & 0x7fffffu) | 0x800000u;
   return e >= 23 ? (m << (e - 23)) : (m >> (23 - e));
 }
+// u64 -> binary32, round to nearest even.  Values below 2^32 convert in one
+// hardware u32 conversion.  Above, the top 32 bits m = b >> s (s = 32 minus
+// the leading zeros of the high word) carry 8 bits below the binary32
+// rounding position; OR-ing "any lower bit set" into m's last bit keeps
+// every tie and sticky decision of the 64-bit value, so converting m and
+// scaling by 2^s (exact) rounds b correctly.
 __device__ __forceinline__ float u64_to_f32_rn(uint64_t b) {
-  if (b == 0) return 0.0f;
-  const int p = 63 - __clzll((long long)b);  // leading bit
-  uint64_t m;
-  int e = p;
-  if (p <= 23) {
-    m = b << (23 - p);
-  } else {
-    const int s = p - 23;
-    m = b >> s;
-    const uint64_t rem = b & ((1ull << s) - 1);
-    const uint64_t half = 1ull << (s - 1);
-    if (rem > half || (rem == half && (m & 1))) m += 1;
-    if (m == (1ull << 24)) {
-      m >>= 1;
-      e += 1;
-    }
-  }
-  return __uint_as_float(((uint32_t)(e + 127) << 23) | ((uint32_t)m & 0x7fffffu));
+  const uint32_t hi = (uint32_t)(b >> 32);
+  if (hi == 0) return __uint2float_rn((uint32_t)b);
+  const int s = 32 - __clz(hi);  // 1 .. 32
+  const uint32_t m = (uint32_t)(b >> s);
+  const uint32_t sticky = (b & ((1ull << s) - 1ull)) != 0ull ? 1u : 0u;
+  const float f = __uint2float_rn(m | sticky);
+  return f * __int_as_float((127 + s) << 23);  // * 2^s, exact
 }
 __device__ __forceinline__ uint64_t f2u64_rz(double v) { return __double2ull_rz(v); }
 

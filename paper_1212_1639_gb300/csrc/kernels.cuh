@@ -1080,6 +1080,10 @@ __global__ void __launch_bounds__(BLOCK, 3) k_cdf_sys(FilterArgs<R> a, uint64_t*
   __shared__ uint64_t s_bc[2];
   __shared__ uint32_t s_run[BB_RUNS][3];
   __shared__ uint32_t s_nruns;
+  // the first tile's quantised weights and log-ML partials, kept from phase
+  // 1 for phase 2 (a CTA that owns one tile quantises once)
+  __shared__ uint64_t s_keep[BLOCK * (SCAN_PER + 1)];
+  __shared__ R s_keep_ep[BLOCK];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   Ctl* c = a.ctl;
   const uint64_t n = a.n;
@@ -1148,6 +1152,11 @@ __global__ void __launch_bounds__(BLOCK, 3) k_cdf_sys(FilterArgs<R> a, uint64_t*
     R ep;
     quant16(tile, W, &ep);
     mine += W[SCAN_PER - 1];
+    if (tile == tb) {
+#pragma unroll
+      for (int e = 0; e < SCAN_PER; ++e) s_keep[threadIdx.x * (SCAN_PER + 1) + e] = W[e];
+      s_keep_ep[threadIdx.x] = ep;
+    }
   }
   mine = block_sum(mine);
   if (threadIdx.x == 0) {
@@ -1190,7 +1199,13 @@ __global__ void __launch_bounds__(BLOCK, 3) k_cdf_sys(FilterArgs<R> a, uint64_t*
   for (uint32_t tile = tb; tile < te; ++tile) {
     uint64_t W[SCAN_PER];
     R ep;
-    quant16(tile, W, &ep);
+    if (tile == tb) {  // this thread's own entries: no barrier needed
+#pragma unroll
+      for (int e = 0; e < SCAN_PER; ++e) W[e] = s_keep[threadIdx.x * (SCAN_PER + 1) + e];
+      ep = s_keep_ep[threadIdx.x];
+    } else {
+      quant16(tile, W, &ep);
+    }
     {
       ES es;
       es.zero();
