@@ -151,6 +151,16 @@ FilterArgs<R> filter_args(pf_filter* f) {
   a.k = f->k;
   a.seed = f->cfg.seed;
   a.filter = f->cfg.filter_id;
+  {
+    // Philox4x32-10 round keys: the key words bumped by the Weyl constants
+    uint32_t k0 = (uint32_t)f->cfg.seed, k1 = (uint32_t)(f->cfg.seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+      a.rk[2 * r] = k0;
+      a.rk[2 * r + 1] = k1;
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+  }
   a.x0_mean = f->cfg.x0_mean;
   a.x0_var = f->cfg.x0_var;
   a.a_sigma = f->cfg.a_sigma;

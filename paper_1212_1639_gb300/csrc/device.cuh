@@ -45,6 +45,26 @@ __device__ __forceinline__ U4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint
   return U4{c0, c1, c2, c3};
 }
 
+// Philox4x32-10 with its ten round keys given (they depend only on the
+// 64-bit key, so a kernel can take them precomputed as parameters instead of
+// bumping the key twice per round in every draw): rk[2r], rk[2r+1] are the
+// key words of round r.
+__device__ __forceinline__ U4 philox_rk(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                        const uint32_t* rk) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t p0 = (uint64_t)0xD2511F53u * c0;
+    const uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
+    const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    c0 = hi1 ^ c1 ^ rk[2 * r];
+    c1 = lo1;
+    c2 = hi0 ^ c3 ^ rk[2 * r + 1];
+    c3 = lo0;
+  }
+  return U4{c0, c1, c2, c3};
+}
+
 enum Purpose : uint32_t {
   P_INIT_X = 1, P_INIT_SIGMA = 2, P_INIT_TAU = 3,
   P_STATE = 4, P_GAMMA_SIGMA = 5, P_GAMMA_TAU = 6,
@@ -430,6 +450,17 @@ __device__ __forceinline__ void theta_draws(uint64_t seed, uint32_t filter, uint
                                             uint32_t j, R* Zx, R* Zs, R* Us, R* Zt, R* Ut) {
   const U4 A = draw(seed, filter, t, j, P_STATE, 0);
   const U4 B = draw(seed, filter, t, j, P_STATE, 1);
+  bm_normal2(A, Zx, Zs);
+  *Us = extra_uniform(A, (R)0);
+  *Zt = bm_normal(B, (R)0);
+  *Ut = extra_uniform(B, (R)0);
+}
+// The same draws with the Philox round keys given (philox_rk).
+template <class R>
+__device__ __forceinline__ void theta_draws_rk(const uint32_t* rk, uint32_t filter, uint32_t t,
+                                               uint32_t j, R* Zx, R* Zs, R* Us, R* Zt, R* Ut) {
+  const U4 A = philox_rk(j, t, filter, P_STATE, rk);
+  const U4 B = philox_rk(j, t, filter, P_STATE | (1u << 8), rk);
   bm_normal2(A, Zx, Zs);
   *Us = extra_uniform(A, (R)0);
   *Zt = bm_normal(B, (R)0);

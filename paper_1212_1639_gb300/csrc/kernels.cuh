@@ -129,6 +129,7 @@ struct FilterArgs {
   int k;                    // CDF shift: W <= 2^k
   uint64_t seed;
   uint32_t filter;
+  uint32_t rk[20];          // Philox round keys of seed (philox_rk)
   double x0_mean, x0_var, a_sigma, b_sigma, a_tau, b_tau, sigma2, tau2;
 };
 
@@ -1451,7 +1452,7 @@ __global__ void __launch_bounds__(BLOCK, 5) k_propagate(FilterArgs<R> a) {
       const R mu = nn / s;
       const R sv = sqrt(V);
       R Z;
-      theta_draws<R>(a.seed, a.filter, t, (uint32_t)j, &Z, &Zs, &Us, &Zt, &Ut);
+      theta_draws_rk<R>(a.rk, a.filter, t, (uint32_t)j, &Z, &Zs, &Us, &Zt, &Ut);
       const R xz = sv * Z;
       const R xj = mu + xz;
       dst.x[j] = xj;
