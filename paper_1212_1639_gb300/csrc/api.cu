@@ -69,6 +69,7 @@ struct pf_filter {
   int scheme = 0;
   unsigned prop_grid = 0;  // persistent propagate grid
   unsigned cdf_grid = 0;   // cooperative CDF + systematic resampling grid (0: not used)
+  bool cdf_staged = false; // its CTAs own several tiles: TMA-staged variant
   uint64_t* cta_tot = nullptr;
   std::vector<void*> allocs;
   void* x[2] = {}; void* s2[2] = {}; void* t2[2] = {}; void* bs[2] = {}; void* bt[2] = {};
@@ -284,7 +285,8 @@ pf_status enqueue_cycle(pf_filter* f, KTimer* tm = nullptr) {
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    CK(cudaLaunchKernelEx(&cfg, k_cdf_sys<R>, a, f->cta_tot));
+    if (f->cdf_staged) CK(cudaLaunchKernelEx(&cfg, k_cdf_sys<R, true>, a, f->cta_tot));
+    else CK(cudaLaunchKernelEx(&cfg, k_cdf_sys<R, false>, a, f->cta_tot));
     mark(tm, "cdf_resample", s);
   } else {
     pf_status st = launch_resample(f->scheme, pa, n, f->I, f->splits, s, tm);
@@ -487,11 +489,19 @@ pf_status pf_create(const pf_config* cfg, pf_filter** out) {
     f->prop_grid = (unsigned)(want < cap ? want : cap);
     if (f->scheme == PF_SYSTEMATIC) {
       // cooperative grid: every CTA resident at once (it waits on the others)
+      // one tile per CTA when the tiles fit at once, else the staged variant
       int cdf_sm = 0;
-      e = f->fp64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cdf_sm, k_cdf_sys<double>, BLOCK, 0)
-                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cdf_sm, k_cdf_sys<float>, BLOCK, 0);
+      e = f->fp64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cdf_sm, k_cdf_sys<double, false>, BLOCK, 0)
+                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cdf_sm, k_cdf_sys<float, false>, BLOCK, 0);
       if (e != cudaSuccess || cdf_sm < 1) return bail(set_err(PF_ERR_CUDA, "occupancy query failed"));
-      const uint64_t g = (uint64_t)cdf_sm * (uint64_t)sms;
+      uint64_t g = (uint64_t)cdf_sm * (uint64_t)sms;
+      if (f->ntiles > g) {
+        f->cdf_staged = true;
+        e = f->fp64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cdf_sm, k_cdf_sys<double, true>, BLOCK, 0)
+                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cdf_sm, k_cdf_sys<float, true>, BLOCK, 0);
+        if (e != cudaSuccess || cdf_sm < 1) return bail(set_err(PF_ERR_CUDA, "occupancy query failed"));
+        g = (uint64_t)cdf_sm * (uint64_t)sms;
+      }
       f->cdf_grid = (unsigned)(f->ntiles < g ? f->ntiles : g);
       if ((st = dev_alloc(f, (size_t)f->cdf_grid * 8, (void**)&f->cta_tot)) != PF_OK) return bail(st);
     }

@@ -1056,6 +1056,49 @@ static __global__ void __launch_bounds__(BLOCK) k_cutpoint_method_explicit(
 }
 
 // ---------------------------------------------------------------------------
+// Bulk asynchronous copies (TMA, cp.async.bulk) into shared memory, completed
+// on an mbarrier.  Waits are bounded: after SPIN_LIMIT polls they report
+// failure instead of hanging.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+// make the barrier initialisation visible to the async proxy
+__device__ __forceinline__ void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// order this thread's earlier shared-memory accesses before later async-proxy ones
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// copy `bytes` (a multiple of 16; both addresses 16-byte aligned) from global
+// to shared memory, completing on `bar`, which expects exactly these bytes
+__device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t bytes,
+                                            uint64_t* bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+               ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+      ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t addr = smem_u32(bar);
+  for (uint32_t i = 0; i < SPIN_LIMIT; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done) : "r"(addr), "r"(parity) : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// ---------------------------------------------------------------------------
 // The CDF and systematic resampling in one cooperative launch (Steps 1b-1c
 // of the cycle for the systematic scheme).  Every CTA owns a contiguous range
 // of 4096-particle tiles:
@@ -1073,8 +1116,11 @@ static __global__ void __launch_bounds__(BLOCK) k_cutpoint_method_explicit(
 // over tiles in flight, one grid-wide barrier; the weights l are read twice
 // (the second time mostly from L2).
 // ---------------------------------------------------------------------------
-template <class R>
-__global__ void __launch_bounds__(BLOCK, 3) k_cdf_sys(FilterArgs<R> a, uint64_t* cta_tot) {
+// STAGED: a CTA owns several tiles, and l of the next one is copied by TMA
+// into a shared-memory double buffer while the CTA works on the current one;
+// otherwise (one tile per CTA) l is read directly.
+template <class R, bool STAGED>
+__global__ void __launch_bounds__(BLOCK, STAGED ? 3 : 4) k_cdf_sys(FilterArgs<R> a, uint64_t* cta_tot) {
   typedef typename ESumT<R>::T ES;
   __shared__ uint64_t s_warp[WARPS + 1];
   __shared__ ES s_es[WARPS];
@@ -1085,6 +1131,9 @@ __global__ void __launch_bounds__(BLOCK, 3) k_cdf_sys(FilterArgs<R> a, uint64_t*
   // 1 for phase 2 (a CTA that owns one tile quantises once)
   __shared__ uint64_t s_keep[BLOCK * (SCAN_PER + 1)];
   __shared__ R s_keep_ep[BLOCK];
+  // l of the next tile arrives by TMA while the CTA works on the current one
+  __shared__ alignas(128) R s_ell[2][STAGED ? TILE : 4];
+  __shared__ alignas(8) uint64_t s_bar[2];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   Ctl* c = a.ctl;
   const uint64_t n = a.n;
@@ -1097,9 +1146,42 @@ __global__ void __launch_bounds__(BLOCK, 3) k_cdf_sys(FilterArgs<R> a, uint64_t*
   if constexpr (sizeof(R) == 4) m = dec_f((uint32_t)c->maxenc);
   else m = dec_d(c->maxenc);
   const int k = a.k;
-  // loads this thread's 16 weights of tile `tile` and quantises them
-  auto quant16 = [&](uint32_t tile, uint64_t* W, R* epart) {
+  // TMA double buffer: copy number q goes to buffer q & 1 and completes
+  // phase (q >> 1) & 1 of that buffer's barrier; copies are waited for in
+  // the order they were issued
+  if (STAGED && threadIdx.x == 0) {
+    mbar_init(&s_bar[0], 1);
+    mbar_init(&s_bar[1], 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  uint32_t q_issued = 0, q_done = 0;
+  auto issue = [&](uint32_t tile) {  // thread 0 only; the buffer is free
+    const uint64_t first = (uint64_t)tile * TILE;
+    const uint64_t cnt = n - first < (uint64_t)TILE ? n - first : (uint64_t)TILE;
+    const uint32_t bytes = (uint32_t)((cnt * sizeof(R) + 15) & ~(uint64_t)15);
+    fence_proxy_async_smem();
+    tma_load_1d(s_ell[q_issued & 1], a.ell + first, bytes, &s_bar[q_issued & 1]);
+  };
+  auto next_issue = [&](uint32_t tile) {
+    if (!STAGED) return;
+    if (threadIdx.x == 0) issue(tile);
+    ++q_issued;
+  };
+  // waits for the oldest copy; returns its buffer (unstaged: l in HBM, at
+  // the tile's start)
+  auto take_tile = [&](uint32_t tile) -> const R* {
+    if (!STAGED) return a.ell + (uint64_t)tile * TILE;
+    const uint32_t b = q_done & 1;
+    if (!mbar_wait(&s_bar[b], (q_done >> 1) & 1) && threadIdx.x == 0)
+      atomicOr(&c->err, ERR_TIMEOUT);
+    ++q_done;
+    return s_ell[b];
+  };
+  // this thread's 16 weights of tile `tile` (l staged in buf) quantised
+  auto quant16 = [&](uint32_t tile, const R* buf, uint64_t* W, R* epart) {
     const uint64_t base = (uint64_t)tile * TILE + (uint64_t)threadIdx.x * SCAN_PER;
+    const R* row = buf + threadIdx.x * SCAN_PER;
     const bool full = base + SCAN_PER <= n;
     uint64_t run = 0;
     R ep = (R)0;
@@ -1108,16 +1190,16 @@ __global__ void __launch_bounds__(BLOCK, 3) k_cdf_sys(FilterArgs<R> a, uint64_t*
       R v[4];
       if (full) {
         if constexpr (sizeof(R) == 4) {
-          const float4 f = *reinterpret_cast<const float4*>(a.ell + base + 4 * q);
+          const float4 f = *reinterpret_cast<const float4*>(row + 4 * q);
           v[0] = f.x; v[1] = f.y; v[2] = f.z; v[3] = f.w;
         } else {
-          const double2 f0 = *reinterpret_cast<const double2*>(a.ell + base + 4 * q);
-          const double2 f1 = *reinterpret_cast<const double2*>(a.ell + base + 4 * q + 2);
+          const double2 f0 = *reinterpret_cast<const double2*>(row + 4 * q);
+          const double2 f1 = *reinterpret_cast<const double2*>(row + 4 * q + 2);
           v[0] = f0.x; v[1] = f0.y; v[2] = f1.x; v[3] = f1.y;
         }
       } else {
 #pragma unroll
-        for (int e = 0; e < 4; ++e) v[e] = (base + 4 * q + e < n) ? a.ell[base + 4 * q + e] : (R)0;
+        for (int e = 0; e < 4; ++e) v[e] = (base + 4 * q + e < n) ? row[4 * q + e] : (R)0;
       }
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
@@ -1148,16 +1230,21 @@ __global__ void __launch_bounds__(BLOCK, 3) k_cdf_sys(FilterArgs<R> a, uint64_t*
 
   // phase 1: this CTA's sum of W
   uint64_t mine = 0;
+  if (tb < te) next_issue(tb);
   for (uint32_t tile = tb; tile < te; ++tile) {
+    if (tile + 1 < te) next_issue(tile + 1);
+    else if (tile + 1 == te && tb + 1 < te) next_issue(tb + 1);  // phase 2's first tile
+    const R* buf = take_tile(tile);
     uint64_t W[SCAN_PER];
     R ep;
-    quant16(tile, W, &ep);
+    quant16(tile, buf, W, &ep);
     mine += W[SCAN_PER - 1];
     if (tile == tb) {
 #pragma unroll
       for (int e = 0; e < SCAN_PER; ++e) s_keep[threadIdx.x * (SCAN_PER + 1) + e] = W[e];
       s_keep_ep[threadIdx.x] = ep;
     }
+    __syncthreads();  // buf is refilled two copies later
   }
   mine = block_sum(mine);
   if (threadIdx.x == 0) {
@@ -1205,7 +1292,9 @@ __global__ void __launch_bounds__(BLOCK, 3) k_cdf_sys(FilterArgs<R> a, uint64_t*
       for (int e = 0; e < SCAN_PER; ++e) W[e] = s_keep[threadIdx.x * (SCAN_PER + 1) + e];
       ep = s_keep_ep[threadIdx.x];
     } else {
-      quant16(tile, W, &ep);
+      if (tile + 1 < te) next_issue(tile + 1);
+      const R* buf = take_tile(tile);
+      quant16(tile, buf, W, &ep);
     }
     {
       ES es;
@@ -1244,15 +1333,20 @@ __global__ void __launch_bounds__(BLOCK, 3) k_cdf_sys(FilterArgs<R> a, uint64_t*
       for (int e = 0; e < SCAN_PER; ++e)
         if (base + e < n) a.Q[base + e] = o + W[e];
     }
-    // systematic walk of this thread's particles from its first slot
+    // systematic walk of this thread's particles from its first slot, with
+    // their CDF values staged in this thread's shared-memory row (a rolled
+    // loop: the walk's code stays small)
+    uint64_t* const qrow = s_keep + threadIdx.x * (SCAN_PER + 1);
+#pragma unroll
+    for (int e = 0; e < SCAN_PER; ++e) qrow[e] = o + W[e];
     if (T > 0 && base < n) {
       uint64_t j = base == 0 ? 0 : sys_first_slot(o, n, r, dv);
       U128 KB = add128(mul64x32(T, (uint32_t)j), r);
-#pragma unroll
-      for (int e = 0; e < SCAN_PER; ++e) {
+      const int ecount = base + SCAN_PER <= n ? SCAN_PER : (int)(n - base);
+#pragma unroll 1
+      for (int e = 0; e < ecount; ++e) {
         const uint64_t i = base + e;
-        if (i >= n) continue;
-        const uint64_t qi = o + W[e];
+        const uint64_t qi = qrow[e];
         const U128 KQ = mul64x32(qi, (uint32_t)n);
         int emitted = 0;
         while (j < n && lt128(KB, KQ)) {

@@ -99,6 +99,14 @@ def test_full_size_2p20_fp32(pf, orc, scheme):
     _run(pf, orc, 1 << 20, 3, scheme, 0, every_step=False, seed=1639)
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_systematic_cdf_several_tiles_per_cta(pf, orc, prec):
+    """Above about 2.5M particles each CTA of the cooperative CDF launch owns
+    several tiles and stages them through shared memory by TMA; ragged last
+    tile, FP32 and FP64."""
+    _run(pf, orc, 3_000_001, 3, 1, prec, every_step=True, seed=77)
+
+
 def test_outlier_observation(pf, orc):
     """y far from every particle: most quantised weights underflow to zero."""
     y = np.array([0.3, 40.0, 40.5, -3.0, 0.0])
