@@ -292,8 +292,13 @@ pf_status enqueue_cycle(pf_filter* f, KTimer* tm = nullptr) {
     pf_status st = launch_resample(f->scheme, pa, n, f->I, f->splits, s, tm);
     if (st != PF_OK) return st;
   }
-  if (f->learn) k_propagate<R, true><<<f->prop_grid, BLOCK, 0, s>>>(a);
-  else k_propagate<R, false><<<f->prop_grid, BLOCK, 0, s>>>(a);
+  if constexpr (sizeof(R) == 4) {  // binary32: two slots per thread, paired arithmetic
+    if (f->learn) k_propagate2<true><<<f->prop_grid, BLOCK, 0, s>>>(a);
+    else k_propagate2<false><<<f->prop_grid, BLOCK, 0, s>>>(a);
+  } else {
+    if (f->learn) k_propagate<R, true><<<f->prop_grid, BLOCK, 0, s>>>(a);
+    else k_propagate<R, false><<<f->prop_grid, BLOCK, 0, s>>>(a);
+  }
   mark(tm, "propagate", s);
   CK(cudaGetLastError());
   return PF_OK;
@@ -482,10 +487,11 @@ pf_status pf_create(const pf_config* cfg, pf_filter** out) {
       e = f->learn ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_propagate<double, true>, BLOCK, 0)
                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_propagate<double, false>, BLOCK, 0);
     else
-      e = f->learn ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_propagate<float, true>, BLOCK, 0)
-                   : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_propagate<float, false>, BLOCK, 0);
+      e = f->learn ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_propagate2<true>, BLOCK, 0)
+                   : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_propagate2<false>, BLOCK, 0);
     if (e != cudaSuccess || per_sm < 1 || sms < 1) return bail(set_err(PF_ERR_CUDA, "occupancy query failed"));
-    const uint64_t want = cdiv(n, BLOCK), cap = (uint64_t)per_sm * (uint64_t)sms;
+    const uint64_t want = cdiv(n, f->fp64 ? (uint64_t)BLOCK : 2ull * BLOCK),
+                   cap = (uint64_t)per_sm * (uint64_t)sms;
     f->prop_grid = (unsigned)(want < cap ? want : cap);
     if (f->scheme == PF_SYSTEMATIC) {
       // cooperative grid: every CTA resident at once (it waits on the others)

@@ -468,6 +468,165 @@ __device__ __forceinline__ void theta_draws_rk(const uint32_t* rk, uint32_t filt
 }
 
 // ---------------------------------------------------------------------------
+// Paired binary32 arithmetic for two particles at once (sm_100+ FADD2 /
+// FMUL2 / FFMA2: one instruction, two independently rounded IEEE results).
+// Each function below performs, lane by lane, exactly the operation sequence
+// of its scalar counterpart above, so the two lanes' results are the scalar
+// results bit for bit.  Division, square root, comparisons and integer
+// conversions stay per lane.
+// ---------------------------------------------------------------------------
+// Additions stay scalar, one add.rn per lane: ptxas contracts a paired
+// mul.rn feeding a paired addition (add.rn.f32x2, or an fma.rn.f32x2 with a
+// unit factor) into one fused FFMA2 -- a different rounding -- even with
+// contraction disabled, which scalar add.rn never allows.  Products and
+// true fused multiply-adds (the Horner steps) are paired.
+__device__ __forceinline__ float2 splat2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\t"
+      "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%6, %7};\n\t"
+      "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return d;
+}
+__device__ __forceinline__ float2 add2(float2 a, float2 b) {
+  return make_float2(__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y));
+}
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+  return make_float2(__fsub_rn(a.x, b.x), __fsub_rn(a.y, b.y));
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+      "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "mul.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+
+__device__ __forceinline__ float2 unif_f32_2(uint32_t w0, uint32_t w1) {
+  const float2 fm = sub2(make_float2(__uint_as_float(0x4B000000u | (w0 >> 9)),
+                                     __uint_as_float(0x4B000000u | (w1 >> 9))),
+                         splat2(8388608.0f));
+  const float2 a = mul2(fm, splat2(0x1p-23f));
+  return add2(a, splat2(0x1p-24f));
+}
+
+// det_log on two positive values
+__device__ __forceinline__ float2 det_log2(float2 x) {
+  int e0, e1;
+  float f0, f1;
+  {
+    const uint32_t b = __float_as_uint(x.x);
+    if ((b & 0x7f800000u) != 0) {
+      e0 = (int)(b >> 23) - 126;
+      f0 = __uint_as_float((b & 0x807fffffu) | 0x3f000000u);
+    } else {
+      f0 = frexpf(x.x, &e0);
+    }
+  }
+  {
+    const uint32_t b = __float_as_uint(x.y);
+    if ((b & 0x7f800000u) != 0) {
+      e1 = (int)(b >> 23) - 126;
+      f1 = __uint_as_float((b & 0x807fffffu) | 0x3f000000u);
+    } else {
+      f1 = frexpf(x.y, &e1);
+    }
+  }
+  float2 f = make_float2(f0, f1);
+  const float2 f2 = mul2(f, splat2(2.0f));
+  if (f.x < Cst<float>::SQRT_HALF) { f.x = f2.x; e0 = e0 - 1; }
+  if (f.y < Cst<float>::SQRT_HALF) { f.y = f2.y; e1 = e1 - 1; }
+  const float2 num = sub2(f, splat2(1.0f));
+  const float2 den = add2(f, splat2(1.0f));
+  const float2 z = make_float2(num.x / den.x, num.y / den.y);
+  const float2 z2 = mul2(z, z);
+  float2 p = splat2(0x1.c71c72p-4f);
+  p = fma2(p, z2, splat2(0x1.24924ap-3f));
+  p = fma2(p, z2, splat2(0x1.99999ap-3f));
+  p = fma2(p, z2, splat2(0x1.555556p-2f));
+  p = fma2(p, z2, splat2(1.0f));
+  const float2 two_z = mul2(z, splat2(2.0f));
+  const float2 lf = mul2(two_z, p);
+  const float2 el = mul2(make_float2(small_int_to_f32(e0), small_int_to_f32(e1)),
+                         splat2(Cst<float>::LN2));
+  return add2(el, lf);
+}
+
+__device__ __forceinline__ float2 cos_poly2(float2 x) {
+  const float2 x2 = mul2(x, x);
+  float2 p = splat2(-0x1.27e4fcp-22f);
+  p = fma2(p, x2, splat2(0x1.a01a02p-16f));
+  p = fma2(p, x2, splat2(-0x1.6c16c2p-10f));
+  p = fma2(p, x2, splat2(0x1.555556p-5f));
+  p = fma2(p, x2, splat2(-0x1p-1f));
+  p = fma2(p, x2, splat2(0x1p+0f));
+  return p;
+}
+__device__ __forceinline__ float2 sin_poly2(float2 x) {
+  const float2 x2 = mul2(x, x);
+  float2 p = splat2(0x1.71de3ap-19f);
+  p = fma2(p, x2, splat2(-0x1.a01a02p-13f));
+  p = fma2(p, x2, splat2(0x1.111112p-7f));
+  p = fma2(p, x2, splat2(-0x1.555556p-3f));
+  p = fma2(p, x2, splat2(0x1p+0f));
+  return mul2(x, p);
+}
+
+// det_sincos2pi on two values of [0, 1]
+__device__ __forceinline__ void det_sincos2pi2(float2 u, float2* s_out, float2* c_out) {
+  const float2 ru = make_float2(u.x > 0.5f ? 1.0f : 0.0f, u.y > 0.5f ? 1.0f : 0.0f);
+  const float2 v = sub2(u, ru);
+  const float2 w = make_float2(fabsf(v.x), fabsf(v.y));
+  const float2 h = sub2(splat2(0.5f), w);
+  const float2 q = sub2(splat2(0.25f), w);
+  const bool o1x = w.x <= 0.125f, o3x = w.x > 0.375f;
+  const bool o1y = w.y <= 0.125f, o3y = w.y > 0.375f;
+  const float2 a = make_float2(o1x ? w.x : (o3x ? h.x : q.x), o1y ? w.y : (o3y ? h.y : q.y));
+  const float2 x = mul2(splat2(Cst<float>::TWO_PI), a);
+  const float2 S = sin_poly2(x);
+  const float2 C = cos_poly2(x);
+  const float svx = (o1x || o3x) ? S.x : C.x, svy = (o1y || o3y) ? S.y : C.y;
+  *s_out = make_float2(v.x < 0.0f ? -svx : svx, v.y < 0.0f ? -svy : svy);
+  *c_out = make_float2(o1x ? C.x : (o3x ? -C.x : S.x), o1y ? C.y : (o3y ? -C.y : S.y));
+}
+
+// the propagation draws (theta_draws_rk) of two slots j0, j1
+__device__ __forceinline__ void theta_draws2(const uint32_t* rk, uint32_t filter, uint32_t t,
+                                             uint32_t j0, uint32_t j1, float2* Zx, float2* Zs,
+                                             float2* Us, float2* Zt, float2* Ut) {
+  const U4 A0 = philox_rk(j0, t, filter, P_STATE, rk);
+  const U4 A1 = philox_rk(j1, t, filter, P_STATE, rk);
+  const U4 B0 = philox_rk(j0, t, filter, P_STATE | (1u << 8), rk);
+  const U4 B1 = philox_rk(j1, t, filter, P_STATE | (1u << 8), rk);
+  {
+    const float2 u1 = unif_f32_2(A0.a, A1.a);
+    const float2 u2 = unif_f32_2(A0.b, A1.b);
+    const float2 L = det_log2(u1);
+    const float2 m2 = mul2(L, splat2(-2.0f));
+    const float2 r = make_float2(sqrtf(m2.x), sqrtf(m2.y));
+    float2 sn, cs;
+    det_sincos2pi2(u2, &sn, &cs);
+    *Zx = mul2(r, cs);
+    *Zs = mul2(r, sn);
+    *Us = unif_f32_2(A0.c, A1.c);
+  }
+  {
+    const float2 u1 = unif_f32_2(B0.a, B1.a);
+    const float2 u2 = unif_f32_2(B0.b, B1.b);
+    const float2 L = det_log2(u1);
+    const float2 m2 = mul2(L, splat2(-2.0f));
+    const float2 r = make_float2(sqrtf(m2.x), sqrtf(m2.y));
+    float2 sn, cs;
+    det_sincos2pi2(u2, &sn, &cs);
+    *Zt = mul2(r, cs);
+    *Ut = unif_f32_2(B0.c, B1.c);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // 128-bit unsigned helpers (hi, lo).
 // ---------------------------------------------------------------------------
 struct U128 {

@@ -1592,6 +1592,137 @@ __global__ void __launch_bounds__(BLOCK, 5) k_propagate(FilterArgs<R> a) {
 }
 
 // ---------------------------------------------------------------------------
+// k_propagate for binary32 state, two slots per thread per pass: slots j and
+// j + G (G = the grid's thread count) share each paired FADD2 / FMUL2 / FFMA2,
+// while divisions, square roots, comparisons and the fixed-point statistics
+// run per lane.  Per slot the operations are those of k_propagate, in the
+// same order, so the results are the same bits.
+// ---------------------------------------------------------------------------
+constexpr uint32_t WQ2_CAP = 160;  // 31 queued + 4 pushes of 32 per pass
+
+template <bool LEARN>
+__global__ void __launch_bounds__(BLOCK, 3) k_propagate2(FilterArgs<float> a) {
+  __shared__ GammaItem<float> s_q[WARPS][WQ2_CAP];
+  const Ctl* c = a.ctl;
+  const uint32_t t = c->t;
+  const StateV<float> src = (t & 1) ? a.st[1] : a.st[0];
+  const StateV<float> dst = (t & 1) ? a.st[0] : a.st[1];
+  const float yr = c->yf, ds = c->mtf[0], cs = c->mtf[1], dt = c->mtf[2], ct = c->mtf[3];
+  const int lane = threadIdx.x & 31;
+  GammaItem<float>* const wq = s_q[threadIdx.x >> 5];
+  uint32_t qn = 0;  // warp-uniform
+  const uint64_t n = a.n;
+  const uint64_t half = (uint64_t)gridDim.x * BLOCK;
+  const uint64_t stride = 2 * half;
+  const uint64_t iters = (n + stride - 1) / stride;
+  auto clampi = [&](uint32_t v) { return v < n ? v : (uint32_t)(n - 1); };
+  bool fail = false;
+  auto finish = [&](const GammaItem<float>& itm) {
+    const bool sig = itm.which == 0;
+    const float G = gamma_mt_from<float>(sig ? ds : dt, sig ? cs : ct, itm.Z, itm.U, a.seed,
+                                         a.filter, t, itm.j, sig ? P_GAMMA_SIGMA : P_GAMMA_TAU,
+                                         &fail);
+    const float v = SuffOps<float>::ig(itm.b, G);
+    if (sig) dst.s2[itm.j] = v;
+    else dst.t2[itm.j] = v;
+  };
+  uint64_t j0 = (uint64_t)blockIdx.x * BLOCK + threadIdx.x;
+  Gathered<float> c0 = gather_rec<float>(src, j0 < n ? clampi(a.anc[j0]) : 0u);
+  Gathered<float> c1 = gather_rec<float>(src, j0 + half < n ? clampi(a.anc[j0 + half]) : 0u);
+  for (uint64_t it = 0; it < iters; ++it, j0 += stride) {
+    const uint64_t j1 = j0 + half;
+    const bool v0 = j0 < n, v1 = j1 < n;
+    // the next pass's records, gathered ahead
+    const uint64_t k0 = j0 + stride, k1 = j1 + stride;
+    const Gathered<float> n0 = gather_rec<float>(src, k0 < n ? clampi(a.anc[k0]) : 0u);
+    const Gathered<float> n1 = gather_rec<float>(src, k1 < n ? clampi(a.anc[k1]) : 0u);
+    const float2 xa = make_float2(c0.x, c1.x), sa = make_float2(c0.s2, c1.s2);
+    const float2 ta = make_float2(c0.t2, c1.t2);
+    const float2 sm = add2(sa, ta);
+    const float2 p = mul2(sa, ta);
+    const float2 V = make_float2(p.x / sm.x, p.y / sm.y);
+    const float2 m1 = mul2(xa, sa);
+    const float2 m2 = mul2(splat2(yr), ta);
+    const float2 nn = add2(m1, m2);
+    const float2 mu = make_float2(nn.x / sm.x, nn.y / sm.y);
+    const float2 sv = make_float2(sqrtf(V.x), sqrtf(V.y));
+    float2 Z, Zs, Us, Zt, Ut;
+    theta_draws2(a.rk, a.filter, t, (uint32_t)j0, (uint32_t)j1, &Z, &Zs, &Us, &Zt, &Ut);
+    const float2 xz = mul2(sv, Z);
+    const float2 xj = add2(mu, xz);
+    if (v0) dst.x[j0] = xj.x;
+    if (v1) dst.x[j1] = xj.y;
+    bool ds0 = false, dt0 = false, ds1 = false, dt1 = false;
+    uint64_t bs0 = 0, bt0 = 0, bs1 = 0, bt1 = 0;
+    if (LEARN) {
+      const float2 rs = sub2(splat2(yr), xj);
+      const float2 rt = sub2(xj, xa);
+      // b + (r^2 / 2) in 2^-32 fixed point, per SuffOps<float>::add_half_square
+      const float2 hs = mul2(splat2(0.5f), mul2(rs, rs));
+      const float2 ht = mul2(splat2(0.5f), mul2(rt, rt));
+      const float2 ws = mul2(hs, splat2(0x1p32f));
+      const float2 wt = mul2(ht, splat2(0x1p32f));
+      bool f0 = false, f1 = false;
+      auto addb = [&](uint64_t b, float v, bool* f) -> uint64_t {
+        if (!(v < 0x1p63f)) {
+          *f = true;
+          return b;
+        }
+        return b + f2u64_rz(v);
+      };
+      bs0 = addb(c0.bs, ws.x, &f0);
+      bt0 = addb(c0.bt, wt.x, &f0);
+      bs1 = addb(c1.bs, ws.y, &f1);
+      bt1 = addb(c1.bt, wt.y, &f1);
+      fail |= (v0 && f0) || (v1 && f1);
+      if (v0) { dst.bs[j0] = bs0; dst.bt[j0] = bt0; }
+      if (v1) { dst.bs[j1] = bs1; dst.bt[j1] = bt1; }
+      // Marsaglia-Tsang squeeze for sigma^2 (x lanes: slot j0, j1) and tau^2
+      const float2 czs = mul2(splat2(cs), Zs), czt = mul2(splat2(ct), Zt);
+      const float2 vs = add2(splat2(1.0f), czs), vt = add2(splat2(1.0f), czt);
+      const float2 v3s = mul2(mul2(vs, vs), vs), v3t = mul2(mul2(vt, vt), vt);
+      const float2 Z2s = mul2(Zs, Zs), Z2t = mul2(Zt, Zt);
+      const float2 thrs = sub2(splat2(1.0f), mul2(splat2(Cst<float>::SQUEEZE), mul2(Z2s, Z2s)));
+      const float2 thrt = sub2(splat2(1.0f), mul2(splat2(Cst<float>::SQUEEZE), mul2(Z2t, Z2t)));
+      const float2 Gs = mul2(splat2(ds), v3s), Gt = mul2(splat2(dt), v3t);
+      const bool as0 = vs.x > 0.0f && Us.x < thrs.x, as1 = vs.y > 0.0f && Us.y < thrs.y;
+      const bool at0 = vt.x > 0.0f && Ut.x < thrt.x, at1 = vt.y > 0.0f && Ut.y < thrt.y;
+      // inverse gamma: (b 2^-32) / G, per SuffOps<float>::ig
+      const float2 bsf = mul2(make_float2(u64_to_f32_rn(bs0), u64_to_f32_rn(bs1)), splat2(0x1p-32f));
+      const float2 btf = mul2(make_float2(u64_to_f32_rn(bt0), u64_to_f32_rn(bt1)), splat2(0x1p-32f));
+      if (v0) {
+        if (as0) dst.s2[j0] = bsf.x / Gs.x;
+        else ds0 = true;
+        if (at0) dst.t2[j0] = btf.x / Gt.x;
+        else dt0 = true;
+      }
+      if (v1) {
+        if (as1) dst.s2[j1] = bsf.y / Gs.y;
+        else ds1 = true;
+        if (at1) dst.t2[j1] = btf.y / Gt.y;
+        else dt1 = true;
+      }
+      wq_push<float>(wq, qn, ds0, GammaItem<float>{bs0, Zs.x, Us.x, (uint32_t)j0, 0u}, lane);
+      wq_push<float>(wq, qn, dt0, GammaItem<float>{bt0, Zt.x, Ut.x, (uint32_t)j0, 1u}, lane);
+      wq_push<float>(wq, qn, ds1, GammaItem<float>{bs1, Zs.y, Us.y, (uint32_t)j1, 0u}, lane);
+      wq_push<float>(wq, qn, dt1, GammaItem<float>{bt1, Zt.y, Ut.y, (uint32_t)j1, 1u}, lane);
+      wq_drain<float>(wq, qn, 32u, lane, finish);
+    } else {
+      if (v0) { dst.s2[j0] = sa.x; dst.t2[j0] = ta.x; dst.bs[j0] = c0.bs; dst.bt[j0] = c0.bt; }
+      if (v1) { dst.s2[j1] = sa.y; dst.t2[j1] = ta.y; dst.bs[j1] = c1.bs; dst.bt[j1] = c1.bt; }
+    }
+    c0 = n0;
+    c1 = n1;
+  }
+  if (LEARN) wq_drain<float>(wq, qn, 1u, lane, finish);
+  if (__any_sync(0xffffffffu, fail) && lane == 0) atomicOr(&a.ctl->err, ERR_NUMERIC);
+  bool last = false;
+  if (lane == 0) last = atomicAdd(&a.ctl->done_prop, 1u) == gridDim.x * WARPS - 1;
+  last = __shfl_sync(0xffffffffu, last, 0);
+  if (last) fold_cycle_warp<float>(a, t);
+}
+
+// ---------------------------------------------------------------------------
 // Posterior summaries (on demand): population means and variances of x,
 // sigma^2 and tau^2.  Per block: sums of v - c and (v - c)^2 with c the value
 // of particle 0 (shift against cancellation), accumulated in binary64 across
