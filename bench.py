@@ -17,7 +17,10 @@ roofline: the dominant kernel's algorithmic bytes per launch / its mean
          CUDA-event duration (pf_step_profiled), against the measured copy
          bandwidth in MEASURED_PEAKS.json.
 Extra keys: the same cycle at N = 2^24 (the single-filter target size) and
-with multinomial resampling.
+with multinomial resampling; batched filters (4096 uneven filters, one
+persistent launch per cycle, against per-filter launches); the served form
+(10,000 streams under Poisson load, continuous batching, p50/p90/p99 latency;
+and under an 8 GB budget where admission waits); FP32 against FP64 precision.
 
 --impl reference times the CPU oracle (single-threaded) on a bounded sample of
 the same workload.  Under torchrun every rank runs its own independent filter
