@@ -421,7 +421,8 @@ pf_status pf_create(const pf_config* cfg, pf_filter** out) {
     if ((st = dev_alloc(f, (size_t)f->ntiles * 8, (void**)&f->stat_w[p])) != PF_OK) return bail(st);
     if ((st = dev_alloc(f, (size_t)f->ntiles * 8, (void**)&f->stat_e[p])) != PF_OK) return bail(st);
   }
-  if ((st = dev_alloc(f, n * rs, &f->ell)) != PF_OK) return bail(st);
+  // l is moved by 16-byte bulk copies: its tail is padded to 16 bytes
+  if ((st = dev_alloc(f, (n * rs + 15) & ~(size_t)15, &f->ell)) != PF_OK) return bail(st);
   if ((st = dev_alloc(f, n * 8, (void**)&f->Q)) != PF_OK) return bail(st);
   if (is_multinomial(f->scheme) && (st = dev_alloc(f, (n + 1) * 8, (void**)&f->S)) != PF_OK) return bail(st);
   if ((st = dev_alloc(f, n * 4, (void**)&f->anc)) != PF_OK) return bail(st);

@@ -249,7 +249,7 @@ __device__ __forceinline__ R block_max(R v, R* s_red) {
 constexpr int W_PER_THREAD = 4;
 
 template <class R>
-__global__ void __launch_bounds__(BLOCK) k_weights(FilterArgs<R> a) {
+__global__ void __launch_bounds__(BLOCK, sizeof(R) == 4 ? 8 : 4) k_weights(FilterArgs<R> a) {
   __shared__ R s_red[WARPS];
   __shared__ R s_y;
   const uint32_t t = a.ctl->t;
@@ -1098,6 +1098,42 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   return false;
 }
 
+// copy `bytes` (a multiple of 16; both addresses 16-byte aligned) from
+// shared to global memory as one bulk async-group
+__device__ __forceinline__ void tma_store_1d(void* dst, const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;"
+               ::"l"(dst), "r"(smem_u32(src)), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+// wait until this thread's bulk stores have read their shared-memory source
+__device__ __forceinline__ void bulk_wait_read() {
+  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+// wait until this thread's bulk stores are complete
+__device__ __forceinline__ void bulk_wait_done() {
+  asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+
+// W = min(floor(e 2^k), 2^k) from e = exp(dl) as quant_exp returns it: e is
+// 0 or a normal number p 2^n, so e 2^k and p 2^(n + k) have the same bits
+// and the floor is the one quant_exp takes.
+__device__ __forceinline__ uint64_t quant_from_e(float e, int k) {
+  uint64_t W = 0;
+  if (e != 0.0f) {
+    const uint32_t eb = __float_as_uint(e);
+    const int sh = (int)(eb >> 23) - 150 + k;
+    const uint32_t m24 = (eb & 0x7fffffu) | 0x800000u;
+    W = sh >= 0 ? ((uint64_t)m24 << sh) : (uint64_t)(m24 >> (-sh < 31 ? -sh : 31));
+  }
+  const uint64_t cap = 1ull << k;
+  return W > cap ? cap : W;
+}
+__device__ __forceinline__ uint64_t quant_from_e(double e, int k) {
+  const uint64_t W = e != 0.0 ? f2u64_rz(e * pow2d(k)) : 0ull;
+  const uint64_t cap = 1ull << k;
+  return W > cap ? cap : W;
+}
+
 // ---------------------------------------------------------------------------
 // The CDF and systematic resampling in one cooperative launch (Steps 1b-1c
 // of the cycle for the systematic scheme).  Every CTA owns a contiguous range
@@ -1160,6 +1196,7 @@ __global__ void __launch_bounds__(BLOCK, STAGED ? 3 : 4) k_cdf_sys(FilterArgs<R>
     const uint64_t first = (uint64_t)tile * TILE;
     const uint64_t cnt = n - first < (uint64_t)TILE ? n - first : (uint64_t)TILE;
     const uint32_t bytes = (uint32_t)((cnt * sizeof(R) + 15) & ~(uint64_t)15);
+    bulk_wait_read();  // the buffer's last bulk store has read it
     fence_proxy_async_smem();
     tma_load_1d(s_ell[q_issued & 1], a.ell + first, bytes, &s_bar[q_issued & 1]);
   };
@@ -1178,10 +1215,13 @@ __global__ void __launch_bounds__(BLOCK, STAGED ? 3 : 4) k_cdf_sys(FilterArgs<R>
     ++q_done;
     return s_ell[b];
   };
-  // this thread's 16 weights of tile `tile` (l staged in buf) quantised
-  auto quant16 = [&](uint32_t tile, const R* buf, uint64_t* W, R* epart) {
+  // this thread's 16 weights of tile `tile` quantised, as inclusive running
+  // sums W and the partial sum of e = exp(l - m).  mode 0: from l in buf;
+  // 1: from l in buf (shared memory), writing e back in its place; 2: from e
+  // in buf (written back by phase 1).
+  auto quant16 = [&](uint32_t tile, const R* buf, uint64_t* W, R* epart, int mode) {
     const uint64_t base = (uint64_t)tile * TILE + (uint64_t)threadIdx.x * SCAN_PER;
-    const R* row = buf + threadIdx.x * SCAN_PER;
+    R* const row = const_cast<R*>(buf) + threadIdx.x * SCAN_PER;
     const bool full = base + SCAN_PER <= n;
     uint64_t run = 0;
     R ep = (R)0;
@@ -1201,17 +1241,32 @@ __global__ void __launch_bounds__(BLOCK, STAGED ? 3 : 4) k_cdf_sys(FilterArgs<R>
 #pragma unroll
         for (int e = 0; e < 4; ++e) v[e] = (base + 4 * q + e < n) ? row[4 * q + e] : (R)0;
       }
+      R ex4[4];
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         uint64_t w = 0;
+        R ex = (R)0;
         if (full || base + 4 * q + e < n) {
-          R ex;
-          const R dl = v[e] - m;
-          w = quant_exp<R>(dl, k, &ex);
+          if (mode == 2) {
+            ex = v[e];
+            w = quant_from_e(ex, k);
+          } else {
+            const R dl = v[e] - m;
+            w = quant_exp<R>(dl, k, &ex);
+          }
           ep = ep + ex;
         }
+        ex4[e] = ex;
         run += w;
         W[4 * q + e] = run;  // inclusive running sum
+      }
+      if (mode == 1) {
+        if constexpr (sizeof(R) == 4) {
+          *reinterpret_cast<float4*>(row + 4 * q) = make_float4(ex4[0], ex4[1], ex4[2], ex4[3]);
+        } else {
+          *reinterpret_cast<double2*>(row + 4 * q) = make_double2(ex4[0], ex4[1]);
+          *reinterpret_cast<double2*>(row + 4 * q + 2) = make_double2(ex4[2], ex4[3]);
+        }
       }
     }
     *epart = ep;
@@ -1233,11 +1288,11 @@ __global__ void __launch_bounds__(BLOCK, STAGED ? 3 : 4) k_cdf_sys(FilterArgs<R>
   if (tb < te) next_issue(tb);
   for (uint32_t tile = tb; tile < te; ++tile) {
     if (tile + 1 < te) next_issue(tile + 1);
-    else if (tile + 1 == te && tb + 1 < te) next_issue(tb + 1);  // phase 2's first tile
     const R* buf = take_tile(tile);
     uint64_t W[SCAN_PER];
     R ep;
-    quant16(tile, buf, W, &ep);
+    quant16(tile, buf, W, &ep, STAGED ? 1 : 0);
+    if (STAGED) fence_proxy_async_smem();  // e in buf, for the bulk store below
     mine += W[SCAN_PER - 1];
     if (tile == tb) {
 #pragma unroll
@@ -1245,12 +1300,23 @@ __global__ void __launch_bounds__(BLOCK, STAGED ? 3 : 4) k_cdf_sys(FilterArgs<R>
       s_keep_ep[threadIdx.x] = ep;
     }
     __syncthreads();  // buf is refilled two copies later
+    if (STAGED && tile != tb && threadIdx.x == 0) {
+      // e goes back to l's place in global memory for phase 2, which then
+      // needs no exponentials (the first tile's W stay in shared memory)
+      const uint64_t first = (uint64_t)tile * TILE;
+      const uint64_t cnt = n - first < (uint64_t)TILE ? n - first : (uint64_t)TILE;
+      tma_store_1d(a.ell + first, buf, (uint32_t)((cnt * sizeof(R) + 15) & ~(uint64_t)15));
+    }
   }
   mine = block_sum(mine);
   if (threadIdx.x == 0) {
     st_status(&cta_tot[blockIdx.x], mine);
     __threadfence();
     atomicAdd(&c->gbar, 1u);
+    if (STAGED && tb + 1 < te) {  // phase 2's first tile from HBM: e stored, complete
+      bulk_wait_done();
+      issue(tb + 1);
+    }
     uint32_t spins = 0;
     while (ld_volatile_u32(&c->gbar) < gridDim.x) {
       if (++spins > SPIN_LIMIT) {
@@ -1262,6 +1328,7 @@ __global__ void __launch_bounds__(BLOCK, STAGED ? 3 : 4) k_cdf_sys(FilterArgs<R>
     __threadfence();
   }
   __syncthreads();
+  if (STAGED && tb + 1 < te) ++q_issued;  // the copy thread 0 issued above
 
   // phase 2: this CTA's exclusive prefix and the total T
   uint64_t pre = 0, all = 0;
@@ -1294,7 +1361,7 @@ __global__ void __launch_bounds__(BLOCK, STAGED ? 3 : 4) k_cdf_sys(FilterArgs<R>
     } else {
       if (tile + 1 < te) next_issue(tile + 1);
       const R* buf = take_tile(tile);
-      quant16(tile, buf, W, &ep);
+      quant16(tile, buf, W, &ep, 2);
     }
     {
       ES es;
@@ -1333,43 +1400,55 @@ __global__ void __launch_bounds__(BLOCK, STAGED ? 3 : 4) k_cdf_sys(FilterArgs<R>
       for (int e = 0; e < SCAN_PER; ++e)
         if (base + e < n) a.Q[base + e] = o + W[e];
     }
-    // systematic walk of this thread's particles from its first slot, with
-    // their CDF values staged in this thread's shared-memory row (a rolled
-    // loop: the walk's code stays small)
-    uint64_t* const qrow = s_keep + threadIdx.x * (SCAN_PER + 1);
+    // systematic walk of this thread's particles, flattened: every step
+    // either gives slot j to the current particle i or moves on to i + 1, so
+    // the lanes of a warp stay converged.  D = n Q_i - (j T + r): slot j
+    // goes to i while D > 0.  Before a move D lies in (-T, 0] and a move adds
+    // n w_{i+1} <= n 2^k <= 2^61 (T <= 2^61 too), so D is an int64 and a step
+    // is one 64-bit addition.  The row holds n w for this thread's particles.
+    uint64_t* const nwrow = s_keep + threadIdx.x * (SCAN_PER + 1);
+    {
+      uint64_t prev = 0;
 #pragma unroll
-    for (int e = 0; e < SCAN_PER; ++e) qrow[e] = o + W[e];
+      for (int e = 0; e < SCAN_PER; ++e) {
+        nwrow[e] = (W[e] - prev) * n;
+        prev = W[e];
+      }
+    }
     if (T > 0 && base < n) {
-      uint64_t j = base == 0 ? 0 : sys_first_slot(o, n, r, dv);
-      U128 KB = add128(mul64x32(T, (uint32_t)j), r);
-      const int ecount = base + SCAN_PER <= n ? SCAN_PER : (int)(n - base);
+      const uint32_t i0 = (uint32_t)base;
+      const uint32_t iend = i0 + (base + SCAN_PER <= n ? (uint32_t)SCAN_PER : (uint32_t)(n - base));
+      uint32_t j = base == 0 ? 0u : (uint32_t)sys_first_slot(o, n, r, dv);
+      const U128 X = mul64x32(o, (uint32_t)n);
+      const U128 KB = add128(mul64x32(T, j), r);
+      int64_t D = (int64_t)(X.lo - KB.lo) + (int64_t)nwrow[0];
+      uint32_t i = i0, emitted = 0;
 #pragma unroll 1
-      for (int e = 0; e < ecount; ++e) {
-        const uint64_t i = base + e;
-        const uint64_t qi = qrow[e];
-        const U128 KQ = mul64x32(qi, (uint32_t)n);
-        int emitted = 0;
-        while (j < n && lt128(KB, KQ)) {
-          if (emitted == SYS_CAP) {  // a heavy particle: its other slots become a run
-            uint64_t Rr = sys_first_slot(qi, n, r, dv);
-            Rr = Rr < j ? j : Rr;
-            const uint32_t kr = atomicAdd(&s_nruns, 1u);
-            if (kr < BB_RUNS) {
-              s_run[kr][0] = (uint32_t)j;
-              s_run[kr][1] = (uint32_t)Rr;
-              s_run[kr][2] = (uint32_t)i;
-            } else {
-              for (uint64_t q = j; q < Rr; ++q) a.anc[q] = (uint32_t)i;
-            }
-            j = Rr;
-            KB = add128(mul64x32(T, (uint32_t)j), r);
-            break;
+      while (true) {
+        const bool emit = D > 0;
+        if (emit && emitted == SYS_CAP) {  // a heavy particle: its other slots become a run
+          const uint64_t cnt = sys_floor_div(U128{0, (uint64_t)D - 1}, dv) + 1;
+          const uint32_t Rr = j + (uint32_t)cnt;
+          const uint32_t kr = atomicAdd(&s_nruns, 1u);
+          if (kr < BB_RUNS) {
+            s_run[kr][0] = j;
+            s_run[kr][1] = Rr;
+            s_run[kr][2] = i;
+          } else {
+            for (uint32_t q = j; q < Rr; ++q) a.anc[q] = i;
           }
-          a.anc[j] = (uint32_t)i;
-          ++j;
-          KB = add128(KB, T);
-          ++emitted;
+          D -= (int64_t)(cnt * T);
+          j = Rr;
+          continue;  // D <= 0 now: the next step moves on
         }
+        if (emit) a.anc[j] = i;
+        const uint32_t inext = i + 1;
+        const int64_t nwn = (int64_t)nwrow[(inext < iend ? inext : i) - i0];
+        D += emit ? -(int64_t)T : nwn;
+        j += emit ? 1u : 0u;
+        emitted = emit ? emitted + 1u : 0u;
+        i = emit ? i : inext;
+        if (i == iend) break;
       }
     }
     __syncthreads();
