@@ -127,7 +127,10 @@ pf_status pf_create(const pf_config* cfg, pf_filter** out);
 pf_status pf_step(pf_filter* f, double y);
 
 /* Enqueue n_steps cycles for the observations y[0..n_steps) (host or device
- * pointer, binary64).  Replays a CUDA graph of one cycle. */
+ * pointer, binary64).  Replays a CUDA graph of one cycle; each launch carries
+ * its observation in the graph's weights-node arguments: a host value by
+ * value, a device observation by address, read when the cycle runs (so a
+ * device buffer must stay valid until the cycles have run, in stream order). */
 pf_status pf_run(pf_filter* f, const double* y, uint32_t n_steps);
 
 /* Reduce the particles to posterior summaries (paper Section 2) and copy

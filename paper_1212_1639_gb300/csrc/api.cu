@@ -45,9 +45,6 @@ int cdf_shift(uint64_t n) {
   return 61 - c;
 }
 
-constexpr uint32_t RING = 8192;          // observation ring (doubles)
-constexpr uint32_t RING_CHUNK = RING / 4;
-
 pf_status map_err(uint32_t err) {
   if (err & ERR_TIMEOUT) return set_err(PF_ERR_TIMEOUT, "device look-back wait timed out");
   if (err & ERR_WEIGHTS) return set_err(PF_ERR_NUMERIC, "weights negative, non-finite or all zero");
@@ -70,6 +67,8 @@ struct pf_filter {
   unsigned prop_grid = 0;  // persistent propagate grid
   unsigned cdf_grid = 0;   // cooperative CDF + systematic resampling grid (0: not used)
   bool cdf_staged = false; // its CTAs own several tiles: TMA-staged variant
+  int cdf_per = 16;         // particles per thread of its tiles (8: 2048-particle tiles)
+  uint32_t nparts = 0;      // log-ML partials per cycle
   uint64_t* cta_tot = nullptr;
   std::vector<void*> allocs;
   void* x[2] = {}; void* s2[2] = {}; void* t2[2] = {}; void* bs[2] = {}; void* bt[2] = {};
@@ -84,13 +83,15 @@ struct pf_filter {
   void* part = nullptr;
   double* part_est = nullptr;
   Ctl* ctl = nullptr;
-  double* y_ring = nullptr;
-  double* y_pinned = nullptr;
   Ctl* ctl_host = nullptr;  // pinned mirror for summaries
-  cudaEvent_t ring_ev[4] = {};
-  uint64_t host_t = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+  // the graph's weights node: each launch sets this cycle's observation in
+  // its arguments (no copy on the stream)
+  cudaGraphNode_t wnode = nullptr;
+  cudaKernelNodeParams wparams = {};
+  alignas(16) unsigned char wargs[sizeof(FilterArgs<double>)] = {};
+  void* wkp[1] = {};
   pf_status sticky = PF_OK;
 };
 
@@ -145,10 +146,11 @@ FilterArgs<R> filter_args(pf_filter* f) {
   a.part = f->part;
   a.part_est = f->part_est;
   a.ctl = f->ctl;
-  a.y_ring = f->y_ring;
-  a.cap = RING;
+  a.y_src = nullptr;
+  a.y_val = 0.0;
   a.n = f->n;
   a.ntiles = f->ntiles;
+  a.nparts = f->nparts;
   a.k = f->k;
   a.seed = f->cfg.seed;
   a.filter = f->cfg.filter_id;
@@ -225,9 +227,12 @@ pf_status launch_resample(int scheme, const PosArgs& pa, uint64_t n, uint32_t* I
 
 // One cycle (Steps 1-4), enqueued on f->stream; reads t and y on the device.
 template <class R>
-pf_status enqueue_cycle(pf_filter* f, KTimer* tm = nullptr) {
+pf_status enqueue_cycle(pf_filter* f, KTimer* tm = nullptr, const double* y_src = nullptr,
+                        double y_val = 0.0) {
   cudaStream_t s = f->stream;
   FilterArgs<R> a = filter_args<R>(f);
+  a.y_src = y_src;
+  a.y_val = y_val;
   const uint64_t n = f->n;
   if (tm) cudaEventRecord(tm->ev[0], s);
   k_weights<R><<<(unsigned)cdiv(n, (uint64_t)BLOCK * W_PER_THREAD), BLOCK, 0, s>>>(a);
@@ -285,8 +290,14 @@ pf_status enqueue_cycle(pf_filter* f, KTimer* tm = nullptr) {
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (f->cdf_staged) CK(cudaLaunchKernelEx(&cfg, k_cdf_sys<R, true>, a, f->cta_tot));
-    else CK(cudaLaunchKernelEx(&cfg, k_cdf_sys<R, false>, a, f->cta_tot));
+    if (f->cdf_staged) {
+      CK(cudaLaunchKernelEx(&cfg, k_cdf_sys<R, true, 16>, a, f->cta_tot));
+    } else if (f->cdf_per == 8) {
+      if constexpr (sizeof(R) == 4)
+        CK(cudaLaunchKernelEx(&cfg, k_cdf_sys<float, false, 8>, a, f->cta_tot));
+    } else {
+      CK(cudaLaunchKernelEx(&cfg, k_cdf_sys<R, false, 16>, a, f->cta_tot));
+    }
     mark(tm, "cdf_resample", s);
   } else {
     pf_status st = launch_resample(f->scheme, pa, n, f->I, f->splits, s, tm);
@@ -316,32 +327,42 @@ pf_status build_graph(pf_filter* f) {
   if (e != cudaSuccess) return set_err(PF_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
   f->graph = g;
   CK(cudaGraphInstantiate(&f->exec, g, 0));
+  size_t nn = 0;
+  CK(cudaGraphGetNodes(g, nullptr, &nn));
+  std::vector<cudaGraphNode_t> nodes(nn);
+  CK(cudaGraphGetNodes(g, nodes.data(), &nn));
+  const void* wfun = f->fp64 ? (const void*)k_weights<double> : (const void*)k_weights<float>;
+  for (cudaGraphNode_t nd : nodes) {
+    cudaGraphNodeType ty;
+    CK(cudaGraphNodeGetType(nd, &ty));
+    if (ty != cudaGraphNodeTypeKernel) continue;
+    cudaKernelNodeParams p;
+    CK(cudaGraphKernelNodeGetParams(nd, &p));
+    if (p.func != wfun) continue;
+    f->wnode = nd;
+    f->wparams = p;
+    std::memcpy(f->wargs, p.kernelParams[0], f->fp64 ? sizeof(FilterArgs<double>) : sizeof(FilterArgs<float>));
+    f->wkp[0] = f->wargs;
+    f->wparams.kernelParams = f->wkp;
+    f->wparams.extra = nullptr;
+  }
+  if (!f->wnode) return set_err(PF_ERR_CUDA, "graph capture: weights node not found");
   return PF_OK;
 }
 
-// Stage observations y[0..cnt) for device cycles host_t .. host_t+cnt-1 into
-// the ring (cnt never crosses a ring chunk boundary).
-pf_status stage_obs(pf_filter* f, const double* y, uint32_t cnt, bool dev_src) {
-  const uint32_t slot = (uint32_t)(f->host_t % RING);
-  const uint32_t chunk = slot / RING_CHUNK;
-  if (slot % RING_CHUNK == 0 && f->host_t >= RING) CK(cudaEventSynchronize(f->ring_ev[chunk]));
-  if (dev_src) {
-    CK(cudaMemcpyAsync(f->y_ring + slot, y, cnt * sizeof(double), cudaMemcpyDeviceToDevice, f->stream));
+// One cycle: the graph, with this cycle's observation in the weights node.
+pf_status launch_cycle(pf_filter* f, const double* y_src, double y_val) {
+  if (f->fp64) {
+    FilterArgs<double>* a = reinterpret_cast<FilterArgs<double>*>(f->wargs);
+    a->y_src = y_src;
+    a->y_val = y_val;
   } else {
-    std::memcpy(f->y_pinned + slot, y, cnt * sizeof(double));
-    CK(cudaMemcpyAsync(f->y_ring + slot, f->y_pinned + slot, cnt * sizeof(double),
-                       cudaMemcpyHostToDevice, f->stream));
+    FilterArgs<float>* a = reinterpret_cast<FilterArgs<float>*>(f->wargs);
+    a->y_src = y_src;
+    a->y_val = y_val;
   }
-  return PF_OK;
-}
-
-pf_status launch_cycles(pf_filter* f, uint32_t cnt) {
-  for (uint32_t i = 0; i < cnt; ++i) {
-    CK(cudaGraphLaunch(f->exec, f->stream));
-    f->host_t++;
-    if (f->host_t % RING_CHUNK == 0)
-      CK(cudaEventRecord(f->ring_ev[((f->host_t - 1) % RING) / RING_CHUNK], f->stream));
-  }
+  CK(cudaGraphExecKernelNodeSetParams(f->exec, f->wnode, &f->wparams));
+  CK(cudaGraphLaunch(f->exec, f->stream));
   return PF_OK;
 }
 
@@ -428,19 +449,15 @@ pf_status pf_create(const pf_config* cfg, pf_filter** out) {
   if ((st = dev_alloc(f, n * 4, (void**)&f->anc)) != PF_OK) return bail(st);
   if (is_cutpoint(f->scheme) && (st = dev_alloc(f, n * 4, (void**)&f->I)) != PF_OK) return bail(st);
   if ((st = dev_alloc(f, ((size_t)merge_chunks(n) + 1) * 8, (void**)&f->splits)) != PF_OK) return bail(st);
-  if ((st = dev_alloc(f, (size_t)f->ntiles * 16, &f->part)) != PF_OK) return bail(st);
+  // log-ML partials: one per CDF tile (2048-particle tiles need twice as many)
+  if ((st = dev_alloc(f, (size_t)f->ntiles * 32, &f->part)) != PF_OK) return bail(st);
+  f->nparts = f->ntiles;
   const uint64_t est_blocks = cdiv(n, (uint64_t)BLOCK * EST_PER_THREAD);
   if ((st = dev_alloc(f, est_blocks * 6 * 8, (void**)&f->part_est)) != PF_OK) return bail(st);
   if ((st = dev_alloc(f, sizeof(Ctl), (void**)&f->ctl)) != PF_OK) return bail(st);
-  if ((st = dev_alloc(f, RING * sizeof(double), (void**)&f->y_ring)) != PF_OK) return bail(st);
-  if (cudaHostAlloc((void**)&f->y_pinned, RING * sizeof(double), cudaHostAllocDefault) != cudaSuccess ||
-      cudaHostAlloc((void**)&f->ctl_host, sizeof(Ctl), cudaHostAllocDefault) != cudaSuccess) {
+  if (cudaHostAlloc((void**)&f->ctl_host, sizeof(Ctl), cudaHostAllocDefault) != cudaSuccess) {
     cudaGetLastError();
     return bail(set_err(PF_ERR_OOM, "pinned host allocation failed"));
-  }
-  for (int i = 0; i < 4; ++i) {
-    if (cudaEventCreateWithFlags(&f->ring_ev[i], cudaEventDisableTiming) != cudaSuccess)
-      return bail(set_err(PF_ERR_CUDA, "cudaEventCreate failed"));
   }
   // control block: t = 0, no error, max = -inf, counters 0
   Ctl c0;
@@ -495,21 +512,36 @@ pf_status pf_create(const pf_config* cfg, pf_filter** out) {
                    cap = (uint64_t)per_sm * (uint64_t)sms;
     f->prop_grid = (unsigned)(want < cap ? want : cap);
     if (f->scheme == PF_SYSTEMATIC) {
-      // cooperative grid: every CTA resident at once (it waits on the others)
-      // one tile per CTA when the tiles fit at once, else the staged variant
+      // cooperative grid: every CTA resident at once (it waits on the others).
+      // One tile per CTA when the tiles fit at once -- in binary32 2048-particle
+      // tiles (8 per thread) if those fit, for twice the parallelism -- else
+      // the staged variant over 4096-particle tiles.
       int cdf_sm = 0;
-      e = f->fp64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cdf_sm, k_cdf_sys<double, false>, BLOCK, 0)
-                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cdf_sm, k_cdf_sys<float, false>, BLOCK, 0);
-      if (e != cudaSuccess || cdf_sm < 1) return bail(set_err(PF_ERR_CUDA, "occupancy query failed"));
-      uint64_t g = (uint64_t)cdf_sm * (uint64_t)sms;
-      if (f->ntiles > g) {
-        f->cdf_staged = true;
-        e = f->fp64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cdf_sm, k_cdf_sys<double, true>, BLOCK, 0)
-                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cdf_sm, k_cdf_sys<float, true>, BLOCK, 0);
+      uint64_t g = 0;
+      if (!f->fp64) {
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cdf_sm, k_cdf_sys<float, false, 8>, BLOCK, 0);
         if (e != cudaSuccess || cdf_sm < 1) return bail(set_err(PF_ERR_CUDA, "occupancy query failed"));
         g = (uint64_t)cdf_sm * (uint64_t)sms;
+        if (cdiv(n, 8ull * BLOCK) <= g) {
+          f->cdf_per = 8;
+          f->nparts = (uint32_t)cdiv(n, 8ull * BLOCK);
+        }
       }
-      f->cdf_grid = (unsigned)(f->ntiles < g ? f->ntiles : g);
+      if (f->cdf_per == 16) {
+        e = f->fp64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cdf_sm, k_cdf_sys<double, false, 16>, BLOCK, 0)
+                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cdf_sm, k_cdf_sys<float, false, 16>, BLOCK, 0);
+        if (e != cudaSuccess || cdf_sm < 1) return bail(set_err(PF_ERR_CUDA, "occupancy query failed"));
+        g = (uint64_t)cdf_sm * (uint64_t)sms;
+        if (f->ntiles > g) {
+          f->cdf_staged = true;
+          e = f->fp64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cdf_sm, k_cdf_sys<double, true, 16>, BLOCK, 0)
+                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cdf_sm, k_cdf_sys<float, true, 16>, BLOCK, 0);
+          if (e != cudaSuccess || cdf_sm < 1) return bail(set_err(PF_ERR_CUDA, "occupancy query failed"));
+          g = (uint64_t)cdf_sm * (uint64_t)sms;
+        }
+      }
+      const uint64_t nt = f->cdf_per == 8 ? f->nparts : f->ntiles;
+      f->cdf_grid = (unsigned)(nt < g ? nt : g);
       if ((st = dev_alloc(f, (size_t)f->cdf_grid * 8, (void**)&f->cta_tot)) != PF_OK) return bail(st);
     }
   }
@@ -521,8 +553,7 @@ pf_status pf_create(const pf_config* cfg, pf_filter** out) {
 pf_status pf_step(pf_filter* f, double y) {
   pf_status st = check_handle(f);
   if (st != PF_OK) return st;
-  if ((st = stage_obs(f, &y, 1, false)) != PF_OK) return f->sticky = st;
-  if ((st = launch_cycles(f, 1)) != PF_OK) return f->sticky = st;
+  if ((st = launch_cycle(f, nullptr, y)) != PF_OK) return f->sticky = st;
   return PF_OK;
 }
 
@@ -535,14 +566,9 @@ pf_status pf_run(pf_filter* f, const double* y, uint32_t n_steps) {
   if (n_steps && cudaPointerGetAttributes(&attr, y) == cudaSuccess)
     dev = attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
   cudaGetLastError();
-  uint32_t done = 0;
-  while (done < n_steps) {
-    const uint32_t slot = (uint32_t)(f->host_t % RING);
-    uint32_t cnt = RING_CHUNK - slot % RING_CHUNK;
-    if (cnt > n_steps - done) cnt = n_steps - done;
-    if ((st = stage_obs(f, y + done, cnt, dev)) != PF_OK) return f->sticky = st;
-    if ((st = launch_cycles(f, cnt)) != PF_OK) return f->sticky = st;
-    done += cnt;
+  for (uint32_t i = 0; i < n_steps; ++i) {
+    if ((st = dev ? launch_cycle(f, y + i, 0.0) : launch_cycle(f, nullptr, y[i])) != PF_OK)
+      return f->sticky = st;
   }
   return PF_OK;
 }
@@ -554,14 +580,8 @@ pf_status pf_step_profiled(pf_filter* f, double y, float* kernel_ms, const char*
   if (!kernel_ms || !n_kernels || max_kernels < 1) return set_err(PF_ERR_INVALID, "NULL output");
   KTimer tm;
   for (int i = 0; i <= KTimer::MAX; ++i) CK(cudaEventCreate(&tm.ev[i]));
-  if ((st = stage_obs(f, &y, 1, false)) == PF_OK)
-    st = f->fp64 ? enqueue_cycle<double>(f, &tm) : enqueue_cycle<float>(f, &tm);
-  if (st == PF_OK) {
-    f->host_t++;
-    if (f->host_t % RING_CHUNK == 0)
-      cudaEventRecord(f->ring_ev[((f->host_t - 1) % RING) / RING_CHUNK], f->stream);
-    st = sync_and_check(f);
-  }
+  st = f->fp64 ? enqueue_cycle<double>(f, &tm, nullptr, y) : enqueue_cycle<float>(f, &tm, nullptr, y);
+  if (st == PF_OK) st = sync_and_check(f);
   if (st == PF_OK) {
     const int cnt = tm.count < max_kernels ? tm.count : max_kernels;
     for (int i = 0; i < cnt; ++i) {
@@ -639,10 +659,6 @@ pf_status pf_destroy(pf_filter* f) {
   if (f->exec) cudaGraphExecDestroy(f->exec);
   if (f->graph) cudaGraphDestroy(f->graph);
   free_all(f);
-  if (f->stream) cudaStreamSynchronize(f->stream);
-  for (int i = 0; i < 4; ++i)
-    if (f->ring_ev[i]) cudaEventDestroy(f->ring_ev[i]);
-  if (f->y_pinned) cudaFreeHost(f->y_pinned);
   if (f->ctl_host) cudaFreeHost(f->ctl_host);
   if (f->own_stream) cudaStreamDestroy(f->stream);
   cudaGetLastError();

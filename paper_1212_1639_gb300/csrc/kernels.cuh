@@ -122,10 +122,13 @@ struct FilterArgs {
   void* part;               // per-tile log-ML partial (U128 for FP32, double for FP64)
   double* part_est;         // per-block estimate partials
   Ctl* ctl;
-  const double* y_ring;
-  uint32_t cap;
+  // this cycle's observation: *y_src when y_src is set (device-resident
+  // observations), else y_val (set per launch in the graph's weights node)
+  const double* y_src;
+  double y_val;
   uint64_t n;
   uint32_t ntiles;
+  uint32_t nparts;          // log-ML partials written this cycle (one per CDF tile)
   int k;                    // CDF shift: W <= 2^k
   uint64_t seed;
   uint32_t filter;
@@ -255,7 +258,7 @@ __global__ void __launch_bounds__(BLOCK, sizeof(R) == 4 ? 8 : 4) k_weights(Filte
   const uint32_t t = a.ctl->t;
   const StateV<R> st = (t & 1) ? a.st[1] : a.st[0];
   if (threadIdx.x == 0) {
-    const double y = a.y_ring[t % a.cap];
+    const double y = a.y_src ? *a.y_src : a.y_val;
     s_y = (R)y;
     if (blockIdx.x == 0) {
       // this cycle's constants for k_propagate: observation and the
@@ -1137,26 +1140,37 @@ __device__ __forceinline__ uint64_t quant_from_e(double e, int k) {
 // ---------------------------------------------------------------------------
 // The CDF and systematic resampling in one cooperative launch (Steps 1b-1c
 // of the cycle for the systematic scheme).  Every CTA owns a contiguous range
-// of 4096-particle tiles:
+// of tiles of BLOCK x PER particles (thread t: particles [PER t, PER t + PER)):
 //   phase 1  the exact sum of its quantised weights W_i;
 //   barrier  all CTAs (the launch is cooperative, so all are resident; the
 //            wait is bounded and reports ERR_TIMEOUT);
 //   phase 2  its exclusive prefix and T from the CTA sums, then for each of
 //            its tiles the block scan of W with a carry -- thread t holds
-//            Q_i for its 16 particles [16 t, 16 t + 16) and Q before them in
-//            registers -- the CDF written out, and the systematic walk of its
-//            particles straight from those registers.
-// The quantisation, the per-thread log-ML partials (16 particles, fixed
-// order) and the tile partials are those of k_scan, and the ancestors those
-// of k_merge_sys: the results are the same bits.  Instead of a look-back
-// over tiles in flight, one grid-wide barrier; the weights l are read twice
-// (the second time mostly from L2).
+//            Q_i for its particles and Q before them in registers -- the CDF
+//            written out, and systematic resampling from those registers:
+//            each particle marks the first of its slots in a shared-memory
+//            window, and the warps fill the slots between marks forward.
+// The quantisation and the log-ML partials (sums over 16 consecutive
+// particles in a fixed order; with PER = 8 a lane pair shares one) are those
+// of k_scan, and the ancestors those of k_merge_sys: the results are the same
+// bits.  Instead of a look-back over tiles in flight, one grid-wide barrier.
+// PER = 8 (binary32) doubles the CTAs for the same particles where one tile
+// per CTA fits at once; the binary32 tile partials are exact, so the tile
+// size does not change them.
 // ---------------------------------------------------------------------------
 // STAGED: a CTA owns several tiles, and l of the next one is copied by TMA
 // into a shared-memory double buffer while the CTA works on the current one;
-// otherwise (one tile per CTA) l is read directly.
-template <class R, bool STAGED>
+// phase 1 writes e = exp(l - m) back in l's place by bulk stores, so phase 2
+// needs no exponentials; the CDF goes out through shared-memory rows,
+// coalesced.  Otherwise (one tile per CTA) l is read directly and the first
+// tile's W stay in shared memory between the phases.
+template <class R, bool STAGED, int PER>
 __global__ void __launch_bounds__(BLOCK, STAGED ? 3 : 4) k_cdf_sys(FilterArgs<R> a, uint64_t* cta_tot) {
+  static_assert(PER == 16 || (PER == 8 && !STAGED && sizeof(R) == 4), "tile shapes");
+  constexpr int TP = BLOCK * PER;  // particles per tile
+  // ancestor window entry of the tile's slot S0 + x: x + 2 (x >> LOGP) with
+  // lanes about PER slots apart, so that they hit distinct banks
+  constexpr int LOGP = PER == 16 ? 4 : 3;
   typedef typename ESumT<R>::T ES;
   __shared__ uint64_t s_warp[WARPS + 1];
   __shared__ ES s_es[WARPS];
@@ -1165,15 +1179,19 @@ __global__ void __launch_bounds__(BLOCK, STAGED ? 3 : 4) k_cdf_sys(FilterArgs<R>
   __shared__ uint32_t s_nruns;
   // the first tile's quantised weights and log-ML partials, kept from phase
   // 1 for phase 2 (a CTA that owns one tile quantises once)
-  __shared__ uint64_t s_keep[BLOCK * (SCAN_PER + 1)];
+  __shared__ uint64_t s_keep[BLOCK * (PER + 1)];
   __shared__ R s_keep_ep[BLOCK];
   // l of the next tile arrives by TMA while the CTA works on the current one
-  __shared__ alignas(128) R s_ell[2][STAGED ? TILE : 4];
+  // (phase 2: a free buffer is the tile's ancestor window, see below)
+  __shared__ alignas(128) R s_ell[2][STAGED ? TP : 4];
+  __shared__ alignas(16) uint16_t s_win[STAGED ? 8 : 2 * TP];
+  __shared__ uint32_t s_wmax[WARPS];
   __shared__ alignas(8) uint64_t s_bar[2];
+  __shared__ uint32_t s_S[2];  // the tile's first slot and the slot after its last
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   Ctl* c = a.ctl;
   const uint64_t n = a.n;
-  const uint32_t ntiles = a.ntiles;
+  const uint32_t ntiles = (uint32_t)((n + TP - 1) / TP);
   const uint32_t per = (ntiles + gridDim.x - 1) / gridDim.x;
   const uint32_t tb = blockIdx.x * per < ntiles ? blockIdx.x * per : ntiles;
   const uint32_t te = tb + per < ntiles ? tb + per : ntiles;
@@ -1193,8 +1211,8 @@ __global__ void __launch_bounds__(BLOCK, STAGED ? 3 : 4) k_cdf_sys(FilterArgs<R>
   __syncthreads();
   uint32_t q_issued = 0, q_done = 0;
   auto issue = [&](uint32_t tile) {  // thread 0 only; the buffer is free
-    const uint64_t first = (uint64_t)tile * TILE;
-    const uint64_t cnt = n - first < (uint64_t)TILE ? n - first : (uint64_t)TILE;
+    const uint64_t first = (uint64_t)tile * TP;
+    const uint64_t cnt = n - first < (uint64_t)TP ? n - first : (uint64_t)TP;
     const uint32_t bytes = (uint32_t)((cnt * sizeof(R) + 15) & ~(uint64_t)15);
     bulk_wait_read();  // the buffer's last bulk store has read it
     fence_proxy_async_smem();
@@ -1208,7 +1226,7 @@ __global__ void __launch_bounds__(BLOCK, STAGED ? 3 : 4) k_cdf_sys(FilterArgs<R>
   // waits for the oldest copy; returns its buffer (unstaged: l in HBM, at
   // the tile's start)
   auto take_tile = [&](uint32_t tile) -> const R* {
-    if (!STAGED) return a.ell + (uint64_t)tile * TILE;
+    if (!STAGED) return a.ell + (uint64_t)tile * TP;
     const uint32_t b = q_done & 1;
     if (!mbar_wait(&s_bar[b], (q_done >> 1) & 1) && threadIdx.x == 0)
       atomicOr(&c->err, ERR_TIMEOUT);
@@ -1219,14 +1237,15 @@ __global__ void __launch_bounds__(BLOCK, STAGED ? 3 : 4) k_cdf_sys(FilterArgs<R>
   // sums W and the partial sum of e = exp(l - m).  mode 0: from l in buf;
   // 1: from l in buf (shared memory), writing e back in its place; 2: from e
   // in buf (written back by phase 1).
-  auto quant16 = [&](uint32_t tile, const R* buf, uint64_t* W, R* epart, int mode) {
-    const uint64_t base = (uint64_t)tile * TILE + (uint64_t)threadIdx.x * SCAN_PER;
-    R* const row = const_cast<R*>(buf) + threadIdx.x * SCAN_PER;
-    const bool full = base + SCAN_PER <= n;
+  auto quantP = [&](uint32_t tile, const R* buf, uint64_t* W, R* epart, int mode) {
+    R exs[PER];
+    const uint64_t base = (uint64_t)tile * TP + (uint64_t)threadIdx.x * PER;
+    R* const row = const_cast<R*>(buf) + threadIdx.x * PER;
+    const bool full = base + PER <= n;
     uint64_t run = 0;
     R ep = (R)0;
 #pragma unroll
-    for (int q = 0; q < SCAN_PER / 4; ++q) {
+    for (int q = 0; q < PER / 4; ++q) {
       R v[4];
       if (full) {
         if constexpr (sizeof(R) == 4) {
@@ -1257,6 +1276,7 @@ __global__ void __launch_bounds__(BLOCK, STAGED ? 3 : 4) k_cdf_sys(FilterArgs<R>
           ep = ep + ex;
         }
         ex4[e] = ex;
+        exs[4 * q + e] = ex;
         run += w;
         W[4 * q + e] = run;  // inclusive running sum
       }
@@ -1268,6 +1288,15 @@ __global__ void __launch_bounds__(BLOCK, STAGED ? 3 : 4) k_cdf_sys(FilterArgs<R>
           *reinterpret_cast<double2*>(row + 4 * q + 2) = make_double2(ex4[2], ex4[3]);
         }
       }
+    }
+    if constexpr (PER == 8) {
+      // the log-ML partials are sums over 16 consecutive particles in
+      // order: the odd lane continues the even lane's sum over its own 8
+      const R prev = __shfl_xor_sync(0xffffffffu, ep, 1);
+      R acc = prev;
+#pragma unroll
+      for (int e = 0; e < PER; ++e) acc = acc + exs[e];  // e = 0 past n: adds nothing
+      ep = (threadIdx.x & 1) ? acc : (R)0;
     }
     *epart = ep;
   };
@@ -1289,22 +1318,22 @@ __global__ void __launch_bounds__(BLOCK, STAGED ? 3 : 4) k_cdf_sys(FilterArgs<R>
   for (uint32_t tile = tb; tile < te; ++tile) {
     if (tile + 1 < te) next_issue(tile + 1);
     const R* buf = take_tile(tile);
-    uint64_t W[SCAN_PER];
+    uint64_t W[PER];
     R ep;
-    quant16(tile, buf, W, &ep, STAGED ? 1 : 0);
+    quantP(tile, buf, W, &ep, STAGED ? 1 : 0);
     if (STAGED) fence_proxy_async_smem();  // e in buf, for the bulk store below
-    mine += W[SCAN_PER - 1];
+    mine += W[PER - 1];
     if (tile == tb) {
 #pragma unroll
-      for (int e = 0; e < SCAN_PER; ++e) s_keep[threadIdx.x * (SCAN_PER + 1) + e] = W[e];
+      for (int e = 0; e < PER; ++e) s_keep[threadIdx.x * (PER + 1) + e] = W[e];
       s_keep_ep[threadIdx.x] = ep;
     }
     __syncthreads();  // buf is refilled two copies later
     if (STAGED && tile != tb && threadIdx.x == 0) {
       // e goes back to l's place in global memory for phase 2, which then
       // needs no exponentials (the first tile's W stay in shared memory)
-      const uint64_t first = (uint64_t)tile * TILE;
-      const uint64_t cnt = n - first < (uint64_t)TILE ? n - first : (uint64_t)TILE;
+      const uint64_t first = (uint64_t)tile * TP;
+      const uint64_t cnt = n - first < (uint64_t)TP ? n - first : (uint64_t)TP;
       tma_store_1d(a.ell + first, buf, (uint32_t)((cnt * sizeof(R) + 15) & ~(uint64_t)15));
     }
   }
@@ -1352,17 +1381,26 @@ __global__ void __launch_bounds__(BLOCK, STAGED ? 3 : 4) k_cdf_sys(FilterArgs<R>
   __syncthreads();
   uint64_t carry = pre;
   for (uint32_t tile = tb; tile < te; ++tile) {
-    uint64_t W[SCAN_PER];
+    uint64_t W[PER];
     R ep;
     if (tile == tb) {  // this thread's own entries: no barrier needed
 #pragma unroll
-      for (int e = 0; e < SCAN_PER; ++e) W[e] = s_keep[threadIdx.x * (SCAN_PER + 1) + e];
+      for (int e = 0; e < PER; ++e) W[e] = s_keep[threadIdx.x * (PER + 1) + e];
       ep = s_keep_ep[threadIdx.x];
     } else {
       if (tile + 1 < te) next_issue(tile + 1);
       const R* buf = take_tile(tile);
-      quant16(tile, buf, W, &ep, 2);
+      quantP(tile, buf, W, &ep, 2);
     }
+    // the tile's first slot S0 = R(carry)
+    if (threadIdx.x == 0) s_S[0] = (uint32_t)sys_first_slot(carry, n, r, dv);
+    // The ancestors of the tile's slots [S0, S1) are built in a shared-memory
+    // window (a free l buffer when staged): entry of slot S0 + x is
+    // x + 2 (x >> LOGP), so lanes about PER slots apart hit distinct banks.
+    constexpr uint32_t WIN_ENTRIES = STAGED ? TP * sizeof(R) / 2 : 2 * TP;
+    constexpr uint32_t WIN_SLOTS = WIN_ENTRIES / (PER + 2) * PER;
+    uint16_t* const win = STAGED ? reinterpret_cast<uint16_t*>(
+        s_ell[tile == tb ? (q_issued & 1) : ((q_done - 1) & 1)]) : s_win;
     {
       ES es;
       es.zero();
@@ -1372,10 +1410,14 @@ __global__ void __launch_bounds__(BLOCK, STAGED ? 3 : 4) k_cdf_sys(FilterArgs<R>
       if (lane == 0) s_es[warp] = es;
     }
     // block exclusive scan of the thread totals
-    const uint64_t tt = W[SCAN_PER - 1];
+    const uint64_t tt = W[PER - 1];
     const uint64_t incl = warp_incl_scan(tt, lane);
     if (lane == 31) s_warp[warp] = incl;
     __syncthreads();
+    {  // every thread is past quantP: the window is free, clear it
+      uint4* const wz = reinterpret_cast<uint4*>(win);
+      for (uint32_t q = threadIdx.x; q < WIN_ENTRIES / 8; q += BLOCK) wz[q] = make_uint4(0u, 0u, 0u, 0u);
+    }
     if (warp == 0) {
       const uint64_t wt = lane < WARPS ? s_warp[lane] : 0;
       const uint64_t wi = warp_incl_scan(wt, lane);
@@ -1390,68 +1432,121 @@ __global__ void __launch_bounds__(BLOCK, STAGED ? 3 : 4) k_cdf_sys(FilterArgs<R>
     __syncthreads();
     const uint64_t o = carry + s_warp[warp] + (incl - tt);  // Q just before this thread's particles
     const uint64_t tile_tot = s_bc[0];
-    const uint64_t base = (uint64_t)tile * TILE + (uint64_t)threadIdx.x * SCAN_PER;
-    if (base + SCAN_PER <= n) {
+    const uint64_t tbase = (uint64_t)tile * TP;
+    const uint64_t base = tbase + (uint64_t)threadIdx.x * PER;
+    const uint32_t S0 = s_S[0];
+    // The CDF: staged (several tiles per CTA, where the store instructions
+    // add up), through this thread's shared-memory row and written out
+    // coalesced below; otherwise stored directly.
+    if constexpr (STAGED) {
+      uint64_t* const qrow = s_keep + threadIdx.x * (PER + 1);
 #pragma unroll
-      for (int e = 0; e < SCAN_PER; e += 2)
-        *reinterpret_cast<ulonglong2*>(a.Q + base + e) = make_ulonglong2(o + W[e], o + W[e + 1]);
+      for (int e = 0; e < PER; ++e) qrow[e] = o + W[e];
     } else {
+      if (base + PER <= n) {
 #pragma unroll
-      for (int e = 0; e < SCAN_PER; ++e)
-        if (base + e < n) a.Q[base + e] = o + W[e];
-    }
-    // systematic walk of this thread's particles, flattened: every step
-    // either gives slot j to the current particle i or moves on to i + 1, so
-    // the lanes of a warp stay converged.  D = n Q_i - (j T + r): slot j
-    // goes to i while D > 0.  Before a move D lies in (-T, 0] and a move adds
-    // n w_{i+1} <= n 2^k <= 2^61 (T <= 2^61 too), so D is an int64 and a step
-    // is one 64-bit addition.  The row holds n w for this thread's particles.
-    uint64_t* const nwrow = s_keep + threadIdx.x * (SCAN_PER + 1);
-    {
-      uint64_t prev = 0;
+        for (int e = 0; e < PER; e += 2)
+          *reinterpret_cast<ulonglong2*>(a.Q + base + e) = make_ulonglong2(o + W[e], o + W[e + 1]);
+      } else {
 #pragma unroll
-      for (int e = 0; e < SCAN_PER; ++e) {
-        nwrow[e] = (W[e] - prev) * n;
-        prev = W[e];
+        for (int e = 0; e < PER; ++e)
+          if (base + e < n) a.Q[base + e] = o + W[e];
       }
     }
-    if (T > 0 && base < n) {
-      const uint32_t i0 = (uint32_t)base;
-      const uint32_t iend = i0 + (base + SCAN_PER <= n ? (uint32_t)SCAN_PER : (uint32_t)(n - base));
-      uint32_t j = base == 0 ? 0u : (uint32_t)sys_first_slot(o, n, r, dv);
-      const U128 X = mul64x32(o, (uint32_t)n);
-      const U128 KB = add128(mul64x32(T, j), r);
-      int64_t D = (int64_t)(X.lo - KB.lo) + (int64_t)nwrow[0];
-      uint32_t i = i0, emitted = 0;
-#pragma unroll 1
-      while (true) {
-        const bool emit = D > 0;
-        if (emit && emitted == SYS_CAP) {  // a heavy particle: its other slots become a run
-          const uint64_t cnt = sys_floor_div(U128{0, (uint64_t)D - 1}, dv) + 1;
-          const uint32_t Rr = j + (uint32_t)cnt;
+    // Systematic resampling, one step per particle: with D = n Q_i - (j T + r)
+    // for particle i and its first slot j, i owns the c = ceil(D / T) slots
+    // j .. j + c - 1 (none if D <= 0); D then drops by c T into (-T, 0] and
+    // the next particle adds n w_{i+1} <= n 2^k <= 2^61 (T <= 2^61 too), so
+    // D is an int64.  A particle marks only its first slot in the window
+    // (with its offset in the tile + 1; 0 is empty); the slots between marks
+    // are filled forward below.  c comes from two comparisons unless it is
+    // above 2 (a heavy particle, divided out).  Slots past the window (rare)
+    // are stored directly, in runs of the block when long.
+    auto mark = [&](uint32_t j, uint32_t c, uint32_t i) {
+      const uint32_t x = j - S0;
+      if (x < WIN_SLOTS) win[x + 2 * (x >> LOGP)] = (uint16_t)(i - (uint32_t)tbase + 1u);
+      const uint32_t wend = S0 + WIN_SLOTS;
+      if (j + c > wend) {
+        const uint32_t st = j > wend ? j : wend;
+        if (j + c - st > (uint32_t)SYS_CAP) {
           const uint32_t kr = atomicAdd(&s_nruns, 1u);
           if (kr < BB_RUNS) {
-            s_run[kr][0] = j;
-            s_run[kr][1] = Rr;
+            s_run[kr][0] = st;
+            s_run[kr][1] = j + c;
             s_run[kr][2] = i;
           } else {
-            for (uint32_t q = j; q < Rr; ++q) a.anc[q] = i;
+            for (uint32_t q = st; q < j + c; ++q) a.anc[q] = i;
           }
-          D -= (int64_t)(cnt * T);
-          j = Rr;
-          continue;  // D <= 0 now: the next step moves on
+        } else {
+          for (uint32_t q = st; q < j + c; ++q) a.anc[q] = i;
         }
-        if (emit) a.anc[j] = i;
-        const uint32_t inext = i + 1;
-        const int64_t nwn = (int64_t)nwrow[(inext < iend ? inext : i) - i0];
-        D += emit ? -(int64_t)T : nwn;
-        j += emit ? 1u : 0u;
-        emitted = emit ? emitted + 1u : 0u;
-        i = emit ? i : inext;
-        if (i == iend) break;
+      }
+    };
+    if (T > 0 && base < n) {
+      const uint32_t i0 = (uint32_t)base;
+      const int ecount = base + PER <= n ? PER : (int)(n - base);
+      uint32_t j = threadIdx.x == 0 ? S0 : (base == 0 ? 0u : (uint32_t)sys_first_slot(o, n, r, dv));
+      const U128 X = mul64x32(o + W[0], (uint32_t)n);
+      const U128 KB = add128(mul64x32(T, j), r);
+      int64_t D = (int64_t)(X.lo - KB.lo);
+      const int64_t Ti = (int64_t)T;
+#pragma unroll
+      for (int e = 0; e < PER; ++e) {
+        if (e < ecount) {
+          uint32_t c = (uint32_t)(D > 0) + (uint32_t)(D > Ti);
+          if (D > 2 * Ti) c = (uint32_t)(sys_floor_div(U128{0, (uint64_t)D - 1}, dv) + 1);
+          if (c) mark(j, c, i0 + (uint32_t)e);
+          D -= (int64_t)c * Ti;
+          j += c;
+          if (e + 1 < PER) D += (int64_t)((W[e + 1] - W[e]) * n);
+        }
+      }
+      if (base + PER >= n || threadIdx.x == BLOCK - 1) s_S[1] = j;  // the tile's end slot
+    }
+    __syncthreads();
+    // fill forward: slot x takes the last mark at or before it (slot S0 is
+    // always marked).  Warp w covers a contiguous part of the window: its
+    // maximum mark first, then a running maximum with the earlier parts'.
+    const uint32_t wcnt = T > 0 ? (s_S[1] - S0 < WIN_SLOTS ? s_S[1] - S0 : WIN_SLOTS) : 0u;
+    const uint32_t cw = (wcnt + WARPS * 32 - 1) / (WARPS * 32) * 32;
+    const uint32_t x0 = warp * cw < wcnt ? warp * cw : wcnt;
+    const uint32_t x1 = x0 + cw < wcnt ? x0 + cw : wcnt;
+    {
+      uint32_t mx = 0;
+      for (uint32_t x = x0 + lane; x < x1; x += 32) mx = max(mx, (uint32_t)win[x + 2 * (x >> LOGP)]);
+      mx = __reduce_max_sync(0xffffffffu, mx);
+      if (lane == 0) s_wmax[warp] = mx;
+    }
+    if constexpr (STAGED) {  // the CDF rows, written out coalesced
+      const uint64_t tcnt = n - tbase < (uint64_t)TP ? n - tbase : (uint64_t)TP;
+      for (uint32_t p = 2 * threadIdx.x; p < tcnt; p += 2 * BLOCK) {
+        const uint64_t q0 = s_keep[(p / PER) * (PER + 1) + (p % PER)];
+        if (p + 1 < tcnt) {
+          const uint64_t q1 = s_keep[(p / PER) * (PER + 1) + (p % PER) + 1];
+          *reinterpret_cast<ulonglong2*>(a.Q + tbase + p) = make_ulonglong2(q0, q1);
+        } else {
+          a.Q[tbase + p] = q0;
+        }
       }
     }
     __syncthreads();
+    {
+      uint32_t run = 0;
+      for (int w = 0; w < warp; ++w) run = max(run, s_wmax[w]);
+      for (uint32_t xb = x0; xb < x1; xb += 32) {
+        const uint32_t x = xb + lane;
+        uint32_t v = x < x1 ? (uint32_t)win[x + 2 * (x >> LOGP)] : 0u;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+          const uint32_t u = __shfl_up_sync(0xffffffffu, v, d);
+          if (lane >= d) v = max(v, u);
+        }
+        v = max(v, run);
+        run = __shfl_sync(0xffffffffu, v, 31);
+        if (x < x1) a.anc[S0 + x] = (uint32_t)tbase + v - 1u;
+      }
+    }
+    // runs past the window, by the whole block
     const uint32_t nr = s_nruns < BB_RUNS ? s_nruns : BB_RUNS;
     for (uint32_t q = 0; q < nr; ++q) {
       const uint32_t st = s_run[q][0], en = s_run[q][1], v = s_run[q][2];
@@ -1496,7 +1591,7 @@ __device__ void fold_cycle_warp(const FilterArgs<R>& a, uint32_t t) {
   const int lane = threadIdx.x & 31;
   ES acc;
   acc.zero();
-  for (uint32_t b = lane; b < a.ntiles; b += 32) acc.add(reinterpret_cast<const ES*>(a.part)[b]);
+  for (uint32_t b = lane; b < a.nparts; b += 32) acc.add(reinterpret_cast<const ES*>(a.part)[b]);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc.add(acc.shfl_xor(o));
   if (lane == 0) {

@@ -107,6 +107,14 @@ def test_systematic_cdf_several_tiles_per_cta(pf, orc, prec):
     _run(pf, orc, 3_000_001, 3, 1, prec, every_step=True, seed=77)
 
 
+def test_systematic_cdf_tile_shapes(pf, orc):
+    """Binary32 systematic cycles take 2048-particle CDF tiles (8 per thread)
+    while one tile per CTA fits at once and 4096-particle tiles above that:
+    both shapes, with ragged last tiles, give the oracle's results."""
+    _run(pf, orc, 1_000_003, 3, 1, 0, every_step=True, seed=91)   # 2048-particle tiles
+    _run(pf, orc, 2_000_001, 3, 1, 0, every_step=True, seed=92)   # 4096-particle tiles
+
+
 def test_outlier_observation(pf, orc):
     """y far from every particle: most quantised weights underflow to zero."""
     y = np.array([0.3, 40.0, 40.5, -3.0, 0.0])
