@@ -1137,6 +1137,28 @@ __device__ __forceinline__ uint64_t quant_from_e(double e, int k) {
   return W > cap ? cap : W;
 }
 
+// Rare paths of the systematic resampling step, kept out of line so that the
+// per-particle loop stays small: the slot count of a heavy particle (more than
+// two slots), and slots past the shared-memory window -- stored directly, or
+// queued as a run for the whole CTA when long.
+static __device__ __noinline__ uint32_t sys_heavy_count(int64_t D, SysDiv dv) {
+  return (uint32_t)(sys_floor_div(U128{0, (uint64_t)D - 1}, dv) + 1);
+}
+static __device__ __noinline__ void sys_past_window(uint32_t j, uint32_t c, uint32_t i, uint32_t wend,
+                                             uint32_t* anc, uint32_t (*runs)[3], uint32_t* nruns) {
+  const uint32_t st = j > wend ? j : wend;
+  if (j + c - st > (uint32_t)SYS_CAP) {
+    const uint32_t kr = atomicAdd(nruns, 1u);
+    if (kr < BB_RUNS) {
+      runs[kr][0] = st;
+      runs[kr][1] = j + c;
+      runs[kr][2] = i;
+      return;
+    }
+  }
+  for (uint32_t q = st; q < j + c; ++q) anc[q] = i;
+}
+
 // ---------------------------------------------------------------------------
 // The CDF and systematic resampling in one cooperative launch (Steps 1b-1c
 // of the cycle for the systematic scheme).  Every CTA owns a contiguous range
@@ -1435,14 +1457,14 @@ __global__ void __launch_bounds__(BLOCK, STAGED ? 3 : 4) k_cdf_sys(FilterArgs<R>
     const uint64_t tbase = (uint64_t)tile * TP;
     const uint64_t base = tbase + (uint64_t)threadIdx.x * PER;
     const uint32_t S0 = s_S[0];
-    // The CDF: staged (several tiles per CTA, where the store instructions
-    // add up), through this thread's shared-memory row and written out
-    // coalesced below; otherwise stored directly.
-    if constexpr (STAGED) {
-      uint64_t* const qrow = s_keep + threadIdx.x * (PER + 1);
+    // The CDF: this thread's values go to its shared-memory row (read by the
+    // resampling step below); staged (several tiles per CTA, where the store
+    // instructions add up) the rows are written out coalesced below,
+    // otherwise the values are stored directly.
+    uint64_t* const qrow = s_keep + threadIdx.x * (PER + 1);
 #pragma unroll
-      for (int e = 0; e < PER; ++e) qrow[e] = o + W[e];
-    } else {
+    for (int e = 0; e < PER; ++e) qrow[e] = o + W[e];
+    if constexpr (!STAGED) {
       if (base + PER <= n) {
 #pragma unroll
         for (int e = 0; e < PER; e += 2)
@@ -1461,45 +1483,32 @@ __global__ void __launch_bounds__(BLOCK, STAGED ? 3 : 4) k_cdf_sys(FilterArgs<R>
     // (with its offset in the tile + 1; 0 is empty); the slots between marks
     // are filled forward below.  c comes from two comparisons unless it is
     // above 2 (a heavy particle, divided out).  Slots past the window (rare)
-    // are stored directly, in runs of the block when long.
-    auto mark = [&](uint32_t j, uint32_t c, uint32_t i) {
-      const uint32_t x = j - S0;
-      if (x < WIN_SLOTS) win[x + 2 * (x >> LOGP)] = (uint16_t)(i - (uint32_t)tbase + 1u);
-      const uint32_t wend = S0 + WIN_SLOTS;
-      if (j + c > wend) {
-        const uint32_t st = j > wend ? j : wend;
-        if (j + c - st > (uint32_t)SYS_CAP) {
-          const uint32_t kr = atomicAdd(&s_nruns, 1u);
-          if (kr < BB_RUNS) {
-            s_run[kr][0] = st;
-            s_run[kr][1] = j + c;
-            s_run[kr][2] = i;
-          } else {
-            for (uint32_t q = st; q < j + c; ++q) a.anc[q] = i;
-          }
-        } else {
-          for (uint32_t q = st; q < j + c; ++q) a.anc[q] = i;
-        }
-      }
-    };
+    // are stored directly, in runs of the CTA when long.  A rolled loop over
+    // the row: the step's code stays small.
     if (T > 0 && base < n) {
-      const uint32_t i0 = (uint32_t)base;
-      const int ecount = base + PER <= n ? PER : (int)(n - base);
+      const uint32_t ecount = base + PER <= n ? (uint32_t)PER : (uint32_t)(n - base);
       uint32_t j = threadIdx.x == 0 ? S0 : (base == 0 ? 0u : (uint32_t)sys_first_slot(o, n, r, dv));
-      const U128 X = mul64x32(o + W[0], (uint32_t)n);
+      const U128 X = mul64x32(o, (uint32_t)n);
       const U128 KB = add128(mul64x32(T, j), r);
-      int64_t D = (int64_t)(X.lo - KB.lo);
+      int64_t D = (int64_t)(X.lo - KB.lo);  // n Q - (j T + r) just before this thread's particles
       const int64_t Ti = (int64_t)T;
-#pragma unroll
-      for (int e = 0; e < PER; ++e) {
-        if (e < ecount) {
-          uint32_t c = (uint32_t)(D > 0) + (uint32_t)(D > Ti);
-          if (D > 2 * Ti) c = (uint32_t)(sys_floor_div(U128{0, (uint64_t)D - 1}, dv) + 1);
-          if (c) mark(j, c, i0 + (uint32_t)e);
-          D -= (int64_t)c * Ti;
-          j += c;
-          if (e + 1 < PER) D += (int64_t)((W[e + 1] - W[e]) * n);
+      const uint32_t wend = S0 + WIN_SLOTS;
+      const uint32_t off0 = (uint32_t)(base - tbase) + 1u;
+      uint64_t qprev = o;
+#pragma unroll 1
+      for (uint32_t e = 0; e < ecount; ++e) {
+        const uint64_t q = qrow[e];
+        D += (int64_t)((q - qprev) * n);
+        qprev = q;
+        uint32_t c = (uint32_t)(D > 0) + (uint32_t)(D > Ti);
+        if (D > 2 * Ti) c = sys_heavy_count(D, dv);
+        if (c) {
+          const uint32_t x = j - S0;
+          if (x < WIN_SLOTS) win[x + 2 * (x >> LOGP)] = (uint16_t)(off0 + e);
+          if (j + c > wend) sys_past_window(j, c, (uint32_t)base + e, wend, a.anc, s_run, &s_nruns);
         }
+        D -= (int64_t)c * Ti;
+        j += c;
       }
       if (base + PER >= n || threadIdx.x == BLOCK - 1) s_S[1] = j;  // the tile's end slot
     }
