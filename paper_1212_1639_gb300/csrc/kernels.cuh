@@ -1187,7 +1187,7 @@ static __device__ __noinline__ void sys_past_window(uint32_t j, uint32_t c, uint
 // coalesced.  Otherwise (one tile per CTA) l is read directly and the first
 // tile's W stay in shared memory between the phases.
 template <class R, bool STAGED, int PER>
-__global__ void __launch_bounds__(BLOCK, STAGED ? 3 : 4) k_cdf_sys(FilterArgs<R> a, uint64_t* cta_tot) {
+__global__ void __launch_bounds__(BLOCK, PER == 8 ? 4 : 3) k_cdf_sys(FilterArgs<R> a, uint64_t* cta_tot) {
   static_assert(PER == 16 || (PER == 8 && !STAGED && sizeof(R) == 4), "tile shapes");
   constexpr int TP = BLOCK * PER;  // particles per tile
   // ancestor window entry of the tile's slot S0 + x: x + 2 (x >> LOGP) with
