@@ -462,37 +462,67 @@ __device__ __forceinline__ void batch_filter(const BatchArgs<R>& a, const BatchI
     if (T > 0 && ib < n) {
       const uint64_t ie = ib + SCAN_PER < n ? ib + SCAN_PER : n;
       uint64_t j = 0;
+      const uint64_t qp = ib > 0 ? a.Q[off + ib - 1] : 0;
       if (ib > 0) {
-        const uint64_t qp = a.Q[off + ib - 1];
         j = POS == POS_SYSTEMATIC ? sys_first_slot(qp, n, r, dv)
                                   : multi_first_slot(Sf, n, T, mul64(qp, A), 0);
       }
-      for (uint64_t i = ib; i < ie; ++i) {
-        const uint64_t qi = a.Q[off + i];
-        const U128 KQ = POS == POS_SYSTEMATIC ? mul64x32(qi, (uint32_t)n) : mul64(qi, A);
-        int emitted = 0;
-        while (j < n) {
-          const U128 KB = POS == POS_SYSTEMATIC ? add128(mul64x32(T, (uint32_t)j), r)
-                                                : mul64(Sf[j], T);
-          if (!lt128(KB, KQ)) break;
-          if (emitted == BB_CAP) {  // a heavy particle: hand its other slots to the CTA
-            uint64_t R2 = POS == POS_SYSTEMATIC ? sys_first_slot(qi, n, r, dv)
-                                                : multi_first_slot(Sf, n, T, KQ, j);
-            R2 = R2 < j ? j : R2;
+      if constexpr (POS == POS_SYSTEMATIC) {
+        // one step per particle: with D = n Q_i - (j T + r), particle i owns
+        // the c = ceil(D / T) slots from j (none if D <= 0); D stays an int64
+        // (in (-T, 0] between particles, n w_i <= 2^61, T <= 2^61)
+        const U128 X = mul64x32(qp, (uint32_t)n);
+        const U128 KB = add128(mul64x32(T, (uint32_t)j), r);
+        int64_t D = (int64_t)(X.lo - KB.lo);
+        const int64_t Ti = (int64_t)T;
+        uint64_t qprev = qp;
+        for (uint64_t i = ib; i < ie; ++i) {
+          const uint64_t qi = a.Q[off + i];
+          D += (int64_t)((qi - qprev) * n);
+          qprev = qi;
+          uint32_t c = (uint32_t)(D > 0) + (uint32_t)(D > Ti);
+          if (D > 2 * Ti) c = (uint32_t)(sys_floor_div(U128{0, (uint64_t)D - 1}, dv) + 1);
+          if (c > (uint32_t)BB_CAP) {  // a heavy particle: hand its slots to the CTA
             const uint32_t kr = atomicAdd(&sm.nruns, 1u);
             if (kr < BB_MAX_RUNS) {
               sm.run[kr][0] = (uint32_t)j;
-              sm.run[kr][1] = (uint32_t)R2;
+              sm.run[kr][1] = (uint32_t)(j + c);
               sm.run[kr][2] = (uint32_t)i;
             } else {
-              for (uint64_t q = j; q < R2; ++q) a.anc[off + q] = (uint32_t)i;
+              for (uint64_t q = j; q < j + c; ++q) a.anc[off + q] = (uint32_t)i;
             }
-            j = R2;
-            break;
+          } else {
+            for (uint32_t q = 0; q < c; ++q) a.anc[off + j + q] = (uint32_t)i;
           }
-          a.anc[off + j] = (uint32_t)i;
-          ++j;
-          ++emitted;
+          D -= (int64_t)c * Ti;
+          j += c;
+        }
+      } else {  // multinomial: slot by slot over the positions S_j T
+        for (uint64_t i = ib; i < ie; ++i) {
+          const uint64_t qi = a.Q[off + i];
+          const U128 KQ = mul64(qi, A);
+          int emitted = 0;
+          while (j < n) {
+            const U128 KB = mul64(Sf[j], T);
+            if (!lt128(KB, KQ)) break;
+            if (emitted == BB_CAP) {  // a heavy particle: hand its other slots to the CTA
+              uint64_t R2 = multi_first_slot(Sf, n, T, KQ, j);
+              R2 = R2 < j ? j : R2;
+              const uint32_t kr = atomicAdd(&sm.nruns, 1u);
+              if (kr < BB_MAX_RUNS) {
+                sm.run[kr][0] = (uint32_t)j;
+                sm.run[kr][1] = (uint32_t)R2;
+                sm.run[kr][2] = (uint32_t)i;
+              } else {
+                for (uint64_t q = j; q < R2; ++q) a.anc[off + q] = (uint32_t)i;
+              }
+              j = R2;
+              break;
+            }
+            a.anc[off + j] = (uint32_t)i;
+            ++j;
+            ++emitted;
+          }
         }
       }
     }

@@ -122,6 +122,17 @@ def test_outlier_observation(pf, orc):
     _run(pf, orc, 4096, y.size, 0, 1, y=y)
 
 
+def test_outlier_observation_large(pf, orc):
+    """Outlying observations at 300,001 particles (2048-particle CDF tiles,
+    one per CTA) and 2,600,003 (several 4096-particle tiles per CTA): a few
+    particles own thousands of slots each, so tiles hold far more slots than
+    the shared-memory ancestor window and the heavy particles' slots past it
+    become runs of the CTA."""
+    y = np.array([0.3, 40.0, 0.1])
+    _run(pf, orc, 300_001, y.size, 1, 0, y=y)
+    _run(pf, orc, 2_600_003, 2, 1, 0, y=np.array([0.3, -35.0]), every_step=True, seed=3)
+
+
 def test_run_matches_step(pf, orc):
     _, y = synth.local_level_series(5, 40)
     a = pf.Filter(2048, seed=5, scheme="multinomial")
