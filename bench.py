@@ -170,9 +170,9 @@ def kernels_hash():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel, n):
-    """dram bytes per launch from the committed ncu summary, scaled to n
-    particles; None if the kernels changed since the capture."""
+def _recorded(kernel, what):
+    """A per-particle figure of `kernel` from the committed ncu summary
+    (profiles/traffic.txt); None if the kernels changed since the capture."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
         return None
@@ -184,10 +184,15 @@ def recorded_traffic(kernel, n):
         rec[k.strip()] = v.strip()
     if rec.get("kernels_hash") != kernels_hash():
         return None
-    key = "%s_bytes_per_particle" % kernel
-    if key not in rec:
-        return None
-    return float(rec[key]) * n
+    key = "%s_%s_per_particle" % (kernel, what)
+    return float(rec[key]) if key in rec else None
+
+
+def recorded_traffic(kernel, n):
+    """dram bytes per launch from the committed ncu summary, scaled to n
+    particles; None if the kernels changed since the capture."""
+    v = _recorded(kernel, "bytes")
+    return None if v is None else v * n
 
 
 def time_cycles(f, y_dev, start, K, stream, flush):
@@ -281,6 +286,18 @@ def bench_ours(args):
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm,
                 "peak_kind": hbm_kind, "unit": "GB/s", "frac": round(achieved / hbm, 4),
                 "traffic": traffic, "algorithmic_bytes": kernels[dom]["bytes"]}
+    # the same kernel against instruction issue, its actual bound: thread
+    # instructions per particle from the committed ncu capture, against one
+    # warp instruction per scheduler per cycle (4 per SM) at the maximum SM
+    # clock seen during the timed region
+    inst = _recorded(dkey, "inst")
+    if inst is not None and clocks.get("sm_max_mhz"):
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
+        peak_i = sms * 4 * 32 * clocks["sm_max_mhz"] * 1e6 / 1e12
+        ach_i = inst * n / (prof[dom] / 1e3) / 1e12
+        roofline["issue"] = {"inst_per_particle": inst, "achieved": round(ach_i, 2),
+                             "peak": round(peak_i, 2), "unit": "T thread-instructions/s",
+                             "frac": round(ach_i / peak_i, 4)}
     cycle_bytes = sum(v["bytes"] for v in kernels.values())
     cycle_ms = sum(prof.values())
 
