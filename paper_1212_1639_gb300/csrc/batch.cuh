@@ -556,16 +556,25 @@ __device__ __forceinline__ void batch_filter(const BatchArgs<R>& a, const BatchI
     if (sig) dst.s2[off + itm.j] = v;
     else dst.t2[off + itm.j] = v;
   };
-  for (uint64_t j0 = (uint64_t)rank * NT; j0 < n; j0 += (uint64_t)G * NT) {
+  // the filter's state, and the record of a slot's ancestor (gathered one
+  // pass ahead, so that its latency overlaps the current pass)
+  StateV<R> fsrc = src;
+  fsrc.x += off; fsrc.s2 += off; fsrc.t2 += off; fsrc.bs += off; fsrc.bt += off;
+  auto gather_slot = [&](uint64_t jj) {
+    uint32_t an = jj < n ? a.anc[off + jj] : 0u;
+    an = an < n ? an : (uint32_t)(n - 1);
+    return gather_rec<R>(fsrc, an);
+  };
+  const uint64_t pstride = (uint64_t)G * NT;
+  Gathered<R> cur = gather_slot((uint64_t)rank * NT + threadIdx.x);
+  for (uint64_t j0 = (uint64_t)rank * NT; j0 < n; j0 += pstride) {
     const uint64_t j = j0 + threadIdx.x;
+    const Gathered<R> nxt = gather_slot(j + pstride);
     bool defer_s = false, defer_t = false;
     typename SuffT<R>::B bsn = 0, btn = 0;
     R Zs = 0, Us = 0, Zt = 0, Ut = 0;
     if (j < n) {
-      uint32_t an = a.anc[off + j];
-      an = an < n ? an : (uint32_t)(n - 1);
-      const uint64_t g = off + an;
-      const R xa = src.x[g], sa = src.s2[g], ta = src.t2[g];
+      const R xa = cur.x, sa = cur.s2, ta = cur.t2;
       const R s = sa + ta;
       const R p = sa * ta;
       const R V = p / s;
@@ -583,8 +592,8 @@ __device__ __forceinline__ void batch_filter(const BatchArgs<R>& a, const BatchI
       if (learn) {
         const R rs = ResidObs<R>::f(y, yr, xj);
         const R rt = xj - xa;
-        bsn = SuffOps<R>::add_half_square(src.bs[g], rs, &fail);
-        btn = SuffOps<R>::add_half_square(src.bt[g], rt, &fail);
+        bsn = SuffOps<R>::add_half_square(cur.bs, rs, &fail);
+        btn = SuffOps<R>::add_half_square(cur.bt, rt, &fail);
         dst.bs[d] = bsn;
         dst.bt[d] = btn;
         R Gs, Gt;
@@ -595,13 +604,14 @@ __device__ __forceinline__ void batch_filter(const BatchArgs<R>& a, const BatchI
       } else {
         dst.s2[d] = sa;
         dst.t2[d] = ta;
-        dst.bs[d] = src.bs[g];
-        dst.bt[d] = src.bt[g];
+        dst.bs[d] = cur.bs;
+        dst.bt[d] = cur.bt;
       }
     }
     wq_push<R>(wq, qn, defer_s, GammaItem<R>{bsn, Zs, Us, (uint32_t)j, 0u}, lane);
     wq_push<R>(wq, qn, defer_t, GammaItem<R>{btn, Zt, Ut, (uint32_t)j, 1u}, lane);
     wq_drain<R>(wq, qn, 32u, lane, finish);
+    cur = nxt;
   }
   wq_drain<R>(wq, qn, 1u, lane, finish);
 
