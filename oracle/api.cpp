@@ -108,19 +108,23 @@ int or_quantize_weights_f32(const float* w, uint64_t n, uint64_t* W) {
 uint64_t or_systematic_offset(uint64_t T, uint64_t seed, uint32_t filter, uint32_t t) {
   return systematic_offset(T, seed, filter, t);
 }
+uint64_t or_stratified_offset(uint64_t T, uint64_t seed, uint32_t filter, uint32_t t, uint64_t j) {
+  return stratified_offset(T, seed, filter, t, j);
+}
 void or_spacing_prefix(uint64_t n, uint64_t seed, uint32_t filter, uint32_t t, uint64_t* S) {
   std::vector<uint64_t> v;
   spacing_prefix(n, seed, filter, t, &v);
   std::memcpy(S, v.data(), (n + 1) * sizeof(uint64_t));
 }
 
-// positions: 0 = multinomial (spacings), 1 = systematic
+// positions: 0 = multinomial (spacings), 1 = systematic, 2 = stratified
 // method: 0 = sequential walk, 1 = naive O(n^2), 2 = cut-point method
 void or_resample_method(const uint64_t* Q, uint64_t n, int positions, int method,
                         uint64_t seed, uint32_t filter, uint32_t t, uint32_t* anc) {
   uint64_t T = Q[n - 1];
-  Positions P = positions == 1 ? systematic_positions(n, T, seed, filter, t)
-                               : multinomial_positions(n, T, seed, filter, t);
+  Positions P = positions == 1   ? systematic_positions(n, T, seed, filter, t)
+                : positions == 2 ? stratified_positions(n, T, seed, filter, t)
+                                 : multinomial_positions(n, T, seed, filter, t);
   if (method == 0) {
     walk(Q, n, P, anc);
   } else if (method == 1) {

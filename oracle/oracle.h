@@ -40,7 +40,7 @@ void philox4x64_10(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]
 enum Purpose : uint32_t {
   P_INIT_X = 1, P_INIT_SIGMA = 2, P_INIT_TAU = 3,
   P_STATE = 4, P_GAMMA_SIGMA = 5, P_GAMMA_TAU = 6,
-  P_SYS_OFFSET = 7, P_SPACING = 8,
+  P_SYS_OFFSET = 7, P_SPACING = 8, P_STRATIFIED = 9,
 };
 
 // One 128-bit draw addressed by (seed, filter, t, j, purpose, attempt):
@@ -123,6 +123,13 @@ Positions systematic_positions(uint64_t n, uint64_t T, uint64_t seed, uint32_t f
                                uint32_t t);
 Positions systematic_positions_with_offset(uint64_t n, uint64_t T, uint64_t r);
 uint64_t systematic_offset(uint64_t T, uint64_t seed, uint32_t filter, uint32_t t);
+// Stratified (paper Section 3.1, "Stratified Resampling"): one uniform in
+// each of the n equal strata, B_j = j*T + r_j, A = n, r_j = floor(R_j*T/2^64)
+// with R_j the 64-bit word pair 2(j mod 2), 2(j mod 2)+1 of the draw
+// (seed, filter, t, floor(j/2), STRATIFIED).
+uint64_t stratified_offset(uint64_t T, uint64_t seed, uint32_t filter, uint32_t t, uint64_t j);
+Positions stratified_positions(uint64_t n, uint64_t T, uint64_t seed, uint32_t filter,
+                               uint32_t t);
 // Multinomial with sorted uniforms: order statistics of n iid uniforms
 // generated directly in ascending order by exponential spacings
 // (Carpenter, Clifford & Fearnhead 1999): E_0..E_n iid Exp(1) in 2^-31 fixed
@@ -146,7 +153,10 @@ void cutpoint_search(const uint64_t* Q, uint64_t n, uint64_t* L, uint32_t* I);
 void cutpoint_method(const uint64_t* Q, uint64_t n, const uint32_t* I, const Positions& P,
                      uint32_t* anc);
 
-enum Scheme { MULTINOMIAL = 0, SYSTEMATIC = 1, MULTINOMIAL_CUTPOINT = 2, SYSTEMATIC_CUTPOINT = 3 };
+enum Scheme {
+  MULTINOMIAL = 0, SYSTEMATIC = 1, MULTINOMIAL_CUTPOINT = 2, SYSTEMATIC_CUTPOINT = 3,
+  STRATIFIED = 4
+};
 
 // Ancestors of one resampling step from a finished CDF.
 void resample(const uint64_t* Q, uint64_t n, int scheme, uint64_t seed, uint32_t filter,

@@ -62,6 +62,7 @@ def _declare(L):
         "or_cdf_scan": (V, [u64p, U64, u64p]),
         "or_quantize_weights_f32": (I, [f32p, U64, u64p]),
         "or_systematic_offset": (U64, [U64, U64, U32, U32]),
+        "or_stratified_offset": (U64, [U64, U64, U32, U32, U64]),
         "or_spacing_prefix": (V, [U64, U64, U32, U32, u64p]),
         "or_resample_method": (V, [u64p, U64, I, I, U64, U32, U32, u32p]),
         "or_systematic_with_offset": (V, [u64p, U64, U64, u32p]),
@@ -92,7 +93,7 @@ P_INIT_X, P_INIT_SIGMA, P_INIT_TAU = 1, 2, 3
 P_STATE, P_GAMMA_SIGMA, P_GAMMA_TAU = 4, 5, 6
 P_SYS_OFFSET, P_SPACING = 7, 8
 
-MULTINOMIAL, SYSTEMATIC, MULTINOMIAL_CUTPOINT, SYSTEMATIC_CUTPOINT = 0, 1, 2, 3
+MULTINOMIAL, SYSTEMATIC, MULTINOMIAL_CUTPOINT, SYSTEMATIC_CUTPOINT, STRATIFIED = 0, 1, 2, 3, 4
 FP32, FP64 = 0, 1
 
 
@@ -200,6 +201,10 @@ def systematic_offset(T, seed, filt, t):
     return lib().or_systematic_offset(T, seed, filt, t)
 
 
+def stratified_offset(T, seed, filt, t, j):
+    return lib().or_stratified_offset(T, seed, filt, t, j)
+
+
 def spacing_prefix(n, seed, filt, t):
     S = np.zeros(n + 1, np.uint64)
     lib().or_spacing_prefix(n, seed, filt, t, S)
@@ -207,10 +212,11 @@ def spacing_prefix(n, seed, filt, t):
 
 
 def resample_method(Q, positions, method, seed, filt, t):
-    """positions: 'multinomial' | 'systematic'; method: 'walk' | 'naive' | 'cutpoint'."""
+    """positions: 'multinomial' | 'systematic' | 'stratified'; method: 'walk' | 'naive' |
+    'cutpoint'."""
     Q = np.ascontiguousarray(Q, np.uint64)
     anc = np.zeros(Q.size, np.uint32)
-    lib().or_resample_method(Q, Q.size, 1 if positions == "systematic" else 0,
+    lib().or_resample_method(Q, Q.size, {"multinomial": 0, "systematic": 1, "stratified": 2}[positions],
                              {"walk": 0, "naive": 1, "cutpoint": 2}[method],
                              seed, filt, t, anc)
     return anc

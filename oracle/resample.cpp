@@ -69,6 +69,30 @@ Positions systematic_positions(uint64_t n, uint64_t T, uint64_t seed, uint32_t f
   return systematic_positions_with_offset(n, T, systematic_offset(T, seed, filter, t));
 }
 
+uint64_t stratified_offset(uint64_t T, uint64_t seed, uint32_t filter, uint32_t t, uint64_t j) {
+  W4 w = draw(seed, filter, t, (uint32_t)(j >> 1), P_STRATIFIED, 0);
+  const int h = (int)(j & 1) * 2;
+  uint64_t R = ((uint64_t)w.w[h + 1] << 32) | w.w[h];
+  return mulhi64(R, T);
+}
+
+// Stratified resampling: slot j's uniform lies in the j-th of n equal strata.
+// pin: every slot stays in its stratum, offspring within one of the exact
+// mean on either side, mean offspring over seeds equal to n W_i / T, and the
+// naive search agrees (tests/test_oracle_resample.py).
+Positions stratified_positions(uint64_t n, uint64_t T, uint64_t seed, uint32_t filter,
+                               uint32_t t) {
+  Positions P;
+  P.A = (u128)n;
+  P.B.resize(n);
+  P.bucket.resize(n);
+  for (uint64_t j = 0; j < n; ++j) {
+    P.B[j] = (u128)j * T + stratified_offset(T, seed, filter, t, j);
+    P.bucket[j] = j;  // r_j < T
+  }
+  return P;
+}
+
 void spacing_prefix(uint64_t n, uint64_t seed, uint32_t filter, uint32_t t,
                     std::vector<uint64_t>* S) {
   S->assign(n + 1, 0);
@@ -149,6 +173,11 @@ void cutpoint_method(const uint64_t* Q, uint64_t n, const uint32_t* I, const Pos
 void resample(const uint64_t* Q, uint64_t n, int scheme, uint64_t seed, uint32_t filter,
               uint32_t t, uint32_t* anc) {
   uint64_t T = Q[n - 1];
+  if (scheme == STRATIFIED) {
+    Positions P = stratified_positions(n, T, seed, filter, t);
+    walk(Q, n, P, anc);
+    return;
+  }
   if (scheme == SYSTEMATIC || scheme == SYSTEMATIC_CUTPOINT) {
     Positions P = systematic_positions(n, T, seed, filter, t);
     if (scheme == SYSTEMATIC) {

@@ -12,6 +12,10 @@
 - Multinomial resampling: the offspring vector follows Multinomial(N, W/T)
   (G-test against the exactly enumerated pmf), and the sorted positions from
   exponential spacings follow the uniform order-statistic laws Beta(j+1, N-j).
+- Stratified resampling: each slot's position stays in its own stratum and
+  picks particle i with probability |stratum j intersect interval i| (G-test per
+  slot against those exact overlaps); offspring within floor(N W_i / T) - 1 and
+  ceil(N W_i / T) + 1; mean offspring N W_i / T.
 """
 import itertools
 import math
@@ -93,7 +97,7 @@ def test_cutpoint_definition_and_L_properties(orc):
                 assert I[k] == ref
 
 
-@pytest.mark.parametrize("positions", ["systematic", "multinomial"])
+@pytest.mark.parametrize("positions", ["systematic", "multinomial", "stratified"])
 def test_walk_naive_cutpoint_agree(orc, positions):
     rng = np.random.default_rng(5)
     for trial in range(60):
@@ -236,7 +240,7 @@ def test_quantize_weights_exact(orc):
         orc.quantize_weights(np.zeros(3, np.float32))
 
 
-@pytest.mark.parametrize("scheme", [0, 1, 2, 3])
+@pytest.mark.parametrize("scheme", [0, 1, 2, 3, 4])
 def test_edge_cases(orc, scheme):
     # single particle
     assert orc.resample_weights(np.array([0.3], np.float32), scheme, 1, 0, 0).tolist() == [0]
@@ -267,3 +271,82 @@ def test_systematic_offset_uniform_and_unbiased(orc):
     p = W.astype(np.float64) / float(Q[-1])
     # systematic counts are floor or ceil of N p_i: per-draw variance <= 1/4
     assert np.all(np.abs(c / reps - n * p) < 5 * 0.5 / np.sqrt(reps))
+
+
+def test_stratified_offsets_in_range_and_uniform(orc):
+    """r_j = floor(R_j T / 2^64) lies in [0, T) and is uniform, for even and odd j
+    (the two word pairs of one draw)."""
+    T = (1 << 61) - 999
+    for j in (0, 1, 6, 7):
+        r = np.array([orc.stratified_offset(T, 23, 1, t, j) for t in range(10_000)], np.float64)
+        assert r.max() < T
+        assert stats.kstest(r / T, "uniform").pvalue > 1e-4
+    # independent across slots: the two words of one draw, and different draws
+    # (one offset for every slot would be systematic resampling)
+    for j0, j1 in ((4, 5), (0, 2), (3, 9)):
+        a = np.array([orc.stratified_offset(T, 23, 1, t, j0) for t in range(5000)], np.float64) / T
+        b = np.array([orc.stratified_offset(T, 23, 1, t, j1) for t in range(5000)], np.float64) / T
+        assert abs(np.corrcoef(a, b)[0, 1]) < 0.06, (j0, j1)
+
+
+def test_stratified_offspring_bounds(orc):
+    """Particle i covers L = N W_i / T strata: at least floor(L) - 1 of its
+    strata lie wholly inside its interval and at most two more touch it."""
+    rng = np.random.default_rng(16)
+    for trial in range(200):
+        n = int(rng.integers(1, 300))
+        W = _random_cdf(rng, n, zero_frac=0.2)
+        Q = orc.cdf_scan(W)
+        T = int(Q[-1])
+        anc = orc.resample_cdf(Q, orc.STRATIFIED, 3, 1, trial)
+        assert np.all(np.diff(anc.astype(np.int64)) >= 0)
+        c = np.bincount(anc, minlength=n)
+        assert c.sum() == n
+        for i in range(n):
+            lo, rem = divmod(n * int(W[i]), T)
+            hi = lo if rem == 0 else lo + 1
+            assert max(0, lo - 1) <= c[i] <= hi + 1, (trial, i, c[i], lo, rem)
+            if W[i] == 0:
+                assert c[i] == 0
+
+
+def test_stratified_per_slot_law(orc):
+    """Slot j's position is uniform on its stratum [j T, (j+1) T) (in units of
+    n Q): it picks particle i with probability |[jT, (j+1)T) intersect
+    [n Q_{i-1}, n Q_i)| / T.  G-test of every slot's ancestor over seeds."""
+    W = np.array([3, 0, 7, 1, 5], np.uint64) * np.uint64(1 << 40)
+    n = W.size
+    Q = orc.cdf_scan(W)
+    T = int(Q[-1])
+    reps = 20_000
+    anc = np.array([orc.resample_cdf(Q, orc.STRATIFIED, 5, 2, t) for t in range(reps)])
+    edges = [0] + [n * int(q) for q in Q]
+    for j in range(n):
+        p = np.array([max(0, min((j + 1) * T, edges[i + 1]) - max(j * T, edges[i])) / T
+                      for i in range(n)])
+        assert abs(p.sum() - 1) < 1e-12
+        obs = np.bincount(anc[:, j], minlength=n)
+        assert np.all(obs[p == 0] == 0)
+        keep = p > 0
+        exp = reps * p[keep]
+        g = 2 * np.sum(np.where(obs[keep] > 0, obs[keep] * np.log(np.maximum(obs[keep], 1) / exp), 0))
+        dof = keep.sum() - 1
+        if dof > 0:
+            assert stats.chi2.sf(g, dof) > 1e-4, (j, obs, exp)
+
+
+def test_stratified_mean_offspring(orc):
+    rng = np.random.default_rng(19)
+    n = 40
+    W = _random_cdf(rng, n, zero_frac=0.25)
+    Q = orc.cdf_scan(W)
+    T = int(Q[-1])
+    reps = 4000
+    c = np.array([np.bincount(orc.resample_cdf(Q, orc.STRATIFIED, 7, 4, t), minlength=n)
+                  for t in range(reps)], np.float64)
+    L = n * W.astype(np.float64) / T
+    sd = c.std(0, ddof=1)
+    ok = sd > 0
+    z = (c.mean(0) - L)[ok] / (sd[ok] / np.sqrt(reps))
+    assert np.all(np.abs(z) < 5)
+    assert np.allclose(c.mean(0)[~ok], L[~ok], atol=1e-9)  # degenerate counts are exact
