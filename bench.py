@@ -17,7 +17,7 @@ roofline: the dominant kernel's algorithmic bytes per launch / its mean
          CUDA-event duration (pf_step_profiled), against the measured copy
          bandwidth in MEASURED_PEAKS.json.
 Extra keys: the same cycle at N = 2^24 (the single-filter target size) and
-with multinomial resampling; batched filters (4096 uneven filters, one
+with multinomial and stratified resampling; batched filters (4096 uneven filters, one
 persistent launch per cycle, against per-filter launches); the served form
 (10,000 streams under Poisson load, continuous batching, p50/p90/p99 latency;
 and under an 8 GB budget where admission waits); FP32 against FP64 precision.
@@ -53,6 +53,7 @@ BYTES_PER_PARTICLE = {
     "spacing_scan": 8,            # write S
     "partition": 0,               # one merge-path split per 2048 merged elements
     "merge_systematic": 8 + 4,    # read Q; write ancestors
+    "stratified": 8 + 4,          # read Q; write ancestors
     "merge_multinomial": 8 + 8 + 4,  # read Q and S; write ancestors
     "cutpoint_search": 8 + 4,     # read Q; write I
     "cutpoint_method": 4 + 8 + 4,  # read I, Q at the start; write ancestors
@@ -70,7 +71,8 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--n", type=int, default=N_DEFAULT)
     p.add_argument("--scheme", default="systematic")
-    p.add_argument("--no-extra", action="store_true", help="skip the 2^24 and multinomial lines")
+    p.add_argument("--no-extra", action="store_true",
+                   help="skip the 2^24, multinomial, stratified, batched, precision and served lines")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     p.add_argument("--batched-only", action="store_true",
                    help="print only the batched-filters measurement (one JSON line)")
@@ -345,14 +347,16 @@ def bench_ours(args):
             "kernels": {k: {"ms": round(v, 5), "gbs": round(b24[k] / (v / 1e3) / 1e9, 1)}
                         for k, v in prof24.items()}}
         f24.close()
-        if "multinomial" not in args.scheme:
-            fm = pf.Filter(n, seed=3, scheme="multinomial", precision="fp32", stream=stream)
+        for other in ("multinomial", "stratified"):  # the other resampling schemes
+            if other == args.scheme:
+                continue
+            fm = pf.Filter(n, seed=3, scheme=other, precision="fp32", stream=stream)
             fm.run(y_dev[:W])
             fm.sync()
             Km = min(K, 100)
             msm = time_cycles(fm, y_dev, W, Km, stream, flush)
             profm = kernel_profile(fm, y, W + Km, 5, flush)
-            extra["multinomial"] = {
+            extra[other] = {
                 "value": n * Km / (msm / 1e3), "unit": UNIT, "steps": Km, "ms_per_step": msm / Km,
                 "kernels": {k: round(v, 5) for k, v in profm.items()}}
             fm.close()

@@ -61,13 +61,21 @@ typedef enum {
  *                         paper's parallelized cut-point search and cut-point
  *                         method (Section 3.2); identical output.
  *  SYSTEMATIC_CUTPOINT    same positions as SYSTEMATIC, cut-point search.
+ *  STRATIFIED             positions = (j + u_j) T / n, one uniform u_j in
+ *                         each stratum (Section 3.1, "Stratified
+ *                         Resampling"): u_j from word pair 2 (j mod 2),
+ *                         2 (j mod 2) + 1 of the draw (seed, filter, t,
+ *                         floor(j/2), purpose 9).  Single filters and
+ *                         pf_resample; the batched and served forms take
+ *                         the first four schemes.
  * Ancestors come out in nondecreasing order (the sorted expansion of the
  * offspring counts). */
 typedef enum {
   PF_MULTINOMIAL = 0,
   PF_SYSTEMATIC = 1,
   PF_MULTINOMIAL_CUTPOINT = 2,
-  PF_SYSTEMATIC_CUTPOINT = 3
+  PF_SYSTEMATIC_CUTPOINT = 3,
+  PF_STRATIFIED = 4
 } pf_scheme;
 
 /* State precision (the paper's GPU(sp) and GPU(dp) modes, Section 4).

@@ -199,7 +199,10 @@ inline uint32_t sys_chunks(uint64_t n) { return (uint32_t)cdiv(2 * n, SYS_D); }
 pf_status launch_resample(int scheme, const PosArgs& pa, uint64_t n, uint32_t* I,
                           uint64_t* splits, cudaStream_t s, KTimer* tm = nullptr) {
   const bool multi = is_multinomial(scheme);
-  if (!is_cutpoint(scheme) && multi) {
+  if (scheme == PF_STRATIFIED) {
+    k_strat<<<(unsigned)cdiv(n, BLOCK), BLOCK, 0, s>>>(pa);
+    mark(tm, "stratified", s);
+  } else if (!is_cutpoint(scheme) && multi) {
     const uint32_t chunks = merge_chunks(n);
     const unsigned pgrid = (unsigned)cdiv((uint64_t)(chunks + 1) * 32, BLOCK);
     k_partition<POS_MULTINOMIAL><<<pgrid, BLOCK, 0, s>>>(pa, splits, chunks + 1, MERGE_D);
@@ -397,7 +400,7 @@ pf_status pf_create(const pf_config* cfg, pf_filter** out) {
   *out = nullptr;
   if (cfg->n_particles < 1 || cfg->n_particles > PF_MAX_PARTICLES)
     return set_err(PF_ERR_INVALID, "n_particles must be in [1, 2^26]");
-  if (cfg->scheme < 0 || cfg->scheme > 3) return set_err(PF_ERR_INVALID, "bad scheme");
+  if (cfg->scheme < 0 || cfg->scheme > 4) return set_err(PF_ERR_INVALID, "bad scheme");
   if (cfg->precision != PF_FP32 && cfg->precision != PF_FP64) return set_err(PF_ERR_INVALID, "bad precision");
   if (!cfg->known_variances && !(cfg->a_sigma >= 1.0 && cfg->a_tau >= 1.0))
     return set_err(PF_ERR_INVALID, "prior shapes must be >= 1");
@@ -775,7 +778,7 @@ pf_status resample_common(const float* w, uint64_t n, uint64_t seed, uint32_t fi
                           uint32_t t, int scheme, uint32_t* anc, uint64_t* Q_out, void* stream) {
   if (!w || (!anc && !Q_out)) return set_err(PF_ERR_INVALID, "NULL pointer");
   if (n < 1 || n > PF_MAX_PARTICLES) return set_err(PF_ERR_INVALID, "n must be in [1, 2^26]");
-  if (scheme < 0 || scheme > 3) return set_err(PF_ERR_INVALID, "bad scheme");
+  if (scheme < 0 || scheme > 4) return set_err(PF_ERR_INVALID, "bad scheme");
   cudaStream_t s = (cudaStream_t)stream;
   Scratch sc;
   const bool multi = anc && is_multinomial(scheme), cut = anc && is_cutpoint(scheme);
@@ -906,7 +909,7 @@ extern "C" pf_status pf_resample_noalloc(const float* w_dev, uint64_t n, uint64_
   if (n < 1 || n > PF_NOALLOC_MAX_PARTICLES)
     return set_err(PF_ERR_INVALID, "pf_resample_noalloc: n must be in [1, %llu]",
                    (unsigned long long)PF_NOALLOC_MAX_PARTICLES);
-  if (scheme < 0 || scheme > 3) return set_err(PF_ERR_INVALID, "bad scheme");
+  if (scheme < 0 || scheme > 4) return set_err(PF_ERR_INVALID, "bad scheme");
   cudaStream_t s = (cudaStream_t)stream;
   char* base = nullptr;
   pf_status st = noalloc_scratch(&base);

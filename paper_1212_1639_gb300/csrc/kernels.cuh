@@ -921,6 +921,60 @@ __device__ __forceinline__ uint64_t sys_first_slot(uint64_t Qi, uint64_t n, uint
   return q < n ? q : n;
 }
 
+// Stratified resampling (Section 3.1, one uniform in each of the n equal
+// strata): slot j's position is P_j = j T + r_j with its own r_j in [0, T),
+// r_j = floor(R_j T / 2^64) from word pair 2 (j mod 2), 2 (j mod 2) + 1 of the
+// draw (seed, filter, t, floor(j/2), STRATIFIED); slot j goes to the particle
+// i with n Q_{i-1} <= P_j < n Q_i.
+__device__ __forceinline__ uint64_t strat_offset(uint64_t T, uint64_t seed, uint32_t filter,
+                                                 uint32_t t, uint64_t j) {
+  const U4 w = draw(seed, filter, t, (uint32_t)(j >> 1), P_STRATIFIED, 0);
+  const uint64_t R = (j & 1) ? (((uint64_t)w.d << 32) | w.c) : (((uint64_t)w.b << 32) | w.a);
+  return __umul64hi(R, T);
+}
+// #{j : P_j < n q}: with c = floor(n q / T), P_c is the only position in
+// [c T, c T + T), so the count is c or c + 1.
+__device__ __forceinline__ uint64_t strat_first(uint64_t q, uint64_t n, uint64_t T, const SysDiv& dv,
+                                                uint64_t seed, uint32_t filter, uint32_t t) {
+  const U128 X = mul64x32(q, (uint32_t)n);
+  if (X.hi == 0 && X.lo == 0) return 0;
+  const uint64_t c = sys_floor_div(X, dv);  // X <= n T < 2^32 T
+  if (c >= n) return n;
+  const U128 P = add128(mul64x32(T, (uint32_t)c), strat_offset(T, seed, filter, t, c));
+  return lt128(P, X) ? c + 1 : c;
+}
+// One thread per particle: particle i owns the slots [first(n Q_{i-1}),
+// first(n Q_i)); the lower end comes from the neighbouring lane.  A warp
+// stores the ranges longer than 32 slots together.
+static __global__ void __launch_bounds__(BLOCK) k_strat(PosArgs a) {
+  const uint64_t n = a.n;
+  const uint32_t t = a.t_dev ? *a.t_dev : a.t_arg;
+  const uint64_t T = a.Q[n - 1];
+  const uint64_t i = (uint64_t)blockIdx.x * BLOCK + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  if (T == 0) {  // empty CDF (flagged): keep every index in range
+    if (i == 0) atomicOr(&a.ctl->err, ERR_NUMERIC);
+    if (i < n) a.anc[i] = (uint32_t)i;
+    return;
+  }
+  const SysDiv dv = make_sysdiv(T);
+  const uint64_t j1 = i < n ? strat_first(a.Q[i], n, T, dv, a.seed, a.filter, t) : n;
+  uint64_t j0 = __shfl_up_sync(0xffffffffu, j1, 1);
+  if (lane == 0) j0 = i == 0 ? 0 : (i < n ? strat_first(a.Q[i - 1], n, T, dv, a.seed, a.filter, t) : n);
+  const uint64_t cnt = i < n ? j1 - j0 : 0;
+  if (cnt <= 32) {
+    for (uint64_t q = j0; q < j0 + cnt; ++q) a.anc[q] = (uint32_t)i;
+  }
+  uint32_t heavy = __ballot_sync(0xffffffffu, cnt > 32);
+  while (heavy) {
+    const int l = __ffs(heavy) - 1;
+    heavy &= heavy - 1;
+    const uint64_t s0 = __shfl_sync(0xffffffffu, j0, l), s1 = __shfl_sync(0xffffffffu, j1, l);
+    const uint32_t v = (uint32_t)__shfl_sync(0xffffffffu, i, l);
+    for (uint64_t q = s0 + lane; q < s1; q += 32) a.anc[q] = v;
+  }
+}
+
 static __global__ void __launch_bounds__(SYS_THREADS) k_merge_sys(PosArgs a, const uint64_t* splits) {
   __shared__ uint32_t s_anc[SYS_D];
   __shared__ uint32_t s_run[SYS_MAX_RUNS][3];

@@ -23,7 +23,8 @@ PF_OK, PF_ERR_INVALID, PF_ERR_OOM, PF_ERR_CUDA, PF_ERR_NUMERIC, PF_ERR_TIMEOUT, 
 STATUS_NAMES = {0: "PF_OK", 1: "PF_ERR_INVALID", 2: "PF_ERR_OOM", 3: "PF_ERR_CUDA",
                 4: "PF_ERR_NUMERIC", 5: "PF_ERR_TIMEOUT", 6: "PF_ERR_BUSY"}
 MULTINOMIAL, SYSTEMATIC, MULTINOMIAL_CUTPOINT, SYSTEMATIC_CUTPOINT = 0, 1, 2, 3
-SCHEMES = {"multinomial": 0, "systematic": 1, "multinomial_cutpoint": 2, "systematic_cutpoint": 3}
+SCHEMES = {"multinomial": 0, "systematic": 1, "multinomial_cutpoint": 2, "systematic_cutpoint": 3,
+           "stratified": 4}
 FP32, FP64 = 0, 1
 MAX_PARTICLES = 1 << 26
 NOALLOC_MAX_PARTICLES = 1 << 20

@@ -71,12 +71,12 @@ def test_fp64_paper_config_multinomial(pf, orc):
     _run(pf, orc, 1024, 100, 0, 1)
 
 
-@pytest.mark.parametrize("scheme", [0, 1, 2, 3])
+@pytest.mark.parametrize("scheme", [0, 1, 2, 3, 4])
 def test_fp32_all_schemes_ragged(pf, orc, scheme):
     _run(pf, orc, 5000, 30, scheme, 0)
 
 
-@pytest.mark.parametrize("scheme", [0, 1])
+@pytest.mark.parametrize("scheme", [0, 1, 4])
 def test_fp64_schemes_multi_tile(pf, orc, scheme):
     _run(pf, orc, 3 * 4096 + 17, 15, scheme, 1)
 
@@ -130,6 +130,7 @@ def test_outlier_observation_large(pf, orc):
     become runs of the CTA."""
     y = np.array([0.3, 40.0, 0.1])
     _run(pf, orc, 300_001, y.size, 1, 0, y=y)
+    _run(pf, orc, 300_001, y.size, 4, 0, y=y)  # stratified: the warp stores long ranges
     _run(pf, orc, 2_600_003, 2, 1, 0, y=np.array([0.3, -35.0]), every_step=True, seed=3)
 
 

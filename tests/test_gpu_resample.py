@@ -18,7 +18,7 @@ from paper_1212_1639_gb300 import synth
 pytestmark = pytest.mark.gpu
 
 SMALL = [1, 2, 3, 5, 64, 1000, 4095, 4096, 4097, 12345, (1 << 16) + 3]
-SCHEMES = [0, 1, 2, 3]
+SCHEMES = [0, 1, 2, 3, 4]
 
 
 def _u32(t):
@@ -45,7 +45,7 @@ def test_resample_2p20_bit_exact(pf, orc, scheme):
         assert np.array_equal(anc, ref), (s, scheme)
 
 
-@pytest.mark.parametrize("scheme", [0, 1])
+@pytest.mark.parametrize("scheme", [0, 1, 4])
 @pytest.mark.parametrize("s", [1.0, 5.0])
 def test_resample_2p24_bit_exact(pf, orc, scheme, s):
     """Full size of the resampling sweep, in the configuration the bench times."""

@@ -28,7 +28,7 @@ def series():
 
 
 @pytest.mark.parametrize("precision", [0, 1])
-@pytest.mark.parametrize("scheme", [0, 1, 2, 3])
+@pytest.mark.parametrize("scheme", [0, 1, 2, 3, 4])
 def test_known_variances_match_kalman(orc, series, precision, scheme):
     _, y = series
     n = 1 << 15
