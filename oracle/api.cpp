@@ -188,6 +188,7 @@ typedef struct {
   int32_t precision;
   int32_t known_variances;
   double x0_mean, x0_var, a_sigma, b_sigma, a_tau, b_tau, sigma2, tau2;
+  int32_t algorithm;
 } or_config;
 
 static Config to_cfg(const or_config* c) {
@@ -197,6 +198,7 @@ static Config to_cfg(const or_config* c) {
   cfg.x0_mean = c->x0_mean; cfg.x0_var = c->x0_var; cfg.a_sigma = c->a_sigma;
   cfg.b_sigma = c->b_sigma; cfg.a_tau = c->a_tau; cfg.b_tau = c->b_tau;
   cfg.sigma2 = c->sigma2; cfg.tau2 = c->tau2;
+  cfg.algorithm = c->algorithm;
   return cfg;
 }
 

@@ -40,7 +40,7 @@ void philox4x64_10(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]
 enum Purpose : uint32_t {
   P_INIT_X = 1, P_INIT_SIGMA = 2, P_INIT_TAU = 3,
   P_STATE = 4, P_GAMMA_SIGMA = 5, P_GAMMA_TAU = 6,
-  P_SYS_OFFSET = 7, P_SPACING = 8, P_STRATIFIED = 9,
+  P_SYS_OFFSET = 7, P_SPACING = 8, P_STRATIFIED = 9, P_BOOT_STATE = 10,
 };
 
 // One 128-bit draw addressed by (seed, filter, t, j, purpose, attempt):
@@ -176,6 +176,7 @@ struct Config {
   double x0_mean, x0_var, a_sigma, b_sigma, a_tau, b_tau;
   int32_t known_variances;
   double sigma2, tau2;
+  int32_t algorithm;  // 0 = particle learning, 1 = bootstrap filter (known variances)
 };
 
 struct Estimates {

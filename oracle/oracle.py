@@ -34,7 +34,10 @@ class OrConfig(C.Structure):
                 ("x0_mean", C.c_double), ("x0_var", C.c_double),
                 ("a_sigma", C.c_double), ("b_sigma", C.c_double),
                 ("a_tau", C.c_double), ("b_tau", C.c_double),
-                ("sigma2", C.c_double), ("tau2", C.c_double)]
+                ("sigma2", C.c_double), ("tau2", C.c_double), ("algorithm", C.c_int32)]
+
+
+PARTICLE_LEARNING, BOOTSTRAP = 0, 1
 
 
 def _declare(L):
@@ -266,11 +269,15 @@ def resample_weights(w, scheme, seed, filt, t):
 
 def make_config(n, seed=1212, filter_id=0, scheme=MULTINOMIAL, precision=FP64,
                 x0_mean=0.0, x0_var=10.0, a_sigma=3.0, b_sigma=2.0, a_tau=3.0, b_tau=2.0,
-                known_variances=False, sigma2=1.0, tau2=0.1):
+                known_variances=False, sigma2=1.0, tau2=0.1, algorithm=PARTICLE_LEARNING):
+    """algorithm: PARTICLE_LEARNING or BOOTSTRAP (Algorithm "Particle Filtering",
+    which takes the variances as known)."""
+    if algorithm == BOOTSTRAP and not known_variances:
+        raise ValueError("the bootstrap filter takes known variances")
     return OrConfig(n=n, seed=seed, filter_id=filter_id, scheme=scheme, precision=precision,
                     known_variances=int(known_variances), x0_mean=x0_mean, x0_var=x0_var,
                     a_sigma=a_sigma, b_sigma=b_sigma, a_tau=a_tau, b_tau=b_tau,
-                    sigma2=sigma2, tau2=tau2)
+                    sigma2=sigma2, tau2=tau2, algorithm=int(algorithm))
 
 
 ESTIMATE_FIELDS = ("t", "x_mean", "x_var", "sigma2_mean", "sigma2_var",

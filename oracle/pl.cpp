@@ -135,6 +135,7 @@ template <class R> class Filter : public FilterBase {
   }
 
   int step(double y) override {
+    if (cfg.algorithm == 1) return step_bootstrap(y);
     const R yr = (R)y;
     // Step 1: predictive weights and the resampling CDF.
     std::vector<R> ell(n);
@@ -195,6 +196,53 @@ template <class R> class Filter : public FilterBase {
     x.swap(xn); s2.swap(s2n); t2.swap(t2n); bs.swap(bsn); bt.swap(btn);
     ++t;
     return fail ? 4 : 0;
+  }
+
+  // Algorithm "Particle Filtering" (paper Section 2) for the local-level
+  // model with known sigma^2, tau^2 (the bootstrap filter):
+  //   Step 1  propagate x_t ~ p(x_t | x~_{t-1}) = N(x~_{t-1}, tau^2),
+  //   Step 2  weights w_t proportional to p(y_t | x_t) = N(y_t; x_t, sigma^2),
+  //   Step 3  resample x~_t from x_t with the weights w_t.
+  // The normal of step 1 is Box-Muller's first output from the draw
+  // (seed, filter, t, i, BOOT_STATE).  The weights, the CDF, the log
+  // marginal likelihood increment and the resampling are those of particle
+  // learning with sigma^2 + tau^2 replaced by sigma^2.
+  // pin: the Kalman filter (tests/test_oracle_pl.py).
+  int step_bootstrap(double y) {
+    const R yr = (R)y;
+    std::vector<R> ell(n);
+    for (uint64_t i = 0; i < n; ++i) {
+      W4 w = draw(cfg.seed, cfg.filter_id, t, (uint32_t)i, P_BOOT_STATE, 0);
+      R Z = bm_normal<R>(w);
+      R sv = std::sqrt(t2[i]);
+      R xz = sv * Z;
+      x[i] = x[i] + xz;
+      ell[i] = log_pred<R>(x[i], s2[i], (R)0, yr);
+    }
+    R m = ell[0];
+    for (uint64_t i = 1; i < n; ++i)
+      if (ell[i] > m) m = ell[i];
+    if (!std::isfinite((double)m)) return 4;
+    std::vector<uint64_t> W(n);
+    typename ExpSum<R>::T S;
+    for (uint64_t i = 0; i < n; ++i) {
+      R e;
+      R dl = ell[i] - m;
+      W[i] = quant_exp<R>(dl, k, &e);
+      S.add(e);
+    }
+    cdf_scan(W.data(), n, Q.data());
+    logml += (double)m + std::log(S.value()) - std::log((double)n) - 0.5 * LOG_2PI;
+    resample(Q.data(), n, cfg.scheme, cfg.seed, cfg.filter_id, t, anc.data());
+    std::vector<R> xn(n), s2n(n), t2n(n);
+    std::vector<B> bsn(n), btn(n);
+    for (uint64_t j = 0; j < n; ++j) {
+      const uint32_t a = anc[j];
+      xn[j] = x[a]; s2n[j] = s2[a]; t2n[j] = t2[a]; bsn[j] = bs[a]; btn[j] = bt[a];
+    }
+    x.swap(xn); s2.swap(s2n); t2.swap(t2n); bs.swap(bsn); bt.swap(btn);
+    ++t;
+    return 0;
   }
 
   // y - x_{t+1}: in binary32 from the rounded observation, in binary64 from y.

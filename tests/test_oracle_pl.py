@@ -54,6 +54,67 @@ def test_known_variances_match_kalman(orc, series, precision, scheme):
 
 
 @pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("scheme", [0, 1, 4])
+def test_bootstrap_filter_matches_kalman(orc, series, precision, scheme):
+    """Algorithm "Particle Filtering" (the bootstrap filter, known variances):
+    blind propagation then weighting by p(y | x) resamples with a noisier
+    sample than particle learning's fully adapted step, so its filtered mean
+    sits within a larger multiple of sd/sqrt(N) of the Kalman mean; the
+    log-likelihood estimate is still within Monte Carlo error."""
+    _, y = series
+    n = 1 << 15
+    km, kv, kll = orc.kalman(y, 0.0, 10.0, 1.0, 0.1)
+    cfg = orc.make_config(n, seed=300 + scheme, scheme=scheme, precision=precision,
+                          known_variances=True, sigma2=1.0, tau2=0.1, algorithm=orc.BOOTSTRAP)
+    f = orc.Filter(cfg)
+    z, vr = [], []
+    for t in range(y.size):
+        f.step(y[t])
+        e = f.estimate()
+        assert e["t"] == t + 1
+        z.append((e["x_mean"] - km[t]) / np.sqrt(kv[t] / n))
+        vr.append(e["x_var"] / kv[t])
+    z = np.array(z)
+    assert np.max(np.abs(z)) < 15, np.max(np.abs(z))
+    assert np.sqrt(np.mean(z ** 2)) < 5
+    assert np.max(np.abs(np.array(vr[5:]) - 1)) < 0.15
+    assert abs(f.estimate()["log_marglik"] - kll) < 0.3
+    s = f.state()
+    assert np.all(s["sigma2"] == np.float32(1.0) if precision == 0 else s["sigma2"] == 1.0)
+    assert np.all(s["tau2"] == np.float32(0.1) if precision == 0 else s["tau2"] == 0.1)
+
+
+def test_bootstrap_one_step_by_hand(orc):
+    """One bootstrap cycle recomputed here step by step in binary64 from the
+    oracle's exported primitives (its normals, deterministic log, weight
+    quantisation and systematic resampling): propagated particles, weights,
+    exact CDF, ancestors, resampled state and log-ML increment."""
+    n, y, s2, t2, seed = 37, 0.7, 1.3, 0.4, 11
+    cfg = orc.make_config(n, seed=seed, scheme=1, precision=1, known_variances=True,
+                          sigma2=s2, tau2=t2, algorithm=orc.BOOTSTRAP)
+    f = orc.Filter(cfg)
+    x0 = f.state()["x"].copy()
+    f.step(y)
+    # Step 1: x' = x + sqrt(tau^2) Z, Z Box-Muller from (seed, 0, t=0, i, BOOT_STATE = 10)
+    Z = orc.normals(seed, 0, 0, 10, n, np.float64)
+    xp = x0 + np.sqrt(t2) * Z
+    # Step 2: l = -(log sigma^2 + (y - x')^2 / sigma^2) / 2 (log(2 pi)/2 dropped)
+    lg = orc.det_log(np.full(n, s2), np.float64)
+    ell = -0.5 * (lg + (y - xp) ** 2 / s2)
+    m = ell.max()
+    W, e = orc.quant_exp(ell - m, orc.cdf_shift(n), np.float64)
+    Q = np.cumsum(W.astype(object)).astype(np.uint64)
+    assert np.array_equal(f.cdf(), Q)
+    # Step 3: systematic ancestors of that CDF, and the resampled particles
+    anc = orc.resample_cdf(Q, orc.SYSTEMATIC, seed, 0, 0)
+    assert np.array_equal(f.ancestors(), anc)
+    assert np.array_equal(f.state()["x"], xp[anc])
+    # log-ML increment: m + log(sum e) - log n - log(2 pi)/2
+    ref = m + np.log(np.sum(e)) - np.log(n) - 0.5 * np.log(2 * np.pi)
+    assert abs(f.estimate()["log_marglik"] - ref) < 1e-12
+
+
+@pytest.mark.parametrize("precision", [0, 1])
 def test_known_states_conjugate_inverse_gamma(orc, precision):
     T = 50
     x, y = synth.local_level_series(7, T, sigma2=1.0, tau2=0.1)
