@@ -105,7 +105,21 @@ typedef struct {
   pf_alloc_fn alloc;       /* NULL: cudaMallocAsync / cudaFreeAsync on stream */
   pf_free_fn free;
   void* alloc_ctx;
+  int32_t algorithm;       /* pf_algorithm; 0 = particle learning */
 } pf_config;
+
+/* The cycle run by a single filter.
+ *  PARTICLE_LEARNING  Algorithm "Particle Learning" (Section 2): resample
+ *                     with p(y_{t+1} | z_t), propagate x conditional on
+ *                     y_{t+1}, update the sufficient statistics, draw theta.
+ *  BOOTSTRAP          Algorithm "Particle Filtering" (Section 2) with the
+ *                     variances known (known_variances != 0 required):
+ *                     propagate x_t ~ N(x~_{t-1}, tau^2) (Box-Muller's first
+ *                     output of the draw (seed, filter, t, i, purpose 10)),
+ *                     weight by p(y_t | x_t) = N(y_t; x_t, sigma^2),
+ *                     resample.  Same CDF, resampling schemes, summaries and
+ *                     log marginal likelihood estimate.  Single filters only. */
+typedef enum { PF_PARTICLE_LEARNING = 0, PF_BOOTSTRAP = 1 } pf_algorithm;
 
 #define PF_MAX_PARTICLES (1ull << 26)
 

@@ -68,6 +68,7 @@ struct pf_filter {
   unsigned cdf_grid = 0;   // cooperative CDF + systematic resampling grid (0: not used)
   bool cdf_staged = false; // its CTAs own several tiles: TMA-staged variant
   int cdf_per = 16;         // particles per thread of its tiles (8: 2048-particle tiles)
+  bool bootstrap = false;   // Algorithm "Particle Filtering" instead of particle learning
   uint32_t nparts = 0;      // log-ML partials per cycle
   uint64_t* cta_tot = nullptr;
   std::vector<void*> allocs;
@@ -238,8 +239,13 @@ pf_status enqueue_cycle(pf_filter* f, KTimer* tm = nullptr, const double* y_src 
   a.y_val = y_val;
   const uint64_t n = f->n;
   if (tm) cudaEventRecord(tm->ev[0], s);
-  k_weights<R><<<(unsigned)cdiv(n, (uint64_t)BLOCK * W_PER_THREAD), BLOCK, 0, s>>>(a);
-  mark(tm, "weights", s);
+  if (f->bootstrap) {  // Algorithm "Particle Filtering": propagate blind, then weigh
+    k_boot_pw<R><<<(unsigned)cdiv(n, BLOCK), BLOCK, 0, s>>>(a);
+    mark(tm, "propagate_weights", s);
+  } else {
+    k_weights<R><<<(unsigned)cdiv(n, (uint64_t)BLOCK * W_PER_THREAD), BLOCK, 0, s>>>(a);
+    mark(tm, "weights", s);
+  }
   ScanArgs sa;
   sa.src = f->ell;
   sa.Q = f->Q;
@@ -306,7 +312,10 @@ pf_status enqueue_cycle(pf_filter* f, KTimer* tm = nullptr, const double* y_src 
     pf_status st = launch_resample(f->scheme, pa, n, f->I, f->splits, s, tm);
     if (st != PF_OK) return st;
   }
-  if constexpr (sizeof(R) == 4) {  // binary32: two slots per thread, paired arithmetic
+  if (f->bootstrap) {
+    k_boot_gather<R><<<(unsigned)cdiv(n, BLOCK), BLOCK, 0, s>>>(a);
+    mark(tm, "gather", s);
+  } else if constexpr (sizeof(R) == 4) {  // binary32: two slots per thread, paired arithmetic
     if (f->learn) k_propagate2<true><<<f->prop_grid, BLOCK, 0, s>>>(a);
     else k_propagate2<false><<<f->prop_grid, BLOCK, 0, s>>>(a);
   } else {
@@ -334,7 +343,9 @@ pf_status build_graph(pf_filter* f) {
   CK(cudaGraphGetNodes(g, nullptr, &nn));
   std::vector<cudaGraphNode_t> nodes(nn);
   CK(cudaGraphGetNodes(g, nodes.data(), &nn));
-  const void* wfun = f->fp64 ? (const void*)k_weights<double> : (const void*)k_weights<float>;
+  const void* wfun = f->bootstrap
+      ? (f->fp64 ? (const void*)k_boot_pw<double> : (const void*)k_boot_pw<float>)
+      : (f->fp64 ? (const void*)k_weights<double> : (const void*)k_weights<float>);
   for (cudaGraphNode_t nd : nodes) {
     cudaGraphNodeType ty;
     CK(cudaGraphNodeGetType(nd, &ty));
@@ -401,6 +412,10 @@ pf_status pf_create(const pf_config* cfg, pf_filter** out) {
   if (cfg->n_particles < 1 || cfg->n_particles > PF_MAX_PARTICLES)
     return set_err(PF_ERR_INVALID, "n_particles must be in [1, 2^26]");
   if (cfg->scheme < 0 || cfg->scheme > 4) return set_err(PF_ERR_INVALID, "bad scheme");
+  if (cfg->algorithm != PF_PARTICLE_LEARNING && cfg->algorithm != PF_BOOTSTRAP)
+    return set_err(PF_ERR_INVALID, "bad algorithm");
+  if (cfg->algorithm == PF_BOOTSTRAP && !cfg->known_variances)
+    return set_err(PF_ERR_INVALID, "the bootstrap filter takes known variances");
   if (cfg->precision != PF_FP32 && cfg->precision != PF_FP64) return set_err(PF_ERR_INVALID, "bad precision");
   if (!cfg->known_variances && !(cfg->a_sigma >= 1.0 && cfg->a_tau >= 1.0))
     return set_err(PF_ERR_INVALID, "prior shapes must be >= 1");
@@ -418,6 +433,7 @@ pf_status pf_create(const pf_config* cfg, pf_filter** out) {
   f->ntiles = (uint32_t)cdiv(f->n, TILE);
   f->fp64 = cfg->precision == PF_FP64;
   f->learn = !cfg->known_variances;
+  f->bootstrap = cfg->algorithm == PF_BOOTSTRAP;
   f->scheme = cfg->scheme;
   pf_status st = PF_OK;
   auto bail = [&](pf_status s) {

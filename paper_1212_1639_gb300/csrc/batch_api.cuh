@@ -214,6 +214,8 @@ pf_status validate_member(const pf_batch* b, const pf_config* c) {
   if (c->n_particles < 1 || c->n_particles > PF_MAX_PARTICLES)
     return set_err(PF_ERR_INVALID, "n_particles must be in [1, 2^26]");
   if (c->scheme != b->scheme) return set_err(PF_ERR_INVALID, "a filter's scheme differs from its batch's");
+  if (c->algorithm != PF_PARTICLE_LEARNING)
+    return set_err(PF_ERR_INVALID, "batched and served filters run particle learning");
   if (c->precision != (b->fp64 ? PF_FP64 : PF_FP32))
     return set_err(PF_ERR_INVALID, "a filter's precision differs from its batch's");
   if (!c->known_variances && !(c->a_sigma >= 1.0 && c->a_tau >= 1.0))

@@ -68,7 +68,7 @@ __device__ __forceinline__ U4 philox_rk(uint32_t c0, uint32_t c1, uint32_t c2, u
 enum Purpose : uint32_t {
   P_INIT_X = 1, P_INIT_SIGMA = 2, P_INIT_TAU = 3,
   P_STATE = 4, P_GAMMA_SIGMA = 5, P_GAMMA_TAU = 6,
-  P_SYS_OFFSET = 7, P_SPACING = 8, P_STRATIFIED = 9,
+  P_SYS_OFFSET = 7, P_SPACING = 8, P_STRATIFIED = 9, P_BOOT_STATE = 10,
 };
 
 // Draw (seed, filter, t, j, purpose, attempt): counter (j, t, filter,

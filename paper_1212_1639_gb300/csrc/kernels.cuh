@@ -317,6 +317,46 @@ __global__ void __launch_bounds__(BLOCK, sizeof(R) == 4 ? 8 : 4) k_weights(Filte
 }
 
 // ---------------------------------------------------------------------------
+// Algorithm "Particle Filtering" (the bootstrap filter, known variances),
+// Steps 1-2: propagate every particle blind, x_t = x~_{t-1} + sqrt(tau^2) Z
+// (Box-Muller's first output of the draw (seed, filter, t, i, BOOT_STATE)),
+// in place, then weigh it by p(y_t | x_t) = N(y_t; x_t, sigma^2): the
+// predictive-weight kernel's l with tau^2 = 0, and its maximum.  Step 3 is
+// the resampling of the particle-learning cycle; k_boot_gather then copies
+// the ancestors.
+// ---------------------------------------------------------------------------
+template <class R>
+__global__ void __launch_bounds__(BLOCK) k_boot_pw(FilterArgs<R> a) {
+  __shared__ R s_red[WARPS];
+  Ctl* c = a.ctl;
+  const uint32_t t = c->t;
+  const StateV<R> st = (t & 1) ? a.st[1] : a.st[0];
+  const double y = a.y_src ? *a.y_src : a.y_val;
+  const R yr = (R)y;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    c->y = y;
+    c->yf = (float)y;
+  }
+  R mx = (R)-INFINITY;
+  bool bad = false;
+  const uint64_t i = (uint64_t)blockIdx.x * BLOCK + threadIdx.x;
+  if (i < a.n) {
+    const R Z = bm_normal(draw(a.seed, a.filter, t, (uint32_t)i, P_BOOT_STATE, 0), (R)0);
+    const R sv = sqrt(st.t2[i]);
+    const R xz = sv * Z;
+    const R xp = st.x[i] + xz;
+    st.x[i] = xp;
+    const R l = log_pred<R>(xp, st.s2[i], (R)0, yr);
+    bad = !(l < (R)INFINITY);  // NaN or +inf
+    mx = l;
+    a.ell[i] = l;
+  }
+  if (bad) atomicOr(&c->err, ERR_NUMERIC);
+  mx = block_max<R>(mx, s_red);
+  if (threadIdx.x == 0 && mx > (R)-INFINITY) atomicMax(&c->maxenc, enc_max(mx));
+}
+
+// ---------------------------------------------------------------------------
 // Step 1b: the exact fixed-point CDF by a single-pass decoupled look-back scan
 // (Merrill & Garland 2016).  Tiles are claimed through an atomic ticket so a
 // tile's predecessors are always resident or finished; the look-back wait is
@@ -1957,6 +1997,35 @@ __global__ void __launch_bounds__(BLOCK, 3) k_propagate2(FilterArgs<float> a) {
   if (lane == 0) last = atomicAdd(&a.ctl->done_prop, 1u) == gridDim.x * WARPS - 1;
   last = __shfl_sync(0xffffffffu, last, 0);
   if (last) fold_cycle_warp<float>(a, t);
+}
+
+// ---------------------------------------------------------------------------
+// The bootstrap filter's Step 3 completed: the resampled particles are the
+// propagated ones at the ancestors (in place in the current buffer), copied
+// into the other buffer; the last warp folds the log-ML increment and
+// advances t, as in the propagation kernels.
+// ---------------------------------------------------------------------------
+template <class R>
+__global__ void __launch_bounds__(BLOCK) k_boot_gather(FilterArgs<R> a) {
+  const uint32_t t = a.ctl->t;
+  const StateV<R> src = (t & 1) ? a.st[1] : a.st[0];
+  const StateV<R> dst = (t & 1) ? a.st[0] : a.st[1];
+  const uint64_t n = a.n;
+  const uint64_t j = (uint64_t)blockIdx.x * BLOCK + threadIdx.x;
+  if (j < n) {
+    uint32_t an = a.anc[j];
+    an = an < n ? an : (uint32_t)(n - 1);
+    dst.x[j] = src.x[an];
+    dst.s2[j] = src.s2[an];
+    dst.t2[j] = src.t2[an];
+    dst.bs[j] = src.bs[an];
+    dst.bt[j] = src.bt[an];
+  }
+  const int lane = threadIdx.x & 31;
+  bool last = false;
+  if (lane == 0) last = atomicAdd(&a.ctl->done_prop, 1u) == gridDim.x * WARPS - 1;
+  last = __shfl_sync(0xffffffffu, last, 0);
+  if (last) fold_cycle_warp<R>(a, t);
 }
 
 // ---------------------------------------------------------------------------

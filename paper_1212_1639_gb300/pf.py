@@ -42,7 +42,9 @@ class PfConfig(C.Structure):
                 ("a_tau", C.c_double), ("b_tau", C.c_double),
                 ("sigma2", C.c_double), ("tau2", C.c_double),
                 ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN),
-                ("alloc_ctx", C.c_void_p)]
+                ("alloc_ctx", C.c_void_p), ("algorithm", C.c_int32)]
+
+ALGORITHMS = {"pl": 0, "particle_learning": 0, "bootstrap": 1}
 
 
 class PfEstimates(C.Structure):
@@ -230,7 +232,10 @@ class Filter:
 
     def __init__(self, n, seed=1212, filter_id=0, scheme="systematic", precision="fp32",
                  x0_mean=0.0, x0_var=10.0, a_sigma=3.0, b_sigma=2.0, a_tau=3.0, b_tau=2.0,
-                 known_variances=False, sigma2=1.0, tau2=0.1, stream=None, torch_alloc=True):
+                 known_variances=False, sigma2=1.0, tau2=0.1, stream=None, torch_alloc=True,
+                 algorithm="pl"):
+        """algorithm: "pl" (Algorithm "Particle Learning") or "bootstrap"
+        (Algorithm "Particle Filtering", with known_variances=True)."""
         torch = _torch()
         self.n = int(n)
         self.precision = FP64 if precision in ("fp64", FP64) else FP32
@@ -244,7 +249,8 @@ class Filter:
                        precision=self.precision, known_variances=int(bool(known_variances)),
                        x0_mean=x0_mean, x0_var=x0_var, a_sigma=a_sigma, b_sigma=b_sigma,
                        a_tau=a_tau, b_tau=b_tau, sigma2=sigma2, tau2=tau2,
-                       stream=C.c_void_p(self.stream.cuda_stream))
+                       stream=C.c_void_p(self.stream.cuda_stream),
+                       algorithm=ALGORITHMS[algorithm] if isinstance(algorithm, str) else int(algorithm))
         if self._alloc is not None:
             cfg.alloc = self._alloc.alloc
             cfg.free = self._alloc.free

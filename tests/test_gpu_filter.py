@@ -134,6 +134,31 @@ def test_outlier_observation_large(pf, orc):
     _run(pf, orc, 2_600_003, 2, 1, 0, y=np.array([0.3, -35.0]), every_step=True, seed=3)
 
 
+@pytest.mark.parametrize("scheme,prec", [(1, 0), (0, 0), (4, 0), (3, 0), (1, 1), (0, 1)])
+def test_bootstrap_filter_matches_oracle(pf, orc, scheme, prec):
+    """Algorithm "Particle Filtering" with known variances: blind propagation,
+    weights p(y | x), resampling; ancestors every step and the final state bit
+    for bit, summaries within the oracle tolerance."""
+    kw = dict(known_variances=True, sigma2=0.8, tau2=0.15, algorithm=1)
+    _run(pf, orc, 5000, 20, scheme, prec, seed=41, **kw)
+
+
+def test_bootstrap_filter_at_scale(pf, orc):
+    """The bootstrap cycle at 2^20 (one 2048-particle CDF tile per CTA) and at
+    2,600,003 particles (several tiles per CTA), systematic, FP32."""
+    kw = dict(known_variances=True, sigma2=1.0, tau2=0.1, algorithm=1)
+    _run(pf, orc, 1 << 20, 3, 1, 0, seed=42, **kw)
+    _run(pf, orc, 2_600_003, 2, 1, 0, seed=43, **kw)
+
+
+def test_bootstrap_needs_known_variances(pf):
+    with pytest.raises(pf.PfError) as e:
+        pf.Filter(1000, algorithm="bootstrap")
+    assert e.value.status == pf.PF_ERR_INVALID
+    with pytest.raises(pf.PfError):
+        pf.Filter(1000, algorithm=7, known_variances=True)
+
+
 def test_run_matches_step(pf, orc):
     _, y = synth.local_level_series(5, 40)
     a = pf.Filter(2048, seed=5, scheme="multinomial")
