@@ -60,6 +60,7 @@ BYTES_PER_PARTICLE = {
     "propagate": 4 + 28 + 28,     # read ancestor; gather 28 B record; write 28 B record
     "cdf_resample": 4 + 8 + 4,   # read l; write Q; write ancestors (l is read twice, the
                                   # second time mostly from L2)
+    "propagate_weights_next": 4 + 28 + 28 + 4,  # propagate, and write the next cycle's l
 }
 
 
@@ -212,6 +213,55 @@ def time_cycles(f, y_dev, start, K, stream, flush):
     return sum(a.elapsed_time(b) for a, b in ev)
 
 
+def time_cycles_ahead(f, y, start, K, stream, flush):
+    """K timed cycles whose propagation also computes the next cycle's
+    weights (pf_step_ahead), each cycle after the first of the run finding its
+    weights ready; L2 flushed before each, outside the events."""
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(K)]
+    f.step_ahead(float(y[start - 1]), float(y[start]))  # untimed: announces y[start]
+    for i in range(K):
+        if flush is not None:
+            flush.zero_()
+        ev[i][0].record(stream)
+        f.step_ahead(float(y[start + i]), float(y[start + i + 1]))
+        ev[i][1].record(stream)
+    f.step(float(y[start + K]))
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in ev)
+
+
+def bench_fused(pf, n, stream, y, y_dev, flush, K, W, unfused_ms):
+    """The same single-filter workload with the next cycle's weights computed
+    in each propagation (the series is known ahead)."""
+    import torch
+    f = pf.Filter(n, seed=1639, scheme="systematic", precision="fp32", stream=stream)
+    f.run(y_dev[:W])
+    f.sync()
+    ms = time_cycles_ahead(f, y, W + 1, K, stream, flush)
+    f.step_profiled(float(y[W + K + 2]))
+    acc = {}
+    for i in range(5):
+        if flush is not None:
+            flush.zero_()
+            torch.cuda.synchronize()
+        t = W + K + 3 + i
+        for k, v in f.step_profiled(float(y[t]), y_next=float(y[t + 1])).items():
+            acc.setdefault(k, []).append(v)
+    f.step(float(y[W + K + 8]))
+    f.sync()
+    f.close()
+    prof = {k: sum(v) / len(v) for k, v in acc.items()}
+    kern = {k: {"ms": round(v, 5), "gbs": round(BYTES_PER_PARTICLE[k] * n / (v / 1e3) / 1e9, 1)}
+            for k, v in prof.items()}
+    return {"value": n * K / (ms / 1e3), "unit": UNIT, "steps": K, "ms_per_step": ms / K,
+            "speedup_vs_unfused": round(unfused_ms / (ms / K), 4),
+            "l2": "flushed before every timed cycle" if flush is not None else
+                  "inputs larger than L2 (no flush)",
+            "kernels": kern}
+
+
 def kernel_profile(f, y, start, P, flush):
     """Mean per-kernel durations (ms) over P profiled cycles."""
     import torch
@@ -347,6 +397,12 @@ def bench_ours(args):
             "kernels": {k: {"ms": round(v, 5), "gbs": round(b24[k] / (v / 1e3) / 1e9, 1)}
                         for k, v in prof24.items()}}
         f24.close()
+        # the series is known ahead: every propagation also computes the next
+        # cycle's weights
+        extra["fused_next_weights"] = bench_fused(pf, n, stream, y, y_dev, flush, min(K, 100), W,
+                                                  ms / K)
+        extra["n_2p24_fused_next_weights"] = bench_fused(pf, n24, stream, y, y_dev, None, K24, 3,
+                                                         ms24 / K24)
         for other in ("multinomial", "stratified"):  # the other resampling schemes
             if other == args.scheme:
                 continue

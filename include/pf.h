@@ -145,14 +145,32 @@ pf_status pf_create(const pf_config* cfg, pf_filter** out);
 
 /* Enqueue one cycle for observation y = y_{t+1} (Steps 1-4): weights
  * w_i ~ p(y | z_t^(i)), the CDF, resampling, propagation of x, update of the
- * sufficient statistics, draw of sigma^2 and tau^2.  Asynchronous. */
+ * sufficient statistics, draw of sigma^2 and tau^2.  Asynchronous.
+ * After pf_step_ahead(f, y', y_next), y must equal y_next bit for bit
+ * (else PF_ERR_INVALID, nothing enqueued, the handle stays usable). */
 pf_status pf_step(pf_filter* f, double y);
 
+/* Enqueue one cycle for observation y, as pf_step, whose propagation (Steps
+ * 2-4) also computes the next cycle's Step 1 weights w_j ~ p(y_next | z_{t+1}^(j))
+ * and their maximum while each new particle is still in registers, so the next
+ * cycle skips the weights kernel and its re-read of the state.  Results are
+ * bit for bit those of pf_step(y) followed by pf_step(y_next).  The next
+ * pf_step / pf_step_ahead / pf_step_profiled call on this handle must pass
+ * y_next as its observation (bitwise; else PF_ERR_INVALID, nothing enqueued).
+ * The first call on a handle captures the fused cycle forms as CUDA graphs on
+ * the handle's stream (make it outside any stream capture).  Bootstrap filters
+ * (PF_BOOTSTRAP) weigh after their own blind propagation: for them this is
+ * pf_step(f, y).  Asynchronous. */
+pf_status pf_step_ahead(pf_filter* f, double y, double y_next);
+
 /* Enqueue n_steps cycles for the observations y[0..n_steps) (host or device
- * pointer, binary64).  Replays a CUDA graph of one cycle; each launch carries
- * its observation in the graph's weights-node arguments: a host value by
- * value, a device observation by address, read when the cycle runs (so a
- * device buffer must stay valid until the cycles have run, in stream order). */
+ * pointer, binary64): n_steps calls of pf_step.  Replays a CUDA graph of one
+ * cycle; each launch carries its observation in the graph's weights-node
+ * arguments: a host value by value, a device observation by address, read
+ * when the cycle runs (so a device buffer must stay valid until the cycles
+ * have run, in stream order).  With device-resident observations,
+ * PF_ERR_INVALID if a pf_step_ahead announcement is pending (it cannot be
+ * compared on the host). */
 pf_status pf_run(pf_filter* f, const double* y, uint32_t n_steps);
 
 /* Reduce the particles to posterior summaries (paper Section 2) and copy
@@ -169,6 +187,11 @@ pf_status pf_sync(pf_filter* f);
  * may be NULL) and the count to *n_kernels.  Synchronises. */
 pf_status pf_step_profiled(pf_filter* f, double y, float* kernel_ms, const char** kernel_names,
                            int max_kernels, int* n_kernels);
+
+/* Measurement: pf_step_ahead(f, y, y_next) with each kernel launched on its
+ * own between CUDA events, as pf_step_profiled.  Synchronises. */
+pf_status pf_step_ahead_profiled(pf_filter* f, double y, double y_next, float* kernel_ms,
+                                 const char** kernel_names, int max_kernels, int* n_kernels);
 
 /* Copy the current particles out (paper Section 4, "Store": optional).
  * Buffers are host or device; NULL skips an array.  FP32 filters write

@@ -55,6 +55,33 @@ pf_status map_err(uint32_t err) {
 
 }  // namespace
 
+// Forms of a captured cycle.  A cycle either runs the weights kernel or finds
+// its weights computed by the previous cycle's propagation; its propagation
+// either stops there or also computes the next cycle's weights.
+enum CycleForm : int {
+  CF_PLAIN = 0,  // weights, CDF, resampling, propagation
+  CF_HEAD = 1,   // weights, CDF, resampling, propagation + next weights
+  CF_MID = 2,    // CDF, resampling, propagation + next weights
+  CF_TAIL = 3,   // CDF, resampling, propagation
+  CF_COUNT = 4
+};
+inline bool form_weighs(int form) { return form == CF_PLAIN || form == CF_HEAD; }
+inline bool form_fuses(int form) { return form == CF_HEAD || form == CF_MID; }
+
+// One captured cycle, with the kernel nodes whose observation arguments each
+// launch sets: the weights node (this cycle's y) and the fused propagation
+// node (the next cycle's y).
+struct CycleGraph {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraphNode_t wnode = nullptr, pnode = nullptr;
+  cudaKernelNodeParams wparams = {}, pparams = {};
+  alignas(16) unsigned char wargs[sizeof(FilterArgs<double>)] = {};
+  alignas(16) unsigned char pargs[sizeof(FilterArgs<double>)] = {};
+  void* wkp[1] = {};
+  void* pkp[1] = {};
+};
+
 struct pf_filter {
   pf_config cfg;
   cudaStream_t stream = nullptr;
@@ -65,6 +92,7 @@ struct pf_filter {
   bool fp64 = false, learn = true;
   int scheme = 0;
   unsigned prop_grid = 0;  // persistent propagate grid
+  unsigned prop_grid_fuse = 0;  // the same for the propagation that also weighs
   unsigned cdf_grid = 0;   // cooperative CDF + systematic resampling grid (0: not used)
   bool cdf_staged = false; // its CTAs own several tiles: TMA-staged variant
   int cdf_per = 16;         // particles per thread of its tiles (8: 2048-particle tiles)
@@ -85,14 +113,13 @@ struct pf_filter {
   double* part_est = nullptr;
   Ctl* ctl = nullptr;
   Ctl* ctl_host = nullptr;  // pinned mirror for summaries
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  // the graph's weights node: each launch sets this cycle's observation in
-  // its arguments (no copy on the stream)
-  cudaGraphNode_t wnode = nullptr;
-  cudaKernelNodeParams wparams = {};
-  alignas(16) unsigned char wargs[sizeof(FilterArgs<double>)] = {};
-  void* wkp[1] = {};
+  // captured cycles by CycleForm (the fused forms on first use); each launch
+  // sets its observations in the kernel nodes' arguments (no copy on the stream)
+  CycleGraph cg[CF_COUNT];
+  // the previous cycle computed this cycle's weights for the observation
+  // ahead_y, announced by pf_step_ahead
+  bool ahead = false;
+  double ahead_y = 0.0;
   pf_status sticky = PF_OK;
 };
 
@@ -230,19 +257,25 @@ pf_status launch_resample(int scheme, const PosArgs& pa, uint64_t n, uint32_t* I
 }
 
 // One cycle (Steps 1-4), enqueued on f->stream; reads t and y on the device.
+// With form CF_HEAD / CF_MID the propagation also computes the next cycle's
+// weights against y_{t+2} (*ynx_src when set, else ynx_val); with CF_MID /
+// CF_TAIL the weights kernel is left out, its work done by the previous cycle.
 template <class R>
 pf_status enqueue_cycle(pf_filter* f, KTimer* tm = nullptr, const double* y_src = nullptr,
-                        double y_val = 0.0) {
+                        double y_val = 0.0, int form = CF_PLAIN, const double* ynx_src = nullptr,
+                        double ynx_val = 0.0) {
   cudaStream_t s = f->stream;
   FilterArgs<R> a = filter_args<R>(f);
   a.y_src = y_src;
   a.y_val = y_val;
+  a.y_nx_src = ynx_src;
+  a.y_nx_val = ynx_val;
   const uint64_t n = f->n;
   if (tm) cudaEventRecord(tm->ev[0], s);
   if (f->bootstrap) {  // Algorithm "Particle Filtering": propagate blind, then weigh
     k_boot_pw<R><<<(unsigned)cdiv(n, BLOCK), BLOCK, 0, s>>>(a);
     mark(tm, "propagate_weights", s);
-  } else {
+  } else if (form_weighs(form)) {
     k_weights<R><<<(unsigned)cdiv(n, (uint64_t)BLOCK * W_PER_THREAD), BLOCK, 0, s>>>(a);
     mark(tm, "weights", s);
   }
@@ -312,24 +345,47 @@ pf_status enqueue_cycle(pf_filter* f, KTimer* tm = nullptr, const double* y_src 
     pf_status st = launch_resample(f->scheme, pa, n, f->I, f->splits, s, tm);
     if (st != PF_OK) return st;
   }
+  const bool fuse = !f->bootstrap && form_fuses(form);
+  const unsigned pg = fuse ? f->prop_grid_fuse : f->prop_grid;
   if (f->bootstrap) {
     k_boot_gather<R><<<(unsigned)cdiv(n, BLOCK), BLOCK, 0, s>>>(a);
     mark(tm, "gather", s);
   } else if constexpr (sizeof(R) == 4) {  // binary32: two slots per thread, paired arithmetic
-    if (f->learn) k_propagate2<true><<<f->prop_grid, BLOCK, 0, s>>>(a);
-    else k_propagate2<false><<<f->prop_grid, BLOCK, 0, s>>>(a);
+    if (f->learn) {
+      if (fuse) k_propagate2<true, true><<<pg, BLOCK, 0, s>>>(a);
+      else k_propagate2<true><<<pg, BLOCK, 0, s>>>(a);
+    } else {
+      if (fuse) k_propagate2<false, true><<<pg, BLOCK, 0, s>>>(a);
+      else k_propagate2<false><<<pg, BLOCK, 0, s>>>(a);
+    }
   } else {
-    if (f->learn) k_propagate<R, true><<<f->prop_grid, BLOCK, 0, s>>>(a);
-    else k_propagate<R, false><<<f->prop_grid, BLOCK, 0, s>>>(a);
+    if (f->learn) {
+      if (fuse) k_propagate<R, true, true><<<pg, BLOCK, 0, s>>>(a);
+      else k_propagate<R, true><<<pg, BLOCK, 0, s>>>(a);
+    } else {
+      if (fuse) k_propagate<R, false, true><<<pg, BLOCK, 0, s>>>(a);
+      else k_propagate<R, false><<<pg, BLOCK, 0, s>>>(a);
+    }
   }
-  mark(tm, "propagate", s);
+  mark(tm, fuse ? "propagate_weights_next" : "propagate", s);
   CK(cudaGetLastError());
   return PF_OK;
 }
 
-pf_status build_graph(pf_filter* f) {
+const void* prop_fuse_fn(const pf_filter* f) {
+  if (f->fp64)
+    return f->learn ? (const void*)k_propagate<double, true, true>
+                    : (const void*)k_propagate<double, false, true>;
+  return f->learn ? (const void*)k_propagate2<true, true> : (const void*)k_propagate2<false, true>;
+}
+
+// Capture one cycle of the given form and find the nodes whose arguments
+// carry observations.
+pf_status build_graph(pf_filter* f, int form) {
+  CycleGraph& G = f->cg[form];
   CK(cudaStreamBeginCapture(f->stream, cudaStreamCaptureModeThreadLocal));
-  pf_status st = f->fp64 ? enqueue_cycle<double>(f) : enqueue_cycle<float>(f);
+  pf_status st = f->fp64 ? enqueue_cycle<double>(f, nullptr, nullptr, 0.0, form)
+                         : enqueue_cycle<float>(f, nullptr, nullptr, 0.0, form);
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamEndCapture(f->stream, &g);
   if (st != PF_OK) {
@@ -337,8 +393,8 @@ pf_status build_graph(pf_filter* f) {
     return st;
   }
   if (e != cudaSuccess) return set_err(PF_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
-  f->graph = g;
-  CK(cudaGraphInstantiate(&f->exec, g, 0));
+  G.graph = g;
+  CK(cudaGraphInstantiate(&G.exec, g, 0));
   size_t nn = 0;
   CK(cudaGraphGetNodes(g, nullptr, &nn));
   std::vector<cudaGraphNode_t> nodes(nn);
@@ -346,37 +402,69 @@ pf_status build_graph(pf_filter* f) {
   const void* wfun = f->bootstrap
       ? (f->fp64 ? (const void*)k_boot_pw<double> : (const void*)k_boot_pw<float>)
       : (f->fp64 ? (const void*)k_weights<double> : (const void*)k_weights<float>);
+  const void* pfun = prop_fuse_fn(f);
+  const size_t asz = f->fp64 ? sizeof(FilterArgs<double>) : sizeof(FilterArgs<float>);
   for (cudaGraphNode_t nd : nodes) {
     cudaGraphNodeType ty;
     CK(cudaGraphNodeGetType(nd, &ty));
     if (ty != cudaGraphNodeTypeKernel) continue;
     cudaKernelNodeParams p;
     CK(cudaGraphKernelNodeGetParams(nd, &p));
-    if (p.func != wfun) continue;
-    f->wnode = nd;
-    f->wparams = p;
-    std::memcpy(f->wargs, p.kernelParams[0], f->fp64 ? sizeof(FilterArgs<double>) : sizeof(FilterArgs<float>));
-    f->wkp[0] = f->wargs;
-    f->wparams.kernelParams = f->wkp;
-    f->wparams.extra = nullptr;
+    if (p.func == wfun) {
+      G.wnode = nd;
+      G.wparams = p;
+      std::memcpy(G.wargs, p.kernelParams[0], asz);
+      G.wkp[0] = G.wargs;
+      G.wparams.kernelParams = G.wkp;
+      G.wparams.extra = nullptr;
+    } else if (p.func == pfun) {
+      G.pnode = nd;
+      G.pparams = p;
+      std::memcpy(G.pargs, p.kernelParams[0], asz);
+      G.pkp[0] = G.pargs;
+      G.pparams.kernelParams = G.pkp;
+      G.pparams.extra = nullptr;
+    }
   }
-  if (!f->wnode) return set_err(PF_ERR_CUDA, "graph capture: weights node not found");
+  if (form_weighs(form) && !G.wnode) return set_err(PF_ERR_CUDA, "graph capture: weights node not found");
+  if (form_fuses(form) && !f->bootstrap && !G.pnode)
+    return set_err(PF_ERR_CUDA, "graph capture: fused propagation node not found");
   return PF_OK;
 }
 
-// One cycle: the graph, with this cycle's observation in the weights node.
-pf_status launch_cycle(pf_filter* f, const double* y_src, double y_val) {
-  if (f->fp64) {
-    FilterArgs<double>* a = reinterpret_cast<FilterArgs<double>*>(f->wargs);
-    a->y_src = y_src;
-    a->y_val = y_val;
+template <class R>
+void set_obs(unsigned char* args, bool next, const double* src, double val) {
+  FilterArgs<R>* a = reinterpret_cast<FilterArgs<R>*>(args);
+  if (next) {
+    a->y_nx_src = src;
+    a->y_nx_val = val;
   } else {
-    FilterArgs<float>* a = reinterpret_cast<FilterArgs<float>*>(f->wargs);
-    a->y_src = y_src;
-    a->y_val = y_val;
+    a->y_src = src;
+    a->y_val = val;
   }
-  CK(cudaGraphExecKernelNodeSetParams(f->exec, f->wnode, &f->wparams));
-  CK(cudaGraphLaunch(f->exec, f->stream));
+}
+
+// One cycle of the given form: its graph (captured on first use), with this
+// cycle's observation in the weights node and the next one in the fused
+// propagation node.
+pf_status launch_cycle(pf_filter* f, const double* y_src, double y_val, int form = CF_PLAIN,
+                       const double* ynx_src = nullptr, double ynx_val = 0.0) {
+  if (f->bootstrap) form = CF_PLAIN;  // its weights follow its own blind propagation
+  CycleGraph& G = f->cg[form];
+  if (!G.exec) {
+    pf_status st = build_graph(f, form);
+    if (st != PF_OK) return st;
+  }
+  auto setter = f->fp64 ? set_obs<double> : set_obs<float>;
+  if (G.wnode) {
+    setter(G.wargs, false, y_src, y_val);
+    CK(cudaGraphExecKernelNodeSetParams(G.exec, G.wnode, &G.wparams));
+  }
+  if (G.pnode) {
+    setter(G.pargs, true, ynx_src, ynx_val);
+    CK(cudaGraphExecKernelNodeSetParams(G.exec, G.pnode, &G.pparams));
+  }
+  CK(cudaGraphLaunch(G.exec, f->stream));
   return PF_OK;
 }
 
@@ -530,6 +618,11 @@ pf_status pf_create(const pf_config* cfg, pf_filter** out) {
     const uint64_t want = cdiv(n, f->fp64 ? (uint64_t)BLOCK : 2ull * BLOCK),
                    cap = (uint64_t)per_sm * (uint64_t)sms;
     f->prop_grid = (unsigned)(want < cap ? want : cap);
+    int per_sm_f = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_f, prop_fuse_fn(f), BLOCK, 0);
+    if (e != cudaSuccess || per_sm_f < 1) return bail(set_err(PF_ERR_CUDA, "occupancy query failed"));
+    const uint64_t cap_f = (uint64_t)per_sm_f * (uint64_t)sms;
+    f->prop_grid_fuse = (unsigned)(want < cap_f ? want : cap_f);
     if (f->scheme == PF_SYSTEMATIC) {
       // cooperative grid: every CTA resident at once (it waits on the others).
       // One tile per CTA when the tiles fit at once -- in binary32 2048-particle
@@ -564,15 +657,40 @@ pf_status pf_create(const pf_config* cfg, pf_filter** out) {
       if ((st = dev_alloc(f, (size_t)f->cdf_grid * 8, (void**)&f->cta_tot)) != PF_OK) return bail(st);
     }
   }
-  if ((st = build_graph(f)) != PF_OK) return bail(st);
+  if ((st = build_graph(f, CF_PLAIN)) != PF_OK) return bail(st);
   *out = f;
+  return PF_OK;
+}
+
+// The form of a cycle that consumes y: without weights when the previous
+// cycle computed them, which requires y to be the observation it announced.
+static pf_status form_for(pf_filter* f, double y, bool fuse_next, int* form) {
+  if (f->ahead && std::memcmp(&y, &f->ahead_y, sizeof(double)) != 0)
+    return set_err(PF_ERR_INVALID,
+                   "observation %.17g differs from %.17g, announced by pf_step_ahead", y, f->ahead_y);
+  *form = f->ahead ? (fuse_next ? CF_MID : CF_TAIL) : (fuse_next ? CF_HEAD : CF_PLAIN);
   return PF_OK;
 }
 
 pf_status pf_step(pf_filter* f, double y) {
   pf_status st = check_handle(f);
   if (st != PF_OK) return st;
-  if ((st = launch_cycle(f, nullptr, y)) != PF_OK) return f->sticky = st;
+  int form = CF_PLAIN;
+  if ((st = form_for(f, y, false, &form)) != PF_OK) return st;
+  if ((st = launch_cycle(f, nullptr, y, form)) != PF_OK) return f->sticky = st;
+  f->ahead = false;
+  return PF_OK;
+}
+
+pf_status pf_step_ahead(pf_filter* f, double y, double y_next) {
+  pf_status st = check_handle(f);
+  if (st != PF_OK) return st;
+  if (f->bootstrap) return pf_step(f, y);
+  int form = CF_PLAIN;
+  if ((st = form_for(f, y, true, &form)) != PF_OK) return st;
+  if ((st = launch_cycle(f, nullptr, y, form, nullptr, y_next)) != PF_OK) return f->sticky = st;
+  f->ahead = true;
+  f->ahead_y = y_next;
   return PF_OK;
 }
 
@@ -585,21 +703,36 @@ pf_status pf_run(pf_filter* f, const double* y, uint32_t n_steps) {
   if (n_steps && cudaPointerGetAttributes(&attr, y) == cudaSuccess)
     dev = attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
   cudaGetLastError();
-  for (uint32_t i = 0; i < n_steps; ++i) {
-    if ((st = dev ? launch_cycle(f, y + i, 0.0) : launch_cycle(f, nullptr, y[i])) != PF_OK)
-      return f->sticky = st;
+  if (!dev) {
+    for (uint32_t i = 0; i < n_steps; ++i)
+      if ((st = pf_step(f, y[i])) != PF_OK) return st;
+    return PF_OK;
   }
+  // device-resident observations cannot be compared with an announced one
+  if (f->ahead && n_steps)
+    return set_err(PF_ERR_INVALID,
+                   "pf_run with device-resident observations after pf_step_ahead: pass the "
+                   "announced observation to pf_step first");
+  for (uint32_t i = 0; i < n_steps; ++i)
+    if ((st = launch_cycle(f, y + i, 0.0)) != PF_OK) return f->sticky = st;
   return PF_OK;
 }
 
-pf_status pf_step_profiled(pf_filter* f, double y, float* kernel_ms, const char** kernel_names,
-                           int max_kernels, int* n_kernels) {
+// One cycle enqueued kernel by kernel between CUDA events.
+static pf_status step_profiled(pf_filter* f, double y, bool fuse_next, double y_next, float* kernel_ms,
+                        const char** kernel_names, int max_kernels, int* n_kernels) {
   pf_status st = check_handle(f);
   if (st != PF_OK) return st;
   if (!kernel_ms || !n_kernels || max_kernels < 1) return set_err(PF_ERR_INVALID, "NULL output");
+  if (f->bootstrap) fuse_next = false;
+  int form = CF_PLAIN;
+  if ((st = form_for(f, y, fuse_next, &form)) != PF_OK) return st;
   KTimer tm;
   for (int i = 0; i <= KTimer::MAX; ++i) CK(cudaEventCreate(&tm.ev[i]));
-  st = f->fp64 ? enqueue_cycle<double>(f, &tm, nullptr, y) : enqueue_cycle<float>(f, &tm, nullptr, y);
+  st = f->fp64 ? enqueue_cycle<double>(f, &tm, nullptr, y, form, nullptr, y_next)
+               : enqueue_cycle<float>(f, &tm, nullptr, y, form, nullptr, y_next);
+  f->ahead = fuse_next && st == PF_OK;
+  f->ahead_y = y_next;
   if (st == PF_OK) st = sync_and_check(f);
   if (st == PF_OK) {
     const int cnt = tm.count < max_kernels ? tm.count : max_kernels;
@@ -613,6 +746,16 @@ pf_status pf_step_profiled(pf_filter* f, double y, float* kernel_ms, const char*
   }
   for (int i = 0; i <= KTimer::MAX; ++i) cudaEventDestroy(tm.ev[i]);
   return st;
+}
+
+pf_status pf_step_profiled(pf_filter* f, double y, float* kernel_ms, const char** kernel_names,
+                           int max_kernels, int* n_kernels) {
+  return step_profiled(f, y, false, 0.0, kernel_ms, kernel_names, max_kernels, n_kernels);
+}
+
+pf_status pf_step_ahead_profiled(pf_filter* f, double y, double y_next, float* kernel_ms,
+                                 const char** kernel_names, int max_kernels, int* n_kernels) {
+  return step_profiled(f, y, true, y_next, kernel_ms, kernel_names, max_kernels, n_kernels);
 }
 
 pf_status pf_sync(pf_filter* f) {
@@ -675,8 +818,10 @@ pf_status pf_get_ancestors(pf_filter* f, uint32_t* anc, uint64_t* Q) {
 pf_status pf_destroy(pf_filter* f) {
   if (!f) return PF_OK;
   if (f->stream) cudaStreamSynchronize(f->stream);
-  if (f->exec) cudaGraphExecDestroy(f->exec);
-  if (f->graph) cudaGraphDestroy(f->graph);
+  for (CycleGraph& G : f->cg) {
+    if (G.exec) cudaGraphExecDestroy(G.exec);
+    if (G.graph) cudaGraphDestroy(G.graph);
+  }
   free_all(f);
   if (f->ctl_host) cudaFreeHost(f->ctl_host);
   if (f->own_stream) cudaStreamDestroy(f->stream);

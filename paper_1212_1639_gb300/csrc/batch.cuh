@@ -608,12 +608,12 @@ __device__ __forceinline__ void batch_filter(const BatchArgs<R>& a, const BatchI
         dst.bt[d] = cur.bt;
       }
     }
-    wq_push<R>(wq, qn, defer_s, GammaItem<R>{bsn, Zs, Us, (uint32_t)j, 0u}, lane);
-    wq_push<R>(wq, qn, defer_t, GammaItem<R>{btn, Zt, Ut, (uint32_t)j, 1u}, lane);
-    wq_drain<R>(wq, qn, 32u, lane, finish);
+    wq_push(wq, qn, defer_s, GammaItem<R>{bsn, Zs, Us, (uint32_t)j, 0u}, lane);
+    wq_push(wq, qn, defer_t, GammaItem<R>{btn, Zt, Ut, (uint32_t)j, 1u}, lane);
+    wq_drain(wq, qn, 32u, lane, finish);
     cur = nxt;
   }
-  wq_drain<R>(wq, qn, 1u, lane, finish);
+  wq_drain(wq, qn, 1u, lane, finish);
 
   // fold the cycle into the filter's log-ML (the single-filter fold's
   // butterfly over the 32 tile accumulators) and advance t

@@ -63,6 +63,9 @@ struct Ctl {
   // resampling key constants written by k_partition (block 0) for k_merge:
   // T = Q_{n-1}, A (n or S_n) and the systematic offset r
   uint64_t keyT, keyA, keyR;
+  // the next cycle's maximum of l, gathered by a propagation that also
+  // computes the next cycle's predictive weights (order-encoded, as maxenc)
+  unsigned long long maxenc_nx;
 };
 
 // Tile status words carry their value and flag in one aligned 64-bit word and
@@ -126,6 +129,10 @@ struct FilterArgs {
   // observations), else y_val (set per launch in the graph's weights node)
   const double* y_src;
   double y_val;
+  // the next cycle's observation y_{t+2}, for a propagation that computes
+  // the next cycle's predictive weights (*y_nx_src when set, else y_nx_val)
+  const double* y_nx_src;
+  double y_nx_val;
   uint64_t n;
   uint32_t ntiles;
   uint32_t nparts;          // log-ML partials written this cycle (one per CDF tile)
@@ -1688,7 +1695,13 @@ __device__ __forceinline__ double esum_value(const ESum64& e) { return e.s; }
 // (lane-strided, then butterfly: a fixed order), accumulate the increment
 // m + log(sum_i e_i) - log n - log(2 pi)/2, reset the per-cycle counters and
 // advance t.
-template <class R>
+//
+// With FUSE the propagation has also computed the next cycle's weights: the
+// maximum it gathered becomes the next cycle's, and the constants that the
+// weights kernel would write for the next cycle (observation y_{t+2},
+// Marsaglia-Tsang constants of the shapes a0 + (t+2)/2) are written here, once
+// every warp has read this cycle's.
+template <class R, bool FUSE = false>
 __device__ void fold_cycle_warp(const FilterArgs<R>& a, uint32_t t) {
   typedef typename ESumT<R>::T ES;
   const int lane = threadIdx.x & 31;
@@ -1703,7 +1716,23 @@ __device__ void fold_cycle_warp(const FilterArgs<R>& a, uint32_t t) {
     const double LOG_2PI = 0x1.d67f1c864beb5p+0;
     const double inc = m + log(esum_value(acc)) - log((double)a.n) - 0.5 * LOG_2PI;
     c->logml = c->logml + inc;
-    c->maxenc = sizeof(R) == 4 ? (unsigned long long)enc_f(-INFINITY) : enc_d(-INFINITY);
+    const unsigned long long ninf =
+        sizeof(R) == 4 ? (unsigned long long)enc_f(-INFINITY) : enc_d(-INFINITY);
+    if constexpr (FUSE) {
+      // every warp's maximum was published before its completion count
+      __threadfence();
+      c->maxenc = atomicExch(&c->maxenc_nx, ninf);
+      const double y = a.y_nx_src ? *a.y_nx_src : a.y_nx_val;
+      double ds, cs, dt, ct;
+      mt_constants(a.a_sigma + 0.5 * (double)(t + 2), &ds, &cs);
+      mt_constants(a.a_tau + 0.5 * (double)(t + 2), &dt, &ct);
+      c->y = y;
+      c->yf = (float)y;
+      c->mtd[0] = ds; c->mtd[1] = cs; c->mtd[2] = dt; c->mtd[3] = ct;
+      c->mtf[0] = (float)ds; c->mtf[1] = (float)cs; c->mtf[2] = (float)dt; c->mtf[3] = (float)ct;
+    } else {
+      c->maxenc = ninf;
+    }
     c->ticket_w = 0;
     c->ticket_e = 0;
     c->done_prop = 0;
@@ -1728,18 +1757,40 @@ struct GammaItem {
 // barrier is needed and the lanes of a finishing round are all busy.
 constexpr uint32_t WQ_CAP = 96;
 
-template <class R>
-__device__ __forceinline__ void wq_push(GammaItem<R>* q, uint32_t& qn, bool dfr,
-                                        const GammaItem<R>& itm, int lane) {
+template <class Item>
+__device__ __forceinline__ void wq_push(Item* q, uint32_t& qn, bool dfr, const Item& itm,
+                                        int lane) {
   const uint32_t m = __ballot_sync(0xffffffffu, dfr);
   if (dfr) q[qn + __popc(m & ((1u << lane) - 1u))] = itm;
   qn += __popc(m);
 }
 
+// Finish queued draws, 32 per round, while at least `lo` (>= 1) are queued;
+// after each round (its writes ordered by the warp barrier) `post` runs on the
+// lanes whose item has bit 1 of `which` set.
+template <class R, class Fin, class Post>
+__device__ __forceinline__ void wq_drain_post(GammaItem<R>* q, uint32_t& qn, uint32_t lo,
+                                              int lane, Fin fin, Post post) {
+  __syncwarp();
+  while (qn >= lo) {
+    const uint32_t take = qn < 32u ? qn : 32u;
+    const uint32_t base = qn - take;
+    const bool mine = (uint32_t)lane < take;
+    GammaItem<R> itm;
+    if (mine) {
+      itm = q[base + lane];
+      fin(itm);
+    }
+    __syncwarp();
+    if (mine && (itm.which & 2u)) post(itm);
+    qn = base;
+    __syncwarp();
+  }
+}
+
 // Finish queued draws, 32 per round, while at least `lo` (>= 1) are queued.
-template <class R, class Fin>
-__device__ __forceinline__ void wq_drain(GammaItem<R>* q, uint32_t& qn, uint32_t lo, int lane,
-                                         Fin fin) {
+template <class Item, class Fin>
+__device__ __forceinline__ void wq_drain(Item* q, uint32_t& qn, uint32_t lo, int lane, Fin fin) {
   __syncwarp();
   while (qn >= lo) {
     const uint32_t take = qn < 32u ? qn : 32u;
@@ -1747,6 +1798,49 @@ __device__ __forceinline__ void wq_drain(GammaItem<R>* q, uint32_t& qn, uint32_t
     if ((uint32_t)lane < take) fin(q[base + lane]);
     qn = base;
     __syncwarp();
+  }
+}
+
+// The next cycle's weight of one slot: l = log p(y_{t+2} | x, sigma^2, tau^2),
+// the weights kernel's arithmetic; its maximum and finiteness are tracked.
+template <class R>
+__device__ __forceinline__ void weigh_next(R* ell, uint64_t j, R x, R s2, R t2, R yn, R& mx,
+                                           bool& bad) {
+  const R l = log_pred<R>(x, s2, t2, yn);
+  ell[j] = l;
+  bad |= !(l < (R)INFINITY);
+  mx = fmax(mx, l);
+}
+
+// log_pred on two slots with paired operations; per lane the same IEEE
+// operations in the same order, so the same bits.
+__device__ __forceinline__ float2 log_pred2(float2 x, float2 s2, float2 t2, float yn) {
+  const float2 s = add2(s2, t2);
+  const float2 dx = sub2(splat2(yn), x);
+  const float2 q = mul2(dx, dx);
+  const float2 lg = det_log2(s);
+  const float2 r = make_float2(q.x / s.x, q.y / s.y);
+  const float2 sum = add2(lg, r);
+  return mul2(splat2(-0.5f), sum);
+}
+
+// Store a next-cycle weight computed elsewhere and track it.
+template <class R>
+__device__ __forceinline__ void keep_next(R* ell, uint64_t j, R l, R& mx, bool& bad) {
+  ell[j] = l;
+  bad |= !(l < (R)INFINITY);
+  mx = fmax(mx, l);
+}
+
+// Publish a warp's maximum of the next cycle's weights (lane 0 only), before
+// the warp's completion count.
+template <class R>
+__device__ __forceinline__ void publish_next_max(Ctl* c, R mx, int lane) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0) {
+    if (mx > (R)-INFINITY) atomicMax(&c->maxenc_nx, enc_max(mx));
+    __threadfence();
   }
 }
 
@@ -1771,9 +1865,18 @@ __device__ __forceinline__ Gathered<R> gather_rec(const StateV<R>& src, uint32_t
 // k * stride.  The ancestor index is loaded two slots ahead and the ancestor's
 // record one slot ahead, so the dependent index -> gather latency overlaps the
 // arithmetic of the current slot.
-template <class R, bool LEARN>
+//
+// With FUSE the kernel also computes the next cycle's predictive weights
+// l_j = log p(y_{t+2} | x'_j, sigma^2'_j, tau^2'_j) and their maximum, which
+// the next cycle then uses instead of running the weights kernel.  A slot
+// whose gamma draw missed the squeeze is weighed by the drain round that
+// finishes its last queued draw (bit 1 of `which` on that item), reading its
+// new state back after the round's warp barrier.  Every value is the one the
+// weights kernel would give.
+template <class R, bool LEARN, bool FUSE = false>
 __global__ void __launch_bounds__(BLOCK, 5) k_propagate(FilterArgs<R> a) {
-  __shared__ GammaItem<R> s_q[WARPS][WQ_CAP];
+  typedef GammaItem<R> Item;
+  __shared__ Item s_q[WARPS][WQ_CAP];
   const Ctl* c = a.ctl;
   const uint32_t t = c->t;
   const StateV<R> src = (t & 1) ? a.st[1] : a.st[0];
@@ -1786,20 +1889,28 @@ __global__ void __launch_bounds__(BLOCK, 5) k_propagate(FilterArgs<R> a) {
     yr = y; ds = c->mtd[0]; cs = c->mtd[1]; dt = c->mtd[2]; ct = c->mtd[3];
   }
   const int lane = threadIdx.x & 31;
-  GammaItem<R>* const wq = s_q[threadIdx.x >> 5];
+  Item* const wq = s_q[threadIdx.x >> 5];
   uint32_t qn = 0;  // warp-uniform
   const uint64_t n = a.n;
   const uint64_t stride = (uint64_t)gridDim.x * BLOCK;
   const uint64_t iters = (n + stride - 1) / stride;
   auto clampi = [&](uint32_t v) { return v < n ? v : (uint32_t)(n - 1); };
   bool fail = false;
-  auto finish = [&](const GammaItem<R>& itm) {
-    const bool sig = itm.which == 0;
+  // next cycle's weights (FUSE)
+  R yn = 0;
+  if constexpr (FUSE) yn = (R)(a.y_nx_src ? *a.y_nx_src : a.y_nx_val);
+  R mxn = (R)-INFINITY;
+  bool badn = false;
+  auto finish = [&](const Item& itm) {
+    const bool sig = (itm.which & 1u) == 0;
     const R G = gamma_mt_from<R>(sig ? ds : dt, sig ? cs : ct, itm.Z, itm.U, a.seed, a.filter, t,
                                  itm.j, sig ? P_GAMMA_SIGMA : P_GAMMA_TAU, &fail);
     const R v = SuffOps<R>::ig(itm.b, G);
     if (sig) dst.s2[itm.j] = v;
     else dst.t2[itm.j] = v;
+  };
+  auto weigh_late = [&](const Item& itm) {  // FUSE: the slot's state is final
+    weigh_next<R>(a.ell, itm.j, dst.x[itm.j], dst.s2[itm.j], dst.t2[itm.j], yn, mxn, badn);
   };
   uint64_t j = (uint64_t)blockIdx.x * BLOCK + threadIdx.x;
   uint32_t an = j < n ? clampi(a.anc[j]) : 0;
@@ -1812,6 +1923,7 @@ __global__ void __launch_bounds__(BLOCK, 5) k_propagate(FilterArgs<R> a) {
     bool defer_s = false, defer_t = false;
     typename SuffT<R>::B bsn = 0, btn = 0;
     R Zs = 0, Us = 0, Zt = 0, Ut = 0;
+    R xj = 0, s2n = 0, t2n = 0;
     if (j < n) {
       const R xa = cur.x, sa = cur.s2, ta = cur.t2;
       const R s = sa + ta;
@@ -1825,7 +1937,7 @@ __global__ void __launch_bounds__(BLOCK, 5) k_propagate(FilterArgs<R> a) {
       R Z;
       theta_draws_rk<R>(a.rk, a.filter, t, (uint32_t)j, &Z, &Zs, &Us, &Zt, &Ut);
       const R xz = sv * Z;
-      const R xj = mu + xz;
+      xj = mu + xz;
       dst.x[j] = xj;
       if (LEARN) {
         const R rs = ResidObs<R>::f(y, yr, xj);
@@ -1835,37 +1947,48 @@ __global__ void __launch_bounds__(BLOCK, 5) k_propagate(FilterArgs<R> a) {
         dst.bs[j] = bsn;
         dst.bt[j] = btn;
         R Gs, Gt;
-        if (gamma_mt_squeeze<R>(ds, cs, Zs, Us, &Gs)) dst.s2[j] = SuffOps<R>::ig(bsn, Gs);
+        if (gamma_mt_squeeze<R>(ds, cs, Zs, Us, &Gs)) dst.s2[j] = s2n = SuffOps<R>::ig(bsn, Gs);
         else defer_s = true;
-        if (gamma_mt_squeeze<R>(dt, ct, Zt, Ut, &Gt)) dst.t2[j] = SuffOps<R>::ig(btn, Gt);
+        if (gamma_mt_squeeze<R>(dt, ct, Zt, Ut, &Gt)) dst.t2[j] = t2n = SuffOps<R>::ig(btn, Gt);
         else defer_t = true;
       } else {
-        dst.s2[j] = sa;
-        dst.t2[j] = ta;
+        dst.s2[j] = s2n = sa;
+        dst.t2[j] = t2n = ta;
         dst.bs[j] = cur.bs;
         dst.bt[j] = cur.bt;
       }
+      if (FUSE && !defer_s && !defer_t) weigh_next<R>(a.ell, j, xj, s2n, t2n, yn, mxn, badn);
     }
-    if (LEARN) {
+    if constexpr (LEARN && FUSE) {
+      // the sigma^2 item sits below the tau^2 item of its slot, so it is
+      // finished in the same round or a later one: it weighs the slot when
+      // both were deferred
+      wq_push(wq, qn, defer_s, Item{bsn, Zs, Us, (uint32_t)j, 2u}, lane);
+      wq_push(wq, qn, defer_t, Item{btn, Zt, Ut, (uint32_t)j, defer_s ? 1u : 3u}, lane);
+      wq_drain_post(wq, qn, 32u, lane, finish, weigh_late);
+    } else if constexpr (LEARN) {
       // queue the draws that missed the squeeze; the warp finishes them 32
       // at a time
-      wq_push<R>(wq, qn, defer_s, GammaItem<R>{bsn, Zs, Us, (uint32_t)j, 0u}, lane);
-      wq_push<R>(wq, qn, defer_t, GammaItem<R>{btn, Zt, Ut, (uint32_t)j, 1u}, lane);
-      wq_drain<R>(wq, qn, 32u, lane, finish);
+      wq_push(wq, qn, defer_s, Item{bsn, Zs, Us, (uint32_t)j, 0u}, lane);
+      wq_push(wq, qn, defer_t, Item{btn, Zt, Ut, (uint32_t)j, 1u}, lane);
+      wq_drain(wq, qn, 32u, lane, finish);
     }
     cur = nxt;
     an_next = an_next2;
   }
-  if (LEARN) wq_drain<R>(wq, qn, 1u, lane, finish);
+  if constexpr (LEARN && FUSE) wq_drain_post(wq, qn, 1u, lane, finish, weigh_late);
+  else if (LEARN) wq_drain(wq, qn, 1u, lane, finish);
   (void)an;
-  if (__any_sync(0xffffffffu, fail) && lane == 0) atomicOr(&a.ctl->err, ERR_NUMERIC);
-  // The fold reads only what earlier kernels wrote (tile partials, the
-  // control block), so the completion count needs no fence; every warp has
-  // read t before its increment.
+  if (__any_sync(0xffffffffu, fail || badn) && lane == 0) atomicOr(&a.ctl->err, ERR_NUMERIC);
+  // Without FUSE the fold reads only what earlier kernels wrote (tile
+  // partials, the control block), so the completion count needs no fence;
+  // every warp has read t before its increment.  With FUSE each warp's
+  // maximum is fenced before its count.
+  if constexpr (FUSE) publish_next_max<R>(a.ctl, mxn, lane);
   bool last = false;
   if (lane == 0) last = atomicAdd(&a.ctl->done_prop, 1u) == gridDim.x * WARPS - 1;
   last = __shfl_sync(0xffffffffu, last, 0);
-  if (last) fold_cycle_warp<R>(a, t);
+  if (last) fold_cycle_warp<R, FUSE>(a, t);
 }
 
 // ---------------------------------------------------------------------------
@@ -1877,16 +2000,19 @@ __global__ void __launch_bounds__(BLOCK, 5) k_propagate(FilterArgs<R> a) {
 // ---------------------------------------------------------------------------
 constexpr uint32_t WQ2_CAP = 160;  // 31 queued + 4 pushes of 32 per pass
 
-template <bool LEARN>
+// With FUSE, the next cycle's weights as in k_propagate, the two slots of a
+// pass weighed by paired operations.
+template <bool LEARN, bool FUSE = false>
 __global__ void __launch_bounds__(BLOCK, 3) k_propagate2(FilterArgs<float> a) {
-  __shared__ GammaItem<float> s_q[WARPS][WQ2_CAP];
+  typedef GammaItem<float> Item;
+  __shared__ Item s_q[WARPS][WQ2_CAP];
   const Ctl* c = a.ctl;
   const uint32_t t = c->t;
   const StateV<float> src = (t & 1) ? a.st[1] : a.st[0];
   const StateV<float> dst = (t & 1) ? a.st[0] : a.st[1];
   const float yr = c->yf, ds = c->mtf[0], cs = c->mtf[1], dt = c->mtf[2], ct = c->mtf[3];
   const int lane = threadIdx.x & 31;
-  GammaItem<float>* const wq = s_q[threadIdx.x >> 5];
+  Item* const wq = s_q[threadIdx.x >> 5];
   uint32_t qn = 0;  // warp-uniform
   const uint64_t n = a.n;
   const uint64_t half = (uint64_t)gridDim.x * BLOCK;
@@ -1894,14 +2020,22 @@ __global__ void __launch_bounds__(BLOCK, 3) k_propagate2(FilterArgs<float> a) {
   const uint64_t iters = (n + stride - 1) / stride;
   auto clampi = [&](uint32_t v) { return v < n ? v : (uint32_t)(n - 1); };
   bool fail = false;
-  auto finish = [&](const GammaItem<float>& itm) {
-    const bool sig = itm.which == 0;
+  // next cycle's weights (FUSE)
+  float yn = 0.0f;
+  if constexpr (FUSE) yn = (float)(a.y_nx_src ? *a.y_nx_src : a.y_nx_val);
+  float mxn = -INFINITY;
+  bool badn = false;
+  auto finish = [&](const Item& itm) {
+    const bool sig = (itm.which & 1u) == 0;
     const float G = gamma_mt_from<float>(sig ? ds : dt, sig ? cs : ct, itm.Z, itm.U, a.seed,
                                          a.filter, t, itm.j, sig ? P_GAMMA_SIGMA : P_GAMMA_TAU,
                                          &fail);
     const float v = SuffOps<float>::ig(itm.b, G);
     if (sig) dst.s2[itm.j] = v;
     else dst.t2[itm.j] = v;
+  };
+  auto weigh_late = [&](const Item& itm) {  // FUSE: the slot's state is final
+    weigh_next<float>(a.ell, itm.j, dst.x[itm.j], dst.s2[itm.j], dst.t2[itm.j], yn, mxn, badn);
   };
   uint64_t j0 = (uint64_t)blockIdx.x * BLOCK + threadIdx.x;
   Gathered<float> c0 = gather_rec<float>(src, j0 < n ? clampi(a.anc[j0]) : 0u);
@@ -1967,36 +2101,60 @@ __global__ void __launch_bounds__(BLOCK, 3) k_propagate2(FilterArgs<float> a) {
       // inverse gamma: (b 2^-32) / G, per SuffOps<float>::ig
       const float2 bsf = mul2(make_float2(u64_to_f32_rn(bs0), u64_to_f32_rn(bs1)), splat2(0x1p-32f));
       const float2 btf = mul2(make_float2(u64_to_f32_rn(bt0), u64_to_f32_rn(bt1)), splat2(0x1p-32f));
+      // 1 for a deferred draw: the paired weight of that slot is discarded,
+      // and a normal operand keeps the log and the division on their fast paths
+      float s20 = 1.0f, t20 = 1.0f, s21 = 1.0f, t21 = 1.0f;
       if (v0) {
-        if (as0) dst.s2[j0] = bsf.x / Gs.x;
+        if (as0) dst.s2[j0] = s20 = bsf.x / Gs.x;
         else ds0 = true;
-        if (at0) dst.t2[j0] = btf.x / Gt.x;
+        if (at0) dst.t2[j0] = t20 = btf.x / Gt.x;
         else dt0 = true;
       }
       if (v1) {
-        if (as1) dst.s2[j1] = bsf.y / Gs.y;
+        if (as1) dst.s2[j1] = s21 = bsf.y / Gs.y;
         else ds1 = true;
-        if (at1) dst.t2[j1] = btf.y / Gt.y;
+        if (at1) dst.t2[j1] = t21 = btf.y / Gt.y;
         else dt1 = true;
       }
-      wq_push<float>(wq, qn, ds0, GammaItem<float>{bs0, Zs.x, Us.x, (uint32_t)j0, 0u}, lane);
-      wq_push<float>(wq, qn, dt0, GammaItem<float>{bt0, Zt.x, Ut.x, (uint32_t)j0, 1u}, lane);
-      wq_push<float>(wq, qn, ds1, GammaItem<float>{bs1, Zs.y, Us.y, (uint32_t)j1, 0u}, lane);
-      wq_push<float>(wq, qn, dt1, GammaItem<float>{bt1, Zt.y, Ut.y, (uint32_t)j1, 1u}, lane);
-      wq_drain<float>(wq, qn, 32u, lane, finish);
+      if constexpr (FUSE) {
+        // both slots weighed paired; a slot with a deferred draw is weighed
+        // by the drain round that finishes it (its sigma^2 item lies below
+        // its tau^2 item, so it weighs when both were deferred)
+        const float2 l = log_pred2(xj, make_float2(s20, s21), make_float2(t20, t21), yn);
+        if (v0 && !ds0 && !dt0) keep_next(a.ell, j0, l.x, mxn, badn);
+        if (v1 && !ds1 && !dt1) keep_next(a.ell, j1, l.y, mxn, badn);
+        wq_push(wq, qn, ds0, Item{bs0, Zs.x, Us.x, (uint32_t)j0, 2u}, lane);
+        wq_push(wq, qn, dt0, Item{bt0, Zt.x, Ut.x, (uint32_t)j0, ds0 ? 1u : 3u}, lane);
+        wq_push(wq, qn, ds1, Item{bs1, Zs.y, Us.y, (uint32_t)j1, 2u}, lane);
+        wq_push(wq, qn, dt1, Item{bt1, Zt.y, Ut.y, (uint32_t)j1, ds1 ? 1u : 3u}, lane);
+        wq_drain_post(wq, qn, 32u, lane, finish, weigh_late);
+      } else {
+        wq_push(wq, qn, ds0, Item{bs0, Zs.x, Us.x, (uint32_t)j0, 0u}, lane);
+        wq_push(wq, qn, dt0, Item{bt0, Zt.x, Ut.x, (uint32_t)j0, 1u}, lane);
+        wq_push(wq, qn, ds1, Item{bs1, Zs.y, Us.y, (uint32_t)j1, 0u}, lane);
+        wq_push(wq, qn, dt1, Item{bt1, Zt.y, Ut.y, (uint32_t)j1, 1u}, lane);
+        wq_drain(wq, qn, 32u, lane, finish);
+      }
     } else {
       if (v0) { dst.s2[j0] = sa.x; dst.t2[j0] = ta.x; dst.bs[j0] = c0.bs; dst.bt[j0] = c0.bt; }
       if (v1) { dst.s2[j1] = sa.y; dst.t2[j1] = ta.y; dst.bs[j1] = c1.bs; dst.bt[j1] = c1.bt; }
+      if constexpr (FUSE) {
+        const float2 l = log_pred2(xj, sa, ta, yn);
+        if (v0) keep_next(a.ell, j0, l.x, mxn, badn);
+        if (v1) keep_next(a.ell, j1, l.y, mxn, badn);
+      }
     }
     c0 = n0;
     c1 = n1;
   }
-  if (LEARN) wq_drain<float>(wq, qn, 1u, lane, finish);
-  if (__any_sync(0xffffffffu, fail) && lane == 0) atomicOr(&a.ctl->err, ERR_NUMERIC);
+  if constexpr (LEARN && FUSE) wq_drain_post(wq, qn, 1u, lane, finish, weigh_late);
+  else if (LEARN) wq_drain(wq, qn, 1u, lane, finish);
+  if (__any_sync(0xffffffffu, fail || badn) && lane == 0) atomicOr(&a.ctl->err, ERR_NUMERIC);
+  if constexpr (FUSE) publish_next_max<float>(a.ctl, mxn, lane);
   bool last = false;
   if (lane == 0) last = atomicAdd(&a.ctl->done_prop, 1u) == gridDim.x * WARPS - 1;
   last = __shfl_sync(0xffffffffu, last, 0);
-  if (last) fold_cycle_warp<float>(a, t);
+  if (last) fold_cycle_warp<float, FUSE>(a, t);
 }
 
 // ---------------------------------------------------------------------------

@@ -117,11 +117,14 @@ _V = C.c_void_p
 _SIGS = {
     "pf_create": [C.POINTER(PfConfig), C.POINTER(_V)],
     "pf_step": [_V, C.c_double],
+    "pf_step_ahead": [_V, C.c_double, C.c_double],
     "pf_run": [_V, _V, C.c_uint32],
     "pf_estimate": [_V, C.POINTER(PfEstimates)],
     "pf_sync": [_V],
     "pf_step_profiled": [_V, C.c_double, C.POINTER(C.c_float), C.POINTER(C.c_char_p), C.c_int,
                          C.POINTER(C.c_int)],
+    "pf_step_ahead_profiled": [_V, C.c_double, C.c_double, C.POINTER(C.c_float),
+                               C.POINTER(C.c_char_p), C.c_int, C.POINTER(C.c_int)],
     "pf_get_particles": [_V, _V, _V, _V, _V, _V],
     "pf_get_ancestors": [_V, _V, _V],
     "pf_destroy": [_V],
@@ -262,6 +265,11 @@ class Filter:
     def step(self, y):
         _check(_lib.pf_step(self.h, float(y)), "pf_step")
 
+    def step_ahead(self, y, y_next):
+        """One cycle for y whose propagation also weighs the particles against
+        y_next, the next call's observation (pf_step_ahead)."""
+        _check(_lib.pf_step_ahead(self.h, float(y), float(y_next)), "pf_step_ahead")
+
     def run(self, y):
         """y: a float64 CUDA tensor (device-resident observations) or array-like."""
         torch = _torch()
@@ -278,13 +286,18 @@ class Filter:
     def sync(self):
         _check(_lib.pf_sync(self.h), "pf_sync")
 
-    def step_profiled(self, y):
-        """One cycle with per-kernel CUDA-event timing: {kernel name: ms}."""
+    def step_profiled(self, y, y_next=None):
+        """One cycle with per-kernel CUDA-event timing: {kernel name: ms}.
+        With y_next, the cycle of step_ahead(y, y_next)."""
         ms = (C.c_float * 8)()
         names = (C.c_char_p * 8)()
         cnt = C.c_int()
-        _check(_lib.pf_step_profiled(self.h, float(y), ms, names, 8, C.byref(cnt)),
-               "pf_step_profiled")
+        if y_next is None:
+            _check(_lib.pf_step_profiled(self.h, float(y), ms, names, 8, C.byref(cnt)),
+                   "pf_step_profiled")
+        else:
+            _check(_lib.pf_step_ahead_profiled(self.h, float(y), float(y_next), ms, names, 8,
+                                               C.byref(cnt)), "pf_step_ahead_profiled")
         return {names[i].decode(): float(ms[i]) for i in range(cnt.value)}
 
     def estimate(self):
