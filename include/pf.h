@@ -208,6 +208,34 @@ pf_status pf_get_ancestors(pf_filter* f, uint32_t* anc, uint64_t* Q);
  * NULL-safe. */
 pf_status pf_destroy(pf_filter* f);
 
+/* Checkpoint and resume.  The paper runs each series in one go; a long-lived
+ * filter (a service restarting, a job moving to another GPU) needs its state
+ * saved and continued.  A checkpoint holds the filter's configuration (model,
+ * priors, seed, filter id, scheme, precision, algorithm), the number of
+ * cycles t, the accumulated log marginal likelihood and every particle's x,
+ * sigma^2, tau^2, b_sigma, b_tau.  Resuming draws the same Philox counters
+ * (seed, filter, t, particle, purpose), so the restored filter continues bit
+ * for bit as the original would have.  The blob is self-describing (magic,
+ * format version, sizes) and valid for this library version.
+ *
+ * pf_checkpoint_size: *bytes receives the blob size for this handle. */
+pf_status pf_checkpoint_size(pf_filter* f, size_t* bytes);
+
+/* Write the checkpoint to buf (host or device memory, at least
+ * pf_checkpoint_size bytes; the caller owns it).  Synchronises the handle's
+ * stream first.  PF_ERR_INVALID if bytes is too small or if a pf_step_ahead
+ * announcement is pending (its precomputed weights are not saved: pass the
+ * announced observation to pf_step first); sticky errors as usual. */
+pf_status pf_checkpoint(pf_filter* f, void* buf, size_t bytes);
+
+/* Create a filter from a checkpoint (host or device memory, `bytes` long).
+ * The model, sizes, seed and scheme come from the checkpoint; cfg (may be
+ * NULL) supplies only stream, alloc, free and alloc_ctx, with the meaning
+ * they have in pf_create.  Synchronises the new handle's stream before
+ * returning.  PF_ERR_INVALID for a blob that is truncated, of another format
+ * version or not a checkpoint; PF_ERR_OOM / PF_ERR_CUDA as pf_create. */
+pf_status pf_restore(const pf_config* cfg, const void* buf, size_t bytes, pf_filter** out);
+
 /* Thread-local description of the last failure on this thread. */
 const char* pf_last_error(void);
 

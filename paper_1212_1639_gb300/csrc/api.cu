@@ -831,6 +831,167 @@ pf_status pf_destroy(pf_filter* f) {
 }
 
 // ---------------------------------------------------------------------------
+// Checkpoint and resume: a header, then the current parity's x, sigma^2,
+// tau^2 (R each), b_sigma, b_tau (8 bytes each), n of each.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr uint64_t CKPT_MAGIC = 0x54504b434c4c4650ull;  // "PFLLCKPT"
+constexpr uint32_t CKPT_VERSION = 1;
+
+struct CkptHeader {
+  uint64_t magic;
+  uint32_t version;
+  uint32_t header_bytes;
+  uint64_t n;
+  uint64_t seed;
+  uint32_t filter_id;
+  int32_t scheme, precision, known_variances, algorithm, pad;
+  double x0_mean, x0_var, a_sigma, b_sigma, a_tau, b_tau, sigma2, tau2;
+  uint64_t t;
+  double logml;
+  uint64_t total_bytes;
+};
+
+size_t ckpt_bytes(uint64_t n, bool fp64) {
+  return sizeof(CkptHeader) + (size_t)n * (3 * (fp64 ? 8 : 4) + 16);
+}
+
+}  // namespace
+
+extern "C" {
+
+pf_status pf_checkpoint_size(pf_filter* f, size_t* bytes) {
+  if (!f || !bytes) return set_err(PF_ERR_INVALID, "NULL argument");
+  *bytes = ckpt_bytes(f->n, f->fp64);
+  return PF_OK;
+}
+
+pf_status pf_checkpoint(pf_filter* f, void* buf, size_t bytes) {
+  pf_status st = check_handle(f);
+  if (st != PF_OK) return st;
+  if (!buf) return set_err(PF_ERR_INVALID, "NULL buffer");
+  const size_t need = ckpt_bytes(f->n, f->fp64);
+  if (bytes < need) return set_err(PF_ERR_INVALID, "checkpoint needs %zu bytes, got %zu", need, bytes);
+  if (f->ahead)
+    return set_err(PF_ERR_INVALID, "a pf_step_ahead announcement is pending: pf_step(%.17g) first",
+                   f->ahead_y);
+  if ((st = sync_and_check(f)) != PF_OK) return st;
+  CkptHeader h;
+  std::memset(&h, 0, sizeof(h));
+  h.magic = CKPT_MAGIC;
+  h.version = CKPT_VERSION;
+  h.header_bytes = sizeof(CkptHeader);
+  h.n = f->n;
+  h.seed = f->cfg.seed;
+  h.filter_id = f->cfg.filter_id;
+  h.scheme = f->cfg.scheme;
+  h.precision = f->cfg.precision;
+  h.known_variances = f->cfg.known_variances;
+  h.algorithm = f->cfg.algorithm;
+  h.x0_mean = f->cfg.x0_mean;
+  h.x0_var = f->cfg.x0_var;
+  h.a_sigma = f->cfg.a_sigma;
+  h.b_sigma = f->cfg.b_sigma;
+  h.a_tau = f->cfg.a_tau;
+  h.b_tau = f->cfg.b_tau;
+  h.sigma2 = f->cfg.sigma2;
+  h.tau2 = f->cfg.tau2;
+  h.t = f->ctl_host->t;
+  h.logml = f->ctl_host->logml;
+  h.total_bytes = need;
+  char* out = static_cast<char*>(buf);
+  CK(cudaMemcpy(out, &h, sizeof(h), cudaMemcpyDefault));
+  const int p = (int)(h.t & 1);
+  const size_t rs = f->fp64 ? 8 : 4;
+  const void* src[5] = {f->x[p], f->s2[p], f->t2[p], f->bs[p], f->bt[p]};
+  const size_t sz[5] = {rs, rs, rs, 8, 8};
+  size_t off = sizeof(h);
+  for (int i = 0; i < 5; ++i) {
+    CK(cudaMemcpyAsync(out + off, src[i], f->n * sz[i], cudaMemcpyDefault, f->stream));
+    off += f->n * sz[i];
+  }
+  CK(cudaStreamSynchronize(f->stream));
+  return PF_OK;
+}
+
+pf_status pf_restore(const pf_config* cfg, const void* buf, size_t bytes, pf_filter** out) {
+  if (!buf || !out) return set_err(PF_ERR_INVALID, "NULL argument");
+  *out = nullptr;
+  if (bytes < sizeof(CkptHeader)) return set_err(PF_ERR_INVALID, "checkpoint truncated (%zu bytes)", bytes);
+  CkptHeader h;
+  CK(cudaMemcpy(&h, buf, sizeof(h), cudaMemcpyDefault));
+  if (h.magic != CKPT_MAGIC) return set_err(PF_ERR_INVALID, "not a filter checkpoint");
+  if (h.version != CKPT_VERSION || h.header_bytes != sizeof(CkptHeader))
+    return set_err(PF_ERR_INVALID, "checkpoint format version %u, this library reads %u", h.version,
+                   CKPT_VERSION);
+  if (h.precision != PF_FP32 && h.precision != PF_FP64) return set_err(PF_ERR_INVALID, "bad precision");
+  if (h.n < 1 || h.n > PF_MAX_PARTICLES) return set_err(PF_ERR_INVALID, "bad particle count");
+  const bool fp64 = h.precision == PF_FP64;
+  const size_t need = ckpt_bytes(h.n, fp64);
+  if (h.total_bytes != need || bytes < need)
+    return set_err(PF_ERR_INVALID, "checkpoint truncated or inconsistent (%zu of %zu bytes)", bytes, need);
+  if (h.t >= 0xffffffffull) return set_err(PF_ERR_INVALID, "bad cycle count");
+  pf_config c;
+  std::memset(&c, 0, sizeof(c));
+  c.n_particles = h.n;
+  c.seed = h.seed;
+  c.filter_id = h.filter_id;
+  c.scheme = h.scheme;
+  c.precision = h.precision;
+  c.known_variances = h.known_variances;
+  c.algorithm = h.algorithm;
+  c.x0_mean = h.x0_mean;
+  c.x0_var = h.x0_var;
+  c.a_sigma = h.a_sigma;
+  c.b_sigma = h.b_sigma;
+  c.a_tau = h.a_tau;
+  c.b_tau = h.b_tau;
+  c.sigma2 = h.sigma2;
+  c.tau2 = h.tau2;
+  if (cfg) {
+    c.stream = cfg->stream;
+    c.alloc = cfg->alloc;
+    c.free = cfg->free;
+    c.alloc_ctx = cfg->alloc_ctx;
+  }
+  pf_filter* f = nullptr;
+  pf_status st = pf_create(&c, &f);
+  if (st != PF_OK) return st;
+  auto bail = [&](pf_status s) {
+    pf_destroy(f);
+    return s;
+  };
+  const int p = (int)(h.t & 1);
+  const size_t rs = fp64 ? 8 : 4;
+  void* dst[5] = {f->x[p], f->s2[p], f->t2[p], f->bs[p], f->bt[p]};
+  const size_t sz[5] = {rs, rs, rs, 8, 8};
+  const char* in = static_cast<const char*>(buf);
+  size_t off = sizeof(h);
+  for (int i = 0; i < 5; ++i) {
+    if (cudaMemcpyAsync(dst[i], in + off, h.n * sz[i], cudaMemcpyDefault, f->stream) != cudaSuccess)
+      return bail(set_err(PF_ERR_CUDA, "checkpoint upload: %s", cudaGetErrorString(cudaGetLastError())));
+    off += h.n * sz[i];
+  }
+  // the cycle count and the log marginal likelihood; the rest of the
+  // control block is as pf_create left it (no error, max -inf, counters 0)
+  if (cudaStreamSynchronize(f->stream) != cudaSuccess)
+    return bail(set_err(PF_ERR_CUDA, "stream: %s", cudaGetErrorString(cudaGetLastError())));
+  f->ctl_host->t = (uint32_t)h.t;
+  f->ctl_host->logml = h.logml;
+  if (cudaMemcpyAsync(&f->ctl->t, &f->ctl_host->t, sizeof(uint32_t), cudaMemcpyHostToDevice,
+                      f->stream) != cudaSuccess ||
+      cudaMemcpyAsync(&f->ctl->logml, &f->ctl_host->logml, sizeof(double), cudaMemcpyHostToDevice,
+                      f->stream) != cudaSuccess ||
+      cudaStreamSynchronize(f->stream) != cudaSuccess)
+    return bail(set_err(PF_ERR_CUDA, "checkpoint upload: %s", cudaGetErrorString(cudaGetLastError())));
+  *out = f;
+  return PF_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
 // Standalone resampling and the paper's cut-point primitives.
 // ---------------------------------------------------------------------------
 namespace {

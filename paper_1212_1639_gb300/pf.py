@@ -6,6 +6,7 @@ allocator callbacks) and streams.  Importing this module loads libpf.so and
 raises if it has not been built; there is no fallback path.
 """
 import ctypes as C
+import struct
 import os
 
 import numpy as np
@@ -128,6 +129,9 @@ _SIGS = {
     "pf_get_particles": [_V, _V, _V, _V, _V, _V],
     "pf_get_ancestors": [_V, _V, _V],
     "pf_destroy": [_V],
+    "pf_checkpoint_size": [_V, C.POINTER(C.c_size_t)],
+    "pf_checkpoint": [_V, _V, C.c_size_t],
+    "pf_restore": [C.POINTER(PfConfig), _V, C.c_size_t, C.POINTER(_V)],
     "pf_resample": [_V, C.c_uint64, C.c_uint64, C.c_uint32, C.c_uint32, C.c_int32, _V, _V],
     "pf_resample_noalloc": [_V, C.c_uint64, C.c_uint64, C.c_uint32, C.c_uint32, C.c_int32, _V,
                             _V],
@@ -230,6 +234,18 @@ def filter_config(n, seed=1212, filter_id=0, scheme="systematic", precision="fp3
                     sigma2=sigma2, tau2=tau2)
 
 
+# Checkpoint header: magic, format version, header size, n, seed, filter id,
+# scheme, precision, known variances, algorithm, pad, eight prior/variance
+# doubles, t, log-ML, total size (see pf_checkpoint).
+_CKPT_FMT = "<QIIQQIiiiii8dQdQ"
+_CKPT_HEAD = struct.calcsize(_CKPT_FMT)
+
+
+def _ckpt_fields(head):
+    v = struct.unpack(_CKPT_FMT, head[:_CKPT_HEAD])
+    return int(v[3]), int(v[6]), int(v[7])
+
+
 class Filter:
     """One particle-learning filter (paper Section 2, Algorithm "Particle Learning")."""
 
@@ -321,6 +337,53 @@ class Filter:
         _check(_lib.pf_get_ancestors(self.h, _ptr(anc), _ptr(Q) if Q is not None else None),
                "pf_get_ancestors")
         return (anc, Q) if with_cdf else anc
+
+    def checkpoint(self, device=False):
+        """The filter's checkpoint (pf_checkpoint): a numpy uint8 array, or a
+        CUDA uint8 tensor with device=True."""
+        torch = _torch()
+        nb = C.c_size_t()
+        _check(_lib.pf_checkpoint_size(self.h, C.byref(nb)), "pf_checkpoint_size")
+        if device:
+            buf = torch.empty(nb.value, dtype=torch.uint8, device="cuda")
+            _check(_lib.pf_checkpoint(self.h, _ptr(buf), nb.value), "pf_checkpoint")
+        else:
+            buf = np.empty(nb.value, dtype=np.uint8)
+            _check(_lib.pf_checkpoint(self.h, buf.ctypes.data_as(C.c_void_p), nb.value),
+                   "pf_checkpoint")
+        return buf
+
+    @classmethod
+    def restore(cls, blob, stream=None, torch_alloc=True):
+        """A filter continuing from a checkpoint (pf_restore); blob is a numpy
+        uint8 array or a CUDA uint8 tensor."""
+        torch = _torch()
+        self = cls.__new__(cls)
+        self.h = None
+        is_dev = isinstance(blob, torch.Tensor) and blob.is_cuda
+        head = blob[:_CKPT_HEAD].cpu().numpy() if is_dev else np.asarray(blob[:_CKPT_HEAD])
+        if head.size < _CKPT_HEAD:
+            raise PfError(PF_ERR_INVALID, "pf_restore: checkpoint truncated")
+        n, scheme, precision = _ckpt_fields(head.tobytes())
+        self.n, self.scheme, self.precision = n, scheme, precision
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        if self.stream.cuda_stream == 0:
+            raise ValueError("pass a non-default torch.cuda.Stream (the cycle is graph-captured)")
+        self._alloc = TorchAllocator() if torch_alloc else None
+        cfg = PfConfig(stream=C.c_void_p(self.stream.cuda_stream))
+        if self._alloc is not None:
+            cfg.alloc = self._alloc.alloc
+            cfg.free = self._alloc.free
+        self._cfg = cfg
+        if is_dev:
+            ptr, size = _ptr(blob), blob.numel()
+        else:
+            arr = np.ascontiguousarray(blob, dtype=np.uint8)
+            ptr, size = arr.ctypes.data_as(C.c_void_p), arr.size
+        h = C.c_void_p()
+        _check(_lib.pf_restore(C.byref(cfg), ptr, size, C.byref(h)), "pf_restore")
+        self.h = h
+        return self
 
     def close(self):
         if getattr(self, "h", None):
