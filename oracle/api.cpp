@@ -189,6 +189,7 @@ typedef struct {
   int32_t known_variances;
   double x0_mean, x0_var, a_sigma, b_sigma, a_tau, b_tau, sigma2, tau2;
   int32_t algorithm;
+  double ess_frac;
 } or_config;
 
 static Config to_cfg(const or_config* c) {
@@ -199,6 +200,7 @@ static Config to_cfg(const or_config* c) {
   cfg.b_sigma = c->b_sigma; cfg.a_tau = c->a_tau; cfg.b_tau = c->b_tau;
   cfg.sigma2 = c->sigma2; cfg.tau2 = c->tau2;
   cfg.algorithm = c->algorithm;
+  cfg.ess_frac = c->ess_frac;
   return cfg;
 }
 
@@ -223,6 +225,10 @@ void or_pl_cdf(void* h, uint64_t* Q) {
   std::memcpy(Q, q.data(), q.size() * sizeof(uint64_t));
 }
 void or_pl_destroy(void* h) { delete (FilterBase*)h; }
+int or_pl_resampled(void* h) { return ((FilterBase*)h)->last_resampled() ? 1 : 0; }
+int or_ess_resample(const uint64_t* W, uint64_t n, double ess_frac) {
+  return ess_resample(W, n, ess_frac) ? 1 : 0;
+}
 
 int or_suffstat_known_states(const or_config* c, const double* xpath, const double* y,
                              uint32_t T, double* bs, double* bt, double* s2, double* t2) {

@@ -177,6 +177,11 @@ struct Config {
   int32_t known_variances;
   double sigma2, tau2;
   int32_t algorithm;  // 0 = particle learning, 1 = bootstrap filter (known variances)
+  // Adaptive resampling (particle learning only): 0 = resample every cycle
+  // (the paper's setting); in (0, 1], resample only when the effective
+  // sample size of the combined weights is below ess_frac * n, else carry
+  // the log-weights to the next cycle.
+  double ess_frac;
 };
 
 struct Estimates {
@@ -192,9 +197,17 @@ class FilterBase {
   virtual void state_raw(void* x, void* s2, void* t2, void* bs, void* bt) const = 0;
   virtual const std::vector<uint32_t>& last_ancestors() const = 0;
   virtual const std::vector<uint64_t>& last_cdf() const = 0;
+  virtual bool last_resampled() const = 0;
 };
 
 FilterBase* make_filter(const Config& cfg);
+
+// Adaptive resampling decision (Kong, Liu & Wong 1994; Liu & Chen 1998):
+// resample iff ESS = (sum W)^2 / sum W^2 < ess_frac * n for the quantised
+// weights W, evaluated as A * A < (ess_frac * n) * B in binary64 with
+// A = sum W and B = sum W^2 exact integers, each rounded to nearest once.
+// pin: exact rational comparison away from ties (tests/test_oracle_pl.py).
+bool ess_resample(const uint64_t* W, uint64_t n, double ess_frac);
 
 // Kalman filter for the local-level model with known variances (the closed
 // form of the Bayes filter, paper Section 2).  Outputs the filtered mean and

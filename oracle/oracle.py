@@ -34,7 +34,8 @@ class OrConfig(C.Structure):
                 ("x0_mean", C.c_double), ("x0_var", C.c_double),
                 ("a_sigma", C.c_double), ("b_sigma", C.c_double),
                 ("a_tau", C.c_double), ("b_tau", C.c_double),
-                ("sigma2", C.c_double), ("tau2", C.c_double), ("algorithm", C.c_int32)]
+                ("sigma2", C.c_double), ("tau2", C.c_double), ("algorithm", C.c_int32),
+                ("ess_frac", C.c_double)]
 
 
 PARTICLE_LEARNING, BOOTSTRAP = 0, 1
@@ -74,6 +75,8 @@ def _declare(L):
         "or_resample_cdf": (V, [u64p, U64, I, U64, U32, U32, u32p]),
         "or_resample_weights": (I, [f32p, U64, I, U64, U32, U32, u32p]),
         "or_pl_create": (C.c_void_p, [C.POINTER(OrConfig)]),
+        "or_pl_resampled": (I, [C.c_void_p]),
+        "or_ess_resample": (I, [u64p, U64, D]),
         "or_pl_step": (I, [C.c_void_p, D]),
         "or_pl_estimate": (V, [C.c_void_p, f64p]),
         "or_pl_state": (V, [C.c_void_p, f64p, f64p, f64p, f64p, f64p]),
@@ -269,15 +272,17 @@ def resample_weights(w, scheme, seed, filt, t):
 
 def make_config(n, seed=1212, filter_id=0, scheme=MULTINOMIAL, precision=FP64,
                 x0_mean=0.0, x0_var=10.0, a_sigma=3.0, b_sigma=2.0, a_tau=3.0, b_tau=2.0,
-                known_variances=False, sigma2=1.0, tau2=0.1, algorithm=PARTICLE_LEARNING):
+                known_variances=False, sigma2=1.0, tau2=0.1, algorithm=PARTICLE_LEARNING,
+                ess_frac=0.0):
     """algorithm: PARTICLE_LEARNING or BOOTSTRAP (Algorithm "Particle Filtering",
-    which takes the variances as known)."""
+    which takes the variances as known).  ess_frac > 0: adaptive resampling
+    (particle learning only), see oracle.h."""
     if algorithm == BOOTSTRAP and not known_variances:
         raise ValueError("the bootstrap filter takes known variances")
     return OrConfig(n=n, seed=seed, filter_id=filter_id, scheme=scheme, precision=precision,
                     known_variances=int(known_variances), x0_mean=x0_mean, x0_var=x0_var,
                     a_sigma=a_sigma, b_sigma=b_sigma, a_tau=a_tau, b_tau=b_tau,
-                    sigma2=sigma2, tau2=tau2, algorithm=int(algorithm))
+                    sigma2=sigma2, tau2=tau2, algorithm=int(algorithm), ess_frac=float(ess_frac))
 
 
 ESTIMATE_FIELDS = ("t", "x_mean", "x_var", "sigma2_mean", "sigma2_var",
@@ -323,6 +328,10 @@ class Filter:
         lib().or_pl_ancestors(self.h, a)
         return a
 
+    def resampled(self):
+        """Whether the last cycle resampled (always, unless adaptive)."""
+        return bool(lib().or_pl_resampled(self.h))
+
     def cdf(self):
         q = np.zeros(self.n, np.uint64)
         lib().or_pl_cdf(self.h, q)
@@ -348,6 +357,12 @@ def suffstat_known_states(cfg, xpath, y):
     outs = [np.zeros(cfg.n, np.float64) for _ in range(4)]
     rc = lib().or_suffstat_known_states(C.byref(cfg), xpath, y, T, *outs)
     return dict(zip(("b_sigma", "b_tau", "sigma2", "tau2"), outs)), rc
+
+
+def ess_resample(W, ess_frac):
+    """The adaptive resampling decision for quantised weights W (uint64)."""
+    W = np.ascontiguousarray(W, np.uint64)
+    return bool(lib().or_ess_resample(W, W.size, float(ess_frac)))
 
 
 def kalman(y, m0, P0, sigma2, tau2):

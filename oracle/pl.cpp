@@ -15,6 +15,20 @@
 //   sigma^2 ~ IG(a_sigma0 + (t+1)/2, b_sigma), tau^2 ~ IG(a_tau0 + (t+1)/2, b_tau).
 // pin: Kalman filter with known variances, conjugate inverse-gamma posterior
 // with known states, prior means (tests/test_oracle_pl.py).
+//
+// Adaptive resampling (cfg.ess_frac > 0; not in the paper, which resamples
+// every cycle): the filter carries log-weights lambda_i (0 after a
+// resampling).  Step 1 combines them with the predictive weights,
+// L_i = lambda_i + log p(y_{t+1} | z_t^(i)), builds the CDF from L and
+// resamples only when the effective sample size of those weights is below
+// ess_frac * n; otherwise every particle is its own ancestor and carries
+// lambda'_i = L_i - max L.  This is the fully adapted auxiliary particle filter
+// with an ESS trigger (Pitt & Shephard 1999; Kong, Liu & Wong 1994).  The log
+// marginal likelihood increment is log sum_i e^{L_i} - log sum_i e^{lambda_i}
+// (log n after a resampling), and the posterior summaries are weighted by
+// e^{lambda_i}.
+// pin: Kalman filter with known variances (adaptive and never-resampling
+// forms), equality with the always-resampling filter when ess_frac = 1.
 #include <cmath>
 #include <limits>
 
@@ -99,6 +113,21 @@ template <class R> static inline R log_pred(R x, R s2, R t2, R y) {
   return (R)-0.5 * a;
 }
 
+bool ess_resample(const uint64_t* W, uint64_t n, double ess_frac) {
+  uint64_t T = 0;
+  u128 B = 0;
+  for (uint64_t i = 0; i < n; ++i) {
+    T += W[i];
+    B += (u128)W[i] * W[i];
+  }
+  const double A = (double)T;    // correctly rounded conversions
+  const double Bd = (double)B;
+  const double lhs = A * A;
+  const double f = ess_frac * (double)n;
+  const double rhs = f * Bd;
+  return lhs < rhs;
+}
+
 template <class R> class Filter : public FilterBase {
   typedef typename Suff<R>::B B;
 
@@ -106,6 +135,9 @@ template <class R> class Filter : public FilterBase {
   explicit Filter(const Config& c) : cfg(c), n(c.n), t(0), k(cdf_shift(c.n)), logml(0.0) {
     x.resize(n); s2.resize(n); t2.resize(n); bs.resize(n); bt.resize(n);
     anc.resize(n); Q.resize(n);
+    ess = cfg.ess_frac > 0.0 && cfg.algorithm == 0;
+    if (ess) lam.assign(n, (R)0);
+    slam = (double)n;
     const R x0m = (R)cfg.x0_mean;
     const R sdx = (R)std::sqrt(cfg.x0_var);
     double ds, cs, dt, ct;
@@ -137,9 +169,13 @@ template <class R> class Filter : public FilterBase {
   int step(double y) override {
     if (cfg.algorithm == 1) return step_bootstrap(y);
     const R yr = (R)y;
-    // Step 1: predictive weights and the resampling CDF.
+    // Step 1: predictive weights and the resampling CDF (with adaptive
+    // resampling: combined with the carried log-weights).
     std::vector<R> ell(n);
-    for (uint64_t i = 0; i < n; ++i) ell[i] = log_pred<R>(x[i], s2[i], t2[i], yr);
+    for (uint64_t i = 0; i < n; ++i) {
+      ell[i] = log_pred<R>(x[i], s2[i], t2[i], yr);
+      if (ess) ell[i] = lam[i] + ell[i];
+    }
     R m = ell[0];
     for (uint64_t i = 1; i < n; ++i)
       if (ell[i] > m) m = ell[i];
@@ -153,8 +189,24 @@ template <class R> class Filter : public FilterBase {
       S.add(e);
     }
     cdf_scan(W.data(), n, Q.data());
-    logml += (double)m + std::log(S.value()) - std::log((double)n) - 0.5 * LOG_2PI;
-    resample(Q.data(), n, cfg.scheme, cfg.seed, cfg.filter_id, t, anc.data());
+    if (ess) {
+      logml += (double)m + std::log(S.value()) - std::log(slam) - 0.5 * LOG_2PI;
+      resampled = ess_resample(W.data(), n, cfg.ess_frac);
+      if (resampled) {
+        resample(Q.data(), n, cfg.scheme, cfg.seed, cfg.filter_id, t, anc.data());
+        for (uint64_t j = 0; j < n; ++j) lam[j] = (R)0;
+        slam = (double)n;
+      } else {
+        for (uint64_t j = 0; j < n; ++j) {
+          anc[j] = (uint32_t)j;
+          lam[j] = ell[j] - m;
+        }
+        slam = S.value();
+      }
+    } else {
+      logml += (double)m + std::log(S.value()) - std::log((double)n) - 0.5 * LOG_2PI;
+      resample(Q.data(), n, cfg.scheme, cfg.seed, cfg.filter_id, t, anc.data());
+    }
 
     // Steps 2-4: propagate, update sufficient statistics, draw theta.
     double ds, cs, dt, ct;
@@ -251,9 +303,22 @@ template <class R> class Filter : public FilterBase {
   Estimates estimate() const override {
     Estimates E;
     E.t = (double)t;
-    moments(x, &E.x_mean, &E.x_var);
-    moments(s2, &E.sigma2_mean, &E.sigma2_var);
-    moments(t2, &E.tau2_mean, &E.tau2_var);
+    if (ess) {
+      // weights e^{lambda_i}, by the deterministic exp of the CDF
+      std::vector<double> w(n);
+      for (uint64_t i = 0; i < n; ++i) {
+        R e;
+        (void)quant_exp<R>(lam[i], k, &e);
+        w[i] = (double)e;
+      }
+      wmoments(x, w, &E.x_mean, &E.x_var);
+      wmoments(s2, w, &E.sigma2_mean, &E.sigma2_var);
+      wmoments(t2, w, &E.tau2_mean, &E.tau2_var);
+    } else {
+      moments(x, &E.x_mean, &E.x_var);
+      moments(s2, &E.sigma2_mean, &E.sigma2_var);
+      moments(t2, &E.tau2_mean, &E.tau2_var);
+    }
     E.log_marglik = logml;
     return E;
   }
@@ -273,8 +338,27 @@ template <class R> class Filter : public FilterBase {
   }
   const std::vector<uint32_t>& last_ancestors() const override { return anc; }
   const std::vector<uint64_t>& last_cdf() const override { return Q; }
+  bool last_resampled() const override { return resampled; }
 
  private:
+  // Weighted mean and variance, two-pass, in binary64.
+  static void wmoments(const std::vector<R>& v, const std::vector<double>& w, double* mean,
+                       double* var) {
+    double sw = 0.0, s = 0.0;
+    for (size_t i = 0; i < v.size(); ++i) {
+      sw += w[i];
+      s += w[i] * (double)v[i];
+    }
+    double mu = s / sw;
+    double q = 0.0;
+    for (size_t i = 0; i < v.size(); ++i) {
+      double d = (double)v[i] - mu;
+      q += w[i] * (d * d);
+    }
+    *mean = mu;
+    *var = q / sw;
+  }
+
   // Population mean and variance, two-pass, in binary64.
   static void moments(const std::vector<R>& v, double* mean, double* var) {
     double s = 0.0;
@@ -295,6 +379,10 @@ template <class R> class Filter : public FilterBase {
   int k;
   double logml;
   int fail = 0;
+  bool ess = false;        // adaptive resampling
+  bool resampled = true;   // the last cycle resampled
+  double slam;             // sum_i e^{lambda_i} of the carried log-weights
+  std::vector<R> lam;      // carried log-weights (adaptive resampling)
   std::vector<R> x, s2, t2;
   std::vector<B> bs, bt;
   std::vector<uint32_t> anc;
