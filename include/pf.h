@@ -106,6 +106,16 @@ typedef struct {
   pf_free_fn free;
   void* alloc_ctx;
   int32_t algorithm;       /* pf_algorithm; 0 = particle learning */
+  /* Adaptive resampling (particle learning, single filters; not in the
+   * paper, which resamples every cycle).  0: resample every cycle.  In
+   * (0, 1]: the filter carries log-weights lambda_i between cycles, combines
+   * them with the predictive weights (L_i = lambda_i + log p(y | z_i)) and
+   * resamples only when ESS = (sum W)^2 / sum W^2 of the quantised weights
+   * is below ess_frac * n_particles (decided in binary64 from the exact
+   * integer sums); otherwise every particle is its own ancestor and carries
+   * lambda_i = L_i - max L.  The log marginal likelihood is normalised by
+   * sum exp(lambda) and the summaries are weighted by exp(lambda). */
+  double ess_frac;
 } pf_config;
 
 /* The cycle run by a single filter.

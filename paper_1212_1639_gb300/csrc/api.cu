@@ -102,6 +102,12 @@ struct pf_filter {
   std::vector<void*> allocs;
   void* x[2] = {}; void* s2[2] = {}; void* t2[2] = {}; void* bs[2] = {}; void* bt[2] = {};
   void* ell = nullptr;
+  // adaptive resampling (cfg.ess_frac > 0): carried log-weights, the grid of
+  // the decision kernel and its per-block partial sums
+  bool ess = false;
+  void* lam = nullptr;
+  unsigned ess_grid = 0;
+  U128* ess_part = nullptr;
   uint64_t* Q = nullptr;
   uint64_t* S = nullptr;
   uint32_t* anc = nullptr;
@@ -167,6 +173,9 @@ FilterArgs<R> filter_args(pf_filter* f) {
     a.stat_e[p] = f->stat_e[p];
   }
   a.ell = (R*)f->ell;
+  a.lam = (R*)f->lam;
+  a.ess_frac = f->cfg.ess_frac;
+  a.ess_part = f->ess_part;
   a.Q = f->Q;
   a.S = f->S;
   a.anc = f->anc;
@@ -295,6 +304,10 @@ pf_status enqueue_cycle(pf_filter* f, KTimer* tm = nullptr, const double* y_src 
     k_scan<FROM_LOGLIK, R><<<f->ntiles, BLOCK, 0, s>>>(sa);
     mark(tm, "scan", s);
   }
+  if (f->ess) {  // adaptive resampling: the decision from the finished CDF
+    k_ess<R><<<f->ess_grid, BLOCK, 0, s>>>(a);
+    mark(tm, "ess", s);
+  }
   if (is_multinomial(f->scheme)) {
     SpacingArgs sp;
     sp.S = f->S;
@@ -345,11 +358,19 @@ pf_status enqueue_cycle(pf_filter* f, KTimer* tm = nullptr, const double* y_src 
     pf_status st = launch_resample(f->scheme, pa, n, f->I, f->splits, s, tm);
     if (st != PF_OK) return st;
   }
-  const bool fuse = !f->bootstrap && form_fuses(form);
+  const bool fuse = !f->bootstrap && !f->ess && form_fuses(form);
   const unsigned pg = fuse ? f->prop_grid_fuse : f->prop_grid;
   if (f->bootstrap) {
     k_boot_gather<R><<<(unsigned)cdiv(n, BLOCK), BLOCK, 0, s>>>(a);
     mark(tm, "gather", s);
+  } else if (f->ess) {  // adaptive resampling (never fused)
+    if constexpr (sizeof(R) == 4) {
+      if (f->learn) k_propagate2<true, false, true><<<pg, BLOCK, 0, s>>>(a);
+      else k_propagate2<false, false, true><<<pg, BLOCK, 0, s>>>(a);
+    } else {
+      if (f->learn) k_propagate<R, true, false, true><<<pg, BLOCK, 0, s>>>(a);
+      else k_propagate<R, false, false, true><<<pg, BLOCK, 0, s>>>(a);
+    }
   } else if constexpr (sizeof(R) == 4) {  // binary32: two slots per thread, paired arithmetic
     if (f->learn) {
       if (fuse) k_propagate2<true, true><<<pg, BLOCK, 0, s>>>(a);
@@ -449,7 +470,9 @@ void set_obs(unsigned char* args, bool next, const double* src, double val) {
 // propagation node.
 pf_status launch_cycle(pf_filter* f, const double* y_src, double y_val, int form = CF_PLAIN,
                        const double* ynx_src = nullptr, double ynx_val = 0.0) {
-  if (f->bootstrap) form = CF_PLAIN;  // its weights follow its own blind propagation
+  // the bootstrap filter's weights follow its own blind propagation;
+  // adaptive resampling carries weights the fused propagation does not add
+  if (f->bootstrap || f->ess) form = CF_PLAIN;
   CycleGraph& G = f->cg[form];
   if (!G.exec) {
     pf_status st = build_graph(f, form);
@@ -511,6 +534,10 @@ pf_status pf_create(const pf_config* cfg, pf_filter** out) {
     return set_err(PF_ERR_INVALID, "prior scales must be > 0 and x0_var >= 0");
   if (cfg->known_variances && !(cfg->sigma2 > 0 && cfg->tau2 > 0))
     return set_err(PF_ERR_INVALID, "known variances must be > 0");
+  if (!(cfg->ess_frac >= 0.0 && cfg->ess_frac <= 1.0))
+    return set_err(PF_ERR_INVALID, "ess_frac must be in [0, 1]");
+  if (cfg->ess_frac > 0.0 && cfg->algorithm != PF_PARTICLE_LEARNING)
+    return set_err(PF_ERR_INVALID, "adaptive resampling runs with particle learning");
   if ((cfg->alloc == nullptr) != (cfg->free == nullptr))
     return set_err(PF_ERR_INVALID, "alloc and free must both be set or both NULL");
   pf_filter* f = new (std::nothrow) pf_filter();
@@ -521,6 +548,7 @@ pf_status pf_create(const pf_config* cfg, pf_filter** out) {
   f->ntiles = (uint32_t)cdiv(f->n, TILE);
   f->fp64 = cfg->precision == PF_FP64;
   f->learn = !cfg->known_variances;
+  f->ess = cfg->ess_frac > 0.0;
   f->bootstrap = cfg->algorithm == PF_BOOTSTRAP;
   f->scheme = cfg->scheme;
   pf_status st = PF_OK;
@@ -560,7 +588,14 @@ pf_status pf_create(const pf_config* cfg, pf_filter** out) {
   if ((st = dev_alloc(f, (size_t)f->ntiles * 32, &f->part)) != PF_OK) return bail(st);
   f->nparts = f->ntiles;
   const uint64_t est_blocks = cdiv(n, (uint64_t)BLOCK * EST_PER_THREAD);
-  if ((st = dev_alloc(f, est_blocks * 6 * 8, (void**)&f->part_est)) != PF_OK) return bail(st);
+  if ((st = dev_alloc(f, est_blocks * 8 * 8, (void**)&f->part_est)) != PF_OK) return bail(st);
+  if (f->ess) {
+    if ((st = dev_alloc(f, n * rs, &f->lam)) != PF_OK) return bail(st);
+    const uint64_t eb = cdiv(n, (uint64_t)BLOCK * ESS_PER_THREAD);
+    f->ess_grid = (unsigned)(eb < 1024 ? eb : 1024);
+    if ((st = dev_alloc(f, (size_t)f->ess_grid * sizeof(U128), (void**)&f->ess_part)) != PF_OK)
+      return bail(st);
+  }
   if ((st = dev_alloc(f, sizeof(Ctl), (void**)&f->ctl)) != PF_OK) return bail(st);
   if (cudaHostAlloc((void**)&f->ctl_host, sizeof(Ctl), cudaHostAllocDefault) != cudaSuccess) {
     cudaGetLastError();
@@ -582,9 +617,13 @@ pf_status pf_create(const pf_config* cfg, pf_filter** out) {
       c0.maxenc = (b & 0x80000000u) ? ~b : (b | 0x80000000u);
     }
   }
+  c0.resamp = 1;
+  c0.slam = (double)n;
   *f->ctl_host = c0;
   if (cudaMemcpyAsync(f->ctl, f->ctl_host, sizeof(Ctl), cudaMemcpyHostToDevice, f->stream) != cudaSuccess)
     return bail(set_err(PF_ERR_CUDA, "control block upload failed"));
+  if (f->ess && cudaMemsetAsync(f->lam, 0, n * rs, f->stream) != cudaSuccess)
+    return bail(set_err(PF_ERR_CUDA, "log-weight memset failed"));
   for (int p = 0; p < 2; ++p) {
     if (cudaMemsetAsync(f->stat_w[p], 0, (size_t)f->ntiles * 8, f->stream) != cudaSuccess ||
         cudaMemsetAsync(f->stat_e[p], 0, (size_t)f->ntiles * 8, f->stream) != cudaSuccess)
@@ -623,7 +662,7 @@ pf_status pf_create(const pf_config* cfg, pf_filter** out) {
     if (e != cudaSuccess || per_sm_f < 1) return bail(set_err(PF_ERR_CUDA, "occupancy query failed"));
     const uint64_t cap_f = (uint64_t)per_sm_f * (uint64_t)sms;
     f->prop_grid_fuse = (unsigned)(want < cap_f ? want : cap_f);
-    if (f->scheme == PF_SYSTEMATIC) {
+    if (f->scheme == PF_SYSTEMATIC && !f->ess) {
       // cooperative grid: every CTA resident at once (it waits on the others).
       // One tile per CTA when the tiles fit at once -- in binary32 2048-particle
       // tiles (8 per thread) if those fit, for twice the parallelism -- else
@@ -685,7 +724,7 @@ pf_status pf_step(pf_filter* f, double y) {
 pf_status pf_step_ahead(pf_filter* f, double y, double y_next) {
   pf_status st = check_handle(f);
   if (st != PF_OK) return st;
-  if (f->bootstrap) return pf_step(f, y);
+  if (f->bootstrap || f->ess) return pf_step(f, y);
   int form = CF_PLAIN;
   if ((st = form_for(f, y, true, &form)) != PF_OK) return st;
   if ((st = launch_cycle(f, nullptr, y, form, nullptr, y_next)) != PF_OK) return f->sticky = st;
@@ -724,7 +763,7 @@ static pf_status step_profiled(pf_filter* f, double y, bool fuse_next, double y_
   pf_status st = check_handle(f);
   if (st != PF_OK) return st;
   if (!kernel_ms || !n_kernels || max_kernels < 1) return set_err(PF_ERR_INVALID, "NULL output");
-  if (f->bootstrap) fuse_next = false;
+  if (f->bootstrap || f->ess) fuse_next = false;
   int form = CF_PLAIN;
   if ((st = form_for(f, y, fuse_next, &form)) != PF_OK) return st;
   KTimer tm;
@@ -769,8 +808,14 @@ pf_status pf_estimate(pf_filter* f, pf_estimates* out) {
   if (st != PF_OK) return st;
   if (!out) return set_err(PF_ERR_INVALID, "NULL output");
   const unsigned grid = (unsigned)cdiv(f->n, (uint64_t)BLOCK * EST_PER_THREAD);
-  if (f->fp64) k_estimate<double><<<grid, BLOCK, 0, f->stream>>>(filter_args<double>(f));
-  else k_estimate<float><<<grid, BLOCK, 0, f->stream>>>(filter_args<float>(f));
+  if (f->ess) {  // weighted by the carried log-weights
+    if (f->fp64) k_estimate_w<double><<<grid, BLOCK, 0, f->stream>>>(filter_args<double>(f));
+    else k_estimate_w<float><<<grid, BLOCK, 0, f->stream>>>(filter_args<float>(f));
+  } else if (f->fp64) {
+    k_estimate<double><<<grid, BLOCK, 0, f->stream>>>(filter_args<double>(f));
+  } else {
+    k_estimate<float><<<grid, BLOCK, 0, f->stream>>>(filter_args<float>(f));
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     f->sticky = PF_ERR_CUDA;
@@ -832,12 +877,13 @@ pf_status pf_destroy(pf_filter* f) {
 
 // ---------------------------------------------------------------------------
 // Checkpoint and resume: a header, then the current parity's x, sigma^2,
-// tau^2 (R each), b_sigma, b_tau (8 bytes each), n of each.
+// tau^2 (R each), b_sigma, b_tau (8 bytes each), n of each, and with
+// adaptive resampling the carried log-weights (R each).
 // ---------------------------------------------------------------------------
 namespace {
 
 constexpr uint64_t CKPT_MAGIC = 0x54504b434c4c4650ull;  // "PFLLCKPT"
-constexpr uint32_t CKPT_VERSION = 1;
+constexpr uint32_t CKPT_VERSION = 2;
 
 struct CkptHeader {
   uint64_t magic;
@@ -850,11 +896,13 @@ struct CkptHeader {
   double x0_mean, x0_var, a_sigma, b_sigma, a_tau, b_tau, sigma2, tau2;
   uint64_t t;
   double logml;
+  double ess_frac, slam;
   uint64_t total_bytes;
 };
 
-size_t ckpt_bytes(uint64_t n, bool fp64) {
-  return sizeof(CkptHeader) + (size_t)n * (3 * (fp64 ? 8 : 4) + 16);
+size_t ckpt_bytes(uint64_t n, bool fp64, bool ess) {
+  const size_t rs = fp64 ? 8 : 4;
+  return sizeof(CkptHeader) + (size_t)n * (3 * rs + 16 + (ess ? rs : 0));
 }
 
 }  // namespace
@@ -863,7 +911,7 @@ extern "C" {
 
 pf_status pf_checkpoint_size(pf_filter* f, size_t* bytes) {
   if (!f || !bytes) return set_err(PF_ERR_INVALID, "NULL argument");
-  *bytes = ckpt_bytes(f->n, f->fp64);
+  *bytes = ckpt_bytes(f->n, f->fp64, f->ess);
   return PF_OK;
 }
 
@@ -871,7 +919,7 @@ pf_status pf_checkpoint(pf_filter* f, void* buf, size_t bytes) {
   pf_status st = check_handle(f);
   if (st != PF_OK) return st;
   if (!buf) return set_err(PF_ERR_INVALID, "NULL buffer");
-  const size_t need = ckpt_bytes(f->n, f->fp64);
+  const size_t need = ckpt_bytes(f->n, f->fp64, f->ess);
   if (bytes < need) return set_err(PF_ERR_INVALID, "checkpoint needs %zu bytes, got %zu", need, bytes);
   if (f->ahead)
     return set_err(PF_ERR_INVALID, "a pf_step_ahead announcement is pending: pf_step(%.17g) first",
@@ -899,6 +947,12 @@ pf_status pf_checkpoint(pf_filter* f, void* buf, size_t bytes) {
   h.tau2 = f->cfg.tau2;
   h.t = f->ctl_host->t;
   h.logml = f->ctl_host->logml;
+  h.ess_frac = f->cfg.ess_frac;
+  if (f->ess) {  // the carried weights' sum lies past the summary part
+    CK(cudaMemcpy(&h.slam, &f->ctl->slam, sizeof(double), cudaMemcpyDeviceToHost));
+  } else {
+    h.slam = (double)f->n;
+  }
   h.total_bytes = need;
   char* out = static_cast<char*>(buf);
   CK(cudaMemcpy(out, &h, sizeof(h), cudaMemcpyDefault));
@@ -911,6 +965,7 @@ pf_status pf_checkpoint(pf_filter* f, void* buf, size_t bytes) {
     CK(cudaMemcpyAsync(out + off, src[i], f->n * sz[i], cudaMemcpyDefault, f->stream));
     off += f->n * sz[i];
   }
+  if (f->ess) CK(cudaMemcpyAsync(out + off, f->lam, f->n * rs, cudaMemcpyDefault, f->stream));
   CK(cudaStreamSynchronize(f->stream));
   return PF_OK;
 }
@@ -928,7 +983,9 @@ pf_status pf_restore(const pf_config* cfg, const void* buf, size_t bytes, pf_fil
   if (h.precision != PF_FP32 && h.precision != PF_FP64) return set_err(PF_ERR_INVALID, "bad precision");
   if (h.n < 1 || h.n > PF_MAX_PARTICLES) return set_err(PF_ERR_INVALID, "bad particle count");
   const bool fp64 = h.precision == PF_FP64;
-  const size_t need = ckpt_bytes(h.n, fp64);
+  if (!(h.ess_frac >= 0.0 && h.ess_frac <= 1.0)) return set_err(PF_ERR_INVALID, "bad ess_frac");
+  const bool ess = h.ess_frac > 0.0;
+  const size_t need = ckpt_bytes(h.n, fp64, ess);
   if (h.total_bytes != need || bytes < need)
     return set_err(PF_ERR_INVALID, "checkpoint truncated or inconsistent (%zu of %zu bytes)", bytes, need);
   if (h.t >= 0xffffffffull) return set_err(PF_ERR_INVALID, "bad cycle count");
@@ -949,6 +1006,7 @@ pf_status pf_restore(const pf_config* cfg, const void* buf, size_t bytes, pf_fil
   c.b_tau = h.b_tau;
   c.sigma2 = h.sigma2;
   c.tau2 = h.tau2;
+  c.ess_frac = h.ess_frac;
   if (cfg) {
     c.stream = cfg->stream;
     c.alloc = cfg->alloc;
@@ -973,15 +1031,21 @@ pf_status pf_restore(const pf_config* cfg, const void* buf, size_t bytes, pf_fil
       return bail(set_err(PF_ERR_CUDA, "checkpoint upload: %s", cudaGetErrorString(cudaGetLastError())));
     off += h.n * sz[i];
   }
-  // the cycle count and the log marginal likelihood; the rest of the
-  // control block is as pf_create left it (no error, max -inf, counters 0)
+  if (ess && cudaMemcpyAsync(f->lam, in + off, h.n * rs, cudaMemcpyDefault, f->stream) != cudaSuccess)
+    return bail(set_err(PF_ERR_CUDA, "checkpoint upload: %s", cudaGetErrorString(cudaGetLastError())));
+  // the cycle count, the log marginal likelihood and the carried weights'
+  // sum; the rest of the control block is as pf_create left it (no error,
+  // max -inf, counters 0)
   if (cudaStreamSynchronize(f->stream) != cudaSuccess)
     return bail(set_err(PF_ERR_CUDA, "stream: %s", cudaGetErrorString(cudaGetLastError())));
   f->ctl_host->t = (uint32_t)h.t;
   f->ctl_host->logml = h.logml;
+  f->ctl_host->slam = h.slam;
   if (cudaMemcpyAsync(&f->ctl->t, &f->ctl_host->t, sizeof(uint32_t), cudaMemcpyHostToDevice,
                       f->stream) != cudaSuccess ||
       cudaMemcpyAsync(&f->ctl->logml, &f->ctl_host->logml, sizeof(double), cudaMemcpyHostToDevice,
+                      f->stream) != cudaSuccess ||
+      cudaMemcpyAsync(&f->ctl->slam, &f->ctl_host->slam, sizeof(double), cudaMemcpyHostToDevice,
                       f->stream) != cudaSuccess ||
       cudaStreamSynchronize(f->stream) != cudaSuccess)
     return bail(set_err(PF_ERR_CUDA, "checkpoint upload: %s", cudaGetErrorString(cudaGetLastError())));

@@ -224,6 +224,8 @@ pf_status validate_member(const pf_batch* b, const pf_config* c) {
     return set_err(PF_ERR_INVALID, "prior scales must be > 0 and x0_var >= 0");
   if (c->known_variances && !(c->sigma2 > 0 && c->tau2 > 0))
     return set_err(PF_ERR_INVALID, "known variances must be > 0");
+  if (c->ess_frac != 0.0)
+    return set_err(PF_ERR_INVALID, "batched and served filters resample every cycle");
   return PF_OK;
 }
 

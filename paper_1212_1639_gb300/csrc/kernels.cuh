@@ -66,6 +66,12 @@ struct Ctl {
   // the next cycle's maximum of l, gathered by a propagation that also
   // computes the next cycle's predictive weights (order-encoded, as maxenc)
   unsigned long long maxenc_nx;
+  // adaptive resampling: this cycle's decision (written by k_ess), the
+  // last-block counter of k_ess, and sum_i exp(lambda_i) of the carried
+  // log-weights (n after a resampling)
+  uint32_t resamp;
+  uint32_t done_ess;
+  double slam;
 };
 
 // Tile status words carry their value and flag in one aligned 64-bit word and
@@ -133,6 +139,11 @@ struct FilterArgs {
   // the next cycle's predictive weights (*y_nx_src when set, else y_nx_val)
   const double* y_nx_src;
   double y_nx_val;
+  // adaptive resampling: carried log-weights (NULL: resample every cycle),
+  // the ESS fraction and k_ess's per-block partial sums of W^2
+  R* lam;
+  double ess_frac;
+  U128* ess_part;
   uint64_t n;
   uint32_t ntiles;
   uint32_t nparts;          // log-ML partials written this cycle (one per CDF tile)
@@ -299,8 +310,18 @@ __global__ void __launch_bounds__(BLOCK, sizeof(R) == 4 ? 8 : 4) k_weights(Filte
       for (int e = 0; e < 4; ++e) { xv[e] = st.x[base + e]; sv[e] = st.s2[base + e]; tv[e] = st.t2[base + e]; }
     }
 #pragma unroll
+    for (int e = 0; e < 4; ++e) lv[e] = log_pred<R>(xv[e], sv[e], tv[e], yr);
+    if (a.lam) {  // adaptive resampling: L = lambda + l
+      if constexpr (sizeof(R) == 4) {
+        const float4 Lm = *reinterpret_cast<const float4*>(a.lam + base);
+        lv[0] = Lm.x + lv[0]; lv[1] = Lm.y + lv[1]; lv[2] = Lm.z + lv[2]; lv[3] = Lm.w + lv[3];
+      } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) lv[e] = a.lam[base + e] + lv[e];
+      }
+    }
+#pragma unroll
     for (int e = 0; e < 4; ++e) {
-      lv[e] = log_pred<R>(xv[e], sv[e], tv[e], yr);
       bad |= !(lv[e] < (R)INFINITY);  // NaN or +inf
       mx = fmax(mx, lv[e]);
     }
@@ -312,7 +333,8 @@ __global__ void __launch_bounds__(BLOCK, sizeof(R) == 4 ? 8 : 4) k_weights(Filte
     }
   } else {
     for (uint64_t i = base; i < a.n; ++i) {
-      const R l = log_pred<R>(st.x[i], st.s2[i], st.t2[i], yr);
+      R l = log_pred<R>(st.x[i], st.s2[i], st.t2[i], yr);
+      if (a.lam) l = a.lam[i] + l;
       bad |= !(l < (R)INFINITY);
       mx = fmax(mx, l);
       a.ell[i] = l;
@@ -1691,6 +1713,82 @@ __device__ __forceinline__ double esum_value(const ESum32& e) {
 }
 __device__ __forceinline__ double esum_value(const ESum64& e) { return e.s; }
 
+// ---------------------------------------------------------------------------
+// Adaptive resampling decision (not in the paper, which resamples every
+// cycle): ESS = (sum W)^2 / sum W^2 of the quantised weights against
+// ess_frac * n (Kong, Liu & Wong 1994).  sum W^2 is summed exactly in 128
+// bits from the finished CDF (W_i = Q_i - Q_{i-1}); sum W = Q_{n-1}.  The
+// comparison is A * A < (ess_frac * n) * B in binary64, A and B the two sums
+// each rounded to nearest once.  The last block writes the decision.
+// ---------------------------------------------------------------------------
+constexpr int ESS_PER_THREAD = 8;
+
+// Correctly rounded conversion of a 128-bit integer to binary64: the top 64
+// significant bits with a sticky bit for the rest, rounded once, scaled by an
+// exact power of two.
+__device__ __forceinline__ double u128_to_f64_rn(U128 v) {
+  if (v.hi == 0) return __ull2double_rn(v.lo);
+  const int lz = __clzll(v.hi);
+  const int sh = 64 - lz;  // 1..64
+  uint64_t top, rest;
+  if (lz == 0) {
+    top = v.hi;
+    rest = v.lo;
+  } else {
+    top = (v.hi << lz) | (v.lo >> sh);
+    rest = v.lo << lz;
+  }
+  const double d = __ull2double_rn(top | (rest != 0 ? 1ull : 0ull));
+  return d * __longlong_as_double((long long)(1023 + sh) << 52);
+}
+
+template <class R>
+__global__ void __launch_bounds__(BLOCK) k_ess(FilterArgs<R> a) {
+  __shared__ U128 s_red[WARPS];
+  __shared__ bool s_last;
+  const uint64_t n = a.n;
+  U128 acc{0, 0};
+  const uint64_t stride = (uint64_t)gridDim.x * BLOCK;
+  for (uint64_t i = (uint64_t)blockIdx.x * BLOCK + threadIdx.x; i < n; i += stride) {
+    const uint64_t W = a.Q[i] - (i ? a.Q[i - 1] : 0ull);
+    acc = add128(acc, mul64(W, W));
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    U128 v;
+    v.hi = __shfl_xor_sync(0xffffffffu, acc.hi, o);
+    v.lo = __shfl_xor_sync(0xffffffffu, acc.lo, o);
+    acc = add128(acc, v);
+  }
+  if (lane == 0) s_red[warp] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    U128 b = s_red[0];
+    for (int w = 1; w < WARPS; ++w) b = add128(b, s_red[w]);
+    a.ess_part[blockIdx.x] = b;
+    __threadfence();
+    s_last = atomicAdd(&a.ctl->done_ess, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!s_last || threadIdx.x != 0) return;
+  __threadfence();
+  U128 B{0, 0};  // an exact integer sum: the order does not matter
+  for (uint32_t b = 0; b < gridDim.x; ++b) {
+    U128 v;
+    v.hi = __ldcg(&a.ess_part[b].hi);
+    v.lo = __ldcg(&a.ess_part[b].lo);
+    B = add128(B, v);
+  }
+  const double A = __ull2double_rn(a.Q[n - 1]);
+  const double Bd = u128_to_f64_rn(B);
+  const double lhs = A * A;
+  const double f = a.ess_frac * (double)n;
+  const double rhs = f * Bd;
+  a.ctl->resamp = lhs < rhs ? 1u : 0u;
+  a.ctl->done_ess = 0;
+}
+
 // Run by the last warp of k_propagate: fold the per-tile log-ML partials
 // (lane-strided, then butterfly: a fixed order), accumulate the increment
 // m + log(sum_i e_i) - log n - log(2 pi)/2, reset the per-cycle counters and
@@ -1701,7 +1799,11 @@ __device__ __forceinline__ double esum_value(const ESum64& e) { return e.s; }
 // weights kernel would write for the next cycle (observation y_{t+2},
 // Marsaglia-Tsang constants of the shapes a0 + (t+2)/2) are written here, once
 // every warp has read this cycle's.
-template <class R, bool FUSE = false>
+//
+// With ESS (adaptive resampling) the increment is normalised by the carried
+// weights, log sum_i exp(lambda_i), instead of log n, and that sum for the
+// next cycle is n after a resampling, else this cycle's sum of exp(L_i - m).
+template <class R, bool FUSE = false, bool ESS = false>
 __device__ void fold_cycle_warp(const FilterArgs<R>& a, uint32_t t) {
   typedef typename ESumT<R>::T ES;
   const int lane = threadIdx.x & 31;
@@ -1714,8 +1816,15 @@ __device__ void fold_cycle_warp(const FilterArgs<R>& a, uint32_t t) {
     Ctl* c = a.ctl;
     const double m = sizeof(R) == 4 ? (double)dec_f((uint32_t)c->maxenc) : dec_d(c->maxenc);
     const double LOG_2PI = 0x1.d67f1c864beb5p+0;
-    const double inc = m + log(esum_value(acc)) - log((double)a.n) - 0.5 * LOG_2PI;
-    c->logml = c->logml + inc;
+    if constexpr (ESS) {
+      const double S = esum_value(acc);
+      const double inc = m + log(S) - log(c->slam) - 0.5 * LOG_2PI;
+      c->logml = c->logml + inc;
+      c->slam = c->resamp ? (double)a.n : S;
+    } else {
+      const double inc = m + log(esum_value(acc)) - log((double)a.n) - 0.5 * LOG_2PI;
+      c->logml = c->logml + inc;
+    }
     const unsigned long long ninf =
         sizeof(R) == 4 ? (unsigned long long)enc_f(-INFINITY) : enc_d(-INFINITY);
     if constexpr (FUSE) {
@@ -1873,7 +1982,7 @@ __device__ __forceinline__ Gathered<R> gather_rec(const StateV<R>& src, uint32_t
 // finishes its last queued draw (bit 1 of `which` on that item), reading its
 // new state back after the round's warp barrier.  Every value is the one the
 // weights kernel would give.
-template <class R, bool LEARN, bool FUSE = false>
+template <class R, bool LEARN, bool FUSE = false, bool ESS = false>
 __global__ void __launch_bounds__(BLOCK, 5) k_propagate(FilterArgs<R> a) {
   typedef GammaItem<R> Item;
   __shared__ Item s_q[WARPS][WQ_CAP];
@@ -1895,6 +2004,29 @@ __global__ void __launch_bounds__(BLOCK, 5) k_propagate(FilterArgs<R> a) {
   const uint64_t stride = (uint64_t)gridDim.x * BLOCK;
   const uint64_t iters = (n + stride - 1) / stride;
   auto clampi = [&](uint32_t v) { return v < n ? v : (uint32_t)(n - 1); };
+  // adaptive resampling: without a resampling every slot is its own ancestor
+  bool rs = true;
+  R mR = 0;
+  if constexpr (ESS) {
+    rs = c->resamp != 0;
+    if constexpr (sizeof(R) == 4) mR = dec_f((uint32_t)c->maxenc);
+    else mR = dec_d(c->maxenc);
+  }
+  auto ancx = [&](uint64_t k) -> uint32_t {
+    if constexpr (ESS) {
+      if (!rs) return (uint32_t)k;
+    }
+    return clampi(a.anc[k]);
+  };
+  // the carried log-weight of slot j: 0 after a resampling, else L_j - m
+  auto carry = [&](uint64_t k) {
+    if (rs) {
+      a.lam[k] = (R)0;
+    } else {
+      a.lam[k] = a.ell[k] - mR;
+      a.anc[k] = (uint32_t)k;
+    }
+  };
   bool fail = false;
   // next cycle's weights (FUSE)
   R yn = 0;
@@ -1913,12 +2045,12 @@ __global__ void __launch_bounds__(BLOCK, 5) k_propagate(FilterArgs<R> a) {
     weigh_next<R>(a.ell, itm.j, dst.x[itm.j], dst.s2[itm.j], dst.t2[itm.j], yn, mxn, badn);
   };
   uint64_t j = (uint64_t)blockIdx.x * BLOCK + threadIdx.x;
-  uint32_t an = j < n ? clampi(a.anc[j]) : 0;
-  uint32_t an_next = j + stride < n ? clampi(a.anc[j + stride]) : 0;
+  uint32_t an = j < n ? ancx(j) : 0;
+  uint32_t an_next = j + stride < n ? ancx(j + stride) : 0;
   Gathered<R> cur = gather_rec<R>(src, an);
   for (uint64_t it = 0; it < iters; ++it, j += stride) {
     // prefetch: the index two slots ahead, the record one slot ahead
-    const uint32_t an_next2 = j + 2 * stride < n ? clampi(a.anc[j + 2 * stride]) : 0;
+    const uint32_t an_next2 = j + 2 * stride < n ? ancx(j + 2 * stride) : 0;
     const Gathered<R> nxt = gather_rec<R>(src, an_next);
     bool defer_s = false, defer_t = false;
     typename SuffT<R>::B bsn = 0, btn = 0;
@@ -1958,6 +2090,7 @@ __global__ void __launch_bounds__(BLOCK, 5) k_propagate(FilterArgs<R> a) {
         dst.bt[j] = cur.bt;
       }
       if (FUSE && !defer_s && !defer_t) weigh_next<R>(a.ell, j, xj, s2n, t2n, yn, mxn, badn);
+      if constexpr (ESS) carry(j);
     }
     if constexpr (LEARN && FUSE) {
       // the sigma^2 item sits below the tau^2 item of its slot, so it is
@@ -1988,7 +2121,7 @@ __global__ void __launch_bounds__(BLOCK, 5) k_propagate(FilterArgs<R> a) {
   bool last = false;
   if (lane == 0) last = atomicAdd(&a.ctl->done_prop, 1u) == gridDim.x * WARPS - 1;
   last = __shfl_sync(0xffffffffu, last, 0);
-  if (last) fold_cycle_warp<R, FUSE>(a, t);
+  if (last) fold_cycle_warp<R, FUSE, ESS>(a, t);
 }
 
 // ---------------------------------------------------------------------------
@@ -2002,7 +2135,7 @@ constexpr uint32_t WQ2_CAP = 160;  // 31 queued + 4 pushes of 32 per pass
 
 // With FUSE, the next cycle's weights as in k_propagate, the two slots of a
 // pass weighed by paired operations.
-template <bool LEARN, bool FUSE = false>
+template <bool LEARN, bool FUSE = false, bool ESS = false>
 __global__ void __launch_bounds__(BLOCK, 3) k_propagate2(FilterArgs<float> a) {
   typedef GammaItem<float> Item;
   __shared__ Item s_q[WARPS][WQ2_CAP];
@@ -2019,6 +2152,28 @@ __global__ void __launch_bounds__(BLOCK, 3) k_propagate2(FilterArgs<float> a) {
   const uint64_t stride = 2 * half;
   const uint64_t iters = (n + stride - 1) / stride;
   auto clampi = [&](uint32_t v) { return v < n ? v : (uint32_t)(n - 1); };
+  // adaptive resampling: without a resampling every slot is its own ancestor
+  bool rs = true;
+  float mR = 0.0f;
+  if constexpr (ESS) {
+    rs = c->resamp != 0;
+    mR = dec_f((uint32_t)c->maxenc);
+  }
+  auto ancx = [&](uint64_t k) -> uint32_t {
+    if constexpr (ESS) {
+      if (!rs) return (uint32_t)k;
+    }
+    return clampi(a.anc[k]);
+  };
+  // the carried log-weight of slot j: 0 after a resampling, else L_j - m
+  auto carry = [&](uint64_t k) {
+    if (rs) {
+      a.lam[k] = 0.0f;
+    } else {
+      a.lam[k] = a.ell[k] - mR;
+      a.anc[k] = (uint32_t)k;
+    }
+  };
   bool fail = false;
   // next cycle's weights (FUSE)
   float yn = 0.0f;
@@ -2038,15 +2193,15 @@ __global__ void __launch_bounds__(BLOCK, 3) k_propagate2(FilterArgs<float> a) {
     weigh_next<float>(a.ell, itm.j, dst.x[itm.j], dst.s2[itm.j], dst.t2[itm.j], yn, mxn, badn);
   };
   uint64_t j0 = (uint64_t)blockIdx.x * BLOCK + threadIdx.x;
-  Gathered<float> c0 = gather_rec<float>(src, j0 < n ? clampi(a.anc[j0]) : 0u);
-  Gathered<float> c1 = gather_rec<float>(src, j0 + half < n ? clampi(a.anc[j0 + half]) : 0u);
+  Gathered<float> c0 = gather_rec<float>(src, j0 < n ? ancx(j0) : 0u);
+  Gathered<float> c1 = gather_rec<float>(src, j0 + half < n ? ancx(j0 + half) : 0u);
   for (uint64_t it = 0; it < iters; ++it, j0 += stride) {
     const uint64_t j1 = j0 + half;
     const bool v0 = j0 < n, v1 = j1 < n;
     // the next pass's records, gathered ahead
     const uint64_t k0 = j0 + stride, k1 = j1 + stride;
-    const Gathered<float> n0 = gather_rec<float>(src, k0 < n ? clampi(a.anc[k0]) : 0u);
-    const Gathered<float> n1 = gather_rec<float>(src, k1 < n ? clampi(a.anc[k1]) : 0u);
+    const Gathered<float> n0 = gather_rec<float>(src, k0 < n ? ancx(k0) : 0u);
+    const Gathered<float> n1 = gather_rec<float>(src, k1 < n ? ancx(k1) : 0u);
     const float2 xa = make_float2(c0.x, c1.x), sa = make_float2(c0.s2, c1.s2);
     const float2 ta = make_float2(c0.t2, c1.t2);
     const float2 sm = add2(sa, ta);
@@ -2144,6 +2299,10 @@ __global__ void __launch_bounds__(BLOCK, 3) k_propagate2(FilterArgs<float> a) {
         if (v1) keep_next(a.ell, j1, l.y, mxn, badn);
       }
     }
+    if constexpr (ESS) {
+      if (v0) carry(j0);
+      if (v1) carry(j1);
+    }
     c0 = n0;
     c1 = n1;
   }
@@ -2154,7 +2313,7 @@ __global__ void __launch_bounds__(BLOCK, 3) k_propagate2(FilterArgs<float> a) {
   bool last = false;
   if (lane == 0) last = atomicAdd(&a.ctl->done_prop, 1u) == gridDim.x * WARPS - 1;
   last = __shfl_sync(0xffffffffu, last, 0);
-  if (last) fold_cycle_warp<float, FUSE>(a, t);
+  if (last) fold_cycle_warp<float, FUSE, ESS>(a, t);
 }
 
 // ---------------------------------------------------------------------------
@@ -2267,6 +2426,75 @@ __global__ void __launch_bounds__(BLOCK) k_estimate(FilterArgs<R> a) {
     for (int q = 0; q < 3; ++q) {
       const double m1 = s_tot[2 * q] / n;
       const double m2 = s_tot[2 * q + 1] / n;
+      a.ctl->est[1 + 2 * q] = cs[q] + m1;
+      a.ctl->est[2 + 2 * q] = m2 - m1 * m1;
+    }
+    a.ctl->est[7] = a.ctl->logml;
+    a.ctl->done_est = 0;
+  }
+}
+
+// Posterior summaries under adaptive resampling: the particles weighted by
+// w_i = exp(lambda_i) (the CDF's deterministic exp).  Per block: sums of w,
+// w (v - c) and w (v - c)^2 with c the value of particle 0, in binary64; the
+// last block folds the block partials in block order.
+template <class R>
+__global__ void __launch_bounds__(BLOCK) k_estimate_w(FilterArgs<R> a) {
+  __shared__ double s_sum[7][WARPS];
+  __shared__ bool s_last;
+  const uint32_t t = a.ctl->t;
+  const StateV<R> st = (t & 1) ? a.st[1] : a.st[0];
+  const R c0 = st.x[0], c1 = st.s2[0], c2 = st.t2[0];
+  double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+  const uint64_t base = ((uint64_t)blockIdx.x * BLOCK + threadIdx.x) * EST_PER_THREAD;
+  for (int e = 0; e < EST_PER_THREAD; ++e) {
+    const uint64_t i = base + e;
+    if (i < a.n) {
+      R wr;
+      (void)quant_exp<R>(a.lam[i], a.k, &wr);
+      const double w = (double)wr;
+      const double dx = (double)(st.x[i] - c0), ds = (double)(st.s2[i] - c1),
+                   dt = (double)(st.t2[i] - c2);
+      acc[0] += w;
+      acc[1] += w * dx; acc[2] += w * (dx * dx);
+      acc[3] += w * ds; acc[4] += w * (ds * ds);
+      acc[5] += w * dt; acc[6] += w * (dt * dt);
+    }
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < 7; ++q) {
+    double v = acc[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) s_sum[q][warp] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 7) {
+    double v = 0;
+    for (int w = 0; w < WARPS; ++w) v += s_sum[threadIdx.x][w];
+    a.part_est[(uint64_t)blockIdx.x * 7 + threadIdx.x] = v;
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = atomicAdd(&a.ctl->done_est, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  if (threadIdx.x < 7) {
+    double v = 0;
+    for (uint32_t b = 0; b < gridDim.x; ++b) v += __ldcg(a.part_est + (uint64_t)b * 7 + threadIdx.x);
+    s_sum[threadIdx.x][0] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const double sw = s_sum[0][0];
+    const double cs[3] = {(double)c0, (double)c1, (double)c2};
+    a.ctl->est[0] = (double)t;
+    for (int q = 0; q < 3; ++q) {
+      const double m1 = s_sum[1 + 2 * q][0] / sw;
+      const double m2 = s_sum[2 + 2 * q][0] / sw;
       a.ctl->est[1 + 2 * q] = cs[q] + m1;
       a.ctl->est[2 + 2 * q] = m2 - m1 * m1;
     }

@@ -43,7 +43,7 @@ class PfConfig(C.Structure):
                 ("a_tau", C.c_double), ("b_tau", C.c_double),
                 ("sigma2", C.c_double), ("tau2", C.c_double),
                 ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN),
-                ("alloc_ctx", C.c_void_p), ("algorithm", C.c_int32)]
+                ("alloc_ctx", C.c_void_p), ("algorithm", C.c_int32), ("ess_frac", C.c_double)]
 
 ALGORITHMS = {"pl": 0, "particle_learning": 0, "bootstrap": 1}
 
@@ -236,8 +236,9 @@ def filter_config(n, seed=1212, filter_id=0, scheme="systematic", precision="fp3
 
 # Checkpoint header: magic, format version, header size, n, seed, filter id,
 # scheme, precision, known variances, algorithm, pad, eight prior/variance
-# doubles, t, log-ML, total size (see pf_checkpoint).
-_CKPT_FMT = "<QIIQQIiiiii8dQdQ"
+# doubles, t, log-ML, ess_frac, carried weights' sum, total size (see
+# pf_checkpoint).
+_CKPT_FMT = "<QIIQQIiiiii8dQdddQ"
 _CKPT_HEAD = struct.calcsize(_CKPT_FMT)
 
 
@@ -252,9 +253,10 @@ class Filter:
     def __init__(self, n, seed=1212, filter_id=0, scheme="systematic", precision="fp32",
                  x0_mean=0.0, x0_var=10.0, a_sigma=3.0, b_sigma=2.0, a_tau=3.0, b_tau=2.0,
                  known_variances=False, sigma2=1.0, tau2=0.1, stream=None, torch_alloc=True,
-                 algorithm="pl"):
+                 algorithm="pl", ess_frac=0.0):
         """algorithm: "pl" (Algorithm "Particle Learning") or "bootstrap"
-        (Algorithm "Particle Filtering", with known_variances=True)."""
+        (Algorithm "Particle Filtering", with known_variances=True).
+        ess_frac > 0: adaptive resampling (pf_config.ess_frac)."""
         torch = _torch()
         self.n = int(n)
         self.precision = FP64 if precision in ("fp64", FP64) else FP32
@@ -269,7 +271,8 @@ class Filter:
                        x0_mean=x0_mean, x0_var=x0_var, a_sigma=a_sigma, b_sigma=b_sigma,
                        a_tau=a_tau, b_tau=b_tau, sigma2=sigma2, tau2=tau2,
                        stream=C.c_void_p(self.stream.cuda_stream),
-                       algorithm=ALGORITHMS[algorithm] if isinstance(algorithm, str) else int(algorithm))
+                       algorithm=ALGORITHMS[algorithm] if isinstance(algorithm, str) else int(algorithm),
+                       ess_frac=float(ess_frac))
         if self._alloc is not None:
             cfg.alloc = self._alloc.alloc
             cfg.free = self._alloc.free
