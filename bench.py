@@ -17,7 +17,9 @@ roofline: the dominant kernel's algorithmic bytes per launch / its mean
          CUDA-event duration (pf_step_profiled), against the measured copy
          bandwidth in MEASURED_PEAKS.json.
 Extra keys: the same cycle at N = 2^24 (the single-filter target size) and
-with multinomial and stratified resampling; batched filters (4096 uneven filters, one
+with multinomial and stratified resampling; with the next cycle's weights
+computed in the propagation (the series known ahead) at 2^20 and 2^24; with
+adaptive resampling (ESS below n/2); batched filters (4096 uneven filters, one
 persistent launch per cycle, against per-filter launches); the served form
 (10,000 streams under Poisson load, continuous batching, p50/p90/p99 latency;
 and under an 8 GB budget where admission waits); FP32 against FP64 precision.
@@ -262,6 +264,22 @@ def bench_fused(pf, n, stream, y, y_dev, flush, K, W, unfused_ms):
             "kernels": kern}
 
 
+def bench_adaptive(pf, n, stream, y, y_dev, flush, K, W, ess_frac=0.5):
+    """The single-filter workload with adaptive resampling: resample only when
+    the effective sample size drops below ess_frac * n."""
+    import torch
+    f = pf.Filter(n, seed=1639, scheme="systematic", precision="fp32", stream=stream,
+                  ess_frac=ess_frac)
+    f.run(y_dev[:W])
+    f.sync()
+    ms = time_cycles(f, y_dev, W, K, stream, flush)
+    prof = kernel_profile(f, y, W + K, 5, flush)
+    f.close()
+    return {"value": n * K / (ms / 1e3), "unit": UNIT, "steps": K, "ms_per_step": ms / K,
+            "ess_frac": ess_frac, "l2": "flushed before every timed cycle",
+            "kernels": {k: round(v, 5) for k, v in prof.items()}}
+
+
 def kernel_profile(f, y, start, P, flush):
     """Mean per-kernel durations (ms) over P profiled cycles."""
     import torch
@@ -403,6 +421,7 @@ def bench_ours(args):
                                                   ms / K)
         extra["n_2p24_fused_next_weights"] = bench_fused(pf, n24, stream, y, y_dev, None, K24, 3,
                                                          ms24 / K24)
+        extra["adaptive_ess"] = bench_adaptive(pf, n, stream, y, y_dev, flush, min(K, 100), W)
         for other in ("multinomial", "stratified"):  # the other resampling schemes
             if other == args.scheme:
                 continue

@@ -1771,15 +1771,29 @@ __global__ void __launch_bounds__(BLOCK) k_ess(FilterArgs<R> a) {
     s_last = atomicAdd(&a.ctl->done_ess, 1u) == gridDim.x - 1;
   }
   __syncthreads();
-  if (!s_last || threadIdx.x != 0) return;
+  if (!s_last) return;
   __threadfence();
-  U128 B{0, 0};  // an exact integer sum: the order does not matter
-  for (uint32_t b = 0; b < gridDim.x; ++b) {
+  // fold the block partials across the block: an exact integer sum, so the
+  // order does not matter
+  U128 B{0, 0};
+  for (uint32_t b = threadIdx.x; b < gridDim.x; b += BLOCK) {
     U128 v;
     v.hi = __ldcg(&a.ess_part[b].hi);
     v.lo = __ldcg(&a.ess_part[b].lo);
     B = add128(B, v);
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    U128 v;
+    v.hi = __shfl_xor_sync(0xffffffffu, B.hi, o);
+    v.lo = __shfl_xor_sync(0xffffffffu, B.lo, o);
+    B = add128(B, v);
+  }
+  if (lane == 0) s_red[warp] = B;
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  B = s_red[0];
+  for (int w = 1; w < WARPS; ++w) B = add128(B, s_red[w]);
   const double A = __ull2double_rn(a.Q[n - 1]);
   const double Bd = u128_to_f64_rn(B);
   const double lhs = A * A;
