@@ -200,6 +200,18 @@ def recorded_traffic(kernel, n):
     return None if v is None else v * n
 
 
+def max_over_ranks(x, world, device="cuda"):
+    """The maximum of a per-rank number over all ranks (the job's time is its
+    slowest rank's); x itself on one rank."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def time_cycles(f, y_dev, start, K, stream, flush):
     """K timed cycles; L2 flushed before each, outside the events."""
     import torch
@@ -331,9 +343,7 @@ def bench_ours(args):
     t_wall1 = time.perf_counter()
     clocks = clk.stop()
     if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = max_over_ranks(ms, world)
         dist.barrier()
     value = world * n * K / (ms / 1e3)
 
@@ -386,10 +396,7 @@ def bench_ours(args):
         est = fe.estimate()
         e2e_s += time.perf_counter() - t0
     assert est["t"] == W + Ke
-    if world > 1:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, world)
     e2e = {"value": world * n * Ke / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8,
            "d2h_bytes_per_step": 104, "steps": Ke,
            "note": "pf_step(y from host) + pf_estimate (reduction, 104-byte summary D2H, sync) per step; "
