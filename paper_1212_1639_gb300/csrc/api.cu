@@ -285,7 +285,9 @@ pf_status enqueue_cycle(pf_filter* f, KTimer* tm = nullptr, const double* y_src 
     k_boot_pw<R><<<(unsigned)cdiv(n, BLOCK), BLOCK, 0, s>>>(a);
     mark(tm, "propagate_weights", s);
   } else if (form_weighs(form)) {
-    k_weights<R><<<(unsigned)cdiv(n, (uint64_t)BLOCK * W_PER_THREAD), BLOCK, 0, s>>>(a);
+    const unsigned wg = (unsigned)cdiv(n, (uint64_t)BLOCK * W_PER_THREAD);
+    if (f->ess) k_weights<R, true><<<wg, BLOCK, 0, s>>>(a);
+    else k_weights<R><<<wg, BLOCK, 0, s>>>(a);
     mark(tm, "weights", s);
   }
   ScanArgs sa;
@@ -420,9 +422,10 @@ pf_status build_graph(pf_filter* f, int form) {
   CK(cudaGraphGetNodes(g, nullptr, &nn));
   std::vector<cudaGraphNode_t> nodes(nn);
   CK(cudaGraphGetNodes(g, nodes.data(), &nn));
-  const void* wfun = f->bootstrap
-      ? (f->fp64 ? (const void*)k_boot_pw<double> : (const void*)k_boot_pw<float>)
-      : (f->fp64 ? (const void*)k_weights<double> : (const void*)k_weights<float>);
+  const void* wfun =
+      f->bootstrap ? (f->fp64 ? (const void*)k_boot_pw<double> : (const void*)k_boot_pw<float>)
+      : f->ess     ? (f->fp64 ? (const void*)k_weights<double, true> : (const void*)k_weights<float, true>)
+                   : (f->fp64 ? (const void*)k_weights<double> : (const void*)k_weights<float>);
   const void* pfun = prop_fuse_fn(f);
   const size_t asz = f->fp64 ? sizeof(FilterArgs<double>) : sizeof(FilterArgs<float>);
   for (cudaGraphNode_t nd : nodes) {

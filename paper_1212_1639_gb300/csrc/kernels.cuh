@@ -269,7 +269,8 @@ __device__ __forceinline__ R block_max(R v, R* s_red) {
 // Four particles per thread, vectorised.
 constexpr int W_PER_THREAD = 4;
 
-template <class R>
+// With ESS (adaptive resampling) the carried log-weights are added: L = lambda + l.
+template <class R, bool ESS = false>
 __global__ void __launch_bounds__(BLOCK, sizeof(R) == 4 ? 8 : 4) k_weights(FilterArgs<R> a) {
   __shared__ R s_red[WARPS];
   __shared__ R s_y;
@@ -311,7 +312,7 @@ __global__ void __launch_bounds__(BLOCK, sizeof(R) == 4 ? 8 : 4) k_weights(Filte
     }
 #pragma unroll
     for (int e = 0; e < 4; ++e) lv[e] = log_pred<R>(xv[e], sv[e], tv[e], yr);
-    if (a.lam) {  // adaptive resampling: L = lambda + l
+    if constexpr (ESS) {  // adaptive resampling: L = lambda + l
       if constexpr (sizeof(R) == 4) {
         const float4 Lm = *reinterpret_cast<const float4*>(a.lam + base);
         lv[0] = Lm.x + lv[0]; lv[1] = Lm.y + lv[1]; lv[2] = Lm.z + lv[2]; lv[3] = Lm.w + lv[3];
@@ -334,7 +335,7 @@ __global__ void __launch_bounds__(BLOCK, sizeof(R) == 4 ? 8 : 4) k_weights(Filte
   } else {
     for (uint64_t i = base; i < a.n; ++i) {
       R l = log_pred<R>(st.x[i], st.s2[i], st.t2[i], yr);
-      if (a.lam) l = a.lam[i] + l;
+      if constexpr (ESS) l = a.lam[i] + l;
       bad |= !(l < (R)INFINITY);
       mx = fmax(mx, l);
       a.ell[i] = l;
@@ -1749,9 +1750,21 @@ __global__ void __launch_bounds__(BLOCK) k_ess(FilterArgs<R> a) {
   const uint64_t n = a.n;
   U128 acc{0, 0};
   const uint64_t stride = (uint64_t)gridDim.x * BLOCK;
-  for (uint64_t i = (uint64_t)blockIdx.x * BLOCK + threadIdx.x; i < n; i += stride) {
-    const uint64_t W = a.Q[i] - (i ? a.Q[i - 1] : 0ull);
-    acc = add128(acc, mul64(W, W));
+  // ESS_PER_THREAD strided elements per pass, their loads issued together
+  for (uint64_t i0 = (uint64_t)blockIdx.x * BLOCK + threadIdx.x; i0 < n;
+       i0 += stride * ESS_PER_THREAD) {
+    uint64_t q[ESS_PER_THREAD], qp[ESS_PER_THREAD];
+#pragma unroll
+    for (int e = 0; e < ESS_PER_THREAD; ++e) {
+      const uint64_t i = i0 + (uint64_t)e * stride;
+      q[e] = i < n ? a.Q[i] : 0ull;
+      qp[e] = (i < n && i > 0) ? a.Q[i - 1] : 0ull;
+    }
+#pragma unroll
+    for (int e = 0; e < ESS_PER_THREAD; ++e) {
+      const uint64_t W = q[e] - qp[e];
+      acc = add128(acc, mul64(W, W));
+    }
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
