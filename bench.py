@@ -10,6 +10,8 @@ value  : particle-steps/s over the K timed cycles, device time from CUDA events
          on the filter's stream, inputs resident in HBM; the 90 MB working set
          fits in L2, so L2 is flushed (256 MB write) before every timed cycle,
          outside the events.
+cycle_ms: median and p99 of the timed cycles, and the paper's statistic (the
+         mean of the 5 closest to the median of the first 10).
 e2e    : the same metric through the C ABI with host buffers: each step sends
          one observation from host memory (pf_step) and reads the posterior
          summaries back (pf_estimate), wall-clock timed.
@@ -19,7 +21,8 @@ roofline: the dominant kernel's algorithmic bytes per launch / its mean
 Extra keys: the same cycle at N = 2^24 (the single-filter target size) and
 with multinomial and stratified resampling; with the next cycle's weights
 computed in the propagation (the series known ahead) at 2^20 and 2^24; with
-adaptive resampling (ESS below n/2); batched filters (4096 uneven filters, one
+adaptive resampling (ESS below n/2); the resampling kernel sweep (pf_resample,
+N = 2^10..2^24, flat to degenerate weights); batched filters (4096 uneven filters, one
 persistent launch per cycle, against per-filter launches); the served form
 (10,000 streams under Poisson load, continuous batching, p50/p90/p99 latency;
 and under an 8 GB budget where admission waits); FP32 against FP64 precision.
@@ -48,7 +51,8 @@ N_DEFAULT = 1 << 20
 T_SERIES = 1000
 L2_FLUSH_BYTES = 256 << 20
 
-# Algorithmic bytes per particle per launch, FP32 state:
+# Algorithmic bytes per particle per launch, FP32 state: what each kernel must
+# read and write for the method, the roofline numerators:
 BYTES_PER_PARTICLE = {
     "weights": 12 + 4,            # read x, sigma2, tau2; write l
     "scan": 4 + 8,                # read l; write Q
@@ -212,8 +216,9 @@ def max_over_ranks(x, world, device="cuda"):
     return float(t.item())
 
 
-def time_cycles(f, y_dev, start, K, stream, flush):
-    """K timed cycles; L2 flushed before each, outside the events."""
+def time_cycles(f, y_dev, start, K, stream, flush, per=None):
+    """K timed cycles; L2 flushed before each, outside the events.  Returns the
+    total ms; per (a list) receives each cycle's ms."""
     import torch
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(K)]
@@ -224,7 +229,52 @@ def time_cycles(f, y_dev, start, K, stream, flush):
         f.run(y_dev[start + i:start + i + 1])
         ev[i][1].record(stream)
     torch.cuda.synchronize()
-    return sum(a.elapsed_time(b) for a, b in ev)
+    ms = [a.elapsed_time(b) for a, b in ev]
+    if per is not None:
+        per.extend(ms)
+    return sum(ms)
+
+
+def cycle_stats(per):
+    """Median and p99 of per-cycle times, and the paper's statistic: the mean
+    of the 5 runs closest to the median of the first 10 (Section 4)."""
+    v = np.array(per)
+    first = v[:10]
+    med10 = np.median(first)
+    closest = first[np.argsort(np.abs(first - med10))[:5]]
+    return {"median_ms": round(float(np.median(v)), 5), "p99_ms": round(float(np.percentile(v, 99)), 5),
+            "mean_of_5_closest_to_median_of_10_ms": round(float(closest.mean()), 5),
+            "cycles": int(v.size)}
+
+
+def bench_sweep(pf, synth, stream, reps=10):
+    """The resampling kernel sweep: pf_resample on normalised FP32 weights with
+    log-weights ~ N(0, s^2), N = 2^10 .. 2^24, resampled particles per second
+    (CUDA events around each call on the stream; scratch from the stream's
+    pool)."""
+    import torch
+    out = {}
+    for scheme, s in (("systematic", 1.0), ("systematic", 0.1), ("systematic", 5.0),
+                      ("multinomial", 1.0), ("stratified", 1.0)):
+        row = {}
+        for e in range(10, 25, 2):
+            n = 1 << e
+            w = torch.from_numpy(synth.sweep_weights(n, s, 7)).to("cuda")
+            anc = torch.empty(n, dtype=torch.int32, device="cuda")
+            torch.cuda.synchronize()
+            for _ in range(2):
+                pf.resample(w, 7, scheme=scheme, out=anc, stream=stream)
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                   for _ in range(reps)]
+            for a, b in evs:
+                a.record(stream)
+                pf.resample(w, 7, scheme=scheme, out=anc, stream=stream)
+                b.record(stream)
+            torch.cuda.synchronize()
+            ms = float(np.median([a.elapsed_time(b) for a, b in evs]))
+            row["2^%d" % e] = {"ms": round(ms, 4), "particles_per_s": n / (ms / 1e3)}
+        out["%s_s%g" % (scheme, s)] = row
+    return out
 
 
 def time_cycles_ahead(f, y, start, K, stream, flush):
@@ -339,7 +389,8 @@ def bench_ours(args):
     clk = Clocks(phys_gpu(local))
     clk.start()
     t_wall0 = time.perf_counter()
-    ms = time_cycles(f, y_dev, W, K, stream, flush)
+    per_cycle = []
+    ms = time_cycles(f, y_dev, W, K, stream, flush, per=per_cycle)
     t_wall1 = time.perf_counter()
     clocks = clk.stop()
     if world > 1:
@@ -429,6 +480,7 @@ def bench_ours(args):
         extra["n_2p24_fused_next_weights"] = bench_fused(pf, n24, stream, y, y_dev, None, K24, 3,
                                                          ms24 / K24)
         extra["adaptive_ess"] = bench_adaptive(pf, n, stream, y, y_dev, flush, min(K, 100), W)
+        extra["resample_sweep"] = bench_sweep(pf, synth, stream)
         for other in ("multinomial", "stratified"):  # the other resampling schemes
             if other == args.scheme:
                 continue
@@ -469,6 +521,7 @@ def bench_ours(args):
                   "hbm_frac_of_graph_time": round(cycle_bytes / (ms / K / 1e3) / 1e9 / hbm, 4),
                   "kernels": kernels},
         "e2e": e2e,
+        "cycle_ms": cycle_stats(per_cycle),
         "gpu_launches": launches_per_cycle * K,
         "clocks": clocks,
         "wall_s_timed": round(t_wall1 - t_wall0, 3),
