@@ -473,6 +473,21 @@ def bench_ours(args):
             "kernels": {k: {"ms": round(v, 5), "gbs": round(b24[k] / (v / 1e3) / 1e9, 1)}
                         for k, v in prof24.items()}}
         f24.close()
+        # multinomial resampling at the same size (116 B/particle with the
+        # spacing prefix and its second CDF read), beside the systematic cycle
+        fm24 = pf.Filter(n24, seed=25, scheme="multinomial", precision="fp32", stream=stream)
+        fm24.run(y_dev[:3])
+        fm24.sync()
+        msm24 = time_cycles(fm24, y_dev, 3, K24, stream, None)
+        profm24 = kernel_profile(fm24, y, 3 + K24, 3, None)
+        fm24.close()
+        bm24 = sum(BYTES_PER_PARTICLE["merge_multinomial" if k == "merge" else k] * n24
+                   for k in profm24)
+        extra["n_2p24_multinomial"] = {
+            "value": n24 * K24 / (msm24 / 1e3), "unit": UNIT, "steps": K24,
+            "ms_per_step": msm24 / K24, "l2": "inputs larger than L2 (no flush)",
+            "cycle_hbm_frac": round(bm24 / (msm24 / K24 / 1e3) / 1e9 / hbm, 4),
+            "kernels": {k: round(v, 5) for k, v in profm24.items()}}
         # the series is known ahead: every propagation also computes the next
         # cycle's weights
         extra["fused_next_weights"] = bench_fused(pf, n, stream, y, y_dev, flush, min(K, 100), W,
@@ -481,6 +496,17 @@ def bench_ours(args):
                                                          ms24 / K24)
         extra["adaptive_ess"] = bench_adaptive(pf, n, stream, y, y_dev, flush, min(K, 100), W)
         extra["resample_sweep"] = bench_sweep(pf, synth, stream)
+        # the same workload with binary64 state (the paper's GPU(dp) column);
+        # binary64 runs at a small fraction of the binary32 rate on GB300
+        fd = pf.Filter(n, seed=3, scheme=args.scheme, precision="fp64", stream=stream)
+        fd.run(y_dev[:W])
+        fd.sync()
+        Kd = min(K, 20)
+        msd = time_cycles(fd, y_dev, W, Kd, stream, flush)
+        profd = kernel_profile(fd, y, W + Kd, 3, flush)
+        fd.close()
+        extra["fp64"] = {"value": n * Kd / (msd / 1e3), "unit": UNIT, "steps": Kd,
+                         "ms_per_step": msd / Kd, "kernels": {k: round(v, 5) for k, v in profd.items()}}
         for other in ("multinomial", "stratified"):  # the other resampling schemes
             if other == args.scheme:
                 continue

@@ -255,8 +255,9 @@ const char* pf_last_error(void);
  * max_i w_i = f 2^e, f in [1/2, 1), and write n ancestor indices to anc_dev
  * (nondecreasing).  Draws use (seed, filter_id, t).  Device pointers on
  * `stream` (cudaStream_t, may be NULL); the call borrows them.  Scratch is
- * allocated with cudaMallocAsync on the stream and freed before return of the
- * stream work.  Errors: PF_ERR_INVALID (NULL, n out of range, bad scheme);
+ * allocated on the stream from a stream-ordered memory pool that the library
+ * owns (one per device, created on first use; it keeps up to 256 MiB of freed
+ * scratch for later calls) and freed before the call returns.  Errors: PF_ERR_INVALID (NULL, n out of range, bad scheme);
  * PF_ERR_NUMERIC (a negative / non-finite weight or all zero), detected on
  * the device and reported after a stream synchronisation, which this call
  * performs. */

@@ -1163,6 +1163,38 @@ pf_status finish_and_check(const Scratch& sc, cudaStream_t s) {
   return map_err(h.err);
 }
 
+// Scratch of pf_resample / pf_cdf comes from a library-owned stream-ordered
+// memory pool per device that keeps up to kScratchKeep bytes of freed scratch
+// between calls.  (The device's default pool hands freed memory back at every
+// synchronisation, which these calls perform, so each call would map fresh
+// memory: about 0.2 ms per call.)  Created on first use on each device.
+constexpr uint64_t kScratchKeep = 256ull << 20;
+constexpr int kMaxDevices = 64;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[kMaxDevices] = {};
+
+pf_status scratch_pool(cudaMemPool_t* out) {
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return set_err(PF_ERR_CUDA, "device index %d out of range", dev);
+  std::lock_guard<std::mutex> lock(g_pool_mu);
+  if (!g_pool[dev]) {
+    cudaMemPoolProps props;
+    std::memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t p = nullptr;
+    CK(cudaMemPoolCreate(&p, &props));
+    uint64_t keep = kScratchKeep;
+    CK(cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep));
+    g_pool[dev] = p;
+  }
+  *out = g_pool[dev];
+  return PF_OK;
+}
+
 pf_status resample_common(const float* w, uint64_t n, uint64_t seed, uint32_t filter,
                           uint32_t t, int scheme, uint32_t* anc, uint64_t* Q_out, void* stream) {
   if (!w || (!anc && !Q_out)) return set_err(PF_ERR_INVALID, "NULL pointer");
@@ -1173,10 +1205,13 @@ pf_status resample_common(const float* w, uint64_t n, uint64_t seed, uint32_t fi
   const bool multi = anc && is_multinomial(scheme), cut = anc && is_cutpoint(scheme);
   const size_t bytes = scratch_layout(n, Q_out == nullptr, multi, cut, nullptr, &sc);
   void* base = nullptr;
-  cudaError_t e = cudaMallocAsync(&base, bytes, s);
+  cudaMemPool_t pool = nullptr;
+  pf_status sp = scratch_pool(&pool);
+  if (sp != PF_OK) return sp;
+  cudaError_t e = cudaMallocFromPoolAsync(&base, bytes, pool, s);
   if (e != cudaSuccess) {
     cudaGetLastError();
-    return set_err(PF_ERR_OOM, "cudaMallocAsync(%zu): %s", bytes, cudaGetErrorString(e));
+    return set_err(PF_ERR_OOM, "cudaMallocFromPoolAsync(%zu): %s", bytes, cudaGetErrorString(e));
   }
   scratch_layout(n, Q_out == nullptr, multi, cut, (char*)base, &sc);
   pf_status st = PF_OK;
