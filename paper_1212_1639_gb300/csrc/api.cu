@@ -325,6 +325,7 @@ pf_status enqueue_cycle(pf_filter* f, KTimer* tm = nullptr, const double* y_src 
     mark(tm, "spacing_scan", s);
   }
   PosArgs pa;
+  pa.gate = f->ess ? &f->ctl->resamp : nullptr;
   pa.Q = f->Q;
   pa.S = f->S;
   pa.anc = f->anc;
@@ -1142,6 +1143,7 @@ pf_status run_resample(const float* w, uint64_t n, uint64_t seed, uint32_t filte
     k_spacing_scan<<<ntiles, BLOCK, 0, s>>>(sp);
   }
   PosArgs pa;
+  pa.gate = nullptr;
   pa.Q = sa.Q;
   pa.S = sc.S;
   pa.anc = anc;

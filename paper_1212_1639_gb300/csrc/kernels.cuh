@@ -787,7 +787,12 @@ struct PosArgs {
   uint64_t n;
   uint64_t seed;
   uint32_t filter;
+  // adaptive resampling: when set and *gate == 0 this cycle does not
+  // resample, and the resampling kernels return at once (NULL: always run)
+  const uint32_t* gate;
 };
+
+__device__ __forceinline__ bool gated_off(const PosArgs& a) { return a.gate && *a.gate == 0u; }
 
 template <int POS>
 struct PosKeys {
@@ -855,6 +860,7 @@ __device__ __forceinline__ uint64_t warp_split(const PosKeys<POS>& K, uint64_t d
 template <int POS>
 __global__ void __launch_bounds__(BLOCK) k_partition(PosArgs a, uint64_t* splits,
                                                      uint32_t nsplits, uint32_t tile) {
+  if (gated_off(a)) return;
   const PosKeys<POS> K = make_keys<POS>(a);
   const int lane = threadIdx.x & 31;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -877,6 +883,7 @@ __global__ void __launch_bounds__(BLOCK) k_partition(PosArgs a, uint64_t* splits
 
 template <int POS>
 __global__ void __launch_bounds__(BLOCK) k_merge(PosArgs a, const uint64_t* splits) {
+  if (gated_off(a)) return;
   __shared__ U128 s_key[MERGE_D];
   PosKeys<POS> K;
   K.Q = a.Q;
@@ -1017,6 +1024,7 @@ __device__ __forceinline__ uint64_t strat_first(uint64_t q, uint64_t n, uint64_t
 // first(n Q_i)); the lower end comes from the neighbouring lane.  A warp
 // stores the ranges longer than 32 slots together.
 static __global__ void __launch_bounds__(BLOCK) k_strat(PosArgs a) {
+  if (gated_off(a)) return;
   const uint64_t n = a.n;
   const uint32_t t = a.t_dev ? *a.t_dev : a.t_arg;
   const uint64_t T = a.Q[n - 1];
@@ -1046,6 +1054,7 @@ static __global__ void __launch_bounds__(BLOCK) k_strat(PosArgs a) {
 }
 
 static __global__ void __launch_bounds__(SYS_THREADS) k_merge_sys(PosArgs a, const uint64_t* splits) {
+  if (gated_off(a)) return;
   __shared__ uint32_t s_anc[SYS_D];
   __shared__ uint32_t s_run[SYS_MAX_RUNS][3];
   __shared__ uint32_t s_nruns;
@@ -1152,6 +1161,7 @@ static __global__ void __launch_bounds__(BLOCK) k_cutpoint_search(const uint64_t
 // while KQ_k <= KB_j.
 template <int POS>
 __global__ void __launch_bounds__(BLOCK) k_cutpoint_method(PosArgs a) {
+  if (gated_off(a)) return;
   const uint64_t j = (uint64_t)blockIdx.x * BLOCK + threadIdx.x;
   if (j >= a.n) return;
   const PosKeys<POS> K = make_keys<POS>(a);
