@@ -13,8 +13,8 @@ value  : particle-steps/s over the K timed cycles, device time from CUDA events
 cycle_ms: median and p99 of the timed cycles, and the paper's statistic (the
          mean of the 5 closest to the median of the first 10).
 e2e    : the same metric through the C ABI with host buffers: each step sends
-         one observation from host memory (pf_step) and reads the posterior
-         summaries back (pf_estimate), wall-clock timed.
+         one observation from host memory and reads the posterior summaries
+         back (pf_step_estimate), wall-clock timed.
 roofline: the dominant kernel's algorithmic bytes per launch / its mean
          CUDA-event duration (pf_step_profiled), against the measured copy
          bandwidth in MEASURED_PEAKS.json.
@@ -443,15 +443,15 @@ def bench_ours(args):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        fe.step(float(y[W + i]))
-        est = fe.estimate()
+        est = fe.step_estimate(float(y[W + i]))
         e2e_s += time.perf_counter() - t0
     assert est["t"] == W + Ke
     e2e_s = max_over_ranks(e2e_s, world)
     e2e = {"value": world * n * Ke / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8,
            "d2h_bytes_per_step": 104, "steps": Ke,
-           "note": "pf_step(y from host) + pf_estimate (reduction, 104-byte summary D2H, sync) per step; "
-                   "L2 flushed before each step outside the timer"}
+           "note": "pf_step_estimate per step: y from the host, the cycle, the summary reduction and "
+                   "the 104-byte summary D2H in one graph, synchronised; L2 flushed before each step "
+                   "outside the timer"}
     fe.close()
 
     extra = {}

@@ -187,6 +187,13 @@ pf_status pf_run(pf_filter* f, const double* y, uint32_t n_steps);
  * them to *out (host).  Synchronises the handle's stream. */
 pf_status pf_estimate(pf_filter* f, pf_estimates* out);
 
+/* One cycle for observation y and its posterior summaries in *out (host):
+ * pf_step(f, y) followed by pf_estimate(f, out) with the same results, as
+ * one captured graph (the cycle, the summary reduction and a 104-byte copy
+ * to pinned host memory) and one synchronisation.  For a caller that reads
+ * the filter's result after every observation.  Synchronises. */
+pf_status pf_step_estimate(pf_filter* f, double y, pf_estimates* out);
+
 /* Wait for all enqueued work and check the device error word. */
 pf_status pf_sync(pf_filter* f);
 

@@ -63,9 +63,10 @@ enum CycleForm : int {
   CF_HEAD = 1,   // weights, CDF, resampling, propagation + next weights
   CF_MID = 2,    // CDF, resampling, propagation + next weights
   CF_TAIL = 3,   // CDF, resampling, propagation
-  CF_COUNT = 4
+  CF_EST = 4,    // CF_PLAIN, then the summaries and their copy to the host mirror
+  CF_COUNT = 5
 };
-inline bool form_weighs(int form) { return form == CF_PLAIN || form == CF_HEAD; }
+inline bool form_weighs(int form) { return form == CF_PLAIN || form == CF_HEAD || form == CF_EST; }
 inline bool form_fuses(int form) { return form == CF_HEAD || form == CF_MID; }
 
 // One captured cycle, with the kernel nodes whose observation arguments each
@@ -392,6 +393,12 @@ pf_status enqueue_cycle(pf_filter* f, KTimer* tm = nullptr, const double* y_src 
     }
   }
   mark(tm, fuse ? "propagate_weights_next" : "propagate", s);
+  if (form == CF_EST) {  // the posterior summaries and their 104-byte copy to the pinned mirror
+    const unsigned eg = (unsigned)cdiv(n, (uint64_t)BLOCK * EST_PER_THREAD);
+    if (f->ess) k_estimate_w<R><<<eg, BLOCK, 0, s>>>(a);
+    else k_estimate<R><<<eg, BLOCK, 0, s>>>(a);
+    CK(cudaMemcpyAsync(f->ctl_host, f->ctl, offsetof(Ctl, y), cudaMemcpyDeviceToHost, s));
+  }
   CK(cudaGetLastError());
   return PF_OK;
 }
@@ -476,7 +483,7 @@ pf_status launch_cycle(pf_filter* f, const double* y_src, double y_val, int form
                        const double* ynx_src = nullptr, double ynx_val = 0.0) {
   // the bootstrap filter's weights follow its own blind propagation;
   // adaptive resampling carries weights the fused propagation does not add
-  if (f->bootstrap || f->ess) form = CF_PLAIN;
+  if ((f->bootstrap || f->ess) && form != CF_EST) form = CF_PLAIN;
   CycleGraph& G = f->cg[form];
   if (!G.exec) {
     pf_status st = build_graph(f, form);
@@ -826,6 +833,32 @@ pf_status pf_estimate(pf_filter* f, pf_estimates* out) {
     return set_err(PF_ERR_CUDA, "estimate launch: %s", cudaGetErrorString(e));
   }
   if ((st = sync_and_check(f)) != PF_OK) return st;
+  const double* v = f->ctl_host->est;
+  out->t = (uint64_t)v[0];
+  out->x_mean = v[1];
+  out->x_var = v[2];
+  out->sigma2_mean = v[3];
+  out->sigma2_var = v[4];
+  out->tau2_mean = v[5];
+  out->tau2_var = v[6];
+  out->log_marglik = v[7];
+  return PF_OK;
+}
+
+pf_status pf_step_estimate(pf_filter* f, double y, pf_estimates* out) {
+  pf_status st = check_handle(f);
+  if (st != PF_OK) return st;
+  if (!out) return set_err(PF_ERR_INVALID, "NULL output");
+  if (f->ahead) {  // this cycle's weights are ready: the cycle without them, then the summaries
+    if ((st = pf_step(f, y)) != PF_OK) return st;
+    return pf_estimate(f, out);
+  }
+  if ((st = launch_cycle(f, nullptr, y, CF_EST)) != PF_OK) return f->sticky = st;
+  if (cudaStreamSynchronize(f->stream) != cudaSuccess) {
+    f->sticky = PF_ERR_CUDA;
+    return set_err(PF_ERR_CUDA, "stream: %s", cudaGetErrorString(cudaGetLastError()));
+  }
+  if ((st = map_err(f->ctl_host->err)) != PF_OK) return f->sticky = st;
   const double* v = f->ctl_host->est;
   out->t = (uint64_t)v[0];
   out->x_mean = v[1];

@@ -121,6 +121,7 @@ _SIGS = {
     "pf_step_ahead": [_V, C.c_double, C.c_double],
     "pf_run": [_V, _V, C.c_uint32],
     "pf_estimate": [_V, C.POINTER(PfEstimates)],
+    "pf_step_estimate": [_V, C.c_double, C.POINTER(PfEstimates)],
     "pf_sync": [_V],
     "pf_step_profiled": [_V, C.c_double, C.POINTER(C.c_float), C.POINTER(C.c_char_p), C.c_int,
                          C.POINTER(C.c_int)],
@@ -322,6 +323,12 @@ class Filter:
     def estimate(self):
         e = PfEstimates()
         _check(_lib.pf_estimate(self.h, C.byref(e)), "pf_estimate")
+        return {f: getattr(e, f) for f, _ in PfEstimates._fields_}
+
+    def step_estimate(self, y):
+        """One cycle and its posterior summaries (pf_step_estimate)."""
+        e = PfEstimates()
+        _check(_lib.pf_step_estimate(self.h, float(y), C.byref(e)), "pf_step_estimate")
         return {f: getattr(e, f) for f, _ in PfEstimates._fields_}
 
     def particles(self):
