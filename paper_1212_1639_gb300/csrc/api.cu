@@ -944,8 +944,6 @@ size_t ckpt_bytes(uint64_t n, bool fp64, bool ess) {
 
 }  // namespace
 
-extern "C" {
-
 pf_status pf_checkpoint_size(pf_filter* f, size_t* bytes) {
   if (!f || !bytes) return set_err(PF_ERR_INVALID, "NULL argument");
   *bytes = ckpt_bytes(f->n, f->fp64, f->ess);
@@ -1089,8 +1087,6 @@ pf_status pf_restore(const pf_config* cfg, const void* buf, size_t bytes, pf_fil
   *out = f;
   return PF_OK;
 }
-
-}  // extern "C"
 
 // ---------------------------------------------------------------------------
 // Standalone resampling and the paper's cut-point primitives.
