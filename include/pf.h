@@ -218,7 +218,9 @@ pf_status pf_get_particles(pf_filter* f, void* x, void* sigma2, void* tau2, void
                            void* b_tau);
 
 /* Copy the last cycle's ancestor indices (n uint32, host or device) and,
- * if Q is not NULL, its CDF (n uint64).  Synchronises. */
+ * if Q is not NULL, its CDF (n uint64).  With adaptive resampling, a cycle
+ * that did not resample has the identity as its ancestors (its CDF is still
+ * that of the combined weights).  Synchronises. */
 pf_status pf_get_ancestors(pf_filter* f, uint32_t* anc, uint64_t* Q);
 
 /* Free every device buffer of the handle (after the stream's pending work).
