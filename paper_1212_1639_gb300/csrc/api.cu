@@ -100,6 +100,7 @@ struct pf_filter {
   bool bootstrap = false;   // Algorithm "Particle Filtering" instead of particle learning
   uint32_t nparts = 0;      // log-ML partials per cycle
   uint64_t* cta_tot = nullptr;
+  U128* cta_sq = nullptr;  // adaptive resampling: per-CTA sums of W^2 of the cooperative kernel
   std::vector<void*> allocs;
   void* x[2] = {}; void* s2[2] = {}; void* t2[2] = {}; void* bs[2] = {}; void* bt[2] = {};
   void* ell = nullptr;
@@ -307,7 +308,7 @@ pf_status enqueue_cycle(pf_filter* f, KTimer* tm = nullptr, const double* y_src 
     k_scan<FROM_LOGLIK, R><<<f->ntiles, BLOCK, 0, s>>>(sa);
     mark(tm, "scan", s);
   }
-  if (f->ess) {  // adaptive resampling: the decision from the finished CDF
+  if (f->ess && !f->cdf_grid) {  // adaptive resampling: the decision from the finished CDF
     k_ess<R><<<f->ess_grid, BLOCK, 0, s>>>(a);
     mark(tm, "ess", s);
   }
@@ -349,13 +350,18 @@ pf_status enqueue_cycle(pf_filter* f, KTimer* tm = nullptr, const double* y_src 
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+    U128* const sq = f->cta_sq;
     if (f->cdf_staged) {
-      CK(cudaLaunchKernelEx(&cfg, k_cdf_sys<R, true, 16>, a, f->cta_tot));
+      if (f->ess) CK(cudaLaunchKernelEx(&cfg, k_cdf_sys<R, true, 16, true>, a, f->cta_tot, sq));
+      else CK(cudaLaunchKernelEx(&cfg, k_cdf_sys<R, true, 16>, a, f->cta_tot, sq));
     } else if (f->cdf_per == 8) {
-      if constexpr (sizeof(R) == 4)
-        CK(cudaLaunchKernelEx(&cfg, k_cdf_sys<float, false, 8>, a, f->cta_tot));
+      if constexpr (sizeof(R) == 4) {
+        if (f->ess) CK(cudaLaunchKernelEx(&cfg, k_cdf_sys<float, false, 8, true>, a, f->cta_tot, sq));
+        else CK(cudaLaunchKernelEx(&cfg, k_cdf_sys<float, false, 8>, a, f->cta_tot, sq));
+      }
     } else {
-      CK(cudaLaunchKernelEx(&cfg, k_cdf_sys<R, false, 16>, a, f->cta_tot));
+      if (f->ess) CK(cudaLaunchKernelEx(&cfg, k_cdf_sys<R, false, 16, true>, a, f->cta_tot, sq));
+      else CK(cudaLaunchKernelEx(&cfg, k_cdf_sys<R, false, 16>, a, f->cta_tot, sq));
     }
     mark(tm, "cdf_resample", s);
   } else {
@@ -401,6 +407,20 @@ pf_status enqueue_cycle(pf_filter* f, KTimer* tm = nullptr, const double* y_src 
   }
   CK(cudaGetLastError());
   return PF_OK;
+}
+
+// The cooperative CDF + systematic resampling kernel of a configuration.
+const void* cdf_fn(bool fp64, bool staged, int per, bool ess) {
+  if (per == 8)
+    return ess ? (const void*)k_cdf_sys<float, false, 8, true> : (const void*)k_cdf_sys<float, false, 8>;
+  if (fp64) {
+    if (staged)
+      return ess ? (const void*)k_cdf_sys<double, true, 16, true> : (const void*)k_cdf_sys<double, true, 16>;
+    return ess ? (const void*)k_cdf_sys<double, false, 16, true> : (const void*)k_cdf_sys<double, false, 16>;
+  }
+  if (staged)
+    return ess ? (const void*)k_cdf_sys<float, true, 16, true> : (const void*)k_cdf_sys<float, true, 16>;
+  return ess ? (const void*)k_cdf_sys<float, false, 16, true> : (const void*)k_cdf_sys<float, false, 16>;
 }
 
 const void* prop_fuse_fn(const pf_filter* f) {
@@ -673,7 +693,7 @@ pf_status pf_create(const pf_config* cfg, pf_filter** out) {
     if (e != cudaSuccess || per_sm_f < 1) return bail(set_err(PF_ERR_CUDA, "occupancy query failed"));
     const uint64_t cap_f = (uint64_t)per_sm_f * (uint64_t)sms;
     f->prop_grid_fuse = (unsigned)(want < cap_f ? want : cap_f);
-    if (f->scheme == PF_SYSTEMATIC && !f->ess) {
+    if (f->scheme == PF_SYSTEMATIC) {
       // cooperative grid: every CTA resident at once (it waits on the others).
       // One tile per CTA when the tiles fit at once -- in binary32 2048-particle
       // tiles (8 per thread) if those fit, for twice the parallelism -- else
@@ -681,7 +701,7 @@ pf_status pf_create(const pf_config* cfg, pf_filter** out) {
       int cdf_sm = 0;
       uint64_t g = 0;
       if (!f->fp64) {
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cdf_sm, k_cdf_sys<float, false, 8>, BLOCK, 0);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cdf_sm, cdf_fn(false, false, 8, f->ess), BLOCK, 0);
         if (e != cudaSuccess || cdf_sm < 1) return bail(set_err(PF_ERR_CUDA, "occupancy query failed"));
         g = (uint64_t)cdf_sm * (uint64_t)sms;
         if (cdiv(n, 8ull * BLOCK) <= g) {
@@ -690,14 +710,12 @@ pf_status pf_create(const pf_config* cfg, pf_filter** out) {
         }
       }
       if (f->cdf_per == 16) {
-        e = f->fp64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cdf_sm, k_cdf_sys<double, false, 16>, BLOCK, 0)
-                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cdf_sm, k_cdf_sys<float, false, 16>, BLOCK, 0);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cdf_sm, cdf_fn(f->fp64, false, 16, f->ess), BLOCK, 0);
         if (e != cudaSuccess || cdf_sm < 1) return bail(set_err(PF_ERR_CUDA, "occupancy query failed"));
         g = (uint64_t)cdf_sm * (uint64_t)sms;
         if (f->ntiles > g) {
           f->cdf_staged = true;
-          e = f->fp64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cdf_sm, k_cdf_sys<double, true, 16>, BLOCK, 0)
-                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cdf_sm, k_cdf_sys<float, true, 16>, BLOCK, 0);
+          e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cdf_sm, cdf_fn(f->fp64, true, 16, f->ess), BLOCK, 0);
           if (e != cudaSuccess || cdf_sm < 1) return bail(set_err(PF_ERR_CUDA, "occupancy query failed"));
           g = (uint64_t)cdf_sm * (uint64_t)sms;
         }
@@ -705,6 +723,8 @@ pf_status pf_create(const pf_config* cfg, pf_filter** out) {
       const uint64_t nt = f->cdf_per == 8 ? f->nparts : f->ntiles;
       f->cdf_grid = (unsigned)(nt < g ? nt : g);
       if ((st = dev_alloc(f, (size_t)f->cdf_grid * 8, (void**)&f->cta_tot)) != PF_OK) return bail(st);
+      if (f->ess && (st = dev_alloc(f, (size_t)f->cdf_grid * sizeof(U128), (void**)&f->cta_sq)) != PF_OK)
+        return bail(st);
     }
   }
   if ((st = build_graph(f, CF_PLAIN)) != PF_OK) return bail(st);

@@ -1293,6 +1293,25 @@ static __device__ __noinline__ void sys_past_window(uint32_t j, uint32_t c, uint
   for (uint32_t q = st; q < j + c; ++q) anc[q] = i;
 }
 
+// Correctly rounded conversion of a 128-bit integer to binary64: the top 64
+// significant bits with a sticky bit for the rest, rounded once, scaled by an
+// exact power of two.
+__device__ __forceinline__ double u128_to_f64_rn(U128 v) {
+  if (v.hi == 0) return __ull2double_rn(v.lo);
+  const int lz = __clzll(v.hi);
+  const int sh = 64 - lz;  // 1..64
+  uint64_t top, rest;
+  if (lz == 0) {
+    top = v.hi;
+    rest = v.lo;
+  } else {
+    top = (v.hi << lz) | (v.lo >> sh);
+    rest = v.lo << lz;
+  }
+  const double d = __ull2double_rn(top | (rest != 0 ? 1ull : 0ull));
+  return d * __longlong_as_double((long long)(1023 + sh) << 52);
+}
+
 // ---------------------------------------------------------------------------
 // The CDF and systematic resampling in one cooperative launch (Steps 1b-1c
 // of the cycle for the systematic scheme).  Every CTA owns a contiguous range
@@ -1320,8 +1339,14 @@ static __device__ __noinline__ void sys_past_window(uint32_t j, uint32_t c, uint
 // needs no exponentials; the CDF goes out through shared-memory rows,
 // coalesced.  Otherwise (one tile per CTA) l is read directly and the first
 // tile's W stay in shared memory between the phases.
-template <class R, bool STAGED, int PER>
-__global__ void __launch_bounds__(BLOCK, PER == 8 ? 4 : 3) k_cdf_sys(FilterArgs<R> a, uint64_t* cta_tot) {
+//
+// With ESS (adaptive resampling) phase 1 also sums W^2 exactly per CTA
+// (cta_sq); after the grid barrier every CTA takes k_ess's decision from the
+// totals, CTA 0 publishes it, and a cycle that does not resample writes the
+// CDF and the log-ML partials but no ancestors.
+template <class R, bool STAGED, int PER, bool ESS = false>
+__global__ void __launch_bounds__(BLOCK, PER == 8 ? 4 : 3) k_cdf_sys(FilterArgs<R> a, uint64_t* cta_tot,
+                                                                    U128* cta_sq) {
   static_assert(PER == 16 || (PER == 8 && !STAGED && sizeof(R) == 4), "tile shapes");
   constexpr int TP = BLOCK * PER;  // particles per tile
   // ancestor window entry of the tile's slot S0 + x: x + 2 (x >> LOGP) with
@@ -1344,6 +1369,7 @@ __global__ void __launch_bounds__(BLOCK, PER == 8 ? 4 : 3) k_cdf_sys(FilterArgs<
   __shared__ uint32_t s_wmax[WARPS];
   __shared__ alignas(8) uint64_t s_bar[2];
   __shared__ uint32_t s_S[2];  // the tile's first slot and the slot after its last
+  __shared__ U128 s_sq[ESS ? WARPS : 1];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   Ctl* c = a.ctl;
   const uint64_t n = a.n;
@@ -1468,24 +1494,53 @@ __global__ void __launch_bounds__(BLOCK, PER == 8 ? 4 : 3) k_cdf_sys(FilterArgs<
     return tot;
   };
 
-  // phase 1: this CTA's sum of W
+  // block sum of one 128-bit value per thread, returned to every thread
+  auto block_sum128 = [&](U128 v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      U128 u;
+      u.hi = __shfl_xor_sync(0xffffffffu, v.hi, o);
+      u.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
+      v = add128(v, u);
+    }
+    if (lane == 0) s_sq[warp] = v;
+    __syncthreads();
+    U128 tot{0, 0};
+    for (int w = 0; w < WARPS; ++w) tot = add128(tot, s_sq[w]);
+    __syncthreads();
+    return tot;
+  };
+
+  // phase 1: this CTA's sum of W (and with ESS of W^2)
   uint64_t mine = 0;
+  U128 sq{0, 0};
   if (tb < te) next_issue(tb);
   for (uint32_t tile = tb; tile < te; ++tile) {
     if (tile + 1 < te) next_issue(tile + 1);
     const R* buf = take_tile(tile);
     uint64_t W[PER];
     R ep;
-    quantP(tile, buf, W, &ep, STAGED ? 1 : 0);
-    if (STAGED) fence_proxy_async_smem();  // e in buf, for the bulk store below
+    // (with ESS l stays in place: a propagation that does not resample
+    // carries L - m from it, so phase 2 quantises from l again)
+    quantP(tile, buf, W, &ep, (STAGED && !ESS) ? 1 : 0);
+    if (STAGED && !ESS) fence_proxy_async_smem();  // e in buf, for the bulk store below
     mine += W[PER - 1];
+    if constexpr (ESS) {
+      uint64_t prev = 0;
+#pragma unroll
+      for (int e = 0; e < PER; ++e) {
+        const uint64_t w = W[e] - prev;
+        prev = W[e];
+        sq = add128(sq, mul64(w, w));
+      }
+    }
     if (tile == tb) {
 #pragma unroll
       for (int e = 0; e < PER; ++e) s_keep[threadIdx.x * (PER + 1) + e] = W[e];
       s_keep_ep[threadIdx.x] = ep;
     }
     __syncthreads();  // buf is refilled two copies later
-    if (STAGED && tile != tb && threadIdx.x == 0) {
+    if (STAGED && !ESS && tile != tb && threadIdx.x == 0) {
       // e goes back to l's place in global memory for phase 2, which then
       // needs no exponentials (the first tile's W stay in shared memory)
       const uint64_t first = (uint64_t)tile * TP;
@@ -1494,8 +1549,13 @@ __global__ void __launch_bounds__(BLOCK, PER == 8 ? 4 : 3) k_cdf_sys(FilterArgs<
     }
   }
   mine = block_sum(mine);
+  if constexpr (ESS) sq = block_sum128(sq);
   if (threadIdx.x == 0) {
     st_status(&cta_tot[blockIdx.x], mine);
+    if constexpr (ESS) {
+      st_status(&cta_sq[blockIdx.x].hi, sq.hi);
+      st_status(&cta_sq[blockIdx.x].lo, sq.lo);
+    }
     __threadfence();
     atomicAdd(&c->gbar, 1u);
     if (STAGED && tb + 1 < te) {  // phase 2's first tile from HBM: e stored, complete
@@ -1524,6 +1584,25 @@ __global__ void __launch_bounds__(BLOCK, PER == 8 ? 4 : 3) k_cdf_sys(FilterArgs<
   }
   pre = block_sum(pre);
   const uint64_t T = block_sum(all);
+  // adaptive resampling: the decision of k_ess, from the same exact sums
+  bool rs = true;
+  if constexpr (ESS) {
+    U128 B{0, 0};
+    for (uint32_t b = threadIdx.x; b < gridDim.x; b += BLOCK) {
+      U128 v;
+      v.hi = ld_status(&cta_sq[b].hi);
+      v.lo = ld_status(&cta_sq[b].lo);
+      B = add128(B, v);
+    }
+    B = block_sum128(B);
+    const double A = __ull2double_rn(T);
+    const double Bd = u128_to_f64_rn(B);
+    const double lhs = A * A;
+    const double f = a.ess_frac * (double)n;
+    const double rhs = f * Bd;
+    rs = lhs < rhs;
+    if (blockIdx.x == 0 && threadIdx.x == 0) c->resamp = rs ? 1u : 0u;
+  }
   const U4 wr = draw(a.seed, a.filter, t, 0, P_SYS_OFFSET, 0);
   const uint64_t r = __umul64hi(((uint64_t)wr.b << 32) | wr.a, T);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -1546,7 +1625,7 @@ __global__ void __launch_bounds__(BLOCK, PER == 8 ? 4 : 3) k_cdf_sys(FilterArgs<
     } else {
       if (tile + 1 < te) next_issue(tile + 1);
       const R* buf = take_tile(tile);
-      quantP(tile, buf, W, &ep, 2);
+      quantP(tile, buf, W, &ep, ESS ? 0 : 2);
     }
     // the tile's first slot S0 = R(carry)
     if (threadIdx.x == 0) s_S[0] = (uint32_t)sys_first_slot(carry, n, r, dv);
@@ -1619,7 +1698,7 @@ __global__ void __launch_bounds__(BLOCK, PER == 8 ? 4 : 3) k_cdf_sys(FilterArgs<
     // above 2 (a heavy particle, divided out).  Slots past the window (rare)
     // are stored directly, in runs of the CTA when long.  A rolled loop over
     // the row: the step's code stays small.
-    if (T > 0 && base < n) {
+    if (rs && T > 0 && base < n) {
       const uint32_t ecount = base + PER <= n ? (uint32_t)PER : (uint32_t)(n - base);
       uint32_t j = threadIdx.x == 0 ? S0 : (base == 0 ? 0u : (uint32_t)sys_first_slot(o, n, r, dv));
       const U128 X = mul64x32(o, (uint32_t)n);
@@ -1650,7 +1729,7 @@ __global__ void __launch_bounds__(BLOCK, PER == 8 ? 4 : 3) k_cdf_sys(FilterArgs<
     // fill forward: slot x takes the last mark at or before it (slot S0 is
     // always marked).  Warp w covers a contiguous part of the window: its
     // maximum mark first, then a running maximum with the earlier parts'.
-    const uint32_t wcnt = T > 0 ? (s_S[1] - S0 < WIN_SLOTS ? s_S[1] - S0 : WIN_SLOTS) : 0u;
+    const uint32_t wcnt = (rs && T > 0) ? (s_S[1] - S0 < WIN_SLOTS ? s_S[1] - S0 : WIN_SLOTS) : 0u;
     const uint32_t cw = (wcnt + WARPS * 32 - 1) / (WARPS * 32) * 32;
     const uint32_t x0 = warp * cw < wcnt ? warp * cw : wcnt;
     const uint32_t x1 = x0 + cw < wcnt ? x0 + cw : wcnt;
@@ -1733,25 +1812,6 @@ __device__ __forceinline__ double esum_value(const ESum64& e) { return e.s; }
 // each rounded to nearest once.  The last block writes the decision.
 // ---------------------------------------------------------------------------
 constexpr int ESS_PER_THREAD = 8;
-
-// Correctly rounded conversion of a 128-bit integer to binary64: the top 64
-// significant bits with a sticky bit for the rest, rounded once, scaled by an
-// exact power of two.
-__device__ __forceinline__ double u128_to_f64_rn(U128 v) {
-  if (v.hi == 0) return __ull2double_rn(v.lo);
-  const int lz = __clzll(v.hi);
-  const int sh = 64 - lz;  // 1..64
-  uint64_t top, rest;
-  if (lz == 0) {
-    top = v.hi;
-    rest = v.lo;
-  } else {
-    top = (v.hi << lz) | (v.lo >> sh);
-    rest = v.lo << lz;
-  }
-  const double d = __ull2double_rn(top | (rest != 0 ? 1ull : 0ull));
-  return d * __longlong_as_double((long long)(1023 + sh) << 52);
-}
 
 template <class R>
 __global__ void __launch_bounds__(BLOCK) k_ess(FilterArgs<R> a) {
