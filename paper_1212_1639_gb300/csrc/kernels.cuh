@@ -2289,119 +2289,142 @@ __global__ void __launch_bounds__(BLOCK, 3) k_propagate2(FilterArgs<float> a) {
   auto weigh_late = [&](const Item& itm) {  // FUSE: the slot's state is final
     weigh_next<float>(a.ell, itm.j, dst.x[itm.j], dst.s2[itm.j], dst.t2[itm.j], yn, mxn, badn);
   };
-  uint64_t j0 = (uint64_t)blockIdx.x * BLOCK + threadIdx.x;
+  // Pass p covers slots [p S, p S + S) (S = stride): thread g takes p S + g
+  // and p S + g + h with h = G, except in a partial last pass, where
+  // h = ceil(rest / 2) packs the rest into full pairs and the threads with
+  // g >= h (whole warps) skip it.
+  const uint64_t g = (uint64_t)blockIdx.x * BLOCK + threadIdx.x;
+  auto pair_of = [&](uint64_t b, uint64_t* j0, uint64_t* j1) {  // b: the pass's first slot
+    if (b + stride <= n) {  // a full pass (the same for every thread)
+      *j0 = b + g;
+      *j1 = b + g + half;
+      return;
+    }
+    const uint64_t rest = n > b ? n - b : 0ull;
+    const uint64_t h = (rest + 1) / 2;
+    *j0 = g < h ? b + g : n;  // n: no slot
+    *j1 = g < h ? b + g + h : n;
+  };
+  uint64_t pb = 0;  // the current pass's first slot
+  uint64_t j0, j1;
+  pair_of(0, &j0, &j1);
   Gathered<float> c0 = gather_rec<float>(src, j0 < n ? ancx(j0) : 0u);
-  Gathered<float> c1 = gather_rec<float>(src, j0 + half < n ? ancx(j0 + half) : 0u);
-  for (uint64_t it = 0; it < iters; ++it, j0 += stride) {
-    const uint64_t j1 = j0 + half;
+  Gathered<float> c1 = gather_rec<float>(src, j1 < n ? ancx(j1) : 0u);
+  for (uint64_t it = 0; it < iters; ++it, pb += stride) {
     const bool v0 = j0 < n, v1 = j1 < n;
     // the next pass's records, gathered ahead
-    const uint64_t k0 = j0 + stride, k1 = j1 + stride;
+    uint64_t k0, k1;
+    pair_of(pb + stride, &k0, &k1);
     const Gathered<float> n0 = gather_rec<float>(src, k0 < n ? ancx(k0) : 0u);
     const Gathered<float> n1 = gather_rec<float>(src, k1 < n ? ancx(k1) : 0u);
-    const float2 xa = make_float2(c0.x, c1.x), sa = make_float2(c0.s2, c1.s2);
-    const float2 ta = make_float2(c0.t2, c1.t2);
-    const float2 sm = add2(sa, ta);
-    const float2 p = mul2(sa, ta);
-    const float2 V = make_float2(p.x / sm.x, p.y / sm.y);
-    const float2 m1 = mul2(xa, sa);
-    const float2 m2 = mul2(splat2(yr), ta);
-    const float2 nn = add2(m1, m2);
-    const float2 mu = make_float2(nn.x / sm.x, nn.y / sm.y);
-    const float2 sv = make_float2(sqrtf(V.x), sqrtf(V.y));
-    float2 Z, Zs, Us, Zt, Ut;
-    theta_draws2(a.rk, a.filter, t, (uint32_t)j0, (uint32_t)j1, &Z, &Zs, &Us, &Zt, &Ut);
-    const float2 xz = mul2(sv, Z);
-    const float2 xj = add2(mu, xz);
-    if (v0) dst.x[j0] = xj.x;
-    if (v1) dst.x[j1] = xj.y;
-    bool ds0 = false, dt0 = false, ds1 = false, dt1 = false;
-    uint64_t bs0 = 0, bt0 = 0, bs1 = 0, bt1 = 0;
-    if (LEARN) {
-      const float2 rs = sub2(splat2(yr), xj);
-      const float2 rt = sub2(xj, xa);
-      // b + (r^2 / 2) in 2^-32 fixed point, per SuffOps<float>::add_half_square
-      const float2 hs = mul2(splat2(0.5f), mul2(rs, rs));
-      const float2 ht = mul2(splat2(0.5f), mul2(rt, rt));
-      const float2 ws = mul2(hs, splat2(0x1p32f));
-      const float2 wt = mul2(ht, splat2(0x1p32f));
-      bool f0 = false, f1 = false;
-      auto addb = [&](uint64_t b, float v, bool* f) -> uint64_t {
-        if (!(v < 0x1p63f)) {
-          *f = true;
-          return b;
+    // a warp with no slot left in a partial last pass skips it
+    if (__any_sync(0xffffffffu, v0)) {
+      const float2 xa = make_float2(c0.x, c1.x), sa = make_float2(c0.s2, c1.s2);
+      const float2 ta = make_float2(c0.t2, c1.t2);
+      const float2 sm = add2(sa, ta);
+      const float2 p = mul2(sa, ta);
+      const float2 V = make_float2(p.x / sm.x, p.y / sm.y);
+      const float2 m1 = mul2(xa, sa);
+      const float2 m2 = mul2(splat2(yr), ta);
+      const float2 nn = add2(m1, m2);
+      const float2 mu = make_float2(nn.x / sm.x, nn.y / sm.y);
+      const float2 sv = make_float2(sqrtf(V.x), sqrtf(V.y));
+      float2 Z, Zs, Us, Zt, Ut;
+      theta_draws2(a.rk, a.filter, t, (uint32_t)j0, (uint32_t)j1, &Z, &Zs, &Us, &Zt, &Ut);
+      const float2 xz = mul2(sv, Z);
+      const float2 xj = add2(mu, xz);
+      if (v0) dst.x[j0] = xj.x;
+      if (v1) dst.x[j1] = xj.y;
+      bool ds0 = false, dt0 = false, ds1 = false, dt1 = false;
+      uint64_t bs0 = 0, bt0 = 0, bs1 = 0, bt1 = 0;
+      if (LEARN) {
+        const float2 rs = sub2(splat2(yr), xj);
+        const float2 rt = sub2(xj, xa);
+        // b + (r^2 / 2) in 2^-32 fixed point, per SuffOps<float>::add_half_square
+        const float2 hs = mul2(splat2(0.5f), mul2(rs, rs));
+        const float2 ht = mul2(splat2(0.5f), mul2(rt, rt));
+        const float2 ws = mul2(hs, splat2(0x1p32f));
+        const float2 wt = mul2(ht, splat2(0x1p32f));
+        bool f0 = false, f1 = false;
+        auto addb = [&](uint64_t b, float v, bool* f) -> uint64_t {
+          if (!(v < 0x1p63f)) {
+            *f = true;
+            return b;
+          }
+          return b + f2u64_rz(v);
+        };
+        bs0 = addb(c0.bs, ws.x, &f0);
+        bt0 = addb(c0.bt, wt.x, &f0);
+        bs1 = addb(c1.bs, ws.y, &f1);
+        bt1 = addb(c1.bt, wt.y, &f1);
+        fail |= (v0 && f0) || (v1 && f1);
+        if (v0) { dst.bs[j0] = bs0; dst.bt[j0] = bt0; }
+        if (v1) { dst.bs[j1] = bs1; dst.bt[j1] = bt1; }
+        // Marsaglia-Tsang squeeze for sigma^2 (x lanes: slot j0, j1) and tau^2
+        const float2 czs = mul2(splat2(cs), Zs), czt = mul2(splat2(ct), Zt);
+        const float2 vs = add2(splat2(1.0f), czs), vt = add2(splat2(1.0f), czt);
+        const float2 v3s = mul2(mul2(vs, vs), vs), v3t = mul2(mul2(vt, vt), vt);
+        const float2 Z2s = mul2(Zs, Zs), Z2t = mul2(Zt, Zt);
+        const float2 thrs = sub2(splat2(1.0f), mul2(splat2(Cst<float>::SQUEEZE), mul2(Z2s, Z2s)));
+        const float2 thrt = sub2(splat2(1.0f), mul2(splat2(Cst<float>::SQUEEZE), mul2(Z2t, Z2t)));
+        const float2 Gs = mul2(splat2(ds), v3s), Gt = mul2(splat2(dt), v3t);
+        const bool as0 = vs.x > 0.0f && Us.x < thrs.x, as1 = vs.y > 0.0f && Us.y < thrs.y;
+        const bool at0 = vt.x > 0.0f && Ut.x < thrt.x, at1 = vt.y > 0.0f && Ut.y < thrt.y;
+        // inverse gamma: (b 2^-32) / G, per SuffOps<float>::ig
+        const float2 bsf = mul2(make_float2(u64_to_f32_rn(bs0), u64_to_f32_rn(bs1)), splat2(0x1p-32f));
+        const float2 btf = mul2(make_float2(u64_to_f32_rn(bt0), u64_to_f32_rn(bt1)), splat2(0x1p-32f));
+        // 1 for a deferred draw: the paired weight of that slot is discarded,
+        // and a normal operand keeps the log and the division on their fast paths
+        float s20 = 1.0f, t20 = 1.0f, s21 = 1.0f, t21 = 1.0f;
+        if (v0) {
+          if (as0) dst.s2[j0] = s20 = bsf.x / Gs.x;
+          else ds0 = true;
+          if (at0) dst.t2[j0] = t20 = btf.x / Gt.x;
+          else dt0 = true;
         }
-        return b + f2u64_rz(v);
-      };
-      bs0 = addb(c0.bs, ws.x, &f0);
-      bt0 = addb(c0.bt, wt.x, &f0);
-      bs1 = addb(c1.bs, ws.y, &f1);
-      bt1 = addb(c1.bt, wt.y, &f1);
-      fail |= (v0 && f0) || (v1 && f1);
-      if (v0) { dst.bs[j0] = bs0; dst.bt[j0] = bt0; }
-      if (v1) { dst.bs[j1] = bs1; dst.bt[j1] = bt1; }
-      // Marsaglia-Tsang squeeze for sigma^2 (x lanes: slot j0, j1) and tau^2
-      const float2 czs = mul2(splat2(cs), Zs), czt = mul2(splat2(ct), Zt);
-      const float2 vs = add2(splat2(1.0f), czs), vt = add2(splat2(1.0f), czt);
-      const float2 v3s = mul2(mul2(vs, vs), vs), v3t = mul2(mul2(vt, vt), vt);
-      const float2 Z2s = mul2(Zs, Zs), Z2t = mul2(Zt, Zt);
-      const float2 thrs = sub2(splat2(1.0f), mul2(splat2(Cst<float>::SQUEEZE), mul2(Z2s, Z2s)));
-      const float2 thrt = sub2(splat2(1.0f), mul2(splat2(Cst<float>::SQUEEZE), mul2(Z2t, Z2t)));
-      const float2 Gs = mul2(splat2(ds), v3s), Gt = mul2(splat2(dt), v3t);
-      const bool as0 = vs.x > 0.0f && Us.x < thrs.x, as1 = vs.y > 0.0f && Us.y < thrs.y;
-      const bool at0 = vt.x > 0.0f && Ut.x < thrt.x, at1 = vt.y > 0.0f && Ut.y < thrt.y;
-      // inverse gamma: (b 2^-32) / G, per SuffOps<float>::ig
-      const float2 bsf = mul2(make_float2(u64_to_f32_rn(bs0), u64_to_f32_rn(bs1)), splat2(0x1p-32f));
-      const float2 btf = mul2(make_float2(u64_to_f32_rn(bt0), u64_to_f32_rn(bt1)), splat2(0x1p-32f));
-      // 1 for a deferred draw: the paired weight of that slot is discarded,
-      // and a normal operand keeps the log and the division on their fast paths
-      float s20 = 1.0f, t20 = 1.0f, s21 = 1.0f, t21 = 1.0f;
-      if (v0) {
-        if (as0) dst.s2[j0] = s20 = bsf.x / Gs.x;
-        else ds0 = true;
-        if (at0) dst.t2[j0] = t20 = btf.x / Gt.x;
-        else dt0 = true;
-      }
-      if (v1) {
-        if (as1) dst.s2[j1] = s21 = bsf.y / Gs.y;
-        else ds1 = true;
-        if (at1) dst.t2[j1] = t21 = btf.y / Gt.y;
-        else dt1 = true;
-      }
-      if constexpr (FUSE) {
-        // both slots weighed paired; a slot with a deferred draw is weighed
-        // by the drain round that finishes it (its sigma^2 item lies below
-        // its tau^2 item, so it weighs when both were deferred)
-        const float2 l = log_pred2(xj, make_float2(s20, s21), make_float2(t20, t21), yn);
-        if (v0 && !ds0 && !dt0) keep_next(a.ell, j0, l.x, mxn, badn);
-        if (v1 && !ds1 && !dt1) keep_next(a.ell, j1, l.y, mxn, badn);
-        wq_push(wq, qn, ds0, Item{bs0, Zs.x, Us.x, (uint32_t)j0, 2u}, lane);
-        wq_push(wq, qn, dt0, Item{bt0, Zt.x, Ut.x, (uint32_t)j0, ds0 ? 1u : 3u}, lane);
-        wq_push(wq, qn, ds1, Item{bs1, Zs.y, Us.y, (uint32_t)j1, 2u}, lane);
-        wq_push(wq, qn, dt1, Item{bt1, Zt.y, Ut.y, (uint32_t)j1, ds1 ? 1u : 3u}, lane);
-        wq_drain_post(wq, qn, 32u, lane, finish, weigh_late);
+        if (v1) {
+          if (as1) dst.s2[j1] = s21 = bsf.y / Gs.y;
+          else ds1 = true;
+          if (at1) dst.t2[j1] = t21 = btf.y / Gt.y;
+          else dt1 = true;
+        }
+        if constexpr (FUSE) {
+          // both slots weighed paired; a slot with a deferred draw is weighed
+          // by the drain round that finishes it (its sigma^2 item lies below
+          // its tau^2 item, so it weighs when both were deferred)
+          const float2 l = log_pred2(xj, make_float2(s20, s21), make_float2(t20, t21), yn);
+          if (v0 && !ds0 && !dt0) keep_next(a.ell, j0, l.x, mxn, badn);
+          if (v1 && !ds1 && !dt1) keep_next(a.ell, j1, l.y, mxn, badn);
+          wq_push(wq, qn, ds0, Item{bs0, Zs.x, Us.x, (uint32_t)j0, 2u}, lane);
+          wq_push(wq, qn, dt0, Item{bt0, Zt.x, Ut.x, (uint32_t)j0, ds0 ? 1u : 3u}, lane);
+          wq_push(wq, qn, ds1, Item{bs1, Zs.y, Us.y, (uint32_t)j1, 2u}, lane);
+          wq_push(wq, qn, dt1, Item{bt1, Zt.y, Ut.y, (uint32_t)j1, ds1 ? 1u : 3u}, lane);
+          wq_drain_post(wq, qn, 32u, lane, finish, weigh_late);
+        } else {
+          wq_push(wq, qn, ds0, Item{bs0, Zs.x, Us.x, (uint32_t)j0, 0u}, lane);
+          wq_push(wq, qn, dt0, Item{bt0, Zt.x, Ut.x, (uint32_t)j0, 1u}, lane);
+          wq_push(wq, qn, ds1, Item{bs1, Zs.y, Us.y, (uint32_t)j1, 0u}, lane);
+          wq_push(wq, qn, dt1, Item{bt1, Zt.y, Ut.y, (uint32_t)j1, 1u}, lane);
+          wq_drain(wq, qn, 32u, lane, finish);
+        }
       } else {
-        wq_push(wq, qn, ds0, Item{bs0, Zs.x, Us.x, (uint32_t)j0, 0u}, lane);
-        wq_push(wq, qn, dt0, Item{bt0, Zt.x, Ut.x, (uint32_t)j0, 1u}, lane);
-        wq_push(wq, qn, ds1, Item{bs1, Zs.y, Us.y, (uint32_t)j1, 0u}, lane);
-        wq_push(wq, qn, dt1, Item{bt1, Zt.y, Ut.y, (uint32_t)j1, 1u}, lane);
-        wq_drain(wq, qn, 32u, lane, finish);
+        if (v0) { dst.s2[j0] = sa.x; dst.t2[j0] = ta.x; dst.bs[j0] = c0.bs; dst.bt[j0] = c0.bt; }
+        if (v1) { dst.s2[j1] = sa.y; dst.t2[j1] = ta.y; dst.bs[j1] = c1.bs; dst.bt[j1] = c1.bt; }
+        if constexpr (FUSE) {
+          const float2 l = log_pred2(xj, sa, ta, yn);
+          if (v0) keep_next(a.ell, j0, l.x, mxn, badn);
+          if (v1) keep_next(a.ell, j1, l.y, mxn, badn);
+        }
       }
-    } else {
-      if (v0) { dst.s2[j0] = sa.x; dst.t2[j0] = ta.x; dst.bs[j0] = c0.bs; dst.bt[j0] = c0.bt; }
-      if (v1) { dst.s2[j1] = sa.y; dst.t2[j1] = ta.y; dst.bs[j1] = c1.bs; dst.bt[j1] = c1.bt; }
-      if constexpr (FUSE) {
-        const float2 l = log_pred2(xj, sa, ta, yn);
-        if (v0) keep_next(a.ell, j0, l.x, mxn, badn);
-        if (v1) keep_next(a.ell, j1, l.y, mxn, badn);
+      if constexpr (ESS) {
+        if (v0) carry(j0);
+        if (v1) carry(j1);
       }
-    }
-    if constexpr (ESS) {
-      if (v0) carry(j0);
-      if (v1) carry(j1);
     }
     c0 = n0;
     c1 = n1;
+    j0 = k0;
+    j1 = k1;
   }
   if constexpr (LEARN && FUSE) wq_drain_post(wq, qn, 1u, lane, finish, weigh_late);
   else if (LEARN) wq_drain(wq, qn, 1u, lane, finish);
