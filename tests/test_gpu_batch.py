@@ -229,3 +229,32 @@ def test_batch_launch_shapes_change_no_result(pf, scheme):
             _same_particles(_raw(b.particles(i), 0), _raw(ref.particles(i), 0))
         b.close()
     ref.close()
+
+
+def test_batch_at_full_size_matches_oracle_on_sampled_filters(pf, orc):
+    """The benchmark's batch: 4096 filters, N log-uniform in [256, 65536]
+    (about 4.7e7 particles), each with its own series from prior-drawn
+    variances, FP32, systematic, the autotuned launch shape.  After three
+    cycles, sampled filters (the smallest, the largest and six others) equal
+    the oracle bit for bit: ancestors of the last cycle and every particle."""
+    nf, seed, T = 4096, 4096, 3
+    ns, s2, t2 = synth.batch_specs(nf, seed)
+    ys = np.stack([synth.local_level_series(seed + i, T + 1, sigma2=s2[i], tau2=t2[i],
+                                            filter_id=i)[1] for i in range(nf)], axis=1)
+    specs = [dict(n=int(ns[i]), seed=seed + i, filter_id=i) for i in range(nf)]
+    b = pf.Batch(specs, scheme="systematic", precision="fp32")
+    b.tune(ys[0])  # trial cycles choose the launch shape and change no result
+    for t in range(T):
+        b.step(ys[t])
+    rng = np.random.default_rng(7)
+    pick = sorted({int(np.argmin(ns)), int(np.argmax(ns))} |
+                  set(int(i) for i in rng.choice(nf, 6, replace=False)))
+    for i in pick:
+        o = orc.Filter(orc.make_config(int(ns[i]), seed=seed + i, filter_id=i, scheme=1,
+                                       precision=0))
+        for t in range(T):
+            o.step(ys[t, i])
+        assert np.array_equal(_u32(b.ancestors(i)), o.ancestors()), i
+        _same_particles(_raw(b.particles(i), 0), o.state_raw())
+        o.close()
+    b.close()
