@@ -137,3 +137,42 @@ def test_replayed_poisson_load(pf):
         len(a) * n for a, n in zip(arr, sizes))
     _check_against_alone(pf, srv.poll(), {i: c for i, c in enumerate(cfgs)}, series)
     srv.close()
+
+
+def test_served_at_full_size_sampled_streams_equal_alone(pf):
+    """The served workload's streams: 10,000 of them, N log-uniform in
+    [512, 131072] (about 2.35e8 particles), in the benchmark's launch
+    configuration (120 GB budget, clusters of 8 for streams of at least
+    16,384 particles, two cycles in flight).  Three observations each,
+    submitted round-robin; sampled streams (the smallest, the largest and six
+    others) give exactly a standalone filter's summaries after each."""
+    n_streams, seed, T = 10000, 10000, 3
+    ns, s2, t2 = synth.batch_specs(n_streams, seed, 512, 131072)
+    series = [synth.local_level_series(seed + i, T, sigma2=s2[i], tau2=t2[i], filter_id=i)[1]
+              for i in range(n_streams)]
+    srv = pf.Server(max_streams=n_streams, hbm_budget_bytes=int(120e9), scheme="systematic",
+                    precision="fp32", max_inflight=2, cluster=8, big_min=16384,
+                    keep_results=True)
+    cfgs = {i: dict(n=int(ns[i]), seed=seed + i, filter_id=i) for i in range(n_streams)}
+    for i, c in cfgs.items():
+        srv.open(i, **c)
+    for k in range(T):
+        for i in range(n_streams):
+            srv.submit(i, series[i][k])
+    for i in range(n_streams):
+        srv.close_stream(i)
+    srv.drain(600)
+    st = srv.stats()
+    assert st["completed"] == n_streams * T
+    rng = np.random.default_rng(3)
+    pick = sorted({int(np.argmin(ns)), int(np.argmax(ns))} |
+                  set(int(i) for i in rng.choice(n_streams, 6, replace=False)))
+    results = []
+    while True:
+        r = srv.poll()
+        if not r:
+            break
+        results.extend(r)
+    res = [r for r in results if r[0] in set(pick)]
+    _check_against_alone(pf, res, {i: cfgs[i] for i in pick}, {i: series[i] for i in pick})
+    srv.close()
