@@ -61,6 +61,14 @@ typedef enum {
  *                         paper's parallelized cut-point search and cut-point
  *                         method (Section 3.2); identical output.
  *  SYSTEMATIC_CUTPOINT    same positions as SYSTEMATIC, cut-point search.
+ *                         In the cut-point search thread i writes the whole
+ *                         run of table entries that point at particle i, as
+ *                         the paper's algorithm does; under degenerate
+ *                         weights (one particle holding nearly all the mass,
+ *                         the worst case Section 3.2 discusses) one thread
+ *                         writes up to n entries serially, so both
+ *                         *_CUTPOINT schemes take O(n) time there.  The
+ *                         other schemes have no such case.
  *  STRATIFIED             positions = (j + u_j) T / n, one uniform u_j in
  *                         each stratum (Section 3.1, "Stratified
  *                         Resampling"): u_j from word pair 2 (j mod 2),
@@ -294,21 +302,27 @@ pf_status pf_cutpoint_method(const uint64_t* Q_dev, uint64_t n, const uint32_t* 
 
 /* Resampling without allocating: the same computation and result as
  * pf_resample, for callers that cannot allocate device memory at the point
- * where they resample (for example host functions enqueued on a stream, which
- * may not call CUDA API functions, latency-critical loops that must not risk an
+ * where they resample: latency-critical loops that must not risk an
  * allocation's synchronisation, or processes whose device memory is reserved
- * up front).  The paper has no counterpart; this is a deployment variant.
+ * up front and must not grow.  It avoids device allocation only: the call
+ * still makes CUDA runtime calls (cudaGetDevice, cudaMemsetAsync, kernel
+ * launches, a small cudaMemcpyAsync) and synchronises `stream` before it
+ * returns, so it may not be called from a host function enqueued on a stream
+ * (where CUDA API calls are forbidden).  The paper has no counterpart; this is
+ * a deployment variant.
  *
  * Scratch lives in one fixed-size device array inside libpf.so, present on
  * every device that loads the library until the process exits (about 20 MiB),
  * and sized for n <= PF_NOALLOC_MAX_PARTICLES; larger n returns
  * PF_ERR_INVALID.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress), so make that first call before any stream
- * capture.  Every call on a device shares the one array, so calls whose GPU
- * work overlaps (other streams, other host threads) race and corrupt each
- * other: serialise them.  The call clears the parts of the scratch that must
- * start at zero, then synchronises `stream` to report device-side errors as
- * pf_resample does.  Arguments and errors as pf_resample. */
+ * address (cudaGetSymbolAddress) with that device current.  The device used is
+ * the calling thread's current device, which must be the one that holds
+ * w_dev and anc_dev.  Every call on a device shares the one array, so calls
+ * whose GPU work overlaps (other streams, other host threads) race and
+ * corrupt each other: serialise them.  The call clears the parts of the
+ * scratch that must start at zero, then synchronises `stream` to report
+ * device-side errors as pf_resample does.  Arguments and errors as
+ * pf_resample. */
 #define PF_NOALLOC_MAX_PARTICLES (1ull << 20)
 pf_status pf_resample_noalloc(const float* w_dev, uint64_t n, uint64_t seed, uint32_t filter_id,
                               uint32_t t, int32_t scheme, uint32_t* anc_dev, void* stream);

@@ -1330,14 +1330,14 @@ pf_status pf_cutpoint_method(const uint64_t* Q_dev, uint64_t n, const uint32_t* 
 // ---------------------------------------------------------------------------
 // Resampling without any allocation.
 //
-// For callers that cannot allocate device memory when they resample: code
-// running where CUDA API calls that allocate are not allowed or not wanted,
-// such as host functions enqueued on a stream (which may not call CUDA API
-// functions at all), latency-critical loops that must not risk an
-// allocation's device synchronisation or unbounded time, and processes whose
-// device memory is fully reserved up front.  The scratch of this entry point
-// lives in one file-scope device array of fixed size, present on every device
-// that loads the library for the life of the process.
+// For callers that cannot allocate device memory when they resample:
+// latency-critical loops that must not risk an allocation's device
+// synchronisation or unbounded time, and processes whose device memory is
+// fully reserved up front.  Only allocation is avoided: the call still makes
+// CUDA runtime calls and synchronises its stream, so it is not for host
+// functions enqueued on a stream.  The scratch of this entry point lives in
+// one file-scope device array of fixed size, present on every device that
+// loads the library for the life of the process.
 // ---------------------------------------------------------------------------
 }  // extern "C"
 

@@ -1385,20 +1385,32 @@ __global__ void __launch_bounds__(BLOCK, PER == 8 ? 4 : 3) k_cdf_sys(FilterArgs<
   // TMA double buffer: copy number q goes to buffer q & 1 and completes
   // phase (q >> 1) & 1 of that buffer's barrier; copies are waited for in
   // the order they were issued
-  if (STAGED && threadIdx.x == 0) {
-    mbar_init(&s_bar[0], 1);
-    mbar_init(&s_bar[1], 1);
-    mbar_init_fence();
+  // After a wait that gave up (s_tmo set, ERR_TIMEOUT raised) the CTA issues
+  // no more copies and waits for none; its CDF and ancestors are then
+  // invalid, which the error word reports.  Before the CTA exits, thread 0
+  // waits once more, bounded, for every copy it issued that it has not seen
+  // complete, so that no copy into this CTA's shared memory outlives it.
+  __shared__ uint32_t s_tmo;
+  if (threadIdx.x == 0) {
+    s_tmo = 0;
+    if (STAGED) {
+      mbar_init(&s_bar[0], 1);
+      mbar_init(&s_bar[1], 1);
+      mbar_init_fence();
+    }
   }
   __syncthreads();
   uint32_t q_issued = 0, q_done = 0;
+  uint32_t iss_b[2] = {0, 0}, ok_b[2] = {0, 0};  // thread 0: copies issued / seen complete per buffer
   auto issue = [&](uint32_t tile) {  // thread 0 only; the buffer is free
+    if (*(volatile uint32_t*)&s_tmo) return;
     const uint64_t first = (uint64_t)tile * TP;
     const uint64_t cnt = n - first < (uint64_t)TP ? n - first : (uint64_t)TP;
     const uint32_t bytes = (uint32_t)((cnt * sizeof(R) + 15) & ~(uint64_t)15);
     bulk_wait_read();  // the buffer's last bulk store has read it
     fence_proxy_async_smem();
     tma_load_1d(s_ell[q_issued & 1], a.ell + first, bytes, &s_bar[q_issued & 1]);
+    ++iss_b[q_issued & 1];
   };
   auto next_issue = [&](uint32_t tile) {
     if (!STAGED) return;
@@ -1410,10 +1422,23 @@ __global__ void __launch_bounds__(BLOCK, PER == 8 ? 4 : 3) k_cdf_sys(FilterArgs<
   auto take_tile = [&](uint32_t tile) -> const R* {
     if (!STAGED) return a.ell + (uint64_t)tile * TP;
     const uint32_t b = q_done & 1;
-    if (!mbar_wait(&s_bar[b], (q_done >> 1) & 1) && threadIdx.x == 0)
-      atomicOr(&c->err, ERR_TIMEOUT);
+    if (!*(volatile uint32_t*)&s_tmo) {
+      if (mbar_wait(&s_bar[b], (q_done >> 1) & 1)) {
+        if (threadIdx.x == 0) ++ok_b[b];
+      } else {
+        s_tmo = 1u;
+        atomicOr(&c->err, ERR_TIMEOUT);
+      }
+    }
     ++q_done;
     return s_ell[b];
+  };
+  auto drain_copies = [&]() {  // thread 0, at exit: copies k of buffer b complete phase k & 1
+    if constexpr (STAGED) {
+      if (!*(volatile uint32_t*)&s_tmo) return;
+      for (int b = 0; b < 2; ++b)
+        for (uint32_t k = ok_b[b]; k < iss_b[b]; ++k) (void)mbar_wait(&s_bar[b], k & 1);
+    }
   };
   // this thread's 16 weights of tile `tile` quantised, as inclusive running
   // sums W and the partial sum of e = exp(l - m).  mode 0: from l in buf;
@@ -1782,6 +1807,10 @@ __global__ void __launch_bounds__(BLOCK, PER == 8 ? 4 : 3) k_cdf_sys(FilterArgs<
     for (uint64_t j = (uint64_t)blockIdx.x * BLOCK + threadIdx.x; j < n;
          j += (uint64_t)gridDim.x * BLOCK)
       a.anc[j] = (uint32_t)j;
+  }
+  if (STAGED && threadIdx.x == 0) {
+    drain_copies();
+    bulk_wait_done();
   }
 }
 

@@ -648,15 +648,29 @@ class Server:
             pass
 
 
-def resample(w, seed, filter_id=0, t=0, scheme="systematic", out=None, stream=None):
-    """Ancestors (int32 CUDA tensor viewed as uint32) for float32 CUDA weights w."""
+def _resample_out(w, out):
+    """The caller's int32 output on w's device with room for n ancestors, or a
+    new one."""
     torch = _torch()
     assert w.is_cuda and w.dtype == torch.float32 and w.is_contiguous()
     n = w.numel()
-    anc = out if out is not None else torch.empty(n, dtype=torch.int32, device=w.device)
+    if out is None:
+        return torch.empty(n, dtype=torch.int32, device=w.device)
+    if out.dtype != torch.int32 or out.device != w.device or not out.is_contiguous():
+        raise ValueError("out must be a contiguous int32 tensor on %s" % w.device)
+    if out.numel() < n:
+        raise ValueError("out holds %d ancestors, %d needed" % (out.numel(), n))
+    return out
+
+
+def resample(w, seed, filter_id=0, t=0, scheme="systematic", out=None, stream=None):
+    """Ancestors (int32 CUDA tensor viewed as uint32) for float32 CUDA weights w."""
+    torch = _torch()
+    anc = _resample_out(w, out)
     sch = SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
-    _check(_lib.pf_resample(_ptr(w), n, seed, filter_id, t, sch, _ptr(anc), _stream_ptr(stream)),
-           "pf_resample")
+    with torch.cuda.device(w.device):  # the library works on the current device
+        _check(_lib.pf_resample(_ptr(w), w.numel(), seed, filter_id, t, sch, _ptr(anc),
+                                _stream_ptr(stream)), "pf_resample")
     return anc
 
 
@@ -665,12 +679,11 @@ def resample_noalloc(w, seed, filter_id=0, t=0, scheme="systematic", out=None, s
     (its scratch is a fixed device array, n <= NOALLOC_MAX_PARTICLES); `out`,
     when given, is the caller's preallocated int32 output."""
     torch = _torch()
-    assert w.is_cuda and w.dtype == torch.float32 and w.is_contiguous()
-    n = w.numel()
-    anc = out if out is not None else torch.empty(n, dtype=torch.int32, device=w.device)
+    anc = _resample_out(w, out)
     sch = SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
-    _check(_lib.pf_resample_noalloc(_ptr(w), n, seed, filter_id, t, sch, _ptr(anc),
-                                    _stream_ptr(stream)), "pf_resample_noalloc")
+    with torch.cuda.device(w.device):  # the fixed array of w's device
+        _check(_lib.pf_resample_noalloc(_ptr(w), w.numel(), seed, filter_id, t, sch, _ptr(anc),
+                                        _stream_ptr(stream)), "pf_resample_noalloc")
     return anc
 
 

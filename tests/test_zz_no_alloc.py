@@ -1,9 +1,9 @@
 """pf_resample_noalloc: resampling for callers that cannot allocate device memory.
 
 The entry point keeps its scratch in a fixed device array inside the library
-instead of allocating, so code that must not allocate at that point (host
-functions enqueued on a stream, latency-critical loops, processes with all
-device memory reserved up front) can still resample.  Its ancestors must equal
+instead of allocating, so code that must not allocate at that point
+(latency-critical loops, processes with all device memory reserved up front)
+can still resample.  Its ancestors must equal
 pf_resample's exactly (integer output), on consecutive calls that reuse the
 same scratch, and sizes above the array's limit must be refused.
 
@@ -28,7 +28,7 @@ def test_noalloc_matches_resample_on_two_calls_in_a_row(pf):
     for call in range(2):  # the second round reuses the scratch the first left behind
         for n, s in cases:
             w = torch.from_numpy(synth.sweep_weights(n, s, seed=40 + call)).cuda()
-            for scheme in (0, 1, 2, 3):
+            for scheme in (0, 1, 2, 3, 4):  # every scheme the entry point accepts
                 ref = _u32(pf.resample(w, seed=11 + call, filter_id=2, t=call, scheme=scheme))
                 got = _u32(pf.resample_noalloc(w, seed=11 + call, filter_id=2, t=call,
                                                scheme=scheme))
