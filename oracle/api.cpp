@@ -82,22 +82,25 @@ void or_normals_f64(uint64_t seed, uint32_t filter, uint32_t t, uint32_t purpose
 
 int or_gamma_f32(double a, uint64_t seed, uint32_t filter, uint32_t t, uint32_t purpose,
                  uint64_t n, float* out) {
-  double d, c;
-  mt_constants(a, &d, &c);
+  double d, c, K;
+  mt_constants(a, &d, &c, &K);
   int fail = 0;
   for (uint64_t j = 0; j < n; ++j)
-    out[j] = gamma_mt<float>((float)d, (float)c, seed, filter, t, (uint32_t)j, purpose, &fail);
+    out[j] = gamma_mt<float>((float)d, (float)c, (float)K, seed, filter, t, (uint32_t)j, purpose,
+                             &fail);
   return fail;
 }
 int or_gamma_f64(double a, uint64_t seed, uint32_t filter, uint32_t t, uint32_t purpose,
                  uint64_t n, double* out) {
-  double d, c;
-  mt_constants(a, &d, &c);
+  double d, c, K;
+  mt_constants(a, &d, &c, &K);
   int fail = 0;
   for (uint64_t j = 0; j < n; ++j)
-    out[j] = gamma_mt<double>(d, c, seed, filter, t, (uint32_t)j, purpose, &fail);
+    out[j] = gamma_mt<double>(d, c, K, seed, filter, t, (uint32_t)j, purpose, &fail);
   return fail;
 }
+
+void or_mt_constants(double a, double* out) { mt_constants(a, &out[0], &out[1], &out[2]); }
 
 int or_cdf_shift(uint64_t n) { return cdf_shift(n); }
 void or_cdf_scan(const uint64_t* W, uint64_t n, uint64_t* Q) { cdf_scan(W, n, Q); }

@@ -10,9 +10,11 @@
 // published definition in its own code.
 //
 // Every floating-point step is written as an explicit sequence of IEEE-754
-// operations and the file is compiled with -ffp-contract=off, so that no
-// multiply-add is fused: the same sequence in the CUDA library (built with
-// -fmad=false) gives the same bits.
+// operations -- each a separately rounded add, multiply, divide or square
+// root, or a fused multiply-add where the code calls std::fma -- and the file
+// is compiled with -ffp-contract=off, so that the compiler fuses nothing
+// else: the same sequence in the CUDA library (built with -fmad=false, fused
+// multiply-adds written explicitly) gives the same bits.
 //
 // Parity status: every function here is pinned by tests under tests/ (see the
 // "pin" line in each function's comment) except where marked
@@ -58,7 +60,7 @@ double unif_f64_32(uint32_t w);                 // (2*w+1) * 2^-33
 // pin: against libm within a few ulp over dense samples
 // (tests/test_oracle_detmath.py).
 // ---------------------------------------------------------------------------
-template <class R> R det_log(R x);          // x > 0, finite, normal
+template <class R> R det_log(R x);          // x > 0 (binary32: +inf, NaN returned unchanged)
 template <class R> R det_exp_core(R r);     // Taylor polynomial of exp on |r| <= ~0.35
 template <class R> R det_cos2pi(R u);       // cos(2*pi*u) for u in [0, 1]
 template <class R> void det_sincos2pi(R u, R* s, R* c);  // both, same reduction
@@ -75,14 +77,20 @@ template <class R> R bm_normal(const W4& w);
 template <class R> void bm_normal2(const W4& w, R* zc, R* zs);
 template <class R> R extra_uniform(const W4& w);
 
-// Gamma(a, 1) by Marsaglia & Tsang (2000), a >= 1, with d = a - 1/3 and
-// c = 1/sqrt(9 d) given in the working precision.  Attempt k uses its own
-// draw (purpose, attempt k); after 16 rejections *fail is set and d returned.
-template <class R> R gamma_mt(R d, R c, uint64_t seed, uint32_t filter, uint32_t t,
+// Gamma(a, 1) by Marsaglia & Tsang (2000), a >= 1, with d = a - 1/3,
+// c = 1/sqrt(9 d) and the squeeze coefficient K = 0.0331 (2/3) / d given in
+// the working precision: v = fma(c, Z, 1); accept d v^3 when v > 0 and
+// U < fma(-K, Z^4, 1) (the squeeze), else when
+// log U < fma(d, (1 - v^3) + log v^3, Z^2 / 2).  Attempt k uses its own draw
+// (purpose, attempt k); after 16 rejections *fail is set and d returned.
+// pin: gamma KS / moments (tests/test_oracle_rng.py); the squeeze bound
+// 1 - K Z^4 <= exp(g(Z)) over a dense grid of d and Z
+// (tests/test_oracle_rng.py::test_gamma_squeeze_is_a_lower_bound).
+template <class R> R gamma_mt(R d, R c, R K, uint64_t seed, uint32_t filter, uint32_t t,
                               uint32_t j, uint32_t purpose, int* fail);
 // The same with the first attempt's (Z, U) given; attempts k >= 1 use draw
 // (purpose, k).
-template <class R> R gamma_mt_from(R d, R c, R Z0, R U0, uint64_t seed, uint32_t filter,
+template <class R> R gamma_mt_from(R d, R c, R K, R Z0, R U0, uint64_t seed, uint32_t filter,
                                    uint32_t t, uint32_t j, uint32_t purpose, int* fail);
 
 // The draws of one propagation step for slot j: two 128-bit draws,
@@ -93,8 +101,9 @@ template <class R> R gamma_mt_from(R d, R c, R Z0, R U0, uint64_t seed, uint32_t
 template <class R> void theta_draws(uint64_t seed, uint32_t filter, uint32_t t, uint32_t j,
                                     R* Zx, R* Zs, R* Us, R* Zt, R* Ut);
 
-// Shape constants (d, c) of Marsaglia-Tsang for shape a, in double.
-void mt_constants(double a, double* d, double* c);
+// Shape constants of Marsaglia-Tsang for shape a, in double: d = a - 1/3,
+// c = 1/sqrt(9 d) and the squeeze coefficient K = 0.0331 (2/3) / d.
+void mt_constants(double a, double* d, double* c, double* K);
 
 // ---------------------------------------------------------------------------
 // Fixed-point CDF (the resampling CDF q(i) of the paper's Section 3.1 in

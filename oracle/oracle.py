@@ -62,6 +62,7 @@ def _declare(L):
         "or_normals_f64": (V, [U64, U32, U32, U32, U64, f64p]),
         "or_gamma_f32": (I, [D, U64, U32, U32, U32, U64, f32p]),
         "or_gamma_f64": (I, [D, U64, U32, U32, U32, U64, f64p]),
+        "or_mt_constants": (V, [D, f64p]),
         "or_cdf_shift": (I, [U64]),
         "or_cdf_scan": (V, [u64p, U64, u64p]),
         "or_quantize_weights_f32": (I, [f32p, U64, u64p]),
@@ -174,6 +175,13 @@ def normals(seed, filt, t, purpose, n, dtype=np.float32):
     f = lib().or_normals_f32 if dtype == np.float32 else lib().or_normals_f64
     f(seed, filt, t, purpose, n, out)
     return out
+
+
+def mt_constants(a):
+    """(d, c, K) of the Marsaglia-Tsang sampler for shape a, in binary64."""
+    out = np.zeros(3, np.float64)
+    lib().or_mt_constants(float(a), out)
+    return float(out[0]), float(out[1]), float(out[2])
 
 
 def gammas(a, seed, filt, t, purpose, n, dtype=np.float32):

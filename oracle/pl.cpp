@@ -11,6 +11,9 @@
 //   p(y_{t+1} | x_t, theta)      = N(y; x_t, sigma^2 + tau^2)
 //   p(x_{t+1} | x_t, theta, y)    = N(mu, V), V = sigma^2 tau^2 / (sigma^2 + tau^2),
 //                                   mu = (x_t sigma^2 + y tau^2) / (sigma^2 + tau^2)
+//                                   (evaluated with r = 1/(sigma^2 + tau^2):
+//                                   V = (sigma^2 tau^2) r, mu = fma(x_t, sigma^2, y tau^2) r,
+//                                   x_{t+1} = fma(sqrt V, Z, mu))
 //   b_sigma <- b_sigma + (y - x_{t+1})^2 / 2,  b_tau <- b_tau + (x_{t+1} - x_t)^2 / 2
 //   sigma^2 ~ IG(a_sigma0 + (t+1)/2, b_sigma), tau^2 ~ IG(a_tau0 + (t+1)/2, b_tau).
 // pin: Kalman filter with known variances, conjugate inverse-gamma posterior
@@ -45,20 +48,24 @@ template <> struct Suff<float> {
   typedef uint64_t B;
   static B from_prior(double b) { return (uint64_t)(b * 0x1p32); }
   static double as_double(B b) { return (double)b * 0x1p-32; }
-  // b + (resid^2)/2 with resid in the working precision.
+  // b + (resid^2)/2 with resid in the working precision: resid^2 2^31 is
+  // (resid^2 / 2) 2^32 exactly (a power-of-two scaling), truncated.
   static B add_half_square(B b, float resid, int* fail) {
     float r2 = resid * resid;
-    float h = 0.5f * r2;
-    float v = h * 0x1p32f;
+    float v = r2 * 0x1p31f;
     if (!(v < 0x1p63f)) {
       *fail = 1;
       return b;
     }
     return b + (uint64_t)v;
   }
+  // The inverse-gamma draw b 2^-32 / G.  b 2^-32 in binary32 is taken from
+  // the two 32-bit halves, each converted to nearest, joined by one fused
+  // multiply-add: fma(lo, 2^-32, hi).
   static float ig(B b, float G) {
-    float bf = (float)b;
-    float bs = bf * 0x1p-32f;
+    float hi = (float)(uint32_t)(b >> 32);
+    float lo = (float)(uint32_t)b;
+    float bs = std::fma(lo, 0x1p-32f, hi);
     return bs / G;
   }
 };
@@ -140,9 +147,9 @@ template <class R> class Filter : public FilterBase {
     slam = (double)n;
     const R x0m = (R)cfg.x0_mean;
     const R sdx = (R)std::sqrt(cfg.x0_var);
-    double ds, cs, dt, ct;
-    mt_constants(cfg.a_sigma, &ds, &cs);
-    mt_constants(cfg.a_tau, &dt, &ct);
+    double ds, cs, ks, dt, ct, kt;
+    mt_constants(cfg.a_sigma, &ds, &cs, &ks);
+    mt_constants(cfg.a_tau, &dt, &ct, &kt);
     for (uint64_t j = 0; j < n; ++j) {
       W4 w = draw(cfg.seed, cfg.filter_id, 0, (uint32_t)j, P_INIT_X, 0);
       R Z = bm_normal<R>(w);
@@ -156,9 +163,9 @@ template <class R> class Filter : public FilterBase {
       } else {
         bs[j] = Suff<R>::from_prior(cfg.b_sigma);
         bt[j] = Suff<R>::from_prior(cfg.b_tau);
-        R Gs = gamma_mt<R>((R)ds, (R)cs, cfg.seed, cfg.filter_id, 0, (uint32_t)j,
+        R Gs = gamma_mt<R>((R)ds, (R)cs, (R)ks, cfg.seed, cfg.filter_id, 0, (uint32_t)j,
                            P_INIT_SIGMA, &fail);
-        R Gt = gamma_mt<R>((R)dt, (R)ct, cfg.seed, cfg.filter_id, 0, (uint32_t)j,
+        R Gt = gamma_mt<R>((R)dt, (R)ct, (R)kt, cfg.seed, cfg.filter_id, 0, (uint32_t)j,
                            P_INIT_TAU, &fail);
         s2[j] = Suff<R>::ig(bs[j], Gs);
         t2[j] = Suff<R>::ig(bt[j], Gt);
@@ -209,26 +216,27 @@ template <class R> class Filter : public FilterBase {
     }
 
     // Steps 2-4: propagate, update sufficient statistics, draw theta.
-    double ds, cs, dt, ct;
-    mt_constants(cfg.a_sigma + 0.5 * (double)(t + 1), &ds, &cs);
-    mt_constants(cfg.a_tau + 0.5 * (double)(t + 1), &dt, &ct);
+    double ds, cs, ks, dt, ct, kt;
+    mt_constants(cfg.a_sigma + 0.5 * (double)(t + 1), &ds, &cs, &ks);
+    mt_constants(cfg.a_tau + 0.5 * (double)(t + 1), &dt, &ct, &kt);
     std::vector<R> xn(n), s2n(n), t2n(n);
     std::vector<B> bsn(n), btn(n);
     for (uint64_t j = 0; j < n; ++j) {
       const uint32_t a = anc[j];
       const R xa = x[a], sa = s2[a], ta = t2[a];
+      // V = sigma^2 tau^2 / s and mu = (x sigma^2 + y tau^2) / s share one
+      // correctly rounded reciprocal of s = sigma^2 + tau^2
       R s = sa + ta;
+      R rs_inv = (R)1 / s;
       R p = sa * ta;
-      R V = p / s;
-      R n1 = xa * sa;
+      R V = p * rs_inv;
       R n2 = yr * ta;
-      R nn = n1 + n2;
-      R mu = nn / s;
+      R nn = std::fma(xa, sa, n2);
+      R mu = nn * rs_inv;
       R sv = std::sqrt(V);
       R Z, Zs, Us, Zt, Ut;
       theta_draws<R>(cfg.seed, cfg.filter_id, t, (uint32_t)j, &Z, &Zs, &Us, &Zt, &Ut);
-      R xz = sv * Z;
-      R xj = mu + xz;
+      R xj = std::fma(sv, Z, mu);
       xn[j] = xj;
       if (cfg.known_variances) {
         s2n[j] = sa; t2n[j] = ta; bsn[j] = bs[a]; btn[j] = bt[a];
@@ -238,10 +246,10 @@ template <class R> class Filter : public FilterBase {
       R rt = xj - xa;
       bsn[j] = Suff<R>::add_half_square(bs[a], rs, &fail);
       btn[j] = Suff<R>::add_half_square(bt[a], rt, &fail);
-      R Gs = gamma_mt_from<R>((R)ds, (R)cs, Zs, Us, cfg.seed, cfg.filter_id, t, (uint32_t)j,
-                              P_GAMMA_SIGMA, &fail);
-      R Gt = gamma_mt_from<R>((R)dt, (R)ct, Zt, Ut, cfg.seed, cfg.filter_id, t, (uint32_t)j,
-                              P_GAMMA_TAU, &fail);
+      R Gs = gamma_mt_from<R>((R)ds, (R)cs, (R)ks, Zs, Us, cfg.seed, cfg.filter_id, t,
+                              (uint32_t)j, P_GAMMA_SIGMA, &fail);
+      R Gt = gamma_mt_from<R>((R)dt, (R)ct, (R)kt, Zt, Ut, cfg.seed, cfg.filter_id, t,
+                              (uint32_t)j, P_GAMMA_TAU, &fail);
       s2n[j] = Suff<R>::ig(bsn[j], Gs);
       t2n[j] = Suff<R>::ig(btn[j], Gt);
     }
@@ -413,15 +421,15 @@ int suffstat_known_states(const Config& cfg, const double* xpath, const double* 
       R rt = xj - xa;
       bs = Suff<R>::add_half_square(bs, rs, &fail);
       bt = Suff<R>::add_half_square(bt, rt, &fail);
-      double ds, cs, dt, ct;
-      mt_constants(cfg.a_sigma + 0.5 * (double)(t + 1), &ds, &cs);
-      mt_constants(cfg.a_tau + 0.5 * (double)(t + 1), &dt, &ct);
+      double ds, cs, ks, dt, ct, kt;
+      mt_constants(cfg.a_sigma + 0.5 * (double)(t + 1), &ds, &cs, &ks);
+      mt_constants(cfg.a_tau + 0.5 * (double)(t + 1), &dt, &ct, &kt);
       R Zx, Zs, Us, Zt, Ut;
       theta_draws<R>(cfg.seed, cfg.filter_id, t, (uint32_t)j, &Zx, &Zs, &Us, &Zt, &Ut);
-      R Gs = gamma_mt_from<R>((R)ds, (R)cs, Zs, Us, cfg.seed, cfg.filter_id, t, (uint32_t)j,
-                              P_GAMMA_SIGMA, &fail);
-      R Gt = gamma_mt_from<R>((R)dt, (R)ct, Zt, Ut, cfg.seed, cfg.filter_id, t, (uint32_t)j,
-                              P_GAMMA_TAU, &fail);
+      R Gs = gamma_mt_from<R>((R)ds, (R)cs, (R)ks, Zs, Us, cfg.seed, cfg.filter_id, t,
+                              (uint32_t)j, P_GAMMA_SIGMA, &fail);
+      R Gt = gamma_mt_from<R>((R)dt, (R)ct, (R)kt, Zt, Ut, cfg.seed, cfg.filter_id, t,
+                              (uint32_t)j, P_GAMMA_TAU, &fail);
       s2v = Suff<R>::ig(bs, Gs);
       t2v = Suff<R>::ig(bt, Gt);
     }

@@ -72,10 +72,16 @@ double unif_f64_32(uint32_t w) { return (double)(2ull * w + 1ull) * 0x1p-33; }
 // ---------------------------------------------------------------------------
 // Deterministic elementary functions.
 //
-// log: x = f * 2^e with f in [sqrt(1/2), sqrt(2)); log f = 2 atanh(z),
+// log, binary64: x = f * 2^e with f in [sqrt(1/2), sqrt(2)); log f = 2 atanh(z),
 //   z = (f - 1)/(f + 1), by the odd series 2z (1 + z^2/3 + z^4/5 + ...)
-//   (terms through z^2K/(2K+1), K = 4 in binary32, 10 in binary64);
-//   log x = e * ln2 + log f.
+//   (terms through z^20/21); log x = e * ln2 + log f.
+// log, binary32 (no division): the same reduction, u = f - 1 (exact), and
+//   log(1 + u) = u + u^2 q(u) with q a degree-8 polynomial fitted for minimal
+//   maximum relative error of log(1 + u) on [sqrt(1/2) - 1, sqrt(2) - 1]
+//   (Lawson's iteratively reweighted least squares, coefficients rounded to
+//   binary32); log x = e ln2_hi + (e ln2_lo + log f) by two fused
+//   multiply-adds.  Error at most 0.93 ulp over every positive normal
+//   binary32 (checked exhaustively against long double log).
 // exp: Taylor polynomial sum_{k<=D} r^k/k! (D = 7 / 13) on the reduced
 //   argument of a Cody & Waite (1980) reduction r = (x - n ln2_hi) - n ln2_lo.
 // cos(2 pi u): reduce u to w = |u - rint(u)| in [0, 1/2]; by octant use
@@ -91,7 +97,6 @@ template <> struct K<float> {
   static constexpr float INV_LN2 = 0x1.715476p+0f;
   static constexpr float TWO_PI = 0x1.921fb6p+2f;
   static constexpr float SQRT_HALF = 0x1.6a09e6p-1f;
-  static constexpr float MT_SQUEEZE = 0x1.0f27bcp-5f;  // 0.0331
   static constexpr int LOG_K = 4;
   static constexpr int EXP_D = 7;
   static constexpr int COS_K = 5;
@@ -104,7 +109,6 @@ template <> struct K<double> {
   static constexpr double INV_LN2 = 0x1.71547652b82fep+0;
   static constexpr double TWO_PI = 0x1.921fb54442d18p+2;
   static constexpr double SQRT_HALF = 0x1.6a09e667f3bcdp-1;
-  static constexpr double MT_SQUEEZE = 0x1.0f27bb2fec56dp-5;  // 0.0331
   static constexpr int LOG_K = 10;
   static constexpr int EXP_D = 13;
   static constexpr int COS_K = 8;
@@ -158,6 +162,40 @@ template <class R> R det_log(R x) {
   R logf = two_z * p;
   R elog2 = (R)e * K<R>::LN2;
   return elog2 + logf;
+}
+
+// q(u) of the binary32 log, c_0 .. c_8 (coefficient of u^j).
+static const float LOGQ_F[9] = {-0x1.fffff8p-2f, 0x1.55555p-2f,   -0x1.000426p-2f,
+                                0x1.99a3f6p-3f,  -0x1.542766p-3f, 0x1.22715ep-3f,
+                                -0x1.0f3756p-3f, 0x1.0849bep-3f,  -0x1.38339ap-4f};
+
+// x > 0 (normal or subnormal); +inf and NaN are returned unchanged.
+template <> float det_log<float>(float x) {
+  if (!(x < INFINITY)) return x;
+  uint32_t b;
+  std::memcpy(&b, &x, 4);
+  int e = 0;
+  if ((b & 0x7f800000u) == 0) {  // subnormal: scale by 2^23 (exact)
+    const float xs = x * 0x1p23f;
+    std::memcpy(&b, &xs, 4);
+    e = -23;
+  }
+  e += (int)(b >> 23) - 127;
+  uint32_t m = (b & 0x7fffffu) | 0x3f800000u;  // f = x 2^-e in [1, 2)
+  if (m >= 0x3fb504f3u) {                       // f >= sqrt(2) rounded: halve it
+    m -= 0x00800000u;
+    e += 1;
+  }
+  float f;
+  std::memcpy(&f, &m, 4);
+  const float u = f - 1.0f;  // exact (Sterbenz)
+  float q = LOGQ_F[8];
+  for (int j = 7; j >= 0; --j) q = std::fma(q, u, LOGQ_F[j]);
+  const float u2 = u * u;
+  const float lf = std::fma(u2, q, u);
+  const float ef = (float)e;  // exact
+  const float lo = std::fma(ef, K<float>::LN2_LO, lf);
+  return std::fma(ef, K<float>::LN2_HI, lo);
 }
 
 template <class R> R det_exp_core(R r) {
@@ -301,16 +339,29 @@ template <> void bm_normal2<double>(const W4& w, double* zc, double* zs) {
 template <> float extra_uniform<float>(const W4& w) { return unif_f32(w.w[2]); }
 template <> double extra_uniform<double>(const W4& w) { return unif_f64_32(w.w[3]); }
 
-void mt_constants(double a, double* d, double* c) {
+void mt_constants(double a, double* d, double* c, double* K) {
   const double ONE_THIRD = 0x1.5555555555555p-2;
+  // 0.0331 * 2/3 = 331/15000 rounded to nearest: the squeeze coefficient
+  // K = 0.0331 (2/3) / d equals Marsaglia & Tsang's 0.0331 at d = 2/3 (a = 1)
+  const double SQZ = 0x1.698a4eea9073cp-6;
   double dd = a - ONE_THIRD;
   double nine_d = 9.0 * dd;
   double s = std::sqrt(nine_d);
   *d = dd;
   *c = 1.0 / s;
+  *K = SQZ / dd;
 }
 
-template <class R> R gamma_mt_from(R d, R c, R Z0, R U0, uint64_t seed, uint32_t filter,
+// Marsaglia & Tsang (2000): with v = (1 + c Z)^3, accept d v when v > 0 and
+// log U < Z^2/2 + d (1 - v + log v).  The squeeze U < 1 - K Z^4 accepts
+// without logarithms; it is valid (implies the full test) because
+// 1 - e^{g(Z)} <= K Z^4 for every Z (g the right-hand side above): the
+// supremum of (1 - e^g) d / Z^4 over Z is 0.02205 at d = 2/3 and falls as d
+// grows (to 1/108), so K = 0.0331 (2/3) / d bounds it for all d >= 2/3.  A
+// draw the squeeze misses takes the full test, so the accepted draws, and
+// the sampler's law, are exactly Marsaglia-Tsang's; the d-scaled squeeze only
+// takes the logarithms far less often (pin: tests/test_oracle_rng.py).
+template <class R> R gamma_mt_from(R d, R c, R K, R Z0, R U0, uint64_t seed, uint32_t filter,
                                    uint32_t t, uint32_t j, uint32_t purpose, int* fail) {
   for (uint32_t attempt = 0; attempt < 16; ++attempt) {
     R Z = Z0, U = U0;
@@ -319,33 +370,30 @@ template <class R> R gamma_mt_from(R d, R c, R Z0, R U0, uint64_t seed, uint32_t
       Z = bm_normal<R>(w);
       U = extra_uniform<R>(w);
     }
-    R cz = c * Z;
-    R v = (R)1 + cz;
+    R v = std::fma(c, Z, (R)1);
     if (!(v > (R)0)) continue;
     R vv = v * v;
     R v3 = vv * v;
     R Z2 = Z * Z;
     R z4 = Z2 * Z2;
-    R sq = K<R>::MT_SQUEEZE * z4;
-    R thr = (R)1 - sq;
+    R thr = std::fma(-K, z4, (R)1);
     if (U < thr) return d * v3;
     R lhs = det_log(U);
     R a1 = (R)1 - v3;
     R a2 = det_log(v3);
     R a3 = a1 + a2;
-    R a4 = d * a3;
     R a5 = (R)0.5 * Z2;
-    R rhs = a5 + a4;
+    R rhs = std::fma(d, a3, a5);
     if (lhs < rhs) return d * v3;
   }
   *fail = 1;
   return d;
 }
 
-template <class R> R gamma_mt(R d, R c, uint64_t seed, uint32_t filter, uint32_t t,
+template <class R> R gamma_mt(R d, R c, R K, uint64_t seed, uint32_t filter, uint32_t t,
                               uint32_t j, uint32_t purpose, int* fail) {
   W4 w = draw(seed, filter, t, j, purpose, 0);
-  return gamma_mt_from<R>(d, c, bm_normal<R>(w), extra_uniform<R>(w), seed, filter, t, j,
+  return gamma_mt_from<R>(d, c, K, bm_normal<R>(w), extra_uniform<R>(w), seed, filter, t, j,
                           purpose, fail);
 }
 
@@ -359,7 +407,6 @@ template <class R> void theta_draws(uint64_t seed, uint32_t filter, uint32_t t, 
   *Ut = extra_uniform<R>(B);
 }
 
-template float det_log<float>(float);
 template double det_log<double>(double);
 template float det_exp_core<float>(float);
 template double det_exp_core<double>(double);
@@ -367,12 +414,14 @@ template float det_cos2pi<float>(float);
 template double det_cos2pi<double>(double);
 template uint64_t quant_exp<float>(float, int, float*);
 template uint64_t quant_exp<double>(double, int, double*);
-template float gamma_mt<float>(float, float, uint64_t, uint32_t, uint32_t, uint32_t, uint32_t, int*);
-template double gamma_mt<double>(double, double, uint64_t, uint32_t, uint32_t, uint32_t, uint32_t, int*);
-template float gamma_mt_from<float>(float, float, float, float, uint64_t, uint32_t, uint32_t,
-                                    uint32_t, uint32_t, int*);
-template double gamma_mt_from<double>(double, double, double, double, uint64_t, uint32_t,
-                                      uint32_t, uint32_t, uint32_t, int*);
+template float gamma_mt<float>(float, float, float, uint64_t, uint32_t, uint32_t, uint32_t,
+                               uint32_t, int*);
+template double gamma_mt<double>(double, double, double, uint64_t, uint32_t, uint32_t, uint32_t,
+                                 uint32_t, int*);
+template float gamma_mt_from<float>(float, float, float, float, float, uint64_t, uint32_t,
+                                    uint32_t, uint32_t, uint32_t, int*);
+template double gamma_mt_from<double>(double, double, double, double, double, uint64_t,
+                                      uint32_t, uint32_t, uint32_t, uint32_t, int*);
 template void det_sincos2pi<float>(float, float*, float*);
 template void det_sincos2pi<double>(double, double*, double*);
 template void theta_draws<float>(uint64_t, uint32_t, uint32_t, uint32_t, float*, float*, float*,

@@ -117,6 +117,60 @@ def test_gamma_marsaglia_tsang(orc, dtype, a):
     assert abs(g.mean() - a) < 5 * np.sqrt(a / g.size)
 
 
+def _g_minus(d, u):
+    """1 - exp(g) for Z = 3 sqrt(d) u: g = d h(u), h(u) = 3 log(1+u) - 3u + 3u^2/2 - u^3 is the
+    log acceptance ratio of Marsaglia-Tsang with v = (1 + u)^3 (u = c Z, c = 1/sqrt(9d))."""
+    h = 3 * np.log1p(u) - 3 * u + 1.5 * u * u - u ** 3
+    return -np.expm1(d * h)
+
+
+def test_gamma_squeeze_is_a_lower_bound(orc):
+    """The squeeze U < 1 - K Z^4 may only accept what the full test accepts:
+    1 - K Z^4 <= exp(g(Z)) for every Z with v > 0, at every shape.  K = 0.0331 (2/3) / d is
+    Marsaglia & Tsang's 0.0331 at d = 2/3, and the supremum of (1 - e^g) d / Z^4 over Z is
+    largest there (0.022049) and falls toward 1/108 as d grows."""
+    u = np.concatenate([np.linspace(-1 + 1e-9, -1e-3, 400_001), np.linspace(1e-3, 30, 200_001)])
+    worst = 0.0
+    for a in np.concatenate([[1.0, 1.1, 1.5, 2.0, 3.0, 3.5, 5.0], np.geomspace(5.5, 1e6, 60)]):
+        d, c, K = orc.mt_constants(a)
+        assert d == a - float.fromhex("0x1.5555555555555p-2")
+        assert K == float.fromhex("0x1.698a4eea9073cp-6") / d
+        Z4 = (u / c) ** 4
+        ratio = _g_minus(d, u) / (K * Z4)
+        worst = max(worst, ratio.max())
+        assert ratio.max() <= 1.0 - 1e-4, (a, ratio.max())
+    assert worst > 0.99  # the bound is tight at a = 1 (Marsaglia-Tsang's own constant)
+
+
+def test_gamma_accepts_exactly_the_full_test(orc):
+    """Attempt 0 of the sampler (binary64) against the plain Marsaglia-Tsang full test written
+    out here with exact rationals for the fused steps: a draw the full test accepts returns
+    d v^3 of that attempt, one it rejects returns something else (a later attempt)."""
+    from fractions import Fraction as F
+    import math
+    n = 20_000
+    for a in (1.0, 1.3, 3.5, 53.5):
+        d, c, K = orc.mt_constants(a)
+        g, fail = orc.gammas(a, 11, 2, 7, orc.P_GAMMA_TAU, n, np.float64)
+        assert fail == 0
+        Z = orc.normals(11, 2, 7, orc.P_GAMMA_TAU, n, np.float64)
+        w = orc.draws(11, 2, 7, 0, n, orc.P_GAMMA_TAU)
+        U = (2.0 * w[:, 3].astype(np.float64) + 1.0) * 2.0**-33
+        acc = 0
+        for j in range(n):
+            v = float(F(c) * F(float(Z[j])) + 1)          # fma(c, Z, 1)
+            if not v > 0:
+                continue
+            v3 = (v * v) * v
+            full = math.log(U[j]) < Z[j] * Z[j] / 2 + d * (1 - v3 + math.log(v3))
+            if full:
+                acc += 1
+                assert g[j] == d * v3, (a, j)
+            else:
+                assert g[j] != d * v3, (a, j)
+        assert acc > 0.9 * n
+
+
 def test_streams_differ_by_purpose_and_time(orc):
     a = orc.draws(9, 0, 0, 0, 1024, orc.P_STATE)
     b = orc.draws(9, 0, 0, 0, 1024, orc.P_GAMMA_SIGMA)
