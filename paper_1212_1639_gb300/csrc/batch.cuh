@@ -180,7 +180,7 @@ struct BatchSmem {
   ES fold[32];                   // log-ML tile partials, lane-strided (group rank 0)
   uint32_t run[BB_MAX_RUNS][3];
   GammaItem<R> wq[NT / 32][WQ_CAP];   // per-warp queues of deferred gamma draws
-  double c[4];
+  double c[6];
   uint32_t nruns;
   // read by the other CTAs of a group (distributed shared memory)
   R gmax;                        // this CTA's maximum of l
@@ -219,11 +219,11 @@ __device__ __forceinline__ void batch_filter(const BatchArgs<R>& a, const BatchI
   const double y = item.y;
   const R yr = (R)y;
   if (threadIdx.x == 0) {
-    // Marsaglia-Tsang (d, c) of the shapes a0 + (t+1)/2
-    double ds, cs, dt, ct;
-    mt_constants(F->a_sigma + 0.5 * (double)(t + 1), &ds, &cs);
-    mt_constants(F->a_tau + 0.5 * (double)(t + 1), &dt, &ct);
-    sm.c[0] = ds; sm.c[1] = cs; sm.c[2] = dt; sm.c[3] = ct;
+    // Marsaglia-Tsang constants of the shapes a0 + (t+1)/2
+    double ds, cs, ks, dt, ct, kt;
+    mt_constants(F->a_sigma + 0.5 * (double)(t + 1), &ds, &cs, &ks);
+    mt_constants(F->a_tau + 0.5 * (double)(t + 1), &dt, &ct, &kt);
+    sm.c[0] = ds; sm.c[1] = cs; sm.c[2] = dt; sm.c[3] = ct; sm.c[4] = ks; sm.c[5] = kt;
   }
   if (rank == 0 && threadIdx.x < 32) sm.fold[threadIdx.x].zero();
   bool fail = false;
@@ -546,12 +546,13 @@ __device__ __forceinline__ void batch_filter(const BatchArgs<R>& a, const BatchI
   // round-robin over the group); draws that miss the squeeze go to the
   // warp's queue, which the warp finishes 32 at a time
   const R ds = (R)sm.c[0], cs = (R)sm.c[1], dt = (R)sm.c[2], ct = (R)sm.c[3];
+  const R ks = (R)sm.c[4], kt = (R)sm.c[5];
   GammaItem<R>* const wq = sm.wq[warp];
   uint32_t qn = 0;  // warp-uniform
   auto finish = [&](const GammaItem<R>& itm) {
     const bool sig = itm.which == 0;
-    const R G2 = gamma_mt_from<R>(sig ? ds : dt, sig ? cs : ct, itm.Z, itm.U, seed, fid, t,
-                                  itm.j, sig ? P_GAMMA_SIGMA : P_GAMMA_TAU, &fail);
+    const R G2 = gamma_mt_from<R>(sig ? ds : dt, sig ? cs : ct, sig ? ks : kt, itm.Z, itm.U, seed,
+                                  fid, t, itm.j, sig ? P_GAMMA_SIGMA : P_GAMMA_TAU, &fail);
     const R v = SuffOps<R>::ig(itm.b, G2);
     if (sig) dst.s2[off + itm.j] = v;
     else dst.t2[off + itm.j] = v;
@@ -575,18 +576,18 @@ __device__ __forceinline__ void batch_filter(const BatchArgs<R>& a, const BatchI
     R Zs = 0, Us = 0, Zt = 0, Ut = 0;
     if (j < n) {
       const R xa = cur.x, sa = cur.s2, ta = cur.t2;
+      // V and mu share one correctly rounded reciprocal of s
       const R s = sa + ta;
+      const R ri = (R)1 / s;
       const R p = sa * ta;
-      const R V = p / s;
-      const R n1 = xa * sa;
+      const R V = p * ri;
       const R n2 = yr * ta;
-      const R nn = n1 + n2;
-      const R mu = nn / s;
+      const R nn = fmaR(xa, sa, n2);
+      const R mu = nn * ri;
       const R sv = sqrt(V);
       R Z;
       theta_draws<R>(seed, fid, t, (uint32_t)j, &Z, &Zs, &Us, &Zt, &Ut);
-      const R xz = sv * Z;
-      const R xj = mu + xz;
+      const R xj = fmaR(sv, Z, mu);
       const uint64_t d = off + j;
       dst.x[d] = xj;
       if (learn) {
@@ -597,9 +598,9 @@ __device__ __forceinline__ void batch_filter(const BatchArgs<R>& a, const BatchI
         dst.bs[d] = bsn;
         dst.bt[d] = btn;
         R Gs, Gt;
-        if (gamma_mt_squeeze<R>(ds, cs, Zs, Us, &Gs)) dst.s2[d] = SuffOps<R>::ig(bsn, Gs);
+        if (gamma_mt_squeeze<R>(ds, cs, ks, Zs, Us, &Gs)) dst.s2[d] = SuffOps<R>::ig(bsn, Gs);
         else defer_s = true;
-        if (gamma_mt_squeeze<R>(dt, ct, Zt, Ut, &Gt)) dst.t2[d] = SuffOps<R>::ig(btn, Gt);
+        if (gamma_mt_squeeze<R>(dt, ct, kt, Zt, Ut, &Gt)) dst.t2[d] = SuffOps<R>::ig(btn, Gt);
         else defer_t = true;
       } else {
         dst.s2[d] = sa;
@@ -608,9 +609,13 @@ __device__ __forceinline__ void batch_filter(const BatchArgs<R>& a, const BatchI
         dst.bt[d] = cur.bt;
       }
     }
-    wq_push(wq, qn, defer_s, GammaItem<R>{bsn, Zs, Us, (uint32_t)j, 0u}, lane);
-    wq_push(wq, qn, defer_t, GammaItem<R>{btn, Zt, Ut, (uint32_t)j, 1u}, lane);
-    wq_drain(wq, qn, 32u, lane, finish);
+    // queue the draws that missed the squeeze (rare); the warp finishes them
+    // 32 at a time
+    if (__any_sync(0xffffffffu, defer_s || defer_t)) {
+      wq_push(wq, qn, defer_s, GammaItem<R>{bsn, Zs, Us, (uint32_t)j, 0u}, lane);
+      wq_push(wq, qn, defer_t, GammaItem<R>{btn, Zt, Ut, (uint32_t)j, 1u}, lane);
+      wq_drain(wq, qn, 32u, lane, finish);
+    }
     cur = nxt;
   }
   wq_drain(wq, qn, 1u, lane, finish);
@@ -691,7 +696,7 @@ k_batch_cycle(BatchArgs<R> a) {
 // and arithmetic as k_init.
 template <class R>
 __global__ void __launch_bounds__(BB) k_batch_init(BatchArgs<R> a) {
-  __shared__ double s_c[5];
+  __shared__ double s_c[7];
   const uint32_t count = *a.count;
   for (uint32_t w = blockIdx.x; w < count; w += gridDim.x) {
     const BatchFilter* rec = &a.inits[w].rec;
@@ -702,11 +707,12 @@ __global__ void __launch_bounds__(BB) k_batch_init(BatchArgs<R> a) {
     __syncthreads();
     if (threadIdx.x == 0) {
       *F = *rec;
-      double ds, cs, dt, ct;
-      mt_constants(rec->a_sigma, &ds, &cs);
-      mt_constants(rec->a_tau, &dt, &ct);
+      double ds, cs, ks, dt, ct, kt;
+      mt_constants(rec->a_sigma, &ds, &cs, &ks);
+      mt_constants(rec->a_tau, &dt, &ct, &kt);
       s_c[0] = ds; s_c[1] = cs; s_c[2] = dt; s_c[3] = ct;
       s_c[4] = sqrt(rec->x0_var);
+      s_c[5] = ks; s_c[6] = kt;
     }
     __syncthreads();
     const StateV<R> st = a.st[0];
@@ -727,8 +733,10 @@ __global__ void __launch_bounds__(BB) k_batch_init(BatchArgs<R> a) {
         st.t2[g] = (R)rec->tau2;
         continue;
       }
-      const R Gs = gamma_mt<R>((R)s_c[0], (R)s_c[1], seed, fid, 0, (uint32_t)j, P_INIT_SIGMA, &fail);
-      const R Gt = gamma_mt<R>((R)s_c[2], (R)s_c[3], seed, fid, 0, (uint32_t)j, P_INIT_TAU, &fail);
+      const R Gs = gamma_mt<R>((R)s_c[0], (R)s_c[1], (R)s_c[5], seed, fid, 0, (uint32_t)j,
+                               P_INIT_SIGMA, &fail);
+      const R Gt = gamma_mt<R>((R)s_c[2], (R)s_c[3], (R)s_c[6], seed, fid, 0, (uint32_t)j,
+                               P_INIT_TAU, &fail);
       st.s2[g] = SuffOps<R>::ig(bs0, Gs);
       st.t2[g] = SuffOps<R>::ig(bt0, Gt);
     }

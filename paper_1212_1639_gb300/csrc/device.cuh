@@ -7,7 +7,10 @@
 //
 // Determinism contract.  The library is compiled with -fmad=false, IEEE
 // division and square root, and no flush-to-zero, and every floating-point
-// expression below is written as one IEEE operation per statement.  Given the
+// expression below is written as one IEEE operation per statement: a
+// separately rounded add, multiply, divide or square root, or an explicit
+// fused multiply-add (__fmaf_rn / __fma_rn / fma.rn.f32x2) where the
+// definition fuses.  Given the
 // same inputs the results are therefore bit-identical on any IEEE-754
 // machine that evaluates the same operation sequence, which is what makes the
 // quantised CDF (and hence every ancestor index) a deterministic function of
@@ -95,9 +98,14 @@ __device__ __forceinline__ double unif_f64_32(uint32_t w) {
 
 // ---------------------------------------------------------------------------
 // Deterministic elementary functions.
-//  log x : x = f 2^e, f in [sqrt(1/2), sqrt(2)); log f = 2 atanh(z),
-//          z = (f-1)/(f+1), series through z^(2K)/(2K+1) (K = 4 / 10);
-//          log x = e ln2 + log f.
+//  log x : x = f 2^e, f in [sqrt(1/2), sqrt(2)).
+//          binary64: log f = 2 atanh(z), z = (f-1)/(f+1), series through
+//          z^20/21; log x = e ln2 + log f.
+//          binary32 (no division): u = f - 1 (exact), log f = u + u^2 q(u)
+//          with q of degree 8, coefficients fitted for the least maximum
+//          relative error of log(1 + u) on [sqrt(1/2) - 1, sqrt(2) - 1] and
+//          rounded to binary32 (at most 0.93 ulp over all binary32);
+//          log x = e ln2_hi + (e ln2_lo + log f), two fused multiply-adds.
 //  exp r : Taylor polynomial through r^D/D! (D = 7 / 13) on a Cody-Waite
 //          reduced argument.
 //  cos(2 pi u): octant reduction of u in [0,1] and Taylor polynomials of cos
@@ -112,7 +120,6 @@ template <> struct Cst<float> {
   static constexpr float INV_LN2 = 0x1.715476p+0f;
   static constexpr float TWO_PI = 0x1.921fb6p+2f;
   static constexpr float SQRT_HALF = 0x1.6a09e6p-1f;
-  static constexpr float SQUEEZE = 0x1.0f27bcp-5f;  // Marsaglia-Tsang 0.0331
 };
 template <> struct Cst<double> {
   static constexpr double LN2 = 0x1.62e42fefa39efp-1;
@@ -121,7 +128,6 @@ template <> struct Cst<double> {
   static constexpr double INV_LN2 = 0x1.71547652b82fep+0;
   static constexpr double TWO_PI = 0x1.921fb54442d18p+2;
   static constexpr double SQRT_HALF = 0x1.6a09e667f3bcdp-1;
-  static constexpr double SQUEEZE = 0x1.0f27bb2fec56dp-5;
 };
 
 // Exact small-integer to binary32 conversion (|e| < 2^22) by the 1.5 * 2^23 bias.
@@ -129,34 +135,46 @@ __device__ __forceinline__ float small_int_to_f32(int e) {
   return __int_as_float(0x4B400000 + e) - 12582912.0f;
 }
 
-// log of a positive normal number.
+// q(u) of the binary32 log: coefficients of u^0 .. u^8
+__device__ __forceinline__ float logq_f(int j) {
+  constexpr float C[9] = {-0x1.fffff8p-2f, 0x1.55555p-2f,   -0x1.000426p-2f,
+                          0x1.99a3f6p-3f,  -0x1.542766p-3f, 0x1.22715ep-3f,
+                          -0x1.0f3756p-3f, 0x1.0849bep-3f,  -0x1.38339ap-4f};
+  return C[j];
+}
+// reduction of the binary32 log: x = f 2^e with f = as_float(m) in
+// [sqrt(1/2), sqrt(2)) (subnormals scaled by 2^23 first)
+__device__ __forceinline__ uint32_t log_reduce(float x, int* e_out) {
+  uint32_t b = __float_as_uint(x);
+  int e = 0;
+  if ((b & 0x7f800000u) == 0) {  // subnormal (or zero): scale by 2^23, exact
+    b = __float_as_uint(__fmul_rn(x, 0x1p23f));
+    e = -23;
+  }
+  e += (int)(b >> 23) - 127;
+  uint32_t m = (b & 0x7fffffu) | 0x3f800000u;  // [1, 2)
+  if (m >= 0x3fb504f3u) {                       // at or above sqrt(2) rounded: halve
+    m -= 0x00800000u;
+    e += 1;
+  }
+  *e_out = e;
+  return m;
+}
+
+// log of x > 0 (normal or subnormal); +inf and NaN are returned unchanged.
 __device__ __forceinline__ float det_log(float x) {
   int e;
-  float f;
-  const uint32_t b = __float_as_uint(x);
-  if ((b & 0x7f800000u) != 0) {  // normal: frexp by bit manipulation
-    e = (int)(b >> 23) - 126;
-    f = __uint_as_float((b & 0x807fffffu) | 0x3f000000u);
-  } else {
-    f = frexpf(x, &e);
-  }
-  if (f < Cst<float>::SQRT_HALF) {
-    f = f * 2.0f;
-    e = e - 1;
-  }
-  const float num = f - 1.0f;
-  const float den = f + 1.0f;
-  const float z = num / den;
-  const float z2 = z * z;
-  float p = 0x1.c71c72p-4f;              // 1/9
-  p = __fmaf_rn(p, z2, 0x1.24924ap-3f);  // 1/7
-  p = __fmaf_rn(p, z2, 0x1.99999ap-3f);  // 1/5
-  p = __fmaf_rn(p, z2, 0x1.555556p-2f);  // 1/3
-  p = __fmaf_rn(p, z2, 1.0f);
-  const float two_z = z * 2.0f;
-  const float lf = two_z * p;
-  const float el = small_int_to_f32(e) * Cst<float>::LN2;
-  return el + lf;
+  const uint32_t m = log_reduce(x, &e);
+  const float u = __fsub_rn(__uint_as_float(m), 1.0f);  // exact
+  float q = logq_f(8);
+#pragma unroll
+  for (int j = 7; j >= 0; --j) q = __fmaf_rn(q, u, logq_f(j));
+  const float u2 = __fmul_rn(u, u);
+  const float lf = __fmaf_rn(u2, q, u);
+  const float ef = small_int_to_f32(e);
+  const float lo = __fmaf_rn(ef, Cst<float>::LN2_LO, lf);
+  const float r = __fmaf_rn(ef, Cst<float>::LN2_HI, lo);
+  return x < INFINITY ? r : x;
 }
 __device__ __forceinline__ double det_log(double x) {
   int e;
@@ -378,12 +396,20 @@ __device__ __forceinline__ double bm_normal(const U4& w, double) { return bm_nor
 __device__ __forceinline__ float extra_uniform(const U4& w, float) { return unif_f32(w.c); }
 __device__ __forceinline__ double extra_uniform(const U4& w, double) { return unif_f64_32(w.d); }
 
+__device__ __forceinline__ float fmaR(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fmaR(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 // Gamma(a, 1) for a >= 1 by Marsaglia & Tsang (2000), d = a - 1/3,
-// c = 1/sqrt(9d).  Attempt k uses draw (purpose, k); after 16 rejections
-// *fail is set and d is returned.
+// c = 1/sqrt(9d), v = fma(c, Z, 1): accept d v^3 when v > 0 and either the
+// squeeze U < fma(-K, Z^4, 1) holds (K = 0.0331 (2/3) / d, a bound that
+// implies the full test for every d >= 2/3 and equals Marsaglia & Tsang's
+// 0.0331 at d = 2/3) or the full test
+// log U < fma(d, (1 - v^3) + log v^3, Z^2 / 2) does.  Attempt k uses draw
+// (purpose, k); after 16 rejections *fail is set and d is returned.
 template <class R>
-__device__ __forceinline__ R gamma_mt_from(R d, R c, R Z0, R U0, uint64_t seed, uint32_t filter,
-                                           uint32_t t, uint32_t j, uint32_t purpose, bool* fail) {
+__device__ __forceinline__ R gamma_mt_from(R d, R c, R K, R Z0, R U0, uint64_t seed,
+                                           uint32_t filter, uint32_t t, uint32_t j,
+                                           uint32_t purpose, bool* fail) {
   for (uint32_t attempt = 0; attempt < 16; ++attempt) {
     R Z = Z0, U = U0;
     if (attempt > 0) {
@@ -391,54 +417,49 @@ __device__ __forceinline__ R gamma_mt_from(R d, R c, R Z0, R U0, uint64_t seed, 
       Z = bm_normal(w, (R)0);
       U = extra_uniform(w, (R)0);
     }
-    const R cz = c * Z;
-    const R v = (R)1 + cz;
+    const R v = fmaR(c, Z, (R)1);
     if (!(v > (R)0)) continue;
     const R vv = v * v;
     const R v3 = vv * v;
     const R Z2 = Z * Z;
     const R z4 = Z2 * Z2;
-    const R sq = Cst<R>::SQUEEZE * z4;
-    const R thr = (R)1 - sq;
+    const R thr = fmaR(-K, z4, (R)1);
     if (U < thr) return d * v3;
     const R lhs = det_log(U);
     const R a1 = (R)1 - v3;
     const R a2 = det_log(v3);
     const R a3 = a1 + a2;
-    const R a4 = d * a3;
     const R a5 = (R)0.5 * Z2;
-    const R rhs = a5 + a4;
+    const R rhs = fmaR(d, a3, a5);
     if (lhs < rhs) return d * v3;
   }
   *fail = true;
   return d;
 }
 // Marsaglia-Tsang attempt 0 restricted to the squeeze: returns true and
-// *G = d v^3 when v > 0 and U < 1 - 0.0331 Z^4 (the same test, in the same
+// *G = d v^3 when v > 0 and U < fma(-K, Z^4, 1) (the same test, in the same
 // order, as the first step of gamma_mt_from); otherwise the draw must be
 // finished by gamma_mt_from with the same (Z, U).
 template <class R>
-__device__ __forceinline__ bool gamma_mt_squeeze(R d, R c, R Z, R U, R* G) {
-  const R cz = c * Z;
-  const R v = (R)1 + cz;
+__device__ __forceinline__ bool gamma_mt_squeeze(R d, R c, R K, R Z, R U, R* G) {
+  const R v = fmaR(c, Z, (R)1);
   if (!(v > (R)0)) return false;
   const R vv = v * v;
   const R v3 = vv * v;
   const R Z2 = Z * Z;
   const R z4 = Z2 * Z2;
-  const R sq = Cst<R>::SQUEEZE * z4;
-  const R thr = (R)1 - sq;
+  const R thr = fmaR(-K, z4, (R)1);
   if (!(U < thr)) return false;
   *G = d * v3;
   return true;
 }
 
 template <class R>
-__device__ __forceinline__ R gamma_mt(R d, R c, uint64_t seed, uint32_t filter, uint32_t t,
+__device__ __forceinline__ R gamma_mt(R d, R c, R K, uint64_t seed, uint32_t filter, uint32_t t,
                                       uint32_t j, uint32_t purpose, bool* fail) {
   const U4 w = draw(seed, filter, t, j, purpose, 0);
-  return gamma_mt_from<R>(d, c, bm_normal(w, (R)0), extra_uniform(w, (R)0), seed, filter, t, j,
-                          purpose, fail);
+  return gamma_mt_from<R>(d, c, K, bm_normal(w, (R)0), extra_uniform(w, (R)0), seed, filter, t,
+                          j, purpose, fail);
 }
 
 // The draws of one propagation step for slot j: A = (j, t, STATE, 0) gives
@@ -493,6 +514,17 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
 __device__ __forceinline__ float2 add2(float2 a, float2 b) {
   return make_float2(__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y));
 }
+// A paired addition (FADD2).  Only for operands that are not the result of a
+// paired multiplication (loads, integer-built values, fused multiply-adds),
+// which ptxas could otherwise contract into one FFMA2.
+__device__ __forceinline__ float2 addp(float2 a, float2 b) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+      "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "add.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
 __device__ __forceinline__ float2 sub2(float2 a, float2 b) {
   return make_float2(__fsub_rn(a.x, b.x), __fsub_rn(a.y, b.y));
 }
@@ -516,43 +548,17 @@ __device__ __forceinline__ float2 unif_f32_2(uint32_t w0, uint32_t w1) {
 // det_log on two positive values
 __device__ __forceinline__ float2 det_log2(float2 x) {
   int e0, e1;
-  float f0, f1;
-  {
-    const uint32_t b = __float_as_uint(x.x);
-    if ((b & 0x7f800000u) != 0) {
-      e0 = (int)(b >> 23) - 126;
-      f0 = __uint_as_float((b & 0x807fffffu) | 0x3f000000u);
-    } else {
-      f0 = frexpf(x.x, &e0);
-    }
-  }
-  {
-    const uint32_t b = __float_as_uint(x.y);
-    if ((b & 0x7f800000u) != 0) {
-      e1 = (int)(b >> 23) - 126;
-      f1 = __uint_as_float((b & 0x807fffffu) | 0x3f000000u);
-    } else {
-      f1 = frexpf(x.y, &e1);
-    }
-  }
-  float2 f = make_float2(f0, f1);
-  const float2 f2 = mul2(f, splat2(2.0f));
-  if (f.x < Cst<float>::SQRT_HALF) { f.x = f2.x; e0 = e0 - 1; }
-  if (f.y < Cst<float>::SQRT_HALF) { f.y = f2.y; e1 = e1 - 1; }
-  const float2 num = sub2(f, splat2(1.0f));
-  const float2 den = add2(f, splat2(1.0f));
-  const float2 z = make_float2(num.x / den.x, num.y / den.y);
-  const float2 z2 = mul2(z, z);
-  float2 p = splat2(0x1.c71c72p-4f);
-  p = fma2(p, z2, splat2(0x1.24924ap-3f));
-  p = fma2(p, z2, splat2(0x1.99999ap-3f));
-  p = fma2(p, z2, splat2(0x1.555556p-2f));
-  p = fma2(p, z2, splat2(1.0f));
-  const float2 two_z = mul2(z, splat2(2.0f));
-  const float2 lf = mul2(two_z, p);
-  const float2 el = mul2(make_float2(small_int_to_f32(e0), small_int_to_f32(e1)),
-                         splat2(Cst<float>::LN2));
-  return add2(el, lf);
+  const uint32_t m0 = log_reduce(x.x, &e0), m1 = log_reduce(x.y, &e1);
+  const float2 u = addp(make_float2(__uint_as_float(m0), __uint_as_float(m1)), splat2(-1.0f));
+  float2 q = splat2(logq_f(8));
+#pragma unroll
+  for (int j = 7; j >= 0; --j) q = fma2(q, u, splat2(logq_f(j)));
+  const float2 u2 = mul2(u, u);
+  const float2 lf = fma2(u2, q, u);
+  const float2 ef = make_float2(small_int_to_f32(e0), small_int_to_f32(e1));
+  const float2 lo = fma2(ef, splat2(Cst<float>::LN2_LO), lf);
+  const float2 r = fma2(ef, splat2(Cst<float>::LN2_HI), lo);
+  return make_float2(x.x < INFINITY ? r.x : x.x, x.y < INFINITY ? r.y : x.y);
 }
 
 __device__ __forceinline__ float2 cos_poly2(float2 x) {

@@ -57,9 +57,10 @@ struct Ctl {
   double est[8];          // t, x mean/var, sigma2 mean/var, tau2 mean/var, log_marglik
   // per-cycle constants written by k_weights (block 0) for k_propagate:
   double y;               // this cycle's observation y_{t+1}
-  double mtd[4];          // Marsaglia-Tsang (d, c) for sigma^2 and tau^2, binary64
+  double mtd[6];          // Marsaglia-Tsang d, c for sigma^2 and tau^2 ([0..3]) and the
+                          // squeeze coefficients K_sigma, K_tau ([4], [5]), binary64
   float yf;               // y rounded to binary32
-  float mtf[4];           // the same constants rounded to binary32
+  float mtf[6];           // the same constants rounded to binary32
   // resampling key constants written by k_partition (block 0) for k_merge:
   // T = Q_{n-1}, A (n or S_n) and the systematic offset r
   uint64_t keyT, keyA, keyR;
@@ -162,21 +163,28 @@ template <> struct SuffOps<float> {
   static __device__ __forceinline__ uint64_t from_prior(double b) {
     return __double2ull_rz(b * 0x1p32);
   }
+  // b + r^2 / 2 in 2^-32 fixed point: trunc(r^2 2^31), which is
+  // (r^2 / 2) 2^32 exactly; below 2^32 by one u32 truncation
+  static __device__ __forceinline__ uint64_t incr(float v) {
+    return v < 0x1p32f ? (uint64_t)__float2uint_rz(v) : f2u64_rz(v);
+  }
   static __device__ __forceinline__ uint64_t add_half_square(uint64_t b, float r, bool* fail) {
     const float r2 = r * r;
-    const float h = 0.5f * r2;
-    const float v = h * 0x1p32f;
+    const float v = r2 * 0x1p31f;
     if (!(v < 0x1p63f)) {
       *fail = true;
       return b;
     }
-    return b + f2u64_rz(v);
+    return b + incr(v);
   }
-  static __device__ __forceinline__ float ig(uint64_t b, float G) {
-    const float bf = u64_to_f32_rn(b);
-    const float bs = bf * 0x1p-32f;
-    return bs / G;
+  // b 2^-32 in binary32 from the two 32-bit halves, each converted to
+  // nearest, joined by one fused multiply-add
+  static __device__ __forceinline__ float bscale(uint64_t b) {
+    const float hi = __uint2float_rn((uint32_t)(b >> 32));
+    const float lo = __uint2float_rn((uint32_t)b);
+    return __fmaf_rn(lo, 0x1p-32f, hi);
   }
+  static __device__ __forceinline__ float ig(uint64_t b, float G) { return bscale(b) / G; }
 };
 template <> struct SuffOps<double> {
   static __device__ __forceinline__ double from_prior(double b) { return b; }
@@ -188,25 +196,45 @@ template <> struct SuffOps<double> {
   static __device__ __forceinline__ double ig(double b, double G) { return b / G; }
 };
 
-// (d, c) of Marsaglia-Tsang for shape a, in binary64.
-__device__ __forceinline__ void mt_constants(double a, double* d, double* c) {
+// Constants of Marsaglia-Tsang for shape a, in binary64: d = a - 1/3,
+// c = 1/sqrt(9 d) and the squeeze coefficient K = 0.0331 (2/3) / d, with
+// 0.0331 (2/3) = 331/15000 rounded to nearest.
+__device__ __forceinline__ void mt_constants(double a, double* d, double* c, double* K) {
   const double ONE_THIRD = 0x1.5555555555555p-2;
+  const double SQZ = 0x1.698a4eea9073cp-6;
   const double dd = a - ONE_THIRD;
   const double nine_d = 9.0 * dd;
   const double s = sqrt(nine_d);
   *d = dd;
   *c = 1.0 / s;
+  *K = SQZ / dd;
+}
+// This cycle's constants for the propagation (observation and the
+// Marsaglia-Tsang constants of the shapes a0 + (t+1)/2), in both precisions.
+__device__ __forceinline__ void write_cycle_constants(Ctl* c, double y, double a_sigma,
+                                                      double a_tau, uint32_t t1) {
+  double ds, cs, ks, dt, ct, kt;
+  mt_constants(a_sigma + 0.5 * (double)t1, &ds, &cs, &ks);
+  mt_constants(a_tau + 0.5 * (double)t1, &dt, &ct, &kt);
+  c->y = y;
+  c->yf = (float)y;
+  const double v[6] = {ds, cs, dt, ct, ks, kt};
+  for (int i = 0; i < 6; ++i) {
+    c->mtd[i] = v[i];
+    c->mtf[i] = (float)v[i];
+  }
 }
 
 template <class R, bool LEARN>
 __global__ void __launch_bounds__(BLOCK) k_init(FilterArgs<R> a) {
-  __shared__ double s_c[6];
+  __shared__ double s_c[7];
   if (threadIdx.x == 0) {
-    double ds, cs, dt, ct;
-    mt_constants(a.a_sigma, &ds, &cs);
-    mt_constants(a.a_tau, &dt, &ct);
+    double ds, cs, ks, dt, ct, kt;
+    mt_constants(a.a_sigma, &ds, &cs, &ks);
+    mt_constants(a.a_tau, &dt, &ct, &kt);
     s_c[0] = ds; s_c[1] = cs; s_c[2] = dt; s_c[3] = ct;
     s_c[4] = sqrt(a.x0_var);
+    s_c[5] = ks; s_c[6] = kt;
   }
   __syncthreads();
   const uint64_t j = (uint64_t)blockIdx.x * BLOCK + threadIdx.x;
@@ -227,8 +255,10 @@ __global__ void __launch_bounds__(BLOCK) k_init(FilterArgs<R> a) {
     return;
   }
   bool fail = false;
-  const R Gs = gamma_mt<R>((R)s_c[0], (R)s_c[1], a.seed, a.filter, 0, (uint32_t)j, P_INIT_SIGMA, &fail);
-  const R Gt = gamma_mt<R>((R)s_c[2], (R)s_c[3], a.seed, a.filter, 0, (uint32_t)j, P_INIT_TAU, &fail);
+  const R Gs = gamma_mt<R>((R)s_c[0], (R)s_c[1], (R)s_c[5], a.seed, a.filter, 0, (uint32_t)j,
+                          P_INIT_SIGMA, &fail);
+  const R Gt = gamma_mt<R>((R)s_c[2], (R)s_c[3], (R)s_c[6], a.seed, a.filter, 0, (uint32_t)j,
+                          P_INIT_TAU, &fail);
   st.s2[j] = SuffOps<R>::ig(bs0, Gs);
   st.t2[j] = SuffOps<R>::ig(bt0, Gt);
   if (fail) atomicOr(&a.ctl->err, ERR_NUMERIC);
@@ -279,18 +309,7 @@ __global__ void __launch_bounds__(BLOCK, sizeof(R) == 4 ? 8 : 4) k_weights(Filte
   if (threadIdx.x == 0) {
     const double y = a.y_src ? *a.y_src : a.y_val;
     s_y = (R)y;
-    if (blockIdx.x == 0) {
-      // this cycle's constants for k_propagate: observation and the
-      // Marsaglia-Tsang (d, c) of the shapes a0 + (t+1)/2
-      double ds, cs, dt, ct;
-      mt_constants(a.a_sigma + 0.5 * (double)(t + 1), &ds, &cs);
-      mt_constants(a.a_tau + 0.5 * (double)(t + 1), &dt, &ct);
-      Ctl* c = a.ctl;
-      c->y = y;
-      c->yf = (float)y;
-      c->mtd[0] = ds; c->mtd[1] = cs; c->mtd[2] = dt; c->mtd[3] = ct;
-      c->mtf[0] = (float)ds; c->mtf[1] = (float)cs; c->mtf[2] = (float)dt; c->mtf[3] = (float)ct;
-    }
+    if (blockIdx.x == 0) write_cycle_constants(a.ctl, y, a.a_sigma, a.a_tau, t + 1);
   }
   __syncthreads();
   const R yr = s_y;
@@ -1958,13 +1977,7 @@ __device__ void fold_cycle_warp(const FilterArgs<R>& a, uint32_t t) {
       __threadfence();
       c->maxenc = atomicExch(&c->maxenc_nx, ninf);
       const double y = a.y_nx_src ? *a.y_nx_src : a.y_nx_val;
-      double ds, cs, dt, ct;
-      mt_constants(a.a_sigma + 0.5 * (double)(t + 2), &ds, &cs);
-      mt_constants(a.a_tau + 0.5 * (double)(t + 2), &dt, &ct);
-      c->y = y;
-      c->yf = (float)y;
-      c->mtd[0] = ds; c->mtd[1] = cs; c->mtd[2] = dt; c->mtd[3] = ct;
-      c->mtf[0] = (float)ds; c->mtf[1] = (float)cs; c->mtf[2] = (float)dt; c->mtf[3] = (float)ct;
+      write_cycle_constants(c, y, a.a_sigma, a.a_tau, t + 2);
     } else {
       c->maxenc = ninf;
     }
@@ -2117,11 +2130,13 @@ __global__ void __launch_bounds__(BLOCK, 5) k_propagate(FilterArgs<R> a) {
   const StateV<R> src = (t & 1) ? a.st[1] : a.st[0];
   const StateV<R> dst = (t & 1) ? a.st[0] : a.st[1];
   const double y = c->y;
-  R yr, ds, cs, dt, ct;
+  R yr, ds, cs, dt, ct, ks, kt;
   if constexpr (sizeof(R) == 4) {
     yr = c->yf; ds = c->mtf[0]; cs = c->mtf[1]; dt = c->mtf[2]; ct = c->mtf[3];
+    ks = c->mtf[4]; kt = c->mtf[5];
   } else {
     yr = y; ds = c->mtd[0]; cs = c->mtd[1]; dt = c->mtd[2]; ct = c->mtd[3];
+    ks = c->mtd[4]; kt = c->mtd[5];
   }
   const int lane = threadIdx.x & 31;
   Item* const wq = s_q[threadIdx.x >> 5];
@@ -2161,8 +2176,8 @@ __global__ void __launch_bounds__(BLOCK, 5) k_propagate(FilterArgs<R> a) {
   bool badn = false;
   auto finish = [&](const Item& itm) {
     const bool sig = (itm.which & 1u) == 0;
-    const R G = gamma_mt_from<R>(sig ? ds : dt, sig ? cs : ct, itm.Z, itm.U, a.seed, a.filter, t,
-                                 itm.j, sig ? P_GAMMA_SIGMA : P_GAMMA_TAU, &fail);
+    const R G = gamma_mt_from<R>(sig ? ds : dt, sig ? cs : ct, sig ? ks : kt, itm.Z, itm.U, a.seed,
+                                 a.filter, t, itm.j, sig ? P_GAMMA_SIGMA : P_GAMMA_TAU, &fail);
     const R v = SuffOps<R>::ig(itm.b, G);
     if (sig) dst.s2[itm.j] = v;
     else dst.t2[itm.j] = v;
@@ -2184,18 +2199,18 @@ __global__ void __launch_bounds__(BLOCK, 5) k_propagate(FilterArgs<R> a) {
     R xj = 0, s2n = 0, t2n = 0;
     if (j < n) {
       const R xa = cur.x, sa = cur.s2, ta = cur.t2;
+      // V and mu share one correctly rounded reciprocal of s
       const R s = sa + ta;
+      const R ri = (R)1 / s;
       const R p = sa * ta;
-      const R V = p / s;
-      const R n1 = xa * sa;
+      const R V = p * ri;
       const R n2 = yr * ta;
-      const R nn = n1 + n2;
-      const R mu = nn / s;
+      const R nn = fmaR(xa, sa, n2);
+      const R mu = nn * ri;
       const R sv = sqrt(V);
       R Z;
       theta_draws_rk<R>(a.rk, a.filter, t, (uint32_t)j, &Z, &Zs, &Us, &Zt, &Ut);
-      const R xz = sv * Z;
-      xj = mu + xz;
+      xj = fmaR(sv, Z, mu);
       dst.x[j] = xj;
       if (LEARN) {
         const R rs = ResidObs<R>::f(y, yr, xj);
@@ -2205,9 +2220,9 @@ __global__ void __launch_bounds__(BLOCK, 5) k_propagate(FilterArgs<R> a) {
         dst.bs[j] = bsn;
         dst.bt[j] = btn;
         R Gs, Gt;
-        if (gamma_mt_squeeze<R>(ds, cs, Zs, Us, &Gs)) dst.s2[j] = s2n = SuffOps<R>::ig(bsn, Gs);
+        if (gamma_mt_squeeze<R>(ds, cs, ks, Zs, Us, &Gs)) dst.s2[j] = s2n = SuffOps<R>::ig(bsn, Gs);
         else defer_s = true;
-        if (gamma_mt_squeeze<R>(dt, ct, Zt, Ut, &Gt)) dst.t2[j] = t2n = SuffOps<R>::ig(btn, Gt);
+        if (gamma_mt_squeeze<R>(dt, ct, kt, Zt, Ut, &Gt)) dst.t2[j] = t2n = SuffOps<R>::ig(btn, Gt);
         else defer_t = true;
       } else {
         dst.s2[j] = s2n = sa;
@@ -2270,6 +2285,7 @@ __global__ void __launch_bounds__(BLOCK, 3) k_propagate2(FilterArgs<float> a) {
   const StateV<float> src = (t & 1) ? a.st[1] : a.st[0];
   const StateV<float> dst = (t & 1) ? a.st[0] : a.st[1];
   const float yr = c->yf, ds = c->mtf[0], cs = c->mtf[1], dt = c->mtf[2], ct = c->mtf[3];
+  const float ks = c->mtf[4], kt = c->mtf[5];
   const int lane = threadIdx.x & 31;
   Item* const wq = s_q[threadIdx.x >> 5];
   uint32_t qn = 0;  // warp-uniform
@@ -2308,9 +2324,9 @@ __global__ void __launch_bounds__(BLOCK, 3) k_propagate2(FilterArgs<float> a) {
   bool badn = false;
   auto finish = [&](const Item& itm) {
     const bool sig = (itm.which & 1u) == 0;
-    const float G = gamma_mt_from<float>(sig ? ds : dt, sig ? cs : ct, itm.Z, itm.U, a.seed,
-                                         a.filter, t, itm.j, sig ? P_GAMMA_SIGMA : P_GAMMA_TAU,
-                                         &fail);
+    const float G = gamma_mt_from<float>(sig ? ds : dt, sig ? cs : ct, sig ? ks : kt, itm.Z,
+                                         itm.U, a.seed, a.filter, t, itm.j,
+                                         sig ? P_GAMMA_SIGMA : P_GAMMA_TAU, &fail);
     const float v = SuffOps<float>::ig(itm.b, G);
     if (sig) dst.s2[itm.j] = v;
     else dst.t2[itm.j] = v;
@@ -2350,37 +2366,33 @@ __global__ void __launch_bounds__(BLOCK, 3) k_propagate2(FilterArgs<float> a) {
     if (__any_sync(0xffffffffu, v0)) {
       const float2 xa = make_float2(c0.x, c1.x), sa = make_float2(c0.s2, c1.s2);
       const float2 ta = make_float2(c0.t2, c1.t2);
-      const float2 sm = add2(sa, ta);
-      const float2 p = mul2(sa, ta);
-      const float2 V = make_float2(p.x / sm.x, p.y / sm.y);
-      const float2 m1 = mul2(xa, sa);
-      const float2 m2 = mul2(splat2(yr), ta);
-      const float2 nn = add2(m1, m2);
-      const float2 mu = make_float2(nn.x / sm.x, nn.y / sm.y);
+      // V and mu share one correctly rounded reciprocal of s = sigma^2 + tau^2
+      const float2 sm = addp(sa, ta);
+      const float2 ri = make_float2(__frcp_rn(sm.x), __frcp_rn(sm.y));
+      const float2 V = mul2(mul2(sa, ta), ri);
+      const float2 nn = fma2(xa, sa, mul2(splat2(yr), ta));
+      const float2 mu = mul2(nn, ri);
       const float2 sv = make_float2(sqrtf(V.x), sqrtf(V.y));
       float2 Z, Zs, Us, Zt, Ut;
       theta_draws2(a.rk, a.filter, t, (uint32_t)j0, (uint32_t)j1, &Z, &Zs, &Us, &Zt, &Ut);
-      const float2 xz = mul2(sv, Z);
-      const float2 xj = add2(mu, xz);
+      const float2 xj = fma2(sv, Z, mu);
       if (v0) dst.x[j0] = xj.x;
       if (v1) dst.x[j1] = xj.y;
       bool ds0 = false, dt0 = false, ds1 = false, dt1 = false;
       uint64_t bs0 = 0, bt0 = 0, bs1 = 0, bt1 = 0;
       if (LEARN) {
-        const float2 rs = sub2(splat2(yr), xj);
-        const float2 rt = sub2(xj, xa);
-        // b + (r^2 / 2) in 2^-32 fixed point, per SuffOps<float>::add_half_square
-        const float2 hs = mul2(splat2(0.5f), mul2(rs, rs));
-        const float2 ht = mul2(splat2(0.5f), mul2(rt, rt));
-        const float2 ws = mul2(hs, splat2(0x1p32f));
-        const float2 wt = mul2(ht, splat2(0x1p32f));
+        const float2 rs = addp(splat2(yr), make_float2(-xj.x, -xj.y));
+        const float2 rt = addp(xj, make_float2(-xa.x, -xa.y));
+        // b + r^2 / 2 in 2^-32 fixed point, per SuffOps<float>::add_half_square
+        const float2 ws = mul2(mul2(rs, rs), splat2(0x1p31f));
+        const float2 wt = mul2(mul2(rt, rt), splat2(0x1p31f));
         bool f0 = false, f1 = false;
         auto addb = [&](uint64_t b, float v, bool* f) -> uint64_t {
           if (!(v < 0x1p63f)) {
             *f = true;
             return b;
           }
-          return b + f2u64_rz(v);
+          return b + SuffOps<float>::incr(v);
         };
         bs0 = addb(c0.bs, ws.x, &f0);
         bt0 = addb(c0.bt, wt.x, &f0);
@@ -2390,33 +2402,38 @@ __global__ void __launch_bounds__(BLOCK, 3) k_propagate2(FilterArgs<float> a) {
         if (v0) { dst.bs[j0] = bs0; dst.bt[j0] = bt0; }
         if (v1) { dst.bs[j1] = bs1; dst.bt[j1] = bt1; }
         // Marsaglia-Tsang squeeze for sigma^2 (x lanes: slot j0, j1) and tau^2
-        const float2 czs = mul2(splat2(cs), Zs), czt = mul2(splat2(ct), Zt);
-        const float2 vs = add2(splat2(1.0f), czs), vt = add2(splat2(1.0f), czt);
+        const float2 vs = fma2(splat2(cs), Zs, splat2(1.0f)), vt = fma2(splat2(ct), Zt, splat2(1.0f));
         const float2 v3s = mul2(mul2(vs, vs), vs), v3t = mul2(mul2(vt, vt), vt);
         const float2 Z2s = mul2(Zs, Zs), Z2t = mul2(Zt, Zt);
-        const float2 thrs = sub2(splat2(1.0f), mul2(splat2(Cst<float>::SQUEEZE), mul2(Z2s, Z2s)));
-        const float2 thrt = sub2(splat2(1.0f), mul2(splat2(Cst<float>::SQUEEZE), mul2(Z2t, Z2t)));
+        const float2 thrs = fma2(splat2(-ks), mul2(Z2s, Z2s), splat2(1.0f));
+        const float2 thrt = fma2(splat2(-kt), mul2(Z2t, Z2t), splat2(1.0f));
         const float2 Gs = mul2(splat2(ds), v3s), Gt = mul2(splat2(dt), v3t);
         const bool as0 = vs.x > 0.0f && Us.x < thrs.x, as1 = vs.y > 0.0f && Us.y < thrs.y;
         const bool at0 = vt.x > 0.0f && Ut.x < thrt.x, at1 = vt.y > 0.0f && Ut.y < thrt.y;
-        // inverse gamma: (b 2^-32) / G, per SuffOps<float>::ig
-        const float2 bsf = mul2(make_float2(u64_to_f32_rn(bs0), u64_to_f32_rn(bs1)), splat2(0x1p-32f));
-        const float2 btf = mul2(make_float2(u64_to_f32_rn(bt0), u64_to_f32_rn(bt1)), splat2(0x1p-32f));
+        // inverse gamma: (b 2^-32) / G, per SuffOps<float>::ig.  The divisions
+        // run for every lane (no branch around them); a draw that missed the
+        // squeeze stores nothing here and is finished from the warp's queue.
+        const float2 bsf = fma2(make_float2(__uint2float_rn((uint32_t)bs0), __uint2float_rn((uint32_t)bs1)),
+                                splat2(0x1p-32f),
+                                make_float2(__uint2float_rn((uint32_t)(bs0 >> 32)),
+                                            __uint2float_rn((uint32_t)(bs1 >> 32))));
+        const float2 btf = fma2(make_float2(__uint2float_rn((uint32_t)bt0), __uint2float_rn((uint32_t)bt1)),
+                                splat2(0x1p-32f),
+                                make_float2(__uint2float_rn((uint32_t)(bt0 >> 32)),
+                                            __uint2float_rn((uint32_t)(bt1 >> 32))));
+        const float q0 = bsf.x / Gs.x, r0 = btf.x / Gt.x, q1 = bsf.y / Gs.y, r1 = btf.y / Gt.y;
+        ds0 = v0 && !as0; dt0 = v0 && !at0; ds1 = v1 && !as1; dt1 = v1 && !at1;
+        if (v0 && as0) dst.s2[j0] = q0;
+        if (v0 && at0) dst.t2[j0] = r0;
+        if (v1 && as1) dst.s2[j1] = q1;
+        if (v1 && at1) dst.t2[j1] = r1;
         // 1 for a deferred draw: the paired weight of that slot is discarded,
         // and a normal operand keeps the log and the division on their fast paths
-        float s20 = 1.0f, t20 = 1.0f, s21 = 1.0f, t21 = 1.0f;
-        if (v0) {
-          if (as0) dst.s2[j0] = s20 = bsf.x / Gs.x;
-          else ds0 = true;
-          if (at0) dst.t2[j0] = t20 = btf.x / Gt.x;
-          else dt0 = true;
-        }
-        if (v1) {
-          if (as1) dst.s2[j1] = s21 = bsf.y / Gs.y;
-          else ds1 = true;
-          if (at1) dst.t2[j1] = t21 = btf.y / Gt.y;
-          else dt1 = true;
-        }
+        const float s20 = as0 ? q0 : 1.0f, t20 = at0 ? r0 : 1.0f;
+        const float s21 = as1 ? q1 : 1.0f, t21 = at1 ? r1 : 1.0f;
+        // queue the draws that missed the squeeze (rare: K Z^4 is small for
+        // the shapes of a running filter); the warp finishes them 32 at a time
+        const bool any_def = __any_sync(0xffffffffu, ds0 || dt0 || ds1 || dt1);
         if constexpr (FUSE) {
           // both slots weighed paired; a slot with a deferred draw is weighed
           // by the drain round that finishes it (its sigma^2 item lies below
@@ -2424,17 +2441,22 @@ __global__ void __launch_bounds__(BLOCK, 3) k_propagate2(FilterArgs<float> a) {
           const float2 l = log_pred2(xj, make_float2(s20, s21), make_float2(t20, t21), yn);
           if (v0 && !ds0 && !dt0) keep_next(a.ell, j0, l.x, mxn, badn);
           if (v1 && !ds1 && !dt1) keep_next(a.ell, j1, l.y, mxn, badn);
-          wq_push(wq, qn, ds0, Item{bs0, Zs.x, Us.x, (uint32_t)j0, 2u}, lane);
-          wq_push(wq, qn, dt0, Item{bt0, Zt.x, Ut.x, (uint32_t)j0, ds0 ? 1u : 3u}, lane);
-          wq_push(wq, qn, ds1, Item{bs1, Zs.y, Us.y, (uint32_t)j1, 2u}, lane);
-          wq_push(wq, qn, dt1, Item{bt1, Zt.y, Ut.y, (uint32_t)j1, ds1 ? 1u : 3u}, lane);
-          wq_drain_post(wq, qn, 32u, lane, finish, weigh_late);
+          if (any_def) {
+            wq_push(wq, qn, ds0, Item{bs0, Zs.x, Us.x, (uint32_t)j0, 2u}, lane);
+            wq_push(wq, qn, dt0, Item{bt0, Zt.x, Ut.x, (uint32_t)j0, ds0 ? 1u : 3u}, lane);
+            wq_push(wq, qn, ds1, Item{bs1, Zs.y, Us.y, (uint32_t)j1, 2u}, lane);
+            wq_push(wq, qn, dt1, Item{bt1, Zt.y, Ut.y, (uint32_t)j1, ds1 ? 1u : 3u}, lane);
+            wq_drain_post(wq, qn, 32u, lane, finish, weigh_late);
+          }
         } else {
-          wq_push(wq, qn, ds0, Item{bs0, Zs.x, Us.x, (uint32_t)j0, 0u}, lane);
-          wq_push(wq, qn, dt0, Item{bt0, Zt.x, Ut.x, (uint32_t)j0, 1u}, lane);
-          wq_push(wq, qn, ds1, Item{bs1, Zs.y, Us.y, (uint32_t)j1, 0u}, lane);
-          wq_push(wq, qn, dt1, Item{bt1, Zt.y, Ut.y, (uint32_t)j1, 1u}, lane);
-          wq_drain(wq, qn, 32u, lane, finish);
+          (void)s20; (void)t20; (void)s21; (void)t21;
+          if (any_def) {
+            wq_push(wq, qn, ds0, Item{bs0, Zs.x, Us.x, (uint32_t)j0, 0u}, lane);
+            wq_push(wq, qn, dt0, Item{bt0, Zt.x, Ut.x, (uint32_t)j0, 1u}, lane);
+            wq_push(wq, qn, ds1, Item{bs1, Zs.y, Us.y, (uint32_t)j1, 0u}, lane);
+            wq_push(wq, qn, dt1, Item{bt1, Zt.y, Ut.y, (uint32_t)j1, 1u}, lane);
+            wq_drain(wq, qn, 32u, lane, finish);
+          }
         }
       } else {
         if (v0) { dst.s2[j0] = sa.x; dst.t2[j0] = ta.x; dst.bs[j0] = c0.bs; dst.bt[j0] = c0.bt; }
