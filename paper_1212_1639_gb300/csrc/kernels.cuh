@@ -1290,26 +1290,58 @@ __device__ __forceinline__ uint64_t quant_from_e(double e, int k) {
   return W > cap ? cap : W;
 }
 
+// The systematic resampling step writes each particle's slots into a
+// shared-memory window (an entry per slot of the tile, the particle's offset
+// in the tile + 1).  Entry of slot x: x with bits 1-3 XORed by bits 6-8, so
+// that threads writing slots about PER apart, and warps reading consecutive
+// slots, hit distinct banks.
+__device__ __forceinline__ uint32_t win_entry(uint32_t x) { return x ^ (((x >> 6) & 7u) << 1); }
+// A run of the CTA's run list: slots [s0, s1) of ancestor v; with WRUN set in
+// v, window slots (relative to the tile's first slot) of mark v & 0xffff.
+constexpr uint32_t WRUN = 0x80000000u;
+
 // Rare paths of the systematic resampling step, kept out of line so that the
 // per-particle loop stays small: the slot count of a heavy particle (more than
-// two slots), and slots past the shared-memory window -- stored directly, or
-// queued as a run for the whole CTA when long.
+// two slots), and the slots of a particle that its two fast-path window
+// writes did not cover -- the rest of a heavy particle's run in the window
+// (by the whole CTA when long) and slots past the window (stored directly, or
+// by the whole CTA when long).
 static __device__ __noinline__ uint32_t sys_heavy_count(int64_t D, SysDiv dv) {
   return (uint32_t)(sys_floor_div(U128{0, (uint64_t)D - 1}, dv) + 1);
 }
-static __device__ __noinline__ void sys_past_window(uint32_t j, uint32_t c, uint32_t i, uint32_t wend,
-                                             uint32_t* anc, uint32_t (*runs)[3], uint32_t* nruns) {
-  const uint32_t st = j > wend ? j : wend;
-  if (j + c - st > (uint32_t)SYS_CAP) {
-    const uint32_t kr = atomicAdd(nruns, 1u);
-    if (kr < BB_RUNS) {
-      runs[kr][0] = st;
-      runs[kr][1] = j + c;
-      runs[kr][2] = i;
-      return;
+static __device__ __noinline__ void sys_rest(uint32_t j, uint32_t c, uint32_t S0, uint32_t wslots,
+                                             uint16_t mk, uint32_t ig, uint16_t* win, uint32_t* anc,
+                                             uint32_t (*runs)[3], uint32_t* nruns) {
+  const uint32_t wend = S0 + wslots, e = j + c;
+  const uint32_t a = j + 2u < e ? j + 2u : e;  // window part [a, b)
+  const uint32_t b = e < wend ? e : wend;
+  if (b > a) {
+    bool queued = false;
+    if (b - a > (uint32_t)SYS_CAP) {
+      const uint32_t kr = atomicAdd(nruns, 1u);
+      if (kr < BB_RUNS) {
+        runs[kr][0] = a - S0;
+        runs[kr][1] = b - S0;
+        runs[kr][2] = WRUN | mk;
+        queued = true;
+      }
     }
+    if (!queued)
+      for (uint32_t q = a; q < b; ++q) win[win_entry(q - S0)] = mk;
   }
-  for (uint32_t q = st; q < j + c; ++q) anc[q] = i;
+  const uint32_t st = j > wend ? j : wend;  // past the window: [st, e)
+  if (e > st) {
+    if (e - st > (uint32_t)SYS_CAP) {
+      const uint32_t kr = atomicAdd(nruns, 1u);
+      if (kr < BB_RUNS) {
+        runs[kr][0] = st;
+        runs[kr][1] = e;
+        runs[kr][2] = ig;
+        return;
+      }
+    }
+    for (uint32_t q = st; q < e; ++q) anc[q] = ig;
+  }
 }
 
 // Correctly rounded conversion of a 128-bit integer to binary64: the top 64
@@ -1342,8 +1374,8 @@ __device__ __forceinline__ double u128_to_f64_rn(U128 v) {
 //            its tiles the block scan of W with a carry -- thread t holds
 //            Q_i for its particles and Q before them in registers -- the CDF
 //            written out, and systematic resampling from those registers:
-//            each particle marks the first of its slots in a shared-memory
-//            window, and the warps fill the slots between marks forward.
+//            each particle writes its slots into a shared-memory window, which
+//            the CTA then stores out coalesced.
 // The quantisation and the log-ML partials (sums over 16 consecutive
 // particles in a fixed order; with PER = 8 a lane pair shares one) are those
 // of k_scan, and the ancestors those of k_merge_sys: the results are the same
@@ -1368,9 +1400,6 @@ __global__ void __launch_bounds__(BLOCK, PER == 8 ? 4 : 3) k_cdf_sys(FilterArgs<
                                                                     U128* cta_sq) {
   static_assert(PER == 16 || (PER == 8 && !STAGED && sizeof(R) == 4), "tile shapes");
   constexpr int TP = BLOCK * PER;  // particles per tile
-  // ancestor window entry of the tile's slot S0 + x: x + 2 (x >> LOGP) with
-  // lanes about PER slots apart, so that they hit distinct banks
-  constexpr int LOGP = PER == 16 ? 4 : 3;
   typedef typename ESumT<R>::T ES;
   __shared__ uint64_t s_warp[WARPS + 1];
   __shared__ ES s_es[WARPS];
@@ -1385,7 +1414,6 @@ __global__ void __launch_bounds__(BLOCK, PER == 8 ? 4 : 3) k_cdf_sys(FilterArgs<
   // (phase 2: a free buffer is the tile's ancestor window, see below)
   __shared__ alignas(128) R s_ell[2][STAGED ? TP : 4];
   __shared__ alignas(16) uint16_t s_win[STAGED ? 8 : 2 * TP];
-  __shared__ uint32_t s_wmax[WARPS];
   __shared__ alignas(8) uint64_t s_bar[2];
   __shared__ uint32_t s_S[2];  // the tile's first slot and the slot after its last
   __shared__ U128 s_sq[ESS ? WARPS : 1];
@@ -1674,10 +1702,10 @@ __global__ void __launch_bounds__(BLOCK, PER == 8 ? 4 : 3) k_cdf_sys(FilterArgs<
     // the tile's first slot S0 = R(carry)
     if (threadIdx.x == 0) s_S[0] = (uint32_t)sys_first_slot(carry, n, r, dv);
     // The ancestors of the tile's slots [S0, S1) are built in a shared-memory
-    // window (a free l buffer when staged): entry of slot S0 + x is
-    // x + 2 (x >> LOGP), so lanes about PER slots apart hit distinct banks.
-    constexpr uint32_t WIN_ENTRIES = STAGED ? TP * sizeof(R) / 2 : 2 * TP;
-    constexpr uint32_t WIN_SLOTS = WIN_ENTRIES / (PER + 2) * PER;
+    // window of one 16-bit entry per slot (a free l buffer when staged), at
+    // least two per particle of the tile, then stored out coalesced.
+    constexpr uint32_t WIN_SLOTS = STAGED ? TP * sizeof(R) / 2 : 2 * TP;
+    static_assert(WIN_SLOTS % 512 == 0 && WIN_SLOTS >= 2 * TP, "window");
     uint16_t* const win = STAGED ? reinterpret_cast<uint16_t*>(
         s_ell[tile == tb ? (q_issued & 1) : ((q_done - 1) & 1)]) : s_win;
     {
@@ -1693,10 +1721,6 @@ __global__ void __launch_bounds__(BLOCK, PER == 8 ? 4 : 3) k_cdf_sys(FilterArgs<
     const uint64_t incl = warp_incl_scan(tt, lane);
     if (lane == 31) s_warp[warp] = incl;
     __syncthreads();
-    {  // every thread is past quantP: the window is free, clear it
-      uint4* const wz = reinterpret_cast<uint4*>(win);
-      for (uint32_t q = threadIdx.x; q < WIN_ENTRIES / 8; q += BLOCK) wz[q] = make_uint4(0u, 0u, 0u, 0u);
-    }
     if (warp == 0) {
       const uint64_t wt = lane < WARPS ? s_warp[lane] : 0;
       const uint64_t wi = warp_incl_scan(wt, lane);
@@ -1736,12 +1760,13 @@ __global__ void __launch_bounds__(BLOCK, PER == 8 ? 4 : 3) k_cdf_sys(FilterArgs<
     // for particle i and its first slot j, i owns the c = ceil(D / T) slots
     // j .. j + c - 1 (none if D <= 0); D then drops by c T into (-T, 0] and
     // the next particle adds n w_{i+1} <= n 2^k <= 2^61 (T <= 2^61 too), so
-    // D is an int64.  A particle marks only its first slot in the window
-    // (with its offset in the tile + 1; 0 is empty); the slots between marks
-    // are filled forward below.  c comes from two comparisons unless it is
-    // above 2 (a heavy particle, divided out).  Slots past the window (rare)
-    // are stored directly, in runs of the CTA when long.  A rolled loop over
-    // the row: the step's code stays small.
+    // D is an int64.  A particle writes its offset in the tile + 1 into the
+    // window entries of its slots: the first two by predicated stores, any
+    // others (a heavy particle) and slots past the window out of line, in
+    // runs of the CTA when long.  c comes from two comparisons unless it is
+    // above 2 (a heavy particle, divided out).  Every slot of [S0, S1) is
+    // written exactly once, so the window needs no clearing.  A rolled loop
+    // over the row: the step's code stays small.
     if (rs && T > 0 && base < n) {
       const uint32_t ecount = base + PER <= n ? (uint32_t)PER : (uint32_t)(n - base);
       uint32_t j = threadIdx.x == 0 ? S0 : (base == 0 ? 0u : (uint32_t)sys_first_slot(o, n, r, dv));
@@ -1749,40 +1774,40 @@ __global__ void __launch_bounds__(BLOCK, PER == 8 ? 4 : 3) k_cdf_sys(FilterArgs<
       const U128 KB = add128(mul64x32(T, j), r);
       int64_t D = (int64_t)(X.lo - KB.lo);  // n Q - (j T + r) just before this thread's particles
       const int64_t Ti = (int64_t)T;
-      const uint32_t wend = S0 + WIN_SLOTS;
       const uint32_t off0 = (uint32_t)(base - tbase) + 1u;
+      const uint32_t n32 = (uint32_t)n;
       uint64_t qprev = o;
 #pragma unroll 1
       for (uint32_t e = 0; e < ecount; ++e) {
         const uint64_t q = qrow[e];
-        D += (int64_t)((q - qprev) * n);
+        const uint64_t w = q - qprev;
+        D += (int64_t)((uint64_t)(uint32_t)w * n32 + (((w >> 32) * n32) << 32));  // w n mod 2^64
         qprev = q;
         uint32_t c = (uint32_t)(D > 0) + (uint32_t)(D > Ti);
         if (D > 2 * Ti) c = sys_heavy_count(D, dv);
-        if (c) {
-          const uint32_t x = j - S0;
-          if (x < WIN_SLOTS) win[x + 2 * (x >> LOGP)] = (uint16_t)(off0 + e);
-          if (j + c > wend) sys_past_window(j, c, (uint32_t)base + e, wend, a.anc, s_run, &s_nruns);
-        }
-        D -= (int64_t)c * Ti;
+        const uint16_t mk = (uint16_t)(off0 + e);
+        const uint32_t x = j - S0;
+        if (c >= 1u && x < WIN_SLOTS) win[win_entry(x)] = mk;
+        if (c >= 2u && x + 1u < WIN_SLOTS) win[win_entry(x + 1u)] = mk;
+        if (c > 2u || x + c > WIN_SLOTS)
+          sys_rest(j, c, S0, WIN_SLOTS, mk, (uint32_t)base + e, win, a.anc, s_run, &s_nruns);
+        D -= c == 1u ? Ti : (int64_t)c * Ti;
         j += c;
       }
       if (base + PER >= n || threadIdx.x == BLOCK - 1) s_S[1] = j;  // the tile's end slot
     }
     __syncthreads();
-    // fill forward: slot x takes the last mark at or before it (slot S0 is
-    // always marked).  Warp w covers a contiguous part of the window: its
-    // maximum mark first, then a running maximum with the earlier parts'.
-    const uint32_t wcnt = (rs && T > 0) ? (s_S[1] - S0 < WIN_SLOTS ? s_S[1] - S0 : WIN_SLOTS) : 0u;
-    const uint32_t cw = (wcnt + WARPS * 32 - 1) / (WARPS * 32) * 32;
-    const uint32_t x0 = warp * cw < wcnt ? warp * cw : wcnt;
-    const uint32_t x1 = x0 + cw < wcnt ? x0 + cw : wcnt;
-    {
-      uint32_t mx = 0;
-      for (uint32_t x = x0 + lane; x < x1; x += 32) mx = max(mx, (uint32_t)win[x + 2 * (x >> LOGP)]);
-      mx = __reduce_max_sync(0xffffffffu, mx);
-      if (lane == 0) s_wmax[warp] = mx;
+    // window runs of heavy particles, by the whole CTA
+    const uint32_t nr = s_nruns < BB_RUNS ? s_nruns : BB_RUNS;
+    bool wr = false;
+    for (uint32_t q = 0; q < nr; ++q) {
+      const uint32_t v = s_run[q][2];
+      if (!(v & WRUN)) continue;
+      wr = true;
+      for (uint32_t x = s_run[q][0] + threadIdx.x; x < s_run[q][1]; x += BLOCK)
+        win[win_entry(x)] = (uint16_t)v;
     }
+    if (wr) __syncthreads();  // (wr is the same in every thread)
     if constexpr (STAGED) {  // the CDF rows, written out coalesced
       const uint64_t tcnt = n - tbase < (uint64_t)TP ? n - tbase : (uint64_t)TP;
       for (uint32_t p = 2 * threadIdx.x; p < tcnt; p += 2 * BLOCK) {
@@ -1795,27 +1820,16 @@ __global__ void __launch_bounds__(BLOCK, PER == 8 ? 4 : 3) k_cdf_sys(FilterArgs<
         }
       }
     }
-    __syncthreads();
+    // the window's slots [S0, S0 + wcnt), stored out coalesced
     {
-      uint32_t run = 0;
-      for (int w = 0; w < warp; ++w) run = max(run, s_wmax[w]);
-      for (uint32_t xb = x0; xb < x1; xb += 32) {
-        const uint32_t x = xb + lane;
-        uint32_t v = x < x1 ? (uint32_t)win[x + 2 * (x >> LOGP)] : 0u;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-          const uint32_t u = __shfl_up_sync(0xffffffffu, v, d);
-          if (lane >= d) v = max(v, u);
-        }
-        v = max(v, run);
-        run = __shfl_sync(0xffffffffu, v, 31);
-        if (x < x1) a.anc[S0 + x] = (uint32_t)tbase + v - 1u;
-      }
+      const uint32_t wcnt = (rs && T > 0) ? (s_S[1] - S0 < WIN_SLOTS ? s_S[1] - S0 : WIN_SLOTS) : 0u;
+      const uint32_t tb32 = (uint32_t)tbase - 1u;
+      for (uint32_t x = threadIdx.x; x < wcnt; x += BLOCK) a.anc[S0 + x] = tb32 + win[win_entry(x)];
     }
-    // runs past the window, by the whole block
-    const uint32_t nr = s_nruns < BB_RUNS ? s_nruns : BB_RUNS;
+    // runs past the window, by the whole CTA
     for (uint32_t q = 0; q < nr; ++q) {
       const uint32_t st = s_run[q][0], en = s_run[q][1], v = s_run[q][2];
+      if (v & WRUN) continue;
       for (uint32_t jj = st + threadIdx.x; jj < en; jj += BLOCK) a.anc[jj] = v;
     }
     __syncthreads();
