@@ -1700,7 +1700,8 @@ __global__ void __launch_bounds__(BLOCK, PER == 8 ? 4 : 3) k_cdf_sys(FilterArgs<
       quantP(tile, buf, W, &ep, ESS ? 0 : 2);
     }
     // the tile's first slot S0 = R(carry)
-    if (threadIdx.x == 0) s_S[0] = (uint32_t)sys_first_slot(carry, n, r, dv);
+    // (a later tile starts where the previous one ended: no division)
+    if (threadIdx.x == 0) s_S[0] = tile == tb ? (uint32_t)sys_first_slot(carry, n, r, dv) : s_S[1];
     // The ancestors of the tile's slots [S0, S1) are built in a shared-memory
     // window of one 16-bit entry per slot (a free l buffer when staged), at
     // least two per particle of the tile, then stored out coalesced.
@@ -2291,7 +2292,7 @@ constexpr uint32_t WQ2_CAP = 160;  // 31 queued + 4 pushes of 32 per pass
 // With FUSE, the next cycle's weights as in k_propagate, the two slots of a
 // pass weighed by paired operations.
 template <bool LEARN, bool FUSE = false, bool ESS = false>
-__global__ void __launch_bounds__(BLOCK, 3) k_propagate2(FilterArgs<float> a) {
+__global__ void __launch_bounds__(BLOCK, 4) k_propagate2(FilterArgs<float> a) {
   typedef GammaItem<float> Item;
   __shared__ Item s_q[WARPS][WQ2_CAP];
   const Ctl* c = a.ctl;
