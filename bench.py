@@ -67,6 +67,7 @@ BYTES_PER_PARTICLE = {
     "cdf_resample": 4 + 8 + 4,   # read l; write Q; write ancestors (l is read twice, the
                                   # second time mostly from L2)
     "propagate_weights_next": 4 + 28 + 28 + 4,  # propagate, and write the next cycle's l
+    "estimate": 12,               # read x, sigma2, tau2 (posterior summaries)
 }
 
 
@@ -448,6 +449,25 @@ def bench_ours(args):
                              "frac": round(ach_i / peak_i, 4)}
     cycle_bytes = sum(v["bytes"] for v in kernels.values())
     cycle_ms = sum(prof.values())
+    # the posterior summaries (pf_estimate: the reduction kernel and the
+    # 104-byte copy), on the same stream after an L2 flush
+    est_ms = []
+    for i in range(5):
+        if flush is not None:
+            flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        f.estimate()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        est_ms.append(e0.elapsed_time(e1))
+    est_mean = float(np.mean(est_ms[1:]))
+    est_bytes = BYTES_PER_PARTICLE["estimate"] * n
+    estimate = {"ms": round(est_mean, 5), "bytes": est_bytes,
+                "gbs": round(est_bytes / (est_mean / 1e3) / 1e9, 1),
+                "frac_of_peak": round(est_bytes / (est_mean / 1e3) / 1e9 / hbm, 4),
+                "note": "pf_estimate: summary kernel plus the 104-byte copy; reads x, sigma^2, tau^2"}
 
     # end to end through the C ABI with host buffers
     fe = pf.Filter(n, seed=7 + rank, filter_id=rank, scheme=args.scheme, precision="fp32",
@@ -544,11 +564,18 @@ def bench_ours(args):
                 "value": n * Km / (msm / 1e3), "unit": UNIT, "steps": Km, "ms_per_step": msm / Km,
                 "kernels": {k: round(v, 5) for k, v in profm.items()}}
             fm.close()
+        extra["plain_config"] = bench_plain_config(pf, synth, stream)
         extra["batched"] = bench_batched(pf, synth, stream)
         extra["precision"] = bench_precision(pf, synth, stream)
         extra["served"] = bench_served(pf, synth, stream, duration=args.served_seconds)
         extra["served_admission"] = bench_served(pf, synth, stream, duration=20.0, budget_gb=8.0,
                                                  session_s=10.0)
+        cap = bench_served_capacity(pf, synth, stream)
+        per = bench_served_per_stream(pf, synth, stream)
+        cap["per_stream_launches"] = per
+        if cap["capacity_obs_per_s"]:
+            cap["speedup_vs_per_stream_launches"] = round(cap["capacity_obs_per_s"] / per["obs_per_s"], 1)
+        extra["served"]["capacity"] = cap
     f.close()
 
     cpu = None
@@ -571,6 +598,7 @@ def bench_ours(args):
                   "hbm_frac_of_graph_time": round(cycle_bytes / (ms / K / 1e3) / 1e9 / hbm, 4),
                   "kernels": kernels},
         "e2e": e2e,
+        "estimate": estimate,
         "cycle_ms": cycle_stats(per_cycle),
         "gpu_launches": launches_per_cycle * K,
         "clocks": clocks,
@@ -651,7 +679,75 @@ def bench_batched(pf, synth, stream, K=20, W=3, Kp=3, n_filters=4096, seed=4096)
                                 "note": "pf_step on each filter in turn, one stream"},
         "speedup_vs_per_filter": round(ms_p / ms_b, 2),
         "accuracy": "bit-identical per filter (tests/test_gpu_batch.py)",
+        "cpu_baseline": oracle_batch_baseline(specs, ys),
     }
+
+
+def bench_plain_config(pf, synth, stream, runs=10, T=100, n=1024):
+    """The paper's plain configuration (its Section 4 run): one filter, N = 1024,
+    T = 100, FP64 state, multinomial resampling.  Ten runs on the same series;
+    each run creates the filter (the initialisation kernel) and runs the 100
+    cycles.  Reported as the paper reports its runs: ms per 100-step run (the
+    mean of the 5 runs closest to the median of the 10) and particle-steps/s,
+    with the per-cycle device time beside it."""
+    import torch
+    _, y = synth.local_level_series(1212, T)
+    y_dev = torch.from_numpy(y).cuda()
+    walls, cyc = [], []
+    for r in range(runs + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        f = pf.Filter(n, seed=1212, scheme="multinomial", precision="fp64", stream=stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        f.run(y_dev)
+        e1.record(stream)
+        f.sync()
+        wall = time.perf_counter() - t0
+        f.close()
+        if r:  # the first run loads the kernels
+            walls.append(wall * 1e3)
+            cyc.append(e0.elapsed_time(e1) / T)
+    w = np.array(walls)
+    med = np.median(w)
+    m5 = float(w[np.argsort(np.abs(w - med))[:5]].mean())
+    return {"workload": "one filter, N=1024, T=100, FP64 state, multinomial resampling, "
+                        "IG(3,2) priors, seeded series (the paper's plain configuration)",
+            "value": n * T / (m5 / 1e3), "unit": UNIT, "ms_per_run": round(m5, 4),
+            "run_statistic": "mean of the 5 runs closest to the median of 10 (wall clock, "
+                             "filter creation and 100 cycles, synchronised)",
+            "cycle_us_median": round(float(np.median(cyc)) * 1e3, 2),
+            "cycle_device_particle_steps_per_s": n / (float(np.median(cyc)) / 1e3)}
+
+
+def oracle_batch_baseline(specs, ys, cycles=3, max_filters=512):
+    """The oracle on a sample of the batched workload (the first max_filters
+    filters of the same batch, `cycles` cycles each), one host core and all
+    host cores (one filter per thread; the oracle's calls release the GIL)."""
+    from concurrent.futures import ThreadPoolExecutor
+    from oracle import oracle as orc
+    sub = specs[:max_filters]
+    total = sum(sp["n"] for sp in sub)
+    out = {"sample": "%d filters (sum N = %d), %d cycles each" % (len(sub), total, cycles),
+           "kind": "oracle", "unit": UNIT, "host": host_cpu()}
+    ncpu = out["host"]["nproc"] or 1
+    for cores in sorted({1, ncpu}):
+        filters = [orc.Filter(orc.make_config(sp["n"], seed=sp["seed"], filter_id=sp["filter_id"],
+                                              scheme=orc.SYSTEMATIC, precision=orc.FP32))
+                   for sp in sub]
+
+        def run(i):
+            for t in range(cycles):
+                filters[i].step(float(ys[t, i]))
+
+        t0 = time.perf_counter()
+        with ThreadPoolExecutor(cores) as ex:
+            list(ex.map(run, range(len(sub))))
+        dt = time.perf_counter() - t0
+        for fo in filters:
+            fo.close()
+        out["cores_%d" % cores] = {"value": total * cycles / dt, "cores": cores}
+    return out
 
 
 def served_events(pf, synth, n_streams, duration, rate, seed, session_s=None):
@@ -737,6 +833,77 @@ def bench_served(pf, synth, stream, duration=60.0, budget_gb=120.0, n_streams=10
     }
 
 
+def bench_served_capacity(pf, synth, stream, rates=(20.0, 50.0, 80.0, 120.0), duration=4.0,
+                          warmup_s=1.0, p99_bound_ms=10.0, n_streams=10000, seed=10000):
+    """Capacity of the served form: the same 10,000 streams under Poisson
+    loads of increasing rate (observations/s per stream) for `duration` s
+    each; the capacity is the highest offered rate whose observations are all
+    served at the offered rate with p99 latency (after the warm-up) within
+    the bound."""
+    import torch
+    rows = []
+    for r in rates:
+        t, kind, sid, y, cfgs, total = served_events(pf, synth, n_streams, duration, r, seed)
+        srv = pf.Server(max_streams=n_streams, hbm_budget_bytes=int(120e9), scheme="systematic",
+                        precision="fp32", max_inflight=2, cluster=8, big_min=16384,
+                        warmup_s=warmup_s, stream=stream)
+        srv.replay(t, kind, sid, y, cfgs)
+        srv.drain(duration + 600)
+        st = srv.stats()
+        srv.close()
+        torch.cuda.empty_cache()
+        offered = r * n_streams
+        rows.append({"offered_obs_per_s": offered, "obs_per_s": round(st["obs_per_s"], 1),
+                     "particle_steps_per_s": st["particle_steps_per_s"],
+                     "p50_us": round(st["steady_p50_us"], 1), "p99_us": round(st["steady_p99_us"], 1),
+                     "mean_streams_per_cycle": round(st["mean_cycle_streams"], 1)})
+    ok = [row for row in rows if row["p99_us"] <= p99_bound_ms * 1e3
+          and row["obs_per_s"] >= 0.97 * row["offered_obs_per_s"]]
+    best = max(ok, key=lambda row: row["offered_obs_per_s"]) if ok else None
+    return {"sweep": rows, "p99_bound_ms": p99_bound_ms, "duration_s": duration,
+            "capacity_obs_per_s": best["obs_per_s"] if best else None,
+            "capacity_particle_steps_per_s": best["particle_steps_per_s"] if best else None,
+            "note": "highest offered rate served in full with p99 (after %.0f s) within %.0f ms; "
+                    "above it the queue grows" % (warmup_s, p99_bound_ms)}
+
+
+def bench_served_per_stream(pf, synth, stream, n_streams=256, rounds=3, seed=10000):
+    """The served streams processed without the server: each stream a
+    standalone filter, each round one observation per stream -- pf_step on
+    every stream (plain-kernel launches, asynchronous), then pf_estimate on
+    every stream for its result.  The same results as served (bit for bit,
+    tests/test_gpu_serve.py); observations/s for comparison with the served
+    capacity."""
+    import torch
+    ns, s2, t2 = synth.batch_specs(10000, seed, 512, 131072)
+    ids = list(range(n_streams))
+    ys = [synth.local_level_series(seed + i, rounds + 2, sigma2=s2[i], tau2=t2[i], filter_id=i)[1]
+          for i in ids]
+    fs = [pf.Filter(int(ns[i]), seed=seed + i, filter_id=i, scheme="systematic", precision="fp32",
+                    stream=stream) for i in ids]
+    for k, f in enumerate(fs):  # one untimed round: graphs captured
+        f.step(ys[k][0])
+        f.estimate()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for r in range(1, rounds + 1):
+        for k, f in enumerate(fs):
+            f.step(ys[k][r])
+        for f in fs:
+            f.estimate()
+    dt = time.perf_counter() - t0
+    for f in fs:
+        f.close()
+    torch.cuda.empty_cache()
+    obs = n_streams * rounds
+    total = int(sum(int(ns[i]) for i in ids))
+    return {"streams": n_streams, "sum_n": total, "rounds": rounds,
+            "obs_per_s": obs / dt, "particle_steps_per_s": total * rounds / dt,
+            "gpu_launches_per_obs": 4,
+            "note": "pf_step on each stream (asynchronous), then pf_estimate on each (its result); "
+                    "the first %d streams of the served workload" % n_streams}
+
+
 def bench_precision(pf, synth, stream, reps=8):
     """FP32 state against FP64 state on the same draws, per posterior summary
     and step, in units of the Monte Carlo sd of the estimate (the spread of
@@ -779,6 +946,30 @@ def bench_precision(pf, synth, stream, reps=8):
     return out
 
 
+def host_cpu():
+    """The host CPU the oracle runs on: model name (lscpu, else /proc/cpuinfo)
+    and the number of cores the process may use."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if model is None:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    ncpu = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return {"model": model, "nproc": ncpu, "machine": os.uname().machine}
+
+
 def cpu_baseline(n, scheme, y, budget_s=15.0):
     """The oracle as it stands, single-threaded, on a bounded sample of the
     workload: the same N and series, as many cycles as fit in ~budget_s."""
@@ -796,7 +987,7 @@ def cpu_baseline(n, scheme, y, budget_s=15.0):
     o.close()
     return {"value": n * steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": "N=%d particles, first %d cycles of the same series (FP32 state, %s)"
-                      % (n, steps, scheme)}
+                      % (n, steps, scheme), "host": host_cpu()}
 
 
 def bench_reference(args):
@@ -871,7 +1062,9 @@ def main():
             "served_no_clusters": bench_served(pf, synth, stream, duration=args.served_seconds,
                                                cluster=1),
             "served_admission": bench_served(pf, synth, stream, duration=20.0, budget_gb=8.0,
-                                             session_s=10.0)}))
+                                             session_s=10.0),
+            "capacity": bench_served_capacity(pf, synth, stream),
+            "per_stream_launches": bench_served_per_stream(pf, synth, stream)}))
     else:
         bench_ours(args)
 

@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "../../include/pf.h"
+#include "../../include/pf_diag.h"
 #include "kernels.cuh"
 
 using namespace pfk;
@@ -121,6 +122,7 @@ struct pf_filter {
   double* part_est = nullptr;
   Ctl* ctl = nullptr;
   Ctl* ctl_host = nullptr;  // pinned mirror for summaries
+  Ctl* ctl_host_dev = nullptr;  // its device address (mapped), or NULL
   // captured cycles by CycleForm (the fused forms on first use); each launch
   // sets its observations in the kernel nodes' arguments (no copy on the stream)
   CycleGraph cg[CF_COUNT];
@@ -185,6 +187,7 @@ FilterArgs<R> filter_args(pf_filter* f) {
   a.part = f->part;
   a.part_est = f->part_est;
   a.ctl = f->ctl;
+  a.ctl_mirror = f->ctl_host_dev;
   a.y_src = nullptr;
   a.y_val = 0.0;
   a.n = f->n;
@@ -303,6 +306,8 @@ pf_status enqueue_cycle(pf_filter* f, KTimer* tm = nullptr, const double* y_src 
   sa.t_arg = 0;
   sa.n = n;
   sa.k = f->k;
+  sa.spin_limit = SPIN_LIMIT;
+  sa.withhold = NO_TILE;
   sa.vec_ok = 1;
   if (!f->cdf_grid) {
     k_scan<FROM_LOGLIK, R><<<f->ntiles, BLOCK, 0, s>>>(sa);
@@ -403,7 +408,9 @@ pf_status enqueue_cycle(pf_filter* f, KTimer* tm = nullptr, const double* y_src 
     const unsigned eg = (unsigned)cdiv(n, (uint64_t)BLOCK * EST_PER_THREAD);
     if (f->ess) k_estimate_w<R><<<eg, BLOCK, 0, s>>>(a);
     else k_estimate<R><<<eg, BLOCK, 0, s>>>(a);
-    CK(cudaMemcpyAsync(f->ctl_host, f->ctl, offsetof(Ctl, y), cudaMemcpyDeviceToHost, s));
+    // the kernel writes the mapped mirror itself; otherwise a 104-byte copy
+    if (!a.ctl_mirror)
+      CK(cudaMemcpyAsync(f->ctl_host, f->ctl, offsetof(Ctl, y), cudaMemcpyDeviceToHost, s));
   }
   CK(cudaGetLastError());
   return PF_OK;
@@ -628,9 +635,14 @@ pf_status pf_create(const pf_config* cfg, pf_filter** out) {
       return bail(st);
   }
   if ((st = dev_alloc(f, sizeof(Ctl), (void**)&f->ctl)) != PF_OK) return bail(st);
-  if (cudaHostAlloc((void**)&f->ctl_host, sizeof(Ctl), cudaHostAllocDefault) != cudaSuccess) {
+  if (cudaHostAlloc((void**)&f->ctl_host, sizeof(Ctl), cudaHostAllocMapped) != cudaSuccess) {
     cudaGetLastError();
     return bail(set_err(PF_ERR_OOM, "pinned host allocation failed"));
+  }
+  // the summary kernels write the mirror directly when it is mapped
+  if (cudaHostGetDevicePointer((void**)&f->ctl_host_dev, f->ctl_host, 0) != cudaSuccess) {
+    cudaGetLastError();
+    f->ctl_host_dev = nullptr;
   }
   // control block: t = 0, no error, max = -inf, counters 0
   Ctl c0;
@@ -852,7 +864,15 @@ pf_status pf_estimate(pf_filter* f, pf_estimates* out) {
     f->sticky = PF_ERR_CUDA;
     return set_err(PF_ERR_CUDA, "estimate launch: %s", cudaGetErrorString(e));
   }
-  if ((st = sync_and_check(f)) != PF_OK) return st;
+  if (f->ctl_host_dev) {  // the kernel wrote the mirror
+    if (cudaStreamSynchronize(f->stream) != cudaSuccess) {
+      f->sticky = PF_ERR_CUDA;
+      return set_err(PF_ERR_CUDA, "stream: %s", cudaGetErrorString(cudaGetLastError()));
+    }
+    if ((st = map_err(f->ctl_host->err)) != PF_OK) return f->sticky = st;
+  } else if ((st = sync_and_check(f)) != PF_OK) {
+    return st;
+  }
   const double* v = f->ctl_host->est;
   out->t = (uint64_t)v[0];
   out->x_mean = v[1];
@@ -1157,9 +1177,15 @@ size_t scratch_zero_bytes(uint64_t n) {
 
 // Weights -> Q (and S for multinomial) -> ancestors, on stream s with the
 // given scratch (already zeroed in its first scratch_zero_bytes bytes).
+// Wait settings of the scan: the normal bound, or a failure-detection test's.
+struct WaitDiag {
+  uint32_t spin_limit = SPIN_LIMIT;
+  uint32_t withhold = NO_TILE;
+};
+
 pf_status run_resample(const float* w, uint64_t n, uint64_t seed, uint32_t filter, uint32_t t,
                        int scheme, uint32_t* anc, uint64_t* Q_out, const Scratch& sc,
-                       cudaStream_t s) {
+                       cudaStream_t s, WaitDiag dg = WaitDiag()) {
   const uint32_t ntiles = (uint32_t)cdiv(n, TILE);
   const unsigned gmax = (unsigned)(cdiv(n, BLOCK) < 152 * 8 ? cdiv(n, BLOCK) : 152 * 8);
   k_wmax<<<gmax, BLOCK, 0, s>>>(w, n, sc.ctl);
@@ -1175,6 +1201,8 @@ pf_status run_resample(const float* w, uint64_t n, uint64_t seed, uint32_t filte
   sa.n = n;
   sa.k = cdf_shift(n);
   sa.vec_ok = ((uintptr_t)w & 15) == 0;
+  sa.spin_limit = dg.spin_limit;
+  sa.withhold = dg.withhold;
   k_scan<FROM_WEIGHTS, float><<<ntiles, BLOCK, 0, s>>>(sa);
   CK(cudaGetLastError());
   if (!anc) return PF_OK;
@@ -1247,7 +1275,8 @@ pf_status scratch_pool(cudaMemPool_t* out) {
 }
 
 pf_status resample_common(const float* w, uint64_t n, uint64_t seed, uint32_t filter,
-                          uint32_t t, int scheme, uint32_t* anc, uint64_t* Q_out, void* stream) {
+                          uint32_t t, int scheme, uint32_t* anc, uint64_t* Q_out, void* stream,
+                          WaitDiag dg = WaitDiag()) {
   if (!w || (!anc && !Q_out)) return set_err(PF_ERR_INVALID, "NULL pointer");
   if (n < 1 || n > PF_MAX_PARTICLES) return set_err(PF_ERR_INVALID, "n must be in [1, 2^26]");
   if (scheme < 0 || scheme > 4) return set_err(PF_ERR_INVALID, "bad scheme");
@@ -1268,7 +1297,7 @@ pf_status resample_common(const float* w, uint64_t n, uint64_t seed, uint32_t fi
   pf_status st = PF_OK;
   if (cudaMemsetAsync(base, 0, scratch_zero_bytes(n), s) != cudaSuccess)
     st = set_err(PF_ERR_CUDA, "scratch memset failed");
-  if (st == PF_OK) st = run_resample(w, n, seed, filter, t, scheme, anc, Q_out, sc, s);
+  if (st == PF_OK) st = run_resample(w, n, seed, filter, t, scheme, anc, Q_out, sc, s, dg);
   pf_status st2 = PF_OK;
   if (st == PF_OK) st2 = finish_and_check(sc, s);
   cudaFreeAsync(base, s);
@@ -1295,6 +1324,16 @@ pf_status pf_resample(const float* w_dev, uint64_t n, uint64_t seed, uint32_t fi
 pf_status pf_cdf(const float* w_dev, uint64_t n, uint64_t* Q_dev, void* stream) {
   if (!Q_dev) return set_err(PF_ERR_INVALID, "NULL CDF output");
   return resample_common(w_dev, n, 0, 0, 0, PF_SYSTEMATIC, nullptr, Q_dev, stream);
+}
+
+pf_status pf_diag_cdf_wait(const float* w_dev, uint64_t n, uint32_t withhold_tile,
+                           uint32_t spin_limit, uint64_t* Q_dev, void* stream) {
+  if (!Q_dev) return set_err(PF_ERR_INVALID, "NULL CDF output");
+  if (spin_limit < 1) return set_err(PF_ERR_INVALID, "spin_limit must be at least 1");
+  WaitDiag dg;
+  dg.spin_limit = spin_limit;
+  dg.withhold = withhold_tile;
+  return resample_common(w_dev, n, 0, 0, 0, PF_SYSTEMATIC, nullptr, Q_dev, stream, dg);
 }
 
 pf_status pf_cutpoint_search(const uint64_t* Q_dev, uint64_t n, uint32_t* I_dev, void* stream) {

@@ -745,11 +745,14 @@ __global__ void __launch_bounds__(BB) k_batch_init(BatchArgs<R> a) {
 }
 
 // Posterior summaries of the listed filters, one filter per CTA pass.  The
-// particles are taken in the single-filter estimate's groups (2048 per
-// virtual block, 8 per thread, shifted by particle 0) and the group sums are
-// folded in its order, so the summaries equal a standalone filter's.
+// particles are taken in the single-filter estimate's groups (BLOCK x
+// EST_PER_THREAD per virtual block, consecutive particles per thread, shifted
+// by particle 0), summed by the same shuffle trees, and the group sums are
+// folded in its order (thread i takes groups i, i + BB, ..., then a shuffle
+// tree and the warps in order), so the summaries equal a standalone filter's.
 template <class R>
 __global__ void __launch_bounds__(BB) k_batch_estimate(BatchArgs<R> a) {
+  static_assert(BB == BLOCK, "the fold mirrors the single-filter estimate's");
   __shared__ double s_sum[6][WARPS];
   __shared__ double s_col[6][BB];
   __shared__ double s_tot[6];
@@ -767,29 +770,20 @@ __global__ void __launch_bounds__(BB) k_batch_estimate(BatchArgs<R> a) {
     for (int q = 0; q < 6; ++q) s_col[q][threadIdx.x] = 0.0;
     const uint64_t nblk = (n + GROUP - 1) / GROUP;
     for (uint64_t b = 0; b < nblk; ++b) {
-      double acc[6];
       {
         R loc[6] = {0, 0, 0, 0, 0, 0};
         const uint64_t base = b * GROUP + (uint64_t)threadIdx.x * EST_PER_THREAD;
-#pragma unroll
         for (int e = 0; e < EST_PER_THREAD; ++e) {
           const uint64_t i = base + e;
-          if (i < n) {
-            const R dx = st.x[off + i] - c0, ds = st.s2[off + i] - c1, dt = st.t2[off + i] - c2;
-            loc[0] += dx; loc[1] += dx * dx;
-            loc[2] += ds; loc[3] += ds * ds;
-            loc[4] += dt; loc[5] += dt * dt;
-          }
+          if (i < n) est_add<R>(loc, st.x[off + i], st.s2[off + i], st.t2[off + i], c0, c1, c2);
         }
 #pragma unroll
-        for (int q = 0; q < 6; ++q) acc[q] = (double)loc[q];
-      }
+        for (int q = 0; q < 6; ++q) {
+          R v = loc[q];
 #pragma unroll
-      for (int q = 0; q < 6; ++q) {
-        double v = acc[q];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) s_sum[q][warp] = v;
+          for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+          if (lane == 0) s_sum[q][warp] = (double)v;
+        }
       }
       __syncthreads();
       if (threadIdx.x < 6) {
@@ -799,23 +793,32 @@ __global__ void __launch_bounds__(BB) k_batch_estimate(BatchArgs<R> a) {
       }
       __syncthreads();
     }
-    if (threadIdx.x < 6) {
+    {
+      double v[6];
+#pragma unroll
+      for (int q = 0; q < 6; ++q) {
+        v[q] = s_col[q][threadIdx.x];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+      }
+      if (lane == 0) {
+#pragma unroll
+        for (int q = 0; q < 6; ++q) s_sum[q][warp] = v[q];
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {  // the warps in order, one quantity per thread
       double v = 0;
-      for (int i = 0; i < BB; ++i) v += s_col[threadIdx.x][i];
+      for (int ww = 0; ww < WARPS; ++ww) v += s_sum[threadIdx.x][ww];
       s_tot[threadIdx.x] = v;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-      const double nd = (double)n;
+      const double* tot = s_tot;
       const double cs[3] = {(double)c0, (double)c1, (double)c2};
       double* o = a.est + (uint64_t)w * BATCH_EST_ROW;
       o[0] = (double)t;
-      for (int q = 0; q < 3; ++q) {
-        const double m1 = s_tot[2 * q] / nd;
-        const double m2 = s_tot[2 * q + 1] / nd;
-        o[1 + 2 * q] = cs[q] + m1;
-        o[2 + 2 * q] = m2 - m1 * m1;
-      }
+      est_finish(tot, (double)n, cs, o + 1);
       o[7] = F->logml;
       o[8] = (double)F->err;
     }

@@ -18,6 +18,7 @@
 //   b_sigma, b_tau  : uint64 2^-32 fixed point (FP32) / binary64 (FP64)
 //   l               : R,    Q : uint64,   S : uint64 (n+1),   anc : uint32
 #pragma once
+#include <cstddef>
 #include <cstdint>
 
 #include "device.cuh"
@@ -132,6 +133,10 @@ struct FilterArgs {
   void* part;               // per-tile log-ML partial (U128 for FP32, double for FP64)
   double* part_est;         // per-block estimate partials
   Ctl* ctl;
+  // device address of the handle's pinned host mirror of the control block
+  // (mapped), or NULL: the summary kernels write the control block's summary
+  // prefix there directly, so no copy follows them
+  Ctl* ctl_mirror;
   // this cycle's observation: *y_src when y_src is set (device-resident
   // observations), else y_val (set per launch in the graph's weights node)
   const double* y_src;
@@ -461,11 +466,12 @@ template <> struct ESumT<double> { typedef ESum64 T; };
 // tile far from the last published prefix needs few round trips.
 constexpr int LB_PER_LANE = 4;
 
-__device__ __forceinline__ uint64_t spin_status(const uint64_t* p, bool* timed_out) {
+__device__ __forceinline__ uint64_t spin_status(const uint64_t* p, bool* timed_out,
+                                                uint32_t limit) {
   uint64_t v = ld_status(p);
   uint32_t spins = 0;
   while ((v >> 62) == 0) {
-    if (++spins > SPIN_LIMIT) {
+    if (++spins > limit) {
       *timed_out = true;
       return FLAG_P;
     }
@@ -475,9 +481,15 @@ __device__ __forceinline__ uint64_t spin_status(const uint64_t* p, bool* timed_o
   return v;
 }
 
+// limit: polls of one status word before the wait gives up (ERR_TIMEOUT);
+// withhold: a tile that publishes nothing (a failure-detection test makes its
+// successors' waits run out this way; NO_TILE otherwise).
+constexpr uint32_t NO_TILE = 0xffffffffu;
 __device__ __forceinline__ uint64_t lookback(uint64_t* stat, uint32_t tile, uint64_t total,
-                                             uint32_t* err) {
+                                             uint32_t* err, uint32_t limit = SPIN_LIMIT,
+                                             uint32_t withhold = NO_TILE) {
   const int lane = threadIdx.x & 31;
+  if (tile == withhold) return 0;
   if (tile == 0) {
     if (lane == 0) st_status(&stat[0], FLAG_P | total);
     return 0;
@@ -497,7 +509,7 @@ __device__ __forceinline__ uint64_t lookback(uint64_t* stat, uint32_t tile, uint
 #pragma unroll
     for (int k = 0; k < LB_PER_LANE; ++k) {
       const int64_t idx = look - (LB_PER_LANE * lane + k);
-      if ((v[k] >> 62) == 0) v[k] = spin_status(&stat[idx], &timed_out);
+      if ((v[k] >> 62) == 0) v[k] = spin_status(&stat[idx], &timed_out, limit);
     }
     int first_p = LB_PER_LANE;
 #pragma unroll
@@ -537,6 +549,8 @@ struct ScanArgs {
   uint64_t n;
   int k;
   int vec_ok;               // src is 16-byte aligned
+  uint32_t spin_limit;      // look-back polls before giving up (SPIN_LIMIT)
+  uint32_t withhold;        // a tile that publishes nothing (NO_TILE; failure tests)
 };
 
 // Thread-blocked scan: thread t of a tile owns the 16 consecutive elements
@@ -644,7 +658,7 @@ __global__ void __launch_bounds__(BLOCK, 4) k_scan(ScanArgs a) {
   if (warp == 0) {
     // tile total = last thread's staged inclusive value
     const uint64_t total = s_stage[(BLOCK - 1) * (SCAN_PER + 1) + SCAN_PER - 1];
-    const uint64_t excl = lookback(stat, tile, total, &a.ctl->err);
+    const uint64_t excl = lookback(stat, tile, total, &a.ctl->err, a.spin_limit, a.withhold);
     if (lane == 0) {
       s_excl = excl;
       stat_next[tile] = 0;
@@ -2291,8 +2305,10 @@ constexpr uint32_t WQ2_CAP = 160;  // 31 queued + 4 pushes of 32 per pass
 
 // With FUSE, the next cycle's weights as in k_propagate, the two slots of a
 // pass weighed by paired operations.
+// 4 CTAs per SM (64 registers) for the plain form; the fused and adaptive
+// forms hold more live values and keep 3 (80 registers, no spills).
 template <bool LEARN, bool FUSE = false, bool ESS = false>
-__global__ void __launch_bounds__(BLOCK, 4) k_propagate2(FilterArgs<float> a) {
+__global__ void __launch_bounds__(BLOCK, (FUSE || ESS) ? 3 : 4) k_propagate2(FilterArgs<float> a) {
   typedef GammaItem<float> Item;
   __shared__ Item s_q[WARPS][WQ2_CAP];
   const Ctl* c = a.ctl;
@@ -2533,11 +2549,51 @@ __global__ void __launch_bounds__(BLOCK) k_boot_gather(FilterArgs<R> a) {
 
 // ---------------------------------------------------------------------------
 // Posterior summaries (on demand): population means and variances of x,
-// sigma^2 and tau^2.  Per block: sums of v - c and (v - c)^2 with c the value
-// of particle 0 (shift against cancellation), accumulated in binary64 across
-// threads; the last block folds the block partials in block order.
+// sigma^2 and tau^2, from sums of v - c and (v - c)^2 with c the value of
+// particle 0 (a shift against cancellation).  Each thread sums its
+// EST_PER_THREAD consecutive particles (vector loads) and each warp its
+// lanes by a shuffle tree in the working precision; the warps of a block are
+// joined in binary64, and the last block to finish folds the block partials
+// in binary64 (each thread a fixed stride of blocks, then a shuffle tree):
+// the result is run-to-run deterministic and binary64 arithmetic runs per
+// block, not per particle (binary64 is a small fraction of the binary32 rate
+// on this part).
 // ---------------------------------------------------------------------------
-constexpr int EST_PER_THREAD = 8;
+constexpr int EST_PER_THREAD = 16;
+
+// The control block's prefix up to the per-cycle constants (t, error word,
+// counters, log-ML, summaries) written to the mapped host mirror, one 8-byte
+// word per thread (called by every thread of the block, after a barrier that
+// follows the writes to the control block); the host reads the mirror after
+// synchronising with the stream, which orders these writes.
+constexpr int SUMMARY_WORDS = (int)(offsetof(Ctl, y) / 8);
+__device__ __forceinline__ void publish_summary(const Ctl* c, Ctl* mirror) {
+  static_assert(offsetof(Ctl, y) % 8 == 0 && SUMMARY_WORDS <= 32, "prefix of whole words");
+  if (!mirror || threadIdx.x >= SUMMARY_WORDS) return;
+  reinterpret_cast<unsigned long long*>(mirror)[threadIdx.x] =
+      __ldcg(reinterpret_cast<const unsigned long long*>(c) + threadIdx.x);
+}
+
+// Means and variances from the shifted sums (sum of v - c, sum of (v - c)^2
+// per quantity) over n particles, one reciprocal of n.
+__device__ __forceinline__ void est_finish(const double* tot, double n, const double* cs,
+                                           double* out) {
+  const double inv_n = 1.0 / n;
+  for (int q = 0; q < 3; ++q) {
+    const double m1 = tot[2 * q] * inv_n;
+    const double m2 = tot[2 * q + 1] * inv_n;
+    out[2 * q] = cs[q] + m1;
+    out[2 * q + 1] = m2 - m1 * m1;
+  }
+}
+
+template <class R>
+__device__ __forceinline__ void est_add(R* loc, R v0, R v1, R v2, R c0, R c1, R c2) {
+  const R dx = v0 - c0, ds = v1 - c1, dt = v2 - c2;
+  loc[0] += dx; loc[1] += dx * dx;
+  loc[2] += ds; loc[3] += ds * ds;
+  loc[4] += dt; loc[5] += dt * dt;
+}
 
 template <class R>
 __global__ void __launch_bounds__(BLOCK) k_estimate(FilterArgs<R> a) {
@@ -2546,30 +2602,43 @@ __global__ void __launch_bounds__(BLOCK) k_estimate(FilterArgs<R> a) {
   const uint32_t t = a.ctl->t;
   const StateV<R> st = (t & 1) ? a.st[1] : a.st[0];
   const R c0 = st.x[0], c1 = st.s2[0], c2 = st.t2[0];
-  double acc[6] = {0, 0, 0, 0, 0, 0};
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   {
     R loc[6] = {0, 0, 0, 0, 0, 0};
     const uint64_t base = ((uint64_t)blockIdx.x * BLOCK + threadIdx.x) * EST_PER_THREAD;
+    if constexpr (sizeof(R) == 4) {
+      if (base + EST_PER_THREAD <= a.n) {
+        float4 X[EST_PER_THREAD / 4], S[EST_PER_THREAD / 4], T[EST_PER_THREAD / 4];
 #pragma unroll
-    for (int e = 0; e < EST_PER_THREAD; ++e) {
-      const uint64_t i = base + e;
-      if (i < a.n) {
-        const R dx = st.x[i] - c0, ds = st.s2[i] - c1, dt = st.t2[i] - c2;
-        loc[0] += dx; loc[1] += dx * dx;
-        loc[2] += ds; loc[3] += ds * ds;
-        loc[4] += dt; loc[5] += dt * dt;
+        for (int q = 0; q < EST_PER_THREAD / 4; ++q) {
+          X[q] = *reinterpret_cast<const float4*>(st.x + base + 4 * q);
+          S[q] = *reinterpret_cast<const float4*>(st.s2 + base + 4 * q);
+          T[q] = *reinterpret_cast<const float4*>(st.t2 + base + 4 * q);
+        }
+#pragma unroll
+        for (int q = 0; q < EST_PER_THREAD / 4; ++q) {
+          est_add<float>(loc, X[q].x, S[q].x, T[q].x, c0, c1, c2);
+          est_add<float>(loc, X[q].y, S[q].y, T[q].y, c0, c1, c2);
+          est_add<float>(loc, X[q].z, S[q].z, T[q].z, c0, c1, c2);
+          est_add<float>(loc, X[q].w, S[q].w, T[q].w, c0, c1, c2);
+        }
+      } else {
+        for (uint64_t i = base; i < a.n; ++i) est_add<R>(loc, st.x[i], st.s2[i], st.t2[i], c0, c1, c2);
+      }
+    } else {
+#pragma unroll 4
+      for (int e = 0; e < EST_PER_THREAD; ++e) {
+        const uint64_t i = base + e;
+        if (i < a.n) est_add<R>(loc, st.x[i], st.s2[i], st.t2[i], c0, c1, c2);
       }
     }
 #pragma unroll
-    for (int q = 0; q < 6; ++q) acc[q] = (double)loc[q];
-  }
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int q = 0; q < 6; ++q) {
+      R v = loc[q];
 #pragma unroll
-  for (int q = 0; q < 6; ++q) {
-    double v = acc[q];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) s_sum[q][warp] = v;
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) s_sum[q][warp] = (double)v;
+    }
   }
   __syncthreads();
   if (threadIdx.x < 6) {
@@ -2585,9 +2654,7 @@ __global__ void __launch_bounds__(BLOCK) k_estimate(FilterArgs<R> a) {
   if (!s_last) return;
   __threadfence();
   // fold the block partials: thread i sums blocks i, i + BLOCK, ... (a fixed
-  // assignment, so the result is run-to-run deterministic), then one thread
-  // per column sums the BLOCK thread totals in order
-  __shared__ double s_col[6][BLOCK];
+  // assignment), then a shuffle tree per warp and the warps in order
   {
     double v[6] = {0, 0, 0, 0, 0, 0};
     for (uint32_t b = threadIdx.x; b < gridDim.x; b += BLOCK) {
@@ -2595,29 +2662,33 @@ __global__ void __launch_bounds__(BLOCK) k_estimate(FilterArgs<R> a) {
       for (int q = 0; q < 6; ++q) v[q] += __ldcg(a.part_est + (uint64_t)b * 6 + q);
     }
 #pragma unroll
-    for (int q = 0; q < 6; ++q) s_col[q][threadIdx.x] = v[q];
+    for (int q = 0; q < 6; ++q) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+    }
+    __syncthreads();  // s_sum is reused
+    if (lane == 0) {
+#pragma unroll
+      for (int q = 0; q < 6; ++q) s_sum[q][warp] = v[q];
+    }
   }
   __syncthreads();
   __shared__ double s_tot[6];
-  if (threadIdx.x < 6) {
+  if (threadIdx.x < 6) {  // the warps in order, one quantity per thread
     double v = 0;
-    for (int i = 0; i < BLOCK; ++i) v += s_col[threadIdx.x][i];
+    for (int w = 0; w < WARPS; ++w) v += s_sum[threadIdx.x][w];
     s_tot[threadIdx.x] = v;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    const double n = (double)a.n;
     const double cs[3] = {(double)c0, (double)c1, (double)c2};
     a.ctl->est[0] = (double)t;
-    for (int q = 0; q < 3; ++q) {
-      const double m1 = s_tot[2 * q] / n;
-      const double m2 = s_tot[2 * q + 1] / n;
-      a.ctl->est[1 + 2 * q] = cs[q] + m1;
-      a.ctl->est[2 + 2 * q] = m2 - m1 * m1;
-    }
+    est_finish(s_tot, (double)a.n, cs, a.ctl->est + 1);
     a.ctl->est[7] = a.ctl->logml;
     a.ctl->done_est = 0;
   }
+  __syncthreads();
+  publish_summary(a.ctl, a.ctl_mirror);
 }
 
 // Posterior summaries under adaptive resampling: the particles weighted by
@@ -2687,6 +2758,8 @@ __global__ void __launch_bounds__(BLOCK) k_estimate_w(FilterArgs<R> a) {
     a.ctl->est[7] = a.ctl->logml;
     a.ctl->done_est = 0;
   }
+  __syncthreads();
+  publish_summary(a.ctl, a.ctl_mirror);
 }
 
 // Maximum of binary32 input weights (pf_resample): non-negative floats order

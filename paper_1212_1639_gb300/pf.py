@@ -137,6 +137,7 @@ _SIGS = {
     "pf_resample_noalloc": [_V, C.c_uint64, C.c_uint64, C.c_uint32, C.c_uint32, C.c_int32, _V,
                             _V],
     "pf_cdf": [_V, C.c_uint64, _V, _V],
+    "pf_diag_cdf_wait": [_V, C.c_uint64, C.c_uint32, C.c_uint32, _V, _V],
     "pf_cutpoint_search": [_V, C.c_uint64, _V, _V],
     "pf_cutpoint_method": [_V, C.c_uint64, _V, _V, C.c_uint64, _V, _V],
     "pf_batch_create": [C.POINTER(PfConfig), C.c_uint32, C.POINTER(PfBatchOpts), C.POINTER(_V)],
@@ -266,7 +267,10 @@ class Filter:
         self.stream = stream if stream is not None else torch.cuda.Stream()
         if self.stream.cuda_stream == 0:
             raise ValueError("pass a non-default torch.cuda.Stream (the cycle is graph-captured)")
-        self._alloc = TorchAllocator() if torch_alloc else None
+        # torch_alloc: True for torch's caching allocator, False for the
+        # library's own cudaMallocAsync, or an object with ctypes callbacks
+        # .alloc / .free (ALLOC_FN / FREE_FN)
+        self._alloc = TorchAllocator() if torch_alloc is True else (torch_alloc or None)
         cfg = PfConfig(n_particles=self.n, seed=seed, filter_id=filter_id, scheme=self.scheme,
                        precision=self.precision, known_variances=int(bool(known_variances)),
                        x0_mean=x0_mean, x0_var=x0_var, a_sigma=a_sigma, b_sigma=b_sigma,
@@ -379,7 +383,10 @@ class Filter:
         self.stream = stream if stream is not None else torch.cuda.Stream()
         if self.stream.cuda_stream == 0:
             raise ValueError("pass a non-default torch.cuda.Stream (the cycle is graph-captured)")
-        self._alloc = TorchAllocator() if torch_alloc else None
+        # torch_alloc: True for torch's caching allocator, False for the
+        # library's own cudaMallocAsync, or an object with ctypes callbacks
+        # .alloc / .free (ALLOC_FN / FREE_FN)
+        self._alloc = TorchAllocator() if torch_alloc is True else (torch_alloc or None)
         cfg = PfConfig(stream=C.c_void_p(self.stream.cuda_stream))
         if self._alloc is not None:
             cfg.alloc = self._alloc.alloc
@@ -422,7 +429,7 @@ class Batch:
         self.stream = stream if stream is not None else torch.cuda.Stream()
         if self.stream.cuda_stream == 0:
             raise ValueError("pass a non-default torch.cuda.Stream (the cycle is graph-captured)")
-        self._alloc = TorchAllocator() if torch_alloc else None
+        self._alloc = TorchAllocator() if torch_alloc is True else (torch_alloc or None)
         cfgs = [self._cfg(f) for f in filters]
         arr = (PfConfig * max(len(cfgs), 1))(*cfgs)
         opts = PfBatchOpts(max_filters=int(max_filters), hbm_budget_bytes=int(hbm_budget_bytes),
@@ -693,6 +700,18 @@ def cdf(w, stream=None):
     Q = torch.empty(w.numel(), dtype=torch.int64, device=w.device)
     _check(_lib.pf_cdf(_ptr(w), w.numel(), _ptr(Q), _stream_ptr(stream)), "pf_cdf")
     return Q
+
+
+def diag_cdf_wait(w, withhold_tile, spin_limit, stream=None):
+    """pf_diag_cdf_wait: pf_cdf with the look-back wait's test settings.
+    Returns (status code, Q); Q is valid only when the status is PF_OK."""
+    torch = _torch()
+    assert w.is_cuda and w.dtype == torch.float32 and w.is_contiguous()
+    Q = torch.empty(w.numel(), dtype=torch.int64, device=w.device)
+    with torch.cuda.device(w.device):
+        st = _lib.pf_diag_cdf_wait(_ptr(w), w.numel(), int(withhold_tile), int(spin_limit), _ptr(Q),
+                                   _stream_ptr(stream))
+    return st, Q
 
 
 def cutpoint_search(Q, stream=None):

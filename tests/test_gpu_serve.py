@@ -87,6 +87,44 @@ def test_served_results_equal_alone_results(pf, inflight):
     srv.close()
 
 
+def test_served_results_match_the_oracle(pf, orc):
+    """Served results against the CPU oracle directly (not through a
+    standalone GPU filter): each observation's summaries within the parity
+    tolerance (1e-5 relative, or of the posterior sd near zero) of the
+    oracle's after the same observations, streams interleaved in the server."""
+    sizes = {5: 1, 6: 777, 7: 4099, 8: 70001}
+    cfgs = {sid: _cfg(sid, n) for sid, n in sizes.items()}
+    series = {sid: synth.local_level_series(200 + sid, 5, filter_id=sid)[1] for sid in sizes}
+    srv = pf.Server(max_streams=8, hbm_budget_bytes=1 << 30, max_inflight=2, keep_results=True)
+    for sid, c in cfgs.items():
+        srv.open(sid, **c)
+    for k in range(5):
+        for sid in sizes:
+            srv.submit(sid, series[sid][k])
+    for sid in sizes:
+        srv.close_stream(sid)
+    srv.drain(120)
+    by = {}
+    for sid, seq, est, lat, status in srv.poll():
+        assert status == pf.PF_OK
+        by.setdefault(sid, {})[seq] = est
+    srv.close()
+    tol = 1e-5
+    for sid, c in cfgs.items():
+        o = orc.Filter(orc.make_config(c["n"], seed=c["seed"], filter_id=c["filter_id"],
+                                       scheme=orc.SYSTEMATIC, precision=orc.FP32))
+        for k, y in enumerate(series[sid]):
+            o.step(y)
+            eo, eg = o.estimate(), by[sid][k]
+            assert eg["t"] == eo["t"] == k + 1
+            for m, v in (("x", "x_var"), ("sigma2", "sigma2_var"), ("tau2", "tau2_var")):
+                sd = np.sqrt(max(eo[v], 0.0))
+                assert abs(eg[m + "_mean"] - eo[m + "_mean"]) <= tol * max(abs(eo[m + "_mean"]), sd), (sid, k, m)
+                assert abs(eg[v] - eo[v]) <= 10 * tol * abs(eo[v]) + 8e-16 * eo[m + "_mean"] ** 2, (sid, k, v)
+            assert abs(eg["log_marglik"] - eo["log_marglik"]) <= tol * max(1.0, abs(eo["log_marglik"]))
+        o.close()
+
+
 def test_admission_waits_for_budget_and_results_stay_exact(pf):
     """A budget of 25,000 particles: streams that do not fit wait in FIFO
     order and enter as earlier streams close."""
