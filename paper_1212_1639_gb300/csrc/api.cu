@@ -1274,6 +1274,46 @@ pf_status scratch_pool(cudaMemPool_t* out) {
   return PF_OK;
 }
 
+// A pinned, mapped 32-bit error word per host thread (calls on one host
+// thread are sequential: each synchronises its stream before returning).
+pf_status small_err_word(uint32_t** host, uint32_t** dev) {
+  thread_local uint32_t* h = nullptr;
+  thread_local uint32_t* d = nullptr;
+  if (!h) {
+    if (cudaHostAlloc((void**)&h, 64, cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess) {
+      cudaGetLastError();
+      h = nullptr;
+      return set_err(PF_ERR_OOM, "pinned host allocation failed");
+    }
+    if (cudaHostGetDevicePointer((void**)&d, h, 0) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFreeHost(h);
+      h = nullptr;
+      return set_err(PF_ERR_CUDA, "mapped host memory unavailable");
+    }
+  }
+  *host = h;
+  *dev = d;
+  return PF_OK;
+}
+
+// Systematic and stratified resampling of up to SMALL_N weights: one CTA, one
+// launch, no scratch (k_resample_small), the same ancestors as the general path.
+pf_status resample_small(const float* w, uint64_t n, uint64_t seed, uint32_t filter, uint32_t t,
+                         int scheme, uint32_t* anc, cudaStream_t s) {
+  uint32_t *eh = nullptr, *ed = nullptr;
+  pf_status st = small_err_word(&eh, &ed);
+  if (st != PF_OK) return st;
+  *(volatile uint32_t*)eh = 0u;
+  if (scheme == PF_STRATIFIED)
+    k_resample_small<true><<<1, SMALL_THREADS, 0, s>>>(w, (uint32_t)n, seed, filter, t, anc, ed);
+  else
+    k_resample_small<false><<<1, SMALL_THREADS, 0, s>>>(w, (uint32_t)n, seed, filter, t, anc, ed);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));
+  return map_err(*(volatile uint32_t*)eh);
+}
+
 pf_status resample_common(const float* w, uint64_t n, uint64_t seed, uint32_t filter,
                           uint32_t t, int scheme, uint32_t* anc, uint64_t* Q_out, void* stream,
                           WaitDiag dg = WaitDiag()) {
@@ -1281,6 +1321,9 @@ pf_status resample_common(const float* w, uint64_t n, uint64_t seed, uint32_t fi
   if (n < 1 || n > PF_MAX_PARTICLES) return set_err(PF_ERR_INVALID, "n must be in [1, 2^26]");
   if (scheme < 0 || scheme > 4) return set_err(PF_ERR_INVALID, "bad scheme");
   cudaStream_t s = (cudaStream_t)stream;
+  if (anc && !Q_out && n <= SMALL_N && dg.withhold == NO_TILE &&
+      (scheme == PF_SYSTEMATIC || scheme == PF_STRATIFIED))
+    return resample_small(w, n, seed, filter, t, scheme, anc, s);
   Scratch sc;
   const bool multi = anc && is_multinomial(scheme), cut = anc && is_cutpoint(scheme);
   const size_t bytes = scratch_layout(n, Q_out == nullptr, multi, cut, nullptr, &sc);

@@ -1413,6 +1413,10 @@ template <class R, bool STAGED, int PER, bool ESS = false>
 __global__ void __launch_bounds__(BLOCK, PER == 8 ? 4 : 3) k_cdf_sys(FilterArgs<R> a, uint64_t* cta_tot,
                                                                     U128* cta_sq) {
   static_assert(PER == 16 || (PER == 8 && !STAGED && sizeof(R) == 4), "tile shapes");
+  // staged: phase 1 writes e = exp(l - m) back in l's place and phase 2
+  // quantises from e (no second exponential); with ESS, or without
+  // write-back, phase 2 quantises from l again
+  constexpr bool WB = STAGED && !ESS;
   constexpr int TP = BLOCK * PER;  // particles per tile
   typedef typename ESumT<R>::T ES;
   __shared__ uint64_t s_warp[WARPS + 1];
@@ -1608,8 +1612,8 @@ __global__ void __launch_bounds__(BLOCK, PER == 8 ? 4 : 3) k_cdf_sys(FilterArgs<
     R ep;
     // (with ESS l stays in place: a propagation that does not resample
     // carries L - m from it, so phase 2 quantises from l again)
-    quantP(tile, buf, W, &ep, (STAGED && !ESS) ? 1 : 0);
-    if (STAGED && !ESS) fence_proxy_async_smem();  // e in buf, for the bulk store below
+    quantP(tile, buf, W, &ep, WB ? 1 : 0);
+    if (WB) fence_proxy_async_smem();  // e in buf, for the bulk store below
     mine += W[PER - 1];
     if constexpr (ESS) {
       uint64_t prev = 0;
@@ -1626,7 +1630,7 @@ __global__ void __launch_bounds__(BLOCK, PER == 8 ? 4 : 3) k_cdf_sys(FilterArgs<
       s_keep_ep[threadIdx.x] = ep;
     }
     __syncthreads();  // buf is refilled two copies later
-    if (STAGED && !ESS && tile != tb && threadIdx.x == 0) {
+    if (WB && tile != tb && threadIdx.x == 0) {
       // e goes back to l's place in global memory for phase 2, which then
       // needs no exponentials (the first tile's W stay in shared memory)
       const uint64_t first = (uint64_t)tile * TP;
@@ -1711,7 +1715,7 @@ __global__ void __launch_bounds__(BLOCK, PER == 8 ? 4 : 3) k_cdf_sys(FilterArgs<
     } else {
       if (tile + 1 < te) next_issue(tile + 1);
       const R* buf = take_tile(tile);
-      quantP(tile, buf, W, &ep, ESS ? 0 : 2);
+      quantP(tile, buf, W, &ep, WB ? 2 : 0);
     }
     // the tile's first slot S0 = R(carry)
     // (a later tile starts where the previous one ended: no division)
@@ -2760,6 +2764,129 @@ __global__ void __launch_bounds__(BLOCK) k_estimate_w(FilterArgs<R> a) {
   }
   __syncthreads();
   publish_summary(a.ctl, a.ctl_mirror);
+}
+
+// ---------------------------------------------------------------------------
+// Resampling of a small weight vector (n <= SMALL_N) in one CTA, for
+// pf_resample's systematic and stratified schemes: the same quantisation
+// (W_i = floor(w_i 2^(k - e)), max w = f 2^e), the same exact CDF and the same
+// positions as the multi-kernel path, so the same ancestors -- one launch
+// instead of four, no scratch.  Thread t owns particles [PER t, PER t + PER);
+// particle i owns the slots [first(Q_{i-1}), first(Q_i)) with first() the
+// number of slot positions below n Q (systematic: j T + r; stratified:
+// j T + r_j).  Errors go to *err (negative / non-finite / all-zero weights:
+// ERR_WEIGHTS).
+// ---------------------------------------------------------------------------
+constexpr int SMALL_THREADS = 1024;
+constexpr int SMALL_PER = 16;
+constexpr uint64_t SMALL_N = (uint64_t)SMALL_THREADS * SMALL_PER;
+
+template <bool STRAT>
+__global__ void __launch_bounds__(SMALL_THREADS) k_resample_small(const float* w, uint32_t n,
+                                                                   uint64_t seed, uint32_t filter,
+                                                                   uint32_t t, uint32_t* anc,
+                                                                   uint32_t* err) {
+  constexpr int NW = SMALL_THREADS / 32;
+  __shared__ uint32_t s_max[NW];
+  __shared__ uint64_t s_tot[NW];
+  __shared__ int s_bad[NW];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // per = ceil(n / threads) particles per thread, so that small n uses every thread
+  const uint32_t per = (n + SMALL_THREADS - 1) / SMALL_THREADS;
+  const uint32_t base = (uint32_t)threadIdx.x * per;
+  float v[SMALL_PER];
+  uint32_t mx = 0;
+  bool bad = false;
+#pragma unroll
+  for (int e = 0; e < SMALL_PER; ++e) {
+    v[e] = ((uint32_t)e < per && base + e < n) ? w[base + e] : 0.0f;
+    if (!(v[e] >= 0.0f) || !(v[e] < INFINITY)) bad = true;
+    else mx = max(mx, __float_as_uint(v[e]));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  const bool wbad = __any_sync(0xffffffffu, bad);
+  if (lane == 0) { s_max[warp] = mx; s_bad[warp] = wbad; }
+  __syncthreads();
+  mx = 0;
+  bool any_bad = false;
+  for (int i = 0; i < NW; ++i) { mx = max(mx, s_max[i]); any_bad |= s_bad[i] != 0; }
+  if (any_bad || mx == 0) {  // (every thread takes the same branch)
+    if (threadIdx.x == 0) *err = ERR_WEIGHTS;
+    for (uint32_t i = threadIdx.x; i < n; i += SMALL_THREADS) anc[i] = i;
+    return;
+  }
+  int e2;
+  (void)frexpf(__uint_as_float(mx), &e2);
+  int k = 0;
+  {
+    uint32_t c = 0, m1 = n - 1;
+    while (m1) { ++c; m1 >>= 1; }
+    k = 61 - (int)c;  // cdf_shift(n)
+  }
+  const int escale = k - e2;
+  uint64_t Qi[SMALL_PER];
+  uint64_t run = 0;
+#pragma unroll
+  for (int e = 0; e < SMALL_PER; ++e) {
+    if ((uint32_t)e < per && base + e < n) run += f2u64_rz(ldexpf(v[e], escale));
+    Qi[e] = run;
+  }
+  // block exclusive scan of the thread totals
+  const uint64_t incl = warp_incl_scan(run, lane);
+  if (lane == 31) s_tot[warp] = incl;
+  __syncthreads();
+  uint64_t pre = 0, T = 0;
+  for (int i = 0; i < NW; ++i) {
+    const uint64_t v2 = s_tot[i];
+    if (i < warp) pre += v2;
+    T += v2;
+  }
+  const uint64_t o = pre + incl - run;  // Q just before this thread's particles
+  const SysDiv dv = make_sysdiv(T);
+  uint64_t r = 0;
+  if (!STRAT) {
+    const U4 wr = draw(seed, filter, t, 0, P_SYS_OFFSET, 0);
+    r = __umul64hi(((uint64_t)wr.b << 32) | wr.a, T);
+  }
+  auto first = [&](uint64_t q) -> uint64_t {
+    if constexpr (STRAT) return strat_first(q, n, T, dv, seed, filter, t);
+    else return sys_first_slot(q, n, r, dv);
+  };
+  // the first slot of each own particle's successor: f[e] = first(Q_{base+e});
+  // the slots of particle base + e are [f[e-1], f[e]), f[-1] from the lane below
+  uint64_t f[SMALL_PER];
+#pragma unroll
+  for (int e = 0; e < SMALL_PER; ++e)
+    f[e] = ((uint32_t)e < per && base + e < n) ? first(o + Qi[e]) : 0;
+  uint64_t flast = 0;  // first(Q of this thread's last particle): the next thread's start
+  {
+    const uint32_t cnt = base < n ? (n - base < per ? n - base : per) : 0u;
+#pragma unroll
+    for (int e = 0; e < SMALL_PER; ++e)
+      if ((uint32_t)e + 1 == cnt) flast = f[e];
+    if (cnt == 0) flast = n;
+  }
+  uint64_t fprev = __shfl_up_sync(0xffffffffu, flast, 1);
+  if (lane == 0) fprev = threadIdx.x == 0 ? 0 : (base < n ? first(o) : n);
+#pragma unroll
+  for (int e = 0; e < SMALL_PER; ++e) {
+    if ((uint32_t)e >= per) break;  // (per is the same in every thread)
+    const uint32_t i = base + e;
+    const uint64_t fe = i < n ? f[e] : fprev;
+    const uint64_t cnt = fe - fprev;
+    if (cnt <= 32)
+      for (uint64_t q = fprev; q < fe; ++q) anc[q] = i;
+    uint32_t heavy = __ballot_sync(0xffffffffu, cnt > 32);
+    while (heavy) {  // long runs by the whole warp
+      const int l = __ffs(heavy) - 1;
+      heavy &= heavy - 1;
+      const uint64_t s0 = __shfl_sync(0xffffffffu, fprev, l), s1 = __shfl_sync(0xffffffffu, fe, l);
+      const uint32_t vi = __shfl_sync(0xffffffffu, i, l);
+      for (uint64_t q = s0 + lane; q < s1; q += 32) anc[q] = vi;
+    }
+    fprev = fe;
+  }
 }
 
 // Maximum of binary32 input weights (pf_resample): non-negative floats order

@@ -670,14 +670,21 @@ def _resample_out(w, out):
     return out
 
 
+def _on_device(dev, fn):
+    """fn() with dev current (the library works on the current device)."""
+    torch = _torch()
+    if dev.index == torch.cuda.current_device():
+        return fn()
+    with torch.cuda.device(dev):
+        return fn()
+
+
 def resample(w, seed, filter_id=0, t=0, scheme="systematic", out=None, stream=None):
     """Ancestors (int32 CUDA tensor viewed as uint32) for float32 CUDA weights w."""
-    torch = _torch()
     anc = _resample_out(w, out)
     sch = SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
-    with torch.cuda.device(w.device):  # the library works on the current device
-        _check(_lib.pf_resample(_ptr(w), w.numel(), seed, filter_id, t, sch, _ptr(anc),
-                                _stream_ptr(stream)), "pf_resample")
+    _check(_on_device(w.device, lambda: _lib.pf_resample(
+        _ptr(w), w.numel(), seed, filter_id, t, sch, _ptr(anc), _stream_ptr(stream))), "pf_resample")
     return anc
 
 
@@ -685,12 +692,11 @@ def resample_noalloc(w, seed, filter_id=0, t=0, scheme="systematic", out=None, s
     """As resample(), through pf_resample_noalloc: the library allocates nothing
     (its scratch is a fixed device array, n <= NOALLOC_MAX_PARTICLES); `out`,
     when given, is the caller's preallocated int32 output."""
-    torch = _torch()
     anc = _resample_out(w, out)
     sch = SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
-    with torch.cuda.device(w.device):  # the fixed array of w's device
-        _check(_lib.pf_resample_noalloc(_ptr(w), w.numel(), seed, filter_id, t, sch, _ptr(anc),
-                                        _stream_ptr(stream)), "pf_resample_noalloc")
+    _check(_on_device(w.device, lambda: _lib.pf_resample_noalloc(  # the fixed array of w's device
+        _ptr(w), w.numel(), seed, filter_id, t, sch, _ptr(anc), _stream_ptr(stream))),
+        "pf_resample_noalloc")
     return anc
 
 

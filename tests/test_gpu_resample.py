@@ -17,7 +17,7 @@ from paper_1212_1639_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 
-SMALL = [1, 2, 3, 5, 64, 1000, 4095, 4096, 4097, 12345, (1 << 16) + 3]
+SMALL = [1, 2, 3, 5, 64, 1000, 4095, 4096, 4097, 12345, 16383, 16384, 16385, (1 << 16) + 3]
 SCHEMES = [0, 1, 2, 3, 4]
 
 
