@@ -359,6 +359,9 @@ typedef struct {
   pf_alloc_fn alloc;         /* NULL: cudaMallocAsync / cudaFreeAsync */
   pf_free_fn free;
   void* alloc_ctx;
+  int32_t adaptive;          /* nonzero: the pool also holds each particle's carried
+                                log-weight (one more value per particle), so that
+                                filters may set ess_frac > 0 (adaptive resampling) */
 } pf_batch_opts;
 
 typedef struct {
@@ -388,9 +391,10 @@ typedef struct {
 
 /* Create a batch with n initial filters cfgs[0..n) (host array, may be NULL
  * when n = 0) in slots 0..n-1, and enqueue their initialisation (Step 0).
- * Per filter, cfgs[i] supplies n_particles, seed, filter_id, the priors and
- * known-variance settings; its scheme and precision must equal opts'; its
- * stream and allocator fields are ignored.  Errors: PF_ERR_INVALID,
+ * Per filter, cfgs[i] supplies n_particles, seed, filter_id, the priors,
+ * known-variance settings and ess_frac (> 0 only in a batch created with
+ * adaptive != 0); its scheme and precision must equal opts'; its algorithm
+ * must be particle learning; its stream and allocator fields are ignored.  Errors: PF_ERR_INVALID,
  * PF_ERR_OOM, PF_ERR_CUDA, PF_ERR_BUSY (the budget cannot hold the initial
  * filters).  The initialisation runs asynchronously on the batch's stream. */
 pf_status pf_batch_create(const pf_config* cfgs, uint32_t n, const pf_batch_opts* opts,
@@ -497,6 +501,7 @@ typedef struct {
   pf_alloc_fn alloc;          /* NULL: cudaMallocAsync / cudaFreeAsync */
   pf_free_fn free;
   void* alloc_ctx;
+  int32_t adaptive;           /* as pf_batch_opts.adaptive: streams may set ess_frac > 0 */
 } pf_server_opts;
 
 typedef struct {

@@ -38,6 +38,11 @@ struct BatchFilter {
   uint32_t learn;      // 0: sigma^2, tau^2 known (held at their given values)
   double x0_mean, x0_var, a_sigma, b_sigma, a_tau, b_tau, sigma2, tau2;
   double logml;        // accumulated log marginal likelihood
+  // adaptive resampling (ess_frac > 0): resample only when the ESS of the
+  // combined weights falls below ess_frac n; slam = sum_i exp(lambda_i) of the
+  // carried log-weights (n after a resampling)
+  double ess_frac;
+  double slam;
 };
 
 // One entry of an admission list: the slot and its new record.
@@ -58,6 +63,8 @@ template <class R>
 struct BatchArgs {
   StateV<R> st[2];          // pooled particles, ping-pong by each filter's parity
   R* ell;                   // per particle
+  R* lam;                   // per particle: carried log-weights lambda of adaptive
+                            // filters (batches created for them; else NULL)
   uint64_t* Q;              // per particle
   uint64_t* S;              // per particle (multinomial spacing prefix S_0..S_{n-1})
   uint32_t* anc;            // per particle
@@ -188,11 +195,13 @@ struct BatchSmem {
   ES ues[2][NT / BLOCK];         // this round's tile partials, by round parity
   uint64_t SN;                   // S_n, if this CTA produced it
   uint32_t fail;
+  U128 sq;                       // this CTA's exact sum of W^2 (adaptive filters)
   uint32_t work;                 // the group leader's claimed item
   // broadcasts within the CTA
   uint64_t roff, rsum;
   R m;
   uint32_t wb;
+  U128 sqw[NT / 32];             // per-warp sums of W^2 (adaptive filters)
 };
 
 // One cycle of one filter by a group of G CTAs (G = 1: one CTA; G > 1: the
@@ -214,6 +223,7 @@ __device__ __forceinline__ void batch_filter(const BatchArgs<R>& a, const BatchI
   const uint32_t fid = F->filter_id, t = F->t;
   const int k = F->k;
   const bool learn = F->learn != 0;
+  const bool ess = F->ess_frac > 0.0;  // adaptive resampling (the same for the whole group)
   const StateV<R> src = (t & 1) ? a.st[1] : a.st[0];
   const StateV<R> dst = (t & 1) ? a.st[0] : a.st[1];
   const double y = item.y;
@@ -237,7 +247,7 @@ __device__ __forceinline__ void batch_filter(const BatchArgs<R>& a, const BatchI
     const uint64_t hi = lo + PASS < n ? lo + PASS : n;
     for (uint64_t i = lo + 4 * (uint64_t)threadIdx.x; i < hi; i += 4 * NT) {
       if (i + 4 <= hi) {
-        R xv[4], sv[4], tv[4], lv[4];
+        R xv[4], sv[4], tv[4], lv[4], lam4[4];
         if constexpr (sizeof(R) == 4) {
           const float4 X = *reinterpret_cast<const float4*>(src.x + off + i);
           const float4 Sg = *reinterpret_cast<const float4*>(src.s2 + off + i);
@@ -245,15 +255,21 @@ __device__ __forceinline__ void batch_filter(const BatchArgs<R>& a, const BatchI
           xv[0] = X.x; xv[1] = X.y; xv[2] = X.z; xv[3] = X.w;
           sv[0] = Sg.x; sv[1] = Sg.y; sv[2] = Sg.z; sv[3] = Sg.w;
           tv[0] = Tu.x; tv[1] = Tu.y; tv[2] = Tu.z; tv[3] = Tu.w;
+          if (ess) {
+            const float4 Lm = *reinterpret_cast<const float4*>(a.lam + off + i);
+            lam4[0] = Lm.x; lam4[1] = Lm.y; lam4[2] = Lm.z; lam4[3] = Lm.w;
+          }
         } else {
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
             xv[e] = src.x[off + i + e]; sv[e] = src.s2[off + i + e]; tv[e] = src.t2[off + i + e];
+            if (ess) lam4[e] = a.lam[off + i + e];
           }
         }
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
           lv[e] = log_pred<R>(xv[e], sv[e], tv[e], yr);
+          if (ess) lv[e] = lam4[e] + lv[e];  // adaptive filters: L = lambda + l
           fail |= !(lv[e] < (R)INFINITY);  // NaN or +inf
           mx = fmax(mx, lv[e]);
         }
@@ -265,7 +281,8 @@ __device__ __forceinline__ void batch_filter(const BatchArgs<R>& a, const BatchI
         }
       } else {
         for (uint64_t q = i; q < hi; ++q) {
-          const R l = log_pred<R>(src.x[off + q], src.s2[off + q], src.t2[off + q], yr);
+          R l = log_pred<R>(src.x[off + q], src.s2[off + q], src.t2[off + q], yr);
+          if (ess) l = a.lam[off + q] + l;
           fail |= !(l < (R)INFINITY);
           mx = fmax(mx, l);
           a.ell[off + q] = l;
@@ -306,8 +323,10 @@ __device__ __forceinline__ void batch_filter(const BatchArgs<R>& a, const BatchI
     }
   };
 
-  // 2. quantised weights and their inclusive scan, round by round
+  // 2. quantised weights and their inclusive scan, round by round (with
+  // adaptive resampling also the exact sum of W^2)
   uint64_t carry = 0;
+  U128 sq{0, 0};
   for (uint64_t jr = 0; jr < rounds; ++jr, par ^= 1u) {
     const uint64_t pidx = jr * G + rank;
     const uint64_t c0 = pidx * PASS;
@@ -341,6 +360,7 @@ __device__ __forceinline__ void batch_filter(const BatchArgs<R>& a, const BatchI
           const R dl = v[e] - m;
           wq = quant_exp<R>(dl, k, &ex);
           epart = epart + ex;
+          if (ess) sq = add128(sq, mul64(wq, wq));
         }
         run += wq;
         W[4 * q + e] = run;  // inclusive running sum
@@ -394,12 +414,48 @@ __device__ __forceinline__ void batch_filter(const BatchArgs<R>& a, const BatchI
   const uint64_t T = carry;
   if (T == 0) fail = true;
 
+  // adaptive resampling: the decision of the single-filter kernels (k_ess,
+  // k_cdf_sys with ESS) from the same exact sums, T = sum W and B = sum W^2
+  // (B summed warps in order, then the group's CTAs in rank order: an exact
+  // integer sum, identical in every CTA of the group)
+  bool resamp = true;
+  if (ess) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      U128 u;
+      u.hi = __shfl_xor_sync(0xffffffffu, sq.hi, o);
+      u.lo = __shfl_xor_sync(0xffffffffu, sq.lo, o);
+      sq = add128(sq, u);
+    }
+    if (lane == 0) sm.sqw[warp] = sq;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      U128 b = sm.sqw[0];
+      for (int w = 1; w < NW; ++w) b = add128(b, sm.sqw[w]);
+      sm.sq = b;
+    }
+    group_sync(G);
+    U128 B = sm.sq;
+    if (G > 1) {
+      B = dsm_ld(&sm.sq, 0u);
+      for (uint32_t r2 = 1; r2 < G; ++r2) B = add128(B, dsm_ld(&sm.sq, r2));
+    }
+    const double Ad = __ull2double_rn(T);
+    const double Bd = u128_to_f64_rn(B);
+    const double lhs = Ad * Ad;
+    const double f = F->ess_frac * (double)n;
+    const double rhs = f * Bd;
+    resamp = lhs < rhs;
+  }
+
   // 3. resampling: slot keys B_j against the CDF keys Q_i A (ties go to the
   // CDF); thread t walks the particles [16 t, 16 t + 16) of each of this
   // CTA's passes from its first slot; a particle with more than BB_CAP slots
   // leaves a run for the whole CTA
   uint64_t A = n, r = 0;
-  if (POS == POS_SYSTEMATIC) {
+  if (!resamp) {
+    // an adaptive filter that keeps its particles this cycle: no keys
+  } else if (POS == POS_SYSTEMATIC) {
     const U4 wr = draw(seed, fid, t, 0, P_SYS_OFFSET, 0);
     const uint64_t Rw = ((uint64_t)wr.b << 32) | wr.a;
     r = __umul64hi(Rw, T);
@@ -457,7 +513,7 @@ __device__ __forceinline__ void batch_filter(const BatchArgs<R>& a, const BatchI
   const uint64_t* Sf = a.S + off;
   if (threadIdx.x == 0) sm.nruns = 0;
   __syncthreads();
-  for (uint64_t jr = 0; jr < rounds; ++jr) {
+  for (uint64_t jr = 0; resamp && jr < rounds; ++jr) {
     const uint64_t ib = (jr * G + rank) * PASS + (uint64_t)threadIdx.x * SCAN_PER;
     if (T > 0 && ib < n) {
       const uint64_t ie = ib + SCAN_PER < n ? ib + SCAN_PER : n;
@@ -536,7 +592,9 @@ __device__ __forceinline__ void batch_filter(const BatchArgs<R>& a, const BatchI
     if (threadIdx.x == 0) sm.nruns = 0;
     __syncthreads();
   }
-  if (T == 0) {  // empty CDF (flagged): keep every index in range
+  if (T == 0 || !resamp) {
+    // an empty CDF (flagged): keep every index in range; an adaptive filter
+    // that keeps its particles: every slot is its own ancestor
     for (uint64_t j = rank * NT + threadIdx.x; j < n; j += (uint64_t)G * NT)
       a.anc[off + j] = (uint32_t)j;
   }
@@ -562,7 +620,7 @@ __device__ __forceinline__ void batch_filter(const BatchArgs<R>& a, const BatchI
   StateV<R> fsrc = src;
   fsrc.x += off; fsrc.s2 += off; fsrc.t2 += off; fsrc.bs += off; fsrc.bt += off;
   auto gather_slot = [&](uint64_t jj) {
-    uint32_t an = jj < n ? a.anc[off + jj] : 0u;
+    uint32_t an = jj < n ? (resamp ? a.anc[off + jj] : (uint32_t)jj) : 0u;
     an = an < n ? an : (uint32_t)(n - 1);
     return gather_rec<R>(fsrc, an);
   };
@@ -608,6 +666,9 @@ __device__ __forceinline__ void batch_filter(const BatchArgs<R>& a, const BatchI
         dst.bs[d] = cur.bs;
         dst.bt[d] = cur.bt;
       }
+      // adaptive filters: the carried log-weight, 0 after a resampling, else
+      // L_j - m (a trial cycle leaves it alone)
+      if (ess && a.commit) a.lam[d] = resamp ? (R)0 : a.ell[d] - m;
     }
     // queue the draws that missed the squeeze (rare); the warp finishes them
     // 32 at a time
@@ -638,8 +699,17 @@ __device__ __forceinline__ void batch_filter(const BatchArgs<R>& a, const BatchI
     if (lane == 0 && a.commit) {
       const double LOG_2PI = 0x1.d67f1c864beb5p+0;
       const double md = (double)m;
-      const double inc = md + log(esum_value(acc)) - log((double)n) - 0.5 * LOG_2PI;
-      F->logml = F->logml + inc;
+      if (ess) {
+        // normalised by the carried weights: log sum_i exp(lambda_i), which
+        // is n after a resampling, else this cycle's sum of exp(L_i - m)
+        const double S = esum_value(acc);
+        const double inc = md + log(S) - log(F->slam) - 0.5 * LOG_2PI;
+        F->logml = F->logml + inc;
+        F->slam = resamp ? (double)n : S;
+      } else {
+        const double inc = md + log(esum_value(acc)) - log((double)n) - 0.5 * LOG_2PI;
+        F->logml = F->logml + inc;
+      }
       if (any_fail) F->err |= ERR_NUMERIC;
       F->t = t + 1;
     }
@@ -704,6 +774,7 @@ __global__ void __launch_bounds__(BB) k_batch_init(BatchArgs<R> a) {
     const uint64_t off = rec->off, n = rec->n, seed = rec->seed;
     const uint32_t fid = rec->filter_id;
     const bool learn = rec->learn != 0;
+    const bool ess = rec->ess_frac > 0.0;
     __syncthreads();
     if (threadIdx.x == 0) {
       *F = *rec;
@@ -728,6 +799,7 @@ __global__ void __launch_bounds__(BB) k_batch_init(BatchArgs<R> a) {
       st.x[g] = x0m + p;
       st.bs[g] = bs0;
       st.bt[g] = bt0;
+      if (ess) a.lam[g] = (R)0;  // adaptive filters start with equal weights
       if (!learn) {
         st.s2[g] = (R)rec->sigma2;
         st.t2[g] = (R)rec->tau2;
@@ -744,6 +816,72 @@ __global__ void __launch_bounds__(BB) k_batch_init(BatchArgs<R> a) {
   }
 }
 
+// Posterior summaries of one adaptive filter (item w of the list) by one CTA:
+// the particles weighted by w_i = exp(lambda_i), in the single-filter weighted
+// estimate's groups (BLOCK x EST_PER_THREAD per virtual block, consecutive
+// particles per thread, binary64 per particle, shifted by particle 0), each
+// group's sums by the same shuffle tree and warps in order, the group sums
+// folded in group order -- so the summaries equal a standalone filter's.
+template <class R>
+__device__ __forceinline__ void batch_estimate_weighted(const BatchArgs<R>& a,
+                                                        const BatchFilter* F, uint32_t w,
+                                                        const StateV<R>& st, R c0, R c1, R c2,
+                                                        double (*s_sum)[WARPS], double* s_tot) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr uint64_t GROUP = (uint64_t)BLOCK * EST_PER_THREAD;
+  const uint64_t off = F->off, n = F->n;
+  const int k = F->k;
+  if (threadIdx.x < 7) s_tot[threadIdx.x] = 0.0;
+  const uint64_t nblk = (n + GROUP - 1) / GROUP;
+  for (uint64_t b = 0; b < nblk; ++b) {
+    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    const uint64_t base = b * GROUP + (uint64_t)threadIdx.x * EST_PER_THREAD;
+    for (int e = 0; e < EST_PER_THREAD; ++e) {
+      const uint64_t i = base + e;
+      if (i < n) {
+        R wr;
+        (void)quant_exp<R>(a.lam[off + i], k, &wr);
+        const double wd = (double)wr;
+        const double dx = (double)(st.x[off + i] - c0), ds = (double)(st.s2[off + i] - c1),
+                     dt = (double)(st.t2[off + i] - c2);
+        acc[0] += wd;
+        acc[1] += wd * dx; acc[2] += wd * (dx * dx);
+        acc[3] += wd * ds; acc[4] += wd * (ds * ds);
+        acc[5] += wd * dt; acc[6] += wd * (dt * dt);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 7; ++q) {
+      double v = acc[q];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) s_sum[q][warp] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 7) {
+      double v = 0;
+      for (int ww = 0; ww < WARPS; ++ww) v += s_sum[threadIdx.x][ww];
+      s_tot[threadIdx.x] += v;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double sw = s_tot[0];
+    const double cs[3] = {(double)c0, (double)c1, (double)c2};
+    double* o = a.est + (uint64_t)w * BATCH_EST_ROW;
+    o[0] = (double)F->t;
+    for (int q = 0; q < 3; ++q) {
+      const double m1 = s_tot[1 + 2 * q] / sw;
+      const double m2 = s_tot[2 + 2 * q] / sw;
+      o[1 + 2 * q] = cs[q] + m1;
+      o[2 + 2 * q] = m2 - m1 * m1;
+    }
+    o[7] = F->logml;
+    o[8] = (double)F->err;
+  }
+  __syncthreads();
+}
+
 // Posterior summaries of the listed filters, one filter per CTA pass.  The
 // particles are taken in the single-filter estimate's groups (BLOCK x
 // EST_PER_THREAD per virtual block, consecutive particles per thread, shifted
@@ -753,9 +891,9 @@ __global__ void __launch_bounds__(BB) k_batch_init(BatchArgs<R> a) {
 template <class R>
 __global__ void __launch_bounds__(BB) k_batch_estimate(BatchArgs<R> a) {
   static_assert(BB == BLOCK, "the fold mirrors the single-filter estimate's");
-  __shared__ double s_sum[6][WARPS];
+  __shared__ double s_sum[7][WARPS];
   __shared__ double s_col[6][BB];
-  __shared__ double s_tot[6];
+  __shared__ double s_tot[7];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t count = *a.count;
   constexpr uint64_t GROUP = (uint64_t)BLOCK * EST_PER_THREAD;
@@ -766,6 +904,10 @@ __global__ void __launch_bounds__(BB) k_batch_estimate(BatchArgs<R> a) {
     const StateV<R> st = (t & 1) ? a.st[1] : a.st[0];
     const R c0 = st.x[off], c1 = st.s2[off], c2 = st.t2[off];
     __syncthreads();
+    if (F->ess_frac > 0.0) {
+      batch_estimate_weighted<R>(a, F, w, st, c0, c1, c2, s_sum, s_tot);
+      continue;
+    }
 #pragma unroll
     for (int q = 0; q < 6; ++q) s_col[q][threadIdx.x] = 0.0;
     const uint64_t nblk = (n + GROUP - 1) / GROUP;

@@ -17,6 +17,7 @@ struct pf_batch {
   int scheme = 0;          // as configured (cut-point variants give the same ancestors)
   int pos = 0;             // POS_MULTINOMIAL or POS_SYSTEMATIC
   bool fp64 = false;
+  bool adaptive = false;   // the pool carries lambda: filters may resample adaptively
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   pf_alloc_fn alloc = nullptr;
@@ -28,6 +29,7 @@ struct pf_batch {
   std::vector<void*> allocs;
   void* x[2] = {}; void* s2[2] = {}; void* t2[2] = {}; void* bs[2] = {}; void* bt[2] = {};
   void* ell = nullptr;
+  void* lam = nullptr;               // adaptive batches: carried log-weights
   uint64_t* Q = nullptr;
   uint64_t* S = nullptr;
   uint32_t* anc = nullptr;
@@ -98,10 +100,11 @@ pf_status batch_alloc(pf_batch* b, size_t bytes, void** out) {
   return PF_OK;
 }
 
-uint64_t batch_bytes_per_particle(bool fp64, bool multi) {
+uint64_t batch_bytes_per_particle(bool fp64, bool multi, bool adaptive) {
   const uint64_t rs = fp64 ? 8 : 4;
-  // x, sigma^2, tau^2 and b_sigma, b_tau, both parities; l; Q; ancestors; S
-  return 2 * (3 * rs + 2 * 8) + rs + 8 + 4 + (multi ? 8 : 0);
+  // x, sigma^2, tau^2 and b_sigma, b_tau, both parities; l; Q; ancestors; S;
+  // lambda
+  return 2 * (3 * rs + 2 * 8) + rs + 8 + 4 + (multi ? 8 : 0) + (adaptive ? rs : 0);
 }
 
 template <class R>
@@ -116,6 +119,7 @@ BatchArgs<R> batch_args(pf_batch* b) {
     a.st[p].bt = (Bt*)b->bt[p];
   }
   a.ell = (R*)b->ell;
+  a.lam = (R*)b->lam;
   a.Q = b->Q;
   a.S = b->S;
   a.anc = b->anc;
@@ -224,8 +228,10 @@ pf_status validate_member(const pf_batch* b, const pf_config* c) {
     return set_err(PF_ERR_INVALID, "prior scales must be > 0 and x0_var >= 0");
   if (c->known_variances && !(c->sigma2 > 0 && c->tau2 > 0))
     return set_err(PF_ERR_INVALID, "known variances must be > 0");
-  if (c->ess_frac != 0.0)
-    return set_err(PF_ERR_INVALID, "batched and served filters resample every cycle");
+  if (!(c->ess_frac >= 0.0 && c->ess_frac <= 1.0))
+    return set_err(PF_ERR_INVALID, "ess_frac must be in [0, 1]");
+  if (c->ess_frac > 0.0 && !b->adaptive)
+    return set_err(PF_ERR_INVALID, "ess_frac > 0 needs a batch created with adaptive = 1");
   return PF_OK;
 }
 
@@ -295,6 +301,8 @@ bool batch_reserve(pf_batch* b, const pf_config& c, uint32_t* slot_out) {
   f.a_sigma = c.a_sigma; f.b_sigma = c.b_sigma;
   f.a_tau = c.a_tau; f.b_tau = c.b_tau;
   f.sigma2 = c.sigma2; f.tau2 = c.tau2;
+  f.ess_frac = c.ess_frac;
+  f.slam = (double)c.n_particles;  // sum of exp(lambda_i) with lambda = 0
   b->Fh[slot] = f;
   b->used += len;
   b->resident++;
@@ -416,11 +424,12 @@ pf_status pf_batch_create(const pf_config* cfgs, uint32_t n, const pf_batch_opts
   b->scheme = opts->scheme;
   b->pos = is_multinomial(opts->scheme) ? POS_MULTINOMIAL : POS_SYSTEMATIC;
   b->fp64 = opts->precision == PF_FP64;
+  b->adaptive = opts->adaptive != 0;
   b->alloc = opts->alloc;
   b->free = opts->free;
   b->alloc_ctx = opts->alloc_ctx;
   b->max_filters = maxf;
-  b->bytes_per_particle = batch_bytes_per_particle(b->fp64, b->pos == POS_MULTINOMIAL);
+  b->bytes_per_particle = batch_bytes_per_particle(b->fp64, b->pos == POS_MULTINOMIAL, b->adaptive);
   auto bail = [&](pf_status s) {
     pf_batch_destroy(b);
     return s;
@@ -467,6 +476,7 @@ pf_status pf_batch_create(const pf_config* cfgs, uint32_t n, const pf_batch_opts
     if ((st = batch_alloc(b, pool * 8, &b->bt[p])) != PF_OK) return bail(st);
   }
   if ((st = batch_alloc(b, pool * rs, &b->ell)) != PF_OK) return bail(st);
+  if (b->adaptive && (st = batch_alloc(b, pool * rs, &b->lam)) != PF_OK) return bail(st);
   if ((st = batch_alloc(b, pool * 8, (void**)&b->Q)) != PF_OK) return bail(st);
   if (b->pos == POS_MULTINOMIAL && (st = batch_alloc(b, pool * 8, (void**)&b->S)) != PF_OK) return bail(st);
   if ((st = batch_alloc(b, pool * 4, (void**)&b->anc)) != PF_OK) return bail(st);

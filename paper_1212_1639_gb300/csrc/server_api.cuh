@@ -411,6 +411,7 @@ pf_status pf_server_create(const pf_server_opts* opts, pf_server** out) {
   bo.hbm_budget_bytes = opts->hbm_budget_bytes;
   bo.scheme = opts->scheme;
   bo.precision = opts->precision;
+  bo.adaptive = opts->adaptive;
   bo.stream = opts->stream;
   bo.alloc = opts->alloc;
   bo.free = opts->free;

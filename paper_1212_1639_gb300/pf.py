@@ -59,7 +59,7 @@ class PfBatchOpts(C.Structure):
     _fields_ = [("max_filters", C.c_uint32), ("hbm_budget_bytes", C.c_uint64),
                 ("scheme", C.c_int32), ("precision", C.c_int32), ("autotune", C.c_int32),
                 ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN),
-                ("alloc_ctx", C.c_void_p)]
+                ("alloc_ctx", C.c_void_p), ("adaptive", C.c_int32)]
 
 
 BATCH_MAX_SHAPES = 16
@@ -87,7 +87,7 @@ class PfServerOpts(C.Structure):
                 ("block", C.c_uint32), ("grid", C.c_uint32),
                 ("cluster", C.c_uint32), ("big_min", C.c_uint32), ("warmup_s", C.c_double),
                 ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN),
-                ("alloc_ctx", C.c_void_p)]
+                ("alloc_ctx", C.c_void_p), ("adaptive", C.c_int32)]
 
 
 class PfServerResult(C.Structure):
@@ -226,14 +226,16 @@ class TorchAllocator:
 
 def filter_config(n, seed=1212, filter_id=0, scheme="systematic", precision="fp32",
                   x0_mean=0.0, x0_var=10.0, a_sigma=3.0, b_sigma=2.0, a_tau=3.0, b_tau=2.0,
-                  known_variances=False, sigma2=1.0, tau2=0.1):
-    """A pf_config for one filter (stream and allocator fields left empty)."""
+                  known_variances=False, sigma2=1.0, tau2=0.1, ess_frac=0.0):
+    """A pf_config for one filter (stream and allocator fields left empty);
+    ess_frac > 0: adaptive resampling (batches and servers created with
+    adaptive=True)."""
     return PfConfig(n_particles=int(n), seed=int(seed), filter_id=int(filter_id),
                     scheme=SCHEMES[scheme] if isinstance(scheme, str) else int(scheme),
                     precision=FP64 if precision in ("fp64", FP64) else FP32,
                     known_variances=int(bool(known_variances)), x0_mean=x0_mean, x0_var=x0_var,
                     a_sigma=a_sigma, b_sigma=b_sigma, a_tau=a_tau, b_tau=b_tau,
-                    sigma2=sigma2, tau2=tau2)
+                    sigma2=sigma2, tau2=tau2, ess_frac=float(ess_frac))
 
 
 # Checkpoint header: magic, format version, header size, n, seed, filter id,
@@ -422,7 +424,8 @@ class Batch:
     slots 0..len(filters)-1."""
 
     def __init__(self, filters=(), scheme="systematic", precision="fp32", max_filters=0,
-                 hbm_budget_bytes=0, autotune=False, stream=None, torch_alloc=True):
+                 hbm_budget_bytes=0, autotune=False, stream=None, torch_alloc=True,
+                 adaptive=False):
         torch = _torch()
         self.scheme = SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
         self.precision = FP64 if precision in ("fp64", FP64) else FP32
@@ -434,7 +437,7 @@ class Batch:
         arr = (PfConfig * max(len(cfgs), 1))(*cfgs)
         opts = PfBatchOpts(max_filters=int(max_filters), hbm_budget_bytes=int(hbm_budget_bytes),
                            scheme=self.scheme, precision=self.precision,
-                           autotune=int(bool(autotune)),
+                           autotune=int(bool(autotune)), adaptive=int(bool(adaptive)),
                            stream=C.c_void_p(self.stream.cuda_stream))
         if self._alloc is not None:
             opts.alloc = self._alloc.alloc
@@ -570,7 +573,7 @@ class Server:
 
     def __init__(self, max_streams, hbm_budget_bytes, scheme="systematic", precision="fp32",
                  max_inflight=2, keep_results=False, block=0, grid=0, cluster=0, big_min=0,
-                 warmup_s=0.0, stream=None, torch_alloc=True):
+                 warmup_s=0.0, stream=None, torch_alloc=True, adaptive=False):
         torch = _torch()
         self.scheme = SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
         self.precision = FP64 if precision in ("fp64", FP64) else FP32
@@ -583,6 +586,7 @@ class Server:
                             max_inflight=int(max_inflight), keep_results=int(bool(keep_results)),
                             block=int(block), grid=int(grid), cluster=int(cluster),
                             big_min=int(big_min), warmup_s=float(warmup_s),
+                            adaptive=int(bool(adaptive)),
                             stream=C.c_void_p(self.stream.cuda_stream))
         if self._alloc is not None:
             opts.alloc = self._alloc.alloc

@@ -231,6 +231,116 @@ def test_batch_launch_shapes_change_no_result(pf, scheme):
     ref.close()
 
 
+ESS = [0.5, 0.0, 0.9, 0.3, 1e-9, 0.5, 0.7]  # per filter of SIZES: adaptive next to plain
+
+
+@pytest.mark.parametrize("scheme,prec", [(1, 0), (0, 0), (1, 1)])
+def test_batch_adaptive_matches_oracle_and_standalone(pf, orc, scheme, prec):
+    """Adaptive resampling per filter (ess_frac > 0) in an adaptive batch,
+    beside plain filters: each filter's ancestors at every cycle (the
+    identity when it does not resample) equal the oracle's and a standalone
+    filter's, its particles equal both bit for bit, its summaries and log-ML
+    equal the standalone filter's bit for bit and the oracle's within the
+    tolerance.  An outlying observation at cycle 4 makes every adaptive filter
+    resample there; both branches occur."""
+    T = 12
+    specs = [_spec(i, n, ess_frac=e) for i, (n, e) in enumerate(zip(SIZES, ESS))]
+    ys = [_series(i, T) for i in range(len(specs))]
+    for y in ys:
+        y[4] += 12.0
+    b = pf.Batch(specs, scheme=scheme, precision=PREC[prec], adaptive=True)
+    alone = [_standalone(pf, s, scheme, prec) for s in specs]
+    orcs = [_oracle(orc, s, scheme, prec) for s in specs]
+    kinds = np.zeros((T, len(specs)), bool)
+    y = np.zeros(b.max_filters)
+    for t in range(T):
+        for i in range(len(specs)):
+            y[i] = ys[i][t]
+            alone[i].step(ys[i][t])
+            orcs[i].step(ys[i][t])
+            kinds[t, i] = orcs[i].resampled()
+        b.step(y)
+        for i in range(len(specs)):
+            got = _u32(b.ancestors(i))
+            assert np.array_equal(got, orcs[i].ancestors()), (t, i, kinds[t, i])
+            assert np.array_equal(got, _u32(alone[i].ancestors())), (t, i)
+        if t % 4 == 3:
+            est = b.estimates()
+            for i in range(len(specs)):
+                assert est[i] == alone[i].estimate(), (t, i)
+    both = [i for i, e in enumerate(ESS) if 0 < kinds[:, i].sum() < T]
+    assert len(both) >= 3, kinds.sum(axis=0)   # adaptive filters that took both branches
+    est = b.estimates()
+    for i, s in enumerate(specs):
+        pb = _raw(b.particles(i), prec)
+        _same_particles(pb, _raw(alone[i].particles(), prec))
+        _same_particles(pb, orcs[i].state_raw())
+        assert est[i] == alone[i].estimate(), i
+        _close_to_oracle(est[i], orcs[i].estimate(), prec)
+        alone[i].close()
+        orcs[i].close()
+    b.close()
+
+
+def test_batch_adaptive_shapes_trials_and_admission(pf):
+    """Adaptive filters under clusters (the ESS sums exchanged between the
+    CTAs of a cluster), autotuner trial cycles (which must leave the carried
+    log-weights alone) and admission into a reused pool range: all equal
+    standalone adaptive filters bit for bit.  A plain batch refuses
+    ess_frac > 0 and an adaptive batch reports the larger per-particle size."""
+    sizes = [140001, 70000, 9000, 4099, 300, 20000]
+    specs = [_spec(i, n, ess_frac=0.6 if i % 2 == 0 else 0.4) for i, n in enumerate(sizes)]
+    T = 8
+    ys = [_series(i, T) for i in range(len(specs))]
+    for y in ys:
+        y[5] -= 10.0
+    plain = pf.Batch([_spec(0, 32)], max_filters=1)
+    with pytest.raises(pf.PfError) as e:
+        plain.add(**_spec(1, 100, ess_frac=0.5))
+    assert e.value.status == pf.PF_ERR_INVALID
+    per = plain.info()["bytes_per_particle"]
+    plain.close()
+    tuned = pf.Batch(specs, adaptive=True, autotune=True)
+    assert tuned.info()["bytes_per_particle"] == per + 4
+    shaped = []
+    for cl in (2, 8):
+        o = pf.Batch(specs, adaptive=True)
+        o.set_shape(256, cl * 3, cl, 1)
+        shaped.append(o)
+    alone = [_standalone(pf, s, 1, 0) for s in specs]
+    for t in range(T):
+        y = np.array([ys[i][t] for i in range(len(specs))])
+        for i in range(len(specs)):
+            alone[i].step(y[i])
+        for bb in [tuned] + shaped:
+            bb.step(y)
+    assert tuned.info()["tuned"] == 1
+    for bb in [tuned] + shaped:
+        est = bb.estimates()
+        for i in range(len(specs)):
+            assert est[i] == alone[i].estimate(), i
+            _same_particles(_raw(bb.particles(i), 0), _raw(alone[i].particles(), 0))
+        bb.close()
+    for a in alone:
+        a.close()
+    # a filter admitted into a freed range starts from equal weights
+    b = pf.Batch([_spec(0, 9000, ess_frac=0.5), _spec(1, 5000)], adaptive=True, max_filters=2)
+    y = np.array([0.2, -0.1])
+    for t in range(5):
+        b.step(y + t)
+    b.remove(0)
+    s = b.add(**_spec(2, 8000, ess_frac=0.5))
+    ref = _standalone(pf, _spec(2, 8000, ess_frac=0.5), 1, 0)
+    for t in range(6):
+        v = 0.3 * t - (9.0 if t == 2 else 0.0)
+        ref.step(v)
+        b.step(np.array([v, 0.0]), np.array([1, 0], np.uint8))
+    assert b.estimates()[s] == ref.estimate()
+    _same_particles(_raw(b.particles(s), 0), _raw(ref.particles(), 0))
+    ref.close()
+    b.close()
+
+
 def test_batch_at_full_size_matches_oracle_on_sampled_filters(pf, orc):
     """The benchmark's batch: 4096 filters, N log-uniform in [256, 65536]
     (about 4.7e7 particles), each with its own series from prior-drawn

@@ -22,7 +22,7 @@ def _cfg(i, n):
 
 def _alone(pf, cfg, ys):
     f = pf.Filter(cfg["n"], seed=cfg["seed"], filter_id=cfg["filter_id"], scheme="systematic",
-                  precision="fp32")
+                  precision="fp32", ess_frac=cfg.get("ess_frac", 0.0))
     out = []
     for y in ys:
         f.step(y)
@@ -123,6 +123,34 @@ def test_served_results_match_the_oracle(pf, orc):
                 assert abs(eg[v] - eo[v]) <= 10 * tol * abs(eo[v]) + 8e-16 * eo[m + "_mean"] ** 2, (sid, k, v)
             assert abs(eg["log_marglik"] - eo["log_marglik"]) <= tol * max(1.0, abs(eo["log_marglik"]))
         o.close()
+
+
+def test_served_adaptive_streams(pf):
+    """A server created for adaptive resampling: streams with ess_frac > 0
+    beside plain ones, interleaved, two cycles in flight; every result equals
+    a standalone filter's of the same configuration."""
+    sizes = {1: 3000, 2: 70001, 3: 512, 4: 20000, 5: 9}
+    cfgs = {sid: dict(_cfg(sid, n), ess_frac=(0.5 if sid % 2 else 0.0)) for sid, n in sizes.items()}
+    series = {sid: synth.local_level_series(90 + sid, 8, filter_id=sid)[1] for sid in sizes}
+    for sid in sizes:
+        series[sid][3] += 10.0
+    srv = pf.Server(max_streams=8, hbm_budget_bytes=1 << 30, max_inflight=2, keep_results=True,
+                    adaptive=True)
+    for sid, c in cfgs.items():
+        srv.open(sid, **c)
+    for k in range(8):
+        for sid in sizes:
+            srv.submit(sid, series[sid][k])
+    for sid in sizes:
+        srv.close_stream(sid)
+    srv.drain(120)
+    _check_against_alone(pf, srv.poll(), cfgs, series)
+    srv.close()
+    plain = pf.Server(max_streams=2, hbm_budget_bytes=1 << 26)
+    with pytest.raises(pf.PfError) as e:
+        plain.open(1, **dict(_cfg(1, 100), ess_frac=0.5))
+    assert e.value.status == pf.PF_ERR_INVALID
+    plain.close()
 
 
 def test_admission_waits_for_budget_and_results_stay_exact(pf):
