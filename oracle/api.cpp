@@ -80,6 +80,20 @@ void or_normals_f64(uint64_t seed, uint32_t filter, uint32_t t, uint32_t purpose
     out[j] = bm_normal<double>(draw(seed, filter, t, (uint32_t)j, purpose, 0));
 }
 
+// The propagation draws of slots 0..n-1: out[5 j + (0..4)] = Zx, Zs, Us, Zt, Ut.
+void or_theta_draws_f32(uint64_t seed, uint32_t filter, uint32_t t, uint64_t n, float* out) {
+  for (uint64_t j = 0; j < n; ++j) {
+    float* o = out + 5 * j;
+    theta_draws<float>(seed, filter, t, (uint32_t)j, o, o + 1, o + 2, o + 3, o + 4);
+  }
+}
+void or_theta_draws_f64(uint64_t seed, uint32_t filter, uint32_t t, uint64_t n, double* out) {
+  for (uint64_t j = 0; j < n; ++j) {
+    double* o = out + 5 * j;
+    theta_draws<double>(seed, filter, t, (uint32_t)j, o, o + 1, o + 2, o + 3, o + 4);
+  }
+}
+
 int or_gamma_f32(double a, uint64_t seed, uint32_t filter, uint32_t t, uint32_t purpose,
                  uint64_t n, float* out) {
   double d, c, K;

@@ -60,6 +60,8 @@ def _declare(L):
         "or_quant_exp_f64": (V, [f64p, U64, I, u64p, f64p]),
         "or_normals_f32": (V, [U64, U32, U32, U32, U64, f32p]),
         "or_normals_f64": (V, [U64, U32, U32, U32, U64, f64p]),
+        "or_theta_draws_f32": (V, [U64, U32, U32, U64, f32p]),
+        "or_theta_draws_f64": (V, [U64, U32, U32, U64, f64p]),
         "or_gamma_f32": (I, [D, U64, U32, U32, U32, U64, f32p]),
         "or_gamma_f64": (I, [D, U64, U32, U32, U32, U64, f64p]),
         "or_mt_constants": (V, [D, f64p]),
@@ -174,6 +176,14 @@ def normals(seed, filt, t, purpose, n, dtype=np.float32):
     out = np.zeros(n, dtype)
     f = lib().or_normals_f32 if dtype == np.float32 else lib().or_normals_f64
     f(seed, filt, t, purpose, n, out)
+    return out
+
+
+def theta_draws(seed, filt, t, n, dtype=np.float32):
+    """The propagation draws of slots 0..n-1 at cycle t: columns Zx, Zs, Us, Zt, Ut."""
+    out = np.zeros((n, 5), dtype)
+    f = lib().or_theta_draws_f32 if dtype == np.float32 else lib().or_theta_draws_f64
+    f(seed, filt, t, n, out)
     return out
 
 

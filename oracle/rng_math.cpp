@@ -397,14 +397,32 @@ template <class R> R gamma_mt(R d, R c, R K, uint64_t seed, uint32_t filter, uin
                           purpose, fail);
 }
 
+// The draws of one propagation step for slot j (Algorithm "Particle
+// Learning", Steps 2 and 4): the state normal Zx, and the first normal and
+// uniform of the sigma^2 and tau^2 gamma draws.  Draw A = (j, t, STATE, 0):
+// its Box-Muller pair gives Zx (cos) and Zs (sin), its word 2 gives Us.
+// binary32: slots 2i and 2i + 1 share draw B = (i, t, STATE, 1): the two
+// outputs of its Box-Muller pair are their tau^2 normals (cos to the even
+// slot, sin to the odd one) and its words 2 and 3 their uniforms -- three
+// 128-bit draws and three Box-Muller transforms per two slots.  binary64
+// (whose Box-Muller takes three words and whose uniform takes the fourth):
+// B = (j, t, STATE, 1) per slot, its first output and its uniform.
 template <class R> void theta_draws(uint64_t seed, uint32_t filter, uint32_t t, uint32_t j,
                                     R* Zx, R* Zs, R* Us, R* Zt, R* Ut) {
   W4 A = draw(seed, filter, t, j, P_STATE, 0);
-  W4 B = draw(seed, filter, t, j, P_STATE, 1);
   bm_normal2<R>(A, Zx, Zs);
   *Us = extra_uniform<R>(A);
-  *Zt = bm_normal<R>(B);
-  *Ut = extra_uniform<R>(B);
+  if (sizeof(R) == 4) {
+    W4 B = draw(seed, filter, t, j >> 1, P_STATE, 1);
+    R zc, zs;
+    bm_normal2<R>(B, &zc, &zs);
+    *Zt = (j & 1) ? zs : zc;
+    *Ut = (R)unif_f32((j & 1) ? B.w[3] : B.w[2]);
+  } else {
+    W4 B = draw(seed, filter, t, j, P_STATE, 1);
+    *Zt = bm_normal<R>(B);
+    *Ut = extra_uniform<R>(B);
+  }
 }
 
 template double det_log<double>(double);

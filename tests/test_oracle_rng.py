@@ -179,3 +179,31 @@ def test_streams_differ_by_purpose_and_time(orc):
     e = orc.draws(9, 0, 0, 0, 1024, orc.P_STATE, attempt=1)
     words = [x.tobytes() for x in (a, b, c, d, e)]
     assert len(set(words)) == 5
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_theta_draws_law(orc, dtype):
+    """The propagation draws of a cycle: Zx, Zs, Zt standard normal and Us, Ut uniform,
+    all mutually uncorrelated within a slot and between the two slots of a pair (in
+    binary32 the pair 2i, 2i + 1 takes its tau^2 normals from one Box-Muller transform
+    and its two uniforms from one draw), and the pair's tau^2 normals jointly standard
+    bivariate normal: angle uniform, squared radius chi-square with 2 degrees of freedom."""
+    n = 200_000
+    d = orc.theta_draws(77, 3, 12, n, dtype).astype(np.float64)
+    for c in (0, 1, 3):
+        assert stats.kstest(d[:, c], "norm").pvalue > 1e-4, c
+    for c in (2, 4):
+        assert d[:, c].min() > 0 and d[:, c].max() < 1
+        counts = np.bincount((d[:, c] * 50).astype(int), minlength=50)
+        assert stats.chisquare(counts).pvalue > 1e-4, c
+    lim = 5 / np.sqrt(n)
+    r = np.corrcoef(d.T)
+    assert np.all(np.abs(r[np.triu_indices(5, 1)]) < lim), r
+    ev, od = d[0::2], d[1::2]
+    rp = np.corrcoef(np.hstack([ev, od]).T)[:5, 5:]
+    assert np.all(np.abs(rp) < 5 / np.sqrt(n // 2)), rp
+    zt0, zt1 = ev[:, 3], od[:, 3]
+    ang = (np.arctan2(zt1, zt0) / (2 * np.pi)) % 1.0
+    assert stats.kstest(ang, "uniform").pvalue > 1e-4
+    assert stats.kstest(zt0 ** 2 + zt1 ** 2, stats.chi2(2).cdf).pvalue > 1e-4
+    assert not np.any(ev[:, 4] == od[:, 4])
