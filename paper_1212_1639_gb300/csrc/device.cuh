@@ -464,28 +464,44 @@ __device__ __forceinline__ R gamma_mt(R d, R c, R K, uint64_t seed, uint32_t fil
 
 // The draws of one propagation step for slot j: A = (j, t, STATE, 0) gives
 // the state normal (cos branch) and the sigma^2 gamma draw's first normal
-// (sin branch) and uniform; B = (j, t, STATE, 1) gives the tau^2 gamma
-// draw's first normal and uniform.
+// (sin branch) and uniform (word 2).  The tau^2 gamma draw's first normal and
+// uniform: in binary32, slots 2i and 2i + 1 share B = (i, t, STATE, 1) -- the
+// cos output of its Box-Muller pair and word 2 go to the even slot, the sin
+// output and word 3 to the odd one; in binary64 (whose Box-Muller takes three
+// words), B = (j, t, STATE, 1), its first output and its uniform.
+template <class R>
+__device__ __forceinline__ void theta_draws_from(const U4& A, const U4& B, uint32_t j, R* Zx,
+                                                 R* Zs, R* Us, R* Zt, R* Ut) {
+  bm_normal2(A, Zx, Zs);
+  *Us = extra_uniform(A, (R)0);
+  if constexpr (sizeof(R) == 4) {
+    R zc, zs;
+    bm_normal2(B, &zc, &zs);
+    *Zt = (j & 1u) ? zs : zc;
+    *Ut = unif_f32((j & 1u) ? B.d : B.c);
+  } else {
+    *Zt = bm_normal(B, (R)0);
+    *Ut = extra_uniform(B, (R)0);
+  }
+}
+template <class R>
+__device__ __forceinline__ uint32_t theta_b_index(uint32_t j) {
+  return sizeof(R) == 4 ? (j >> 1) : j;
+}
 template <class R>
 __device__ __forceinline__ void theta_draws(uint64_t seed, uint32_t filter, uint32_t t,
                                             uint32_t j, R* Zx, R* Zs, R* Us, R* Zt, R* Ut) {
   const U4 A = draw(seed, filter, t, j, P_STATE, 0);
-  const U4 B = draw(seed, filter, t, j, P_STATE, 1);
-  bm_normal2(A, Zx, Zs);
-  *Us = extra_uniform(A, (R)0);
-  *Zt = bm_normal(B, (R)0);
-  *Ut = extra_uniform(B, (R)0);
+  const U4 B = draw(seed, filter, t, theta_b_index<R>(j), P_STATE, 1);
+  theta_draws_from<R>(A, B, j, Zx, Zs, Us, Zt, Ut);
 }
 // The same draws with the Philox round keys given (philox_rk).
 template <class R>
 __device__ __forceinline__ void theta_draws_rk(const uint32_t* rk, uint32_t filter, uint32_t t,
                                                uint32_t j, R* Zx, R* Zs, R* Us, R* Zt, R* Ut) {
   const U4 A = philox_rk(j, t, filter, P_STATE, rk);
-  const U4 B = philox_rk(j, t, filter, P_STATE | (1u << 8), rk);
-  bm_normal2(A, Zx, Zs);
-  *Us = extra_uniform(A, (R)0);
-  *Zt = bm_normal(B, (R)0);
-  *Ut = extra_uniform(B, (R)0);
+  const U4 B = philox_rk(theta_b_index<R>(j), t, filter, P_STATE | (1u << 8), rk);
+  theta_draws_from<R>(A, B, j, Zx, Zs, Us, Zt, Ut);
 }
 
 // ---------------------------------------------------------------------------
@@ -599,14 +615,15 @@ __device__ __forceinline__ void det_sincos2pi2(float2 u, float2* s_out, float2* 
   *c_out = make_float2(o1x ? C.x : (o3x ? -C.x : S.x), o1y ? C.y : (o3y ? -C.y : S.y));
 }
 
-// the propagation draws (theta_draws_rk) of two slots j0, j1
+// the propagation draws (theta_draws_rk) of the two slots 2i, 2i + 1 of a
+// pair: A of each slot through one paired Box-Muller transform, the pair's
+// shared B through one scalar transform whose two outputs both serve
 __device__ __forceinline__ void theta_draws2(const uint32_t* rk, uint32_t filter, uint32_t t,
-                                             uint32_t j0, uint32_t j1, float2* Zx, float2* Zs,
-                                             float2* Us, float2* Zt, float2* Ut) {
-  const U4 A0 = philox_rk(j0, t, filter, P_STATE, rk);
-  const U4 A1 = philox_rk(j1, t, filter, P_STATE, rk);
-  const U4 B0 = philox_rk(j0, t, filter, P_STATE | (1u << 8), rk);
-  const U4 B1 = philox_rk(j1, t, filter, P_STATE | (1u << 8), rk);
+                                             uint32_t i, float2* Zx, float2* Zs, float2* Us,
+                                             float2* Zt, float2* Ut) {
+  const U4 A0 = philox_rk(2u * i, t, filter, P_STATE, rk);
+  const U4 A1 = philox_rk(2u * i + 1u, t, filter, P_STATE, rk);
+  const U4 B = philox_rk(i, t, filter, P_STATE | (1u << 8), rk);
   {
     const float2 u1 = unif_f32_2(A0.a, A1.a);
     const float2 u2 = unif_f32_2(A0.b, A1.b);
@@ -620,15 +637,10 @@ __device__ __forceinline__ void theta_draws2(const uint32_t* rk, uint32_t filter
     *Us = unif_f32_2(A0.c, A1.c);
   }
   {
-    const float2 u1 = unif_f32_2(B0.a, B1.a);
-    const float2 u2 = unif_f32_2(B0.b, B1.b);
-    const float2 L = det_log2(u1);
-    const float2 m2 = mul2(L, splat2(-2.0f));
-    const float2 r = make_float2(sqrtf(m2.x), sqrtf(m2.y));
-    float2 sn, cs;
-    det_sincos2pi2(u2, &sn, &cs);
-    *Zt = mul2(r, cs);
-    *Ut = unif_f32_2(B0.c, B1.c);
+    float zc, zs;
+    bm_normal2_f(B, &zc, &zs);
+    *Zt = make_float2(zc, zs);
+    *Ut = unif_f32_2(B.c, B.d);
   }
 }
 

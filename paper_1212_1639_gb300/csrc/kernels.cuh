@@ -2299,20 +2299,20 @@ __global__ void __launch_bounds__(BLOCK, 5) k_propagate(FilterArgs<R> a) {
 }
 
 // ---------------------------------------------------------------------------
-// k_propagate for binary32 state, two slots per thread per pass: slots j and
-// j + G (G = the grid's thread count) share each paired FADD2 / FMUL2 / FFMA2,
-// while divisions, square roots, comparisons and the fixed-point statistics
-// run per lane.  Per slot the operations are those of k_propagate, in the
-// same order, so the results are the same bits.
+// k_propagate for binary32 state, two slots per thread per pass: the pair
+// 2i, 2i + 1, which shares its second draw (theta_draws2), shares each paired
+// FADD2 / FMUL2 / FFMA2, while divisions, square roots, comparisons and the
+// fixed-point statistics run per lane.  Per slot the operations are those of
+// the scalar propagation, in the same order, so the results are the same bits.
 // ---------------------------------------------------------------------------
 constexpr uint32_t WQ2_CAP = 160;  // 31 queued + 4 pushes of 32 per pass
 
 // With FUSE, the next cycle's weights as in k_propagate, the two slots of a
 // pass weighed by paired operations.
-// 4 CTAs per SM (64 registers) for the plain form; the fused and adaptive
-// forms hold more live values and keep 3 (80 registers, no spills).
+// 3 CTAs per SM (up to 85 registers, no spills): measured faster at N = 2^24
+// than 4 CTAs at 64 registers, where the plain form spills.
 template <bool LEARN, bool FUSE = false, bool ESS = false>
-__global__ void __launch_bounds__(BLOCK, (FUSE || ESS) ? 3 : 4) k_propagate2(FilterArgs<float> a) {
+__global__ void __launch_bounds__(BLOCK, 3) k_propagate2(FilterArgs<float> a) {
   typedef GammaItem<float> Item;
   __shared__ Item s_q[WARPS][WQ2_CAP];
   const Ctl* c = a.ctl;
@@ -2336,12 +2336,6 @@ __global__ void __launch_bounds__(BLOCK, (FUSE || ESS) ? 3 : 4) k_propagate2(Fil
     rs = c->resamp != 0;
     mR = dec_f((uint32_t)c->maxenc);
   }
-  auto ancx = [&](uint64_t k) -> uint32_t {
-    if constexpr (ESS) {
-      if (!rs) return (uint32_t)k;
-    }
-    return clampi(a.anc[k]);
-  };
   // the carried log-weight of slot j: 0 after a resampling, else L_j - m
   auto carry = [&](uint64_t k) {
     if (rs) {
@@ -2369,34 +2363,33 @@ __global__ void __launch_bounds__(BLOCK, (FUSE || ESS) ? 3 : 4) k_propagate2(Fil
   auto weigh_late = [&](const Item& itm) {  // FUSE: the slot's state is final
     weigh_next<float>(a.ell, itm.j, dst.x[itm.j], dst.s2[itm.j], dst.t2[itm.j], yn, mxn, badn);
   };
-  // Pass p covers slots [p S, p S + S) (S = stride): thread g takes p S + g
-  // and p S + g + h with h = G, except in a partial last pass, where
-  // h = ceil(rest / 2) packs the rest into full pairs and the threads with
-  // g >= h (whole warps) skip it.
-  const uint64_t g = (uint64_t)blockIdx.x * BLOCK + threadIdx.x;
-  auto pair_of = [&](uint64_t b, uint64_t* j0, uint64_t* j1) {  // b: the pass's first slot
-    if (b + stride <= n) {  // a full pass (the same for every thread)
-      *j0 = b + g;
-      *j1 = b + g + half;
-      return;
+  // Pass p covers slots [p S, p S + S) (S = stride): thread g takes the
+  // pair j0 = p S + 2g, j1 = j0 + 1 (the two slots that share a draw), so its
+  // ancestor load and its stores are 8 or 16 bytes wide.  In a partial last
+  // pass the threads past the end (whole warps) skip it.
+  const uint64_t g2 = 2 * ((uint64_t)blockIdx.x * BLOCK + threadIdx.x);
+  // the ancestors of the pair starting at slot j (even; clamped into range)
+  auto anc_pair = [&](uint64_t j) -> uint2 {
+    if constexpr (ESS) {
+      if (!rs) return make_uint2((uint32_t)j, (uint32_t)j + 1u);
     }
-    const uint64_t rest = n > b ? n - b : 0ull;
-    const uint64_t h = (rest + 1) / 2;
-    *j0 = g < h ? b + g : n;  // n: no slot
-    *j1 = g < h ? b + g + h : n;
+    if (j + 1 < n) {
+      const uint2 v = *reinterpret_cast<const uint2*>(a.anc + j);
+      return make_uint2(clampi(v.x), clampi(v.y));
+    }
+    return make_uint2(j < n ? clampi(a.anc[j]) : 0u, 0u);
   };
-  uint64_t pb = 0;  // the current pass's first slot
-  uint64_t j0, j1;
-  pair_of(0, &j0, &j1);
-  Gathered<float> c0 = gather_rec<float>(src, j0 < n ? ancx(j0) : 0u);
-  Gathered<float> c1 = gather_rec<float>(src, j1 < n ? ancx(j1) : 0u);
-  for (uint64_t it = 0; it < iters; ++it, pb += stride) {
+  uint64_t j0 = g2;
+  uint2 an = anc_pair(j0);
+  Gathered<float> c0 = gather_rec<float>(src, an.x);
+  Gathered<float> c1 = gather_rec<float>(src, an.y);
+  for (uint64_t it = 0; it < iters; ++it, j0 += stride) {
+    const uint64_t j1 = j0 + 1;
     const bool v0 = j0 < n, v1 = j1 < n;
     // the next pass's records, gathered ahead
-    uint64_t k0, k1;
-    pair_of(pb + stride, &k0, &k1);
-    const Gathered<float> n0 = gather_rec<float>(src, k0 < n ? ancx(k0) : 0u);
-    const Gathered<float> n1 = gather_rec<float>(src, k1 < n ? ancx(k1) : 0u);
+    const uint2 na = anc_pair(j0 + stride);
+    const Gathered<float> n0 = gather_rec<float>(src, na.x);
+    const Gathered<float> n1 = gather_rec<float>(src, na.y);
     // a warp with no slot left in a partial last pass skips it
     if (__any_sync(0xffffffffu, v0)) {
       const float2 xa = make_float2(c0.x, c1.x), sa = make_float2(c0.s2, c1.s2);
@@ -2409,10 +2402,13 @@ __global__ void __launch_bounds__(BLOCK, (FUSE || ESS) ? 3 : 4) k_propagate2(Fil
       const float2 mu = mul2(nn, ri);
       const float2 sv = make_float2(sqrtf(V.x), sqrtf(V.y));
       float2 Z, Zs, Us, Zt, Ut;
-      theta_draws2(a.rk, a.filter, t, (uint32_t)j0, (uint32_t)j1, &Z, &Zs, &Us, &Zt, &Ut);
+      theta_draws2(a.rk, a.filter, t, (uint32_t)(j0 >> 1), &Z, &Zs, &Us, &Zt, &Ut);
       const float2 xj = fma2(sv, Z, mu);
-      if (v0) dst.x[j0] = xj.x;
-      if (v1) dst.x[j1] = xj.y;
+      if (v1) {
+        *reinterpret_cast<float2*>(dst.x + j0) = xj;
+      } else if (v0) {
+        dst.x[j0] = xj.x;
+      }
       bool ds0 = false, dt0 = false, ds1 = false, dt1 = false;
       uint64_t bs0 = 0, bt0 = 0, bs1 = 0, bt1 = 0;
       if (LEARN) {
@@ -2434,8 +2430,13 @@ __global__ void __launch_bounds__(BLOCK, (FUSE || ESS) ? 3 : 4) k_propagate2(Fil
         bs1 = addb(c1.bs, ws.y, &f1);
         bt1 = addb(c1.bt, wt.y, &f1);
         fail |= (v0 && f0) || (v1 && f1);
-        if (v0) { dst.bs[j0] = bs0; dst.bt[j0] = bt0; }
-        if (v1) { dst.bs[j1] = bs1; dst.bt[j1] = bt1; }
+        if (v1) {
+          *reinterpret_cast<ulonglong2*>(dst.bs + j0) = make_ulonglong2(bs0, bs1);
+          *reinterpret_cast<ulonglong2*>(dst.bt + j0) = make_ulonglong2(bt0, bt1);
+        } else if (v0) {
+          dst.bs[j0] = bs0;
+          dst.bt[j0] = bt0;
+        }
         // Marsaglia-Tsang squeeze for sigma^2 (x lanes: slot j0, j1) and tau^2
         const float2 vs = fma2(splat2(cs), Zs, splat2(1.0f)), vt = fma2(splat2(ct), Zt, splat2(1.0f));
         const float2 v3s = mul2(mul2(vs, vs), vs), v3t = mul2(mul2(vt, vt), vt);
@@ -2458,10 +2459,18 @@ __global__ void __launch_bounds__(BLOCK, (FUSE || ESS) ? 3 : 4) k_propagate2(Fil
                                             __uint2float_rn((uint32_t)(bt1 >> 32))));
         const float q0 = bsf.x / Gs.x, r0 = btf.x / Gt.x, q1 = bsf.y / Gs.y, r1 = btf.y / Gt.y;
         ds0 = v0 && !as0; dt0 = v0 && !at0; ds1 = v1 && !as1; dt1 = v1 && !at1;
-        if (v0 && as0) dst.s2[j0] = q0;
-        if (v0 && at0) dst.t2[j0] = r0;
-        if (v1 && as1) dst.s2[j1] = q1;
-        if (v1 && at1) dst.t2[j1] = r1;
+        if (v1 && as0 && as1) {
+          *reinterpret_cast<float2*>(dst.s2 + j0) = make_float2(q0, q1);
+        } else {
+          if (v0 && as0) dst.s2[j0] = q0;
+          if (v1 && as1) dst.s2[j1] = q1;
+        }
+        if (v1 && at0 && at1) {
+          *reinterpret_cast<float2*>(dst.t2 + j0) = make_float2(r0, r1);
+        } else {
+          if (v0 && at0) dst.t2[j0] = r0;
+          if (v1 && at1) dst.t2[j1] = r1;
+        }
         // 1 for a deferred draw: the paired weight of that slot is discarded,
         // and a normal operand keeps the log and the division on their fast paths
         const float s20 = as0 ? q0 : 1.0f, t20 = at0 ? r0 : 1.0f;
@@ -2509,8 +2518,6 @@ __global__ void __launch_bounds__(BLOCK, (FUSE || ESS) ? 3 : 4) k_propagate2(Fil
     }
     c0 = n0;
     c1 = n1;
-    j0 = k0;
-    j1 = k1;
   }
   if constexpr (LEARN && FUSE) wq_drain_post(wq, qn, 1u, lane, finish, weigh_late);
   else if (LEARN) wq_drain(wq, qn, 1u, lane, finish);
