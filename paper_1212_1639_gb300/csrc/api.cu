@@ -94,6 +94,7 @@ struct pf_filter {
   bool fp64 = false, learn = true;
   int scheme = 0;
   unsigned prop_grid = 0;  // persistent propagate grid
+  uint64_t w_cap = 1;      // resident CTAs of the weights kernel
   unsigned prop_grid_fuse = 0;  // the same for the propagation that also weighs
   unsigned cdf_grid = 0;   // cooperative CDF + systematic resampling grid (0: not used)
   bool cdf_staged = false; // its CTAs own several tiles: TMA-staged variant
@@ -290,7 +291,7 @@ pf_status enqueue_cycle(pf_filter* f, KTimer* tm = nullptr, const double* y_src 
     k_boot_pw<R><<<(unsigned)cdiv(n, BLOCK), BLOCK, 0, s>>>(a);
     mark(tm, "propagate_weights", s);
   } else if (form_weighs(form)) {
-    const unsigned wg = (unsigned)cdiv(n, (uint64_t)BLOCK * W_PER_THREAD);
+    const unsigned wg = weights_grid<R>(n, f->w_cap);
     if (f->ess) k_weights<R, true><<<wg, BLOCK, 0, s>>>(a);
     else k_weights<R><<<wg, BLOCK, 0, s>>>(a);
     mark(tm, "weights", s);
@@ -704,6 +705,11 @@ pf_status pf_create(const pf_config* cfg, pf_filter** out) {
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_f, prop_fuse_fn(f), BLOCK, 0);
     if (e != cudaSuccess || per_sm_f < 1) return bail(set_err(PF_ERR_CUDA, "occupancy query failed"));
     const uint64_t cap_f = (uint64_t)per_sm_f * (uint64_t)sms;
+    int per_sm_w = 0;
+    e = f->fp64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_w, k_weights<double>, BLOCK, 0)
+                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_w, k_weights<float>, BLOCK, 0);
+    if (e != cudaSuccess || per_sm_w < 1) return bail(set_err(PF_ERR_CUDA, "occupancy query failed"));
+    f->w_cap = (uint64_t)per_sm_w * (uint64_t)sms;
     f->prop_grid_fuse = (unsigned)(want < cap_f ? want : cap_f);
     if (f->scheme == PF_SYSTEMATIC) {
       // cooperative grid: every CTA resident at once (it waits on the others).

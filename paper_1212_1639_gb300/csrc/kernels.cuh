@@ -301,12 +301,33 @@ __device__ __forceinline__ R block_max(R v, R* s_red) {
   return v;
 }
 
-// Four particles per thread, vectorised.
-constexpr int W_PER_THREAD = 4;
+// Persistent over the particles: per pass a warp takes a chunk of 64 16-byte
+// vectors of each array (2 x 32 x W_VEC particles), each load and store
+// instruction 512 contiguous bytes, two of each in flight per thread and array;
+// the rest of the last chunk element by element.  One block maximum and one
+// atomic per CTA.
+template <class R> struct WVec;
+template <> struct WVec<float> {
+  static constexpr int N = 4;
+  typedef float4 V;
+  static __device__ __forceinline__ void get(const V& v, float* o) { o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w; }
+  static __device__ __forceinline__ V make(const float* o) { return make_float4(o[0], o[1], o[2], o[3]); }
+};
+template <> struct WVec<double> {
+  static constexpr int N = 2;
+  typedef double2 V;
+  static __device__ __forceinline__ void get(const V& v, double* o) { o[0] = v.x; o[1] = v.y; }
+  static __device__ __forceinline__ V make(const double* o) { return make_double2(o[0], o[1]); }
+};
+constexpr int W_CTAS_PER_SM = 4;  // 64 registers: the pass's 2 x 3 vectors stay in registers
 
 // With ESS (adaptive resampling) the carried log-weights are added: L = lambda + l.
 template <class R, bool ESS = false>
-__global__ void __launch_bounds__(BLOCK, sizeof(R) == 4 ? 8 : 4) k_weights(FilterArgs<R> a) {
+__global__ void __launch_bounds__(BLOCK, W_CTAS_PER_SM) k_weights(FilterArgs<R> a) {
+  typedef WVec<R> VW;
+  typedef typename VW::V V;
+  constexpr int NV = VW::N;
+  constexpr uint64_t CHUNK = 64 * NV;  // particles per warp pass
   __shared__ R s_red[WARPS];
   __shared__ R s_y;
   const uint32_t t = a.ctl->t;
@@ -318,56 +339,53 @@ __global__ void __launch_bounds__(BLOCK, sizeof(R) == 4 ? 8 : 4) k_weights(Filte
   }
   __syncthreads();
   const R yr = s_y;
-  const uint64_t base = ((uint64_t)blockIdx.x * BLOCK + threadIdx.x) * W_PER_THREAD;
+  const uint64_t n = a.n;
+  const int lane = threadIdx.x & 31;
+  const uint64_t gw = (uint64_t)blockIdx.x * WARPS + (threadIdx.x >> 5);
+  const uint64_t nw = (uint64_t)gridDim.x * WARPS;
   R mx = (R)-INFINITY;
   bool bad = false;
-  if (base + W_PER_THREAD <= a.n) {
-    R xv[4], sv[4], tv[4], lv[4];
-    if constexpr (sizeof(R) == 4) {
-      const float4 X = *reinterpret_cast<const float4*>(st.x + base);
-      const float4 Sg = *reinterpret_cast<const float4*>(st.s2 + base);
-      const float4 Tu = *reinterpret_cast<const float4*>(st.t2 + base);
-      xv[0] = X.x; xv[1] = X.y; xv[2] = X.z; xv[3] = X.w;
-      sv[0] = Sg.x; sv[1] = Sg.y; sv[2] = Sg.z; sv[3] = Sg.w;
-      tv[0] = Tu.x; tv[1] = Tu.y; tv[2] = Tu.z; tv[3] = Tu.w;
-    } else {
-#pragma unroll
-      for (int e = 0; e < 4; ++e) { xv[e] = st.x[base + e]; sv[e] = st.s2[base + e]; tv[e] = st.t2[base + e]; }
-    }
-#pragma unroll
-    for (int e = 0; e < 4; ++e) lv[e] = log_pred<R>(xv[e], sv[e], tv[e], yr);
-    if constexpr (ESS) {  // adaptive resampling: L = lambda + l
-      if constexpr (sizeof(R) == 4) {
-        const float4 Lm = *reinterpret_cast<const float4*>(a.lam + base);
-        lv[0] = Lm.x + lv[0]; lv[1] = Lm.y + lv[1]; lv[2] = Lm.z + lv[2]; lv[3] = Lm.w + lv[3];
-      } else {
-#pragma unroll
-        for (int e = 0; e < 4; ++e) lv[e] = a.lam[base + e] + lv[e];
+  auto weigh = [&](R x, R s2, R t2, R lam) {
+    R l = log_pred<R>(x, s2, t2, yr);
+    if constexpr (ESS) l = lam + l;
+    bad |= !(l < (R)INFINITY);  // NaN or +inf
+    mx = fmax(mx, l);
+    return l;
+  };
+  for (uint64_t cb = gw * CHUNK; cb < n; cb += nw * CHUNK) {
+    if (cb + CHUNK <= n) {
+      const uint64_t i0 = cb + (uint64_t)lane * NV, i1 = i0 + 32 * NV;
+      const V x0 = *reinterpret_cast<const V*>(st.x + i0), x1 = *reinterpret_cast<const V*>(st.x + i1);
+      const V s0 = *reinterpret_cast<const V*>(st.s2 + i0), s1 = *reinterpret_cast<const V*>(st.s2 + i1);
+      const V u0 = *reinterpret_cast<const V*>(st.t2 + i0), u1 = *reinterpret_cast<const V*>(st.t2 + i1);
+      R xv[2 * NV], sv[2 * NV], tv[2 * NV], lm[2 * NV], lv[2 * NV];
+      VW::get(x0, xv); VW::get(x1, xv + NV);
+      VW::get(s0, sv); VW::get(s1, sv + NV);
+      VW::get(u0, tv); VW::get(u1, tv + NV);
+      if constexpr (ESS) {
+        VW::get(*reinterpret_cast<const V*>(a.lam + i0), lm);
+        VW::get(*reinterpret_cast<const V*>(a.lam + i1), lm + NV);
       }
-    }
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      bad |= !(lv[e] < (R)INFINITY);  // NaN or +inf
-      mx = fmax(mx, lv[e]);
-    }
-    if constexpr (sizeof(R) == 4) {
-      *reinterpret_cast<float4*>(a.ell + base) = make_float4(lv[0], lv[1], lv[2], lv[3]);
+      for (int e = 0; e < 2 * NV; ++e) lv[e] = weigh(xv[e], sv[e], tv[e], ESS ? lm[e] : (R)0);
+      *reinterpret_cast<V*>(a.ell + i0) = VW::make(lv);
+      *reinterpret_cast<V*>(a.ell + i1) = VW::make(lv + NV);
     } else {
-#pragma unroll
-      for (int e = 0; e < 4; ++e) a.ell[base + e] = lv[e];
-    }
-  } else {
-    for (uint64_t i = base; i < a.n; ++i) {
-      R l = log_pred<R>(st.x[i], st.s2[i], st.t2[i], yr);
-      if constexpr (ESS) l = a.lam[i] + l;
-      bad |= !(l < (R)INFINITY);
-      mx = fmax(mx, l);
-      a.ell[i] = l;
+      for (uint64_t i = cb + lane; i < n; i += 32)
+        a.ell[i] = weigh(st.x[i], st.s2[i], st.t2[i], ESS ? a.lam[i] : (R)0);
     }
   }
   if (bad) atomicOr(&a.ctl->err, ERR_NUMERIC);
   mx = block_max<R>(mx, s_red);
   if (threadIdx.x == 0 && mx > (R)-INFINITY) atomicMax(&a.ctl->maxenc, enc_max(mx));
+}
+// CTAs of the weights kernel for n particles: the resident maximum `cap`, or
+// fewer when the particles make fewer chunks than the resident warps.
+template <class R>
+inline unsigned weights_grid(uint64_t n, uint64_t cap) {
+  const uint64_t per_cta = 64ull * WVec<R>::N * WARPS;  // one chunk per warp
+  const uint64_t ctas = (n + per_cta - 1) / per_cta;
+  return (unsigned)(ctas < cap ? (ctas > 0 ? ctas : 1) : cap);
 }
 
 // ---------------------------------------------------------------------------
