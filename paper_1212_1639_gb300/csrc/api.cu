@@ -8,6 +8,7 @@
 #include <cstdarg>
 #include <cstddef>
 #include <cstdio>
+#include <chrono>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -124,6 +125,12 @@ struct pf_filter {
   Ctl* ctl = nullptr;
   Ctl* ctl_host = nullptr;  // pinned mirror for summaries
   Ctl* ctl_host_dev = nullptr;  // its device address (mapped), or NULL
+  // pf_step_estimate: the observation and a sequence number in mapped host
+  // memory (no graph-node update per call), the summary kernel's copy of the
+  // number marking the summaries complete (no stream synchronisation)
+  EstIO* io = nullptr;
+  EstIO* io_dev = nullptr;
+  uint64_t io_seq = 0;
   // captured cycles by CycleForm (the fused forms on first use); each launch
   // sets its observations in the kernel nodes' arguments (no copy on the stream)
   CycleGraph cg[CF_COUNT];
@@ -189,6 +196,7 @@ FilterArgs<R> filter_args(pf_filter* f) {
   a.part_est = f->part_est;
   a.ctl = f->ctl;
   a.ctl_mirror = f->ctl_host_dev;
+  a.io = nullptr;
   a.y_src = nullptr;
   a.y_val = 0.0;
   a.n = f->n;
@@ -285,6 +293,10 @@ pf_status enqueue_cycle(pf_filter* f, KTimer* tm = nullptr, const double* y_src 
   a.y_val = y_val;
   a.y_nx_src = ynx_src;
   a.y_nx_val = ynx_val;
+  if (form == CF_EST && f->io_dev) {  // pf_step_estimate: y and completion through mapped words
+    a.io = f->io_dev;
+    a.y_src = &f->io_dev->y;
+  }
   const uint64_t n = f->n;
   if (tm) cudaEventRecord(tm->ev[0], s);
   if (f->bootstrap) {  // Algorithm "Particle Filtering": propagate blind, then weigh
@@ -470,7 +482,7 @@ pf_status build_graph(pf_filter* f, int form) {
     if (ty != cudaGraphNodeTypeKernel) continue;
     cudaKernelNodeParams p;
     CK(cudaGraphKernelNodeGetParams(nd, &p));
-    if (p.func == wfun) {
+    if (p.func == wfun && !(form == CF_EST && f->io_dev)) {
       G.wnode = nd;
       G.wparams = p;
       std::memcpy(G.wargs, p.kernelParams[0], asz);
@@ -486,7 +498,8 @@ pf_status build_graph(pf_filter* f, int form) {
       G.pparams.extra = nullptr;
     }
   }
-  if (form_weighs(form) && !G.wnode) return set_err(PF_ERR_CUDA, "graph capture: weights node not found");
+  if (form_weighs(form) && !G.wnode && !(form == CF_EST && f->io_dev))
+    return set_err(PF_ERR_CUDA, "graph capture: weights node not found");
   if (form_fuses(form) && !f->bootstrap && !G.pnode)
     return set_err(PF_ERR_CUDA, "graph capture: fused propagation node not found");
   return PF_OK;
@@ -645,6 +658,15 @@ pf_status pf_create(const pf_config* cfg, pf_filter** out) {
     cudaGetLastError();
     f->ctl_host_dev = nullptr;
   }
+  if (f->ctl_host_dev && cudaHostAlloc((void**)&f->io, sizeof(EstIO), cudaHostAllocMapped) == cudaSuccess) {
+    std::memset(f->io, 0, sizeof(EstIO));
+    if (cudaHostGetDevicePointer((void**)&f->io_dev, f->io, 0) != cudaSuccess) {
+      cudaFreeHost(f->io);
+      f->io = nullptr;
+      f->io_dev = nullptr;
+    }
+  }
+  cudaGetLastError();
   // control block: t = 0, no error, max = -inf, counters 0
   Ctl c0;
   std::memset(&c0, 0, sizeof(c0));
@@ -899,10 +921,38 @@ pf_status pf_step_estimate(pf_filter* f, double y, pf_estimates* out) {
     if ((st = pf_step(f, y)) != PF_OK) return st;
     return pf_estimate(f, out);
   }
-  if ((st = launch_cycle(f, nullptr, y, CF_EST)) != PF_OK) return f->sticky = st;
-  if (cudaStreamSynchronize(f->stream) != cudaSuccess) {
-    f->sticky = PF_ERR_CUDA;
-    return set_err(PF_ERR_CUDA, "stream: %s", cudaGetErrorString(cudaGetLastError()));
+  if (f->io) {
+    // the observation and the next sequence number into the mapped words,
+    // then the graph; the summaries are complete once the summary kernel has
+    // copied the number to seq_out (a bounded wait on the host, then the
+    // stream's own synchronisation, which also reports a failed launch)
+    const uint64_t want = ++f->io_seq;
+    f->io->y = y;
+    __atomic_store_n(&f->io->seq_in, (unsigned long long)want, __ATOMIC_RELEASE);
+    if ((st = launch_cycle(f, nullptr, y, CF_EST)) != PF_OK) return f->sticky = st;
+    const auto t0 = std::chrono::steady_clock::now();
+    uint32_t k = 0;
+    while (__atomic_load_n(&f->io->seq_out, __ATOMIC_ACQUIRE) != want) {
+      if ((++k & 1023u) == 0 &&
+          std::chrono::steady_clock::now() - t0 > std::chrono::milliseconds(20))
+        break;
+    }
+    if (__atomic_load_n(&f->io->seq_out, __ATOMIC_ACQUIRE) != want) {
+      if (cudaStreamSynchronize(f->stream) != cudaSuccess) {
+        f->sticky = PF_ERR_CUDA;
+        return set_err(PF_ERR_CUDA, "stream: %s", cudaGetErrorString(cudaGetLastError()));
+      }
+      if (__atomic_load_n(&f->io->seq_out, __ATOMIC_ACQUIRE) != want) {
+        f->sticky = PF_ERR_CUDA;
+        return set_err(PF_ERR_CUDA, "summaries not published");
+      }
+    }
+  } else {
+    if ((st = launch_cycle(f, nullptr, y, CF_EST)) != PF_OK) return f->sticky = st;
+    if (cudaStreamSynchronize(f->stream) != cudaSuccess) {
+      f->sticky = PF_ERR_CUDA;
+      return set_err(PF_ERR_CUDA, "stream: %s", cudaGetErrorString(cudaGetLastError()));
+    }
   }
   if ((st = map_err(f->ctl_host->err)) != PF_OK) return f->sticky = st;
   const double* v = f->ctl_host->est;
@@ -952,6 +1002,7 @@ pf_status pf_destroy(pf_filter* f) {
   }
   free_all(f);
   if (f->ctl_host) cudaFreeHost(f->ctl_host);
+  if (f->io) cudaFreeHost(f->io);
   if (f->own_stream) cudaStreamDestroy(f->stream);
   cudaGetLastError();
   delete f;

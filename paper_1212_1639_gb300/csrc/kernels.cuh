@@ -120,6 +120,16 @@ struct StateV {
   typename SuffT<R>::B* bt;
 };
 
+// Host-mapped words of a synchronous cycle with summaries (pf_step_estimate):
+// the observation, and the host's sequence number, which the summary kernel
+// copies to seq_out once the summaries are in the host mirror.
+struct EstIO {
+  double y;
+  unsigned long long seq_in;
+  unsigned long long seq_out;
+  unsigned long long pad;
+};
+
 template <class R>
 struct FilterArgs {
   StateV<R> st[2];          // ping-pong by cycle parity
@@ -137,6 +147,7 @@ struct FilterArgs {
   // (mapped), or NULL: the summary kernels write the control block's summary
   // prefix there directly, so no copy follows them
   Ctl* ctl_mirror;
+  EstIO* io;                // mapped words of pf_step_estimate, or NULL
   // this cycle's observation: *y_src when y_src is set (device-resident
   // observations), else y_val (set per launch in the graph's weights node)
   const double* y_src;
@@ -329,16 +340,13 @@ __global__ void __launch_bounds__(BLOCK, W_CTAS_PER_SM) k_weights(FilterArgs<R> 
   constexpr int NV = VW::N;
   constexpr uint64_t CHUNK = 64 * NV;  // particles per warp pass
   __shared__ R s_red[WARPS];
-  __shared__ R s_y;
   const uint32_t t = a.ctl->t;
   const StateV<R> st = (t & 1) ? a.st[1] : a.st[0];
-  if (threadIdx.x == 0) {
-    const double y = a.y_src ? *a.y_src : a.y_val;
-    s_y = (R)y;
-    if (blockIdx.x == 0) write_cycle_constants(a.ctl, y, a.a_sigma, a.a_tau, t + 1);
-  }
-  __syncthreads();
-  const R yr = s_y;
+  // every thread reads y itself (no barrier), so that its first loads of the
+  // state overlap that read (y may sit in host memory)
+  const double y = a.y_src ? *a.y_src : a.y_val;
+  if (blockIdx.x == 0 && threadIdx.x == 0) write_cycle_constants(a.ctl, y, a.a_sigma, a.a_tau, t + 1);
+  const R yr = (R)y;
   const uint64_t n = a.n;
   const int lane = threadIdx.x & 31;
   const uint64_t gw = (uint64_t)blockIdx.x * WARPS + (threadIdx.x >> 5);
@@ -2602,6 +2610,18 @@ __device__ __forceinline__ void publish_summary(const Ctl* c, Ctl* mirror) {
   reinterpret_cast<unsigned long long*>(mirror)[threadIdx.x] =
       __ldcg(reinterpret_cast<const unsigned long long*>(c) + threadIdx.x);
 }
+// After publish_summary, by the whole block: the host's sequence number to
+// io->seq_out, ordered after every mirror word (each writer's system-scope
+// fence, the block barrier, a release store).
+__device__ __forceinline__ void publish_done(EstIO* io) {
+  if (!io) return;
+  __threadfence_system();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned long long sq = *reinterpret_cast<volatile unsigned long long*>(&io->seq_in);
+    asm volatile("st.release.sys.global.u64 [%0], %1;" ::"l"(&io->seq_out), "l"(sq) : "memory");
+  }
+}
 
 // Means and variances from the shifted sums (sum of v - c, sum of (v - c)^2
 // per quantity) over n particles, one reciprocal of n.
@@ -2718,6 +2738,7 @@ __global__ void __launch_bounds__(BLOCK) k_estimate(FilterArgs<R> a) {
   }
   __syncthreads();
   publish_summary(a.ctl, a.ctl_mirror);
+  publish_done(a.io);
 }
 
 // Posterior summaries under adaptive resampling: the particles weighted by
@@ -2789,6 +2810,7 @@ __global__ void __launch_bounds__(BLOCK) k_estimate_w(FilterArgs<R> a) {
   }
   __syncthreads();
   publish_summary(a.ctl, a.ctl_mirror);
+  publish_done(a.io);
 }
 
 // ---------------------------------------------------------------------------
