@@ -1305,6 +1305,11 @@ __device__ __forceinline__ void tma_store_1d(void* dst, const void* src, uint32_
 __device__ __forceinline__ void bulk_wait_read() {
   asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
 }
+// wait until all but the most recent of this thread's bulk store groups
+// have read their shared-memory source
+__device__ __forceinline__ void bulk_wait_read1() {
+  asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+}
 // wait until this thread's bulk stores are complete
 __device__ __forceinline__ void bulk_wait_done() {
   asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
@@ -1332,9 +1337,12 @@ __device__ __forceinline__ uint64_t quant_from_e(double e, int k) {
 
 // The systematic resampling step writes each particle's slots into a
 // shared-memory window (an entry per slot of the tile, the particle's offset
-// in the tile + 1).  Entry of slot x: x with bits 1-3 XORed by bits 6-8, so
+// in the tile + 1; the window starts at the tile's first slot rounded down to
+// a multiple of four).  Entry of slot x: x with bits 1-3 XORed by bits 6-8, so
 // that threads writing slots about PER apart, and warps reading consecutive
-// slots, hit distinct banks.
+// slots, hit distinct banks.  The four slots 4g .. 4g + 3 keep one aligned
+// group of four entries (in the order 0 1 2 3, or 2 3 0 1 when bit 1 is
+// flipped), so the window is read out four slots per 8-byte load.
 __device__ __forceinline__ uint32_t win_entry(uint32_t x) { return x ^ (((x >> 6) & 7u) << 1); }
 // A run of the CTA's run list: slots [s0, s1) of ancestor v; with WRUN set in
 // v, window slots (relative to the tile's first slot) of mark v & 0xffff.
@@ -1342,7 +1350,7 @@ constexpr uint32_t WRUN = 0x80000000u;
 
 // Rare paths of the systematic resampling step, kept out of line so that the
 // per-particle loop stays small: the slot count of a heavy particle (more than
-// two slots), and the slots of a particle that its two fast-path window
+// three slots), and the slots of a particle that its `inl` in-line window
 // writes did not cover -- the rest of a heavy particle's run in the window
 // (by the whole CTA when long) and slots past the window (stored directly, or
 // by the whole CTA when long).
@@ -1351,9 +1359,9 @@ static __device__ __noinline__ uint32_t sys_heavy_count(int64_t D, SysDiv dv) {
 }
 static __device__ __noinline__ void sys_rest(uint32_t j, uint32_t c, uint32_t S0, uint32_t wslots,
                                              uint16_t mk, uint32_t ig, uint16_t* win, uint32_t* anc,
-                                             uint32_t (*runs)[3], uint32_t* nruns) {
+                                             uint32_t (*runs)[3], uint32_t* nruns, uint32_t inl = 2u) {
   const uint32_t wend = S0 + wslots, e = j + c;
-  const uint32_t a = j + 2u < e ? j + 2u : e;  // window part [a, b)
+  const uint32_t a = j + inl < e ? j + inl : e;  // window part [a, b)
   const uint32_t b = e < wend ? e : wend;
   if (b > a) {
     bool queued = false;
@@ -1424,12 +1432,14 @@ __device__ __forceinline__ double u128_to_f64_rn(U128 v) {
 // per CTA fits at once; the binary32 tile partials are exact, so the tile
 // size does not change them.
 // ---------------------------------------------------------------------------
-// STAGED: a CTA owns several tiles, and l of the next one is copied by TMA
-// into a shared-memory double buffer while the CTA works on the current one;
-// phase 1 writes e = exp(l - m) back in l's place by bulk stores, so phase 2
-// needs no exponentials; the CDF goes out through shared-memory rows,
-// coalesced.  Otherwise (one tile per CTA) l is read directly and the first
-// tile's W stay in shared memory between the phases.
+// STAGED: a CTA owns several tiles, copied by TMA into shared memory ahead of
+// use.  Phase 1 streams l through a ring of NB1 buffers (NB1 - 1 tiles in
+// flight: phase 1 is bound by the bytes in flight, and the CDF rows' space
+// is free until phase 2) and writes e = exp(l - m) back in l's place by bulk
+// stores, so phase 2 needs no exponentials; phase 2 reads e through a double
+// buffer; the CDF goes out through shared-memory rows, coalesced.  Otherwise
+// (one tile per CTA) l is read directly and the tile's W stay in shared
+// memory between the phases.
 //
 // With ESS (adaptive resampling) phase 1 also sums W^2 exactly per CTA
 // (cta_sq); after the grid barrier every CTA takes k_ess's decision from the
@@ -1450,15 +1460,21 @@ __global__ void __launch_bounds__(BLOCK, PER == 8 ? 4 : 3) k_cdf_sys(FilterArgs<
   __shared__ uint64_t s_bc[2];
   __shared__ uint32_t s_run[BB_RUNS][3];
   __shared__ uint32_t s_nruns;
-  // the first tile's quantised weights and log-ML partials, kept from phase
-  // 1 for phase 2 (a CTA that owns one tile quantises once)
-  __shared__ uint64_t s_keep[BLOCK * (PER + 1)];
-  __shared__ R s_keep_ep[BLOCK];
-  // l of the next tile arrives by TMA while the CTA works on the current one
-  // (phase 2: a free buffer is the tile's ancestor window, see below)
+  // one tile per CTA: the tile's quantised weights and log-ML partials, kept
+  // from phase 1 for phase 2 (the CTA quantises once).  Staged: phase 1 uses
+  // this space as further TMA buffers and phase 2 as the rows of the CDF.
+  __shared__ alignas(128) uint64_t s_keep[BLOCK * (PER + 1)];
+  __shared__ R s_keep_ep[STAGED ? 1 : BLOCK];
+  // staged: l (phase 1) or e (phase 2) of the next tiles arrives by TMA while
+  // the CTA works on the current one; in phase 2 the buffer of the current
+  // tile, once quantised, is the tile's ancestor window (see below)
   __shared__ alignas(128) R s_ell[2][STAGED ? TP : 4];
   __shared__ alignas(16) uint16_t s_win[STAGED ? 8 : 2 * TP];
-  __shared__ alignas(8) uint64_t s_bar[2];
+  // phase 1's ring of NB1 buffers (s_ell[0], s_ell[1], then s_keep), so that
+  // NB1 - 1 tiles are in flight while one is quantised: four 16 KB tiles in
+  // binary32, three 32 KB tiles in binary64; phase 2's ring is s_ell
+  constexpr int NB1 = STAGED ? 2 + (int)(sizeof(uint64_t) * BLOCK * (PER + 1) / (sizeof(R) * TP)) : 1;
+  __shared__ alignas(8) uint64_t s_bar[NB1 + 2];
   __shared__ uint32_t s_S[2];  // the tile's first slot and the slot after its last
   __shared__ U128 s_sq[ESS ? WARPS : 1];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1473,9 +1489,10 @@ __global__ void __launch_bounds__(BLOCK, PER == 8 ? 4 : 3) k_cdf_sys(FilterArgs<
   if constexpr (sizeof(R) == 4) m = dec_f((uint32_t)c->maxenc);
   else m = dec_d(c->maxenc);
   const int k = a.k;
-  // TMA double buffer: copy number q goes to buffer q & 1 and completes
-  // phase (q >> 1) & 1 of that buffer's barrier; copies are waited for in
-  // the order they were issued
+  // TMA rings (staged).  Phase 1: the CTA's tile i goes to ring buffer
+  // i % NB1 with barrier i % NB1; phase 2: tile i to s_ell[i & 1] with
+  // barrier NB1 + (i & 1).  The k-th copy through a barrier completes its
+  // phase k, waited for with parity k & 1.
   // After a wait that gave up (s_tmo set, ERR_TIMEOUT raised) the CTA issues
   // no more copies and waits for none; its CDF and ancestors are then
   // invalid, which the error word reports.  Before the CTA exits, thread 0
@@ -1485,58 +1502,54 @@ __global__ void __launch_bounds__(BLOCK, PER == 8 ? 4 : 3) k_cdf_sys(FilterArgs<
   if (threadIdx.x == 0) {
     s_tmo = 0;
     if (STAGED) {
-      mbar_init(&s_bar[0], 1);
-      mbar_init(&s_bar[1], 1);
+      for (int b = 0; b < NB1 + 2; ++b) mbar_init(&s_bar[b], 1);
       mbar_init_fence();
     }
   }
   __syncthreads();
-  uint32_t q_issued = 0, q_done = 0;
-  uint32_t iss_b[2] = {0, 0}, ok_b[2] = {0, 0};  // thread 0: copies issued / seen complete per buffer
-  auto issue = [&](uint32_t tile) {  // thread 0 only; the buffer is free
+  uint32_t iss_b[NB1 + 2], ok_b[NB1 + 2];  // thread 0: copies issued / seen complete per barrier
+#pragma unroll
+  for (int b = 0; b < NB1 + 2; ++b) iss_b[b] = ok_b[b] = 0;
+  // phase 1's ring buffer b
+  auto ring1 = [&](uint32_t b) -> R* {
+    return b < 2 ? s_ell[b] : reinterpret_cast<R*>(s_keep) + (b - 2) * TP;
+  };
+  // thread 0: copy tile `tile` of l (or e) into dst through barrier bi; dst
+  // is free (any bulk store from it has read it)
+  auto issue = [&](uint32_t bi, R* dst, uint32_t tile) {
     if (*(volatile uint32_t*)&s_tmo) return;
     const uint64_t first = (uint64_t)tile * TP;
     const uint64_t cnt = n - first < (uint64_t)TP ? n - first : (uint64_t)TP;
     const uint32_t bytes = (uint32_t)((cnt * sizeof(R) + 15) & ~(uint64_t)15);
-    bulk_wait_read();  // the buffer's last bulk store has read it
-    fence_proxy_async_smem();
-    tma_load_1d(s_ell[q_issued & 1], a.ell + first, bytes, &s_bar[q_issued & 1]);
-    ++iss_b[q_issued & 1];
+    fence_proxy_async_smem();  // (phase 2: the buffer held the previous tile's window)
+    tma_load_1d(dst, a.ell + first, bytes, &s_bar[bi]);
+    ++iss_b[bi];
   };
-  auto next_issue = [&](uint32_t tile) {
-    if (!STAGED) return;
-    if (threadIdx.x == 0) issue(tile);
-    ++q_issued;
-  };
-  // waits for the oldest copy; returns its buffer (unstaged: l in HBM, at
-  // the tile's start)
-  auto take_tile = [&](uint32_t tile) -> const R* {
-    if (!STAGED) return a.ell + (uint64_t)tile * TP;
-    const uint32_t b = q_done & 1;
+  // every thread: wait for the k-th copy through barrier bi
+  auto take = [&](uint32_t bi, uint32_t k) {
     if (!*(volatile uint32_t*)&s_tmo) {
-      if (mbar_wait(&s_bar[b], (q_done >> 1) & 1)) {
-        if (threadIdx.x == 0) ++ok_b[b];
+      if (mbar_wait(&s_bar[bi], k & 1)) {
+        if (threadIdx.x == 0) ++ok_b[bi];
       } else {
         s_tmo = 1u;
         atomicOr(&c->err, ERR_TIMEOUT);
       }
     }
-    ++q_done;
-    return s_ell[b];
   };
-  auto drain_copies = [&]() {  // thread 0, at exit: copies k of buffer b complete phase k & 1
+  auto drain_copies = [&]() {  // thread 0, at exit
     if constexpr (STAGED) {
       if (!*(volatile uint32_t*)&s_tmo) return;
-      for (int b = 0; b < 2; ++b)
+      for (int b = 0; b < NB1 + 2; ++b)
         for (uint32_t k = ok_b[b]; k < iss_b[b]; ++k) (void)mbar_wait(&s_bar[b], k & 1);
     }
   };
   // this thread's 16 weights of tile `tile` quantised, as inclusive running
-  // sums W and the partial sum of e = exp(l - m).  mode 0: from l in buf;
-  // 1: from l in buf (shared memory), writing e back in its place; 2: from e
-  // in buf (written back by phase 1).
-  auto quantP = [&](uint32_t tile, const R* buf, uint64_t* W, R* epart, int mode) {
+  // sums W, the partial sum of e = exp(l - m) and the largest e.  mode 0:
+  // from l in buf; 1: from l in buf (shared memory), writing e back in its
+  // place; 2: from e in buf (written back by phase 1).
+  auto quantP = [&](uint32_t tile, const R* buf, uint64_t* W, R* epart, R* emx, int mode) {
     R exs[PER];
+    R mx = (R)0;
     const uint64_t base = (uint64_t)tile * TP + (uint64_t)threadIdx.x * PER;
     R* const row = const_cast<R*>(buf) + threadIdx.x * PER;
     const bool full = base + PER <= n;
@@ -1572,6 +1585,7 @@ __global__ void __launch_bounds__(BLOCK, PER == 8 ? 4 : 3) k_cdf_sys(FilterArgs<
             w = quant_exp<R>(dl, k, &ex);
           }
           ep = ep + ex;
+          mx = ex > mx ? ex : mx;
         }
         ex4[e] = ex;
         exs[4 * q + e] = ex;
@@ -1597,6 +1611,7 @@ __global__ void __launch_bounds__(BLOCK, PER == 8 ? 4 : 3) k_cdf_sys(FilterArgs<
       ep = (threadIdx.x & 1) ? acc : (R)0;
     }
     *epart = ep;
+    *emx = mx;
   };
   // block sum of one value per thread, returned to every thread
   auto block_sum = [&](uint64_t v) {
@@ -1629,18 +1644,9 @@ __global__ void __launch_bounds__(BLOCK, PER == 8 ? 4 : 3) k_cdf_sys(FilterArgs<
 
   // phase 1: this CTA's sum of W (and with ESS of W^2)
   uint64_t mine = 0;
+  R emx_keep = (R)0;
   U128 sq{0, 0};
-  if (tb < te) next_issue(tb);
-  for (uint32_t tile = tb; tile < te; ++tile) {
-    if (tile + 1 < te) next_issue(tile + 1);
-    const R* buf = take_tile(tile);
-    uint64_t W[PER];
-    R ep;
-    // (with ESS l stays in place: a propagation that does not resample
-    // carries L - m from it, so phase 2 quantises from l again)
-    quantP(tile, buf, W, &ep, WB ? 1 : 0);
-    if (WB) fence_proxy_async_smem();  // e in buf, for the bulk store below
-    mine += W[PER - 1];
+  auto add_sq = [&](const uint64_t* W) {
     if constexpr (ESS) {
       uint64_t prev = 0;
 #pragma unroll
@@ -1650,18 +1656,54 @@ __global__ void __launch_bounds__(BLOCK, PER == 8 ? 4 : 3) k_cdf_sys(FilterArgs<
         sq = add128(sq, mul64(w, w));
       }
     }
-    if (tile == tb) {
+  };
+  if constexpr (STAGED) {
+    if (threadIdx.x == 0)
+      for (uint32_t b = 0; b + 1 < (uint32_t)NB1 && tb + b < te; ++b) issue(b, ring1(b), tb + b);
+    uint32_t i = 0;
+    for (uint32_t tile = tb; tile < te; ++tile, ++i) {
+      const uint32_t b = i % NB1;
+      R* const buf = ring1(b);
+      take(b, i / NB1);
+      uint64_t W[PER];
+      R ep;
+      // (with ESS l stays in place: a propagation that does not resample
+      // carries L - m from it, so phase 2 quantises from l again)
+      R emx;
+      quantP(tile, buf, W, &ep, &emx, WB ? 1 : 0);
+      if (WB) fence_proxy_async_smem();  // e in buf, for the bulk store below
+      mine += W[PER - 1];
+      add_sq(W);
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        if (WB) {
+          // e goes back to l's place in global memory for phase 2, which
+          // then needs no exponentials
+          const uint64_t first = (uint64_t)tile * TP;
+          const uint64_t cnt = n - first < (uint64_t)TP ? n - first : (uint64_t)TP;
+          tma_store_1d(a.ell + first, buf, (uint32_t)((cnt * sizeof(R) + 15) & ~(uint64_t)15));
+        }
+        if (tile + NB1 - 1 < te) {
+          // the previous tile's buffer takes the tile NB1 - 1 ahead, once
+          // its bulk store has read it (this tile's may still be reading)
+          if (WB) bulk_wait_read1();
+          const uint32_t nb = (i + NB1 - 1) % NB1;
+          issue(nb, ring1(nb), tile + NB1 - 1);
+        }
+      }
+    }
+  } else {
+    // at most one tile: l read directly, its W (and this thread's largest e)
+    // kept for phase 2
+    for (uint32_t tile = tb; tile < te; ++tile) {
+      uint64_t W[PER];
+      R ep;
+      quantP(tile, a.ell + (uint64_t)tile * TP, W, &ep, &emx_keep, 0);
+      mine += W[PER - 1];
+      add_sq(W);
 #pragma unroll
       for (int e = 0; e < PER; ++e) s_keep[threadIdx.x * (PER + 1) + e] = W[e];
       s_keep_ep[threadIdx.x] = ep;
-    }
-    __syncthreads();  // buf is refilled two copies later
-    if (WB && tile != tb && threadIdx.x == 0) {
-      // e goes back to l's place in global memory for phase 2, which then
-      // needs no exponentials (the first tile's W stay in shared memory)
-      const uint64_t first = (uint64_t)tile * TP;
-      const uint64_t cnt = n - first < (uint64_t)TP ? n - first : (uint64_t)TP;
-      tma_store_1d(a.ell + first, buf, (uint32_t)((cnt * sizeof(R) + 15) & ~(uint64_t)15));
     }
   }
   mine = block_sum(mine);
@@ -1674,9 +1716,9 @@ __global__ void __launch_bounds__(BLOCK, PER == 8 ? 4 : 3) k_cdf_sys(FilterArgs<
     }
     __threadfence();
     atomicAdd(&c->gbar, 1u);
-    if (STAGED && tb + 1 < te) {  // phase 2's first tile from HBM: e stored, complete
+    if (STAGED && tb < te) {  // phase 2's first tile from HBM: e stored, complete
       bulk_wait_done();
-      issue(tb + 1);
+      issue(NB1, s_ell[0], tb);
     }
     uint32_t spins = 0;
     while (ld_volatile_u32(&c->gbar) < gridDim.x) {
@@ -1689,7 +1731,6 @@ __global__ void __launch_bounds__(BLOCK, PER == 8 ? 4 : 3) k_cdf_sys(FilterArgs<
     __threadfence();
   }
   __syncthreads();
-  if (STAGED && tb + 1 < te) ++q_issued;  // the copy thread 0 issued above
 
   // phase 2: this CTA's exclusive prefix and the total T
   uint64_t pre = 0, all = 0;
@@ -1728,20 +1769,31 @@ __global__ void __launch_bounds__(BLOCK, PER == 8 ? 4 : 3) k_cdf_sys(FilterArgs<
     if (T == 0) atomicOr(&c->err, ERR_NUMERIC);
   }
   const SysDiv dv = make_sysdiv(T > 0 ? T : 1);
+  // a particle with n W_i <= 2 T owns at most two slots, and e_i <= thr
+  // implies it: W_i <= e_i 2^k <= floor(2 T / n), thr rounded down
+  R thr;
+  {
+    const uint64_t q2 = (2 * T) / n;
+    if constexpr (sizeof(R) == 4) thr = __ull2float_rd(q2) * pow2f(-k);
+    else thr = __ull2double_rd(q2) * pow2d(-k);
+  }
   if (threadIdx.x == 0) s_nruns = 0;
   __syncthreads();
   uint64_t carry = pre;
-  for (uint32_t tile = tb; tile < te; ++tile) {
+  uint32_t i2 = 0;
+  for (uint32_t tile = tb; tile < te; ++tile, ++i2) {
     uint64_t W[PER];
-    R ep;
-    if (tile == tb) {  // this thread's own entries: no barrier needed
+    R ep, emx = emx_keep;
+    if constexpr (!STAGED) {  // this thread's own entries: no barrier needed
 #pragma unroll
       for (int e = 0; e < PER; ++e) W[e] = s_keep[threadIdx.x * (PER + 1) + e];
       ep = s_keep_ep[threadIdx.x];
     } else {
-      if (tile + 1 < te) next_issue(tile + 1);
-      const R* buf = take_tile(tile);
-      quantP(tile, buf, W, &ep, WB ? 2 : 0);
+      // the next tile into the other buffer (the previous tile's window,
+      // stored out), then this one
+      if (threadIdx.x == 0 && tile + 1 < te) issue(NB1 + ((i2 + 1) & 1), s_ell[(i2 + 1) & 1], tile + 1);
+      take(NB1 + (i2 & 1), i2 >> 1);
+      quantP(tile, s_ell[i2 & 1], W, &ep, &emx, WB ? 2 : 0);
     }
     // the tile's first slot S0 = R(carry)
     // (a later tile starts where the previous one ended: no division)
@@ -1751,8 +1803,7 @@ __global__ void __launch_bounds__(BLOCK, PER == 8 ? 4 : 3) k_cdf_sys(FilterArgs<
     // least two per particle of the tile, then stored out coalesced.
     constexpr uint32_t WIN_SLOTS = STAGED ? TP * sizeof(R) / 2 : 2 * TP;
     static_assert(WIN_SLOTS % 512 == 0 && WIN_SLOTS >= 2 * TP, "window");
-    uint16_t* const win = STAGED ? reinterpret_cast<uint16_t*>(
-        s_ell[tile == tb ? (q_issued & 1) : ((q_done - 1) & 1)]) : s_win;
+    uint16_t* const win = STAGED ? reinterpret_cast<uint16_t*>(s_ell[i2 & 1]) : s_win;
     {
       ES es;
       es.zero();
@@ -1783,6 +1834,7 @@ __global__ void __launch_bounds__(BLOCK, PER == 8 ? 4 : 3) k_cdf_sys(FilterArgs<
     const uint64_t tbase = (uint64_t)tile * TP;
     const uint64_t base = tbase + (uint64_t)threadIdx.x * PER;
     const uint32_t S0 = s_S[0];
+    const uint32_t S0a = S0 & ~3u;  // the window's base: slots in aligned groups of four
     // The CDF: this thread's values go to its shared-memory row (read by the
     // resampling step below); staged (several tiles per CTA, where the store
     // instructions add up) the rows are written out coalesced below,
@@ -1806,38 +1858,63 @@ __global__ void __launch_bounds__(BLOCK, PER == 8 ? 4 : 3) k_cdf_sys(FilterArgs<
     // j .. j + c - 1 (none if D <= 0); D then drops by c T into (-T, 0] and
     // the next particle adds n w_{i+1} <= n 2^k <= 2^61 (T <= 2^61 too), so
     // D is an int64.  A particle writes its offset in the tile + 1 into the
-    // window entries of its slots: the first two by predicated stores, any
+    // window entries of its slots: the first three by predicated stores, any
     // others (a heavy particle) and slots past the window out of line, in
-    // runs of the CTA when long.  c comes from two comparisons unless it is
-    // above 2 (a heavy particle, divided out).  Every slot of [S0, S1) is
+    // runs of the CTA when long.  c comes from three comparisons unless it is
+    // above 3 (a heavy particle, divided out): no branch for up to three slots,
+    // which covers all but a few particles in a hundred even when an outlying
+    // observation concentrates the weights.  Every slot of [S0, S1) is
     // written exactly once, so the window needs no clearing.  A rolled loop
     // over the row: the step's code stays small.
+    // a warp none of whose particles can own more than two slots takes the
+    // lean step; any other warp counts up to three slots without a branch
+    const bool light = !__any_sync(0xffffffffu, emx > thr);
     if (rs && T > 0 && base < n) {
       const uint32_t ecount = base + PER <= n ? (uint32_t)PER : (uint32_t)(n - base);
       uint32_t j = threadIdx.x == 0 ? S0 : (base == 0 ? 0u : (uint32_t)sys_first_slot(o, n, r, dv));
       const U128 X = mul64x32(o, (uint32_t)n);
       const U128 KB = add128(mul64x32(T, j), r);
       int64_t D = (int64_t)(X.lo - KB.lo);  // n Q - (j T + r) just before this thread's particles
-      const int64_t Ti = (int64_t)T;
+      const int64_t Ti = (int64_t)T, T2 = 2 * Ti, T3 = 3 * Ti;
       const uint32_t off0 = (uint32_t)(base - tbase) + 1u;
       const uint32_t n32 = (uint32_t)n;
       uint64_t qprev = o;
+      if (light) {
+#pragma unroll 1
+        for (uint32_t e = 0; e < ecount; ++e) {
+          const uint64_t q = qrow[e];
+          const uint64_t w = q - qprev;
+          D += (int64_t)((uint64_t)(uint32_t)w * n32 + (((w >> 32) * n32) << 32));  // w n mod 2^64
+          qprev = q;
+          const uint32_t c = (uint32_t)(D > 0) + (uint32_t)(D > Ti);
+          const uint16_t mk = (uint16_t)(off0 + e);
+          const uint32_t x = j - S0a;
+          if (c >= 1u && x < WIN_SLOTS) win[win_entry(x)] = mk;
+          if (c >= 2u && x + 1u < WIN_SLOTS) win[win_entry(x + 1u)] = mk;
+          if (x + c > WIN_SLOTS)
+            sys_rest(j, c, S0a, WIN_SLOTS, mk, (uint32_t)base + e, win, a.anc, s_run, &s_nruns, 2u);
+          D -= c == 1u ? Ti : (int64_t)c * Ti;
+          j += c;
+        }
+      } else {
 #pragma unroll 1
       for (uint32_t e = 0; e < ecount; ++e) {
         const uint64_t q = qrow[e];
         const uint64_t w = q - qprev;
         D += (int64_t)((uint64_t)(uint32_t)w * n32 + (((w >> 32) * n32) << 32));  // w n mod 2^64
         qprev = q;
-        uint32_t c = (uint32_t)(D > 0) + (uint32_t)(D > Ti);
-        if (D > 2 * Ti) c = sys_heavy_count(D, dv);
+        uint32_t c = (uint32_t)(D > 0) + (uint32_t)(D > Ti) + (uint32_t)(D > T2);
+        if (D > T3) c = sys_heavy_count(D, dv);
         const uint16_t mk = (uint16_t)(off0 + e);
-        const uint32_t x = j - S0;
+        const uint32_t x = j - S0a;
         if (c >= 1u && x < WIN_SLOTS) win[win_entry(x)] = mk;
         if (c >= 2u && x + 1u < WIN_SLOTS) win[win_entry(x + 1u)] = mk;
-        if (c > 2u || x + c > WIN_SLOTS)
-          sys_rest(j, c, S0, WIN_SLOTS, mk, (uint32_t)base + e, win, a.anc, s_run, &s_nruns);
+        if (c >= 3u && x + 2u < WIN_SLOTS) win[win_entry(x + 2u)] = mk;
+        if (c > 3u || x + c > WIN_SLOTS)
+          sys_rest(j, c, S0a, WIN_SLOTS, mk, (uint32_t)base + e, win, a.anc, s_run, &s_nruns, 3u);
         D -= c == 1u ? Ti : (int64_t)c * Ti;
         j += c;
+      }
       }
       if (base + PER >= n || threadIdx.x == BLOCK - 1) s_S[1] = j;  // the tile's end slot
     }
@@ -1865,11 +1942,30 @@ __global__ void __launch_bounds__(BLOCK, PER == 8 ? 4 : 3) k_cdf_sys(FilterArgs<
         }
       }
     }
-    // the window's slots [S0, S0 + wcnt), stored out coalesced
+    // the window's slots [S0, wend), stored out coalesced, four per 16-byte
+    // store (the partial groups at either end slot by slot)
     {
-      const uint32_t wcnt = (rs && T > 0) ? (s_S[1] - S0 < WIN_SLOTS ? s_S[1] - S0 : WIN_SLOTS) : 0u;
+      const uint32_t S1 = s_S[1];
+      const uint32_t wend = (rs && T > 0) ? (S1 - S0a < WIN_SLOTS ? S1 : S0a + WIN_SLOTS) : S0;
       const uint32_t tb32 = (uint32_t)tbase - 1u;
-      for (uint32_t x = threadIdx.x; x < wcnt; x += BLOCK) a.anc[S0 + x] = tb32 + win[win_entry(x)];
+      const uint32_t ng = wend > S0 ? (wend - S0a + 3u) >> 2 : 0u;
+      for (uint32_t g = threadIdx.x; g < ng; g += BLOCK) {
+        const uint32_t x0 = g << 2;
+        const uint32_t sw = ((x0 >> 6) & 7u) << 1;
+        const uint2 v = *reinterpret_cast<const uint2*>(win + (x0 ^ (sw & 12u)));
+        const uint32_t lo = (sw & 2u) ? v.y : v.x, hi = (sw & 2u) ? v.x : v.y;
+        const uint32_t slot = S0a + x0;
+        const uint4 o4 = make_uint4(tb32 + (lo & 0xffffu), tb32 + (lo >> 16), tb32 + (hi & 0xffffu),
+                                    tb32 + (hi >> 16));
+        if (slot >= S0 && slot + 4u <= wend) {
+          *reinterpret_cast<uint4*>(a.anc + slot) = o4;
+        } else {
+          if (slot >= S0 && slot < wend) a.anc[slot] = o4.x;
+          if (slot + 1u >= S0 && slot + 1u < wend) a.anc[slot + 1u] = o4.y;
+          if (slot + 2u >= S0 && slot + 2u < wend) a.anc[slot + 2u] = o4.z;
+          if (slot + 3u >= S0 && slot + 3u < wend) a.anc[slot + 3u] = o4.w;
+        }
+      }
     }
     // runs past the window, by the whole CTA
     for (uint32_t q = 0; q < nr; ++q) {
