@@ -89,6 +89,12 @@ struct pf_filter {
   pf_config cfg;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
+  // multinomial schemes: the exponential spacings need nothing from the
+  // cycle's weights or CDF, so they are scanned on a second stream, forked
+  // from and joined back into the filter's stream (a parallel branch of the
+  // captured graph)
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   uint64_t n = 0;
   int k = 0;
   uint32_t ntiles = 0;
@@ -299,6 +305,29 @@ pf_status enqueue_cycle(pf_filter* f, KTimer* tm = nullptr, const double* y_src 
   }
   const uint64_t n = f->n;
   if (tm) cudaEventRecord(tm->ev[0], s);
+  // multinomial: the spacing scan (Section 3.1's sorted uniforms) depends only
+  // on the seed, the filter and t, so outside a timed cycle it runs on the
+  // side stream beside the weights and the CDF scan
+  const bool fork = is_multinomial(f->scheme) && !tm;
+  auto spacing = [&](cudaStream_t on) {
+    SpacingArgs sp;
+    sp.S = f->S;
+    sp.stat[0] = f->stat_e[0];
+    sp.stat[1] = f->stat_e[1];
+    sp.ctl = f->ctl;
+    sp.t_dev = &f->ctl->t;
+    sp.t_arg = 0;
+    sp.n = n;
+    sp.seed = f->cfg.seed;
+    sp.filter = f->cfg.filter_id;
+    k_spacing_scan<<<f->ntiles, BLOCK, 0, on>>>(sp);
+  };
+  if (fork) {
+    CK(cudaEventRecord(f->ev_fork, s));
+    CK(cudaStreamWaitEvent(f->side, f->ev_fork, 0));
+    spacing(f->side);
+    CK(cudaEventRecord(f->ev_join, f->side));
+  }
   if (f->bootstrap) {  // Algorithm "Particle Filtering": propagate blind, then weigh
     k_boot_pw<R><<<(unsigned)cdiv(n, BLOCK), BLOCK, 0, s>>>(a);
     mark(tm, "propagate_weights", s);
@@ -330,18 +359,10 @@ pf_status enqueue_cycle(pf_filter* f, KTimer* tm = nullptr, const double* y_src 
     k_ess<R><<<f->ess_grid, BLOCK, 0, s>>>(a);
     mark(tm, "ess", s);
   }
-  if (is_multinomial(f->scheme)) {
-    SpacingArgs sp;
-    sp.S = f->S;
-    sp.stat[0] = f->stat_e[0];
-    sp.stat[1] = f->stat_e[1];
-    sp.ctl = f->ctl;
-    sp.t_dev = &f->ctl->t;
-    sp.t_arg = 0;
-    sp.n = n;
-    sp.seed = f->cfg.seed;
-    sp.filter = f->cfg.filter_id;
-    k_spacing_scan<<<f->ntiles, BLOCK, 0, s>>>(sp);
+  if (fork) {
+    CK(cudaStreamWaitEvent(s, f->ev_join, 0));
+  } else if (is_multinomial(f->scheme)) {
+    spacing(s);
     mark(tm, "spacing_scan", s);
   }
   PosArgs pa;
@@ -632,7 +653,13 @@ pf_status pf_create(const pf_config* cfg, pf_filter** out) {
   // l is moved by 16-byte bulk copies: its tail is padded to 16 bytes
   if ((st = dev_alloc(f, (n * rs + 15) & ~(size_t)15, &f->ell)) != PF_OK) return bail(st);
   if ((st = dev_alloc(f, n * 8, (void**)&f->Q)) != PF_OK) return bail(st);
-  if (is_multinomial(f->scheme) && (st = dev_alloc(f, (n + 1) * 8, (void**)&f->S)) != PF_OK) return bail(st);
+  if (is_multinomial(f->scheme)) {
+    if ((st = dev_alloc(f, (n + 1) * 8, (void**)&f->S)) != PF_OK) return bail(st);
+    if (cudaStreamCreateWithFlags(&f->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&f->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&f->ev_join, cudaEventDisableTiming) != cudaSuccess)
+      return bail(set_err(PF_ERR_CUDA, "side stream: %s", cudaGetErrorString(cudaGetLastError())));
+  }
   if ((st = dev_alloc(f, n * 4, (void**)&f->anc)) != PF_OK) return bail(st);
   if (is_cutpoint(f->scheme) && (st = dev_alloc(f, n * 4, (void**)&f->I)) != PF_OK) return bail(st);
   if ((st = dev_alloc(f, ((size_t)merge_chunks(n) + 1) * 8, (void**)&f->splits)) != PF_OK) return bail(st);
@@ -1003,6 +1030,12 @@ pf_status pf_destroy(pf_filter* f) {
   free_all(f);
   if (f->ctl_host) cudaFreeHost(f->ctl_host);
   if (f->io) cudaFreeHost(f->io);
+  if (f->side) {
+    cudaStreamSynchronize(f->side);
+    cudaStreamDestroy(f->side);
+  }
+  if (f->ev_fork) cudaEventDestroy(f->ev_fork);
+  if (f->ev_join) cudaEventDestroy(f->ev_join);
   if (f->own_stream) cudaStreamDestroy(f->stream);
   cudaGetLastError();
   delete f;
