@@ -289,6 +289,12 @@ pf_status launch_resample(int scheme, const PosArgs& pa, uint64_t n, uint32_t* I
 // With form CF_HEAD / CF_MID the propagation also computes the next cycle's
 // weights against y_{t+2} (*ynx_src when set, else ynx_val); with CF_MID /
 // CF_TAIL the weights kernel is left out, its work done by the previous cycle.
+// The binary32 propagation with or without slots handed out by ticket.
+template <bool LEARN, bool FUSE, bool ESS>
+void launch_prop2(bool dyn, unsigned grid, cudaStream_t s, const FilterArgs<float>& a) {
+  if (dyn) k_propagate2<LEARN, FUSE, ESS, true><<<grid, BLOCK, 0, s>>>(a);
+  else k_propagate2<LEARN, FUSE, ESS, false><<<grid, BLOCK, 0, s>>>(a);
+}
 template <class R>
 pf_status enqueue_cycle(pf_filter* f, KTimer* tm = nullptr, const double* y_src = nullptr,
                         double y_val = 0.0, int form = CF_PLAIN, const double* ynx_src = nullptr,
@@ -409,24 +415,26 @@ pf_status enqueue_cycle(pf_filter* f, KTimer* tm = nullptr, const double* y_src 
   }
   const bool fuse = !f->bootstrap && !f->ess && form_fuses(form);
   const unsigned pg = fuse ? f->prop_grid_fuse : f->prop_grid;
+  // binary32: slots handed out by ticket when each warp has many 64-slot units
+  const bool dyn = (n + 63) / 64 >= (uint64_t)PROP_DYN * pg * WARPS;
   if (f->bootstrap) {
     k_boot_gather<R><<<(unsigned)cdiv(n, BLOCK), BLOCK, 0, s>>>(a);
     mark(tm, "gather", s);
   } else if (f->ess) {  // adaptive resampling (never fused)
     if constexpr (sizeof(R) == 4) {
-      if (f->learn) k_propagate2<true, false, true><<<pg, BLOCK, 0, s>>>(a);
-      else k_propagate2<false, false, true><<<pg, BLOCK, 0, s>>>(a);
+      if (f->learn) launch_prop2<true, false, true>(dyn, pg, s, a);
+      else launch_prop2<false, false, true>(dyn, pg, s, a);
     } else {
       if (f->learn) k_propagate<R, true, false, true><<<pg, BLOCK, 0, s>>>(a);
       else k_propagate<R, false, false, true><<<pg, BLOCK, 0, s>>>(a);
     }
   } else if constexpr (sizeof(R) == 4) {  // binary32: two slots per thread, paired arithmetic
     if (f->learn) {
-      if (fuse) k_propagate2<true, true><<<pg, BLOCK, 0, s>>>(a);
-      else k_propagate2<true><<<pg, BLOCK, 0, s>>>(a);
+      if (fuse) launch_prop2<true, true, false>(dyn, pg, s, a);
+      else launch_prop2<true, false, false>(dyn, pg, s, a);
     } else {
-      if (fuse) k_propagate2<false, true><<<pg, BLOCK, 0, s>>>(a);
-      else k_propagate2<false><<<pg, BLOCK, 0, s>>>(a);
+      if (fuse) launch_prop2<false, true, false>(dyn, pg, s, a);
+      else launch_prop2<false, false, false>(dyn, pg, s, a);
     }
   } else {
     if (f->learn) {
@@ -789,6 +797,8 @@ pf_status pf_create(const pf_config* cfg, pf_filter** out) {
       }
       const uint64_t nt = f->cdf_per == 8 ? f->nparts : f->ntiles;
       f->cdf_grid = (unsigned)(nt < g ? nt : g);
+      // the staged binary32 kernel leaves one exact log-ML partial per CTA
+      if (f->cdf_staged && !f->fp64) f->nparts = f->cdf_grid;
       if ((st = dev_alloc(f, (size_t)f->cdf_grid * 8, (void**)&f->cta_tot)) != PF_OK) return bail(st);
       if (f->ess && (st = dev_alloc(f, (size_t)f->cdf_grid * sizeof(U128), (void**)&f->cta_sq)) != PF_OK)
         return bail(st);

@@ -74,6 +74,8 @@ struct Ctl {
   uint32_t resamp;
   uint32_t done_ess;
   double slam;
+  // binary32 propagation: the next unit of 64 slots to hand out
+  unsigned long long prop_ticket;
 };
 
 // Tile status words carry their value and flag in one aligned 64-bit word and
@@ -1781,6 +1783,10 @@ __global__ void __launch_bounds__(BLOCK, PER == 8 ? 4 : 3) k_cdf_sys(FilterArgs<
   __syncthreads();
   uint64_t carry = pre;
   uint32_t i2 = 0;
+  // the log-ML partial of the CTA's tiles (thread 0)
+  constexpr bool CTA_PART = STAGED && sizeof(R) == 4;
+  ES cta_es;
+  cta_es.zero();
   for (uint32_t tile = tb; tile < te; ++tile, ++i2) {
     uint64_t W[PER];
     R ep, emx = emx_keep;
@@ -1825,7 +1831,10 @@ __global__ void __launch_bounds__(BLOCK, PER == 8 ? 4 : 3) k_cdf_sys(FilterArgs<
       if (lane == 0) {
         ES tot = s_es[0];
         for (int w = 1; w < WARPS; ++w) tot.add(s_es[w]);
-        reinterpret_cast<ES*>(a.part)[tile] = tot;
+        // staged binary32: one exact partial per CTA (the sum of its tiles'),
+        // so that the propagation's final fold reads one per CTA
+        if constexpr (CTA_PART) cta_es.add(tot);
+        else reinterpret_cast<ES*>(a.part)[tile] = tot;
       }
     }
     __syncthreads();
@@ -1977,6 +1986,7 @@ __global__ void __launch_bounds__(BLOCK, PER == 8 ? 4 : 3) k_cdf_sys(FilterArgs<
     if (threadIdx.x == 0) s_nruns = 0;
     carry += tile_tot;
   }
+  if (CTA_PART && threadIdx.x == 0) reinterpret_cast<ES*>(a.part)[blockIdx.x] = cta_es;
   if (T == 0) {  // empty CDF (flagged): keep every index in range
     for (uint64_t j = (uint64_t)blockIdx.x * BLOCK + threadIdx.x; j < n;
          j += (uint64_t)gridDim.x * BLOCK)
@@ -2109,7 +2119,23 @@ __device__ void fold_cycle_warp(const FilterArgs<R>& a, uint32_t t) {
   const int lane = threadIdx.x & 31;
   ES acc;
   acc.zero();
-  for (uint32_t b = lane; b < a.nparts; b += 32) acc.add(reinterpret_cast<const ES*>(a.part)[b]);
+  const ES* const part = reinterpret_cast<const ES*>(a.part);
+  if constexpr (sizeof(R) == 4) {
+    // exact fixed-point partials: any grouping gives the same sum, so each
+    // lane issues eight loads at once
+    for (uint32_t b = lane; b < a.nparts; b += 256) {
+      ES v[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        v[q].zero();
+        if (b + 32u * q < a.nparts) v[q] = part[b + 32u * q];
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) acc.add(v[q]);
+    }
+  } else {
+    for (uint32_t b = lane; b < a.nparts; b += 32) acc.add(part[b]);
+  }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc.add(acc.shfl_xor(o));
   if (lane == 0) {
@@ -2140,6 +2166,7 @@ __device__ void fold_cycle_warp(const FilterArgs<R>& a, uint32_t t) {
     c->ticket_e = 0;
     c->done_prop = 0;
     c->gbar = 0;
+    c->prop_ticket = 0;
     __threadfence();
     c->t = t + 1;
   }
@@ -2428,12 +2455,16 @@ __global__ void __launch_bounds__(BLOCK, 5) k_propagate(FilterArgs<R> a) {
 // the scalar propagation, in the same order, so the results are the same bits.
 // ---------------------------------------------------------------------------
 constexpr uint32_t WQ2_CAP = 160;  // 31 queued + 4 pushes of 32 per pass
+// k_propagate2's units of 64 slots: with DYN handed out by ticket, PROP_GRAB
+// at a time; the launch takes DYN when there are at least PROP_DYN per warp
+constexpr uint32_t PROP_GRAB = 4;
+constexpr uint32_t PROP_DYN = 16;
 
 // With FUSE, the next cycle's weights as in k_propagate, the two slots of a
 // pass weighed by paired operations.
 // 3 CTAs per SM (up to 85 registers, no spills): measured faster at N = 2^24
 // than 4 CTAs at 64 registers, where the plain form spills.
-template <bool LEARN, bool FUSE = false, bool ESS = false>
+template <bool LEARN, bool FUSE = false, bool ESS = false, bool DYN = false>
 __global__ void __launch_bounds__(BLOCK, 3) k_propagate2(FilterArgs<float> a) {
   typedef GammaItem<float> Item;
   __shared__ Item s_q[WARPS][WQ2_CAP];
@@ -2447,9 +2478,6 @@ __global__ void __launch_bounds__(BLOCK, 3) k_propagate2(FilterArgs<float> a) {
   Item* const wq = s_q[threadIdx.x >> 5];
   uint32_t qn = 0;  // warp-uniform
   const uint64_t n = a.n;
-  const uint64_t half = (uint64_t)gridDim.x * BLOCK;
-  const uint64_t stride = 2 * half;
-  const uint64_t iters = (n + stride - 1) / stride;
   auto clampi = [&](uint32_t v) { return v < n ? v : (uint32_t)(n - 1); };
   // adaptive resampling: without a resampling every slot is its own ancestor
   bool rs = true;
@@ -2485,15 +2513,33 @@ __global__ void __launch_bounds__(BLOCK, 3) k_propagate2(FilterArgs<float> a) {
   auto weigh_late = [&](const Item& itm) {  // FUSE: the slot's state is final
     weigh_next<float>(a.ell, itm.j, dst.x[itm.j], dst.s2[itm.j], dst.t2[itm.j], yn, mxn, badn);
   };
-  // Pass p covers slots [p S, p S + S) (S = stride): thread g takes the
-  // pair j0 = p S + 2g, j1 = j0 + 1 (the two slots that share a draw), so its
-  // ancestor load and its stores are 8 or 16 bytes wide.  In a partial last
-  // pass the threads past the end (whole warps) skip it.
-  const uint64_t g2 = 2 * ((uint64_t)blockIdx.x * BLOCK + threadIdx.x);
+  // Slots go out in units of 64: lane l of a warp takes the pair j0 = 64 u +
+  // 2 l, j1 = j0 + 1 of unit u (the two slots that share a draw), so its
+  // ancestor load and its stores are 8 or 16 bytes wide.  Without DYN, pass
+  // p of warp w (of the grid's W) is unit p W + w.  With DYN (many units per
+  // warp) a warp takes PROP_GRAB consecutive units per ticket, each ticket
+  // taken a batch ahead of its use, so that a warp on a slower SM (or with
+  // more draws that missed the squeeze) takes fewer of them and the kernel
+  // ends with its work: under the fixed assignment the CTAs' finishing times
+  // at N = 2^24 spread from 187 to 234 us.  A slot's arithmetic does not
+  // depend on the warp that computes it.
+  const uint64_t nunits = (n + 63) / 64;
+  const uint64_t stride = (uint64_t)gridDim.x * BLOCK * 2;  // slots per pass
+  const uint64_t iters = (n + stride - 1) / stride;
+  unsigned long long tick = 0;  // lane 0: the ticket of the next batch
+  uint64_t u = 0;
+  uint64_t j0 = 2 * ((uint64_t)blockIdx.x * BLOCK + threadIdx.x);
+  if constexpr (DYN) {
+    if (lane == 0) tick = atomicAdd(&a.ctl->prop_ticket, (unsigned long long)PROP_GRAB);
+    u = __shfl_sync(0xffffffffu, tick, 0);
+    if (lane == 0) tick = atomicAdd(&a.ctl->prop_ticket, (unsigned long long)PROP_GRAB);
+    j0 = u * 64 + 2 * (uint64_t)lane;
+  }
+  (void)nunits; (void)iters; (void)u;
   // the ancestors of the pair starting at slot j (even; clamped into range)
   auto anc_pair = [&](uint64_t j) -> uint2 {
-    if constexpr (ESS) {
-      if (!rs) return make_uint2((uint32_t)j, (uint32_t)j + 1u);
+    if constexpr (ESS) {  // (past the end: the last slot, a valid address)
+      if (!rs) return make_uint2(clampi((uint32_t)j), clampi((uint32_t)j + 1u));
     }
     if (j + 1 < n) {
       const uint2 v = *reinterpret_cast<const uint2*>(a.anc + j);
@@ -2501,18 +2547,29 @@ __global__ void __launch_bounds__(BLOCK, 3) k_propagate2(FilterArgs<float> a) {
     }
     return make_uint2(j < n ? clampi(a.anc[j]) : 0u, 0u);
   };
-  uint64_t j0 = g2;
   uint2 an = anc_pair(j0);
   Gathered<float> c0 = gather_rec<float>(src, an.x);
   Gathered<float> c1 = gather_rec<float>(src, an.y);
-  for (uint64_t it = 0; it < iters; ++it, j0 += stride) {
+  for (uint64_t it = 0; DYN ? u < nunits : it < iters; ++it) {  // (the same in every lane)
+    // the next pair: the next pass's; with DYN the next unit of the batch,
+    // or the first of the batch taken a batch ago (then the ticket of the
+    // batch after it)
+    uint64_t jn = j0 + stride;
+    uint64_t un = u + 1;
+    if constexpr (DYN) {
+      if (un % PROP_GRAB == 0) {
+        un = __shfl_sync(0xffffffffu, tick, 0);
+        if (lane == 0 && un < nunits) tick = atomicAdd(&a.ctl->prop_ticket, (unsigned long long)PROP_GRAB);
+      }
+      jn = un * 64 + 2 * (uint64_t)lane;
+    }
     const uint64_t j1 = j0 + 1;
     const bool v0 = j0 < n, v1 = j1 < n;
-    // the next pass's records, gathered ahead
-    const uint2 na = anc_pair(j0 + stride);
+    // the next unit's records, gathered ahead
+    const uint2 na = anc_pair(jn);
     const Gathered<float> n0 = gather_rec<float>(src, na.x);
     const Gathered<float> n1 = gather_rec<float>(src, na.y);
-    // a warp with no slot left in a partial last pass skips it
+    // the last unit may be partial: a warp skips it when no lane has a slot
     if (__any_sync(0xffffffffu, v0)) {
       const float2 xa = make_float2(c0.x, c1.x), sa = make_float2(c0.s2, c1.s2);
       const float2 ta = make_float2(c0.t2, c1.t2);
@@ -2640,6 +2697,8 @@ __global__ void __launch_bounds__(BLOCK, 3) k_propagate2(FilterArgs<float> a) {
     }
     c0 = n0;
     c1 = n1;
+    u = un;
+    j0 = jn;
   }
   if constexpr (LEARN && FUSE) wq_drain_post(wq, qn, 1u, lane, finish, weigh_late);
   else if (LEARN) wq_drain(wq, qn, 1u, lane, finish);
