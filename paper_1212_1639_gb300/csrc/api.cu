@@ -472,10 +472,15 @@ const void* cdf_fn(bool fp64, bool staged, int per, bool ess) {
   return ess ? (const void*)k_cdf_sys<float, false, 16, true> : (const void*)k_cdf_sys<float, false, 16>;
 }
 
-const void* prop_fuse_fn(const pf_filter* f) {
+// The propagation that also computes the next cycle's weights (binary32:
+// the form with slots handed out by ticket when dyn).
+const void* prop_fuse_fn(const pf_filter* f, bool dyn = false) {
   if (f->fp64)
     return f->learn ? (const void*)k_propagate<double, true, true>
                     : (const void*)k_propagate<double, false, true>;
+  if (dyn)
+    return f->learn ? (const void*)k_propagate2<true, true, false, true>
+                    : (const void*)k_propagate2<false, true, false, true>;
   return f->learn ? (const void*)k_propagate2<true, true> : (const void*)k_propagate2<false, true>;
 }
 
@@ -504,6 +509,7 @@ pf_status build_graph(pf_filter* f, int form) {
       : f->ess     ? (f->fp64 ? (const void*)k_weights<double, true> : (const void*)k_weights<float, true>)
                    : (f->fp64 ? (const void*)k_weights<double> : (const void*)k_weights<float>);
   const void* pfun = prop_fuse_fn(f);
+  const void* pfun_dyn = prop_fuse_fn(f, true);
   const size_t asz = f->fp64 ? sizeof(FilterArgs<double>) : sizeof(FilterArgs<float>);
   for (cudaGraphNode_t nd : nodes) {
     cudaGraphNodeType ty;
@@ -518,7 +524,7 @@ pf_status build_graph(pf_filter* f, int form) {
       G.wkp[0] = G.wargs;
       G.wparams.kernelParams = G.wkp;
       G.wparams.extra = nullptr;
-    } else if (p.func == pfun) {
+    } else if (p.func == pfun || p.func == pfun_dyn) {
       G.pnode = nd;
       G.pparams = p;
       std::memcpy(G.pargs, p.kernelParams[0], asz);

@@ -1458,6 +1458,7 @@ __global__ void __launch_bounds__(BLOCK, PER == 8 ? 4 : 3) k_cdf_sys(FilterArgs<
   constexpr int TP = BLOCK * PER;  // particles per tile
   typedef typename ESumT<R>::T ES;
   __shared__ uint64_t s_warp[WARPS + 1];
+  __shared__ uint64_t s_pre2[WARPS];
   __shared__ ES s_es[WARPS];
   __shared__ uint64_t s_bc[2];
   __shared__ uint32_t s_run[BB_RUNS][3];
@@ -1741,8 +1742,24 @@ __global__ void __launch_bounds__(BLOCK, PER == 8 ? 4 : 3) k_cdf_sys(FilterArgs<
     all += v;
     if (b < blockIdx.x) pre += v;
   }
-  pre = block_sum(pre);
-  const uint64_t T = block_sum(all);
+  // both block sums in one pass (two block barriers)
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    pre += __shfl_xor_sync(0xffffffffu, pre, o);
+    all += __shfl_xor_sync(0xffffffffu, all, o);
+  }
+  if (lane == 0) {
+    s_warp[warp] = pre;
+    s_pre2[warp] = all;
+  }
+  __syncthreads();
+  pre = 0;
+  uint64_t T = 0;
+  for (int w = 0; w < WARPS; ++w) {
+    pre += s_warp[w];
+    T += s_pre2[w];
+  }
+  __syncthreads();
   // adaptive resampling: the decision of k_ess, from the same exact sums
   bool rs = true;
   if constexpr (ESS) {
@@ -1772,13 +1789,13 @@ __global__ void __launch_bounds__(BLOCK, PER == 8 ? 4 : 3) k_cdf_sys(FilterArgs<
   }
   const SysDiv dv = make_sysdiv(T > 0 ? T : 1);
   // a particle with n W_i <= 2 T owns at most two slots, and e_i <= thr
-  // implies it: W_i <= e_i 2^k <= floor(2 T / n), thr rounded down
+  // implies it: W_i <= e_i 2^k <= thr 2^k <= 2 T / n, every rounding of
+  // thr = T (1 / n) 2^(1 - k) taken downward
   R thr;
-  {
-    const uint64_t q2 = (2 * T) / n;
-    if constexpr (sizeof(R) == 4) thr = __ull2float_rd(q2) * pow2f(-k);
-    else thr = __ull2double_rd(q2) * pow2d(-k);
-  }
+  if constexpr (sizeof(R) == 4)
+    thr = __fmul_rd(__fmul_rd(__ull2float_rd(T), __frcp_rd(__ull2float_ru(n))), pow2f(1 - k));
+  else
+    thr = __dmul_rd(__dmul_rd(__ull2double_rd(T), __drcp_rd((double)n)), pow2d(1 - k));
   if (threadIdx.x == 0) s_nruns = 0;
   __syncthreads();
   uint64_t carry = pre;

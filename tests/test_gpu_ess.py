@@ -92,6 +92,17 @@ def test_adaptive_at_scale(pf, orc):
     _run(pf, orc, 2_600_003, 4, 1, 0, 0.3, y=y, seed=5)
 
 
+def test_adaptive_ticketed_propagation(pf, orc):
+    """4,194,305 particles, FP32: the adaptive propagation hands its slots
+    out by ticket (and carries the log-weights of the cycles that do not
+    resample); systematic through the staged cooperative kernel, and
+    stratified through the general path."""
+    y = np.array([0.3, 0.5, 7.5, 7.9, 0.2])
+    kinds = _run(pf, orc, 4_194_305, 5, 1, 0, 0.6, y=y, seed=17)
+    assert kinds.any() and not kinds.all()
+    _run(pf, orc, 4_194_305, 3, 4, 0, 0.6, seed=18, every_step=False)
+
+
 def test_ess_one_equals_always_resampling_filter(pf):
     """At ess_frac = 1 every cycle resamples: the adaptive filter's particles
     and log marginal likelihood equal those of the plain filter (the

@@ -94,6 +94,19 @@ def test_step_ahead_at_scale(pf, orc):
     _run_ahead(pf, orc, 2_600_003, 3, 1, 0, seed=7, every_step=True)
 
 
+def test_step_ahead_ticketed_propagation(pf, orc):
+    """4,194,305 particles: at least 16 units of 64 slots per warp, so the
+    binary32 propagation (fused and not) hands its slots out by ticket; the
+    CDF kernel is TMA-staged.  Systematic (an outlying observation for heavy
+    particles), multinomial, and known variances."""
+    n = 4_194_305
+    y = np.array([0.2, 6.5, 6.8, 0.4])
+    _run_ahead(pf, orc, n, 4, 1, 0, y=y, seed=11, every_step=True)
+    _run_ahead(pf, orc, n, 3, 0, 0, seed=12, every_step=False)
+    _run_ahead(pf, orc, n, 3, 1, 0, seed=13, every_step=False, known_variances=True, sigma2=0.9,
+               tau2=0.2)
+
+
 def test_step_ahead_equals_unfused_cycles(pf):
     """A chain of fused cycles equals the unfused cycles (pf_step, and pf_run
     over host or device-resident observations) bit for bit, every scheme and
