@@ -76,6 +76,8 @@ struct Ctl {
   double slam;
   // binary32 propagation: the next unit of 64 slots to hand out
   unsigned long long prop_ticket;
+  // weights kernel: the next round of WARPS chunks to hand out
+  uint32_t w_ticket;
 };
 
 // Tile status words carry their value and flag in one aligned 64-bit word and
@@ -362,7 +364,7 @@ __global__ void __launch_bounds__(BLOCK, W_CTAS_PER_SM) k_weights(FilterArgs<R> 
     mx = fmax(mx, l);
     return l;
   };
-  for (uint64_t cb = gw * CHUNK; cb < n; cb += nw * CHUNK) {
+  auto chunk = [&](uint64_t cb) {  // the warp's chunk of CHUNK particles from cb
     if (cb + CHUNK <= n) {
       const uint64_t i0 = cb + (uint64_t)lane * NV, i1 = i0 + 32 * NV;
       const V x0 = *reinterpret_cast<const V*>(st.x + i0), x1 = *reinterpret_cast<const V*>(st.x + i1);
@@ -384,6 +386,30 @@ __global__ void __launch_bounds__(BLOCK, W_CTAS_PER_SM) k_weights(FilterArgs<R> 
       for (uint64_t i = cb + lane; i < n; i += 32)
         a.ell[i] = weigh(st.x[i], st.s2[i], st.t2[i], ESS ? a.lam[i] : (R)0);
     }
+  };
+  const uint64_t nchunks = (n + CHUNK - 1) / CHUNK;
+  if (nchunks >= 4 * nw) {
+    // Many chunks per warp: rounds of WARPS chunks (one per warp) go to
+    // CTAs by ticket, each ticket taken a round ahead by thread 0, so that
+    // CTAs on faster SMs take more rounds (the CTAs' finishing times under
+    // the grid stride at N = 2^24 spread from 35 to 43 us).
+    __shared__ uint32_t s_round[2];
+    const uint64_t nrounds = (nchunks + WARPS - 1) / WARPS;
+    uint64_t rd = blockIdx.x;
+    uint32_t tk = 0;
+    if (threadIdx.x == 0) tk = atomicAdd(&a.ctl->w_ticket, 1u);
+    for (uint32_t q = 0; rd < nrounds; ++q) {
+      const uint64_t ch = rd * WARPS + (threadIdx.x >> 5);
+      if (ch < nchunks) chunk(ch * CHUNK);
+      if (threadIdx.x == 0) {
+        s_round[q & 1] = gridDim.x + tk;
+        tk = atomicAdd(&a.ctl->w_ticket, 1u);
+      }
+      __syncthreads();
+      rd = s_round[q & 1];
+    }
+  } else {
+    for (uint64_t cb = gw * CHUNK; cb < n; cb += nw * CHUNK) chunk(cb);
   }
   if (bad) atomicOr(&a.ctl->err, ERR_NUMERIC);
   mx = block_max<R>(mx, s_red);
@@ -2184,6 +2210,7 @@ __device__ void fold_cycle_warp(const FilterArgs<R>& a, uint32_t t) {
     c->done_prop = 0;
     c->gbar = 0;
     c->prop_ticket = 0;
+    c->w_ticket = 0;
     __threadfence();
     c->t = t + 1;
   }
