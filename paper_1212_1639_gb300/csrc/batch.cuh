@@ -202,6 +202,7 @@ struct BatchSmem {
   R m;
   uint32_t wb;
   U128 sqw[NT / 32];             // per-warp sums of W^2 (adaptive filters)
+  uint32_t rk[20];               // Philox round keys of the filter's seed (binary32 propagation)
 };
 
 // One cycle of one filter by a group of G CTAs (G = 1: one CTA; G > 1: the
@@ -598,6 +599,12 @@ __device__ __forceinline__ void batch_filter(const BatchArgs<R>& a, const BatchI
     for (uint64_t j = rank * NT + threadIdx.x; j < n; j += (uint64_t)G * NT)
       a.anc[off + j] = (uint32_t)j;
   }
+  // the Philox round keys of the filter's seed: the key words bumped by the
+  // Weyl constants, round by round (read after the barrier below)
+  if (sizeof(R) == 4 && threadIdx.x < 10) {
+    sm.rk[2 * threadIdx.x] = (uint32_t)seed + threadIdx.x * 0x9E3779B9u;
+    sm.rk[2 * threadIdx.x + 1] = (uint32_t)(seed >> 32) + threadIdx.x * 0xBB67AE85u;
+  }
   group_sync(G);  // every ancestor written
 
   // 4. propagation, one slot per thread per pass (slot blocks of NT dealt
@@ -624,6 +631,135 @@ __device__ __forceinline__ void batch_filter(const BatchArgs<R>& a, const BatchI
     an = an < n ? an : (uint32_t)(n - 1);
     return gather_rec<R>(fsrc, an);
   };
+  if constexpr (sizeof(R) == 4) {
+    // binary32: the slot pair 2k, 2k + 1 per thread (pair blocks of NT dealt
+    // round-robin over the group), the two slots sharing draw B (reading 19)
+    // and each paired FMUL2 / FFMA2: the operations of the single-filter
+    // paired propagation, lane by lane the scalar ones, so the same bits
+    const uint64_t np = (n + 1) / 2, ppstride = (uint64_t)G * NT;
+    // the ancestors of a pair (clamped into range), loaded a pass ahead
+    auto anc_of = [&](uint64_t jj) -> uint32_t {
+      uint32_t an = jj < n ? (resamp ? a.anc[off + jj] : (uint32_t)jj) : 0u;
+      return an < n ? an : (uint32_t)(n - 1);
+    };
+    uint64_t kq = (uint64_t)rank * NT + threadIdx.x;
+    uint32_t a0 = anc_of(2 * kq), a1 = anc_of(2 * kq + 1);
+    for (uint64_t k0 = (uint64_t)rank * NT; k0 < np; k0 += ppstride) {
+      const uint64_t kp = k0 + threadIdx.x;
+      const uint64_t j0 = 2 * kp, j1 = j0 + 1;
+      const bool v0 = j0 < n, v1 = j1 < n;
+      const Gathered<float> c0 = gather_rec<float>(fsrc, a0), c1 = gather_rec<float>(fsrc, a1);
+      a0 = anc_of(2 * (kp + ppstride));
+      a1 = anc_of(2 * (kp + ppstride) + 1);
+      bool ds0 = false, dt0 = false, ds1 = false, dt1 = false;
+      uint64_t bs0 = 0, bt0 = 0, bs1 = 0, bt1 = 0;
+      float2 Zs = make_float2(0.0f, 0.0f), Us = Zs, Zt = Zs, Ut = Zs;
+      if (v0) {
+        const float2 xa = make_float2(c0.x, c1.x), sa = make_float2(c0.s2, c1.s2);
+        const float2 ta = make_float2(c0.t2, c1.t2);
+        // V and mu share one correctly rounded reciprocal of s = sigma^2 + tau^2
+        const float2 sp = addp(sa, ta);
+        const float2 ri = make_float2(__frcp_rn(sp.x), __frcp_rn(sp.y));
+        const float2 V = mul2(mul2(sa, ta), ri);
+        const float2 nn = fma2(xa, sa, mul2(splat2(yr), ta));
+        const float2 mu = mul2(nn, ri);
+        const float2 sv = make_float2(sqrtf(V.x), sqrtf(V.y));
+        float2 Z;
+        theta_draws2(sm.rk, fid, t, (uint32_t)kp, &Z, &Zs, &Us, &Zt, &Ut);
+        const float2 xj = fma2(sv, Z, mu);
+        const uint64_t d = off + j0;  // even: filter offsets are multiples of 32
+        if (v1) *reinterpret_cast<float2*>(dst.x + d) = xj;
+        else dst.x[d] = xj.x;
+        if (learn) {
+          const float2 rsd = addp(splat2(yr), make_float2(-xj.x, -xj.y));
+          const float2 rtd = addp(xj, make_float2(-xa.x, -xa.y));
+          // b + r^2 / 2 in 2^-32 fixed point, per SuffOps<float>::add_half_square
+          const float2 ws = mul2(mul2(rsd, rsd), splat2(0x1p31f));
+          const float2 wt = mul2(mul2(rtd, rtd), splat2(0x1p31f));
+          bool f0 = false, f1 = false;
+          auto addb = [&](uint64_t b, float v, bool* f) -> uint64_t {
+            if (!(v < 0x1p63f)) {
+              *f = true;
+              return b;
+            }
+            return b + SuffOps<float>::incr(v);
+          };
+          bs0 = addb(c0.bs, ws.x, &f0);
+          bt0 = addb(c0.bt, wt.x, &f0);
+          bs1 = addb(c1.bs, ws.y, &f1);
+          bt1 = addb(c1.bt, wt.y, &f1);
+          fail |= f0 || (v1 && f1);
+          if (v1) {
+            *reinterpret_cast<ulonglong2*>(dst.bs + d) = make_ulonglong2(bs0, bs1);
+            *reinterpret_cast<ulonglong2*>(dst.bt + d) = make_ulonglong2(bt0, bt1);
+          } else {
+            dst.bs[d] = bs0;
+            dst.bt[d] = bt0;
+          }
+          // Marsaglia-Tsang squeeze for sigma^2 and tau^2 (x lanes: slot j0, y: j1)
+          const float2 vs = fma2(splat2(cs), Zs, splat2(1.0f)), vt = fma2(splat2(ct), Zt, splat2(1.0f));
+          const float2 v3s = mul2(mul2(vs, vs), vs), v3t = mul2(mul2(vt, vt), vt);
+          const float2 Z2s = mul2(Zs, Zs), Z2t = mul2(Zt, Zt);
+          const float2 thrs = fma2(splat2(-ks), mul2(Z2s, Z2s), splat2(1.0f));
+          const float2 thrt = fma2(splat2(-kt), mul2(Z2t, Z2t), splat2(1.0f));
+          const float2 Gs = mul2(splat2(ds), v3s), Gt = mul2(splat2(dt), v3t);
+          const bool as0 = vs.x > 0.0f && Us.x < thrs.x, as1 = vs.y > 0.0f && Us.y < thrs.y;
+          const bool at0 = vt.x > 0.0f && Ut.x < thrt.x, at1 = vt.y > 0.0f && Ut.y < thrt.y;
+          // inverse gamma (b 2^-32) / G, per SuffOps<float>::ig, every lane
+          const float2 bsf = fma2(make_float2(__uint2float_rn((uint32_t)bs0), __uint2float_rn((uint32_t)bs1)),
+                                  splat2(0x1p-32f),
+                                  make_float2(__uint2float_rn((uint32_t)(bs0 >> 32)),
+                                              __uint2float_rn((uint32_t)(bs1 >> 32))));
+          const float2 btf = fma2(make_float2(__uint2float_rn((uint32_t)bt0), __uint2float_rn((uint32_t)bt1)),
+                                  splat2(0x1p-32f),
+                                  make_float2(__uint2float_rn((uint32_t)(bt0 >> 32)),
+                                              __uint2float_rn((uint32_t)(bt1 >> 32))));
+          const float q0 = bsf.x / Gs.x, r0 = btf.x / Gt.x, q1 = bsf.y / Gs.y, r1 = btf.y / Gt.y;
+          ds0 = !as0; dt0 = !at0; ds1 = v1 && !as1; dt1 = v1 && !at1;
+          if (v1 && as0 && as1) {
+            *reinterpret_cast<float2*>(dst.s2 + d) = make_float2(q0, q1);
+          } else {
+            if (as0) dst.s2[d] = q0;
+            if (v1 && as1) dst.s2[d + 1] = q1;
+          }
+          if (v1 && at0 && at1) {
+            *reinterpret_cast<float2*>(dst.t2 + d) = make_float2(r0, r1);
+          } else {
+            if (at0) dst.t2[d] = r0;
+            if (v1 && at1) dst.t2[d + 1] = r1;
+          }
+        } else {
+          dst.s2[d] = sa.x;
+          dst.t2[d] = ta.x;
+          dst.bs[d] = c0.bs;
+          dst.bt[d] = c0.bt;
+          if (v1) {
+            dst.s2[d + 1] = sa.y;
+            dst.t2[d + 1] = ta.y;
+            dst.bs[d + 1] = c1.bs;
+            dst.bt[d + 1] = c1.bt;
+          }
+        }
+        // adaptive filters: the carried log-weight, 0 after a resampling, else
+        // L_j - m (a trial cycle leaves it alone)
+        if (ess && a.commit) {
+          a.lam[d] = resamp ? (R)0 : a.ell[d] - m;
+          if (v1) a.lam[d + 1] = resamp ? (R)0 : a.ell[d + 1] - m;
+        }
+      }
+      // queue the draws that missed the squeeze (rare), a slot's two at a
+      // time so that the queue never holds more than 95; the warp finishes
+      // them 32 at a time
+      if (__any_sync(0xffffffffu, ds0 || dt0 || ds1 || dt1)) {
+        wq_push(wq, qn, ds0, GammaItem<R>{bs0, Zs.x, Us.x, (uint32_t)j0, 0u}, lane);
+        wq_push(wq, qn, dt0, GammaItem<R>{bt0, Zt.x, Ut.x, (uint32_t)j0, 1u}, lane);
+        wq_drain(wq, qn, 32u, lane, finish);
+        wq_push(wq, qn, ds1, GammaItem<R>{bs1, Zs.y, Us.y, (uint32_t)j1, 0u}, lane);
+        wq_push(wq, qn, dt1, GammaItem<R>{bt1, Zt.y, Ut.y, (uint32_t)j1, 1u}, lane);
+        wq_drain(wq, qn, 32u, lane, finish);
+      }
+    }
+  } else {
   const uint64_t pstride = (uint64_t)G * NT;
   Gathered<R> cur = gather_slot((uint64_t)rank * NT + threadIdx.x);
   for (uint64_t j0 = (uint64_t)rank * NT; j0 < n; j0 += pstride) {
@@ -678,6 +814,7 @@ __device__ __forceinline__ void batch_filter(const BatchArgs<R>& a, const BatchI
       wq_drain(wq, qn, 32u, lane, finish);
     }
     cur = nxt;
+  }
   }
   wq_drain(wq, qn, 1u, lane, finish);
 
